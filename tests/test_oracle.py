@@ -1,0 +1,410 @@
+"""Pins of the FP64 CPU oracle against facts that do not come from the oracle itself.
+
+Each test names what fixes the expected value: a published coefficient table, a library
+routine (numpy.pad wrap mode), the exact Fourier-mode decay factor of the discrete
+operator, telescoping of the flux form (conservation), exact rational arithmetic on tiny
+grids, exactness of linear interpolation on linear data, and layout invariance (Sec. 3.2:
+tiling and the box layout change the access pattern, not the data or the result).
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import coeffs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rel_err(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def whole_domain(N):
+    return [0, 0, 0], [N[0] - 1, N[1] - 1, N[2] - 1]
+
+
+# --------------------------------------------------------------------------- coefficients
+
+def _read_golden_coeffs():
+    rows = {}
+    with open(os.path.join(GOLDEN, "fd_laplacian_coefficients.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            parts = line.split()
+            rows[int(parts[0])] = [Fraction(p) for p in parts[1:]]
+    return rows
+
+
+@pytest.mark.parametrize("R", [1, 2, 3, 4])
+def test_coefficients_match_published_table(R):
+    """Fornberg (1988) Table 1, second-derivative rows: the moment-system solution agrees."""
+    gold = _read_golden_coeffs()[R]
+    c = coeffs.laplacian_coefficients(R)
+    mine = [c[m] for m in range(R, 0, -1)] + [c[0]] + [c[m] for m in range(1, R + 1)]
+    assert mine == gold
+
+
+@pytest.mark.parametrize("R", [1, 2, 4])
+def test_flux_coefficients_telescoping(R):
+    """b_m = sum_{j>=m} c_j, printed values of the survey's reading for R = 2 and 4."""
+    b = coeffs.flux_coefficients(R)
+    expected = {1: [Fraction(1)], 2: [Fraction(15, 12), Fraction(-1, 12)],
+                4: [Fraction(205, 144), Fraction(-127, 720), Fraction(17, 720), Fraction(-1, 560)]}[R]
+    assert b == expected
+
+
+@pytest.mark.parametrize("R", [1, 2, 4])
+def test_symbol_order_of_accuracy(R):
+    """sigma_R(theta) = -theta^2 + O(theta^(2R+2)): the error shrinks by 2^(2R+2) when theta halves."""
+    e1 = abs(coeffs.symbol(R, 0.2) + 0.04)
+    e2 = abs(coeffs.symbol(R, 0.1) + 0.01)
+    ratio = e1 / e2
+    assert abs(math.log2(ratio) - (2 * R + 2)) < 0.2, ratio
+
+
+# --------------------------------------------------------------------------- chop
+
+def test_chop_even_and_remainder():
+    b = oracle.chop([0, 0, 0], [63, 63, 63], 32)
+    assert b.shape == (8, 6)
+    assert b[0].tolist() == [0, 0, 0, 31, 31, 31] and b[1].tolist() == [32, 0, 0, 63, 31, 31]
+    assert b[2].tolist() == [0, 32, 0, 31, 63, 31] and b[7].tolist() == [32, 32, 32, 63, 63, 63]
+    b = oracle.chop([0, 0, 0], [9, 3, 4], 4)
+    sides_x = sorted(set((r[3] - r[0] + 1) for r in b.tolist()))
+    assert sides_x == [2, 4] and b.shape[0] == 3 * 1 * 2
+    cells = sum((r[3] - r[0] + 1) * (r[4] - r[1] + 1) * (r[5] - r[2] + 1) for r in b.tolist())
+    assert cells == 10 * 4 * 5
+
+
+# --------------------------------------------------------------------------- FillBoundary
+
+def _rand(shape, seed=7):
+    return np.random.default_rng(seed).standard_normal(shape)
+
+
+@pytest.mark.parametrize("g", [1, 2, 3])
+def test_fill_single_box_equals_numpy_wrap(g):
+    """One box = the whole periodic domain: FillBoundary is numpy.pad(mode='wrap')."""
+    N = (6, 5, 7)  # Nx, Ny, Nz
+    lo, hi = whole_domain(N)
+    L = oracle.Level([lo + hi], lo, hi, g, 2)
+    dense = _rand((2, N[2], N[1], N[0]))
+    u = L.from_dense(dense)
+    oracle.fill_boundary(L, u)
+    fab = L.fab(u, 0)
+    for c in range(2):
+        np.testing.assert_array_equal(fab[c], np.pad(dense[c], g, mode="wrap"))
+
+
+def _boxes_uneven():
+    # a 12 x 8 x 10 domain cut into 7 unequal boxes that tile it
+    return np.array([
+        [0, 0, 0, 4, 7, 3], [5, 0, 0, 11, 2, 3], [5, 3, 0, 11, 7, 3],
+        [0, 0, 4, 2, 7, 9], [3, 0, 4, 11, 4, 6], [3, 5, 4, 11, 7, 6], [3, 0, 7, 11, 7, 9]], dtype=np.int32)
+
+
+@pytest.mark.parametrize("g", [1, 2])
+def test_fill_multibox_equals_carved_padded_array(g):
+    """Many boxes: every grown FArrayBox equals its window of the wrap-padded global array."""
+    boxes = _boxes_uneven()
+    N = (12, 8, 10)
+    lo, hi = whole_domain(N)
+    L = oracle.Level(boxes, lo, hi, g, 1)
+    dense = _rand((1, N[2], N[1], N[0]), seed=3)
+    u = L.from_dense(dense)
+    oracle.fill_boundary(L, u)
+    padded = np.pad(dense[0], g, mode="wrap")
+    for b, B in enumerate(boxes):
+        win = padded[B[2]:B[5] + 1 + 2 * g, B[1]:B[4] + 1 + 2 * g, B[0]:B[3] + 1 + 2 * g]
+        np.testing.assert_array_equal(L.fab(u, b)[0], win)
+
+
+def test_fill_partial_level_leaves_unowned_ghosts():
+    """A level that does not cover the domain: ghosts owned by no box stay untouched."""
+    N = (16, 16, 16)
+    lo, hi = whole_domain(N)
+    boxes = np.array([[0, 0, 0, 3, 3, 3], [4, 0, 0, 7, 3, 3]], dtype=np.int32)
+    L = oracle.Level(boxes, lo, hi, 1, 1)
+    u = L.from_dense(_rand((1, 16, 16, 16)))
+    n = oracle.fill_boundary(L, u)
+    # box 0's +x face (4 x 4 cells) comes from box 1 and vice versa; the x-periodic wrap of
+    # box 0's -x face is x = 15: unowned.  Edges/corners within the pair: +-y, +-z are unowned.
+    assert n == 2 * 16
+    f0 = L.fab(u, 0)[0]
+    assert np.isnan(f0[0, 0, 0]) and not np.isnan(f0[1, 1, 5])
+
+
+# --------------------------------------------------------------------------- stencil forms
+
+@pytest.mark.parametrize("R", [1, 2, 4])
+def test_flux_form_equals_direct_form(R):
+    N = (16, 16, 16)
+    lo, hi = whole_domain(N)
+    L = oracle.Level(oracle.chop(lo, hi, 8), lo, hi, R, 1)
+    u = L.from_dense(_rand((1, 16, 16, 16), seed=R))
+    oracle.fill_boundary(L, u)
+    a, b = L.alloc(), L.alloc()
+    oracle.stencil(L, R, 0.05, u, a, "flux")
+    oracle.stencil(L, R, 0.05, u, b, "direct")
+    da, db = L.to_dense(a), L.to_dense(b)
+    assert rel_err(da, db) < 1e-13
+
+
+# --------------------------------------------------------------------------- Fourier decay
+
+@pytest.mark.parametrize("R,k", [(1, (1, 2, 3)), (1, (8, 8, 8)), (2, (3, -1, 5)), (2, (8, 1, 8)),
+                                 (4, (2, 5, -7)), (4, (8, 8, 1))])
+def test_single_mode_decays_by_exact_factor(R, k):
+    """u0 = sin(2 pi k.x + phi) at cell centres: after n steps u_n = g^n u0 exactly, with
+    g = 1 + lam * sum_d sigma_R(2 pi k_d / N); k_d = N/2 is the Nyquist mode."""
+    N = 16
+    lo, hi = whole_domain((N, N, N))
+    L = oracle.Level(oracle.chop(lo, hi, 8), lo, hi, R, 1)
+    u0 = synth.single_mode((N, N, N), k)
+    lam = {1: 0.15, 2: 0.1125, 4: 0.09}[R]
+    g = 1.0 + lam * sum(coeffs.symbol(R, 2 * math.pi * kd / N) for kd in k)
+    assert abs(g) <= 1.0
+    # as many steps (<= 40) as keep |g|^n >= 1e-2, so the comparison stays relative to a
+    # solution that has not decayed into rounding noise
+    nsteps = max(1, min(40, int(math.log(1e-2) / math.log(abs(g)))))
+    out = L.to_dense(oracle.advance(L, L.from_dense(u0[None]), R, lam, nsteps))[0]
+    exact = (g ** nsteps) * u0
+    assert rel_err(out, exact) <= 1e-12
+
+
+# --------------------------------------------------------------------------- conservation
+
+@pytest.mark.parametrize("R", [1, 2, 4])
+def test_domain_sum_conserved(R):
+    """Flux form on a periodic level telescopes: the domain sum is invariant up to rounding."""
+    N = 16
+    lo, hi = whole_domain((N, N, N))
+    boxes = oracle.chop(lo, hi, 8)
+    L = oracle.Level(boxes, lo, hi, R, 1)
+    dense = 1.0 + _rand((1, N, N, N), seed=11)
+    u = L.from_dense(dense)
+    s0 = oracle.domain_sum(L, u)
+    nsteps = 30
+    out = oracle.advance(L, u, R, 0.05, nsteps)
+    s1 = oracle.domain_sum(L, out)
+    mass = math.fsum(np.abs(dense).ravel().tolist())
+    assert abs(s1 - s0) <= nsteps * 1e-15 * mass
+
+
+def test_domain_sum_is_correctly_rounded():
+    """fsum cancels exactly where naive summation does not."""
+    L = oracle.Level([[0, 0, 0, 3, 0, 0]], [0, 0, 0], [3, 0, 0], 1, 1)
+    u = L.from_dense(np.array([1e16, 1.0, -1e16, 1.0]).reshape(1, 1, 1, 4))
+    assert oracle.domain_sum(L, u) == 2.0
+
+
+# --------------------------------------------------------------------------- layout invariance
+
+@pytest.mark.parametrize("R", [1, 2])
+def test_layout_invariance_bitwise(R):
+    """The same domain under 1 box, 8 boxes and uneven boxes gives identical bits."""
+    N = (12, 8, 10)
+    lo, hi = whole_domain(N)
+    dense = _rand((2, N[2], N[1], N[0]), seed=5)
+    results = []
+    for boxes in ([lo + hi], oracle.chop(lo, hi, 4), _boxes_uneven()):
+        L = oracle.Level(boxes, lo, hi, R, 2)
+        out = oracle.advance(L, L.from_dense(dense), R, [0.08, 0.03], 7)
+        results.append(L.to_dense(out))
+    for r in results[1:]:
+        np.testing.assert_array_equal(r, results[0])
+
+
+# --------------------------------------------------------------------------- brute force
+
+def _exact_evolve(u, R, lam, nsteps):
+    """Exact rational evolution of the periodic direct-form operator on a global array."""
+    c = coeffs.laplacian_coefficients(R)
+    for _ in range(nsteps):
+        lap = np.zeros_like(u)
+        for ax in range(3):
+            lap = lap + c[0] * u
+            for m in range(1, R + 1):
+                lap = lap + c[m] * (np.roll(u, m, axis=ax) + np.roll(u, -m, axis=ax))
+        u = u + lam * lap
+    return u
+
+
+@pytest.mark.parametrize("N,R,mgs,nsteps", [(4, 1, 2, 4), (6, 1, 3, 3), (6, 2, 3, 3), (8, 4, 4, 2), (8, 2, 8, 3)])
+def test_bruteforce_exact_rational(N, R, mgs, nsteps):
+    """Tiny grids: the FP64 oracle (boxwise, flux form, FillBoundary) against exact rational
+    arithmetic of (I + lam A)^n applied to dyadic data on one periodic array."""
+    rng = np.random.default_rng(N * 10 + R)
+    ints = rng.integers(-64, 64, size=(N, N, N))
+    u0 = np.vectorize(lambda v: Fraction(int(v), 16))(ints).astype(object)
+    lam = Fraction(1, 16)
+    exact = _exact_evolve(u0, R, lam, nsteps)
+    exact_f = np.vectorize(float)(exact).astype(np.float64)
+    lo, hi = whole_domain((N, N, N))
+    L = oracle.Level(oracle.chop(lo, hi, mgs), lo, hi, R, 1)
+    out = L.to_dense(oracle.advance(L, L.from_dense(ints[None] / 16.0), R, float(lam), nsteps))[0]
+    assert float(np.max(np.abs(out - exact_f))) <= 1e-14 * float(np.max(np.abs(exact_f)))
+
+
+# --------------------------------------------------------------------------- AMR pieces
+
+def _fine_setup(Nc=8, gf=1):
+    crse = oracle.Level(oracle.chop([0, 0, 0], [Nc - 1] * 3, 4), [0, 0, 0], [Nc - 1] * 3, 1, 1)
+    fboxes = np.array([[4, 4, 4, 7, 11, 7], [8, 4, 4, 11, 7, 9]], dtype=np.int32)
+    fine = oracle.Level(fboxes, [0, 0, 0], [2 * Nc - 1] * 3, gf, 1)
+    return crse, fine
+
+
+def _level_from_fn(level, N, fn):
+    x = (np.arange(N) + 0.5) / N
+    z, y, xx = np.meshgrid(x, x, x, indexing="ij")
+    return level.from_dense(fn(xx, y, z)[None])
+
+
+def test_interp_reproduces_linear_field_exactly():
+    """Trilinear interpolation is exact on linear data (dyadic values, exact bits), and the
+    time blend at alpha = 1/2 of two linear fields is their mean."""
+    Nc = 8
+    crse, fine = _fine_setup(Nc)
+    f_old = lambda x, y, z: 0.5 + 0.25 * x - 0.75 * y + 0.125 * z
+    f_new = lambda x, y, z: 1.5 - 0.5 * x + 0.25 * y + 0.375 * z
+    c_old, c_new = _level_from_fn(crse, Nc, f_old), _level_from_fn(crse, Nc, f_new)
+    fd = fine.alloc()
+    n = oracle.interp_cf(fine, crse, 2, 0.5, c_old, c_new, fd)
+    xf = (np.arange(2 * Nc) + 0.5) / (2 * Nc)
+    checked = 0
+    for b, B in enumerate(fine.boxes):
+        fab = fine.fab(fd, b)[0]
+        for k in range(B[2] - 1, B[5] + 2):
+            for j in range(B[1] - 1, B[4] + 2):
+                for i in range(B[0] - 1, B[3] + 2):
+                    v = fab[k - B[2] + 1, j - B[1] + 1, i - B[0] + 1]
+                    if np.isnan(v):
+                        continue
+                    x, y, z = xf[i], xf[j], xf[k]
+                    assert v == 0.5 * f_old(x, y, z) + 0.5 * f_new(x, y, z)
+                    checked += 1
+    assert checked == n > 0
+
+
+def test_interp_fills_exactly_the_uncovered_ghosts():
+    """Brute-force coverage count: fine ghosts whose periodic point lies in no fine box."""
+    Nc = 8
+    crse, fine = _fine_setup(Nc)
+    ones = crse.from_dense(np.ones((1, Nc, Nc, Nc)))
+    fd = fine.alloc()
+    n = oracle.interp_cf(fine, crse, 2, 0.0, ones, ones, fd)
+    expect = 0
+    for B in fine.boxes:
+        for k in range(B[2] - 1, B[5] + 2):
+            for j in range(B[1] - 1, B[4] + 2):
+                for i in range(B[0] - 1, B[3] + 2):
+                    inside = B[0] <= i <= B[3] and B[1] <= j <= B[4] and B[2] <= k <= B[5]
+                    if inside:
+                        continue
+                    p = (i % 16, j % 16, k % 16)
+                    covered = any(o[0] <= p[0] <= o[3] and o[1] <= p[1] <= o[4] and o[2] <= p[2] <= o[5]
+                                  for o in fine.boxes)
+                    expect += 0 if covered else 1
+    assert n == expect
+    vals = np.concatenate([fine.fab(fd, b)[0].ravel() for b in range(fine.nbox)])
+    vals = vals[~np.isnan(vals)]
+    assert vals.size == n and np.all(vals == 1.0)
+
+
+def test_interp_weights_at_periodic_wrap():
+    """Near the domain edge the coarse index wraps: a fine box at the corner of the domain
+    interpolating a coarse field constant along each periodic line gets the constant."""
+    Nc = 8
+    crse = oracle.Level(oracle.chop([0, 0, 0], [Nc - 1] * 3, 4), [0, 0, 0], [Nc - 1] * 3, 1, 1)
+    fine = oracle.Level([[0, 0, 0, 3, 3, 3]], [0, 0, 0], [2 * Nc - 1] * 3, 2, 1)
+    c = crse.from_dense(np.full((1, Nc, Nc, Nc), 3.25))
+    fd = fine.alloc()
+    n = oracle.interp_cf(fine, crse, 2, 0.25, c, c, fd)
+    assert n == 8 ** 3 - 4 ** 3
+    vals = fine.fab(fd, 0)[0]
+    assert np.all(vals[~np.isnan(vals)] == 3.25)
+
+
+def test_average_down_of_constant_refinement_is_identity():
+    Nc = 8
+    crse, fine = _fine_setup(Nc)
+    # dyadic values with few significant bits, so that the 8-term sum is exact
+    dense_c = np.random.default_rng(2).integers(-512, 512, size=(1, Nc, Nc, Nc)) / 64.0
+    dense_f = np.repeat(np.repeat(np.repeat(dense_c, 2, axis=1), 2, axis=2), 2, axis=3)
+    fd = fine.from_dense(dense_f)
+    cd = crse.from_dense(dense_c)
+    before = crse.to_dense(cd)
+    n = oracle.average_down(fine, crse, 2, fd, cd)
+    assert n == (2 * 4 * 2) + (2 * 2 * 3)
+    np.testing.assert_array_equal(crse.to_dense(cd), before)
+
+
+def test_average_down_of_linear_field():
+    """The mean of the 8 children of a linear field is its value at the coarse centre."""
+    Nc = 8
+    crse, fine = _fine_setup(Nc)
+    fn = lambda x, y, z: 0.25 + 0.5 * x - 0.25 * y + 0.75 * z
+    fd = _level_from_fn(fine, 2 * Nc, fn)
+    cd = crse.from_dense(np.zeros((1, Nc, Nc, Nc)))
+    oracle.average_down(fine, crse, 2, fd, cd)
+    xc = (np.arange(Nc) + 0.5) / Nc
+    dense = crse.to_dense(cd)[0]
+    for B in fine.boxes:
+        for k in range(B[2] // 2, B[5] // 2 + 1):
+            for j in range(B[1] // 2, B[4] // 2 + 1):
+                for i in range(B[0] // 2, B[3] // 2 + 1):
+                    assert dense[k, j, i] == fn(xc[i], xc[j], xc[k])
+
+
+def test_amr_with_full_fine_cover_equals_fine_single_level():
+    """A fine level covering the whole domain needs no interpolation: after n coarse steps
+    the fine data equal 2n single-level fine steps with lam_f = 2 lam_c, bit for bit, and the
+    coarse data equal the average-down of that fine result."""
+    Nc = 8
+    crse = oracle.Level(oracle.chop([0, 0, 0], [Nc - 1] * 3, 4), [0, 0, 0], [Nc - 1] * 3, 1, 1)
+    fine = oracle.Level(oracle.chop([0, 0, 0], [2 * Nc - 1] * 3, 8), [0, 0, 0], [2 * Nc - 1] * 3, 1, 1)
+    dense_f = _rand((1, 2 * Nc, 2 * Nc, 2 * Nc), seed=9)
+    fd = fine.from_dense(dense_f)
+    cd = crse.from_dense(np.zeros((1, Nc, Nc, Nc)))
+    oracle.average_down(fine, crse, 2, fd, cd)
+    c_out, f_out = oracle.amr_advance(crse, fine, 1, 0.075, cd, fd, 3)
+    f_ref = oracle.advance(fine, fd, 1, 0.15, 6)
+    np.testing.assert_array_equal(fine.to_dense(f_out), fine.to_dense(f_ref))
+    c_ref = crse.from_dense(np.zeros((1, Nc, Nc, Nc)))
+    oracle.average_down(fine, crse, 2, f_ref, c_ref)
+    np.testing.assert_array_equal(crse.to_dense(c_out), crse.to_dense(c_ref))
+
+
+def test_amr_keeps_constant_state():
+    Nc = 8
+    crse, fine = _fine_setup(Nc)
+    cd = crse.from_dense(np.full((1, Nc, Nc, Nc), 2.0))
+    fd = fine.from_dense(np.full((1, 2 * Nc, 2 * Nc, 2 * Nc), 2.0))
+    c_out, f_out = oracle.amr_advance(crse, fine, 1, 0.075, cd, fd, 2)
+    assert np.all(crse.to_dense(c_out) == 2.0)
+    fo = fine.to_dense(f_out)
+    assert np.all(fo[~np.isnan(fo)] == 2.0)
+
+
+# --------------------------------------------------------------------------- workloads
+
+def test_heat64_workload_runs_and_conserves():
+    cfg = synth.WORKLOADS["c1"]
+    N = cfg["N"]
+    lo, hi = whole_domain((N, N, N))
+    L = oracle.Level(oracle.chop(lo, hi, cfg["max_grid_size"]), lo, hi, cfg["ngrow"], 1)
+    u = L.from_dense(synth.initial_field(cfg))
+    lam = 1.0 * synth.dt_for(cfg) * float(N * N)
+    assert abs(lam - 0.15) < 1e-15
+    out = oracle.advance(L, u, 1, lam, cfg["nsteps"])
+    mass = math.fsum(np.abs(L.to_dense(u)).ravel().tolist())
+    assert abs(oracle.domain_sum(L, out) - oracle.domain_sum(L, u)) <= cfg["nsteps"] * 1e-15 * mass
