@@ -408,3 +408,33 @@ def test_heat64_workload_runs_and_conserves():
     out = oracle.advance(L, u, 1, lam, cfg["nsteps"])
     mass = math.fsum(np.abs(L.to_dense(u)).ravel().tolist())
     assert abs(oracle.domain_sum(L, out) - oracle.domain_sum(L, u)) <= cfg["nsteps"] * 1e-15 * mass
+
+
+def test_fill_with_offset_domain_equals_numpy_wrap():
+    """A domain whose lower corner is not the origin: the wrap is relative to domain_lo."""
+    lo, hi = [-3, 2, 5], [2, 6, 11]  # 6 x 5 x 7 cells
+    boxes = oracle.chop(lo, hi, 3)
+    L = oracle.Level(boxes, lo, hi, 2, 1)
+    dense = _rand((1, 7, 5, 6), seed=21)
+    u = L.from_dense(dense)
+    oracle.fill_boundary(L, u)
+    padded = np.pad(dense[0], 2, mode="wrap")
+    for b, B in enumerate(boxes):
+        s = [B[d] - lo[d] for d in range(3)]
+        e = [B[3 + d] - lo[d] + 1 + 4 for d in range(3)]
+        np.testing.assert_array_equal(L.fab(u, b)[0], padded[s[2]:e[2], s[1]:e[1], s[0]:e[0]])
+
+
+def test_average_down_matches_block_mean():
+    """Random fine data: the average-down equals numpy's mean over 2x2x2 blocks."""
+    Nc = 8
+    crse, fine = _fine_setup(Nc)
+    dense_f = _rand((1, 2 * Nc, 2 * Nc, 2 * Nc), seed=4)
+    fd = fine.from_dense(dense_f)
+    cd = crse.from_dense(np.zeros((1, Nc, Nc, Nc)))
+    oracle.average_down(fine, crse, 2, fd, cd)
+    block = dense_f[0].reshape(Nc, 2, Nc, 2, Nc, 2).mean(axis=(1, 3, 5))
+    dense = crse.to_dense(cd)[0]
+    for B in fine.boxes:
+        sl = (slice(B[2] // 2, B[5] // 2 + 1), slice(B[1] // 2, B[4] // 2 + 1), slice(B[0] // 2, B[3] // 2 + 1))
+        np.testing.assert_allclose(dense[sl], block[sl], rtol=0, atol=4e-16 * np.max(np.abs(block)))
