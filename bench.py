@@ -1,0 +1,386 @@
+"""Benchmark of the MultiFab time-step sweep (FillBoundary + flux-form stencil) on GB300.
+
+One bench step = one call of mf_advance over the whole workload: 100 forward-Euler time
+steps of the periodic 256^3 heat equation in 64 boxes of 64^3 with one ghost cell (the
+paper's Sec. 4.1 test scaled to one GPU), every time step a FillBoundary launch and a
+persistent stencil launch, replayed as one CUDA graph.  Metric: cell-updates per second
+including the ghost fill.  The headline runs FP32 storage/arithmetic; the same line also
+reports the FP64 batched sweep and the FP64 plain per-box sweep (Sec. 3.1 untiled MFIter
+baseline) and their ratio.
+
+Timing: CUDA events on the launching stream, W untimed warm-ups, K timed steps, the L2 cache
+flushed (a 512 MB write) before every timed step; max over ranks.  Under torchrun every rank
+runs an independent replica (weak scaling; the sweep has no cross-GPU exchange here).
+
+--impl reference times the FP64 CPU oracle (the plain definition the GPU path is checked
+against) on the host cores: one bench step = one oracle time step of the same 256^3 grid.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+WORKLOAD = "c2"
+METRIC = "cell-updates/s per step incl. ghost fill"
+UNIT = "cell-updates/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--dtype", default="f32", choices=["f32", "f64", "bf16"])
+    p.add_argument("--no-extras", action="store_true", help="headline only (no FP64, e2e, CPU baseline)")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_config(cfg):
+    N = cfg["N"]
+    return {"workload": "%s: periodic %d^3, %d boxes of %d^3, ngrow %d, %d comp, 7-point flux-form heat "
+                        "stencil, %d time steps per bench step" % (cfg["name"], N, (N // cfg["max_grid_size"]) ** 3,
+                                                                   cfg["max_grid_size"], cfg["ngrow"], cfg["ncomp"],
+                                                                   cfg["nsteps"]),
+            "domain": N, "max_grid_size": cfg["max_grid_size"], "ngrow": cfg["ngrow"], "ncomp": cfg["ncomp"],
+            "stencil_radius": cfg["R"], "time_steps_per_bench_step": cfg["nsteps"],
+            "initial_data": "8 seeded sine modes, |k_d| in 1..16",
+            "l2": "flushed (512 MB write) before every timed bench step; per-step working set "
+                  "(two time levels incl. ghosts) %.0f MB (FP32)"}
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ reference arm (oracle on the host)
+
+def run_reference(args, cfg):
+    import oracle
+    N = cfg["N"]
+    lo, hi = [0, 0, 0], [N - 1] * 3
+    L = oracle.Level(oracle.chop(lo, hi, cfg["max_grid_size"]), lo, hi, cfg["ngrow"], cfg["ncomp"])
+    u = L.from_dense(synth.initial_field(cfg))
+    lam = 1.0 * synth.dt_for(cfg) * float(N * N)
+    for _ in range(args.warmup):
+        u = oracle.advance(L, u, cfg["R"], lam, 1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        u = oracle.advance(L, u, cfg["R"], lam, 1)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    V = N ** 3
+    value = V * args.steps / total
+    sample = "one FP64 oracle time step (FillBoundary + flux-form stencil) of the %d^3 / %d-box grid per bench " \
+             "step, single-threaded C (gcc -O2)" % (N, (N // cfg["max_grid_size"]) ** 3)
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": workload_config(cfg),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def cpu_baseline(cfg, budget_s=15.0):
+    import oracle
+    N = cfg["N"]
+    lo, hi = [0, 0, 0], [N - 1] * 3
+    L = oracle.Level(oracle.chop(lo, hi, cfg["max_grid_size"]), lo, hi, cfg["ngrow"], cfg["ncomp"])
+    u = L.from_dense(synth.initial_field(cfg))
+    lam = 1.0 * synth.dt_for(cfg) * float(N * N)
+    t0 = time.perf_counter()
+    u = oracle.advance(L, u, cfg["R"], lam, 1)
+    t1 = time.perf_counter() - t0
+    n = max(1, min(cfg["nsteps"], int(budget_s / max(t1, 1e-3)) - 1))
+    t0 = time.perf_counter()
+    oracle.advance(L, u, cfg["R"], lam, n)
+    t = time.perf_counter() - t0
+    return {"value": N ** 3 * n / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d of the %d FP64 time steps of the %d^3 / %d-box workload, single-threaded C oracle "
+                      "(gcc -O2 -ffp-contract=off) on the GPU host" % (n, cfg["nsteps"], N,
+                                                                         (N // cfg["max_grid_size"]) ** 3)}
+
+
+# ------------------------------------------------------------------ our arm
+
+def src_hash():
+    h = hashlib.sha256()
+    p = os.path.join(ROOT, "paper_1604_03570_gb300", "csrc", "mf_kernels.cu")
+    with open(p, "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel, workload_key, dtype):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
+    kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    rec = t.get("%s|%s|%s" % (kernel, workload_key, dtype))
+    if not rec or rec.get("src_sha") != src_hash():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def time_advances(mfab, R, D, dt, nsteps, K, flush, flags=0):
+    import torch
+    import paper_1604_03570_gb300 as mf
+    s = mfab.stream
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for k in range(K):
+        flush()
+        ev[k][0].record(s)
+        mf.mf_advance(mfab.h, R, D, dt, nsteps, flags)
+        ev[k][1].record(s)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def run_ours(args, cfg, ws, rank, local):
+    import torch
+    import paper_1604_03570_gb300 as mf
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    N, R, nsteps = cfg["N"], cfg["R"], cfg["nsteps"]
+    lo, hi = [0, 0, 0], [N - 1] * 3
+    D = [1.0] * cfg["ncomp"]
+    dt = synth.dt_for(cfg)
+    V = N ** 3
+    dense = synth.initial_field(cfg)
+    flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def flush():
+        flush_buf.fill_(1)
+
+    def level(dtype):
+        m = mf.MultiFab(lo, hi, max_grid_size=cfg["max_grid_size"], ncomp=cfg["ncomp"], ngrow=cfg["ngrow"],
+                        dtype=dtype)
+        m.from_host(dense)
+        return m
+
+    # ---- headline: batched, graph-captured sweep
+    head = level(args.dtype)
+    for _ in range(args.warmup):
+        mf.mf_advance(head.h, R, D, dt, nsteps)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        times = time_advances(head, R, D, dt, nsteps, args.steps, flush)
+    torch.cuda.synchronize()
+    total_ms = sum(times)
+    if dist:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    value = ws * V * nsteps * args.steps / (total_ms * 1e-3)
+    tile, _ = mf.mf_get_tile(head.h)
+
+    # ---- roofline of the dominant kernel (stencil) from events inside the graph
+    mf.mf_set_timing(head.h, 1)
+    for _ in range(2):
+        mf.mf_advance(head.h, R, D, dt, nsteps)
+    fill_ms = st_ms = 0.0
+    tim_total = time_advances(head, R, D, dt, nsteps, 1, flush)  # recapture + warm
+    fill_ms, st_ms = 0.0, 0.0
+    t_timed = []
+    for _ in range(args.steps):
+        t_timed += time_advances(head, R, D, dt, nsteps, 1, flush)
+        a, b = mf.mf_phase_ms(head.h)
+        fill_ms += a
+        st_ms += b
+    mf.mf_set_timing(head.h, 0)
+    launches = args.steps * nsteps
+    st_avg_s = st_ms * 1e-3 / launches
+    fill_avg_s = fill_ms * 1e-3 / launches
+    S = {"f64": 8, "f32": 4, "bf16": 2}[args.dtype]
+    nbox = (N // cfg["max_grid_size"]) ** 3
+    b = cfg["max_grid_size"]
+    G = mf.mf_fb_regions(head.h)[1]
+    st_bytes = S * cfg["ncomp"] * (2 * V + nbox * 6 * R * b * b)
+    fill_bytes = S * cfg["ncomp"] * 2 * G
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    achieved = st_bytes / st_avg_s / 1e9
+    roof = {"bound": "hbm", "kernel": "k_stencil<%s,R=%d>" % (args.dtype, R), "achieved": achieved, "peak": hbm,
+            "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,
+            "traffic": traffic_for("k_stencil", WORKLOAD, args.dtype),
+            "algorithmic_bytes_per_launch": st_bytes, "avg_launch_us": st_avg_s * 1e6,
+            "fill_kernel": {"achieved": fill_bytes / fill_avg_s / 1e9, "algorithmic_bytes_per_launch": fill_bytes,
+                            "avg_launch_us": fill_avg_s * 1e6},
+            "step_bytes": mf.mf_step_bytes(head.h, R),
+            "step_frac": mf.mf_step_bytes(head.h, R) * nsteps * args.steps / (total_ms * 1e-3) / 1e9 / hbm,
+            "fill_fraction": fill_ms / (fill_ms + st_ms),
+            "timed_with_events_ms_per_step": sum(t_timed) / len(t_timed)}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+           "config": workload_config(cfg), "roofline": roof, "gpu_launches": 2 * nsteps * args.steps,
+           "tile": list(tile)}
+    out["config"]["l2"] = out["config"]["l2"] % (2 * mf.mf_bytes(head.h) / 2 / 1e6)
+    out["clocks"] = clk.summary()
+
+    if not args.no_extras:
+        # ---- e2e through the public API with pinned host buffers
+        pin_in = torch.from_numpy(dense).pin_memory()
+        pin_out = torch.empty(dense.shape, dtype=torch.float64).pin_memory()
+        e2e_t = []
+        for k in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            mf.mf_copy_from_host(head.h, pin_in)
+            mf.mf_advance(head.h, R, D, dt, nsteps)
+            mf.mf_copy_to_host(head.h, pin_out)
+            t1 = time.perf_counter()
+            if k >= args.warmup:
+                e2e_t.append(t1 - t0)
+        e2e_s = sum(e2e_t)
+        if dist:
+            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        out["e2e"] = {"value": ws * V * nsteps * args.steps / e2e_s, "unit": UNIT,
+                      "h2d_bytes_per_step": int(dense.nbytes), "d2h_bytes_per_step": int(dense.nbytes)}
+        del head
+        # ---- FP64 batched and FP64 plain per box
+        k2 = max(2, args.steps // 2)
+        f64 = level("f64")
+        for _ in range(2):
+            mf.mf_advance(f64.h, R, D, dt, nsteps)
+        t64 = time_advances(f64, R, D, dt, nsteps, k2, flush)
+        v64 = V * nsteps * k2 / (sum(t64) * 1e-3)
+        tile64, _ = mf.mf_get_tile(f64.h)
+        del f64
+        plain = level("f64")
+        mf.mf_advance(plain.h, R, D, dt, nsteps, mf.MF_PLAIN_PER_BOX)
+        tp = time_advances(plain, R, D, dt, nsteps, 2, flush, mf.MF_PLAIN_PER_BOX)
+        vplain = V * nsteps * 2 / (sum(tp) * 1e-3)
+        del plain
+        out["fp64_batched"] = {"value": v64, "unit": UNIT, "tile": list(tile64),
+                               "frac_of_hbm": (8 * (2 * V + 2 * G) + 8 * nbox * 6 * b * b) * nsteps * k2
+                               / (sum(t64) * 1e-3) / 1e9 / hbm}
+        out["fp64_plain_per_box"] = {"value": vplain, "unit": UNIT,
+                                     "launches_per_time_step": 2 * nbox}
+        out["speedup_batched_vs_fp64_plain_per_box"] = value / vplain
+        if rank == 0 and ws == 1:
+            out["cpu_baseline"] = cpu_baseline(cfg)
+    elif "e2e" not in out:
+        out["e2e"] = None
+    if dist:
+        dist.destroy_process_group()
+    return out if rank == 0 else None
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    cfg = dict(synth.WORKLOADS[WORKLOAD])
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        print(json.dumps(run_reference(args, cfg)))
+        return 0
+    out = run_ours(args, cfg, ws, rank, local)
+    if out is not None:
+        print(json.dumps(out))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,197 @@
+/*
+ * mf.h -- C ABI of the GB300 MultiFab time-step sweep (libmf.so).
+ *
+ * The objects follow arXiv 1604.03570 ("BoxLib with Tiling"):
+ *   Box        a rectangle of cells in index space, six integers (Sec. 3.1).
+ *   FArrayBox  the data of one box grown by the ghost width, ncomp components, stored with
+ *              x fastest, then y, z, component (Sec. 3.1).
+ *   MultiFab   all FArrayBoxes of one level (Sec. 3.1, Fig. 1); here one handle per level,
+ *              living on one GPU.
+ *   MFIter     the loop over boxes, or over logical tiles of boxes (Sec. 3.2); here a
+ *              device work list of (box, component, tile) entries consumed by persistent kernels.
+ *
+ * Conventions for every call:
+ *   - Boxes are int[6] = {lo0, lo1, lo2, hi0, hi1, hi2}, inclusive bounds, in the index space
+ *     of the level's domain.  The domain is periodic in x, y and z.  Cells are cubes of side
+ *     dx = 1/N_x (N_x cells along x), so an N^3 domain is the unit cube.
+ *   - Return 0 on success, a negative MF_E* code on error; mf_last_error() then gives a
+ *     message (thread-local).  No call aborts the process.
+ *   - Field memory is owned by the caller (e.g. allocated by PyTorch) and attached with
+ *     mf_attach; it must outlive the handle.  The library allocates small device metadata
+ *     (intersection and work lists, reduction partials) inside mf_attach and never again
+ *     while advancing, so mf_advance can be captured and replayed as a CUDA graph.
+ *   - Every call that touches field data is asynchronous on the attached stream, except
+ *     mf_sum, mf_copy_to_host and mf_copy_fab_to_host, which synchronise that stream.
+ *   - Host pointers passed in are only read during the call.
+ */
+#ifndef MF_H
+#define MF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mf mf_t;
+
+/* Storage type of the field.  F64 computes in FP64; F32 and BF16 compute in FP32. */
+typedef enum { MF_F64 = 0, MF_F32 = 1, MF_BF16 = 2 } mf_dtype;
+
+/* Centred (2R+1)-point Laplacian of order 2R per direction; the value is the radius R.
+ * R = 1 is the paper's second-order heat kernel (Sec. 4.1, 7-point star); R = 4 is the
+ * 9-cell-wide 8th-order stencil of the SMC code (Sec. 4.2, 25-point star). */
+typedef enum { MF_LAP2_7PT = 1, MF_LAP4_13PT = 2, MF_LAP8_25PT = 4 } mf_stencil_kind;
+
+/* mf_stencil.flags */
+enum {
+    MF_FP64_DIFF = 1,     /* FP32/BF16 storage: compute the flux differences in FP64 */
+    MF_PLAIN_PER_BOX = 2  /* the untiled baseline of Sec. 3.1: one launch per box per phase,
+                             launched eagerly, no work list, no graph */
+};
+
+typedef struct {
+    int kind;                  /* mf_stencil_kind */
+    const double *diffusivity; /* [ncomp] D_c > 0 */
+    int flags;                 /* MF_FP64_DIFF | MF_PLAIN_PER_BOX */
+} mf_stencil;
+
+/* Error codes */
+enum {
+    MF_OK = 0,
+    MF_EINVAL = -1,     /* bad argument: box outside the domain, overlapping boxes, bad sizes */
+    MF_ENOMEM = -2,     /* host or device allocation failed */
+    MF_ECUDA = -3,      /* a CUDA runtime call failed (message has the CUDA error string) */
+    MF_EUNSTABLE = -4,  /* lam * 3 * |sigma_R(pi)| > 2: forward Euler would blow up */
+    MF_EALIGN = -5,     /* attached pointer not 256-byte aligned or buffer too small */
+    MF_ESTATE = -6      /* operation needs an attached handle (or a missing setup step) */
+};
+
+/*
+ * mf_create -- a level whose boxes chop the domain [domain_lo, domain_hi] into pieces of
+ * max_grid_size cells per side (the last piece along a direction takes the remainder).
+ * Box order: x fastest, then y, then z.  Sec. 3: a level is a union of non-intersecting
+ * grids; Sec. 3.1: MultiFab.  ngrow >= 0 ghost cells per side, 1 <= ncomp <= 16.
+ * The handle is created on the host only; no CUDA call is made.
+ */
+int mf_create(mf_t **out, const int domain_lo[3], const int domain_hi[3], int max_grid_size,
+              int ncomp, int ngrow, int dtype);
+
+/*
+ * mf_create_boxes -- a level from an explicit box list (nboxes * 6 ints).  Boxes must lie in
+ * the domain and must not overlap; they need not cover the domain (a refined level, Sec. 3:
+ * "not necessarily of equal size and shape", "do not necessarily span the entire domain").
+ */
+int mf_create_boxes(mf_t **out, const int domain_lo[3], const int domain_hi[3], const int *boxes,
+                    int nboxes, int ncomp, int ngrow, int dtype);
+
+void mf_destroy(mf_t *mf);
+
+/* Layout queries (host only). */
+int mf_nboxes(const mf_t *mf);
+int mf_get_boxes(const mf_t *mf, int *boxes /* nboxes*6 */);
+/* Bytes of device memory mf_attach needs: two time levels of all FArrayBoxes, each
+ * FArrayBox 256-byte aligned, rows padded so that every valid row starts 16-byte aligned. */
+size_t mf_bytes(const mf_t *mf);
+/* Number of FillBoundary copy regions (box-box intersections incl. periodic images) and
+ * the number of ghost cells per component they write. */
+long long mf_fb_regions(const mf_t *mf, long long *ghost_cells_out);
+/* Copies up to max regions as 11 ints each: {dst box, src box, dst lo[3] (global index,
+ * may lie outside the domain), src lo[3] (inside the domain), extent[3]}. */
+long long mf_get_fb_regions(const mf_t *mf, int *out, long long max);
+
+/*
+ * mf_attach -- give the handle its field memory (mf_bytes(mf) bytes, 256-byte aligned, device
+ * memory of the current device) and the CUDA stream (cudaStream_t, may be NULL for the
+ * legacy stream) every later call runs on.  Builds and uploads the FillBoundary list and the
+ * tile work list.  May be called again to move the handle to another buffer or stream.
+ */
+int mf_attach(mf_t *mf, void *dev_ptr, size_t bytes, void *cuda_stream);
+
+/* Tile shape of the stencil sweep (Sec. 3.2 MFIter(mf, tilesize)); tile[d] <= 0 along a
+ * direction means "whole box".  tile == NULL selects the autotuner on the next advance. */
+int mf_set_tile(mf_t *mf, const int tile[3]);
+int mf_get_tile(const mf_t *mf, int tile[3]);
+
+/*
+ * Dense host arrays are (ncomp, Nz, Ny, Nx) doubles over the whole domain, x fastest.
+ * mf_copy_from_host writes the valid cells of every box of the current time level
+ * (ghosts unchanged); cells of the dense array outside every box are ignored.
+ * mf_copy_to_host writes every dense cell: valid data where a box covers it, NaN elsewhere.
+ * Both convert to/from the storage type on the GPU and stage through the non-current time
+ * level, which they overwrite.
+ */
+int mf_copy_from_host(mf_t *mf, const double *dense);
+int mf_copy_to_host(mf_t *mf, double *dense);
+
+/* One FArrayBox including ghosts, (ncomp, nz+2g, ny+2g, nx+2g) doubles, current time level. */
+int mf_copy_fab_to_host(mf_t *mf, int box, double *out);
+int mf_copy_fab_from_host(mf_t *mf, int box, const double *in);
+
+/*
+ * mf_fill_boundary -- Sec. 3.1 mf.FillBoundary(): every ghost cell of every FArrayBox of the
+ * current time level (faces, edges and corners) takes the value of the valid cell that owns
+ * the same point of the periodic domain.  One fused copy kernel over the precomputed
+ * intersection list.  Ghost cells no box owns are left unchanged.
+ */
+int mf_fill_boundary(mf_t *mf);
+
+/*
+ * mf_interp_cf -- coarse-to-fine ghost interpolation between AMR levels (Sec. 3; ratio 2 or
+ * 4).  Every ghost cell of the fine level's current time level whose point lies in no fine
+ * box gets the trilinear interpolant of the coarse data, each coarse value taken as
+ * (1 - alpha) * crse_old + alpha * crse_new (current time levels of the two handles, which
+ * may be the same handle).  The coarse level must cover its domain, have ngrow >= 1, have
+ * its ghosts filled, and fine domain = ratio * coarse domain.  Runs on the fine handle's stream.
+ */
+int mf_interp_cf(mf_t *fine, const mf_t *crse_old, const mf_t *crse_new, double alpha, int ratio);
+
+/* mf_average_down -- every coarse valid cell whose children are all fine valid cells becomes
+ * their mean (current time levels).  Runs on the coarse handle's stream. */
+int mf_average_down(const mf_t *fine, mf_t *crse, int ratio);
+
+/*
+ * mf_advance -- nsteps forward-Euler steps of u_t = D_c Lap u (Sec. 4.1): each step is
+ * FillBoundary on the current level, then the flux-form stencil (face fluxes, then their
+ * divergence) from the current into the other time level, then the two swap.  All boxes and
+ * tiles go through one persistent launch per phase; the whole advance is captured once as a
+ * CUDA graph and replayed.  With MF_PLAIN_PER_BOX it runs the untiled per-box baseline.
+ * lam_c = D_c dt / dx^2 = D_c dt N_x^2.  Returns MF_EUNSTABLE if max_c lam_c * 3 |sigma_R(pi)| > 2.
+ */
+int mf_advance(mf_t *mf, const mf_stencil *st, double dt, int nsteps);
+
+/*
+ * mf_amr_advance -- two-level subcycled advance (fine = crse refined by ratio): per coarse step,
+ * FillBoundary + stencil on the coarse level; then nsub fine substeps of dt/nsub, each
+ * FillBoundary + coarse-fine interpolation at alpha = s/nsub + stencil; then average-down
+ * onto the new coarse level.  Both levels must have the same dtype and ncomp.  No refluxing.
+ */
+int mf_amr_advance(mf_t *crse, mf_t *fine, const mf_stencil *st, double dt_crse, int ncrse_steps, int nsub,
+                   int ratio);
+
+/* mf_sum -- sum of component comp over all valid cells of the current time level, FP64 with
+ * compensated (Neumaier) accumulation; synchronises the stream.  Sec. 3.1 whole-level
+ * reduction (the paper's example is mf.max(0)). */
+int mf_sum(mf_t *mf, int comp, double *out);
+
+/* Algorithmic bytes per step of the sweep: S*C*(2V + 2G + G_face) (valid cells read and
+ * written, ghost cells copied, face ghosts read by the stencil of radius R). */
+double mf_step_bytes(const mf_t *mf, int R);
+
+/* Phase timing (Sec. 4.1 times the ghost fill and the kernel separately): when on, the
+ * graph of mf_advance also records CUDA events between the launches; mf_phase_ms then
+ * returns the summed device time of the FillBoundary launches (out[0]) and of the stencil
+ * launches (out[1]) of the last mf_advance, waiting for it to finish. */
+int mf_set_timing(mf_t *mf, int on);
+int mf_phase_ms(mf_t *mf, double out[2]);
+
+/* Which time level (0 or 1) is current. */
+int mf_current(const mf_t *mf);
+
+const char *mf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MF_H */

@@ -1,0 +1,1193 @@
+// mf_host.cpp -- host side of libmf: Box algebra, FArrayBox layout, FillBoundary
+// intersection lists, tile work lists, coarse-fine lists, CUDA-graph capture and the
+// extern "C" entry points declared in include/mf.h.
+//
+// Correspondence with arXiv 1604.03570:
+//   Box / BoxArray chop          Sec. 3 (levels of non-intersecting grids), Sec. 3.1 (Box)
+//   FArrayBox layout             Sec. 3.1 (contiguous, x fastest, ghost cells around the box)
+//   FillBoundary metadata        Sec. 3.1 / 3.3: box-box intersections with every periodic
+//                                image, computed once per BoxArray (their cost grows with the
+//                                number of boxes, Sec. 3.3), via a uniform bin hash
+//   MFIter / tilebox()           Sec. 3.2: tiles of a given size from each box's lower corner,
+//                                the last tile along a direction smaller; flattened into one
+//                                device work list for all boxes
+//   thread-private arenas        Sec. 3.3: nothing allocates while advancing; every list and
+//                                scratch buffer is sized at attach
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/mf.h"
+#include "mf_internal.h"
+
+using namespace mfk;
+
+// ------------------------------------------------------------------ errors
+
+static thread_local std::string g_err;
+
+static int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CU(call)                                                                                 \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) return fail(MF_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));   \
+    } while (0)
+
+// ------------------------------------------------------------------ boxes
+
+struct Box {
+    int lo[3], hi[3];
+    bool empty() const { return lo[0] > hi[0] || lo[1] > hi[1] || lo[2] > hi[2]; }
+    long long cells() const {
+        return empty() ? 0 : (long long)(hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1);
+    }
+    int len(int d) const { return hi[d] - lo[d] + 1; }
+    bool contains(int i, int j, int k) const {
+        return i >= lo[0] && i <= hi[0] && j >= lo[1] && j <= hi[1] && k >= lo[2] && k <= hi[2];
+    }
+};
+
+static Box intersect(const Box &a, const Box &b) {
+    Box r;
+    for (int d = 0; d < 3; ++d) {
+        r.lo[d] = std::max(a.lo[d], b.lo[d]);
+        r.hi[d] = std::min(a.hi[d], b.hi[d]);
+    }
+    return r;
+}
+static Box grow(const Box &a, int g) {
+    Box r = a;
+    for (int d = 0; d < 3; ++d) { r.lo[d] -= g; r.hi[d] += g; }
+    return r;
+}
+static Box shift(const Box &a, const int s[3]) {
+    Box r = a;
+    for (int d = 0; d < 3; ++d) { r.lo[d] += s[d]; r.hi[d] += s[d]; }
+    return r;
+}
+static int floor_div(int a, int b) {
+    int q = a / b;
+    if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
+    return q;
+}
+static Box coarsen(const Box &a, int r) {
+    Box c;
+    for (int d = 0; d < 3; ++d) { c.lo[d] = floor_div(a.lo[d], r); c.hi[d] = floor_div(a.hi[d], r); }
+    return c;
+}
+
+// Uniform bin hash over the domain: each box is registered in every bin it touches.
+struct BinHash {
+    Box dom;
+    int bs = 1, nb[3] = {1, 1, 1};
+    std::vector<std::vector<int>> bins;
+    void build(const Box &domain, const std::vector<Box> &boxes) {
+        dom = domain;
+        int maxlen = 1;
+        for (auto &b : boxes) for (int d = 0; d < 3; ++d) maxlen = std::max(maxlen, b.len(d));
+        bs = std::max(8, maxlen);
+        for (int d = 0; d < 3; ++d) nb[d] = (dom.len(d) + bs - 1) / bs;
+        bins.assign((size_t)nb[0] * nb[1] * nb[2], {});
+        for (int i = 0; i < (int)boxes.size(); ++i) {
+            Box c = intersect(boxes[i], dom);
+            if (c.empty()) continue;
+            int l[3], h[3];
+            for (int d = 0; d < 3; ++d) {
+                l[d] = (c.lo[d] - dom.lo[d]) / bs;
+                h[d] = (c.hi[d] - dom.lo[d]) / bs;
+            }
+            for (int z = l[2]; z <= h[2]; ++z)
+                for (int y = l[1]; y <= h[1]; ++y)
+                    for (int x = l[0]; x <= h[0]; ++x) bins[((size_t)z * nb[1] + y) * nb[0] + x].push_back(i);
+        }
+    }
+    // Boxes that may intersect q (q clipped to the domain), each once.
+    void query(const Box &q, std::vector<int> &out, std::vector<int> &stamp, int tag) const {
+        out.clear();
+        Box c = intersect(q, dom);
+        if (c.empty()) return;
+        int l[3], h[3];
+        for (int d = 0; d < 3; ++d) {
+            l[d] = (c.lo[d] - dom.lo[d]) / bs;
+            h[d] = (c.hi[d] - dom.lo[d]) / bs;
+        }
+        for (int z = l[2]; z <= h[2]; ++z)
+            for (int y = l[1]; y <= h[1]; ++y)
+                for (int x = l[0]; x <= h[0]; ++x)
+                    for (int i : bins[((size_t)z * nb[1] + y) * nb[0] + x])
+                        if (stamp[i] != tag) { stamp[i] = tag; out.push_back(i); }
+    }
+};
+
+// ------------------------------------------------------------------ device buffers
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    ~DevBuf() { if (p) cudaFree(p); }
+    int ensure(size_t n) {
+        if (n <= bytes && p) return 0;
+        if (p) { cudaFree(p); p = nullptr; bytes = 0; }
+        if (n == 0) n = 16;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e != cudaSuccess) { p = nullptr; return fail(MF_ENOMEM, "cudaMalloc(%zu): %s", n, cudaGetErrorString(e)); }
+        bytes = n;
+        return 0;
+    }
+    template <typename T> int upload(const std::vector<T> &v, cudaStream_t s) {
+        int rc = ensure(std::max<size_t>(16, v.size() * sizeof(T)));
+        if (rc) return rc;
+        if (!v.empty()) CU(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+        return 0;
+    }
+};
+
+struct GraphExec {
+    cudaGraphExec_t exec = nullptr;
+    ~GraphExec() { if (exec) cudaGraphExecDestroy(exec); }
+};
+
+// ------------------------------------------------------------------ the handle
+
+struct InterpPlan {
+    const mf_t *crse = nullptr;
+    int ratio = 0;
+    std::vector<InterpRun> runs;
+    DevBuf d_runs;
+};
+struct AvgPlan {
+    const mf_t *fine = nullptr;
+    int ratio = 0;
+    std::vector<AvgRegion> regs;
+    DevBuf d_regs;
+};
+
+struct mf {
+    Box domain;
+    std::vector<Box> boxes;
+    int ncomp = 1, ngrow = 0, dtype = F64, esize = 8;
+    // layout
+    std::vector<FabInfo> fabs;     // level slot 0
+    std::vector<long long> fab_start;  // element offset of each FArrayBox's allocation
+    size_t level_elems = 0;        // elements per time level (multiple of 256 bytes)
+    // FillBoundary
+    std::vector<FbEntry> fb;
+    std::vector<FbTask> fbtasks;
+    long long ghost_cells = 0;     // per component
+    std::vector<int> fb_group;     // first entry of each destination box (size nbox+1)
+    std::vector<int> fb_cbeg;      // cells before entry within its destination-box group
+    std::vector<std::array<int, 6>> fb_corner;  // global lower corners: dst (may lie outside
+                                                // the domain), then src
+    // tiles
+    int tile[3] = {0, 0, 0};
+    bool tile_auto = true;
+    std::vector<Tile> tiles;
+    int block[2] = {32, 8};
+    // attach
+    char *base = nullptr;
+    size_t bytes = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;    // private stream for graph capture
+    int cur = 0;
+    bool attached = false;
+    DevBuf d_fabs, d_fb, d_fbtasks, d_tiles, d_cbeg, d_partials, d_sumout;
+    double *h_sum = nullptr;       // pinned
+    size_t tile_capacity = 0;
+    std::map<std::string, std::unique_ptr<GraphExec>> graphs;
+    // phase timing: events recorded inside the captured graph around every launch
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;   // 2*nsteps+1 of the last timed advance
+    int ev_used = 0;
+    std::vector<std::unique_ptr<InterpPlan>> interp;
+    std::vector<std::unique_ptr<AvgPlan>> avg;
+    ~mf() {
+        graphs.clear();
+        for (auto e : ev) cudaEventDestroy(e);
+        if (cap) cudaStreamDestroy(cap);
+        if (h_sum) cudaFreeHost(h_sum);
+    }
+    void *level_ptr(int which) const { return base + (size_t)which * level_elems * esize; }
+};
+
+// ------------------------------------------------------------------ layout
+
+static void build_layout(mf_t *m) {
+    const int g = m->ngrow, S = m->esize;
+    const int A = 16 / S;                  // elements per 16 bytes
+    const long long align = 256 / S;       // FArrayBox start alignment in elements
+    long long off = 0;
+    m->fabs.clear();
+    m->fab_start.clear();
+    for (auto &b : m->boxes) {
+        FabInfo f{};
+        for (int d = 0; d < 3; ++d) { f.n[d] = b.len(d); f.lo[d] = b.lo[d]; }
+        const int fpad = (A - g % A) % A;  // puts x = lo on a 16-byte boundary
+        f.px = (int)(((long long)fpad + f.n[0] + 2 * g + A - 1) / A * A);
+        const long long py = f.n[1] + 2 * g, nzg = f.n[2] + 2 * g;
+        f.plane = (long long)f.px * py;
+        f.cstride = f.plane * nzg;
+        off = (off + align - 1) / align * align;
+        m->fab_start.push_back(off);
+        f.org = off + g * f.plane + (long long)g * f.px + fpad + g;
+        f.level = 0;
+        m->fabs.push_back(f);
+        off += f.cstride * m->ncomp;
+    }
+    off = (off + align - 1) / align * align;
+    m->level_elems = (size_t)off;
+}
+
+static long long elem_at(const FabInfo &f, int i, int j, int k) {  // global (i,j,k), comp 0
+    return f.org + (long long)(k - f.lo[2]) * f.plane + (long long)(j - f.lo[1]) * f.px + (i - f.lo[0]);
+}
+
+// ------------------------------------------------------------------ FillBoundary list
+
+static int build_fb(mf_t *m) {
+    const int nb = (int)m->boxes.size(), g = m->ngrow;
+    m->fb.clear();
+    m->fbtasks.clear();
+    m->fb_group.assign(nb + 1, 0);
+    m->fb_cbeg.clear();
+    m->fb_corner.clear();
+    m->ghost_cells = 0;
+    if (g == 0) return 0;
+    BinHash hash;
+    hash.build(m->domain, m->boxes);
+    std::vector<int> cand, stamp(nb, -1);
+    int tag = 0;
+    const int L[3] = {m->domain.len(0), m->domain.len(1), m->domain.len(2)};
+    for (int b = 0; b < nb; ++b) {
+        m->fb_group[b] = (int)m->fb.size();
+        const Box gb = grow(m->boxes[b], g);
+        int cells_in_group = 0;
+        for (int sz = -1; sz <= 1; ++sz)
+            for (int sy = -1; sy <= 1; ++sy)
+                for (int sx = -1; sx <= 1; ++sx) {
+                    const int s[3] = {sx * L[0], sy * L[1], sz * L[2]};
+                    const int ms[3] = {-s[0], -s[1], -s[2]};
+                    const Box q = shift(gb, ms);  // the grown box seen from the periodic image
+                    hash.query(q, cand, stamp, ++tag);
+                    std::sort(cand.begin(), cand.end());
+                    for (int a : cand) {
+                        if (a == b && sx == 0 && sy == 0 && sz == 0) continue;
+                        const Box src = intersect(m->boxes[a], q);
+                        if (src.empty()) continue;
+                        const Box dst = shift(src, s);
+                        FbEntry e{};
+                        for (int d = 0; d < 3; ++d) e.n[d] = src.len(d);
+                        e.sfab = a;
+                        e.dfab = b;
+                        e.level = 0;
+                        e.src = elem_at(m->fabs[a], src.lo[0], src.lo[1], src.lo[2]);
+                        e.dst = elem_at(m->fabs[b], dst.lo[0], dst.lo[1], dst.lo[2]);
+                        const long long cells = src.cells() * m->ncomp;
+                        if (cells > 0x7fffffffLL) return fail(MF_EINVAL, "ghost region too large");
+                        m->fb_cbeg.push_back(cells_in_group);
+                        m->fb_corner.push_back({dst.lo[0], dst.lo[1], dst.lo[2], src.lo[0], src.lo[1], src.lo[2]});
+                        cells_in_group += (int)cells;
+                        m->ghost_cells += src.cells();
+                        m->fb.push_back(e);
+                    }
+                }
+    }
+    m->fb_group[nb] = (int)m->fb.size();
+    // split entries into CTA-sized tasks
+    const int kTask = 2048;
+    for (int e = 0; e < (int)m->fb.size(); ++e) {
+        const long long cells = (long long)m->fb[e].n[0] * m->fb[e].n[1] * m->fb[e].n[2] * m->ncomp;
+        for (long long f = 0; f < cells; f += kTask)
+            m->fbtasks.push_back(FbTask{e, (int)f, (int)std::min<long long>(kTask, cells - f), 0});
+    }
+    return 0;
+}
+
+// ------------------------------------------------------------------ tiles
+
+static void make_tiles(const mf_t *m, const int tile[3], std::vector<Tile> &out) {
+    out.clear();
+    for (int b = 0; b < (int)m->boxes.size(); ++b) {
+        const FabInfo &f = m->fabs[b];
+        int t[3];
+        for (int d = 0; d < 3; ++d) t[d] = (tile[d] <= 0 || tile[d] > f.n[d]) ? f.n[d] : tile[d];
+        for (int c = 0; c < m->ncomp; ++c)
+            for (int z = 0; z < f.n[2]; z += t[2])
+                for (int y = 0; y < f.n[1]; y += t[1])
+                    for (int x = 0; x < f.n[0]; x += t[0]) {
+                        Tile w;
+                        w.fab = b;
+                        w.comp = c;
+                        w.x0 = (short)x; w.y0 = (short)y; w.z0 = (short)z;
+                        w.tx = (short)std::min(t[0], f.n[0] - x);
+                        w.ty = (short)std::min(t[1], f.n[1] - y);
+                        w.tz = (short)std::min(t[2], f.n[2] - z);
+                        out.push_back(w);
+                    }
+    }
+}
+
+// Candidate tile shapes for the autotuner (Sec. 3.2: the tile size can differ per loop).
+static std::vector<std::array<int, 3>> tile_candidates(const mf_t *m) {
+    int mx[3] = {1, 1, 1};
+    for (auto &b : m->boxes) for (int d = 0; d < 3; ++d) mx[d] = std::max(mx[d], b.len(d));
+    std::vector<std::array<int, 3>> c;
+    const int xs[] = {0, 64, 32};
+    const int ys[] = {4, 8, 16, 0};
+    const int zs[] = {8, 16, 32, 0};
+    for (int x : xs) for (int y : ys) for (int z : zs) {
+        std::array<int, 3> t = {x, y, z};
+        // normalise: a size >= the largest box extent means "whole box"
+        for (int d = 0; d < 3; ++d) if (t[d] >= mx[d]) t[d] = 0;
+        if (std::find(c.begin(), c.end(), t) == c.end()) c.push_back(t);
+    }
+    return c;
+}
+
+// ------------------------------------------------------------------ creation
+
+static int check_create(const int dlo[3], const int dhi[3], int ncomp, int ngrow, int dtype) {
+    if (!dlo || !dhi) return fail(MF_EINVAL, "null domain");
+    for (int d = 0; d < 3; ++d)
+        if (dhi[d] < dlo[d]) return fail(MF_EINVAL, "empty domain along %d", d);
+    if (ncomp < 1 || ncomp > kMaxComp) return fail(MF_EINVAL, "ncomp must be in [1, %d]", kMaxComp);
+    if (ngrow < 0) return fail(MF_EINVAL, "ngrow must be >= 0");
+    for (int d = 0; d < 3; ++d)
+        if (ngrow >= dhi[d] - dlo[d] + 1) return fail(MF_EINVAL, "ngrow must be smaller than the domain");
+    if (dtype != F64 && dtype != F32 && dtype != BF16) return fail(MF_EINVAL, "unknown dtype %d", dtype);
+    return 0;
+}
+
+static int finish_create(mf_t *m) {
+    build_layout(m);
+    int rc = build_fb(m);
+    if (rc) return rc;
+    make_tiles(m, m->tile, m->tiles);
+    return 0;
+}
+
+extern "C" int mf_create(mf_t **out, const int domain_lo[3], const int domain_hi[3], int max_grid_size, int ncomp,
+                         int ngrow, int dtype) {
+    if (!out) return fail(MF_EINVAL, "null out");
+    *out = nullptr;
+    int rc = check_create(domain_lo, domain_hi, ncomp, ngrow, dtype);
+    if (rc) return rc;
+    if (max_grid_size < 1) return fail(MF_EINVAL, "max_grid_size must be >= 1");
+    std::unique_ptr<mf_t> m(new (std::nothrow) mf_t());
+    if (!m) return fail(MF_ENOMEM, "host allocation");
+    for (int d = 0; d < 3; ++d) { m->domain.lo[d] = domain_lo[d]; m->domain.hi[d] = domain_hi[d]; }
+    int n[3];
+    for (int d = 0; d < 3; ++d) n[d] = (m->domain.len(d) + max_grid_size - 1) / max_grid_size;
+    if ((long long)n[0] * n[1] * n[2] > (1 << 24)) return fail(MF_EINVAL, "too many boxes");
+    for (int bz = 0; bz < n[2]; ++bz)
+        for (int by = 0; by < n[1]; ++by)
+            for (int bx = 0; bx < n[0]; ++bx) {
+                Box b;
+                const int idx[3] = {bx, by, bz};
+                for (int d = 0; d < 3; ++d) {
+                    b.lo[d] = domain_lo[d] + idx[d] * max_grid_size;
+                    b.hi[d] = std::min(b.lo[d] + max_grid_size - 1, domain_hi[d]);
+                }
+                m->boxes.push_back(b);
+            }
+    m->ncomp = ncomp;
+    m->ngrow = ngrow;
+    m->dtype = dtype;
+    m->esize = dtype_size(dtype);
+    for (auto &b : m->boxes)
+        for (int d = 0; d < 3; ++d)
+            if (b.len(d) > 32767) return fail(MF_EINVAL, "box side above 32767");
+    rc = finish_create(m.get());
+    if (rc) return rc;
+    *out = m.release();
+    return 0;
+}
+
+extern "C" int mf_create_boxes(mf_t **out, const int domain_lo[3], const int domain_hi[3], const int *boxes,
+                               int nboxes, int ncomp, int ngrow, int dtype) {
+    if (!out) return fail(MF_EINVAL, "null out");
+    *out = nullptr;
+    int rc = check_create(domain_lo, domain_hi, ncomp, ngrow, dtype);
+    if (rc) return rc;
+    if (nboxes < 1 || !boxes) return fail(MF_EINVAL, "need at least one box");
+    std::unique_ptr<mf_t> m(new (std::nothrow) mf_t());
+    if (!m) return fail(MF_ENOMEM, "host allocation");
+    for (int d = 0; d < 3; ++d) { m->domain.lo[d] = domain_lo[d]; m->domain.hi[d] = domain_hi[d]; }
+    for (int i = 0; i < nboxes; ++i) {
+        Box b;
+        for (int d = 0; d < 3; ++d) { b.lo[d] = boxes[6 * i + d]; b.hi[d] = boxes[6 * i + 3 + d]; }
+        if (b.empty()) return fail(MF_EINVAL, "box %d is empty", i);
+        for (int d = 0; d < 3; ++d) {
+            if (b.lo[d] < domain_lo[d] || b.hi[d] > domain_hi[d]) return fail(MF_EINVAL, "box %d outside the domain", i);
+            if (b.len(d) > 32767) return fail(MF_EINVAL, "box side above 32767");
+        }
+        m->boxes.push_back(b);
+    }
+    // overlap check through the bin hash
+    BinHash hash;
+    hash.build(m->domain, m->boxes);
+    std::vector<int> cand, stamp(nboxes, -1);
+    for (int i = 0; i < nboxes; ++i) {
+        hash.query(m->boxes[i], cand, stamp, i);
+        for (int a : cand)
+            if (a != i && !intersect(m->boxes[a], m->boxes[i]).empty())
+                return fail(MF_EINVAL, "boxes %d and %d overlap", std::min(a, i), std::max(a, i));
+    }
+    m->ncomp = ncomp;
+    m->ngrow = ngrow;
+    m->dtype = dtype;
+    m->esize = dtype_size(dtype);
+    rc = finish_create(m.get());
+    if (rc) return rc;
+    *out = m.release();
+    return 0;
+}
+
+extern "C" void mf_destroy(mf_t *m) { delete m; }
+
+extern "C" int mf_nboxes(const mf_t *m) { return m ? (int)m->boxes.size() : fail(MF_EINVAL, "null handle"); }
+
+extern "C" int mf_get_boxes(const mf_t *m, int *out) {
+    if (!m || !out) return fail(MF_EINVAL, "null argument");
+    for (size_t i = 0; i < m->boxes.size(); ++i)
+        for (int d = 0; d < 3; ++d) { out[6 * i + d] = m->boxes[i].lo[d]; out[6 * i + 3 + d] = m->boxes[i].hi[d]; }
+    return 0;
+}
+
+extern "C" size_t mf_bytes(const mf_t *m) { return m ? 2 * m->level_elems * m->esize : 0; }
+
+extern "C" long long mf_fb_regions(const mf_t *m, long long *ghost_cells_out) {
+    if (!m) return fail(MF_EINVAL, "null handle");
+    if (ghost_cells_out) *ghost_cells_out = m->ghost_cells;
+    return (long long)m->fb.size();
+}
+
+extern "C" long long mf_get_fb_regions(const mf_t *m, int *out, long long max) {
+    if (!m || !out) return fail(MF_EINVAL, "null argument");
+    long long n = std::min<long long>(max, (long long)m->fb.size());
+    for (long long i = 0; i < n; ++i) {
+        const FbEntry &e = m->fb[i];
+        int *o = out + 11 * i;
+        o[0] = e.dfab;
+        o[1] = e.sfab;
+        for (int d = 0; d < 3; ++d) {
+            o[2 + d] = m->fb_corner[i][d];
+            o[5 + d] = m->fb_corner[i][3 + d];
+            o[8 + d] = e.n[d];
+        }
+    }
+    return n;
+}
+
+extern "C" const char *mf_last_error(void) { return g_err.c_str(); }
+
+extern "C" int mf_current(const mf_t *m) { return m ? m->cur : fail(MF_EINVAL, "null handle"); }
+
+extern "C" double mf_step_bytes(const mf_t *m, int R) {
+    if (!m) return 0.0;
+    double V = 0, Gf = 0;
+    for (auto &b : m->boxes) {
+        const double n0 = b.len(0), n1 = b.len(1), n2 = b.len(2);
+        V += n0 * n1 * n2;
+        Gf += 2.0 * R * (n0 * n1 + n1 * n2 + n0 * n2);
+    }
+    return (double)m->esize * m->ncomp * (2.0 * V + 2.0 * (double)m->ghost_cells + Gf);
+}
+
+// ------------------------------------------------------------------ attach
+
+static void invalidate_graphs(mf_t *m) { m->graphs.clear(); }
+
+extern "C" int mf_attach(mf_t *m, void *dev_ptr, size_t bytes, void *stream) {
+    if (!m) return fail(MF_EINVAL, "null handle");
+    if (!dev_ptr || ((uintptr_t)dev_ptr & 255)) return fail(MF_EALIGN, "device pointer must be 256-byte aligned");
+    if (bytes < mf_bytes(m)) return fail(MF_EALIGN, "buffer of %zu bytes, need %zu", bytes, mf_bytes(m));
+    invalidate_graphs(m);
+    m->base = (char *)dev_ptr;
+    m->bytes = bytes;
+    m->stream = (cudaStream_t)stream;
+    m->cur = 0;
+    if (!m->cap) CU(cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking));
+    if (!m->h_sum) CU(cudaMallocHost((void **)&m->h_sum, sizeof(double)));
+    int rc;
+    if ((rc = m->d_fabs.upload(m->fabs, m->stream))) return rc;
+    if ((rc = m->d_fb.upload(m->fb, m->stream))) return rc;
+    if ((rc = m->d_fbtasks.upload(m->fbtasks, m->stream))) return rc;
+    if ((rc = m->d_cbeg.upload(m->fb_cbeg, m->stream))) return rc;
+    // tile buffer large enough for every autotune candidate
+    size_t cap = m->tiles.size();
+    std::vector<Tile> tmp;
+    for (auto &t : tile_candidates(m)) {
+        make_tiles(m, t.data(), tmp);
+        cap = std::max(cap, tmp.size());
+    }
+    m->tile_capacity = cap;
+    if ((rc = m->d_tiles.ensure(cap * sizeof(Tile)))) return rc;
+    CU(cudaMemcpyAsync(m->d_tiles.p, m->tiles.data(), m->tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice, m->stream));
+    if ((rc = m->d_partials.ensure(512 * sizeof(double2)))) return rc;
+    if ((rc = m->d_sumout.ensure(sizeof(double)))) return rc;
+    CU(cudaStreamSynchronize(m->stream));  // host vectors may change after return
+    m->attached = true;
+    return 0;
+}
+
+static int need_attached(const mf_t *m) {
+    if (!m) return fail(MF_EINVAL, "null handle");
+    if (!m->attached) return fail(MF_ESTATE, "handle not attached");
+    return 0;
+}
+
+static int set_tiles(mf_t *m, const int t[3]) {
+    for (int d = 0; d < 3; ++d) m->tile[d] = t[d];
+    make_tiles(m, m->tile, m->tiles);
+    if (m->attached) {
+        if (m->tiles.size() > m->tile_capacity) return fail(MF_EINVAL, "tile list larger than its buffer");
+        CU(cudaMemcpyAsync(m->d_tiles.p, m->tiles.data(), m->tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice,
+                           m->stream));
+        CU(cudaStreamSynchronize(m->stream));
+        invalidate_graphs(m);
+    }
+    return 0;
+}
+
+extern "C" int mf_set_tile(mf_t *m, const int tile[3]) {
+    if (!m) return fail(MF_EINVAL, "null handle");
+    if (!tile) {
+        m->tile_auto = true;
+        return 0;
+    }
+    for (int d = 0; d < 3; ++d)
+        if (tile[d] > 32767) return fail(MF_EINVAL, "tile size too large");
+    if (m->attached) {
+        std::vector<Tile> tmp;
+        make_tiles(m, tile, tmp);
+        if (tmp.size() > m->tile_capacity) return fail(MF_EINVAL, "tile %dx%dx%d gives more tiles than the work-list "
+                                                                  "buffer sized at attach", tile[0], tile[1], tile[2]);
+    }
+    m->tile_auto = false;
+    return set_tiles(m, tile);
+}
+
+extern "C" int mf_get_tile(const mf_t *m, int tile[3]) {
+    if (!m || !tile) return fail(MF_EINVAL, "null argument");
+    for (int d = 0; d < 3; ++d) tile[d] = m->tile[d];
+    return m->tile_auto ? 1 : 0;
+}
+
+// ------------------------------------------------------------------ host <-> device copies
+
+static int dense_extent(const mf_t *m, int dn[3]) {
+    for (int d = 0; d < 3; ++d) dn[d] = m->domain.len(d);
+    return 0;
+}
+
+extern "C" int mf_copy_from_host(mf_t *m, const double *dense) {
+    int rc = need_attached(m);
+    if (rc) return rc;
+    if (!dense) return fail(MF_EINVAL, "null dense");
+    int dn[3];
+    dense_extent(m, dn);
+    const long long plane = (long long)dn[0] * dn[1];
+    const long long cap = (long long)(m->level_elems * m->esize / sizeof(double));
+    const long long zc = std::min<long long>(dn[2], cap / plane);
+    if (zc < 1) return fail(MF_EINVAL, "a dense z-plane does not fit in one time level");
+    double *stage = (double *)m->level_ptr(1 - m->cur);
+    void *dst = m->level_ptr(m->cur);
+    for (int c = 0; c < m->ncomp; ++c)
+        for (long long z0 = 0; z0 < dn[2]; z0 += zc) {
+            const long long z1 = std::min<long long>(dn[2], z0 + zc);
+            CU(cudaMemcpyAsync(stage, dense + ((long long)c * dn[2] + z0) * plane, (z1 - z0) * plane * sizeof(double),
+                               cudaMemcpyHostToDevice, m->stream));
+            CU(launch_scatter_dense(m->dtype, dst, (const FabInfo *)m->d_fabs.p, (int)m->fabs.size(), stage,
+                                    m->domain.lo, dn, m->domain.lo[2] + (int)z0, m->domain.lo[2] + (int)z1, c, 1,
+                                    m->stream));
+        }
+    return 0;
+}
+
+extern "C" int mf_copy_to_host(mf_t *m, double *dense) {
+    int rc = need_attached(m);
+    if (rc) return rc;
+    if (!dense) return fail(MF_EINVAL, "null dense");
+    int dn[3];
+    dense_extent(m, dn);
+    const long long plane = (long long)dn[0] * dn[1];
+    const long long cap = (long long)(m->level_elems * m->esize / sizeof(double));
+    const long long zc = std::min<long long>(dn[2], cap / plane);
+    if (zc < 1) return fail(MF_EINVAL, "a dense z-plane does not fit in one time level");
+    double *stage = (double *)m->level_ptr(1 - m->cur);
+    const void *src = m->level_ptr(m->cur);
+    for (int c = 0; c < m->ncomp; ++c)
+        for (long long z0 = 0; z0 < dn[2]; z0 += zc) {
+            const long long z1 = std::min<long long>(dn[2], z0 + zc);
+            CU(launch_gather_dense(m->dtype, src, (const FabInfo *)m->d_fabs.p, (int)m->fabs.size(), stage,
+                                   m->domain.lo, dn, m->domain.lo[2] + (int)z0, m->domain.lo[2] + (int)z1, c, 1,
+                                   m->stream));
+            CU(cudaMemcpyAsync(dense + ((long long)c * dn[2] + z0) * plane, stage, (z1 - z0) * plane * sizeof(double),
+                               cudaMemcpyDeviceToHost, m->stream));
+        }
+    CU(cudaStreamSynchronize(m->stream));
+    return 0;
+}
+
+// Host conversions for the FArrayBox debug copies.
+static double bf16_to_double(uint16_t h) {
+    uint32_t u = (uint32_t)h << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+static uint16_t double_to_bf16(double d) {
+    // round to odd into float (24 bits >= 8 + 2), then round-to-nearest-even into bf16
+    float f = (float)d;
+    if (std::isfinite(f) && std::fabs((double)f) > std::fabs(d)) f = std::nextafter(f, 0.0f);
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    if (std::isfinite(d) && (double)f != d) u |= 1u;
+    if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)((u >> 16) | ((u & 0xffff) ? 0x40 : 0));
+    const uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7fffu + lsb;
+    return (uint16_t)(u >> 16);
+}
+
+static void fab_shape(const mf_t *m, int b, long long sh[3]) {
+    for (int d = 0; d < 3; ++d) sh[d] = m->fabs[b].n[d] + 2 * m->ngrow;
+}
+
+extern "C" int mf_copy_fab_to_host(mf_t *m, int box, double *out) {
+    int rc = need_attached(m);
+    if (rc) return rc;
+    if (box < 0 || box >= (int)m->boxes.size() || !out) return fail(MF_EINVAL, "bad box or null out");
+    const FabInfo &f = m->fabs[box];
+    const size_t n = (size_t)f.cstride * m->ncomp;
+    std::vector<char> raw(n * m->esize);
+    CU(cudaMemcpyAsync(raw.data(), (char *)m->level_ptr(m->cur) + (size_t)m->fab_start[box] * m->esize,
+                       raw.size(), cudaMemcpyDeviceToHost, m->stream));
+    CU(cudaStreamSynchronize(m->stream));
+    long long sh[3];
+    fab_shape(m, box, sh);
+    const long long org_local = f.org - m->fab_start[box];
+    const int g = m->ngrow;
+    size_t q = 0;
+    for (int c = 0; c < m->ncomp; ++c)
+        for (long long z = 0; z < sh[2]; ++z)
+            for (long long y = 0; y < sh[1]; ++y)
+                for (long long x = 0; x < sh[0]; ++x) {
+                    const long long at = org_local + c * f.cstride + (z - g) * f.plane + (y - g) * f.px + (x - g);
+                    const char *p = raw.data() + at * m->esize;
+                    double v;
+                    if (m->dtype == F64) memcpy(&v, p, 8);
+                    else if (m->dtype == F32) { float t; memcpy(&t, p, 4); v = t; }
+                    else { uint16_t t; memcpy(&t, p, 2); v = bf16_to_double(t); }
+                    out[q++] = v;
+                }
+    return 0;
+}
+
+extern "C" int mf_copy_fab_from_host(mf_t *m, int box, const double *in) {
+    int rc = need_attached(m);
+    if (rc) return rc;
+    if (box < 0 || box >= (int)m->boxes.size() || !in) return fail(MF_EINVAL, "bad box or null in");
+    const FabInfo &f = m->fabs[box];
+    const size_t n = (size_t)f.cstride * m->ncomp;
+    std::vector<char> raw(n * m->esize);
+    char *dev = (char *)m->level_ptr(m->cur) + (size_t)m->fab_start[box] * m->esize;
+    CU(cudaMemcpyAsync(raw.data(), dev, raw.size(), cudaMemcpyDeviceToHost, m->stream));
+    CU(cudaStreamSynchronize(m->stream));
+    long long sh[3];
+    fab_shape(m, box, sh);
+    const long long org_local = f.org - m->fab_start[box];
+    const int g = m->ngrow;
+    size_t q = 0;
+    for (int c = 0; c < m->ncomp; ++c)
+        for (long long z = 0; z < sh[2]; ++z)
+            for (long long y = 0; y < sh[1]; ++y)
+                for (long long x = 0; x < sh[0]; ++x) {
+                    const long long at = org_local + c * f.cstride + (z - g) * f.plane + (y - g) * f.px + (x - g);
+                    char *p = raw.data() + at * m->esize;
+                    const double v = in[q++];
+                    if (m->dtype == F64) memcpy(p, &v, 8);
+                    else if (m->dtype == F32) { float t = (float)v; memcpy(p, &t, 4); }
+                    else { uint16_t t = double_to_bf16(v); memcpy(p, &t, 2); }
+                }
+    CU(cudaMemcpyAsync(dev, raw.data(), raw.size(), cudaMemcpyHostToDevice, m->stream));
+    CU(cudaStreamSynchronize(m->stream));
+    return 0;
+}
+
+// ------------------------------------------------------------------ phases
+
+static LevelPtrs level_ptrs(const mf_t *m, int which) {
+    LevelPtrs lv{};
+    lv.base[0] = m->level_ptr(which);
+    return lv;
+}
+
+static int enqueue_fill(mf_t *m, int which, cudaStream_t s) {
+    CU(launch_fill(m->dtype, level_ptrs(m, which), (const FabInfo *)m->d_fabs.p, (const FbEntry *)m->d_fb.p,
+                   (const FbTask *)m->d_fbtasks.p, (int)m->fbtasks.size(), 0, s));
+    return 0;
+}
+
+static StencilParams stencil_params(const mf_t *m, int from, const double *lam) {
+    StencilParams p{};
+    p.src[0] = m->level_ptr(from);
+    p.dst[0] = m->level_ptr(1 - from);
+    p.ftab = (const FabInfo *)m->d_fabs.p;
+    p.tiles = (const Tile *)m->d_tiles.p;
+    p.ntiles = (int)m->tiles.size();
+    for (int c = 0; c < m->ncomp; ++c) p.lam[0][c] = lam[c];
+    return p;
+}
+
+static int enqueue_stencil(mf_t *m, int from, int R, bool fp64diff, const double *lam, cudaStream_t s) {
+    StencilParams p = stencil_params(m, from, lam);
+    CU(launch_stencil(m->dtype, R, fp64diff, p, m->block[0], m->block[1], 0, s));
+    return 0;
+}
+
+extern "C" int mf_fill_boundary(mf_t *m) {
+    int rc = need_attached(m);
+    if (rc) return rc;
+    return enqueue_fill(m, m->cur, m->stream);
+}
+
+static int check_stencil(const mf_t *m, const mf_stencil *st, double dt, double lam[kMaxComp], double dx_scale) {
+    if (!st) return fail(MF_EINVAL, "null stencil");
+    const int R = st->kind;
+    if (R != 1 && R != 2 && R != 4) return fail(MF_EINVAL, "stencil kind must be 1, 2 or 4");
+    if (m->ngrow < R) return fail(MF_EINVAL, "ngrow %d below the stencil radius %d", m->ngrow, R);
+    if (!st->diffusivity) return fail(MF_EINVAL, "null diffusivity");
+    if (!(dt > 0.0)) return fail(MF_EINVAL, "dt must be positive");
+    const int N = m->domain.len(0);  // cubic cells of side dx = 1 / N_x
+    // |sigma_R(pi)|: 4, 16/3, 2048/315
+    const double smax = R == 1 ? 4.0 : R == 2 ? 16.0 / 3.0 : 2048.0 / 315.0;
+    const double n2 = (double)N * (double)N * dx_scale;
+    for (int c = 0; c < m->ncomp; ++c) {
+        const double D = st->diffusivity[c];
+        if (!(D > 0.0)) return fail(MF_EINVAL, "diffusivity[%d] must be positive", c);
+        lam[c] = D * dt * n2;
+        if (lam[c] * 3.0 * smax > 2.0 * (1.0 + 1e-12))
+            return fail(MF_EUNSTABLE, "lam = %.6g exceeds the forward-Euler limit %.6g", lam[c], 2.0 / (3.0 * smax));
+    }
+    return 0;
+}
+
+// Autotune: time every candidate tile shape on the live data (current -> other level, which
+// is scratch at this point) and keep the fastest.  Synchronous; runs once per handle.
+static int autotune(mf_t *m, int R, bool fp64diff, const double *lam) {
+    auto cands = tile_candidates(m);
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    float best = 1e30f;
+    std::array<int, 3> best_t = {0, 0, 0};
+    for (auto &t : cands) {
+        int rc = set_tiles(m, t.data());
+        if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
+        // warm-up, then 3 timed launches
+        if ((rc = enqueue_stencil(m, m->cur, R, fp64diff, lam, m->stream))) return rc;
+        CU(cudaEventRecord(e0, m->stream));
+        for (int i = 0; i < 3; ++i)
+            if ((rc = enqueue_stencil(m, m->cur, R, fp64diff, lam, m->stream))) return rc;
+        CU(cudaEventRecord(e1, m->stream));
+        CU(cudaEventSynchronize(e1));
+        float ms = 0;
+        CU(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) { best = ms; best_t = t; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    m->tile_auto = false;
+    return set_tiles(m, best_t.data());
+}
+
+static std::string graph_key(const char *what, int R, bool fp64diff, const double *lam, int nc, int nsteps, int from) {
+    std::string k = what;
+    char buf[64];
+    snprintf(buf, sizeof buf, "|R%d|d%d|n%d|f%d", R, (int)fp64diff, nsteps, from);
+    k += buf;
+    for (int c = 0; c < nc; ++c) {
+        snprintf(buf, sizeof buf, "|%a", lam[c]);
+        k += buf;
+    }
+    return k;
+}
+
+static int capture_begin(mf_t *m) {
+    CU(cudaStreamBeginCapture(m->cap, cudaStreamCaptureModeThreadLocal));
+    return 0;
+}
+
+static int capture_end(mf_t *m, const std::string &key, int body_rc) {
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(m->cap, &graph);
+    if (body_rc) { if (graph) cudaGraphDestroy(graph); return body_rc; }
+    if (e != cudaSuccess) return fail(MF_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+    auto ge = std::make_unique<GraphExec>();
+    e = cudaGraphInstantiate(&ge->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(MF_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+    if (m->graphs.size() >= 16) m->graphs.erase(m->graphs.begin());
+    m->graphs[key] = std::move(ge);
+    return 0;
+}
+
+static int ensure_events(mf_t *m, int n) {
+    while ((int)m->ev.size() < n) {
+        cudaEvent_t e;
+        CU(cudaEventCreate(&e));
+        m->ev.push_back(e);
+    }
+    return 0;
+}
+
+static int record(mf_t *m, int i) {
+    CU(cudaEventRecord(m->ev[i], m->cap));
+    return 0;
+}
+
+extern "C" int mf_set_timing(mf_t *m, int on) {
+    if (!m) return fail(MF_EINVAL, "null handle");
+    m->timing = on != 0;
+    return 0;
+}
+
+extern "C" int mf_phase_ms(mf_t *m, double out[2]) {
+    if (!m || !out) return fail(MF_EINVAL, "null argument");
+    out[0] = out[1] = 0.0;
+    if (m->ev_used < 3) return fail(MF_ESTATE, "no timed advance recorded");
+    CU(cudaEventSynchronize(m->ev[m->ev_used - 1]));
+    for (int i = 0; 2 * i + 2 < m->ev_used; ++i) {
+        float a = 0, b = 0;
+        CU(cudaEventElapsedTime(&a, m->ev[2 * i], m->ev[2 * i + 1]));
+        CU(cudaEventElapsedTime(&b, m->ev[2 * i + 1], m->ev[2 * i + 2]));
+        out[0] += a;
+        out[1] += b;
+    }
+    return 0;
+}
+
+static int advance_plain(mf_t *m, int R, const double *lam, int nsteps) {
+    const int nb = (int)m->boxes.size();
+    for (int s = 0; s < nsteps; ++s) {
+        void *cur = m->level_ptr(m->cur), *nxt = m->level_ptr(1 - m->cur);
+        for (int b = 0; b < nb; ++b) {
+            const int e0 = m->fb_group[b], cnt = m->fb_group[b + 1] - e0;
+            if (cnt == 0) continue;
+            long long total = 0;
+            for (int e = e0; e < e0 + cnt; ++e)
+                total += (long long)m->fb[e].n[0] * m->fb[e].n[1] * m->fb[e].n[2] * m->ncomp;
+            CU(launch_fill_plain(m->dtype, cur, (const FabInfo *)m->d_fabs.p, (const FbEntry *)m->d_fb.p + e0, cnt,
+                                 total, (const int *)m->d_cbeg.p + e0, m->stream));
+        }
+        for (int b = 0; b < nb; ++b)
+            for (int c = 0; c < m->ncomp; ++c)
+                CU(launch_stencil_plain(m->dtype, R, cur, nxt, m->fabs[b], lam[c], c, m->stream));
+        m->cur = 1 - m->cur;
+    }
+    return 0;
+}
+
+extern "C" int mf_advance(mf_t *m, const mf_stencil *st, double dt, int nsteps) {
+    int rc = need_attached(m);
+    if (rc) return rc;
+    double lam[kMaxComp];
+    if ((rc = check_stencil(m, st, dt, lam, 1.0))) return rc;
+    if (nsteps < 0) return fail(MF_EINVAL, "nsteps must be >= 0");
+    if (nsteps == 0) return 0;
+    const int R = st->kind;
+    const bool fp64diff = (st->flags & MF_FP64_DIFF) && m->dtype != F64;
+    if (st->flags & MF_PLAIN_PER_BOX) {
+        if (fp64diff) return fail(MF_EINVAL, "MF_PLAIN_PER_BOX does not combine with MF_FP64_DIFF");
+        return advance_plain(m, R, lam, nsteps);
+    }
+    if (m->tile_auto && (rc = autotune(m, R, fp64diff, lam))) return rc;
+    const std::string key = graph_key(m->timing ? "advT" : "adv", R, fp64diff, lam, m->ncomp, nsteps, m->cur);
+    auto it = m->graphs.find(key);
+    if (it == m->graphs.end()) {
+        if (m->timing && (rc = ensure_events(m, 2 * nsteps + 1))) return rc;
+        if ((rc = capture_begin(m))) return rc;
+        int body = 0, from = m->cur;
+        if (m->timing) body = record(m, 0);
+        for (int s = 0; s < nsteps && !body; ++s) {
+            body = enqueue_fill(m, from, m->cap);
+            if (!body && m->timing) body = record(m, 2 * s + 1);
+            if (!body) body = enqueue_stencil(m, from, R, fp64diff, lam, m->cap);
+            if (!body && m->timing) body = record(m, 2 * s + 2);
+            from = 1 - from;
+        }
+        if ((rc = capture_end(m, key, body))) return rc;
+        it = m->graphs.find(key);
+    }
+    m->ev_used = m->timing ? 2 * nsteps + 1 : 0;
+    CU(cudaGraphLaunch(it->second->exec, m->stream));
+    if (nsteps & 1) m->cur = 1 - m->cur;
+    return 0;
+}
+
+// ------------------------------------------------------------------ reduction
+
+extern "C" int mf_sum(mf_t *m, int comp, double *out) {
+    int rc = need_attached(m);
+    if (rc) return rc;
+    if (comp < 0 || comp >= m->ncomp || !out) return fail(MF_EINVAL, "bad component or null out");
+    const int grid = 304;  // fixed: the reduction tree, hence the bits, do not depend on the GPU
+    CU(launch_sum(m->dtype, m->level_ptr(m->cur), (const FabInfo *)m->d_fabs.p, (const Tile *)m->d_tiles.p,
+                  (int)m->tiles.size(), comp, (double2 *)m->d_partials.p, grid, (double *)m->d_sumout.p, m->stream));
+    CU(cudaMemcpyAsync(m->h_sum, m->d_sumout.p, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    CU(cudaStreamSynchronize(m->stream));
+    *out = *m->h_sum;
+    return 0;
+}
+
+// ------------------------------------------------------------------ AMR
+
+static int wrap_idx(int i, int lo, int len) {
+    int r = (i - lo) % len;
+    if (r < 0) r += len;
+    return lo + r;
+}
+
+static int build_interp(mf_t *fine, const mf_t *crse, int ratio, InterpPlan &plan) {
+    for (int d = 0; d < 3; ++d)
+        if (fine->domain.lo[d] != crse->domain.lo[d] * ratio || fine->domain.len(d) != crse->domain.len(d) * ratio)
+            return fail(MF_EINVAL, "fine domain must be the coarse domain refined by %d", ratio);
+    if (crse->ngrow < 1) return fail(MF_EINVAL, "coarse level needs ngrow >= 1");
+    if (crse->ncomp != fine->ncomp || crse->dtype != fine->dtype)
+        return fail(MF_EINVAL, "levels differ in ncomp or dtype");
+    const int g = fine->ngrow;
+    BinHash chash;
+    chash.build(crse->domain, crse->boxes);
+    std::vector<int> cand, stamp(crse->boxes.size(), -1);
+    int tag = 0;
+    auto crse_owner = [&](int i, int j, int k) -> int {
+        Box q{{i, j, k}, {i, j, k}};
+        chash.query(q, cand, stamp, ++tag);
+        for (int a : cand) if (crse->boxes[a].contains(i, j, k)) return a;
+        return -1;
+    };
+    plan.runs.clear();
+    for (int b = 0; b < (int)fine->boxes.size(); ++b) {
+        const Box &B = fine->boxes[b];
+        const Box gb = grow(B, g);
+        const long long nx = gb.len(0), ny = gb.len(1), nz = gb.len(2);
+        std::vector<char> covered((size_t)(nx * ny * nz), 0);
+        for (int k = B.lo[2]; k <= B.hi[2]; ++k)
+            for (int j = B.lo[1]; j <= B.hi[1]; ++j)
+                for (int i = B.lo[0]; i <= B.hi[0]; ++i)
+                    covered[((k - gb.lo[2]) * ny + (j - gb.lo[1])) * nx + (i - gb.lo[0])] = 1;
+        const FabInfo &ff = fine->fabs[b];
+        for (int e = fine->fb_group[b]; e < fine->fb_group[b + 1]; ++e) {
+            const FbEntry &en = fine->fb[e];
+            const int c0 = fine->fb_corner[e][0] - B.lo[0], c1 = fine->fb_corner[e][1] - B.lo[1],
+                      c2 = fine->fb_corner[e][2] - B.lo[2];
+            for (int z = 0; z < en.n[2]; ++z)
+                for (int y = 0; y < en.n[1]; ++y)
+                    for (int x = 0; x < en.n[0]; ++x)
+                        covered[((c2 + z + g) * ny + (c1 + y + g)) * nx + (c0 + x + g)] = 1;
+        }
+        for (int k = gb.lo[2]; k <= gb.hi[2]; ++k)
+            for (int j = gb.lo[1]; j <= gb.hi[1]; ++j) {
+                int i = gb.lo[0];
+                while (i <= gb.hi[0]) {
+                    if (covered[((k - gb.lo[2]) * ny + (j - gb.lo[1])) * nx + (i - gb.lo[0])]) { ++i; continue; }
+                    // start a run: coarse owner and periodic shift of floor(I/r) per direction
+                    const int kj = floor_div(j, ratio), kk = floor_div(k, ratio);
+                    const int wj = wrap_idx(kj, crse->domain.lo[1], crse->domain.len(1));
+                    const int wk = wrap_idx(kk, crse->domain.lo[2], crse->domain.len(2));
+                    const int ki = floor_div(i, ratio);
+                    const int wi = wrap_idx(ki, crse->domain.lo[0], crse->domain.len(0));
+                    const int a = crse_owner(wi, wj, wk);
+                    if (a < 0) return fail(MF_EINVAL, "coarse level does not cover its domain");
+                    InterpRun run{};
+                    run.ffab = b;
+                    run.cfab = a;
+                    run.I = i; run.J = j; run.K = k;
+                    run.shift[0] = ki - wi; run.shift[1] = kj - wj; run.shift[2] = kk - wk;
+                    run.fdst = elem_at(ff, i, j, k);
+                    int len = 0;
+                    while (i <= gb.hi[0] && !covered[((k - gb.lo[2]) * ny + (j - gb.lo[1])) * nx + (i - gb.lo[0])]) {
+                        const int kx = floor_div(i, ratio);
+                        const int wx = wrap_idx(kx, crse->domain.lo[0], crse->domain.len(0));
+                        if (kx - wx != run.shift[0] || !crse->boxes[a].contains(wx, wj, wk)) break;
+                        ++len;
+                        ++i;
+                    }
+                    run.len = len;
+                    plan.runs.push_back(run);
+                }
+            }
+    }
+    return 0;
+}
+
+static InterpPlan *get_interp(mf_t *fine, const mf_t *crse, int ratio, int *rc) {
+    for (auto &p : fine->interp)
+        if (p->crse == crse && p->ratio == ratio) { *rc = 0; return p.get(); }
+    auto p = std::make_unique<InterpPlan>();
+    p->crse = crse;
+    p->ratio = ratio;
+    if ((*rc = build_interp(fine, crse, ratio, *p))) return nullptr;
+    if ((*rc = p->d_runs.upload(p->runs, fine->stream))) return nullptr;
+    if (cudaStreamSynchronize(fine->stream) != cudaSuccess) { *rc = fail(MF_ECUDA, "sync"); return nullptr; }
+    fine->interp.push_back(std::move(p));
+    return fine->interp.back().get();
+}
+
+static int build_avg(const mf_t *fine, mf_t *crse, int ratio, AvgPlan &plan) {
+    for (int d = 0; d < 3; ++d)
+        if (fine->domain.lo[d] != crse->domain.lo[d] * ratio || fine->domain.len(d) != crse->domain.len(d) * ratio)
+            return fail(MF_EINVAL, "fine domain must be the coarse domain refined by %d", ratio);
+    if (crse->ncomp != fine->ncomp || crse->dtype != fine->dtype)
+        return fail(MF_EINVAL, "levels differ in ncomp or dtype");
+    BinHash chash;
+    chash.build(crse->domain, crse->boxes);
+    std::vector<int> cand, stamp(crse->boxes.size(), -1);
+    int tag = 0;
+    plan.regs.clear();
+    for (int f = 0; f < (int)fine->boxes.size(); ++f) {
+        const Box &B = fine->boxes[f];
+        for (int d = 0; d < 3; ++d)
+            if (B.lo[d] % ratio != 0 || (B.hi[d] + 1) % ratio != 0)
+                return fail(MF_EINVAL, "fine box %d not aligned to the refinement ratio", f);
+        const Box cb = coarsen(B, ratio);
+        chash.query(cb, cand, stamp, ++tag);
+        std::sort(cand.begin(), cand.end());
+        for (int a : cand) {
+            const Box r = intersect(cb, crse->boxes[a]);
+            if (r.empty()) continue;
+            AvgRegion g{};
+            g.cfab = a;
+            g.ffab = f;
+            for (int d = 0; d < 3; ++d) { g.clo[d] = r.lo[d]; g.n[d] = r.len(d); }
+            plan.regs.push_back(g);
+        }
+    }
+    return 0;
+}
+
+static AvgPlan *get_avg(const mf_t *fine, mf_t *crse, int ratio, int *rc) {
+    for (auto &p : crse->avg)
+        if (p->fine == fine && p->ratio == ratio) { *rc = 0; return p.get(); }
+    auto p = std::make_unique<AvgPlan>();
+    p->fine = fine;
+    p->ratio = ratio;
+    if ((*rc = build_avg(fine, crse, ratio, *p))) return nullptr;
+    if ((*rc = p->d_regs.upload(p->regs, crse->stream))) return nullptr;
+    if (cudaStreamSynchronize(crse->stream) != cudaSuccess) { *rc = fail(MF_ECUDA, "sync"); return nullptr; }
+    crse->avg.push_back(std::move(p));
+    return crse->avg.back().get();
+}
+
+static int enqueue_interp(mf_t *fine, int fwhich, const mf_t *cold, int cold_which, const mf_t *cnew, int cnew_which,
+                          InterpPlan *plan, int ratio, double alpha, cudaStream_t s) {
+    CU(launch_interp(fine->dtype, fine->level_ptr(fwhich), (const FabInfo *)fine->d_fabs.p,
+                     cold->level_ptr(cold_which), cnew->level_ptr(cnew_which), (const FabInfo *)cold->d_fabs.p,
+                     (const InterpRun *)plan->d_runs.p, (int)plan->runs.size(), fine->ncomp, ratio, alpha, s));
+    return 0;
+}
+
+static int enqueue_avg(const mf_t *fine, int fwhich, mf_t *crse, int cwhich, AvgPlan *plan, int ratio,
+                       cudaStream_t s) {
+    CU(launch_avgdown(fine->dtype, fine->level_ptr(fwhich), (const FabInfo *)fine->d_fabs.p, crse->level_ptr(cwhich),
+                      (const FabInfo *)crse->d_fabs.p, (const AvgRegion *)plan->d_regs.p, (int)plan->regs.size(),
+                      fine->ncomp, ratio, s));
+    return 0;
+}
+
+extern "C" int mf_interp_cf(mf_t *fine, const mf_t *crse_old, const mf_t *crse_new, double alpha, int ratio) {
+    int rc = need_attached(fine);
+    if (rc) return rc;
+    if ((rc = need_attached(crse_old)) || (rc = need_attached(crse_new))) return rc;
+    if (ratio != 2 && ratio != 4) return fail(MF_EINVAL, "ratio must be 2 or 4");
+    if (crse_old->boxes.size() != crse_new->boxes.size() || crse_old->level_elems != crse_new->level_elems)
+        return fail(MF_EINVAL, "coarse handles must share one layout");
+    InterpPlan *plan = get_interp(fine, crse_old, ratio, &rc);
+    if (!plan) return rc;
+    return enqueue_interp(fine, fine->cur, crse_old, crse_old->cur, crse_new, crse_new->cur, plan, ratio, alpha,
+                          fine->stream);
+}
+
+extern "C" int mf_average_down(const mf_t *fine, mf_t *crse, int ratio) {
+    int rc = need_attached(crse);
+    if (rc) return rc;
+    if ((rc = need_attached(fine))) return rc;
+    if (ratio != 2 && ratio != 4) return fail(MF_EINVAL, "ratio must be 2 or 4");
+    AvgPlan *plan = get_avg(fine, crse, ratio, &rc);
+    if (!plan) return rc;
+    return enqueue_avg(fine, fine->cur, crse, crse->cur, plan, ratio, crse->stream);
+}
+
+extern "C" int mf_amr_advance(mf_t *crse, mf_t *fine, const mf_stencil *st, double dt_crse, int ncrse_steps, int nsub,
+                              int ratio) {
+    int rc = need_attached(crse);
+    if (rc) return rc;
+    if ((rc = need_attached(fine))) return rc;
+    if (ratio != 2 && ratio != 4) return fail(MF_EINVAL, "ratio must be 2 or 4");
+    if (nsub < 1) return fail(MF_EINVAL, "nsub must be >= 1");
+    if (ncrse_steps < 0) return fail(MF_EINVAL, "ncrse_steps must be >= 0");
+    if (st && (st->flags & MF_PLAIN_PER_BOX)) return fail(MF_EINVAL, "MF_PLAIN_PER_BOX is single-level only");
+    double lam_c[kMaxComp], lam_f[kMaxComp];
+    if ((rc = check_stencil(crse, st, dt_crse, lam_c, 1.0))) return rc;
+    // fine: dx_f = dx_c / ratio, dt_f = dt_c / nsub; lam_f = D dt_f / dx_f^2 on the fine domain
+    if ((rc = check_stencil(fine, st, dt_crse / nsub, lam_f, 1.0))) return rc;
+    if (ncrse_steps == 0) return 0;
+    const int R = st->kind;
+    const bool fp64diff = (st->flags & MF_FP64_DIFF) && crse->dtype != F64;
+    InterpPlan *ip = get_interp(fine, crse, ratio, &rc);
+    if (!ip) return rc;
+    AvgPlan *ap = get_avg(fine, crse, ratio, &rc);
+    if (!ap) return rc;
+    if (crse->tile_auto && (rc = autotune(crse, R, fp64diff, lam_c))) return rc;
+    if (fine->tile_auto && (rc = autotune(fine, R, fp64diff, lam_f))) return rc;
+    // the coarse stream orders everything; the fine stream waits for nothing else (same
+    // stream expected); capture the whole advance into one graph
+    char buf[96];
+    snprintf(buf, sizeof buf, "amr|%p|s%d|r%d|fc%d", (void *)fine, nsub, ratio, fine->cur);
+    const std::string key = graph_key(buf, R, fp64diff, lam_c, crse->ncomp, ncrse_steps, crse->cur);
+    auto it = crse->graphs.find(key);
+    if (it == crse->graphs.end()) {
+        if ((rc = capture_begin(crse))) return rc;
+        cudaStream_t s = crse->cap;
+        int body = 0, c = crse->cur, f = fine->cur;
+        for (int step = 0; step < ncrse_steps && !body; ++step) {
+            body = enqueue_fill(crse, c, s);
+            if (!body) body = enqueue_stencil(crse, c, R, fp64diff, lam_c, s);
+            if (!body) body = enqueue_fill(crse, 1 - c, s);
+            for (int sub = 0; sub < nsub && !body; ++sub) {
+                body = enqueue_fill(fine, f, s);
+                if (!body)
+                    body = enqueue_interp(fine, f, crse, c, crse, 1 - c, ip, ratio, (double)sub / (double)nsub, s);
+                if (!body) body = enqueue_stencil(fine, f, R, fp64diff, lam_f, s);
+                f = 1 - f;
+            }
+            if (!body) body = enqueue_avg(fine, f, crse, 1 - c, ap, ratio, s);
+            c = 1 - c;
+        }
+        if ((rc = capture_end(crse, key, body))) return rc;
+        it = crse->graphs.find(key);
+    }
+    CU(cudaGraphLaunch(it->second->exec, crse->stream));
+    if (ncrse_steps & 1) crse->cur = 1 - crse->cur;
+    if ((ncrse_steps * nsub) & 1) fine->cur = 1 - fine->cur;
+    return 0;
+}

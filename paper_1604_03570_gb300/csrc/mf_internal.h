@@ -1,0 +1,111 @@
+// mf_internal.h -- device-side tables and kernel launchers shared by mf_host.cpp and the
+// CUDA translation units.  Not part of the public ABI (see include/mf.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mfk {
+
+constexpr int kMaxComp = 16;
+constexpr int kMaxLev = 2;
+
+enum DType { F64 = 0, F32 = 1, BF16 = 2 };
+
+inline int dtype_size(int dt) { return dt == F64 ? 8 : dt == F32 ? 4 : 2; }
+
+// One FArrayBox.  Element (x, y, z, c) of the box, in coordinates relative to the valid
+// lower corner (x in [-g, n0 + g)), lives at  org + c*cstride + z*plane + y*px + x.
+struct FabInfo {
+    long long org;      // element offset of valid cell (0,0,0), comp 0, within a time level
+    long long plane;    // px * py
+    long long cstride;  // plane * (n2 + 2g)
+    int px;             // row pitch in elements (multiple of 16 bytes)
+    int n[3];           // valid extents
+    int lo[3];          // valid lower corner, global index
+    int level;          // level slot in merged launches
+};
+
+// One FillBoundary copy region: extents n, src/dst element offsets of the region's first
+// cell (comp 0) within a time level, and the FArrayBoxes whose strides apply.
+struct FbEntry {
+    long long src, dst;
+    int n[3];
+    int sfab, dfab;
+    int level;
+};
+
+// Work unit of the fill kernel: cells [first, first + count) of entry `entry` in the
+// linear order (comp, z, y, x).
+struct FbTask {
+    int entry;
+    int first;
+    int count;
+    int pad_;
+};
+
+// Stencil work list entry: a logical tile of one box and one component (Sec. 3.2 tilebox()).
+struct Tile {
+    int fab;
+    int comp;
+    short x0, y0, z0;   // tile lower corner relative to the box's valid lower corner
+    short tx, ty, tz;   // tile extents
+};
+
+// Coarse-fine interpolation: a run of fine ghost cells along x, all with the same coarse box.
+struct InterpRun {
+    long long fdst;     // element offset of the first fine cell (comp 0)
+    int ffab;           // fine FArrayBox
+    int cfab;           // coarse FArrayBox containing floor(i_f / r) of every cell of the run
+    int I, J, K;        // global fine index of the first cell
+    int len;
+    int shift[3];       // coarse index shift: coarse_local = floor-part - shift (periodic image)
+};
+
+// Average-down region: coarse valid cells [clo, clo + n) of coarse box cfab from fine box ffab.
+struct AvgRegion {
+    int cfab, ffab;
+    int clo[3];         // global coarse index
+    int n[3];
+};
+
+struct LevelPtrs {
+    void *base[kMaxLev];
+};
+
+struct StencilParams {
+    const void *src[kMaxLev];
+    void *dst[kMaxLev];
+    const FabInfo *ftab;
+    const Tile *tiles;
+    int ntiles;
+    double lam[kMaxLev][kMaxComp];
+};
+
+// ---- launchers (mf_kernels.cu); all asynchronous on `s`
+cudaError_t launch_fill(int dtype, const LevelPtrs &lv, const FabInfo *ftab, const FbEntry *ent, const FbTask *tasks,
+                        int ntasks, int grid, cudaStream_t s);
+cudaError_t launch_stencil(int dtype, int R, bool fp64diff, const StencilParams &p, int bx, int by, int grid,
+                           cudaStream_t s);
+// untiled per-box baseline (one box per launch)
+cudaError_t launch_stencil_plain(int dtype, int R, const void *src, void *dst, const FabInfo &f, double lam,
+                                 int comp, cudaStream_t s);
+cudaError_t launch_fill_plain(int dtype, void *base, const FabInfo *ftab, const FbEntry *ent, int count,
+                              long long total, const int *cbeg, cudaStream_t s);
+cudaError_t launch_sum(int dtype, const void *base, const FabInfo *ftab, const Tile *tiles, int ntiles, int comp,
+                       double2 *partials, int grid, double *out_dev, cudaStream_t s);
+cudaError_t launch_scatter_dense(int dtype, void *base, const FabInfo *ftab, int nfab, const double *stage,
+                                 const int dlo[3], const int dn[3], int z0, int z1, int comp, int ncomp_chunk,
+                                 cudaStream_t s);
+cudaError_t launch_gather_dense(int dtype, const void *base, const FabInfo *ftab, int nfab, double *stage,
+                                const int dlo[3], const int dn[3], int z0, int z1, int comp, int ncomp_chunk,
+                                cudaStream_t s);
+cudaError_t launch_interp(int dtype, void *fbase, const FabInfo *ffabs, const void *cold, const void *cnew,
+                          const FabInfo *cfabs, const InterpRun *runs, int nruns, int ncomp, int ratio, double alpha,
+                          cudaStream_t s);
+cudaError_t launch_avgdown(int dtype, const void *fbase, const FabInfo *ffabs, void *cbase, const FabInfo *cfabs,
+                           const AvgRegion *regs, int nregs, int ncomp, int ratio, cudaStream_t s);
+
+int sm_count();
+
+}  // namespace mfk

@@ -1,0 +1,622 @@
+// mf_kernels.cu -- CUDA kernels of the MultiFab sweep for sm_103a (GB300).
+//
+//   k_fill          FillBoundary (Sec. 3.1): one persistent copy kernel over the precomputed
+//                   list of box-box intersections (periodic images included) of every level.
+//   k_stencil       the heat-equation kernel of Sec. 4.1 in flux form (face fluxes, then
+//                   their divergence), out of place, over the device work list of logical
+//                   tiles (Sec. 3.2 MFIter / tilebox()); one persistent launch for all boxes.
+//                   Each thread owns an (x, y) column of the tile and marches along z with
+//                   a register queue of 2R+1 values, so the z-face flux of the previous
+//                   cell is reused; x and y neighbours come through L1.
+//   k_stencil_plain the untiled per-box baseline of Sec. 3.1 (one launch per box).
+//   k_sum_*         whole-level reduction (Sec. 3.1 mf.max(0) analogue): FP64 Neumaier
+//                   compensated sums, fixed reduction tree, so the result does not depend
+//                   on timing.
+//   k_interp / k_avgdown   inter-level operations of a refined level (Sec. 3).
+//   k_scatter / k_gather   dense host layout <-> FArrayBoxes with dtype conversion.
+//
+// Per-cell floating-point order is fixed (explicit _rn intrinsics, no contraction left to
+// the compiler), so every tile shape and every box layout gives identical bits.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "mf_internal.h"
+
+namespace mfk {
+
+// ------------------------------------------------------------------ scalar helpers
+
+template <typename A> struct Ar;
+template <> struct Ar<double> {
+    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+};
+template <> struct Ar<float> {
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+};
+
+template <typename S, typename A> __device__ __forceinline__ A ld(const S *p);
+template <> __device__ __forceinline__ double ld<double, double>(const double *p) { return __ldg(p); }
+template <> __device__ __forceinline__ float ld<float, float>(const float *p) { return __ldg(p); }
+template <> __device__ __forceinline__ double ld<float, double>(const float *p) { return (double)__ldg(p); }
+template <> __device__ __forceinline__ float ld<__nv_bfloat16, float>(const __nv_bfloat16 *p) {
+    return __bfloat162float(__ldg(p));
+}
+template <> __device__ __forceinline__ double ld<__nv_bfloat16, double>(const __nv_bfloat16 *p) {
+    return (double)__bfloat162float(__ldg(p));
+}
+
+__device__ __forceinline__ void st(double *p, double v) { *p = v; }
+__device__ __forceinline__ void st(float *p, float v) { *p = v; }
+__device__ __forceinline__ void st(float *p, double v) { *p = __double2float_rn(v); }
+__device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+__device__ __forceinline__ void st(__nv_bfloat16 *p, double v) { *p = __double2bfloat16(v); }
+
+__device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ double to_f64(float v) { return (double)v; }
+__device__ __forceinline__ double to_f64(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+__device__ __forceinline__ void from_f64(double *p, double v) { *p = v; }
+__device__ __forceinline__ void from_f64(float *p, double v) { *p = __double2float_rn(v); }
+__device__ __forceinline__ void from_f64(__nv_bfloat16 *p, double v) { *p = __double2bfloat16(v); }
+
+// Face-flux weights b_m of the centred (2R+1)-point Laplacian of order 2R written as a flux
+// difference, F_{i+1/2} = sum_m b_m (u_{i+m} - u_{i+1-m}), b_m = sum_{j>=m} c_j with the
+// classical centred second-derivative weights c_j (R=1: c=(-2,1); R=2: (-5/2,4/3,-1/12);
+// R=4: (-205/72, 8/5, -1/5, 8/315, -1/560)).
+template <int R> struct FluxW;
+template <> struct FluxW<1> { static __device__ __forceinline__ double b(int) { return 1.0; } };
+template <> struct FluxW<2> {
+    static __device__ __forceinline__ double b(int m) { return m == 1 ? 15.0 / 12.0 : -1.0 / 12.0; }
+};
+template <> struct FluxW<4> {
+    static __device__ __forceinline__ double b(int m) {
+        return m == 1 ? 205.0 / 144.0 : m == 2 ? -127.0 / 720.0 : m == 3 ? 17.0 / 720.0 : -1.0 / 560.0;
+    }
+};
+
+// Flux at the face between q[c] and q[c+1] of a line of values q (index c = centre - 1 for
+// the lower face): F = b_1 (q[c+1] - q[c]) + sum_{m>=2} b_m (q[c+m] - q[c+1-m]).
+template <typename A, int R>
+__device__ __forceinline__ A face_flux(const A *q, int c) {
+    A f = Ar<A>::mul((A)FluxW<R>::b(1), Ar<A>::sub(q[c + 1], q[c]));
+#pragma unroll
+    for (int m = 2; m <= R; ++m) f = Ar<A>::fma((A)FluxW<R>::b(m), Ar<A>::sub(q[c + m], q[c + 1 - m]), f);
+    return f;
+}
+
+// ------------------------------------------------------------------ FillBoundary
+
+template <typename E>
+__global__ void __launch_bounds__(256) k_fill(LevelPtrs lv, const FabInfo *__restrict__ ftab,
+                                              const FbEntry *__restrict__ ent, const FbTask *__restrict__ tasks,
+                                              int ntasks) {
+    for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
+        const FbTask tk = tasks[t];
+        const FbEntry e = ent[tk.entry];
+        const FabInfo &sf = ftab[e.sfab];
+        const FabInfo &df = ftab[e.dfab];
+        const long long s_pl = sf.plane, s_cs = sf.cstride, d_pl = df.plane, d_cs = df.cstride;
+        const int s_px = sf.px, d_px = df.px;
+        E *base = (E *)lv.base[e.level];
+        const unsigned n0 = e.n[0], n1 = e.n[1], n2 = e.n[2];
+        for (int i = threadIdx.x; i < tk.count; i += blockDim.x) {
+            unsigned l = (unsigned)(tk.first + i);
+            unsigned x = l % n0;
+            l /= n0;
+            unsigned y = l % n1;
+            l /= n1;
+            unsigned z = l % n2;
+            unsigned c = l / n2;
+            base[e.dst + c * d_cs + z * d_pl + (long long)y * d_px + x] =
+                base[e.src + c * s_cs + z * s_pl + (long long)y * s_px + x];
+        }
+    }
+}
+
+// Per-box baseline: the entries of one destination box, one thread per cell.
+template <typename E>
+__global__ void k_fill_plain(E *base, const FabInfo *__restrict__ ftab, const FbEntry *__restrict__ ent, int count,
+                             long long total, const int *__restrict__ cbeg) {
+    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {  // last entry with cbeg <= g
+        int mid = (lo + hi + 1) >> 1;
+        if (cbeg[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    const FbEntry e = ent[lo];
+    const FabInfo &sf = ftab[e.sfab];
+    const FabInfo &df = ftab[e.dfab];
+    unsigned l = (unsigned)(g - cbeg[lo]);
+    unsigned x = l % e.n[0];
+    l /= e.n[0];
+    unsigned y = l % e.n[1];
+    l /= e.n[1];
+    unsigned z = l % e.n[2];
+    unsigned c = l / e.n[2];
+    base[e.dst + c * df.cstride + z * df.plane + (long long)y * df.px + x] =
+        base[e.src + c * sf.cstride + z * sf.plane + (long long)y * sf.px + x];
+}
+
+// ------------------------------------------------------------------ stencil
+
+// One cell's update from the lines through it: x line qx, y line qy (2R+1 values each,
+// centre at R) and the z fluxes below/above.  Order: ((Dx + Dy) + Dz), then u + lam*div.
+template <typename A, int R>
+__device__ __forceinline__ A update_cell(const A *qx, const A *qy, A fzm, A fzp, A u, A lam) {
+    A dxv = Ar<A>::sub(face_flux<A, R>(qx, R), face_flux<A, R>(qx, R - 1));
+    A dyv = Ar<A>::sub(face_flux<A, R>(qy, R), face_flux<A, R>(qy, R - 1));
+    A dzv = Ar<A>::sub(fzp, fzm);
+    A div = Ar<A>::add(Ar<A>::add(dxv, dyv), dzv);
+    return Ar<A>::fma(lam, div, u);
+}
+
+template <typename S, typename A, int R>
+__global__ void __launch_bounds__(256) k_stencil(StencilParams p) {
+    for (int w = blockIdx.x; w < p.ntiles; w += gridDim.x) {
+        const Tile t = p.tiles[w];
+        const FabInfo f = p.ftab[t.fab];
+        const long long pl = f.plane;
+        const int px = f.px;
+        const S *src = (const S *)p.src[f.level] + f.org + t.comp * f.cstride;
+        S *dst = (S *)p.dst[f.level] + f.org + t.comp * f.cstride;
+        const A lam = (A)p.lam[f.level][t.comp];
+        for (int yy = threadIdx.y; yy < t.ty; yy += blockDim.y) {
+            for (int xx = threadIdx.x; xx < t.tx; xx += blockDim.x) {
+                const int x = t.x0 + xx, y = t.y0 + yy;
+                const S *col = src + (long long)y * px + x;
+                S *ocol = dst + (long long)y * px + x;
+                A q[2 * R + 1];  // q[j] = u(x, y, z - R + j)
+                int z = t.z0;
+#pragma unroll
+                for (int j = 0; j < 2 * R + 1; ++j) q[j] = ld<S, A>(col + (long long)(z - R + j) * pl);
+                A fzm = face_flux<A, R>(q, R - 1);
+                for (int k = 0; k < t.tz; ++k) {
+                    z = t.z0 + k;
+                    const S *c0 = col + (long long)z * pl;
+                    A qx[2 * R + 1], qy[2 * R + 1];
+#pragma unroll
+                    for (int j = 0; j < 2 * R + 1; ++j) {
+                        qx[j] = (j == R) ? q[R] : ld<S, A>(c0 + (j - R));
+                        qy[j] = (j == R) ? q[R] : ld<S, A>(c0 + (long long)(j - R) * px);
+                    }
+                    const A fzp = face_flux<A, R>(q, R);
+                    st(ocol + (long long)z * pl, update_cell<A, R>(qx, qy, fzm, fzp, q[R], lam));
+                    fzm = fzp;
+                    if (k + 1 < t.tz) {
+#pragma unroll
+                        for (int j = 0; j < 2 * R; ++j) q[j] = q[j + 1];
+                        q[2 * R] = ld<S, A>(col + (long long)(z + 1 + R) * pl);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Untiled per-box baseline: one thread per cell, every neighbour loaded, every flux
+// computed on its own (same formulas and order, hence the same bits).
+template <typename S, typename A, int R>
+__global__ void k_stencil_plain(const S *__restrict__ src, S *__restrict__ dst, FabInfo f, A lam) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= f.n[0] || y >= f.n[1]) return;
+    const long long pl = f.plane;
+    const int px = f.px;
+    const S *c0 = src + f.org + (long long)z * pl + (long long)y * px + x;
+    A qx[2 * R + 1], qy[2 * R + 1], qz[2 * R + 1];
+#pragma unroll
+    for (int j = 0; j < 2 * R + 1; ++j) {
+        qx[j] = ld<S, A>(c0 + (j - R));
+        qy[j] = ld<S, A>(c0 + (long long)(j - R) * px);
+        qz[j] = ld<S, A>(c0 + (long long)(j - R) * pl);
+    }
+    const A fzm = face_flux<A, R>(qz, R - 1);
+    const A fzp = face_flux<A, R>(qz, R);
+    st(dst + f.org + (long long)z * pl + (long long)y * px + x, update_cell<A, R>(qx, qy, fzm, fzp, qz[R], lam));
+}
+
+// ------------------------------------------------------------------ reduction
+
+// Neumaier: running sum s with compensation c.
+__device__ __forceinline__ void neu_add(double &s, double &c, double x) {
+    double t = __dadd_rn(s, x);
+    if (::fabs(s) >= ::fabs(x)) c = __dadd_rn(c, __dadd_rn(__dsub_rn(s, t), x));
+    else c = __dadd_rn(c, __dadd_rn(__dsub_rn(x, t), s));
+    s = t;
+}
+// Combine (s2, c2) into (s, c): TwoSum of the heads, compensations added.
+__device__ __forceinline__ void neu_merge(double &s, double &c, double s2, double c2) {
+    neu_add(s, c, s2);
+    c = __dadd_rn(c, c2);
+}
+
+__device__ __forceinline__ void block_reduce(double &s, double &c) {
+    for (int off = 16; off > 0; off >>= 1) {
+        double s2 = __shfl_down_sync(0xffffffffu, s, off);
+        double c2 = __shfl_down_sync(0xffffffffu, c, off);
+        neu_merge(s, c, s2, c2);
+    }
+    __shared__ double ss[32], sc[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) { ss[wid] = s; sc[wid] = c; }
+    __syncthreads();
+    if (wid == 0) {
+        s = lane < nw ? ss[lane] : 0.0;
+        c = lane < nw ? sc[lane] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) {
+            double s2 = __shfl_down_sync(0xffffffffu, s, off);
+            double c2 = __shfl_down_sync(0xffffffffu, c, off);
+            neu_merge(s, c, s2, c2);
+        }
+    }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256) k_sum_partial(const S *__restrict__ base, const FabInfo *__restrict__ ftab,
+                                                     const Tile *__restrict__ tiles, int ntiles, int comp,
+                                                     double2 *partials) {
+    double s = 0.0, c = 0.0;
+    for (int w = blockIdx.x; w < ntiles; w += gridDim.x) {
+        const Tile t = tiles[w];
+        if (t.comp != comp) continue;
+        const FabInfo f = ftab[t.fab];
+        const S *p = base + f.org + comp * f.cstride;
+        const int cells = t.tx * t.ty * t.tz;
+        for (int i = threadIdx.x; i < cells; i += blockDim.x) {
+            int x = i % t.tx, r = i / t.tx, y = r % t.ty, z = r / t.ty;
+            neu_add(s, c, to_f64(p[(long long)(t.z0 + z) * f.plane + (long long)(t.y0 + y) * f.px + t.x0 + x]));
+        }
+    }
+    block_reduce(s, c);
+    if (threadIdx.x == 0) partials[blockIdx.x] = make_double2(s, c);
+}
+
+__global__ void __launch_bounds__(256) k_sum_final(const double2 *partials, int n, double *out) {
+    double s = 0.0, c = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) neu_merge(s, c, partials[i].x, partials[i].y);
+    block_reduce(s, c);
+    if (threadIdx.x == 0) out[0] = __dadd_rn(s, c);
+}
+
+// ------------------------------------------------------------------ dense staging
+
+__global__ void k_fill_nan(double *p, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = __longlong_as_double(0x7ff8000000000000LL);
+}
+
+struct DenseChunk {
+    int dlo[3], dn[3];
+    int z0, z1;       // global z range [z0, z1) held by the stage
+    int comp, nc;     // components [comp, comp + nc) held by the stage
+};
+
+template <typename S, bool kScatter>
+__global__ void k_dense(S *base, const FabInfo *__restrict__ ftab, double *stage, DenseChunk d) {
+    const FabInfo f = ftab[blockIdx.y];
+    const int zlo = max(f.lo[2], d.z0), zhi = min(f.lo[2] + f.n[2], d.z1);
+    if (zlo >= zhi) return;
+    const int nz = zhi - zlo, ny = f.n[1];
+    const long long rows = (long long)nz * ny * d.nc;
+    const long long zs = (long long)(d.z1 - d.z0) * d.dn[1] * d.dn[0];
+    for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int y = (int)(r % ny);
+        const int z = (int)((r / ny) % nz) + zlo;
+        const int cc = (int)(r / ((long long)ny * nz));
+        S *frow = base + f.org + (long long)(d.comp + cc) * f.cstride + (long long)(z - f.lo[2]) * f.plane +
+                  (long long)y * f.px;
+        double *srow = stage + cc * zs + ((long long)(z - d.z0) * d.dn[1] + (y + f.lo[1] - d.dlo[1])) * d.dn[0] +
+                       (f.lo[0] - d.dlo[0]);
+        for (int x = threadIdx.x; x < f.n[0]; x += blockDim.x) {
+            if (kScatter) from_f64(frow + x, srow[x]);
+            else srow[x] = to_f64(frow[x]);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ AMR
+
+// Linear-interpolation stencil of fine index i at ratio r: coarse k0 and weight of k0+1
+// from the cell-centre position x = (2i + 1 - r) / (2r) in coarse index units.
+__device__ __forceinline__ void lin_w(int i, int r, int &k0, double &w1) {
+    const int num = 2 * i + 1 - r, den = 2 * r;
+    int q = num / den;
+    if (num % den != 0 && num < 0) --q;
+    k0 = q;
+    w1 = (double)(num - den * q) / (double)den;
+}
+
+template <typename S>
+__global__ void __launch_bounds__(128) k_interp(S *fbase, const FabInfo *__restrict__ ffabs, const S *cold,
+                                                const S *cnew, const FabInfo *__restrict__ cfabs,
+                                                const InterpRun *__restrict__ runs, int nruns, int ncomp, int ratio,
+                                                double alpha) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int w = warp; w < nruns; w += nwarps) {
+        const InterpRun run = runs[w];
+        const FabInfo ff = ffabs[run.ffab];
+        const FabInfo cf = cfabs[run.cfab];
+        int ky, kz;
+        double wy1, wz1;
+        lin_w(run.J, ratio, ky, wy1);
+        lin_w(run.K, ratio, kz, wz1);
+        const int cy = ky - run.shift[1] - cf.lo[1], cz = kz - run.shift[2] - cf.lo[2];
+        const double wy[2] = {1.0 - wy1, wy1}, wz[2] = {1.0 - wz1, wz1};
+        for (int t = lane; t < run.len; t += 32) {
+            int kx;
+            double wx1;
+            lin_w(run.I + t, ratio, kx, wx1);
+            const int cx = kx - run.shift[0] - cf.lo[0];
+            const double wx[2] = {1.0 - wx1, wx1};
+            for (int c = 0; c < ncomp; ++c) {
+                double v = 0.0;
+#pragma unroll
+                for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+                    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                        for (int dx = 0; dx < 2; ++dx) {
+                            const long long at = cf.org + c * cf.cstride + (long long)(cz + dz) * cf.plane +
+                                                 (long long)(cy + dy) * cf.px + (cx + dx);
+                            const double tv = __dadd_rn(__dmul_rn(1.0 - alpha, to_f64(cold[at])),
+                                                        __dmul_rn(alpha, to_f64(cnew[at])));
+                            v = __dadd_rn(v, __dmul_rn(__dmul_rn(__dmul_rn(wz[dz], wy[dy]), wx[dx]), tv));
+                        }
+                from_f64(fbase + run.fdst + c * ff.cstride + t, v);
+            }
+        }
+    }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256) k_avgdown(const S *fbase, const FabInfo *__restrict__ ffabs, S *cbase,
+                                                 const FabInfo *__restrict__ cfabs, const AvgRegion *__restrict__ regs,
+                                                 int nregs, int ncomp, int ratio) {
+    const double inv = 1.0 / (double)(ratio * ratio * ratio);
+    for (int w = blockIdx.x; w < nregs; w += gridDim.x) {
+        const AvgRegion rg = regs[w];
+        const FabInfo ff = ffabs[rg.ffab];
+        const FabInfo cf = cfabs[rg.cfab];
+        const int cells = rg.n[0] * rg.n[1] * rg.n[2];
+        for (int i = threadIdx.x; i < cells * ncomp; i += blockDim.x) {
+            const int x = i % rg.n[0], y = (i / rg.n[0]) % rg.n[1], z = (i / (rg.n[0] * rg.n[1])) % rg.n[2];
+            const int c = i / cells;
+            const int I = rg.clo[0] + x, J = rg.clo[1] + y, K = rg.clo[2] + z;
+            const S *fp = fbase + ff.org + c * ff.cstride;
+            double s = 0.0;
+            for (int dz = 0; dz < ratio; ++dz)
+                for (int dy = 0; dy < ratio; ++dy)
+                    for (int dx = 0; dx < ratio; ++dx) {
+                        const int fx = I * ratio + dx - ff.lo[0], fy = J * ratio + dy - ff.lo[1],
+                                  fz = K * ratio + dz - ff.lo[2];
+                        s = __dadd_rn(s, to_f64(fp[(long long)fz * ff.plane + (long long)fy * ff.px + fx]));
+                    }
+            from_f64(cbase + cf.org + c * cf.cstride + (long long)(K - cf.lo[2]) * cf.plane +
+                         (long long)(J - cf.lo[1]) * cf.px + (I - cf.lo[0]),
+                     __dmul_rn(s, inv));
+        }
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    }
+    return n;
+}
+
+template <typename K>
+static int persistent_grid(K kernel, int block, int work) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    long long g = (long long)per_sm * sm_count();
+    if (work < g) g = work;
+    return g < 1 ? 1 : (int)g;
+}
+
+cudaError_t launch_fill(int dtype, const LevelPtrs &lv, const FabInfo *ftab, const FbEntry *ent, const FbTask *tasks,
+                        int ntasks, int grid, cudaStream_t s) {
+    if (ntasks == 0) return cudaSuccess;
+    switch (dtype_size(dtype)) {
+        case 8: {
+            int g = grid > 0 ? grid : persistent_grid(k_fill<unsigned long long>, 256, ntasks);
+            k_fill<unsigned long long><<<g, 256, 0, s>>>(lv, ftab, ent, tasks, ntasks);
+            break;
+        }
+        case 4: {
+            int g = grid > 0 ? grid : persistent_grid(k_fill<unsigned int>, 256, ntasks);
+            k_fill<unsigned int><<<g, 256, 0, s>>>(lv, ftab, ent, tasks, ntasks);
+            break;
+        }
+        default: {
+            int g = grid > 0 ? grid : persistent_grid(k_fill<unsigned short>, 256, ntasks);
+            k_fill<unsigned short><<<g, 256, 0, s>>>(lv, ftab, ent, tasks, ntasks);
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_plain(int dtype, void *base, const FabInfo *ftab, const FbEntry *ent, int count,
+                              long long total, const int *cbeg, cudaStream_t s) {
+    if (total == 0) return cudaSuccess;
+    const int blocks = (int)((total + 255) / 256);
+    switch (dtype_size(dtype)) {
+        case 8: k_fill_plain<<<blocks, 256, 0, s>>>((unsigned long long *)base, ftab, ent, count, total, cbeg); break;
+        case 4: k_fill_plain<<<blocks, 256, 0, s>>>((unsigned int *)base, ftab, ent, count, total, cbeg); break;
+        default: k_fill_plain<<<blocks, 256, 0, s>>>((unsigned short *)base, ftab, ent, count, total, cbeg);
+    }
+    return cudaGetLastError();
+}
+
+template <typename S, typename A, int R>
+static cudaError_t stencil_t(const StencilParams &p, int bx, int by, int grid, cudaStream_t s) {
+    dim3 block(bx, by);
+    int g = grid > 0 ? grid : persistent_grid(k_stencil<S, A, R>, bx * by, p.ntiles);
+    k_stencil<S, A, R><<<g, block, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename S, typename A>
+static cudaError_t stencil_r(int R, const StencilParams &p, int bx, int by, int grid, cudaStream_t s) {
+    switch (R) {
+        case 1: return stencil_t<S, A, 1>(p, bx, by, grid, s);
+        case 2: return stencil_t<S, A, 2>(p, bx, by, grid, s);
+        case 4: return stencil_t<S, A, 4>(p, bx, by, grid, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_stencil(int dtype, int R, bool fp64diff, const StencilParams &p, int bx, int by, int grid,
+                           cudaStream_t s) {
+    if (p.ntiles == 0) return cudaSuccess;
+    if (bx * by > 256 || bx <= 0 || by <= 0) return cudaErrorInvalidValue;
+    switch (dtype) {
+        case F64: return stencil_r<double, double>(R, p, bx, by, grid, s);
+        case F32: return fp64diff ? stencil_r<float, double>(R, p, bx, by, grid, s)
+                                  : stencil_r<float, float>(R, p, bx, by, grid, s);
+        case BF16: return fp64diff ? stencil_r<__nv_bfloat16, double>(R, p, bx, by, grid, s)
+                                   : stencil_r<__nv_bfloat16, float>(R, p, bx, by, grid, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename S, typename A, int R>
+static cudaError_t plain_t(const void *src, void *dst, const FabInfo &f, double lam, int comp, cudaStream_t s) {
+    dim3 block(32, 4);
+    dim3 grid((f.n[0] + 31) / 32, (f.n[1] + 3) / 4, f.n[2]);
+    const long long off = (long long)comp * f.cstride;
+    k_stencil_plain<S, A, R><<<grid, block, 0, s>>>((const S *)src + off, (S *)dst + off, f, (A)lam);
+    return cudaGetLastError();
+}
+
+template <typename S, typename A>
+static cudaError_t plain_r(int R, const void *src, void *dst, const FabInfo &f, double lam, int comp,
+                           cudaStream_t s) {
+    switch (R) {
+        case 1: return plain_t<S, A, 1>(src, dst, f, lam, comp, s);
+        case 2: return plain_t<S, A, 2>(src, dst, f, lam, comp, s);
+        case 4: return plain_t<S, A, 4>(src, dst, f, lam, comp, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_stencil_plain(int dtype, int R, const void *src, void *dst, const FabInfo &f, double lam, int comp,
+                                 cudaStream_t s) {
+    switch (dtype) {
+        case F64: return plain_r<double, double>(R, src, dst, f, lam, comp, s);
+        case F32: return plain_r<float, float>(R, src, dst, f, lam, comp, s);
+        case BF16: return plain_r<__nv_bfloat16, float>(R, src, dst, f, lam, comp, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_sum(int dtype, const void *base, const FabInfo *ftab, const Tile *tiles, int ntiles, int comp,
+                       double2 *partials, int grid, double *out_dev, cudaStream_t s) {
+    switch (dtype) {
+        case F64: k_sum_partial<<<grid, 256, 0, s>>>((const double *)base, ftab, tiles, ntiles, comp, partials); break;
+        case F32: k_sum_partial<<<grid, 256, 0, s>>>((const float *)base, ftab, tiles, ntiles, comp, partials); break;
+        default:
+            k_sum_partial<<<grid, 256, 0, s>>>((const __nv_bfloat16 *)base, ftab, tiles, ntiles, comp, partials);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_sum_final<<<1, 256, 0, s>>>(partials, grid, out_dev);
+    return cudaGetLastError();
+}
+
+static cudaError_t dense_common(bool scatter, int dtype, void *base, const FabInfo *ftab, int nfab, double *stage,
+                                const int dlo[3], const int dn[3], int z0, int z1, int comp, int nc, cudaStream_t s) {
+    DenseChunk d;
+    for (int i = 0; i < 3; ++i) { d.dlo[i] = dlo[i]; d.dn[i] = dn[i]; }
+    d.z0 = z0; d.z1 = z1; d.comp = comp; d.nc = nc;
+    if (!scatter) {
+        long long n = (long long)nc * (z1 - z0) * dn[1] * dn[0];
+        k_fill_nan<<<4 * sm_count(), 256, 0, s>>>(stage, n);
+    }
+    dim3 grid(64, nfab);
+    switch (dtype) {
+        case F64:
+            if (scatter) k_dense<double, true><<<grid, 128, 0, s>>>((double *)base, ftab, stage, d);
+            else k_dense<double, false><<<grid, 128, 0, s>>>((double *)base, ftab, stage, d);
+            break;
+        case F32:
+            if (scatter) k_dense<float, true><<<grid, 128, 0, s>>>((float *)base, ftab, stage, d);
+            else k_dense<float, false><<<grid, 128, 0, s>>>((float *)base, ftab, stage, d);
+            break;
+        default:
+            if (scatter) k_dense<__nv_bfloat16, true><<<grid, 128, 0, s>>>((__nv_bfloat16 *)base, ftab, stage, d);
+            else k_dense<__nv_bfloat16, false><<<grid, 128, 0, s>>>((__nv_bfloat16 *)base, ftab, stage, d);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_dense(int dtype, void *base, const FabInfo *ftab, int nfab, const double *stage,
+                                 const int dlo[3], const int dn[3], int z0, int z1, int comp, int nc, cudaStream_t s) {
+    return dense_common(true, dtype, base, ftab, nfab, const_cast<double *>(stage), dlo, dn, z0, z1, comp, nc, s);
+}
+
+cudaError_t launch_gather_dense(int dtype, const void *base, const FabInfo *ftab, int nfab, double *stage,
+                                const int dlo[3], const int dn[3], int z0, int z1, int comp, int nc, cudaStream_t s) {
+    return dense_common(false, dtype, const_cast<void *>(base), ftab, nfab, stage, dlo, dn, z0, z1, comp, nc, s);
+}
+
+cudaError_t launch_interp(int dtype, void *fbase, const FabInfo *ffabs, const void *cold, const void *cnew,
+                          const FabInfo *cfabs, const InterpRun *runs, int nruns, int ncomp, int ratio, double alpha,
+                          cudaStream_t s) {
+    if (nruns == 0) return cudaSuccess;
+    int grid = (nruns + 3) / 4;
+    if (grid > 8 * sm_count()) grid = 8 * sm_count();
+    switch (dtype) {
+        case F64:
+            k_interp<<<grid, 128, 0, s>>>((double *)fbase, ffabs, (const double *)cold, (const double *)cnew, cfabs,
+                                          runs, nruns, ncomp, ratio, alpha);
+            break;
+        case F32:
+            k_interp<<<grid, 128, 0, s>>>((float *)fbase, ffabs, (const float *)cold, (const float *)cnew, cfabs,
+                                          runs, nruns, ncomp, ratio, alpha);
+            break;
+        default:
+            k_interp<<<grid, 128, 0, s>>>((__nv_bfloat16 *)fbase, ffabs, (const __nv_bfloat16 *)cold,
+                                          (const __nv_bfloat16 *)cnew, cfabs, runs, nruns, ncomp, ratio, alpha);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_avgdown(int dtype, const void *fbase, const FabInfo *ffabs, void *cbase, const FabInfo *cfabs,
+                           const AvgRegion *regs, int nregs, int ncomp, int ratio, cudaStream_t s) {
+    if (nregs == 0) return cudaSuccess;
+    int grid = nregs < 4 * sm_count() ? nregs : 4 * sm_count();
+    switch (dtype) {
+        case F64:
+            k_avgdown<<<grid, 256, 0, s>>>((const double *)fbase, ffabs, (double *)cbase, cfabs, regs, nregs, ncomp,
+                                           ratio);
+            break;
+        case F32:
+            k_avgdown<<<grid, 256, 0, s>>>((const float *)fbase, ffabs, (float *)cbase, cfabs, regs, nregs, ncomp,
+                                           ratio);
+            break;
+        default:
+            k_avgdown<<<grid, 256, 0, s>>>((const __nv_bfloat16 *)fbase, ffabs, (__nv_bfloat16 *)cbase, cfabs, regs,
+                                           nregs, ncomp, ratio);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace mfk

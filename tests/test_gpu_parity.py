@@ -1,0 +1,365 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Bars: bit-exact for copies (FillBoundary, dense staging) and for the FP64 interpolation and
+average-down, whose per-cell operation order matches the oracle's; max-norm relative error
+<= 1e-12 for the FP64 stencil sweep; stated, measured bounds for FP32 / BF16 storage.  Inputs
+are seeded; reduced-precision runs give both sides the same inputs rounded to the storage
+type on the host first.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+mf = pytest.importorskip("paper_1604_03570_gb300")
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+
+
+def rel_err(got, ref):
+    """max over components of ||got - ref||_inf / ||ref||_inf over the valid cells."""
+    e = 0.0
+    for c in range(ref.shape[0]):
+        e = max(e, float(np.max(np.abs(got[c] - ref[c])) / np.max(np.abs(ref[c]))))
+    return e
+
+
+def round_to(x, dtype):
+    if dtype == "f64":
+        return np.array(x, dtype=np.float64)
+    if dtype == "f32":
+        return np.asarray(x, dtype=np.float32).astype(np.float64)
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def rand_field(shape, seed, dtype="f64"):
+    return round_to(np.random.default_rng(seed).standard_normal(shape), dtype)
+
+
+UNEVEN = np.array([
+    [0, 0, 0, 9, 15, 7], [10, 0, 0, 23, 6, 7], [10, 7, 0, 23, 15, 7],
+    [0, 0, 8, 5, 15, 19], [6, 0, 8, 23, 8, 12], [6, 9, 8, 23, 15, 12], [6, 0, 13, 23, 15, 19]], dtype=np.int32)
+UNEVEN_DOM = ([0, 0, 0], [23, 15, 19])
+
+
+def gpu_level(lo, hi, boxes=None, mgs=None, ncomp=1, ngrow=1, dtype="f64"):
+    return mf.MultiFab(lo, hi, max_grid_size=mgs, boxes=boxes, ncomp=ncomp, ngrow=ngrow, dtype=dtype)
+
+
+# --------------------------------------------------------------------------- staging copies
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+def test_dense_roundtrip_exact(dtype):
+    lo, hi = UNEVEN_DOM
+    g = gpu_level(lo, hi, boxes=UNEVEN, ncomp=3, ngrow=2, dtype=dtype)
+    dense = rand_field((3, 20, 16, 24), 1, dtype)
+    g.from_host(dense)
+    np.testing.assert_array_equal(g.to_host(), dense)
+
+
+def test_dense_partial_level_gives_nan_outside_boxes():
+    boxes = np.array([[0, 0, 0, 7, 7, 7], [8, 0, 0, 15, 7, 3]], dtype=np.int32)
+    g = gpu_level([0, 0, 0], [15, 15, 15], boxes=boxes, ngrow=1, dtype="f32")
+    dense = rand_field((1, 16, 16, 16), 2, "f32")
+    g.from_host(dense)
+    out = g.to_host()
+    mask = np.zeros((16, 16, 16), dtype=bool)
+    mask[0:8, 0:8, 0:8] = True
+    mask[0:4, 0:8, 8:16] = True
+    np.testing.assert_array_equal(out[0][mask], dense[0][mask])
+    assert np.all(np.isnan(out[0][~mask]))
+
+
+# --------------------------------------------------------------------------- FillBoundary
+
+def _fabs_equal(g, L, odata, nan_ok=False):
+    for b in range(L.nbox):
+        got = g.fab_to_host(b)
+        ref = L.fab(odata, b)
+        np.testing.assert_array_equal(got, ref)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("ngrow", [1, 2, 4])
+def test_fill_boundary_bit_exact(dtype, ngrow):
+    lo, hi = UNEVEN_DOM
+    g = gpu_level(lo, hi, boxes=UNEVEN, ncomp=2, ngrow=ngrow, dtype=dtype)
+    dense = rand_field((2, 20, 16, 24), 3, dtype)
+    g.from_host(dense)
+    g.fill_boundary()
+    L = oracle.Level(UNEVEN, lo, hi, ngrow, 2)
+    u = L.from_dense(dense)
+    oracle.fill_boundary(L, u)
+    _fabs_equal(g, L, u)
+
+
+def test_fill_boundary_partial_level_leaves_unowned_ghosts():
+    boxes = np.array([[8, 8, 8, 15, 23, 15], [16, 8, 8, 23, 15, 19], [0, 0, 24, 7, 7, 31]], dtype=np.int32)
+    lo, hi = [0, 0, 0], [31, 31, 31]
+    g = gpu_level(lo, hi, boxes=boxes, ngrow=2, dtype="f64")
+    L = oracle.Level(boxes, lo, hi, 2, 1)
+    dense = rand_field((1, 32, 32, 32), 4)
+    u = L.from_dense(dense)  # ghosts NaN
+    for b in range(L.nbox):
+        g.fab_from_host(b, L.fab(u, b))
+    g.fill_boundary()
+    oracle.fill_boundary(L, u)
+    _fabs_equal(g, L, u)
+
+
+# --------------------------------------------------------------------------- stencil sweep, FP64
+
+def _oracle_advance(boxes, lo, hi, g, C, R, lam, nsteps, dense):
+    L = oracle.Level(boxes, lo, hi, g, C)
+    return L.to_dense(oracle.advance(L, L.from_dense(dense), R, lam, nsteps))
+
+
+@pytest.mark.parametrize("R", [1, 2, 4])
+@pytest.mark.parametrize("layout", ["uniform", "uneven"])
+def test_advance_fp64_matches_oracle(R, layout):
+    """Uniform 16^3 boxes of a 32^3 domain, or the non-cubic 24x16x20 domain in 7 uneven
+    boxes (cells of side 1/N_x); ragged 12x5x7 tiles; 2 components."""
+    if layout == "uniform":
+        lo, hi = [0, 0, 0], [31, 31, 31]
+        boxes = oracle.chop(lo, hi, 16)
+    else:
+        lo, hi = UNEVEN_DOM
+        boxes = UNEVEN
+    shape = tuple(h - l + 1 for l, h in zip(lo[::-1], hi[::-1]))
+    C = 2
+    D = np.array([1.0, 0.625])
+    Nx = hi[0] - lo[0] + 1
+    dt = {1: 0.15, 2: 0.1125, 4: 0.09}[R] / float(Nx * Nx)
+    lam = D * dt * float(Nx * Nx)
+    dense = np.stack([synth.eval_modes(shape, synth.sine_modes(1604, 10 + c, 8, 8)) for c in range(C)])
+    nsteps = 7
+    g = gpu_level(lo, hi, boxes=boxes, ncomp=C, ngrow=R, dtype="f64")
+    g.set_tile((12, 5, 7))  # ragged tiles
+    g.from_host(dense)
+    g.advance(R, D, dt, nsteps)
+    ref = _oracle_advance(boxes, lo, hi, R, C, R, lam, nsteps, dense)
+    assert rel_err(g.to_host(), ref) <= FP64_TOL
+
+
+CUBE_UNEVEN = np.array([
+    [0, 0, 0, 15, 23, 7], [16, 0, 0, 31, 8, 7], [16, 9, 0, 31, 31, 7], [0, 24, 0, 15, 31, 7],
+    [0, 0, 8, 7, 31, 31], [8, 0, 8, 31, 15, 20], [8, 16, 8, 31, 31, 20], [8, 0, 21, 31, 31, 31]], dtype=np.int32)
+
+
+@pytest.mark.parametrize("R", [1, 2, 4])
+def test_advance_fp64_uneven_boxes_matches_oracle(R):
+    lo, hi = [0, 0, 0], [31, 31, 31]
+    C = 2
+    D = np.array([1.0, 1.75])
+    dt = {1: 0.15, 2: 0.1125, 4: 0.09}[R] / (1.75 * 32 * 32)
+    lam = D * dt * float(32 * 32)
+    dense = np.stack([synth.eval_modes((32, 32, 32), synth.sine_modes(1604, 20 + c, 8, 8)) for c in range(C)])
+    dense += synth.noise(1604, 30, dense.shape, 1e-3)
+    g = gpu_level(lo, hi, boxes=CUBE_UNEVEN, ncomp=C, ngrow=R, dtype="f64")
+    g.from_host(dense)
+    g.advance(R, D, dt, 6)
+    ref = _oracle_advance(CUBE_UNEVEN, lo, hi, R, C, R, lam, 6, dense)
+    assert rel_err(g.to_host(), ref) <= FP64_TOL
+
+
+def test_heat64_fp64_workload_matches_oracle():
+    """The 64^3 / 8 boxes of 32^3 / 10-step FP64 workload at full size."""
+    cfg = synth.WORKLOADS["c1"]
+    N = cfg["N"]
+    lo, hi = [0, 0, 0], [N - 1] * 3
+    dense = synth.initial_field(cfg)
+    dt = synth.dt_for(cfg)
+    g = gpu_level(lo, hi, mgs=cfg["max_grid_size"], ngrow=1, dtype="f64")
+    g.set_tile(None)  # autotuned
+    g.from_host(dense)
+    g.advance(1, [1.0], dt, cfg["nsteps"])
+    ref = _oracle_advance(oracle.chop(lo, hi, 32), lo, hi, 1, 1, 1, 1.0 * dt * float(N * N), cfg["nsteps"], dense)
+    assert rel_err(g.to_host(), ref) <= FP64_TOL
+
+
+def test_odd_and_even_step_counts_and_graph_replay():
+    """Graph replay from either time level: 3 + 4 + 3 steps equal 10 steps of the oracle."""
+    lo, hi = [0, 0, 0], [23, 23, 23]
+    dense = rand_field((1, 24, 24, 24), 8)
+    dt = 0.1 / (24 * 24)
+    g = gpu_level(lo, hi, mgs=12, ngrow=1, dtype="f64")
+    g.set_tile((12, 4, 4))
+    g.from_host(dense)
+    for n in (3, 4, 3):
+        g.advance(1, [1.0], dt, n)
+    ref = _oracle_advance(oracle.chop(lo, hi, 12), lo, hi, 1, 1, 1, 1.0 * dt * 576.0, 10, dense)
+    assert rel_err(g.to_host(), ref) <= FP64_TOL
+
+
+# --------------------------------------------------------------------------- layout invariance
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("R", [1, 4])
+def test_layout_and_tile_invariance_bitwise(dtype, R):
+    """Sec. 3.2: tiling changes the access pattern, not the data: identical bits for every
+    box layout, tile shape and for the untiled per-box baseline."""
+    lo, hi = [0, 0, 0], [31, 31, 31]
+    dense = rand_field((1, 32, 32, 32), 9, dtype)
+    dt = 0.05 / 1024
+    outs = []
+    for boxes, tile, flags in [(oracle.chop(lo, hi, 32), (0, 0, 0), 0), (oracle.chop(lo, hi, 16), (16, 4, 4), 0),
+                               (CUBE_UNEVEN, (7, 3, 5), 0), (oracle.chop(lo, hi, 8), (8, 8, 8), 0),
+                               (oracle.chop(lo, hi, 16), (0, 0, 0), mf.MF_PLAIN_PER_BOX)]:
+        g = gpu_level(lo, hi, boxes=boxes, ngrow=R, dtype=dtype)
+        g.set_tile(tile)
+        g.from_host(dense)
+        g.advance(R, [1.0], dt, 5, flags)
+        outs.append(g.to_host())
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o, outs[0])
+
+
+# --------------------------------------------------------------------------- reduced precision
+
+@pytest.mark.parametrize("dtype,bound", [("f32", 2e-6), ("bf16", 3e-2)])
+def test_reduced_precision_error_bound(dtype, bound):
+    """FP32 / BF16 storage with FP32 arithmetic against the FP64 oracle on the same rounded
+    input: the stated bound (parity unpinned analytically; measured)."""
+    lo, hi = [0, 0, 0], [31, 31, 31]
+    dense = round_to(synth.eval_modes((32, 32, 32), synth.sine_modes(1604, 40, 8, 8))[None], dtype)
+    dt = 0.15 / 1024
+    g = gpu_level(lo, hi, mgs=16, ngrow=1, dtype=dtype)
+    g.from_host(dense)
+    g.advance(1, [1.0], dt, 10)
+    ref = _oracle_advance(oracle.chop(lo, hi, 16), lo, hi, 1, 1, 1, 0.15, 10, dense)
+    err = rel_err(g.to_host(), ref)
+    print("%s rel err after 10 steps: %.3e" % (dtype, err))
+    assert err <= bound
+
+
+def test_fp32_fp64_diff_flag_is_at_least_as_accurate():
+    lo, hi = [0, 0, 0], [31, 31, 31]
+    dense = round_to(synth.eval_modes((32, 32, 32), synth.sine_modes(1604, 41, 8, 4))[None], "f32")
+    dt = 0.09 / 1024
+    errs = []
+    for flags in (0, mf.MF_FP64_DIFF):
+        g = gpu_level(lo, hi, mgs=16, ngrow=4, dtype="f32")
+        g.from_host(dense)
+        g.advance(4, [1.0], dt, 10, flags)
+        errs.append(rel_err(g.to_host(), _oracle_advance(oracle.chop(lo, hi, 16), lo, hi, 4, 1, 4, 0.09, 10, dense)))
+    print("R=4 FP32 rel err: fp32 arithmetic %.3e, fp64 differences %.3e" % tuple(errs))
+    assert errs[1] <= errs[0] * 1.01 and errs[1] < 1e-6
+
+
+# --------------------------------------------------------------------------- reduction
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_sum_matches_fsum(dtype):
+    lo, hi = [0, 0, 0], [31, 31, 31]
+    dense = round_to(1.0 + np.random.default_rng(5).standard_normal((2, 32, 32, 32)), dtype)
+    g = gpu_level(lo, hi, boxes=CUBE_UNEVEN, ncomp=2, ngrow=1, dtype=dtype)
+    g.from_host(dense)
+    for c in range(2):
+        exact = math.fsum(dense[c].ravel().tolist())
+        got = g.sum(c)
+        assert abs(got - exact) <= 2 * math.ulp(abs(exact)), (got, exact)
+
+
+def test_conservation_fp64():
+    lo, hi = [0, 0, 0], [31, 31, 31]
+    dense = 1.0 + rand_field((1, 32, 32, 32), 6)
+    g = gpu_level(lo, hi, boxes=CUBE_UNEVEN, ngrow=2, dtype="f64")
+    g.from_host(dense)
+    s0 = g.sum(0)
+    g.advance(2, [1.0], 0.1 / 1024, 20)
+    s1 = g.sum(0)
+    mass = math.fsum(np.abs(dense).ravel().tolist())
+    assert abs(s1 - s0) <= 20 * 1e-15 * mass
+
+
+# --------------------------------------------------------------------------- AMR
+
+def _two_level(dtype="f64", C=1):
+    Nc = 16
+    clo, chi = [0, 0, 0], [Nc - 1] * 3
+    fboxes = np.array([[8, 8, 8, 15, 23, 15], [16, 8, 8, 23, 15, 19], [0, 0, 24, 7, 7, 31]], dtype=np.int32)
+    flo, fhi = [0, 0, 0], [2 * Nc - 1] * 3
+    return Nc, clo, chi, oracle.chop(clo, chi, 8), flo, fhi, fboxes
+
+
+def test_interp_cf_bit_exact_fp64():
+    Nc, clo, chi, cboxes, flo, fhi, fboxes = _two_level()
+    cold = rand_field((1, Nc, Nc, Nc), 11)
+    cnew = rand_field((1, Nc, Nc, Nc), 12)
+    gc_old = gpu_level(clo, chi, boxes=cboxes, ngrow=1)
+    gc_new = gpu_level(clo, chi, boxes=cboxes, ngrow=1)
+    gf = gpu_level(flo, fhi, boxes=fboxes, ngrow=2)
+    gc_old.from_host(cold)
+    gc_new.from_host(cnew)
+    gc_old.fill_boundary()
+    gc_new.fill_boundary()
+    CL = oracle.Level(cboxes, clo, chi, 1, 1)
+    FL = oracle.Level(fboxes, flo, fhi, 2, 1)
+    fd = FL.from_dense(rand_field((1, 2 * Nc, 2 * Nc, 2 * Nc), 13))
+    for b in range(FL.nbox):
+        gf.fab_from_host(b, FL.fab(fd, b))
+    mf.mf_interp_cf(gf.h, gc_old.h, gc_new.h, 0.5, 2)
+    oracle.interp_cf(FL, CL, 2, 0.5, CL.from_dense(cold), CL.from_dense(cnew), fd)
+    _fabs_equal(gf, FL, fd)
+
+
+def test_average_down_bit_exact_fp64():
+    Nc, clo, chi, cboxes, flo, fhi, fboxes = _two_level()
+    gc = gpu_level(clo, chi, boxes=cboxes, ngrow=1)
+    gf = gpu_level(flo, fhi, boxes=fboxes, ngrow=1)
+    cden = rand_field((1, Nc, Nc, Nc), 14)
+    fden = rand_field((1, 2 * Nc, 2 * Nc, 2 * Nc), 15)
+    gc.from_host(cden)
+    gf.from_host(fden)
+    mf.mf_average_down(gf.h, gc.h, 2)
+    CL = oracle.Level(cboxes, clo, chi, 1, 1)
+    FL = oracle.Level(fboxes, flo, fhi, 1, 1)
+    cd = CL.from_dense(cden)
+    oracle.average_down(FL, CL, 2, FL.from_dense(fden), cd)
+    np.testing.assert_array_equal(gc.to_host(), CL.to_dense(cd))
+
+
+def test_amr_advance_fp64_matches_oracle():
+    Nc, clo, chi, cboxes, flo, fhi, fboxes = _two_level()
+    modes = synth.sine_modes(1604, 50, 4, 3)
+    cden = synth.eval_modes((Nc, Nc, Nc), modes)[None]
+    fden = synth.eval_modes((2 * Nc,) * 3, modes)[None]
+    dt_c = 0.075 / (Nc * Nc)
+    gc = gpu_level(clo, chi, boxes=cboxes, ngrow=1)
+    gf = gpu_level(flo, fhi, boxes=fboxes, ngrow=1)
+    gc.from_host(cden)
+    gf.from_host(fden)
+    mf.mf_amr_advance(gc.h, gf.h, 1, [1.0], dt_c, 3, 2, 2)
+    CL = oracle.Level(cboxes, clo, chi, 1, 1)
+    FL = oracle.Level(fboxes, flo, fhi, 1, 1)
+    c_out, f_out = oracle.amr_advance(CL, FL, 1, 1.0 * dt_c * float(Nc * Nc), CL.from_dense(cden),
+                                      FL.from_dense(fden), 3)
+    assert rel_err(gc.to_host(), CL.to_dense(c_out)) <= FP64_TOL
+    fo, fr = gf.to_host(), FL.to_dense(f_out)
+    mask = ~np.isnan(fr)
+    np.testing.assert_array_equal(mask, ~np.isnan(fo))
+    assert float(np.max(np.abs(fo[mask] - fr[mask])) / np.max(np.abs(fr[mask]))) <= FP64_TOL
+
+
+# --------------------------------------------------------------------------- errors on the GPU path
+
+def test_unstable_dt_rejected():
+    g = gpu_level([0, 0, 0], [15, 15, 15], mgs=8, ngrow=1)
+    with pytest.raises(mf.MFError) as e:
+        g.advance(1, [1.0], 0.2 / 256, 1)
+    assert e.value.code == mf.MF_EUNSTABLE
+
+
+def test_phase_timing_reports_both_phases():
+    g = gpu_level([0, 0, 0], [63, 63, 63], mgs=32, ngrow=1, dtype="f32")
+    g.from_host(rand_field((1, 64, 64, 64), 16, "f32"))
+    mf.mf_set_timing(g.h, 1)
+    g.advance(1, [1.0], 0.1 / 4096, 6)
+    fill_ms, st_ms = mf.mf_phase_ms(g.h)
+    assert fill_ms > 0 and st_ms > 0

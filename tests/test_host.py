@@ -1,0 +1,199 @@
+"""Host-side tests of libmf (no GPU): the library loads and exports the C ABI, the box chop and
+the FillBoundary intersection lists are right, argument errors come back as error codes.
+
+The FillBoundary list is checked against the definition (Sec. 3.1): every ghost cell of
+every box is written exactly once, from the valid cell owning its periodic point."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+mf = pytest.importorskip("paper_1604_03570_gb300")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "mf.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(mf_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    names = declared_symbols()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(mf.lib, n), n
+    assert sorted(mf.EXPORTS) == names
+
+
+@pytest.mark.parametrize("N,mgs", [((64, 64, 64), 32), ((10, 4, 5), 4), ((256, 256, 256), 64)])
+def test_chop_matches_oracle(N, mgs):
+    lo, hi = [0, 0, 0], [N[0] - 1, N[1] - 1, N[2] - 1]
+    h = mf.mf_create(lo, hi, mgs, 1, 1, "f64")
+    try:
+        np.testing.assert_array_equal(mf.mf_get_boxes(h), oracle.chop(lo, hi, mgs))
+    finally:
+        mf.mf_destroy(h)
+
+
+def _check_fb_regions(h, boxes, dlo, dhi, g, expect_cover=True):
+    """Brute-force set check of the FillBoundary list."""
+    regs = mf.mf_get_fb_regions(h)
+    L = [dhi[d] - dlo[d] + 1 for d in range(3)]
+    written = {}
+    for r in regs:
+        db, sb = int(r[0]), int(r[1])
+        dl, sl, n = r[2:5], r[5:8], r[8:11]
+        assert np.all(n > 0)
+        B, A = boxes[db], boxes[sb]
+        for d in range(3):
+            # source inside the source box's valid region
+            assert A[d] <= sl[d] and sl[d] + n[d] - 1 <= A[3 + d]
+            # destination inside the grown destination box, and a periodic image of the source
+            assert B[d] - g <= dl[d] and dl[d] + n[d] - 1 <= B[3 + d] + g
+            assert (dl[d] - sl[d]) % L[d] == 0
+        for z in range(n[2]):
+            for y in range(n[1]):
+                for x in range(n[0]):
+                    key = (db, dl[0] + x, dl[1] + y, dl[2] + z)
+                    assert key not in written, "ghost cell written twice"
+                    written[key] = sb
+    # every written cell is a ghost cell, and (for covering levels) every ghost cell is written
+    for (db, i, j, k) in written:
+        B = boxes[db]
+        assert not (B[0] <= i <= B[3] and B[1] <= j <= B[4] and B[2] <= k <= B[5])
+    if expect_cover:
+        total = sum(int(np.prod(B[3:] - B[:3] + 1 + 2 * g) - np.prod(B[3:] - B[:3] + 1)) for B in boxes)
+        assert len(written) == total
+    return len(written)
+
+
+def test_fb_list_covers_every_ghost_once_uniform():
+    lo, hi = [0, 0, 0], [15, 15, 15]
+    h = mf.mf_create(lo, hi, 8, 1, 2, "f32")
+    try:
+        boxes = mf.mf_get_boxes(h)
+        n = _check_fb_regions(h, boxes, lo, hi, 2)
+        assert mf.mf_fb_regions(h)[1] == n
+    finally:
+        mf.mf_destroy(h)
+
+
+def test_fb_list_covers_every_ghost_once_uneven():
+    lo, hi = [0, 0, 0], [11, 7, 9]
+    boxes = np.array([
+        [0, 0, 0, 4, 7, 3], [5, 0, 0, 11, 2, 3], [5, 3, 0, 11, 7, 3],
+        [0, 0, 4, 2, 7, 9], [3, 0, 4, 11, 4, 6], [3, 5, 4, 11, 7, 6], [3, 0, 7, 11, 7, 9]], dtype=np.int32)
+    h = mf.mf_create_boxes(lo, hi, boxes, 2, 2, "f64")
+    try:
+        _check_fb_regions(h, boxes, lo, hi, 2)
+    finally:
+        mf.mf_destroy(h)
+
+
+def test_fb_list_partial_level_matches_oracle_count():
+    lo, hi = [0, 0, 0], [31, 31, 31]
+    boxes = np.array([[8, 8, 8, 15, 23, 15], [16, 8, 8, 23, 15, 19], [0, 0, 24, 7, 7, 31]], dtype=np.int32)
+    h = mf.mf_create_boxes(lo, hi, boxes, 1, 1, "f32")
+    try:
+        n = _check_fb_regions(h, boxes, lo, hi, 1, expect_cover=False)
+        L = oracle.Level(boxes, lo, hi, 1, 1)
+        u = L.from_dense(np.zeros((1, 32, 32, 32)))
+        assert n == oracle.fill_boundary(L, u)
+    finally:
+        mf.mf_destroy(h)
+
+
+def test_many_small_boxes_list_builds_quickly():
+    """4096+ uneven boxes: the bin hash keeps the list build far from O(n^2)."""
+    import time
+    boxes = synth.uneven_boxes(256, 8192 // 8)
+    t0 = time.time()
+    h = mf.mf_create_boxes([0, 0, 0], [255, 255, 255], boxes, 2, 2, "f32")
+    try:
+        n, ghosts = mf.mf_fb_regions(h)
+        assert n > 0 and ghosts > 0
+        total = sum(int(np.prod(B[3:] - B[:3] + 1 + 4) - np.prod(B[3:] - B[:3] + 1)) for B in boxes)
+        assert ghosts == total
+    finally:
+        mf.mf_destroy(h)
+    assert time.time() - t0 < 20
+
+
+def test_step_bytes_formula():
+    h = mf.mf_create([0, 0, 0], [255, 255, 255], 64, 1, 1, "f32")
+    try:
+        V = 256 ** 3
+        G = 64 * (66 ** 3 - 64 ** 3)
+        Gf = 64 * 6 * 64 * 64
+        assert mf.mf_fb_regions(h)[1] == G
+        assert mf.mf_step_bytes(h, 1) == 4 * (2 * V + 2 * G + Gf)
+    finally:
+        mf.mf_destroy(h)
+
+
+def test_layout_bytes_alignment():
+    for dt, s in (("f64", 8), ("f32", 4), ("bf16", 2)):
+        h = mf.mf_create([0, 0, 0], [63, 63, 63], 32, 3, 1, dt)
+        try:
+            b = mf.mf_bytes(h)
+            assert b % 512 == 0
+            assert b >= 2 * 3 * 8 * 34 ** 3 * s
+        finally:
+            mf.mf_destroy(h)
+
+
+@pytest.mark.parametrize("bad", ["overlap", "outside", "ngrow", "ncomp", "dtype", "empty"])
+def test_create_rejects_bad_arguments(bad):
+    lo, hi = [0, 0, 0], [15, 15, 15]
+    boxes = [[0, 0, 0, 7, 7, 7], [8, 0, 0, 15, 7, 7]]
+    kw = dict(ncomp=1, ngrow=1, dtype="f64")
+    if bad == "overlap":
+        boxes = [[0, 0, 0, 7, 7, 7], [7, 0, 0, 15, 7, 7]]
+    elif bad == "outside":
+        boxes = [[0, 0, 0, 7, 7, 16]]
+    elif bad == "ngrow":
+        kw["ngrow"] = 16
+    elif bad == "ncomp":
+        kw["ncomp"] = 0
+    elif bad == "dtype":
+        kw["dtype"] = 7
+    elif bad == "empty":
+        boxes = [[0, 0, 0, 7, -1, 7]]
+    with pytest.raises(mf.MFError) as e:
+        mf.mf_create_boxes(lo, hi, boxes, kw["ncomp"], kw["ngrow"], kw["dtype"])
+    assert e.value.code == mf.MF_EINVAL
+
+
+def test_calls_before_attach_fail_with_state_error():
+    h = mf.mf_create([0, 0, 0], [15, 15, 15], 8, 1, 1, "f32")
+    try:
+        with pytest.raises(mf.MFError) as e:
+            mf.mf_fill_boundary(h)
+        assert e.value.code == mf.MF_ESTATE
+        with pytest.raises(mf.MFError) as e:
+            mf.mf_advance(h, 1, [1.0], 1e-6, 1)
+        assert e.value.code == mf.MF_ESTATE
+        with pytest.raises(mf.MFError) as e:
+            mf.mf_attach(h, 0x1001, 1 << 30, 0)
+        assert e.value.code == mf.MF_EALIGN
+    finally:
+        mf.mf_destroy(h)
+
+
+def test_set_tile_roundtrip():
+    h = mf.mf_create([0, 0, 0], [63, 63, 63], 32, 1, 1, "f32")
+    try:
+        assert mf.mf_get_tile(h)[1] is True
+        mf.mf_set_tile(h, (32, 8, 4))
+        assert mf.mf_get_tile(h) == ((32, 8, 4), False)
+        mf.mf_set_tile(h, None)
+        assert mf.mf_get_tile(h)[1] is True
+    finally:
+        mf.mf_destroy(h)
