@@ -45,6 +45,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--dtype", default="f32", choices=["f32", "f64", "bf16"])
     p.add_argument("--no-extras", action="store_true", help="headline only (no FP64, e2e, CPU baseline)")
+    p.add_argument("--tile", default=None, help="fixed tile 'x,y,z' instead of the autotuner (0 = whole box)")
     return p.parse_args()
 
 
@@ -253,6 +254,8 @@ def run_ours(args, cfg, ws, rank, local):
 
     # ---- headline: batched, graph-captured sweep
     head = level(args.dtype)
+    if args.tile:
+        head.set_tile(tuple(int(v) for v in args.tile.split(",")))
     for _ in range(args.warmup):
         mf.mf_advance(head.h, R, D, dt, nsteps)
     torch.cuda.synchronize()
@@ -275,8 +278,6 @@ def run_ours(args, cfg, ws, rank, local):
     mf.mf_set_timing(head.h, 1)
     for _ in range(2):
         mf.mf_advance(head.h, R, D, dt, nsteps)
-    fill_ms = st_ms = 0.0
-    tim_total = time_advances(head, R, D, dt, nsteps, 1, flush)  # recapture + warm
     fill_ms, st_ms = 0.0, 0.0
     t_timed = []
     for _ in range(args.steps):

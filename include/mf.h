@@ -109,7 +109,9 @@ long long mf_get_fb_regions(const mf_t *mf, int *out, long long max);
 int mf_attach(mf_t *mf, void *dev_ptr, size_t bytes, void *cuda_stream);
 
 /* Tile shape of the stencil sweep (Sec. 3.2 MFIter(mf, tilesize)); tile[d] <= 0 along a
- * direction means "whole box".  tile == NULL selects the autotuner on the next advance. */
+ * direction means "whole box".  tile == NULL selects the autotuner on the next advance.
+ * Synchronises the stream; may grow the device work list (the one allocation after attach,
+ * never made while advancing). */
 int mf_set_tile(mf_t *mf, const int tile[3]);
 int mf_get_tile(const mf_t *mf, int tile[3]);
 

@@ -559,7 +559,11 @@ static int set_tiles(mf_t *m, const int t[3]) {
     for (int d = 0; d < 3; ++d) m->tile[d] = t[d];
     make_tiles(m, m->tile, m->tiles);
     if (m->attached) {
-        if (m->tiles.size() > m->tile_capacity) return fail(MF_EINVAL, "tile list larger than its buffer");
+        if (m->tiles.size() > m->tile_capacity) {  // only from mf_set_tile, never while advancing
+            int rc = m->d_tiles.ensure(m->tiles.size() * sizeof(Tile));
+            if (rc) return rc;
+            m->tile_capacity = m->tiles.size();
+        }
         CU(cudaMemcpyAsync(m->d_tiles.p, m->tiles.data(), m->tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice,
                            m->stream));
         CU(cudaStreamSynchronize(m->stream));
@@ -576,12 +580,6 @@ extern "C" int mf_set_tile(mf_t *m, const int tile[3]) {
     }
     for (int d = 0; d < 3; ++d)
         if (tile[d] > 32767) return fail(MF_EINVAL, "tile size too large");
-    if (m->attached) {
-        std::vector<Tile> tmp;
-        make_tiles(m, tile, tmp);
-        if (tmp.size() > m->tile_capacity) return fail(MF_EINVAL, "tile %dx%dx%d gives more tiles than the work-list "
-                                                                  "buffer sized at attach", tile[0], tile[1], tile[2]);
-    }
     m->tile_auto = false;
     return set_tiles(m, tile);
 }
@@ -861,7 +859,9 @@ static int ensure_events(mf_t *m, int n) {
 }
 
 static int record(mf_t *m, int i) {
-    CU(cudaEventRecord(m->ev[i], m->cap));
+    // an external record node: the event is recorded when the graph runs, and can be
+    // synchronised on and timed afterwards
+    CU(cudaEventRecordWithFlags(m->ev[i], m->cap, cudaEventRecordExternal));
     return 0;
 }
 
