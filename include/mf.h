@@ -115,6 +115,12 @@ int mf_attach(mf_t *mf, void *dev_ptr, size_t bytes, void *cuda_stream);
 int mf_set_tile(mf_t *mf, const int tile[3]);
 int mf_get_tile(const mf_t *mf, int tile[3]);
 
+/* Stencil kernel variant.  MF_KERNEL_TMA (default): tile planes staged into shared memory by
+ * TMA bulk-tensor copies (used whenever the tile shape fits, else the next one).
+ * MF_KERNEL_GLOBAL: neighbours read through L1 from global memory.  Both give identical bits. */
+enum { MF_KERNEL_TMA = 0, MF_KERNEL_GLOBAL = 1 };
+int mf_set_kernel(mf_t *mf, int variant);
+
 /*
  * Dense host arrays are (ncomp, Nz, Ny, Nx) doubles over the whole domain, x fastest.
  * mf_copy_from_host writes the valid cells of every box of the current time level

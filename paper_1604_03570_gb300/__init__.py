@@ -20,6 +20,7 @@ MF_F64, MF_F32, MF_BF16 = 0, 1, 2
 DTYPES = {"f64": MF_F64, "f32": MF_F32, "bf16": MF_BF16}
 MF_LAP2_7PT, MF_LAP4_13PT, MF_LAP8_25PT = 1, 2, 4
 MF_FP64_DIFF, MF_PLAIN_PER_BOX = 1, 2
+MF_KERNEL_TMA, MF_KERNEL_GLOBAL = 0, 1
 MF_EINVAL, MF_ENOMEM, MF_ECUDA, MF_EUNSTABLE, MF_EALIGN, MF_ESTATE = -1, -2, -3, -4, -5, -6
 
 EXPORTS = [
@@ -27,7 +28,7 @@ EXPORTS = [
     "mf_get_fb_regions", "mf_attach", "mf_set_tile", "mf_get_tile", "mf_copy_from_host", "mf_copy_to_host",
     "mf_copy_fab_to_host", "mf_copy_fab_from_host", "mf_fill_boundary", "mf_interp_cf", "mf_average_down",
     "mf_advance", "mf_amr_advance", "mf_sum", "mf_step_bytes", "mf_current", "mf_last_error", "mf_set_timing",
-    "mf_phase_ms",
+    "mf_phase_ms", "mf_set_kernel",
 ]
 
 
@@ -75,6 +76,7 @@ def _load():
         "mf_last_error": (ctypes.c_char_p, []),
         "mf_set_timing": (I, [P, I]),
         "mf_phase_ms": (I, [P, P]),
+        "mf_set_kernel": (I, [P, I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -239,6 +241,10 @@ def mf_step_bytes(h, R):
 
 def mf_current(h):
     return _check(lib.mf_current(h))
+
+
+def mf_set_kernel(h, variant):
+    _check(lib.mf_set_kernel(h, int(variant)))
 
 
 def mf_set_timing(h, on):

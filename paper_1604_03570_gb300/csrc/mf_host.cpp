@@ -13,6 +13,8 @@
 //                                device work list for all boxes
 //   thread-private arenas        Sec. 3.3: nothing allocates while advancing; every list and
 //                                scratch buffer is sized at attach
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -210,6 +212,12 @@ struct mf {
     int cur = 0;
     bool attached = false;
     DevBuf d_fabs, d_fb, d_fbtasks, d_tiles, d_cbeg, d_partials, d_sumout;
+    // TMA-staged stencil: tensor maps of every FArrayBox over each time level, plane geometry
+    DevBuf d_maps, d_tfab, d_err;
+    int tma_R = 0;            // radius the maps were encoded for (0 = none)
+    bool tma_ok = false;      // current tile shape fits the TMA kernel
+    int tma_cpt = 1, tma_slot = 0, tma_ns = 0;
+    bool use_tma = true;
     double *h_sum = nullptr;       // pinned
     size_t tile_capacity = 0;
     std::map<std::string, std::unique_ptr<GraphExec>> graphs;
@@ -240,8 +248,10 @@ static void build_layout(mf_t *m) {
     for (auto &b : m->boxes) {
         FabInfo f{};
         for (int d = 0; d < 3; ++d) { f.n[d] = b.len(d); f.lo[d] = b.lo[d]; }
-        const int fpad = (A - g % A) % A;  // puts x = lo on a 16-byte boundary
-        f.px = (int)(((long long)fpad + f.n[0] + 2 * g + A - 1) / A * A);
+        // every row starts 16-byte aligned at its first ghost cell (x = -g), so a TMA plane load
+        // of a tile with its x halo starts on a 16-byte boundary when the halo equals ngrow
+        const int fpad = 0;
+        f.px = (int)(((long long)f.n[0] + 2 * g + A - 1) / A * A);
         const long long py = f.n[1] + 2 * g, nzg = f.n[2] + 2 * g;
         f.plane = (long long)f.px * py;
         f.cstride = f.plane * nzg;
@@ -543,6 +553,11 @@ extern "C" int mf_attach(mf_t *m, void *dev_ptr, size_t bytes, void *stream) {
     if ((rc = m->d_tiles.ensure(cap * sizeof(Tile)))) return rc;
     CU(cudaMemcpyAsync(m->d_tiles.p, m->tiles.data(), m->tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice, m->stream));
     if ((rc = m->d_partials.ensure(512 * sizeof(double2)))) return rc;
+    if ((rc = m->d_maps.ensure(2 * m->fabs.size() * sizeof(CUtensorMap)))) return rc;
+    if ((rc = m->d_tfab.ensure(m->fabs.size() * sizeof(TmaFab)))) return rc;
+    if ((rc = m->d_err.ensure(sizeof(int)))) return rc;
+    CU(cudaMemsetAsync(m->d_err.p, 0, sizeof(int), m->stream));
+    m->tma_R = 0;
     if ((rc = m->d_sumout.ensure(sizeof(double)))) return rc;
     CU(cudaStreamSynchronize(m->stream));  // host vectors may change after return
     m->attached = true;
@@ -552,6 +567,17 @@ extern "C" int mf_attach(mf_t *m, void *dev_ptr, size_t bytes, void *stream) {
 static int need_attached(const mf_t *m) {
     if (!m) return fail(MF_EINVAL, "null handle");
     if (!m->attached) return fail(MF_ESTATE, "handle not attached");
+    return 0;
+}
+
+static int check_device_error(mf_t *m) {
+    if (!m->d_err.p) return 0;
+    int e = 0;
+    CU(cudaMemcpy(&e, m->d_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        cudaMemsetAsync(m->d_err.p, 0, sizeof(int), m->stream);
+        return fail(MF_ECUDA, "a bounded wait inside a stencil kernel expired (device error word %d)", e);
+    }
     return 0;
 }
 
@@ -569,6 +595,7 @@ static int set_tiles(mf_t *m, const int t[3]) {
         CU(cudaStreamSynchronize(m->stream));
         invalidate_graphs(m);
     }
+    m->tma_R = 0;  // plane geometry follows the tile shape
     return 0;
 }
 
@@ -582,6 +609,15 @@ extern "C" int mf_set_tile(mf_t *m, const int tile[3]) {
         if (tile[d] > 32767) return fail(MF_EINVAL, "tile size too large");
     m->tile_auto = false;
     return set_tiles(m, tile);
+}
+
+extern "C" int mf_set_kernel(mf_t *m, int variant) {
+    if (!m) return fail(MF_EINVAL, "null handle");
+    if (variant != MF_KERNEL_TMA && variant != MF_KERNEL_GLOBAL) return fail(MF_EINVAL, "unknown kernel variant");
+    m->use_tma = variant == MF_KERNEL_TMA;
+    m->tma_R = 0;
+    invalidate_graphs(m);
+    return 0;
 }
 
 extern "C" int mf_get_tile(const mf_t *m, int tile[3]) {
@@ -643,7 +679,7 @@ extern "C" int mf_copy_to_host(mf_t *m, double *dense) {
                                cudaMemcpyDeviceToHost, m->stream));
         }
     CU(cudaStreamSynchronize(m->stream));
-    return 0;
+    return check_device_error(m);
 }
 
 // Host conversions for the FArrayBox debug copies.
@@ -731,6 +767,95 @@ extern "C" int mf_copy_fab_from_host(mf_t *m, int box, const double *in) {
     return 0;
 }
 
+// ------------------------------------------------------------------ TMA tensor maps
+
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)ptr;
+    }
+    return fn;
+}
+
+// Plane geometry of every FArrayBox for the current tile shape and radius R; false when a
+// box needs a plane wider than the TMA box limit (256 per dimension) or more cells per
+// thread than the kernel keeps in registers.
+static bool tma_geometry(mf_t *m, int R, std::vector<TmaFab> &tf, int &slot_bytes, int &cpt) {
+    const int S = m->esize, A = 16 / S, g = m->ngrow;
+    tf.assign(m->fabs.size(), TmaFab{});
+    int maxplane = 0, maxcells = 0;
+    for (auto &t : m->tiles) maxcells = std::max(maxcells, (int)t.tx * (int)t.ty);
+    for (size_t b = 0; b < m->fabs.size(); ++b) {
+        const FabInfo &f = m->fabs[b];
+        int bx = A, ty = 1;
+        for (auto &t : m->tiles) {
+            if (t.fab != (int)b || t.comp != 0) continue;
+            const int first = (g + t.x0 - R) & ~(A - 1);
+            const int last = g + t.x0 + t.tx - 1 + R;
+            bx = std::max(bx, (last - first + 1 + A - 1) / A * A);
+            ty = std::max(ty, (int)t.ty);
+        }
+        (void)f;
+        tf[b].bx = bx;
+        tf[b].by = ty + 2 * R;
+        tf[b].ngrow = g;
+        if (bx > 256 || tf[b].by > 256) return false;
+        maxplane = std::max(maxplane, bx * tf[b].by * S);
+    }
+    cpt = maxcells <= kTmaThreads ? 1 : maxcells <= 2 * kTmaThreads ? 2 : maxcells <= 4 * kTmaThreads ? 4 : 0;
+    if (cpt == 0) return false;
+    slot_bytes = (maxplane + 127) / 128 * 128;
+    return true;
+}
+
+static int build_tma(mf_t *m, int R) {
+    m->tma_ok = false;
+    m->tma_R = R;
+    if (!m->use_tma) return 0;
+    std::vector<TmaFab> tf;
+    int slot = 0, cpt = 0;
+    if (!tma_geometry(m, R, tf, slot, cpt)) return 0;
+    const int ns = std::min(kMaxStages, R + 7);
+    if ((long long)ns * slot + 128 > 200 * 1024) return 0;
+    auto encode = tensor_map_encoder();
+    if (!encode) return 0;
+    const int nf = (int)m->fabs.size();
+    std::vector<CUtensorMap> maps(2 * (size_t)nf);
+    const CUtensorMapDataType dt = m->dtype == F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                   : m->dtype == F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                     : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const int S = m->esize;
+    for (int which = 0; which < 2; ++which)
+        for (int b = 0; b < nf; ++b) {
+            const FabInfo &f = m->fabs[b];
+            const int g = m->ngrow;
+            cuuint64_t dims[4] = {(cuuint64_t)f.px, (cuuint64_t)(f.n[1] + 2 * g), (cuuint64_t)(f.n[2] + 2 * g),
+                                  (cuuint64_t)m->ncomp};
+            cuuint64_t strides[3] = {(cuuint64_t)f.px * S, (cuuint64_t)f.plane * S, (cuuint64_t)f.cstride * S};
+            cuuint32_t box[4] = {(cuuint32_t)tf[b].bx, (cuuint32_t)tf[b].by, 1, 1};
+            cuuint32_t estr[4] = {1, 1, 1, 1};
+            void *gaddr = (char *)m->level_ptr(which) + (size_t)m->fab_start[b] * S;
+            CUresult r = encode(&maps[(size_t)which * nf + b], dt, 4, gaddr, dims, strides, box, estr,
+                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return fail(MF_ECUDA, "cuTensorMapEncodeTiled failed (%d) for box %d", (int)r, b);
+        }
+    int rc;
+    if ((rc = m->d_maps.upload(maps, m->stream))) return rc;
+    if ((rc = m->d_tfab.upload(tf, m->stream))) return rc;
+    CU(cudaStreamSynchronize(m->stream));
+    m->tma_cpt = cpt;
+    m->tma_slot = slot;
+    m->tma_ns = ns;
+    m->tma_ok = true;
+    return 0;
+}
+
 // ------------------------------------------------------------------ phases
 
 static LevelPtrs level_ptrs(const mf_t *m, int which) {
@@ -757,6 +882,25 @@ static StencilParams stencil_params(const mf_t *m, int from, const double *lam) 
 }
 
 static int enqueue_stencil(mf_t *m, int from, int R, bool fp64diff, const double *lam, cudaStream_t s) {
+    if (m->use_tma && m->tma_R != R) {
+        int rc = build_tma(m, R);
+        if (rc) return rc;
+    }
+    if (m->use_tma && m->tma_ok) {
+        StencilTmaParams p{};
+        p.maps = (const CUtensorMap *)m->d_maps.p + (size_t)from * m->fabs.size();
+        p.tfab = (const TmaFab *)m->d_tfab.p;
+        p.ftab = (const FabInfo *)m->d_fabs.p;
+        p.tiles = (const Tile *)m->d_tiles.p;
+        p.ntiles = (int)m->tiles.size();
+        p.nstages = m->tma_ns;
+        p.slot_bytes = m->tma_slot;
+        p.dst[0] = m->level_ptr(1 - from);
+        p.err = (int *)m->d_err.p;
+        for (int c = 0; c < m->ncomp; ++c) p.lam[0][c] = lam[c];
+        CU(launch_stencil_tma(m->dtype, R, fp64diff, m->tma_cpt, p, 0, s));
+        return 0;
+    }
     StencilParams p = stencil_params(m, from, lam);
     CU(launch_stencil(m->dtype, R, fp64diff, p, m->block[0], m->block[1], 0, s));
     return 0;
@@ -921,6 +1065,7 @@ extern "C" int mf_advance(mf_t *m, const mf_stencil *st, double dt, int nsteps) 
         return advance_plain(m, R, lam, nsteps);
     }
     if (m->tile_auto && (rc = autotune(m, R, fp64diff, lam))) return rc;
+    if (m->use_tma && m->tma_R != R && (rc = build_tma(m, R))) return rc;  // never inside a capture
     const std::string key = graph_key(m->timing ? "advT" : "adv", R, fp64diff, lam, m->ncomp, nsteps, m->cur);
     auto it = m->graphs.find(key);
     if (it == m->graphs.end()) {
@@ -955,6 +1100,7 @@ extern "C" int mf_sum(mf_t *m, int comp, double *out) {
                   (int)m->tiles.size(), comp, (double2 *)m->d_partials.p, grid, (double *)m->d_sumout.p, m->stream));
     CU(cudaMemcpyAsync(m->h_sum, m->d_sumout.p, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
     CU(cudaStreamSynchronize(m->stream));
+    if ((rc = check_device_error(m))) return rc;
     *out = *m->h_sum;
     return 0;
 }
@@ -1159,6 +1305,8 @@ extern "C" int mf_amr_advance(mf_t *crse, mf_t *fine, const mf_stencil *st, doub
     if (!ap) return rc;
     if (crse->tile_auto && (rc = autotune(crse, R, fp64diff, lam_c))) return rc;
     if (fine->tile_auto && (rc = autotune(fine, R, fp64diff, lam_f))) return rc;
+    if (crse->use_tma && crse->tma_R != R && (rc = build_tma(crse, R))) return rc;
+    if (fine->use_tma && fine->tma_R != R && (rc = build_tma(fine, R))) return rc;
     // the coarse stream orders everything; the fine stream waits for nothing else (same
     // stream expected); capture the whole advance into one graph
     char buf[96];

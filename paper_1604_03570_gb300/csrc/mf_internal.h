@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace mfk {
@@ -82,7 +83,33 @@ struct StencilParams {
     double lam[kMaxLev][kMaxComp];
 };
 
-// ---- launchers (mf_kernels.cu); all asynchronous on `s`
+// TMA-staged stencil: per FArrayBox, the shared-memory plane geometry of its tensor map.
+constexpr int kTmaThreads = 256;
+constexpr int kMaxStages = 16;
+
+struct TmaFab {
+    int bx, by;   // box of one plane load: bx elements along x (multiple of 16 bytes), by rows
+    int ngrow;
+    int pad_;
+};
+
+struct StencilTmaParams {
+    const CUtensorMap *maps;   // one per FArrayBox, over the source time level
+    const TmaFab *tfab;
+    const FabInfo *ftab;
+    const Tile *tiles;
+    int ntiles;
+    int nstages;               // shared-memory ring slots
+    int slot_bytes;            // bytes per slot (multiple of 128)
+    int pad_;
+    void *dst[kMaxLev];
+    int *err;                  // set non-zero when a bounded wait expires
+    double lam[kMaxLev][kMaxComp];
+};
+
+// ---- launchers (mf_kernels.cu, stencil_tma.cu); all asynchronous on `s`
+cudaError_t launch_stencil_tma(int dtype, int R, bool fp64diff, int cpt, const StencilTmaParams &p, int grid,
+                               cudaStream_t s);
 cudaError_t launch_fill(int dtype, const LevelPtrs &lv, const FabInfo *ftab, const FbEntry *ent, const FbTask *tasks,
                         int ntasks, int grid, cudaStream_t s);
 cudaError_t launch_stencil(int dtype, int R, bool fp64diff, const StencilParams &p, int bx, int by, int grid,

@@ -1,0 +1,98 @@
+// stencil_common.cuh -- scalar helpers and the per-cell flux-form update shared by the
+// stencil kernels (global-memory and TMA-staged variants), so that every variant evaluates
+// the same expression in the same order.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace mfk {
+
+// ------------------------------------------------------------------ scalar helpers
+
+template <typename A> struct Ar;
+template <> struct Ar<double> {
+    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+};
+template <> struct Ar<float> {
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+};
+
+template <typename S, typename A> __device__ __forceinline__ A ld(const S *p);
+template <> __device__ __forceinline__ double ld<double, double>(const double *p) { return __ldg(p); }
+template <> __device__ __forceinline__ float ld<float, float>(const float *p) { return __ldg(p); }
+template <> __device__ __forceinline__ double ld<float, double>(const float *p) { return (double)__ldg(p); }
+template <> __device__ __forceinline__ float ld<__nv_bfloat16, float>(const __nv_bfloat16 *p) {
+    return __bfloat162float(__ldg(p));
+}
+template <> __device__ __forceinline__ double ld<__nv_bfloat16, double>(const __nv_bfloat16 *p) {
+    return (double)__bfloat162float(__ldg(p));
+}
+
+__device__ __forceinline__ void st(double *p, double v) { *p = v; }
+__device__ __forceinline__ void st(float *p, float v) { *p = v; }
+__device__ __forceinline__ void st(float *p, double v) { *p = __double2float_rn(v); }
+__device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+__device__ __forceinline__ void st(__nv_bfloat16 *p, double v) { *p = __double2bfloat16(v); }
+
+__device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ double to_f64(float v) { return (double)v; }
+__device__ __forceinline__ double to_f64(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+__device__ __forceinline__ void from_f64(double *p, double v) { *p = v; }
+__device__ __forceinline__ void from_f64(float *p, double v) { *p = __double2float_rn(v); }
+__device__ __forceinline__ void from_f64(__nv_bfloat16 *p, double v) { *p = __double2bfloat16(v); }
+
+// Face-flux weights b_m of the centred (2R+1)-point Laplacian of order 2R written as a flux
+// difference, F_{i+1/2} = sum_m b_m (u_{i+m} - u_{i+1-m}), b_m = sum_{j>=m} c_j with the
+// classical centred second-derivative weights c_j (R=1: c=(-2,1); R=2: (-5/2,4/3,-1/12);
+// R=4: (-205/72, 8/5, -1/5, 8/315, -1/560)).
+template <int R> struct FluxW;
+template <> struct FluxW<1> { static __device__ __forceinline__ double b(int) { return 1.0; } };
+template <> struct FluxW<2> {
+    static __device__ __forceinline__ double b(int m) { return m == 1 ? 15.0 / 12.0 : -1.0 / 12.0; }
+};
+template <> struct FluxW<4> {
+    static __device__ __forceinline__ double b(int m) {
+        return m == 1 ? 205.0 / 144.0 : m == 2 ? -127.0 / 720.0 : m == 3 ? 17.0 / 720.0 : -1.0 / 560.0;
+    }
+};
+
+// Flux at the face between q[c] and q[c+1] of a line of values q (index c = centre - 1 for
+// the lower face): F = b_1 (q[c+1] - q[c]) + sum_{m>=2} b_m (q[c+m] - q[c+1-m]).
+template <typename A, int R>
+__device__ __forceinline__ A face_flux(const A *q, int c) {
+    A f = Ar<A>::mul((A)FluxW<R>::b(1), Ar<A>::sub(q[c + 1], q[c]));
+#pragma unroll
+    for (int m = 2; m <= R; ++m) f = Ar<A>::fma((A)FluxW<R>::b(m), Ar<A>::sub(q[c + m], q[c + 1 - m]), f);
+    return f;
+}
+
+template <typename S, typename A> __device__ __forceinline__ A ld_smem(const S *p);
+template <> __device__ __forceinline__ double ld_smem<double, double>(const double *p) { return *p; }
+template <> __device__ __forceinline__ float ld_smem<float, float>(const float *p) { return *p; }
+template <> __device__ __forceinline__ double ld_smem<float, double>(const float *p) { return (double)*p; }
+template <> __device__ __forceinline__ float ld_smem<__nv_bfloat16, float>(const __nv_bfloat16 *p) {
+    return __bfloat162float(*p);
+}
+template <> __device__ __forceinline__ double ld_smem<__nv_bfloat16, double>(const __nv_bfloat16 *p) {
+    return (double)__bfloat162float(*p);
+}
+
+// One cell's update from the lines through it: x line qx, y line qy (2R+1 values each,
+// centre at R) and the z fluxes below/above.  Order: ((Dx + Dy) + Dz), then u + lam*div.
+template <typename A, int R>
+__device__ __forceinline__ A update_cell(const A *qx, const A *qy, A fzm, A fzp, A u, A lam) {
+    A dxv = Ar<A>::sub(face_flux<A, R>(qx, R), face_flux<A, R>(qx, R - 1));
+    A dyv = Ar<A>::sub(face_flux<A, R>(qy, R), face_flux<A, R>(qy, R - 1));
+    A dzv = Ar<A>::sub(fzp, fzm);
+    A div = Ar<A>::add(Ar<A>::add(dxv, dyv), dzv);
+    return Ar<A>::fma(lam, div, u);
+}
+
+}  // namespace mfk

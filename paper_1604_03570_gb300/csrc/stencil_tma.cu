@@ -1,0 +1,256 @@
+// stencil_tma.cu -- the flux-form stencil sweep (Sec. 4.1) over the logical-tile work list
+// (Sec. 3.2), staged through shared memory by the Tensor Memory Accelerator.
+//
+// One persistent CTA takes tiles (box, component, x/y/z extent) from the work list.  For a
+// tile it streams the z-planes of the tile plus R halo planes on each side: plane p is one
+// cp.async.bulk.tensor load of (BX x (ty + 2R)) elements -- the tile's rows with their x/y
+// halo, read from the FArrayBox (ghost cells included) -- into a ring of NS shared-memory
+// slots, completion signalled on one mbarrier per slot.  Thread 0 keeps NS planes in flight;
+// every thread owns up to CPT (x, y) cells of the tile and marches them along z with a
+// register queue of 2R+1 values, so the lower z-face flux is the previous cell's upper one.
+// x and y neighbours come from the centre plane in shared memory.  The per-cell arithmetic
+// (face fluxes, then their divergence, then u + lam * div) is the same expression, in the
+// same order, as the untiled kernel, so every tile shape gives identical bits.
+//
+// Every mbarrier wait is bounded (about one second of clock64 cycles); on expiry the CTA
+// sets the error word, drains its own copies (again bounded) and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "mf_internal.h"
+#include "stencil_common.cuh"
+
+namespace mfk {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false after ~kWaitCycles without completion.
+constexpr long long kWaitCycles = 2000000000LL;
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kWaitCycles) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z,
+                                            int c) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(c), "r"(smem_u32(bar))
+        : "memory");
+}
+
+template <typename S, typename A, int R, int CPT>
+__global__ void __launch_bounds__(kTmaThreads) k_stencil_tma(const __grid_constant__ StencilTmaParams p) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bars[kMaxStages];
+    __shared__ int abort_flag;
+    unsigned char *slots = (unsigned char *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    const int NS = p.nstages;
+    const int tid = threadIdx.x;
+    constexpr int AL = 16 / (int)sizeof(S);  // elements per 16 bytes
+
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+
+    uint32_t seq = 0;  // planes issued by this CTA so far; plane seq+i lives in slot (seq+i) % NS
+    for (int w = blockIdx.x; w < p.ntiles; w += gridDim.x) {
+        const Tile t = p.tiles[w];
+        const TmaFab tf = p.tfab[t.fab];
+        const FabInfo f = p.ftab[t.fab];
+        const CUtensorMap *map = p.maps + t.fab;
+        const int g = tf.ngrow;
+        const int first_col = (g + t.x0 - R) & ~(AL - 1);
+        const int xoff = g + t.x0 - first_col;  // smem column of the tile's first valid cell
+        const int bx = tf.bx;                  // smem row length (elements)
+        const int ntot = t.tz + 2 * R;         // planes of this tile, halo included
+        const uint32_t plane_bytes = (uint32_t)(tf.bx * tf.by * (int)sizeof(S));
+        const int ycoord = g + t.y0 - R, zcoord = g + t.z0 - R;
+
+        auto issue = [&](int pl) {
+            const uint32_t sq = seq + (uint32_t)pl;
+            uint64_t *bar = &bars[sq % NS];
+            mbar_expect_tx(bar, plane_bytes);
+            tma_load_4d(slots + (size_t)(sq % NS) * p.slot_bytes, map, bar, first_col, ycoord, zcoord + pl, t.comp);
+        };
+        auto wait_plane = [&](int pl) -> bool {
+            const uint32_t sq = seq + (uint32_t)pl;
+            return mbar_wait(&bars[sq % NS], (sq / NS) & 1u);
+        };
+        auto plane_ptr = [&](int pl) -> const S * {
+            return (const S *)(slots + (size_t)((seq + (uint32_t)pl) % NS) * p.slot_bytes);
+        };
+
+        const int issued0 = ntot < NS ? ntot : NS;
+        if (tid == 0)
+            for (int pl = 0; pl < issued0; ++pl) issue(pl);
+        int issued = issued0;
+
+        // cells owned by this thread
+        const int ncell = t.tx * t.ty;
+        int cx[CPT], cy[CPT];
+        bool act[CPT];
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+            const int idx = tid + c * kTmaThreads;
+            act[c] = idx < ncell;
+            cx[c] = act[c] ? idx % t.tx : 0;
+            cy[c] = act[c] ? idx / t.tx : 0;
+        }
+        A q[CPT][2 * R + 1];
+        A fzm[CPT];
+        bool ok = true;
+        // queue start: planes 0 .. 2R-1 are u(z0 - R) .. u(z0 + R - 1)
+#pragma unroll
+        for (int pl = 0; pl < 2 * R; ++pl) {
+            ok = ok && wait_plane(pl);
+            const S *sp = plane_ptr(pl);
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) q[c][pl] = ld_smem<S, A>(sp + (cy[c] + R) * bx + cx[c] + xoff);
+        }
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) fzm[c] = face_flux<A, R>(q[c], R - 1);
+        if (!ok) { abort_flag = 1; atomicOr(p.err, 1); }
+        __syncthreads();
+        int waited = 2 * R;  // planes [0, waited) have completed
+        if (abort_flag) {
+            if (tid == 0)
+                for (int pl = waited; pl < issued; ++pl) wait_plane(pl);
+            break;
+        }
+        // planes 0 .. R-1 are no longer needed: refill their slots
+        if (tid == 0)
+            for (int pl = 0; pl < R && issued < ntot; ++pl) issue(issued++);
+
+        S *dst = (S *)p.dst[f.level] + f.org + t.comp * f.cstride;
+        const A lam = (A)p.lam[f.level][t.comp];
+        for (int k = 0; k < t.tz; ++k) {
+            ok = wait_plane(k + 2 * R);
+            const S *newp = plane_ptr(k + 2 * R);
+            const S *cp = plane_ptr(k + R);
+            const int z = t.z0 + k;
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                if (!act[c]) continue;
+                const S *cc = cp + (cy[c] + R) * bx + cx[c] + xoff;
+                q[c][2 * R] = ld_smem<S, A>(newp + (cy[c] + R) * bx + cx[c] + xoff);
+                A qx[2 * R + 1], qy[2 * R + 1];
+#pragma unroll
+                for (int j = 0; j < 2 * R + 1; ++j) {
+                    qx[j] = (j == R) ? q[c][R] : ld_smem<S, A>(cc + (j - R));
+                    qy[j] = (j == R) ? q[c][R] : ld_smem<S, A>(cc + (j - R) * bx);
+                }
+                const A fzp = face_flux<A, R>(q[c], R);
+                st(dst + (long long)z * f.plane + (long long)(t.y0 + cy[c]) * f.px + (t.x0 + cx[c]),
+                   update_cell<A, R>(qx, qy, fzm[c], fzp, q[c][R], lam));
+                fzm[c] = fzp;
+#pragma unroll
+                for (int j = 0; j < 2 * R; ++j) q[c][j] = q[c][j + 1];
+            }
+            if (!ok) { abort_flag = 1; atomicOr(p.err, 1); }
+            __syncthreads();  // every thread is done with the centre plane k + R
+            waited = k + 2 * R + 1;
+            if (abort_flag) break;
+            if (tid == 0 && issued < ntot) issue(issued++);
+        }
+        if (abort_flag) {
+            // drain the copies this CTA issued for the tile (bounded waits), then stop
+            if (tid == 0)
+                for (int pl = waited; pl < issued; ++pl) wait_plane(pl);
+            break;
+        }
+        seq += (uint32_t)ntot;
+    }
+}
+
+template <typename S, typename A, int R, int CPT>
+static cudaError_t tma_t(const StencilTmaParams &p, int grid, cudaStream_t s) {
+    const int smem = p.nstages * p.slot_bytes + 128;
+    auto kern = k_stencil_tma<S, A, R, CPT>;
+    static int configured = 0;
+    if (smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    int g = grid;
+    if (g <= 0) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTmaThreads, smem) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        long long gg = (long long)per_sm * sm_count();
+        g = (int)(gg < p.ntiles ? gg : p.ntiles);
+        if (g < 1) g = 1;
+    }
+    kern<<<g, kTmaThreads, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename S, typename A, int R>
+static cudaError_t tma_c(int cpt, const StencilTmaParams &p, int grid, cudaStream_t s) {
+    switch (cpt) {
+        case 1: return tma_t<S, A, R, 1>(p, grid, s);
+        case 2: return tma_t<S, A, R, 2>(p, grid, s);
+        case 4: return tma_t<S, A, R, 4>(p, grid, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename S, typename A>
+static cudaError_t tma_r(int R, int cpt, const StencilTmaParams &p, int grid, cudaStream_t s) {
+    switch (R) {
+        case 1: return tma_c<S, A, 1>(cpt, p, grid, s);
+        case 2: return tma_c<S, A, 2>(cpt, p, grid, s);
+        case 4: return tma_c<S, A, 4>(cpt, p, grid, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_stencil_tma(int dtype, int R, bool fp64diff, int cpt, const StencilTmaParams &p, int grid,
+                               cudaStream_t s) {
+    if (p.ntiles == 0) return cudaSuccess;
+    if (p.nstages > kMaxStages || p.nstages < R + 2) return cudaErrorInvalidValue;
+    switch (dtype) {
+        case F64: return tma_r<double, double>(R, cpt, p, grid, s);
+        case F32: return fp64diff ? tma_r<float, double>(R, cpt, p, grid, s) : tma_r<float, float>(R, cpt, p, grid, s);
+        case BF16:
+            return fp64diff ? tma_r<__nv_bfloat16, double>(R, cpt, p, grid, s)
+                            : tma_r<__nv_bfloat16, float>(R, cpt, p, grid, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace mfk

@@ -208,11 +208,17 @@ def test_layout_and_tile_invariance_bitwise(dtype, R):
     dense = rand_field((1, 32, 32, 32), 9, dtype)
     dt = 0.05 / 1024
     outs = []
-    for boxes, tile, flags in [(oracle.chop(lo, hi, 32), (0, 0, 0), 0), (oracle.chop(lo, hi, 16), (16, 4, 4), 0),
-                               (CUBE_UNEVEN, (7, 3, 5), 0), (oracle.chop(lo, hi, 8), (8, 8, 8), 0),
-                               (oracle.chop(lo, hi, 16), (0, 0, 0), mf.MF_PLAIN_PER_BOX)]:
+    for boxes, tile, flags, kern in [
+            (oracle.chop(lo, hi, 32), (0, 0, 0), 0, mf.MF_KERNEL_GLOBAL),
+            (oracle.chop(lo, hi, 32), (32, 8, 16), 0, mf.MF_KERNEL_TMA),
+            (oracle.chop(lo, hi, 16), (16, 4, 4), 0, mf.MF_KERNEL_TMA),
+            (CUBE_UNEVEN, (7, 3, 5), 0, mf.MF_KERNEL_TMA),
+            (CUBE_UNEVEN, (8, 5, 32), 0, mf.MF_KERNEL_GLOBAL),
+            (oracle.chop(lo, hi, 8), (8, 8, 8), 0, mf.MF_KERNEL_TMA),
+            (oracle.chop(lo, hi, 16), (0, 0, 0), mf.MF_PLAIN_PER_BOX, mf.MF_KERNEL_TMA)]:
         g = gpu_level(lo, hi, boxes=boxes, ngrow=R, dtype=dtype)
         g.set_tile(tile)
+        mf.mf_set_kernel(g.h, kern)
         g.from_host(dense)
         g.advance(R, [1.0], dt, 5, flags)
         outs.append(g.to_host())
