@@ -46,6 +46,7 @@ def parse():
     p.add_argument("--dtype", default="f32", choices=["f32", "f64", "bf16"])
     p.add_argument("--no-extras", action="store_true", help="headline only (no FP64, e2e, CPU baseline)")
     p.add_argument("--tile", default=None, help="fixed tile 'x,y,z' instead of the autotuner (0 = whole box)")
+    p.add_argument("--kernel", default="tma", choices=["tma", "global"], help="stencil kernel variant")
     return p.parse_args()
 
 
@@ -256,6 +257,7 @@ def run_ours(args, cfg, ws, rank, local):
     head = level(args.dtype)
     if args.tile:
         head.set_tile(tuple(int(v) for v in args.tile.split(",")))
+    mf.mf_set_kernel(head.h, mf.MF_KERNEL_TMA if args.kernel == "tma" else mf.MF_KERNEL_GLOBAL)
     for _ in range(args.warmup):
         mf.mf_advance(head.h, R, D, dt, nsteps)
     torch.cuda.synchronize()

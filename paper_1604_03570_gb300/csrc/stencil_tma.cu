@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(kTmaThreads) k_stencil_tma(const __grid_consta
     const int NS = p.nstages;
     const int tid = threadIdx.x;
     constexpr int AL = 16 / (int)sizeof(S);  // elements per 16 bytes
+    if (*(volatile int *)p.err) return;       // an earlier launch already failed: do nothing
 
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
