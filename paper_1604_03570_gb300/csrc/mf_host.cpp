@@ -248,10 +248,11 @@ static void build_layout(mf_t *m) {
     for (auto &b : m->boxes) {
         FabInfo f{};
         for (int d = 0; d < 3; ++d) { f.n[d] = b.len(d); f.lo[d] = b.lo[d]; }
-        // every row starts 16-byte aligned at its first ghost cell (x = -g), so a TMA plane load
-        // of a tile with its x halo starts on a 16-byte boundary when the halo equals ngrow
-        const int fpad = 0;
-        f.px = (int)(((long long)f.n[0] + 2 * g + A - 1) / A * A);
+        // valid x = 0 of every row sits on a 16-byte boundary: vector loads and stores of the
+        // valid cells are aligned, and a TMA plane load that starts a whole 16-byte chunk
+        // left of a tile is aligned too
+        const int fpad = (A - g % A) % A;
+        f.px = (int)(((long long)fpad + f.n[0] + 2 * g + A - 1) / A * A);
         const long long py = f.n[1] + 2 * g, nzg = f.n[2] + 2 * g;
         f.plane = (long long)f.px * py;
         f.cstride = f.plane * nzg;
@@ -321,12 +322,30 @@ static int build_fb(mf_t *m) {
                 }
     }
     m->fb_group[nb] = (int)m->fb.size();
-    // split entries into CTA-sized tasks
-    const int kTask = 2048;
+    // split entries into CTA-sized tasks (256 threads x 4 cells)
+    const int kTask = 1024;
     for (int e = 0; e < (int)m->fb.size(); ++e) {
-        const long long cells = (long long)m->fb[e].n[0] * m->fb[e].n[1] * m->fb[e].n[2] * m->ncomp;
-        for (long long f = 0; f < cells; f += kTask)
-            m->fbtasks.push_back(FbTask{e, (int)f, (int)std::min<long long>(kTask, cells - f), 0});
+        const FbEntry &en = m->fb[e];
+        const FabInfo &sf = m->fabs[en.sfab], &df = m->fabs[en.dfab];
+        const long long cells = (long long)en.n[0] * en.n[1] * en.n[2] * m->ncomp;
+        for (long long f = 0; f < cells; f += kTask) {
+            FbTask t{};
+            t.src = en.src;
+            t.dst = en.dst;
+            t.s_pl = sf.plane;
+            t.d_pl = df.plane;
+            t.s_cs = sf.cstride;
+            t.d_cs = df.cstride;
+            t.s_px = sf.px;
+            t.d_px = df.px;
+            t.n0 = en.n[0];
+            t.n1 = en.n[1];
+            t.n2 = en.n[2];
+            t.first = (int)f;
+            t.count = (int)std::min<long long>(kTask, cells - f);
+            t.level = en.level;
+            m->fbtasks.push_back(t);
+        }
     }
     return 0;
 }
@@ -785,30 +804,31 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // Plane geometry of every FArrayBox for the current tile shape and radius R; false when a
 // box needs a plane wider than the TMA box limit (256 per dimension) or more cells per
 // thread than the kernel keeps in registers.
-static bool tma_geometry(mf_t *m, int R, std::vector<TmaFab> &tf, int &slot_bytes, int &cpt) {
+static bool tma_geometry(mf_t *m, int R, std::vector<TmaFab> &tf, int &slot_bytes, int &gpt) {
     const int S = m->esize, A = 16 / S, g = m->ngrow;
+    const int XH = (R + A - 1) / A * A;  // x halo columns loaded on each side
     tf.assign(m->fabs.size(), TmaFab{});
-    int maxplane = 0, maxcells = 0;
-    for (auto &t : m->tiles) maxcells = std::max(maxcells, (int)t.tx * (int)t.ty);
+    int maxplane = 0, maxgroups = 0;
+    for (auto &t : m->tiles) {
+        if (t.x0 % A) return false;  // a plane load must start on a 16-byte boundary
+        maxgroups = std::max(maxgroups, ((int)t.tx + A - 1) / A * (int)t.ty);
+    }
     for (size_t b = 0; b < m->fabs.size(); ++b) {
-        const FabInfo &f = m->fabs[b];
-        int bx = A, ty = 1;
+        int tx = 1, ty = 1;
         for (auto &t : m->tiles) {
             if (t.fab != (int)b || t.comp != 0) continue;
-            const int first = (g + t.x0 - R) & ~(A - 1);
-            const int last = g + t.x0 + t.tx - 1 + R;
-            bx = std::max(bx, (last - first + 1 + A - 1) / A * A);
+            tx = std::max(tx, (int)t.tx);
             ty = std::max(ty, (int)t.ty);
         }
-        (void)f;
-        tf[b].bx = bx;
+        tf[b].bx = XH + (tx + A - 1) / A * A + XH;
         tf[b].by = ty + 2 * R;
         tf[b].ngrow = g;
-        if (bx > 256 || tf[b].by > 256) return false;
-        maxplane = std::max(maxplane, bx * tf[b].by * S);
+        tf[b].xv = (g + A - 1) / A * A;  // fpad + g
+        if (tf[b].bx > 256 || tf[b].by > 256) return false;
+        maxplane = std::max(maxplane, tf[b].bx * tf[b].by * S);
     }
-    cpt = maxcells <= kTmaThreads ? 1 : maxcells <= 2 * kTmaThreads ? 2 : maxcells <= 4 * kTmaThreads ? 4 : 0;
-    if (cpt == 0) return false;
+    gpt = maxgroups <= kTmaThreads ? 1 : maxgroups <= 2 * kTmaThreads ? 2 : maxgroups <= 4 * kTmaThreads ? 4 : 0;
+    if (gpt == 0 || (R == 4 && gpt > 2)) return false;
     slot_bytes = (maxplane + 127) / 128 * 128;
     return true;
 }
@@ -820,8 +840,9 @@ static int build_tma(mf_t *m, int R) {
     std::vector<TmaFab> tf;
     int slot = 0, cpt = 0;
     if (!tma_geometry(m, R, tf, slot, cpt)) return 0;
-    const int ns = std::min(kMaxStages, R + 7);
-    if ((long long)ns * slot + 128 > 200 * 1024) return 0;
+    int ns = R == 4 ? 16 : 8;  // ring slots (power of two)
+    while (ns > 8 && (long long)ns * slot + 128 > 160 * 1024) ns /= 2;
+    if (ns < 2 * R || (long long)ns * slot + 128 > 200 * 1024) return 0;
     auto encode = tensor_map_encoder();
     if (!encode) return 0;
     const int nf = (int)m->fabs.size();
@@ -865,8 +886,7 @@ static LevelPtrs level_ptrs(const mf_t *m, int which) {
 }
 
 static int enqueue_fill(mf_t *m, int which, cudaStream_t s) {
-    CU(launch_fill(m->dtype, level_ptrs(m, which), (const FabInfo *)m->d_fabs.p, (const FbEntry *)m->d_fb.p,
-                   (const FbTask *)m->d_fbtasks.p, (int)m->fbtasks.size(), 0, s));
+    CU(launch_fill(m->dtype, level_ptrs(m, which), (const FbTask *)m->d_fbtasks.p, (int)m->fbtasks.size(), 0, s));
     return 0;
 }
 

@@ -36,13 +36,16 @@ struct FbEntry {
     int level;
 };
 
-// Work unit of the fill kernel: cells [first, first + count) of entry `entry` in the
-// linear order (comp, z, y, x).
+// Work unit of the fill kernel, self-contained so that a CTA needs one load to start:
+// cells [first, first + count) of one copy region in the linear order (comp, z, y, x).
 struct FbTask {
-    int entry;
-    int first;
-    int count;
-    int pad_;
+    long long src, dst;    // element offsets of the region's first cell, comp 0
+    long long s_pl, d_pl;  // plane strides
+    long long s_cs, d_cs;  // component strides
+    int s_px, d_px;        // row pitches
+    int n0, n1, n2;        // region extents
+    int first, count;
+    int level;
 };
 
 // Stencil work list entry: a logical tile of one box and one component (Sec. 3.2 tilebox()).
@@ -90,7 +93,7 @@ constexpr int kMaxStages = 16;
 struct TmaFab {
     int bx, by;   // box of one plane load: bx elements along x (multiple of 16 bytes), by rows
     int ngrow;
-    int pad_;
+    int xv;       // row element of valid x = 0 (16-byte aligned)
 };
 
 struct StencilTmaParams {
@@ -110,8 +113,7 @@ struct StencilTmaParams {
 // ---- launchers (mf_kernels.cu, stencil_tma.cu); all asynchronous on `s`
 cudaError_t launch_stencil_tma(int dtype, int R, bool fp64diff, int cpt, const StencilTmaParams &p, int grid,
                                cudaStream_t s);
-cudaError_t launch_fill(int dtype, const LevelPtrs &lv, const FabInfo *ftab, const FbEntry *ent, const FbTask *tasks,
-                        int ntasks, int grid, cudaStream_t s);
+cudaError_t launch_fill(int dtype, const LevelPtrs &lv, const FbTask *tasks, int ntasks, int grid, cudaStream_t s);
 cudaError_t launch_stencil(int dtype, int R, bool fp64diff, const StencilParams &p, int bx, int by, int grid,
                            cudaStream_t s);
 // untiled per-box baseline (one box per launch)

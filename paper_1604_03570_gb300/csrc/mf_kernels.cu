@@ -30,42 +30,30 @@ namespace mfk {
 // ------------------------------------------------------------------ FillBoundary
 
 template <typename E>
-__global__ void __launch_bounds__(256) k_fill(LevelPtrs lv, const FabInfo *__restrict__ ftab,
-                                              const FbEntry *__restrict__ ent, const FbTask *__restrict__ tasks,
-                                              int ntasks) {
-    constexpr int U = 4;  // cells per thread per round: all loads issued before the stores
+__global__ void __launch_bounds__(256) k_fill(LevelPtrs lv, const FbTask *__restrict__ tasks, int ntasks) {
+    constexpr int U = 4;  // cells per thread per task: all loads issued before the stores
     for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
         const FbTask tk = tasks[t];
-        const FbEntry e = ent[tk.entry];
-        const FabInfo &sf = ftab[e.sfab];
-        const FabInfo &df = ftab[e.dfab];
-        const long long s_pl = sf.plane, s_cs = sf.cstride, d_pl = df.plane, d_cs = df.cstride;
-        const int s_px = sf.px, d_px = df.px;
-        E *base = (E *)lv.base[e.level];
-        const unsigned n0 = e.n[0], n1 = e.n[1], n2 = e.n[2];
-        for (int i0 = threadIdx.x; i0 < tk.count; i0 += blockDim.x * U) {
-            E v[U];
-            long long dof[U];
+        E *base = (E *)lv.base[tk.level];
+        const unsigned n0 = tk.n0, n1 = tk.n1, n2 = tk.n2;
+        E v[U];
+        long long dof[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int i = i0 + u * (int)blockDim.x;
-                dof[u] = -1;
-                if (i < tk.count) {
-                    unsigned l = (unsigned)(tk.first + i);
-                    const unsigned x = l % n0;
-                    l /= n0;
-                    const unsigned y = l % n1;
-                    l /= n1;
-                    const unsigned z = l % n2;
-                    const unsigned c = l / n2;
-                    v[u] = __ldg(base + e.src + c * s_cs + z * s_pl + (long long)y * s_px + x);
-                    dof[u] = e.dst + c * d_cs + z * d_pl + (long long)y * d_px + x;
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (dof[u] >= 0) base[dof[u]] = v[u];
+        for (int u = 0; u < U; ++u) {
+            const int i = threadIdx.x + u * (int)blockDim.x;
+            unsigned l = (unsigned)(tk.first + i);
+            const unsigned x = l % n0;
+            l /= n0;
+            const unsigned y = l % n1;
+            l /= n1;
+            const unsigned z = l % n2;
+            const unsigned c = l / n2;
+            dof[u] = tk.dst + c * tk.d_cs + z * tk.d_pl + (long long)y * tk.d_px + x;
+            if (i < tk.count) v[u] = __ldg(base + tk.src + c * tk.s_cs + z * tk.s_pl + (long long)y * tk.s_px + x);
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (threadIdx.x + u * (int)blockDim.x < tk.count) base[dof[u]] = v[u];
     }
 }
 
@@ -369,23 +357,22 @@ static int persistent_grid(K kernel, int block, int work) {
     return g < 1 ? 1 : (int)g;
 }
 
-cudaError_t launch_fill(int dtype, const LevelPtrs &lv, const FabInfo *ftab, const FbEntry *ent, const FbTask *tasks,
-                        int ntasks, int grid, cudaStream_t s) {
+cudaError_t launch_fill(int dtype, const LevelPtrs &lv, const FbTask *tasks, int ntasks, int grid, cudaStream_t s) {
     if (ntasks == 0) return cudaSuccess;
     switch (dtype_size(dtype)) {
         case 8: {
             int g = grid > 0 ? grid : persistent_grid(k_fill<unsigned long long>, 256, ntasks);
-            k_fill<unsigned long long><<<g, 256, 0, s>>>(lv, ftab, ent, tasks, ntasks);
+            k_fill<unsigned long long><<<g, 256, 0, s>>>(lv, tasks, ntasks);
             break;
         }
         case 4: {
             int g = grid > 0 ? grid : persistent_grid(k_fill<unsigned int>, 256, ntasks);
-            k_fill<unsigned int><<<g, 256, 0, s>>>(lv, ftab, ent, tasks, ntasks);
+            k_fill<unsigned int><<<g, 256, 0, s>>>(lv, tasks, ntasks);
             break;
         }
         default: {
             int g = grid > 0 ? grid : persistent_grid(k_fill<unsigned short>, 256, ntasks);
-            k_fill<unsigned short><<<g, 256, 0, s>>>(lv, ftab, ent, tasks, ntasks);
+            k_fill<unsigned short><<<g, 256, 0, s>>>(lv, tasks, ntasks);
         }
     }
     return cudaGetLastError();

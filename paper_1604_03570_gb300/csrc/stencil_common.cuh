@@ -95,4 +95,15 @@ __device__ __forceinline__ A update_cell(const A *qx, const A *qy, A fzm, A fzp,
     return Ar<A>::fma(lam, div, u);
 }
 
+// The same update with the two x-face fluxes given (computed once per face and shared by
+// the two cells beside it: the identical expression on identical operands).
+template <typename A, int R>
+__device__ __forceinline__ A update_cell_fx(A fxp, A fxm, const A *qy, A fzm, A fzp, A u, A lam) {
+    A dxv = Ar<A>::sub(fxp, fxm);
+    A dyv = Ar<A>::sub(face_flux<A, R>(qy, R), face_flux<A, R>(qy, R - 1));
+    A dzv = Ar<A>::sub(fzp, fzm);
+    A div = Ar<A>::add(Ar<A>::add(dxv, dyv), dzv);
+    return Ar<A>::fma(lam, div, u);
+}
+
 }  // namespace mfk

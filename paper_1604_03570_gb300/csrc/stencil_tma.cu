@@ -67,16 +67,60 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
-template <typename S, typename A, int R, int CPT>
+// 16-byte vectors of the storage type: VX elements, converted to the arithmetic type.
+template <typename S> struct V16;
+template <> struct V16<double> {
+    static constexpr int n = 2;
+    template <typename A> static __device__ __forceinline__ void ld(const double *p, A *o) {
+        const double2 v = *(const double2 *)p;
+        o[0] = (A)v.x; o[1] = (A)v.y;
+    }
+    static __device__ __forceinline__ void st(double *p, const double *v) { *(double2 *)p = make_double2(v[0], v[1]); }
+};
+template <> struct V16<float> {
+    static constexpr int n = 4;
+    template <typename A> static __device__ __forceinline__ void ld(const float *p, A *o) {
+        const float4 v = *(const float4 *)p;
+        o[0] = (A)v.x; o[1] = (A)v.y; o[2] = (A)v.z; o[3] = (A)v.w;
+    }
+    static __device__ __forceinline__ void st(float *p, const float *v) {
+        *(float4 *)p = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    static __device__ __forceinline__ void st(float *p, const double *v) {
+        *(float4 *)p = make_float4(__double2float_rn(v[0]), __double2float_rn(v[1]), __double2float_rn(v[2]),
+                                   __double2float_rn(v[3]));
+    }
+};
+template <> struct V16<__nv_bfloat16> {
+    static constexpr int n = 8;
+    template <typename A> static __device__ __forceinline__ void ld(const __nv_bfloat16 *p, A *o) {
+        const uint4 v = *(const uint4 *)p;
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            o[2 * i] = (A)__uint_as_float(w[i] << 16);
+            o[2 * i + 1] = (A)__uint_as_float(w[i] & 0xffff0000u);
+        }
+    }
+    template <typename A> static __device__ __forceinline__ void st(__nv_bfloat16 *p, const A *v) {
+        __nv_bfloat16 b[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) mfk::st(&b[i], v[i]);
+        *(uint4 *)p = *(const uint4 *)b;
+    }
+};
+
+template <typename S, typename A, int R, int GPT>
 __global__ void __launch_bounds__(kTmaThreads) k_stencil_tma(const __grid_constant__ StencilTmaParams p) {
+    constexpr int VX = V16<S>::n;                   // cells per group: one 16-byte vector
+    constexpr int XH = ((R + VX - 1) / VX) * VX;    // x halo loaded on each side (16-byte multiple)
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bars[kMaxStages];
     __shared__ int abort_flag;
     unsigned char *slots = (unsigned char *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
-    const int NS = p.nstages;
+    const int NS = p.nstages;                       // power of two
     const int tid = threadIdx.x;
-    constexpr int AL = 16 / (int)sizeof(S);  // elements per 16 bytes
-    if (*(volatile int *)p.err) return;       // an earlier launch already failed: do nothing
+    if (*(volatile int *)p.err) return;             // an earlier launch already failed: do nothing
 
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
@@ -92,57 +136,61 @@ __global__ void __launch_bounds__(kTmaThreads) k_stencil_tma(const __grid_consta
         const TmaFab tf = p.tfab[t.fab];
         const FabInfo f = p.ftab[t.fab];
         const CUtensorMap *map = p.maps + t.fab;
-        const int g = tf.ngrow;
-        const int first_col = (g + t.x0 - R) & ~(AL - 1);
-        const int xoff = g + t.x0 - first_col;  // smem column of the tile's first valid cell
-        const int bx = tf.bx;                  // smem row length (elements)
-        const int ntot = t.tz + 2 * R;         // planes of this tile, halo included
+        const int bx = tf.bx;                       // smem row length (elements)
+        const int ntot = t.tz + 2 * R;              // planes of this tile, halo included
         const uint32_t plane_bytes = (uint32_t)(tf.bx * tf.by * (int)sizeof(S));
-        const int ycoord = g + t.y0 - R, zcoord = g + t.z0 - R;
+        const int xcoord = tf.xv + t.x0 - XH;       // 16-byte aligned row element of the first loaded column
+        const int ycoord = tf.ngrow + t.y0 - R, zcoord = tf.ngrow + t.z0 - R;
 
+        auto slot_of = [&](int pl) -> uint32_t { return (seq + (uint32_t)pl) & (uint32_t)(NS - 1); };
         auto issue = [&](int pl) {
-            const uint32_t sq = seq + (uint32_t)pl;
-            uint64_t *bar = &bars[sq % NS];
-            mbar_expect_tx(bar, plane_bytes);
-            tma_load_4d(slots + (size_t)(sq % NS) * p.slot_bytes, map, bar, first_col, ycoord, zcoord + pl, t.comp);
+            const uint32_t sl = slot_of(pl);
+            mbar_expect_tx(&bars[sl], plane_bytes);
+            tma_load_4d(slots + (size_t)sl * p.slot_bytes, map, &bars[sl], xcoord, ycoord, zcoord + pl, t.comp);
         };
         auto wait_plane = [&](int pl) -> bool {
             const uint32_t sq = seq + (uint32_t)pl;
-            return mbar_wait(&bars[sq % NS], (sq / NS) & 1u);
+            return mbar_wait(&bars[sq & (uint32_t)(NS - 1)], (sq / (uint32_t)NS) & 1u);
         };
-        auto plane_ptr = [&](int pl) -> const S * {
-            return (const S *)(slots + (size_t)((seq + (uint32_t)pl) % NS) * p.slot_bytes);
-        };
+        auto plane_ptr = [&](int pl) -> const S * { return (const S *)(slots + (size_t)slot_of(pl) * p.slot_bytes); };
 
         const int issued0 = ntot < NS ? ntot : NS;
         if (tid == 0)
             for (int pl = 0; pl < issued0; ++pl) issue(pl);
         int issued = issued0;
 
-        // cells owned by this thread
-        const int ncell = t.tx * t.ty;
-        int cx[CPT], cy[CPT];
-        bool act[CPT];
+        // groups of VX consecutive x cells owned by this thread
+        const int ngx = (t.tx + VX - 1) / VX;
+        const int ngroups = ngx * t.ty;
+        int soff[GPT], gx0[GPT], gy[GPT];
+        bool act[GPT];
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) {
-            const int idx = tid + c * kTmaThreads;
-            act[c] = idx < ncell;
-            cx[c] = act[c] ? idx % t.tx : 0;
-            cy[c] = act[c] ? idx / t.tx : 0;
+        for (int j = 0; j < GPT; ++j) {
+            const int gi = tid + j * kTmaThreads;
+            act[j] = gi < ngroups;
+            gx0[j] = act[j] ? (gi % ngx) * VX : 0;
+            gy[j] = act[j] ? gi / ngx : 0;
+            soff[j] = (gy[j] + R) * bx + XH + gx0[j];  // smem offset of the group's first cell
         }
-        A q[CPT][2 * R + 1];
-        A fzm[CPT];
+        A q[GPT][VX][2 * R + 1];  // z queue per cell: q[..][..][i] = u(z - R + i)
+        A fzm[GPT][VX];
         bool ok = true;
-        // queue start: planes 0 .. 2R-1 are u(z0 - R) .. u(z0 + R - 1)
 #pragma unroll
         for (int pl = 0; pl < 2 * R; ++pl) {
             ok = ok && wait_plane(pl);
             const S *sp = plane_ptr(pl);
 #pragma unroll
-            for (int c = 0; c < CPT; ++c) q[c][pl] = ld_smem<S, A>(sp + (cy[c] + R) * bx + cx[c] + xoff);
+            for (int j = 0; j < GPT; ++j) {
+                A v[VX];
+                V16<S>::ld(sp + soff[j], v);
+#pragma unroll
+                for (int c = 0; c < VX; ++c) q[j][c][pl] = v[c];
+            }
         }
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) fzm[c] = face_flux<A, R>(q[c], R - 1);
+        for (int j = 0; j < GPT; ++j)
+#pragma unroll
+            for (int c = 0; c < VX; ++c) fzm[j][c] = face_flux<A, R>(q[j][c], R - 1);
         if (!ok) { abort_flag = 1; atomicOr(p.err, 1); }
         __syncthreads();
         int waited = 2 * R;  // planes [0, waited) have completed
@@ -157,28 +205,61 @@ __global__ void __launch_bounds__(kTmaThreads) k_stencil_tma(const __grid_consta
 
         S *dst = (S *)p.dst[f.level] + f.org + t.comp * f.cstride;
         const A lam = (A)p.lam[f.level][t.comp];
+        const bool vec_store = (t.x0 % VX) == 0;
         for (int k = 0; k < t.tz; ++k) {
             ok = wait_plane(k + 2 * R);
             const S *newp = plane_ptr(k + 2 * R);
             const S *cp = plane_ptr(k + R);
-            const int z = t.z0 + k;
+            const long long zoff = (long long)(t.z0 + k) * f.plane;
 #pragma unroll
-            for (int c = 0; c < CPT; ++c) {
-                if (!act[c]) continue;
-                const S *cc = cp + (cy[c] + R) * bx + cx[c] + xoff;
-                q[c][2 * R] = ld_smem<S, A>(newp + (cy[c] + R) * bx + cx[c] + xoff);
-                A qx[2 * R + 1], qy[2 * R + 1];
+            for (int j = 0; j < GPT; ++j) {
+                if (!act[j]) continue;
+                {
+                    A v[VX];
+                    V16<S>::ld(newp + soff[j], v);
 #pragma unroll
-                for (int j = 0; j < 2 * R + 1; ++j) {
-                    qx[j] = (j == R) ? q[c][R] : ld_smem<S, A>(cc + (j - R));
-                    qy[j] = (j == R) ? q[c][R] : ld_smem<S, A>(cc + (j - R) * bx);
+                    for (int c = 0; c < VX; ++c) q[j][c][2 * R] = v[c];
                 }
-                const A fzp = face_flux<A, R>(q[c], R);
-                st(dst + (long long)z * f.plane + (long long)(t.y0 + cy[c]) * f.px + (t.x0 + cx[c]),
-                   update_cell<A, R>(qx, qy, fzm[c], fzp, q[c][R], lam));
-                fzm[c] = fzp;
+                // x window: w[i] = u(x0 - R + i), i = 0 .. VX + 2R - 1
+                A wx[VX + 2 * R];
+                const S *cc = cp + soff[j];
 #pragma unroll
-                for (int j = 0; j < 2 * R; ++j) q[c][j] = q[c][j + 1];
+                for (int i = 0; i < R; ++i) {
+                    wx[i] = ld_smem<S, A>(cc - R + i);
+                    wx[R + VX + i] = ld_smem<S, A>(cc + VX + i);
+                }
+#pragma unroll
+                for (int c = 0; c < VX; ++c) wx[R + c] = q[j][c][R];
+                // y rows: ry[m][c] = u(x + c, y - R + m), m != R
+                A ry[2 * R + 1][VX];
+#pragma unroll
+                for (int m = 0; m < 2 * R + 1; ++m) {
+                    if (m == R) continue;
+                    V16<S>::ld(cc + (m - R) * bx, ry[m]);
+                }
+                A fx[VX + 1];  // x-face fluxes: fx[c] is the face left of cell c
+#pragma unroll
+                for (int c = 0; c <= VX; ++c) fx[c] = face_flux<A, R>(wx, c + R - 1);
+                A out[VX];
+#pragma unroll
+                for (int c = 0; c < VX; ++c) {
+                    A qy[2 * R + 1];
+#pragma unroll
+                    for (int m = 0; m < 2 * R + 1; ++m) qy[m] = (m == R) ? q[j][c][R] : ry[m][c];
+                    const A fzp = face_flux<A, R>(q[j][c], R);
+                    out[c] = update_cell_fx<A, R>(fx[c + 1], fx[c], qy, fzm[j][c], fzp, q[j][c][R], lam);
+                    fzm[j][c] = fzp;
+#pragma unroll
+                    for (int i = 0; i < 2 * R; ++i) q[j][c][i] = q[j][c][i + 1];
+                }
+                S *op = dst + zoff + (long long)(t.y0 + gy[j]) * f.px + (t.x0 + gx0[j]);
+                if (vec_store && gx0[j] + VX <= t.tx) {
+                    V16<S>::st(op, out);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < VX; ++c)
+                        if (gx0[j] + c < t.tx) st(op + c, out[c]);
+                }
             }
             if (!ok) { abort_flag = 1; atomicOr(p.err, 1); }
             __syncthreads();  // every thread is done with the centre plane k + R
@@ -225,7 +306,9 @@ static cudaError_t tma_c(int cpt, const StencilTmaParams &p, int grid, cudaStrea
     switch (cpt) {
         case 1: return tma_t<S, A, R, 1>(p, grid, s);
         case 2: return tma_t<S, A, R, 2>(p, grid, s);
-        case 4: return tma_t<S, A, R, 4>(p, grid, s);
+        case 4:
+            if constexpr (R < 4) return tma_t<S, A, R, 4>(p, grid, s);  // radius 4 keeps <= 2 groups per thread
+            break;
     }
     return cudaErrorInvalidValue;
 }
@@ -243,7 +326,7 @@ static cudaError_t tma_r(int R, int cpt, const StencilTmaParams &p, int grid, cu
 cudaError_t launch_stencil_tma(int dtype, int R, bool fp64diff, int cpt, const StencilTmaParams &p, int grid,
                                cudaStream_t s) {
     if (p.ntiles == 0) return cudaSuccess;
-    if (p.nstages > kMaxStages || p.nstages < R + 2) return cudaErrorInvalidValue;
+    if (p.nstages > kMaxStages || p.nstages < R + 2 || (p.nstages & (p.nstages - 1))) return cudaErrorInvalidValue;
     switch (dtype) {
         case F64: return tma_r<double, double>(R, cpt, p, grid, s);
         case F32: return fp64diff ? tma_r<float, double>(R, cpt, p, grid, s) : tma_r<float, float>(R, cpt, p, grid, s);
