@@ -344,6 +344,9 @@ static int build_fb(mf_t *m) {
             t.first = (int)f;
             t.count = (int)std::min<long long>(kTask, cells - f);
             t.level = en.level;
+            t.f0 = make_fastdiv((uint32_t)en.n[0]);
+            t.f1 = make_fastdiv((uint32_t)en.n[1]);
+            t.f2 = make_fastdiv((uint32_t)en.n[2]);
             m->fbtasks.push_back(t);
         }
     }

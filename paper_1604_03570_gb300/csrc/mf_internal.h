@@ -36,6 +36,18 @@ struct FbEntry {
     int level;
 };
 
+// Division by a runtime constant d >= 1 for numerators below 2^31 (round-up multiplier,
+// Granlund & Montgomery 1994): q = (umulhi(n, m) + n) >> s with s = ceil(log2 d),
+// m = floor(2^32 (2^s - d) / d) + 1.
+struct FastDiv {
+    uint32_t m, s;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+    uint32_t s = 0;
+    while ((1ull << s) < d) ++s;
+    return FastDiv{(uint32_t)(((1ull << 32) * ((1ull << s) - d)) / d + 1), s};
+}
+
 // Work unit of the fill kernel, self-contained so that a CTA needs one load to start:
 // cells [first, first + count) of one copy region in the linear order (comp, z, y, x).
 struct FbTask {
@@ -46,7 +58,9 @@ struct FbTask {
     int n0, n1, n2;        // region extents
     int first, count;
     int level;
+    FastDiv f0, f1, f2;    // division by n0, n1, n2
 };
+static_assert(sizeof(FbTask) % 8 == 0, "the fill kernel copies its task header in 8-byte words");
 
 // Stencil work list entry: a logical tile of one box and one component (Sec. 3.2 tilebox()).
 struct Tile {

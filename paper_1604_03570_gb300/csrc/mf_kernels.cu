@@ -29,25 +29,31 @@ namespace mfk {
 
 // ------------------------------------------------------------------ FillBoundary
 
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, FastDiv d) { return (__umulhi(n, d.m) + n) >> d.s; }
+
 template <typename E>
 __global__ void __launch_bounds__(256) k_fill(LevelPtrs lv, const FbTask *__restrict__ tasks, int ntasks) {
     constexpr int U = 4;  // cells per thread per task: all loads issued before the stores
+    __shared__ FbTask sh;
     for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
-        const FbTask tk = tasks[t];
+        __syncthreads();  // the previous task's header is no longer read
+        if (threadIdx.x < (int)(sizeof(FbTask) / 8))
+            ((unsigned long long *)&sh)[threadIdx.x] = __ldg((const unsigned long long *)(tasks + t) + threadIdx.x);
+        __syncthreads();
+        const FbTask &tk = sh;
         E *base = (E *)lv.base[tk.level];
-        const unsigned n0 = tk.n0, n1 = tk.n1, n2 = tk.n2;
         E v[U];
         long long dof[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int i = threadIdx.x + u * (int)blockDim.x;
-            unsigned l = (unsigned)(tk.first + i);
-            const unsigned x = l % n0;
-            l /= n0;
-            const unsigned y = l % n1;
-            l /= n1;
-            const unsigned z = l % n2;
-            const unsigned c = l / n2;
+            const uint32_t l = (uint32_t)(tk.first + i);
+            const uint32_t r0 = fdiv(l, tk.f0);
+            const uint32_t x = l - r0 * (uint32_t)tk.n0;
+            const uint32_t r1 = fdiv(r0, tk.f1);
+            const uint32_t y = r0 - r1 * (uint32_t)tk.n1;
+            const uint32_t c = fdiv(r1, tk.f2);
+            const uint32_t z = r1 - c * (uint32_t)tk.n2;
             dof[u] = tk.dst + c * tk.d_cs + z * tk.d_pl + (long long)y * tk.d_px + x;
             if (i < tk.count) v[u] = __ldg(base + tk.src + c * tk.s_cs + z * tk.s_pl + (long long)y * tk.s_px + x);
         }

@@ -67,6 +67,7 @@ template <> struct FluxW<4> {
 // the lower face): F = b_1 (q[c+1] - q[c]) + sum_{m>=2} b_m (q[c+m] - q[c+1-m]).
 template <typename A, int R>
 __device__ __forceinline__ A face_flux(const A *q, int c) {
+    if constexpr (R == 1) return Ar<A>::sub(q[c + 1], q[c]);  // b_1 = 1: the product is exact
     A f = Ar<A>::mul((A)FluxW<R>::b(1), Ar<A>::sub(q[c + 1], q[c]));
 #pragma unroll
     for (int m = 2; m <= R; ++m) f = Ar<A>::fma((A)FluxW<R>::b(m), Ar<A>::sub(q[c + m], q[c + 1 - m]), f);
