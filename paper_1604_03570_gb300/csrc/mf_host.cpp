@@ -199,6 +199,8 @@ struct mf {
     std::vector<int> fb_cbeg;      // cells before entry within its destination-box group
     std::vector<std::array<int, 6>> fb_corner;  // global lower corners: dst (may lie outside
                                                 // the domain), then src
+    std::vector<int> fb_kind;      // 2*d + (side > 0) for a face region along d, 6 for edges/corners
+    std::vector<FbTask> fbtasks_adv;  // the fill inside mf_advance when the stencil pulls x halos
     // tiles
     int tile[3] = {0, 0, 0};
     bool tile_auto = true;
@@ -213,10 +215,12 @@ struct mf {
     bool attached = false;
     DevBuf d_fabs, d_fb, d_fbtasks, d_tiles, d_cbeg, d_partials, d_sumout;
     // TMA-staged stencil: tensor maps of every FArrayBox over each time level, plane geometry
-    DevBuf d_maps, d_tfab, d_err;
+    DevBuf d_maps, d_tfab, d_err, d_smaps, d_strips, d_fbtasks_adv;
+    bool tma_strips = false;  // x halos pulled from neighbour boxes (fill skips x faces)
     int tma_R = 0;            // radius the maps were encoded for (0 = none)
     bool tma_ok = false;      // current tile shape fits the TMA kernel
     int tma_cpt = 1, tma_slot = 0, tma_ns = 0;
+    int tma_main_slot = 0, tma_strip_rows = 0, tma_strip_bytes = 0, tma_strip_pitch = 0;
     bool use_tma = true;
     double *h_sum = nullptr;       // pinned
     size_t tile_capacity = 0;
@@ -273,58 +277,12 @@ static long long elem_at(const FabInfo &f, int i, int j, int k) {  // global (i,
 
 // ------------------------------------------------------------------ FillBoundary list
 
-static int build_fb(mf_t *m) {
-    const int nb = (int)m->boxes.size(), g = m->ngrow;
-    m->fb.clear();
-    m->fbtasks.clear();
-    m->fb_group.assign(nb + 1, 0);
-    m->fb_cbeg.clear();
-    m->fb_corner.clear();
-    m->ghost_cells = 0;
-    if (g == 0) return 0;
-    BinHash hash;
-    hash.build(m->domain, m->boxes);
-    std::vector<int> cand, stamp(nb, -1);
-    int tag = 0;
-    const int L[3] = {m->domain.len(0), m->domain.len(1), m->domain.len(2)};
-    for (int b = 0; b < nb; ++b) {
-        m->fb_group[b] = (int)m->fb.size();
-        const Box gb = grow(m->boxes[b], g);
-        int cells_in_group = 0;
-        for (int sz = -1; sz <= 1; ++sz)
-            for (int sy = -1; sy <= 1; ++sy)
-                for (int sx = -1; sx <= 1; ++sx) {
-                    const int s[3] = {sx * L[0], sy * L[1], sz * L[2]};
-                    const int ms[3] = {-s[0], -s[1], -s[2]};
-                    const Box q = shift(gb, ms);  // the grown box seen from the periodic image
-                    hash.query(q, cand, stamp, ++tag);
-                    std::sort(cand.begin(), cand.end());
-                    for (int a : cand) {
-                        if (a == b && sx == 0 && sy == 0 && sz == 0) continue;
-                        const Box src = intersect(m->boxes[a], q);
-                        if (src.empty()) continue;
-                        const Box dst = shift(src, s);
-                        FbEntry e{};
-                        for (int d = 0; d < 3; ++d) e.n[d] = src.len(d);
-                        e.sfab = a;
-                        e.dfab = b;
-                        e.level = 0;
-                        e.src = elem_at(m->fabs[a], src.lo[0], src.lo[1], src.lo[2]);
-                        e.dst = elem_at(m->fabs[b], dst.lo[0], dst.lo[1], dst.lo[2]);
-                        const long long cells = src.cells() * m->ncomp;
-                        if (cells > 0x7fffffffLL) return fail(MF_EINVAL, "ghost region too large");
-                        m->fb_cbeg.push_back(cells_in_group);
-                        m->fb_corner.push_back({dst.lo[0], dst.lo[1], dst.lo[2], src.lo[0], src.lo[1], src.lo[2]});
-                        cells_in_group += (int)cells;
-                        m->ghost_cells += src.cells();
-                        m->fb.push_back(e);
-                    }
-                }
-    }
-    m->fb_group[nb] = (int)m->fb.size();
-    // split entries into CTA-sized tasks (256 threads x 4 cells)
+// FillBoundary tasks for the entries selected by `use`: CTA-sized pieces (256 threads x 4 cells).
+static void make_fill_tasks(const mf_t *m, const std::vector<char> &use, std::vector<FbTask> &out) {
     const int kTask = 1024;
+    out.clear();
     for (int e = 0; e < (int)m->fb.size(); ++e) {
+        if (!use[e]) continue;
         const FbEntry &en = m->fb[e];
         const FabInfo &sf = m->fabs[en.sfab], &df = m->fabs[en.dfab];
         const long long cells = (long long)en.n[0] * en.n[1] * en.n[2] * m->ncomp;
@@ -347,9 +305,84 @@ static int build_fb(mf_t *m) {
             t.f0 = make_fastdiv((uint32_t)en.n[0]);
             t.f1 = make_fastdiv((uint32_t)en.n[1]);
             t.f2 = make_fastdiv((uint32_t)en.n[2]);
-            m->fbtasks.push_back(t);
+            out.push_back(t);
         }
     }
+}
+
+static int build_fb(mf_t *m) {
+    const int nb = (int)m->boxes.size(), g = m->ngrow;
+    m->fb.clear();
+    m->fbtasks.clear();
+    m->fb_group.assign(nb + 1, 0);
+    m->fb_cbeg.clear();
+    m->fb_corner.clear();
+    m->fb_kind.clear();
+    m->ghost_cells = 0;
+    if (g == 0) return 0;
+    BinHash hash;
+    hash.build(m->domain, m->boxes);
+    std::vector<int> cand, stamp(nb, -1);
+    int tag = 0;
+    const int L[3] = {m->domain.len(0), m->domain.len(1), m->domain.len(2)};
+    for (int b = 0; b < nb; ++b) {
+        m->fb_group[b] = (int)m->fb.size();
+        const Box gb = grow(m->boxes[b], g);
+        int cells_in_group = 0;
+        for (int sz = -1; sz <= 1; ++sz)
+            for (int sy = -1; sy <= 1; ++sy)
+                for (int sx = -1; sx <= 1; ++sx) {
+                    const int s[3] = {sx * L[0], sy * L[1], sz * L[2]};
+                    const int ms[3] = {-s[0], -s[1], -s[2]};
+                    const Box q = shift(gb, ms);  // the grown box seen from the periodic image
+                    hash.query(q, cand, stamp, ++tag);
+                    std::sort(cand.begin(), cand.end());
+                    for (int a : cand) {
+                        if (a == b && sx == 0 && sy == 0 && sz == 0) continue;
+                        const Box src0 = intersect(m->boxes[a], q);
+                        if (src0.empty()) continue;
+                        const Box dst0 = shift(src0, s);
+                        // split by the 27 parts of the grown box: faces, edges, corners
+                        const Box &B = m->boxes[b];
+                        for (int pz = 0; pz < 3; ++pz)
+                            for (int py = 0; py < 3; ++py)
+                                for (int px = 0; px < 3; ++px) {
+                                    const int part[3] = {px, py, pz};
+                                    Box cut;
+                                    int outside = 0, fdim = -1, fside = 0;
+                                    for (int d = 0; d < 3; ++d) {
+                                        const int lo = part[d] == 0 ? B.lo[d] - g : part[d] == 1 ? B.lo[d] : B.hi[d] + 1;
+                                        const int hi = part[d] == 0 ? B.lo[d] - 1 : part[d] == 1 ? B.hi[d] : B.hi[d] + g;
+                                        cut.lo[d] = lo;
+                                        cut.hi[d] = hi;
+                                        if (part[d] != 1) { ++outside; fdim = d; fside = part[d] == 2 ? 1 : 0; }
+                                    }
+                                    const Box dst = intersect(dst0, cut);
+                                    if (dst.empty()) continue;
+                                    const Box src = shift(dst, ms);
+                                    FbEntry e{};
+                                    for (int d = 0; d < 3; ++d) e.n[d] = src.len(d);
+                                    e.sfab = a;
+                                    e.dfab = b;
+                                    e.level = 0;
+                                    e.src = elem_at(m->fabs[a], src.lo[0], src.lo[1], src.lo[2]);
+                                    e.dst = elem_at(m->fabs[b], dst.lo[0], dst.lo[1], dst.lo[2]);
+                                    const long long cells = src.cells() * m->ncomp;
+                                    if (cells > 0x7fffffffLL) return fail(MF_EINVAL, "ghost region too large");
+                                    m->fb_cbeg.push_back(cells_in_group);
+                                    m->fb_corner.push_back(
+                                        {dst.lo[0], dst.lo[1], dst.lo[2], src.lo[0], src.lo[1], src.lo[2]});
+                                    m->fb_kind.push_back(outside == 1 ? 2 * fdim + fside : 6);
+                                    cells_in_group += (int)cells;
+                                    m->ghost_cells += src.cells();
+                                    m->fb.push_back(e);
+                                }
+                    }
+                }
+    }
+    m->fb_group[nb] = (int)m->fb.size();
+    std::vector<char> all(m->fb.size(), 1);
+    make_fill_tasks(m, all, m->fbtasks);
     return 0;
 }
 
@@ -836,24 +869,94 @@ static bool tma_geometry(mf_t *m, int R, std::vector<TmaFab> &tf, int &slot_byte
     return true;
 }
 
+// x-halo strips: for a tile on the low (high) x face of its box, the box owning the column
+// just outside that face over all the tile's rows and planes, when one box owns all of it.
+static void find_strips(mf_t *m, int R, std::vector<TileStrip> &st, std::vector<char> &served) {
+    const int S = m->esize, A = 16 / S, g = m->ngrow;
+    const int XH = (R + A - 1) / A * A;
+    const int nb = (int)m->boxes.size();
+    st.assign(m->tiles.size(), TileStrip{-1, -1, 0, 0, 0, 0, 0, 0});
+    // served[2b + side]: every tile on that face pulls its halo from a neighbour
+    served.assign(2 * (size_t)nb, 1);
+    std::vector<char> touched(2 * (size_t)nb, 0);
+    BinHash hash;
+    hash.build(m->domain, m->boxes);
+    std::vector<int> cand, stamp(nb, -1);
+    int tag = 0;
+    const int Lx = m->domain.len(0);
+    for (size_t w = 0; w < m->tiles.size(); ++w) {
+        const Tile &t = m->tiles[w];
+        const Box &B = m->boxes[t.fab];
+        for (int side = 0; side < 2; ++side) {
+            const bool at_face = side == 0 ? t.x0 == 0 : t.x0 + t.tx == B.len(0);
+            if (!at_face) continue;
+            touched[2 * t.fab + side] = 1;
+            const int X = side == 0 ? B.lo[0] - 1 : B.hi[0] + 1;
+            const int wx = m->domain.lo[0] + (((X - m->domain.lo[0]) % Lx) + Lx) % Lx;
+            Box q;
+            q.lo[0] = q.hi[0] = wx;
+            q.lo[1] = B.lo[1] + t.y0;
+            q.hi[1] = q.lo[1] + t.ty - 1;
+            q.lo[2] = B.lo[2] + t.z0;
+            q.hi[2] = q.lo[2] + t.tz - 1;
+            hash.query(q, cand, stamp, ++tag);
+            int owner = -1;
+            for (int a : cand) {
+                const Box &Ab = m->boxes[a];
+                bool in = true;
+                for (int d = 0; d < 3; ++d) in = in && Ab.lo[d] <= q.lo[d] && q.hi[d] <= Ab.hi[d];
+                if (in) { owner = a; break; }
+            }
+            const bool ok = owner >= 0 && m->boxes[owner].len(0) >= XH && m->boxes[owner].len(0) % A == 0 &&
+                            t.tx % A == 0;
+            if (!ok) {
+                served[2 * t.fab + side] = 0;
+                continue;
+            }
+            const Box &Ab = m->boxes[owner];
+            const int xvA = (g + A - 1) / A * A;
+            const int x = side == 0 ? xvA + Ab.len(0) - XH : xvA;
+            const int y = g + q.lo[1] - Ab.lo[1], z = g + q.lo[2] - Ab.lo[2];
+            if (side == 0) { st[w].lfab = owner; st[w].lx = x; st[w].ly = y; st[w].lz = z; }
+            else { st[w].rfab = owner; st[w].rx = x; st[w].ry = y; st[w].rz = z; }
+        }
+    }
+    for (size_t i = 0; i < served.size(); ++i) served[i] = served[i] && touched[i];
+    // a tile uses a strip only if its whole face is served (so the face is never filled)
+    for (size_t w = 0; w < m->tiles.size(); ++w) {
+        if (st[w].lfab >= 0 && !served[2 * m->tiles[w].fab]) st[w].lfab = -1;
+        if (st[w].rfab >= 0 && !served[2 * m->tiles[w].fab + 1]) st[w].rfab = -1;
+    }
+}
+
 static int build_tma(mf_t *m, int R) {
     m->tma_ok = false;
+    m->tma_strips = false;
     m->tma_R = R;
     if (!m->use_tma) return 0;
     std::vector<TmaFab> tf;
-    int slot = 0, cpt = 0;
-    if (!tma_geometry(m, R, tf, slot, cpt)) return 0;
+    int main_slot = 0, gpt = 0;
+    if (!tma_geometry(m, R, tf, main_slot, gpt)) return 0;
+    const int S = m->esize, A = 16 / S;
+    const int XH = (R + A - 1) / A * A;
+    int srows = 1;
+    for (auto &t : m->tiles) srows = std::max(srows, (int)t.ty);
+    std::vector<TileStrip> strips;
+    std::vector<char> served;
+    find_strips(m, R, strips, served);
+    const int strip_bytes = XH * srows * S;
+    const int strip_pitch = (strip_bytes + 127) / 128 * 128;
+    const int slot = main_slot + 2 * strip_pitch;
     int ns = R == 4 ? 16 : 8;  // ring slots (power of two)
     while (ns > 8 && (long long)ns * slot + 128 > 160 * 1024) ns /= 2;
     if (ns < 2 * R || (long long)ns * slot + 128 > 200 * 1024) return 0;
     auto encode = tensor_map_encoder();
     if (!encode) return 0;
     const int nf = (int)m->fabs.size();
-    std::vector<CUtensorMap> maps(2 * (size_t)nf);
+    std::vector<CUtensorMap> maps(2 * (size_t)nf), smaps(2 * (size_t)nf);
     const CUtensorMapDataType dt = m->dtype == F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
                                    : m->dtype == F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                                      : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    const int S = m->esize;
     for (int which = 0; which < 2; ++which)
         for (int b = 0; b < nf; ++b) {
             const FabInfo &f = m->fabs[b];
@@ -862,21 +965,44 @@ static int build_tma(mf_t *m, int R) {
                                   (cuuint64_t)m->ncomp};
             cuuint64_t strides[3] = {(cuuint64_t)f.px * S, (cuuint64_t)f.plane * S, (cuuint64_t)f.cstride * S};
             cuuint32_t box[4] = {(cuuint32_t)tf[b].bx, (cuuint32_t)tf[b].by, 1, 1};
+            cuuint32_t sbox[4] = {(cuuint32_t)XH, (cuuint32_t)srows, 1, 1};
             cuuint32_t estr[4] = {1, 1, 1, 1};
             void *gaddr = (char *)m->level_ptr(which) + (size_t)m->fab_start[b] * S;
             CUresult r = encode(&maps[(size_t)which * nf + b], dt, 4, gaddr, dims, strides, box, estr,
                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             if (r != CUDA_SUCCESS) return fail(MF_ECUDA, "cuTensorMapEncodeTiled failed (%d) for box %d", (int)r, b);
+            r = encode(&smaps[(size_t)which * nf + b], dt, 4, gaddr, dims, strides, sbox, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return fail(MF_ECUDA, "cuTensorMapEncodeTiled (strip) failed (%d)", (int)r);
         }
+    // the fill inside the advance: faces only (the star stencil reads no edge or corner), and
+    // no x face that the stencil pulls from the neighbour
+    std::vector<char> use(m->fb.size(), 0);
+    for (size_t e = 0; e < m->fb.size(); ++e) {
+        const int k = m->fb_kind[e];
+        if (k == 6) continue;
+        if (k < 2 && served[2 * (size_t)m->fb[e].dfab + k]) continue;
+        use[e] = 1;
+    }
+    make_fill_tasks(m, use, m->fbtasks_adv);
     int rc;
     if ((rc = m->d_maps.upload(maps, m->stream))) return rc;
+    if ((rc = m->d_smaps.upload(smaps, m->stream))) return rc;
     if ((rc = m->d_tfab.upload(tf, m->stream))) return rc;
+    if ((rc = m->d_strips.upload(strips, m->stream))) return rc;
+    if ((rc = m->d_fbtasks_adv.upload(m->fbtasks_adv, m->stream))) return rc;
     CU(cudaStreamSynchronize(m->stream));
-    m->tma_cpt = cpt;
+    m->tma_cpt = gpt;
     m->tma_slot = slot;
     m->tma_ns = ns;
+    m->tma_main_slot = main_slot;
+    m->tma_strip_rows = srows;
+    m->tma_strip_bytes = strip_bytes;
+    m->tma_strip_pitch = strip_pitch;
     m->tma_ok = true;
+    m->tma_strips = true;
     return 0;
 }
 
@@ -890,6 +1016,16 @@ static LevelPtrs level_ptrs(const mf_t *m, int which) {
 
 static int enqueue_fill(mf_t *m, int which, cudaStream_t s) {
     CU(launch_fill(m->dtype, level_ptrs(m, which), (const FbTask *)m->d_fbtasks.p, (int)m->fbtasks.size(), 0, s));
+    return 0;
+}
+
+// The ghost exchange a time step needs: with the TMA stencil, only the face regions it reads
+// from ghost cells (edges and corners are never read by a star stencil; x faces whose tiles
+// take their halo from the neighbour box are skipped).
+static int enqueue_fill_step(mf_t *m, int which, cudaStream_t s) {
+    if (!(m->use_tma && m->tma_ok && m->tma_strips)) return enqueue_fill(m, which, s);
+    CU(launch_fill(m->dtype, level_ptrs(m, which), (const FbTask *)m->d_fbtasks_adv.p, (int)m->fbtasks_adv.size(), 0,
+                   s));
     return 0;
 }
 
@@ -920,6 +1056,12 @@ static int enqueue_stencil(mf_t *m, int from, int R, bool fp64diff, const double
         p.slot_bytes = m->tma_slot;
         p.dst[0] = m->level_ptr(1 - from);
         p.err = (int *)m->d_err.p;
+        p.smaps = (const CUtensorMap *)m->d_smaps.p + (size_t)from * m->fabs.size();
+        p.strips = (const TileStrip *)m->d_strips.p;
+        p.strip_rows = m->tma_strip_rows;
+        p.strip_off = m->tma_main_slot;
+        p.strip_bytes = m->tma_strip_bytes;
+        p.strip_pitch = m->tma_strip_pitch;
         for (int c = 0; c < m->ncomp; ++c) p.lam[0][c] = lam[c];
         CU(launch_stencil_tma(m->dtype, R, fp64diff, m->tma_cpt, p, 0, s));
         return 0;
@@ -1097,7 +1239,7 @@ extern "C" int mf_advance(mf_t *m, const mf_stencil *st, double dt, int nsteps) 
         int body = 0, from = m->cur;
         if (m->timing) body = record(m, 0);
         for (int s = 0; s < nsteps && !body; ++s) {
-            body = enqueue_fill(m, from, m->cap);
+            body = enqueue_fill_step(m, from, m->cap);
             if (!body && m->timing) body = record(m, 2 * s + 1);
             if (!body) body = enqueue_stencil(m, from, R, fp64diff, lam, m->cap);
             if (!body && m->timing) body = record(m, 2 * s + 2);
@@ -1341,11 +1483,12 @@ extern "C" int mf_amr_advance(mf_t *crse, mf_t *fine, const mf_stencil *st, doub
         cudaStream_t s = crse->cap;
         int body = 0, c = crse->cur, f = fine->cur;
         for (int step = 0; step < ncrse_steps && !body; ++step) {
+            // full exchange: the coarse-fine interpolation reads coarse edge and corner ghosts
             body = enqueue_fill(crse, c, s);
             if (!body) body = enqueue_stencil(crse, c, R, fp64diff, lam_c, s);
             if (!body) body = enqueue_fill(crse, 1 - c, s);
             for (int sub = 0; sub < nsub && !body; ++sub) {
-                body = enqueue_fill(fine, f, s);
+                body = enqueue_fill_step(fine, f, s);
                 if (!body)
                     body = enqueue_interp(fine, f, crse, c, crse, 1 - c, ip, ratio, (double)sub / (double)nsub, s);
                 if (!body) body = enqueue_stencil(fine, f, R, fp64diff, lam_f, s);

@@ -110,8 +110,23 @@ struct TmaFab {
     int xv;       // row element of valid x = 0 (16-byte aligned)
 };
 
+// x halo of a tile taken straight from the neighbouring box (its valid cells), or -1 when
+// the tile's own ghost columns hold it.  Coordinates are the neighbour tensor's (x, y, z) of
+// the strip for the tile's first z plane.
+struct TileStrip {
+    int lfab, rfab;
+    int lx, ly, lz;
+    int rx, ry, rz;
+};
+
 struct StencilTmaParams {
     const CUtensorMap *maps;   // one per FArrayBox, over the source time level
+    const CUtensorMap *smaps;  // strip maps (box XH x strip_rows), over the source time level
+    const TileStrip *strips;   // per tile, or nullptr
+    int strip_rows;            // rows of a strip load
+    int strip_off;             // byte offset of the left strip in a slot; right strip follows
+    int strip_bytes;           // bytes of one strip load (right strip at strip_off + strip_pitch)
+    int strip_pitch;
     const TmaFab *tfab;
     const FabInfo *ftab;
     const Tile *tiles;

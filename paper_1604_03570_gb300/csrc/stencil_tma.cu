@@ -142,11 +142,22 @@ __global__ void __launch_bounds__(kTmaThreads) k_stencil_tma(const __grid_consta
         const int xcoord = tf.xv + t.x0 - XH;       // 16-byte aligned row element of the first loaded column
         const int ycoord = tf.ngrow + t.y0 - R, zcoord = tf.ngrow + t.z0 - R;
 
+        TileStrip ts;
+        ts.lfab = ts.rfab = -1;
+        if (p.strips) ts = p.strips[w];
         auto slot_of = [&](int pl) -> uint32_t { return (seq + (uint32_t)pl) & (uint32_t)(NS - 1); };
         auto issue = [&](int pl) {
             const uint32_t sl = slot_of(pl);
-            mbar_expect_tx(&bars[sl], plane_bytes);
-            tma_load_4d(slots + (size_t)sl * p.slot_bytes, map, &bars[sl], xcoord, ycoord, zcoord + pl, t.comp);
+            unsigned char *sp = slots + (size_t)sl * p.slot_bytes;
+            // centre planes (the x neighbours of the tile's cells) also take the x halo strips
+            const bool centre = pl >= R && pl < R + t.tz;
+            const bool ls = centre && ts.lfab >= 0, rs = centre && ts.rfab >= 0;
+            mbar_expect_tx(&bars[sl], plane_bytes + (ls ? p.strip_bytes : 0) + (rs ? p.strip_bytes : 0));
+            tma_load_4d(sp, map, &bars[sl], xcoord, ycoord, zcoord + pl, t.comp);
+            if (ls) tma_load_4d(sp + p.strip_off, p.smaps + ts.lfab, &bars[sl], ts.lx, ts.ly, ts.lz + pl - R, t.comp);
+            if (rs)
+                tma_load_4d(sp + p.strip_off + p.strip_pitch, p.smaps + ts.rfab, &bars[sl], ts.rx, ts.ry,
+                            ts.rz + pl - R, t.comp);
         };
         auto wait_plane = [&](int pl) -> bool {
             const uint32_t sq = seq + (uint32_t)pl;
@@ -220,13 +231,19 @@ __global__ void __launch_bounds__(kTmaThreads) k_stencil_tma(const __grid_consta
 #pragma unroll
                     for (int c = 0; c < VX; ++c) q[j][c][2 * R] = v[c];
                 }
-                // x window: w[i] = u(x0 - R + i), i = 0 .. VX + 2R - 1
+                // x window: w[i] = u(x0 - R + i), i = 0 .. VX + 2R - 1; at the box edge the halo
+                // comes from the neighbour's strip when the tile has one
                 A wx[VX + 2 * R];
                 const S *cc = cp + soff[j];
+                const S *lh = cc - R, *rh = cc + VX;
+                if (gx0[j] == 0 && ts.lfab >= 0)
+                    lh = (const S *)((const unsigned char *)cp + p.strip_off) + gy[j] * XH + (XH - R);
+                if (gx0[j] + VX == t.tx && ts.rfab >= 0)
+                    rh = (const S *)((const unsigned char *)cp + p.strip_off + p.strip_pitch) + gy[j] * XH;
 #pragma unroll
                 for (int i = 0; i < R; ++i) {
-                    wx[i] = ld_smem<S, A>(cc - R + i);
-                    wx[R + VX + i] = ld_smem<S, A>(cc + VX + i);
+                    wx[i] = ld_smem<S, A>(lh + i);
+                    wx[R + VX + i] = ld_smem<S, A>(rh + i);
                 }
 #pragma unroll
                 for (int c = 0; c < VX; ++c) wx[R + c] = q[j][c][R];
