@@ -235,15 +235,15 @@ __global__ void __launch_bounds__(kTmaThreads) k_stencil_tma(const __grid_consta
                 // comes from the neighbour's strip when the tile has one
                 A wx[VX + 2 * R];
                 const S *cc = cp + soff[j];
-                const S *lh = cc - R, *rh = cc + VX;
-                if (gx0[j] == 0 && ts.lfab >= 0)
-                    lh = (const S *)((const unsigned char *)cp + p.strip_off) + gy[j] * XH + (XH - R);
-                if (gx0[j] + VX == t.tx && ts.rfab >= 0)
-                    rh = (const S *)((const unsigned char *)cp + p.strip_off + p.strip_pitch) + gy[j] * XH;
+                const S *ls = (const S *)((const unsigned char *)cp + p.strip_off) + gy[j] * XH + XH;
+                const S *rs = (const S *)((const unsigned char *)cp + p.strip_off + p.strip_pitch) + gy[j] * XH;
 #pragma unroll
                 for (int i = 0; i < R; ++i) {
-                    wx[i] = ld_smem<S, A>(lh + i);
-                    wx[R + VX + i] = ld_smem<S, A>(rh + i);
+                    // cell gx0 - R + i (left) and gx0 + VX + i (right), tile coordinates; strips
+                    // exist only for tiles on a box face, so outside the tile means outside the box
+                    const int xl = gx0[j] - R + i, xr = gx0[j] + VX + i;
+                    wx[i] = ld_smem<S, A>((xl < 0 && ts.lfab >= 0) ? ls + xl : cc - R + i);
+                    wx[R + VX + i] = ld_smem<S, A>((xr >= t.tx && ts.rfab >= 0) ? rs + (xr - t.tx) : cc + VX + i);
                 }
 #pragma unroll
                 for (int c = 0; c < VX; ++c) wx[R + c] = q[j][c][R];
