@@ -869,8 +869,9 @@ static bool tma_geometry(mf_t *m, int R, std::vector<TmaFab> &tf, int &slot_byte
     return true;
 }
 
-// x-halo strips: for a tile on the low (high) x face of its box, the box owning the column
-// just outside that face over all the tile's rows and planes, when one box owns all of it.
+// x-halo strips: for a tile whose x halo leaves its box on the low (high) side, the box
+// owning the column just outside that face over all the tile's rows and planes, when one box
+// owns all of it.  The strip holds that box's XH valid columns next to the face.
 static void find_strips(mf_t *m, int R, std::vector<TileStrip> &st, std::vector<char> &served) {
     const int S = m->esize, A = 16 / S, g = m->ngrow;
     const int XH = (R + A - 1) / A * A;
@@ -888,7 +889,8 @@ static void find_strips(mf_t *m, int R, std::vector<TileStrip> &st, std::vector<
         const Tile &t = m->tiles[w];
         const Box &B = m->boxes[t.fab];
         for (int side = 0; side < 2; ++side) {
-            const bool at_face = side == 0 ? t.x0 == 0 : t.x0 + t.tx == B.len(0);
+            // the tile's x halo leaves the box on this side
+            const bool at_face = side == 0 ? t.x0 < R : t.x0 + t.tx + R > B.len(0);
             if (!at_face) continue;
             touched[2 * t.fab + side] = 1;
             const int X = side == 0 ? B.lo[0] - 1 : B.hi[0] + 1;
@@ -907,8 +909,7 @@ static void find_strips(mf_t *m, int R, std::vector<TileStrip> &st, std::vector<
                 for (int d = 0; d < 3; ++d) in = in && Ab.lo[d] <= q.lo[d] && q.hi[d] <= Ab.hi[d];
                 if (in) { owner = a; break; }
             }
-            const bool ok = owner >= 0 && m->boxes[owner].len(0) >= XH && m->boxes[owner].len(0) % A == 0 &&
-                            t.tx % A == 0;
+            const bool ok = owner >= 0 && m->boxes[owner].len(0) >= XH && m->boxes[owner].len(0) % A == 0;
             if (!ok) {
                 served[2 * t.fab + side] = 0;
                 continue;

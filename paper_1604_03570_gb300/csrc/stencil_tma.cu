@@ -239,11 +239,11 @@ __global__ void __launch_bounds__(kTmaThreads) k_stencil_tma(const __grid_consta
                 const S *rs = (const S *)((const unsigned char *)cp + p.strip_off + p.strip_pitch) + gy[j] * XH;
 #pragma unroll
                 for (int i = 0; i < R; ++i) {
-                    // cell gx0 - R + i (left) and gx0 + VX + i (right), tile coordinates; strips
-                    // exist only for tiles on a box face, so outside the tile means outside the box
-                    const int xl = gx0[j] - R + i, xr = gx0[j] + VX + i;
+                    // cells x0 + gx0 - R + i (left) and x0 + gx0 + VX + i (right) of the box: outside
+                    // the box they come from the neighbour strips when the tile has them
+                    const int xl = t.x0 + gx0[j] - R + i, xr = t.x0 + gx0[j] + VX + i;
                     wx[i] = ld_smem<S, A>((xl < 0 && ts.lfab >= 0) ? ls + xl : cc - R + i);
-                    wx[R + VX + i] = ld_smem<S, A>((xr >= t.tx && ts.rfab >= 0) ? rs + (xr - t.tx) : cc + VX + i);
+                    wx[R + VX + i] = ld_smem<S, A>((xr >= f.n[0] && ts.rfab >= 0) ? rs + (xr - f.n[0]) : cc + VX + i);
                 }
 #pragma unroll
                 for (int c = 0; c < VX; ++c) wx[R + c] = q[j][c][R];
