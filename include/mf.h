@@ -198,6 +198,28 @@ int mf_current(const mf_t *mf);
 
 const char *mf_last_error(void);
 
+/*
+ * mf_sum_strided_noalloc -- the compensated FP64 sum of mf_sum for one strided 3-D device
+ * array, for callers that cannot allocate device memory: code running while another component
+ * owns every device allocation (a caching allocator or a fixed memory pool), real-time loops
+ * where an allocation could stall or fail, plug-ins in processes that forbid new allocations.
+ * It calls no cudaMalloc, cudaFree or allocating library routine and needs no mf_t handle.
+ * The paper has no counterpart of this entry point.
+ *
+ * data   device pointer (current device) to element (0,0,0); element (x, y, z) is at
+ *        data + x + y*sy + z*sz (strides in elements, sy >= nx, sz >= sy*ny); dtype MF_F64,
+ *        MF_F32 or MF_BF16.  nx*ny*nz <= 268,435,456 cells, else MF_EINVAL.
+ * out    host pointer receiving the sum.  stream: cudaStream_t (NULL = legacy stream); the
+ *        call enqueues two kernels and a copy on it and synchronises it.
+ * Scratch: a file-scope device array of 1 MiB (65,536 block partials), present on every GPU
+ * that loads the library until the process exits.  The first call on a device looks up the
+ * array's device address (with that device current) and caches it; make that first call
+ * before any stream capture.  Every call reuses the same array, so calls whose kernels overlap
+ * on the GPU (other streams, other host threads) race and must be serialised by the caller.
+ */
+int mf_sum_strided_noalloc(const void *data, int dtype, int nx, int ny, int nz, long long sy, long long sz,
+                           double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

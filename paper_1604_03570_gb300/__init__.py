@@ -28,7 +28,7 @@ EXPORTS = [
     "mf_get_fb_regions", "mf_attach", "mf_set_tile", "mf_get_tile", "mf_copy_from_host", "mf_copy_to_host",
     "mf_copy_fab_to_host", "mf_copy_fab_from_host", "mf_fill_boundary", "mf_interp_cf", "mf_average_down",
     "mf_advance", "mf_amr_advance", "mf_sum", "mf_step_bytes", "mf_current", "mf_last_error", "mf_set_timing",
-    "mf_phase_ms", "mf_set_kernel",
+    "mf_phase_ms", "mf_set_kernel", "mf_sum_strided_noalloc",
 ]
 
 
@@ -77,6 +77,7 @@ def _load():
         "mf_set_timing": (I, [P, I]),
         "mf_phase_ms": (I, [P, P]),
         "mf_set_kernel": (I, [P, I]),
+        "mf_sum_strided_noalloc": (I, [P, I, I, I, I, LL, LL, ctypes.POINTER(D), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -255,6 +256,15 @@ def mf_phase_ms(h):
     out = np.zeros(2, dtype=np.float64)
     _check(lib.mf_phase_ms(h, _ptr(out)))
     return float(out[0]), float(out[1])
+
+
+def mf_sum_strided_noalloc(data_ptr, dtype, nx, ny, nz, sy, sz, stream=0):
+    """Compensated FP64 sum of a strided device array (element strides sy, sz), allocating
+    nothing (scratch in a fixed device array of the library)."""
+    out = ctypes.c_double()
+    _check(lib.mf_sum_strided_noalloc(ctypes.c_void_p(int(data_ptr)), _dtype_code(dtype), int(nx), int(ny), int(nz),
+                                      int(sy), int(sz), ctypes.byref(out), ctypes.c_void_p(int(stream or 0))))
+    return out.value
 
 
 def mf_last_error():

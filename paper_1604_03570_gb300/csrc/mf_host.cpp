@@ -48,6 +48,11 @@ static int fail(int code, const char *fmt, ...) {
     return code;
 }
 
+int mfk::set_error(int code, const char *msg) {
+    g_err = msg;
+    return code;
+}
+
 #define CU(call)                                                                                 \
     do {                                                                                         \
         cudaError_t e_ = (call);                                                                 \

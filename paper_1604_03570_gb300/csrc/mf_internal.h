@@ -166,4 +166,7 @@ cudaError_t launch_avgdown(int dtype, const void *fbase, const FabInfo *ffabs, v
 
 int sm_count();
 
+// Sets the message mf_last_error() returns on this thread; returns code.
+int set_error(int code, const char *msg);
+
 }  // namespace mfk
