@@ -220,7 +220,9 @@ struct mf {
     bool attached = false;
     DevBuf d_fabs, d_fb, d_fbtasks, d_tiles, d_cbeg, d_partials, d_sumout;
     // TMA-staged stencil: tensor maps of every FArrayBox over each time level, plane geometry
-    DevBuf d_maps, d_tfab, d_err, d_smaps, d_strips, d_fbtasks_adv;
+    DevBuf d_maps, d_tfab, d_err, d_smaps, d_strips, d_fbtasks_adv, d_push, d_fbtasks_res;
+    std::vector<FbTask> fbtasks_res;  // the fill left once the stencil pushes face ghosts
+    bool tma_push = false;
     bool tma_strips = false;  // x halos pulled from neighbour boxes (fill skips x faces)
     int tma_R = 0;            // radius the maps were encoded for (0 = none)
     bool tma_ok = false;      // current tile shape fits the TMA kernel
@@ -938,6 +940,7 @@ static void find_strips(mf_t *m, int R, std::vector<TileStrip> &st, std::vector<
 static int build_tma(mf_t *m, int R) {
     m->tma_ok = false;
     m->tma_strips = false;
+    m->tma_push = false;
     m->tma_R = R;
     if (!m->use_tma) return 0;
     std::vector<TmaFab> tf;
@@ -993,12 +996,55 @@ static int build_tma(mf_t *m, int R) {
         use[e] = 1;
     }
     make_fill_tasks(m, use, m->fbtasks_adv);
+    // ghost push: every y/z face region is written by the tiles that compute its source cells;
+    // only x faces not served by strips remain for the fill of later steps
+    std::vector<PushPiece> pieces;
+    {
+        std::vector<std::vector<int>> by_src(m->boxes.size());
+        for (size_t e = 0; e < m->fb.size(); ++e)
+            if (m->fb_kind[e] >= 2 && m->fb_kind[e] < 6) by_src[m->fb[e].sfab].push_back((int)e);
+        for (size_t w = 0; w < m->tiles.size(); ++w) {
+            const Tile &t = m->tiles[w];
+            const Box &B = m->boxes[t.fab];
+            const int tlo[3] = {B.lo[0] + t.x0, B.lo[1] + t.y0, B.lo[2] + t.z0};
+            const int thi[3] = {tlo[0] + t.tx - 1, tlo[1] + t.ty - 1, tlo[2] + t.tz - 1};
+            strips[w].pfirst = (int)pieces.size();
+            for (int e : by_src[t.fab]) {
+                const FbEntry &en = m->fb[e];
+                const auto &cr = m->fb_corner[e];
+                int lo[3], hi[3];
+                bool empty = false;
+                for (int d = 0; d < 3; ++d) {
+                    lo[d] = std::max(cr[3 + d], tlo[d]);
+                    hi[d] = std::min(cr[3 + d] + en.n[d] - 1, thi[d]);
+                    empty = empty || lo[d] > hi[d];
+                }
+                if (empty) continue;
+                PushPiece pp{};
+                pp.dfab = en.dfab;
+                pp.x0 = lo[0] - tlo[0]; pp.y0 = lo[1] - tlo[1]; pp.z0 = lo[2] - tlo[2];
+                pp.nx = hi[0] - lo[0] + 1; pp.ny = hi[1] - lo[1] + 1; pp.nz = hi[2] - lo[2] + 1;
+                pp.dst = elem_at(m->fabs[en.dfab], cr[0] + (lo[0] - cr[3]), cr[1] + (lo[1] - cr[4]),
+                                 cr[2] + (lo[2] - cr[5]));
+                pieces.push_back(pp);
+            }
+            strips[w].pcount = (int)pieces.size() - strips[w].pfirst;
+        }
+        std::vector<char> res(m->fb.size(), 0);
+        for (size_t e = 0; e < m->fb.size(); ++e) {
+            const int k = m->fb_kind[e];
+            res[e] = k < 2 && !served[2 * (size_t)m->fb[e].dfab + k];
+        }
+        make_fill_tasks(m, res, m->fbtasks_res);
+    }
     int rc;
     if ((rc = m->d_maps.upload(maps, m->stream))) return rc;
     if ((rc = m->d_smaps.upload(smaps, m->stream))) return rc;
     if ((rc = m->d_tfab.upload(tf, m->stream))) return rc;
     if ((rc = m->d_strips.upload(strips, m->stream))) return rc;
     if ((rc = m->d_fbtasks_adv.upload(m->fbtasks_adv, m->stream))) return rc;
+    if ((rc = m->d_fbtasks_res.upload(m->fbtasks_res, m->stream))) return rc;
+    if ((rc = m->d_push.upload(pieces, m->stream))) return rc;
     CU(cudaStreamSynchronize(m->stream));
     m->tma_cpt = gpt;
     m->tma_slot = slot;
@@ -1009,6 +1055,7 @@ static int build_tma(mf_t *m, int R) {
     m->tma_strip_pitch = strip_pitch;
     m->tma_ok = true;
     m->tma_strips = true;
+    m->tma_push = true;
     return 0;
 }
 
@@ -1046,7 +1093,8 @@ static StencilParams stencil_params(const mf_t *m, int from, const double *lam) 
     return p;
 }
 
-static int enqueue_stencil(mf_t *m, int from, int R, bool fp64diff, const double *lam, cudaStream_t s) {
+static int enqueue_stencil(mf_t *m, int from, int R, bool fp64diff, const double *lam, cudaStream_t s,
+                           bool push = false) {
     if (m->use_tma && m->tma_R != R) {
         int rc = build_tma(m, R);
         if (rc) return rc;
@@ -1068,6 +1116,7 @@ static int enqueue_stencil(mf_t *m, int from, int R, bool fp64diff, const double
         p.strip_off = m->tma_main_slot;
         p.strip_bytes = m->tma_strip_bytes;
         p.strip_pitch = m->tma_strip_pitch;
+        p.push = (push && m->tma_push) ? (const PushPiece *)m->d_push.p : nullptr;
         for (int c = 0; c < m->ncomp; ++c) p.lam[0][c] = lam[c];
         CU(launch_stencil_tma(m->dtype, R, fp64diff, m->tma_cpt, p, 0, s));
         return 0;
@@ -1244,10 +1293,20 @@ extern "C" int mf_advance(mf_t *m, const mf_stencil *st, double dt, int nsteps) 
         if ((rc = capture_begin(m))) return rc;
         int body = 0, from = m->cur;
         if (m->timing) body = record(m, 0);
+        const bool push = m->use_tma && m->tma_ok && m->tma_push;
         for (int s = 0; s < nsteps && !body; ++s) {
-            body = enqueue_fill_step(m, from, m->cap);
+            if (push && s > 0) {
+                // the previous stencil launch pushed the face ghosts; fill what is left
+                if (!m->fbtasks_res.empty())
+                    body = launch_fill(m->dtype, level_ptrs(m, from), (const FbTask *)m->d_fbtasks_res.p,
+                                       (int)m->fbtasks_res.size(), 0, m->cap) == cudaSuccess
+                               ? 0
+                               : fail(MF_ECUDA, "fill launch failed");
+            } else {
+                body = enqueue_fill_step(m, from, m->cap);
+            }
             if (!body && m->timing) body = record(m, 2 * s + 1);
-            if (!body) body = enqueue_stencil(m, from, R, fp64diff, lam, m->cap);
+            if (!body) body = enqueue_stencil(m, from, R, fp64diff, lam, m->cap, push);
             if (!body && m->timing) body = record(m, 2 * s + 2);
             from = 1 - from;
         }

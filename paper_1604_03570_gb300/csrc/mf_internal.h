@@ -117,6 +117,15 @@ struct TileStrip {
     int lfab, rfab;
     int lx, ly, lz;
     int rx, ry, rz;
+    int pfirst, pcount;  // this tile's ghost-push pieces
+};
+
+// Ghost push: cells [x0, x0+nx) x [y0, y0+ny) x [z0, z0+nz) of a tile (tile coordinates) are
+// ghost cells of box dfab; dst is the element offset (comp 0) of the piece's first cell there.
+struct PushPiece {
+    long long dst;
+    int x0, y0, z0, nx, ny, nz;
+    int dfab;
 };
 
 struct StencilTmaParams {
@@ -136,6 +145,7 @@ struct StencilTmaParams {
     int pad_;
     void *dst[kMaxLev];
     int *err;                  // set non-zero when a bounded wait expires
+    const PushPiece *push;     // ghost-push pieces (nullptr: no push)
     double lam[kMaxLev][kMaxComp];
 };
 

@@ -144,7 +144,9 @@ __global__ void __launch_bounds__(kTmaThreads) k_stencil_tma(const __grid_consta
 
         TileStrip ts;
         ts.lfab = ts.rfab = -1;
+        ts.pcount = 0;
         if (p.strips) ts = p.strips[w];
+        if (!p.push) ts.pcount = 0;
         auto slot_of = [&](int pl) -> uint32_t { return (seq + (uint32_t)pl) & (uint32_t)(NS - 1); };
         auto issue = [&](int pl) {
             const uint32_t sl = slot_of(pl);
@@ -276,6 +278,24 @@ __global__ void __launch_bounds__(kTmaThreads) k_stencil_tma(const __grid_consta
 #pragma unroll
                     for (int c = 0; c < VX; ++c)
                         if (gx0[j] + c < t.tx) st(op + c, out[c]);
+                }
+                // ghost push: the same values into the neighbour boxes whose ghost faces hold them
+                for (int pi = 0; pi < ts.pcount; ++pi) {
+                    const PushPiece pp = p.push[ts.pfirst + pi];
+                    if (k < pp.z0 || k >= pp.z0 + pp.nz || gy[j] < pp.y0 || gy[j] >= pp.y0 + pp.ny) continue;
+                    const FabInfo &df = p.ftab[pp.dfab];
+                    S *gp = (S *)p.dst[df.level] + pp.dst + t.comp * df.cstride + (long long)(k - pp.z0) * df.plane +
+                            (long long)(gy[j] - pp.y0) * df.px + (gx0[j] - pp.x0);
+                    if (gx0[j] >= pp.x0 && gx0[j] + VX <= pp.x0 + pp.nx && gx0[j] + VX <= t.tx &&
+                        ((uintptr_t)gp & 15) == 0) {
+                        V16<S>::st(gp, out);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < VX; ++c) {
+                            const int x = gx0[j] + c;
+                            if (x >= pp.x0 && x < pp.x0 + pp.nx && x < t.tx) st(gp + c, out[c]);
+                        }
+                    }
                 }
             }
             if (!ok) { abort_flag = 1; atomicOr(p.err, 1); }
