@@ -999,6 +999,7 @@ static int build_tma(mf_t *m, int R) {
     // ghost push: every y/z face region is written by the tiles that compute its source cells;
     // only x faces not served by strips remain for the fill of later steps
     std::vector<PushPiece> pieces;
+    bool push_ok = true;
     {
         std::vector<std::vector<int>> by_src(m->boxes.size());
         for (size_t e = 0; e < m->fb.size(); ++e)
@@ -1029,6 +1030,7 @@ static int build_tma(mf_t *m, int R) {
                 pieces.push_back(pp);
             }
             strips[w].pcount = (int)pieces.size() - strips[w].pfirst;
+            if (strips[w].pcount > kMaxPush) push_ok = false;
         }
         std::vector<char> res(m->fb.size(), 0);
         for (size_t e = 0; e < m->fb.size(); ++e) {
@@ -1055,7 +1057,7 @@ static int build_tma(mf_t *m, int R) {
     m->tma_strip_pitch = strip_pitch;
     m->tma_ok = true;
     m->tma_strips = true;
-    m->tma_push = true;
+    m->tma_push = push_ok;
     return 0;
 }
 

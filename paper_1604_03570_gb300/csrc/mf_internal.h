@@ -103,6 +103,7 @@ struct StencilParams {
 // TMA-staged stencil: per FArrayBox, the shared-memory plane geometry of its tensor map.
 constexpr int kTmaThreads = 256;
 constexpr int kMaxStages = 16;
+constexpr int kMaxPush = 16;  // ghost-push pieces per tile
 
 struct TmaFab {
     int bx, by;   // box of one plane load: bx elements along x (multiple of 16 bytes), by rows

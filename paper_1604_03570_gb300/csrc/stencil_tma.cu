@@ -117,6 +117,12 @@ __global__ void __launch_bounds__(kTmaThreads) k_stencil_tma(const __grid_consta
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bars[kMaxStages];
     __shared__ int abort_flag;
+    struct SPiece {
+        S *base;           // destination of the piece's first cell, this tile's component
+        long long plane;
+        int px, x0, y0, z0, nx, ny, nz, full_z;
+    };
+    __shared__ SPiece spc[kMaxPush];
     unsigned char *slots = (unsigned char *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     const int NS = p.nstages;                       // power of two
     const int tid = threadIdx.x;
@@ -147,6 +153,18 @@ __global__ void __launch_bounds__(kTmaThreads) k_stencil_tma(const __grid_consta
         ts.pcount = 0;
         if (p.strips) ts = p.strips[w];
         if (!p.push) ts.pcount = 0;
+        if (tid < ts.pcount) {  // ghost-push pieces of the tile, resolved once
+            const PushPiece pp = p.push[ts.pfirst + tid];
+            const FabInfo &df = p.ftab[pp.dfab];
+            SPiece sp;
+            sp.base = (S *)p.dst[df.level] + pp.dst + t.comp * df.cstride;
+            sp.plane = df.plane;
+            sp.px = df.px;
+            sp.x0 = pp.x0; sp.y0 = pp.y0; sp.z0 = pp.z0;
+            sp.nx = pp.nx; sp.ny = pp.ny; sp.nz = pp.nz;
+            sp.full_z = pp.z0 == 0 && pp.nz == t.tz;
+            spc[tid] = sp;
+        }
         auto slot_of = [&](int pl) -> uint32_t { return (seq + (uint32_t)pl) & (uint32_t)(NS - 1); };
         auto issue = [&](int pl) {
             const uint32_t sl = slot_of(pl);
@@ -215,6 +233,28 @@ __global__ void __launch_bounds__(kTmaThreads) k_stencil_tma(const __grid_consta
         // planes 0 .. R-1 are no longer needed: refill their slots
         if (tid == 0)
             for (int pl = 0; pl < R && issued < ntot; ++pl) issue(issued++);
+        // push masks per group: pieces spanning the whole tile in z (checked every plane) and
+        // the others (checked only inside their planes)
+        uint32_t pmask_full[GPT], pmask_part[GPT];
+        int kpart_lo = 0x7fffffff, kpart_hi = -1;  // planes where some partial piece applies
+#pragma unroll
+        for (int j = 0; j < GPT; ++j) { pmask_full[j] = 0; pmask_part[j] = 0; }
+        for (int pi = 0; pi < ts.pcount; ++pi) {
+            const SPiece &sp = spc[pi];
+            if (!sp.full_z) {
+                kpart_lo = min(kpart_lo, sp.z0);
+                kpart_hi = max(kpart_hi, sp.z0 + sp.nz - 1);
+            }
+#pragma unroll
+            for (int j = 0; j < GPT; ++j) {
+                const bool hit = act[j] && gy[j] >= sp.y0 && gy[j] < sp.y0 + sp.ny && gx0[j] < sp.x0 + sp.nx &&
+                                 gx0[j] + VX > sp.x0;
+                if (hit) {
+                    if (sp.full_z) pmask_full[j] |= 1u << pi;
+                    else pmask_part[j] |= 1u << pi;
+                }
+            }
+        }
 
         S *dst = (S *)p.dst[f.level] + f.org + t.comp * f.cstride;
         const A lam = (A)p.lam[f.level][t.comp];
@@ -280,20 +320,22 @@ __global__ void __launch_bounds__(kTmaThreads) k_stencil_tma(const __grid_consta
                         if (gx0[j] + c < t.tx) st(op + c, out[c]);
                 }
                 // ghost push: the same values into the neighbour boxes whose ghost faces hold them
-                for (int pi = 0; pi < ts.pcount; ++pi) {
-                    const PushPiece pp = p.push[ts.pfirst + pi];
-                    if (k < pp.z0 || k >= pp.z0 + pp.nz || gy[j] < pp.y0 || gy[j] >= pp.y0 + pp.ny) continue;
-                    const FabInfo &df = p.ftab[pp.dfab];
-                    S *gp = (S *)p.dst[df.level] + pp.dst + t.comp * df.cstride + (long long)(k - pp.z0) * df.plane +
-                            (long long)(gy[j] - pp.y0) * df.px + (gx0[j] - pp.x0);
-                    if (gx0[j] >= pp.x0 && gx0[j] + VX <= pp.x0 + pp.nx && gx0[j] + VX <= t.tx &&
+                uint32_t pm = pmask_full[j] | ((k >= kpart_lo && k <= kpart_hi) ? pmask_part[j] : 0u);
+                while (pm) {
+                    const int pi = __ffs(pm) - 1;
+                    pm &= pm - 1;
+                    const SPiece &sp = spc[pi];
+                    if (k < sp.z0 || k >= sp.z0 + sp.nz) continue;
+                    S *gp = sp.base + (long long)(k - sp.z0) * sp.plane + (long long)(gy[j] - sp.y0) * sp.px +
+                            (gx0[j] - sp.x0);
+                    if (gx0[j] >= sp.x0 && gx0[j] + VX <= sp.x0 + sp.nx && gx0[j] + VX <= t.tx &&
                         ((uintptr_t)gp & 15) == 0) {
                         V16<S>::st(gp, out);
                     } else {
 #pragma unroll
                         for (int c = 0; c < VX; ++c) {
                             const int x = gx0[j] + c;
-                            if (x >= pp.x0 && x < pp.x0 + pp.nx && x < t.tx) st(gp + c, out[c]);
+                            if (x >= sp.x0 && x < sp.x0 + sp.nx && x < t.tx) st(gp + c, out[c]);
                         }
                     }
                 }
