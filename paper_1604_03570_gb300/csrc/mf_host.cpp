@@ -229,6 +229,7 @@ struct mf {
     int tma_cpt = 1, tma_slot = 0, tma_ns = 0;
     int tma_main_slot = 0, tma_strip_rows = 0, tma_strip_bytes = 0, tma_strip_pitch = 0;
     bool use_tma = true;
+    int cta_threads = 256;    // TMA stencil CTA size (128 or 256), picked by the autotuner
     double *h_sum = nullptr;       // pinned
     size_t tile_capacity = 0;
     std::map<std::string, std::unique_ptr<GraphExec>> graphs;
@@ -423,7 +424,7 @@ static std::vector<std::array<int, 3>> tile_candidates(const mf_t *m) {
     for (auto &b : m->boxes) for (int d = 0; d < 3; ++d) mx[d] = std::max(mx[d], b.len(d));
     std::vector<std::array<int, 3>> c;
     const int xs[] = {0, 64, 32};
-    const int ys[] = {4, 8, 16, 0};
+    const int ys[] = {4, 8, 16, 32, 0};
     const int zs[] = {8, 16, 32, 0};
     for (int x : xs) for (int y : ys) for (int z : zs) {
         std::array<int, 3> t = {x, y, z};
@@ -870,7 +871,8 @@ static bool tma_geometry(mf_t *m, int R, std::vector<TmaFab> &tf, int &slot_byte
         if (tf[b].bx > 256 || tf[b].by > 256) return false;
         maxplane = std::max(maxplane, tf[b].bx * tf[b].by * S);
     }
-    gpt = maxgroups <= kTmaThreads ? 1 : maxgroups <= 2 * kTmaThreads ? 2 : maxgroups <= 4 * kTmaThreads ? 4 : 0;
+    const int nt = m->cta_threads;
+    gpt = maxgroups <= nt ? 1 : maxgroups <= 2 * nt ? 2 : maxgroups <= 4 * nt ? 4 : 0;
     if (gpt == 0 || (R == 4 && gpt > 2)) return false;
     slot_bytes = (maxplane + 127) / 128 * 128;
     return true;
@@ -1120,7 +1122,7 @@ static int enqueue_stencil(mf_t *m, int from, int R, bool fp64diff, const double
         p.strip_pitch = m->tma_strip_pitch;
         p.push = (push && m->tma_push) ? (const PushPiece *)m->d_push.p : nullptr;
         for (int c = 0; c < m->ncomp; ++c) p.lam[0][c] = lam[c];
-        CU(launch_stencil_tma(m->dtype, R, fp64diff, m->tma_cpt, p, 0, s));
+        CU(launch_stencil_tma(m->dtype, R, fp64diff, m->cta_threads, m->tma_cpt, p, 0, s));
         return 0;
     }
     StencilParams p = stencil_params(m, from, lam);
@@ -1164,23 +1166,29 @@ static int autotune(mf_t *m, int R, bool fp64diff, const double *lam) {
     CU(cudaEventCreate(&e1));
     float best = 1e30f;
     std::array<int, 3> best_t = {0, 0, 0};
-    for (auto &t : cands) {
-        int rc = set_tiles(m, t.data());
-        if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
-        // warm-up, then 3 timed launches
-        if ((rc = enqueue_stencil(m, m->cur, R, fp64diff, lam, m->stream))) return rc;
-        CU(cudaEventRecord(e0, m->stream));
-        for (int i = 0; i < 3; ++i)
+    int best_nt = 256;
+    const int nts[2] = {128, 256};
+    for (auto &t : cands)
+        for (int nt : nts) {
+            if (!m->use_tma && nt != 256) continue;
+            m->cta_threads = nt;
+            int rc = set_tiles(m, t.data());
+            if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
+            // warm-up (also encodes the tensor maps), then 3 timed launches
             if ((rc = enqueue_stencil(m, m->cur, R, fp64diff, lam, m->stream))) return rc;
-        CU(cudaEventRecord(e1, m->stream));
-        CU(cudaEventSynchronize(e1));
-        float ms = 0;
-        CU(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) { best = ms; best_t = t; }
-    }
+            CU(cudaEventRecord(e0, m->stream));
+            for (int i = 0; i < 3; ++i)
+                if ((rc = enqueue_stencil(m, m->cur, R, fp64diff, lam, m->stream))) return rc;
+            CU(cudaEventRecord(e1, m->stream));
+            CU(cudaEventSynchronize(e1));
+            float ms = 0;
+            CU(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) { best = ms; best_t = t; best_nt = nt; }
+        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     m->tile_auto = false;
+    m->cta_threads = best_nt;
     return set_tiles(m, best_t.data());
 }
 

@@ -110,8 +110,8 @@ template <> struct V16<__nv_bfloat16> {
     }
 };
 
-template <typename S, typename A, int R, int GPT>
-__global__ void __launch_bounds__(kTmaThreads) k_stencil_tma(const __grid_constant__ StencilTmaParams p) {
+template <typename S, typename A, int R, int GPT, int NT>
+__global__ void __launch_bounds__(NT) k_stencil_tma(const __grid_constant__ StencilTmaParams p) {
     constexpr int VX = V16<S>::n;                   // cells per group: one 16-byte vector
     constexpr int XH = ((R + VX - 1) / VX) * VX;    // x halo loaded on each side (16-byte multiple)
     extern __shared__ unsigned char smem_raw[];
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(kTmaThreads) k_stencil_tma(const __grid_consta
         bool act[GPT];
 #pragma unroll
         for (int j = 0; j < GPT; ++j) {
-            const int gi = tid + j * kTmaThreads;
+            const int gi = tid + j * NT;
             act[j] = gi < ngroups;
             gx0[j] = act[j] ? (gi % ngx) * VX : 0;
             gy[j] = act[j] ? gi / ngx : 0;
@@ -264,9 +264,11 @@ __global__ void __launch_bounds__(kTmaThreads) k_stencil_tma(const __grid_consta
             const S *newp = plane_ptr(k + 2 * R);
             const S *cp = plane_ptr(k + R);
             const long long zoff = (long long)(t.z0 + k) * f.plane;
+            const int lane = tid & 31;
 #pragma unroll
             for (int j = 0; j < GPT; ++j) {
-                if (!act[j]) continue;
+                // every lane runs the body (the x halo is exchanged by shuffles); inactive groups
+                // compute on a valid row and store nothing
                 {
                     A v[VX];
                     V16<S>::ld(newp + soff[j], v);
@@ -279,13 +281,22 @@ __global__ void __launch_bounds__(kTmaThreads) k_stencil_tma(const __grid_consta
                 const S *cc = cp + soff[j];
                 const S *ls = (const S *)((const unsigned char *)cp + p.strip_off) + gy[j] * XH + XH;
                 const S *rs = (const S *)((const unsigned char *)cp + p.strip_off + p.strip_pitch) + gy[j] * XH;
+                const int gxi = gx0[j] / VX;
 #pragma unroll
                 for (int i = 0; i < R; ++i) {
-                    // cells x0 + gx0 - R + i (left) and x0 + gx0 + VX + i (right) of the box: outside
-                    // the box they come from the neighbour strips when the tile has them
+                    // cells x0 + gx0 - R + i (left) and x0 + gx0 + VX + i (right) of the box: from the
+                    // lane holding them when it is in the same row of the tile, else from shared
+                    // memory (ghost columns, or the neighbour's strip outside the box)
+                    const int dl = (R - i + VX - 1) / VX, cl = VX * dl - (R - i);
+                    const int dr = (VX + i) / VX, cr = VX + i - VX * dr;
+                    const A vl = __shfl_up_sync(0xffffffffu, q[j][cl][R], dl);
+                    const A vr = __shfl_down_sync(0xffffffffu, q[j][cr][R], dr);
                     const int xl = t.x0 + gx0[j] - R + i, xr = t.x0 + gx0[j] + VX + i;
-                    wx[i] = ld_smem<S, A>((xl < 0 && ts.lfab >= 0) ? ls + xl : cc - R + i);
-                    wx[R + VX + i] = ld_smem<S, A>((xr >= f.n[0] && ts.rfab >= 0) ? rs + (xr - f.n[0]) : cc + VX + i);
+                    if (lane >= dl && gxi >= dl) wx[i] = vl;
+                    else wx[i] = ld_smem<S, A>((xl < 0 && ts.lfab >= 0) ? ls + xl : cc - R + i);
+                    if (lane + dr < 32 && gxi + dr < ngx && xr < f.n[0]) wx[R + VX + i] = vr;
+                    else wx[R + VX + i] = ld_smem<S, A>((xr >= f.n[0] && ts.rfab >= 0) ? rs + (xr - f.n[0])
+                                                                                       : cc + VX + i);
                 }
 #pragma unroll
                 for (int c = 0; c < VX; ++c) wx[R + c] = q[j][c][R];
@@ -311,6 +322,7 @@ __global__ void __launch_bounds__(kTmaThreads) k_stencil_tma(const __grid_consta
 #pragma unroll
                     for (int i = 0; i < 2 * R; ++i) q[j][c][i] = q[j][c][i + 1];
                 }
+                if (!act[j]) continue;
                 S *op = dst + zoff + (long long)(t.y0 + gy[j]) * f.px + (t.x0 + gx0[j]);
                 if (vec_store && gx0[j] + VX <= t.tx) {
                     V16<S>::st(op, out);
@@ -356,10 +368,10 @@ __global__ void __launch_bounds__(kTmaThreads) k_stencil_tma(const __grid_consta
     }
 }
 
-template <typename S, typename A, int R, int CPT>
+template <typename S, typename A, int R, int GPT, int NT>
 static cudaError_t tma_t(const StencilTmaParams &p, int grid, cudaStream_t s) {
     const int smem = p.nstages * p.slot_bytes + 128;
-    auto kern = k_stencil_tma<S, A, R, CPT>;
+    auto kern = k_stencil_tma<S, A, R, GPT, NT>;
     static int configured = 0;
     if (smem > configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -369,49 +381,56 @@ static cudaError_t tma_t(const StencilTmaParams &p, int grid, cudaStream_t s) {
     int g = grid;
     if (g <= 0) {
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTmaThreads, smem) != cudaSuccess ||
-            per_sm < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem) != cudaSuccess || per_sm < 1)
             per_sm = 1;
         long long gg = (long long)per_sm * sm_count();
         g = (int)(gg < p.ntiles ? gg : p.ntiles);
         if (g < 1) g = 1;
     }
-    kern<<<g, kTmaThreads, smem, s>>>(p);
+    kern<<<g, NT, smem, s>>>(p);
     return cudaGetLastError();
 }
 
-template <typename S, typename A, int R>
-static cudaError_t tma_c(int cpt, const StencilTmaParams &p, int grid, cudaStream_t s) {
-    switch (cpt) {
-        case 1: return tma_t<S, A, R, 1>(p, grid, s);
-        case 2: return tma_t<S, A, R, 2>(p, grid, s);
+template <typename S, typename A, int R, int NT>
+static cudaError_t tma_c(int gpt, const StencilTmaParams &p, int grid, cudaStream_t s) {
+    switch (gpt) {
+        case 1: return tma_t<S, A, R, 1, NT>(p, grid, s);
+        case 2: return tma_t<S, A, R, 2, NT>(p, grid, s);
         case 4:
-            if constexpr (R < 4) return tma_t<S, A, R, 4>(p, grid, s);  // radius 4 keeps <= 2 groups per thread
+            if constexpr (R < 4) return tma_t<S, A, R, 4, NT>(p, grid, s);  // radius 4 keeps <= 2 groups per thread
             break;
     }
     return cudaErrorInvalidValue;
 }
 
+template <typename S, typename A, int R>
+static cudaError_t tma_n(int nt, int gpt, const StencilTmaParams &p, int grid, cudaStream_t s) {
+    if (nt == 128) return tma_c<S, A, R, 128>(gpt, p, grid, s);
+    if (nt == 256) return tma_c<S, A, R, 256>(gpt, p, grid, s);
+    return cudaErrorInvalidValue;
+}
+
 template <typename S, typename A>
-static cudaError_t tma_r(int R, int cpt, const StencilTmaParams &p, int grid, cudaStream_t s) {
+static cudaError_t tma_r(int R, int nt, int gpt, const StencilTmaParams &p, int grid, cudaStream_t s) {
     switch (R) {
-        case 1: return tma_c<S, A, 1>(cpt, p, grid, s);
-        case 2: return tma_c<S, A, 2>(cpt, p, grid, s);
-        case 4: return tma_c<S, A, 4>(cpt, p, grid, s);
+        case 1: return tma_n<S, A, 1>(nt, gpt, p, grid, s);
+        case 2: return tma_n<S, A, 2>(nt, gpt, p, grid, s);
+        case 4: return tma_n<S, A, 4>(nt, gpt, p, grid, s);
     }
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_stencil_tma(int dtype, int R, bool fp64diff, int cpt, const StencilTmaParams &p, int grid,
+cudaError_t launch_stencil_tma(int dtype, int R, bool fp64diff, int nt, int gpt, const StencilTmaParams &p, int grid,
                                cudaStream_t s) {
     if (p.ntiles == 0) return cudaSuccess;
     if (p.nstages > kMaxStages || p.nstages < R + 2 || (p.nstages & (p.nstages - 1))) return cudaErrorInvalidValue;
     switch (dtype) {
-        case F64: return tma_r<double, double>(R, cpt, p, grid, s);
-        case F32: return fp64diff ? tma_r<float, double>(R, cpt, p, grid, s) : tma_r<float, float>(R, cpt, p, grid, s);
+        case F64: return tma_r<double, double>(R, nt, gpt, p, grid, s);
+        case F32:
+            return fp64diff ? tma_r<float, double>(R, nt, gpt, p, grid, s) : tma_r<float, float>(R, nt, gpt, p, grid, s);
         case BF16:
-            return fp64diff ? tma_r<__nv_bfloat16, double>(R, cpt, p, grid, s)
-                            : tma_r<__nv_bfloat16, float>(R, cpt, p, grid, s);
+            return fp64diff ? tma_r<__nv_bfloat16, double>(R, nt, gpt, p, grid, s)
+                            : tma_r<__nv_bfloat16, float>(R, nt, gpt, p, grid, s);
     }
     return cudaErrorInvalidValue;
 }
