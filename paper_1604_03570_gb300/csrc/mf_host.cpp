@@ -671,7 +671,15 @@ extern "C" int mf_set_tile(mf_t *m, const int tile[3]) {
     for (int d = 0; d < 3; ++d)
         if (tile[d] > 32767) return fail(MF_EINVAL, "tile size too large");
     m->tile_auto = false;
-    return set_tiles(m, tile);
+    int rc = set_tiles(m, tile);
+    if (rc) return rc;
+    // CTA size for a user tile: the smaller one when a tile has at most 128 16-byte groups
+    int maxgroups = 0;
+    const int A = 16 / m->esize;
+    for (auto &t : m->tiles) maxgroups = std::max(maxgroups, ((int)t.tx + A - 1) / A * (int)t.ty);
+    m->cta_threads = maxgroups <= 128 ? 128 : 256;
+    m->tma_R = 0;
+    return 0;
 }
 
 extern "C" int mf_set_kernel(mf_t *m, int variant) {

@@ -256,52 +256,52 @@ __global__ void __launch_bounds__(NT) k_stencil_tma(const __grid_constant__ Sten
             }
         }
 
-        S *dst = (S *)p.dst[f.level] + f.org + t.comp * f.cstride;
         const A lam = (A)p.lam[f.level][t.comp];
-        const bool vec_store = (t.x0 % VX) == 0;
+        // per group, fixed for the tile: output pointer (advanced one plane per step), whether
+        // the 16-byte store is whole, and the shared-memory element offset (from the slot base)
+        // of every x-halo cell: the loaded row, or the neighbour strip outside the box
+        S *op[GPT];
+        bool vst[GPT];
+        int hl[GPT][R], hr[GPT][R];
+        {
+            S *dst = (S *)p.dst[f.level] + f.org + t.comp * f.cstride + (long long)t.z0 * f.plane;
+            const int lso = p.strip_off / (int)sizeof(S), rso = (p.strip_off + p.strip_pitch) / (int)sizeof(S);
+#pragma unroll
+            for (int j = 0; j < GPT; ++j) {
+                op[j] = dst + (long long)(t.y0 + gy[j]) * f.px + (t.x0 + gx0[j]);
+                vst[j] = (t.x0 % VX) == 0 && gx0[j] + VX <= t.tx;
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    const int xl = t.x0 + gx0[j] - R + i, xr = t.x0 + gx0[j] + VX + i;
+                    hl[j][i] = (xl < 0 && ts.lfab >= 0) ? lso + gy[j] * XH + XH + xl : soff[j] - R + i;
+                    hr[j][i] = (xr >= f.n[0] && ts.rfab >= 0) ? rso + gy[j] * XH + (xr - f.n[0]) : soff[j] + VX + i;
+                }
+            }
+        }
         for (int k = 0; k < t.tz; ++k) {
             ok = wait_plane(k + 2 * R);
             const S *newp = plane_ptr(k + 2 * R);
             const S *cp = plane_ptr(k + R);
-            const long long zoff = (long long)(t.z0 + k) * f.plane;
-            const int lane = tid & 31;
 #pragma unroll
             for (int j = 0; j < GPT; ++j) {
-                // every lane runs the body (the x halo is exchanged by shuffles); inactive groups
-                // compute on a valid row and store nothing
                 {
                     A v[VX];
                     V16<S>::ld(newp + soff[j], v);
 #pragma unroll
                     for (int c = 0; c < VX; ++c) q[j][c][2 * R] = v[c];
                 }
-                // x window: w[i] = u(x0 - R + i), i = 0 .. VX + 2R - 1; at the box edge the halo
-                // comes from the neighbour's strip when the tile has one
+                // x window: w[i] = u(x0 - R + i), i = 0 .. VX + 2R - 1
                 A wx[VX + 2 * R];
-                const S *cc = cp + soff[j];
-                const S *ls = (const S *)((const unsigned char *)cp + p.strip_off) + gy[j] * XH + XH;
-                const S *rs = (const S *)((const unsigned char *)cp + p.strip_off + p.strip_pitch) + gy[j] * XH;
-                const int gxi = gx0[j] / VX;
 #pragma unroll
                 for (int i = 0; i < R; ++i) {
-                    // cells x0 + gx0 - R + i (left) and x0 + gx0 + VX + i (right) of the box: from the
-                    // lane holding them when it is in the same row of the tile, else from shared
-                    // memory (ghost columns, or the neighbour's strip outside the box)
-                    const int dl = (R - i + VX - 1) / VX, cl = VX * dl - (R - i);
-                    const int dr = (VX + i) / VX, cr = VX + i - VX * dr;
-                    const A vl = __shfl_up_sync(0xffffffffu, q[j][cl][R], dl);
-                    const A vr = __shfl_down_sync(0xffffffffu, q[j][cr][R], dr);
-                    const int xl = t.x0 + gx0[j] - R + i, xr = t.x0 + gx0[j] + VX + i;
-                    if (lane >= dl && gxi >= dl) wx[i] = vl;
-                    else wx[i] = ld_smem<S, A>((xl < 0 && ts.lfab >= 0) ? ls + xl : cc - R + i);
-                    if (lane + dr < 32 && gxi + dr < ngx && xr < f.n[0]) wx[R + VX + i] = vr;
-                    else wx[R + VX + i] = ld_smem<S, A>((xr >= f.n[0] && ts.rfab >= 0) ? rs + (xr - f.n[0])
-                                                                                       : cc + VX + i);
+                    wx[i] = ld_smem<S, A>(cp + hl[j][i]);
+                    wx[R + VX + i] = ld_smem<S, A>(cp + hr[j][i]);
                 }
 #pragma unroll
                 for (int c = 0; c < VX; ++c) wx[R + c] = q[j][c][R];
                 // y rows: ry[m][c] = u(x + c, y - R + m), m != R
                 A ry[2 * R + 1][VX];
+                const S *cc = cp + soff[j];
 #pragma unroll
                 for (int m = 0; m < 2 * R + 1; ++m) {
                     if (m == R) continue;
@@ -322,14 +322,15 @@ __global__ void __launch_bounds__(NT) k_stencil_tma(const __grid_constant__ Sten
 #pragma unroll
                     for (int i = 0; i < 2 * R; ++i) q[j][c][i] = q[j][c][i + 1];
                 }
+                S *o = op[j];
+                op[j] += f.plane;
                 if (!act[j]) continue;
-                S *op = dst + zoff + (long long)(t.y0 + gy[j]) * f.px + (t.x0 + gx0[j]);
-                if (vec_store && gx0[j] + VX <= t.tx) {
-                    V16<S>::st(op, out);
+                if (vst[j]) {
+                    V16<S>::st(o, out);
                 } else {
 #pragma unroll
                     for (int c = 0; c < VX; ++c)
-                        if (gx0[j] + c < t.tx) st(op + c, out[c]);
+                        if (gx0[j] + c < t.tx) st(o + c, out[c]);
                 }
                 // ghost push: the same values into the neighbour boxes whose ghost faces hold them
                 uint32_t pm = pmask_full[j] | ((k >= kpart_lo && k <= kpart_hi) ? pmask_part[j] : 0u);
