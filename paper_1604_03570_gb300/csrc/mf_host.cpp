@@ -260,11 +260,13 @@ static void build_layout(mf_t *m) {
     for (auto &b : m->boxes) {
         FabInfo f{};
         for (int d = 0; d < 3; ++d) { f.n[d] = b.len(d); f.lo[d] = b.lo[d]; }
-        // valid x = 0 of every row sits on a 16-byte boundary: vector loads and stores of the
-        // valid cells are aligned, and a TMA plane load that starts a whole 16-byte chunk
-        // left of a tile is aligned too
-        const int fpad = (A - g % A) % A;
-        f.px = (int)(((long long)fpad + f.n[0] + 2 * g + A - 1) / A * A);
+        // valid x = 0 of every row starts a 128-byte line and the row pitch is a whole number of
+        // lines: the valid cells of a row are whole sectors (no partial-sector writes, no ghost
+        // sector fetched with them), and a TMA plane load that starts a 16-byte chunk left of a
+        // tile is aligned too
+        const int AL = 128 / S;
+        const int fpad = (AL - g % AL) % AL;
+        f.px = (int)(((long long)fpad + f.n[0] + 2 * g + AL - 1) / AL * AL);
         const long long py = f.n[1] + 2 * g, nzg = f.n[2] + 2 * g;
         f.plane = (long long)f.px * py;
         f.cstride = f.plane * nzg;
@@ -856,14 +858,22 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // Plane geometry of every FArrayBox for the current tile shape and radius R; false when a
 // box needs a plane wider than the TMA box limit (256 per dimension) or more cells per
 // thread than the kernel keeps in registers.
-static bool tma_geometry(mf_t *m, int R, std::vector<TmaFab> &tf, int &slot_bytes, int &gpt) {
-    const int S = m->esize, A = 16 / S, g = m->ngrow;
+static bool tma_geometry(mf_t *m, int R, const std::vector<TileStrip> &st, std::vector<TmaFab> &tf, int &slot_bytes,
+                         int &gpt) {
+    const int S = m->esize, A = 16 / S, g = m->ngrow, AL = 128 / S;
     const int XH = (R + A - 1) / A * A;  // x halo columns loaded on each side
     tf.assign(m->fabs.size(), TmaFab{});
     int maxplane = 0, maxgroups = 0;
     for (auto &t : m->tiles) {
         if (t.x0 % A) return false;  // a plane load must start on a 16-byte boundary
         maxgroups = std::max(maxgroups, ((int)t.tx + A - 1) / A * (int)t.ty);
+    }
+    std::vector<char> narrow(m->fabs.size(), 1);
+    for (size_t w = 0; w < m->tiles.size(); ++w) {
+        const Tile &t = m->tiles[w];
+        // only the valid columns are loaded when every tile spans the box and takes both x
+        // halos from the neighbours' strips
+        if (!(t.x0 == 0 && t.tx == m->fabs[t.fab].n[0] && st[w].lfab >= 0 && st[w].rfab >= 0)) narrow[t.fab] = 0;
     }
     for (size_t b = 0; b < m->fabs.size(); ++b) {
         int tx = 1, ty = 1;
@@ -872,10 +882,11 @@ static bool tma_geometry(mf_t *m, int R, std::vector<TmaFab> &tf, int &slot_byte
             tx = std::max(tx, (int)t.tx);
             ty = std::max(ty, (int)t.ty);
         }
-        tf[b].bx = XH + (tx + A - 1) / A * A + XH;
+        tf[b].xs = narrow[b] ? 0 : XH;
+        tf[b].bx = tf[b].xs + (tx + A - 1) / A * A + tf[b].xs;
         tf[b].by = ty + 2 * R;
         tf[b].ngrow = g;
-        tf[b].xv = (g + A - 1) / A * A;  // fpad + g
+        tf[b].xv = (g + AL - 1) / AL * AL;  // fpad + g: row element of valid x = 0
         if (tf[b].bx > 256 || tf[b].by > 256) return false;
         maxplane = std::max(maxplane, tf[b].bx * tf[b].by * S);
     }
@@ -932,7 +943,8 @@ static void find_strips(mf_t *m, int R, std::vector<TileStrip> &st, std::vector<
                 continue;
             }
             const Box &Ab = m->boxes[owner];
-            const int xvA = (g + A - 1) / A * A;
+            const int AL = 128 / S;
+            const int xvA = (g + AL - 1) / AL * AL;
             const int x = side == 0 ? xvA + Ab.len(0) - XH : xvA;
             const int y = g + q.lo[1] - Ab.lo[1], z = g + q.lo[2] - Ab.lo[2];
             if (side == 0) { st[w].lfab = owner; st[w].lx = x; st[w].ly = y; st[w].lz = z; }
@@ -953,9 +965,6 @@ static int build_tma(mf_t *m, int R) {
     m->tma_push = false;
     m->tma_R = R;
     if (!m->use_tma) return 0;
-    std::vector<TmaFab> tf;
-    int main_slot = 0, gpt = 0;
-    if (!tma_geometry(m, R, tf, main_slot, gpt)) return 0;
     const int S = m->esize, A = 16 / S;
     const int XH = (R + A - 1) / A * A;
     int srows = 1;
@@ -963,6 +972,9 @@ static int build_tma(mf_t *m, int R) {
     std::vector<TileStrip> strips;
     std::vector<char> served;
     find_strips(m, R, strips, served);
+    std::vector<TmaFab> tf;
+    int main_slot = 0, gpt = 0;
+    if (!tma_geometry(m, R, strips, tf, main_slot, gpt)) return 0;
     const int strip_bytes = XH * srows * S;
     const int strip_pitch = (strip_bytes + 127) / 128 * 128;
     const int slot = main_slot + 2 * strip_pitch;

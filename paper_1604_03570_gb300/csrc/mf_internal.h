@@ -108,7 +108,9 @@ constexpr int kMaxPush = 16;  // ghost-push pieces per tile
 struct TmaFab {
     int bx, by;   // box of one plane load: bx elements along x (multiple of 16 bytes), by rows
     int ngrow;
-    int xv;       // row element of valid x = 0 (16-byte aligned)
+    int xv;       // row element of valid x = 0 (128-byte aligned)
+    int xs;       // columns loaded left of the tile (0 when both x halos come from strips)
+    int pad_;
 };
 
 // x halo of a tile taken straight from the neighbouring box (its valid cells), or -1 when

@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(NT) k_stencil_tma(const __grid_constant__ Sten
         const int bx = tf.bx;                       // smem row length (elements)
         const int ntot = t.tz + 2 * R;              // planes of this tile, halo included
         const uint32_t plane_bytes = (uint32_t)(tf.bx * tf.by * (int)sizeof(S));
-        const int xcoord = tf.xv + t.x0 - XH;       // 16-byte aligned row element of the first loaded column
+        const int xcoord = tf.xv + t.x0 - tf.xs;    // 16-byte aligned row element of the first loaded column
         const int ycoord = tf.ngrow + t.y0 - R, zcoord = tf.ngrow + t.z0 - R;
 
         TileStrip ts;
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(NT) k_stencil_tma(const __grid_constant__ Sten
             act[j] = gi < ngroups;
             gx0[j] = act[j] ? (gi % ngx) * VX : 0;
             gy[j] = act[j] ? gi / ngx : 0;
-            soff[j] = (gy[j] + R) * bx + XH + gx0[j];  // smem offset of the group's first cell
+            soff[j] = (gy[j] + R) * bx + tf.xs + gx0[j];  // smem offset of the group's first cell
         }
         A q[GPT][VX][2 * R + 1];  // z queue per cell: q[..][..][i] = u(z - R + i)
         A fzm[GPT][VX];
