@@ -227,7 +227,7 @@ struct mf {
     int tma_R = 0;            // radius the maps were encoded for (0 = none)
     bool tma_ok = false;      // current tile shape fits the TMA kernel
     int tma_cpt = 1, tma_slot = 0, tma_ns = 0;
-    int tma_main_slot = 0, tma_strip_rows = 0, tma_strip_bytes = 0, tma_strip_pitch = 0;
+    int tma_main_slot = 0, tma_strip_rows = 0, tma_strip_bytes = 0, tma_strip_pitch = 0, tma_strip_w = 0;
     bool use_tma = true;
     int cta_threads = 256;    // TMA stencil CTA size (128 or 256), picked by the autotuner
     double *h_sum = nullptr;       // pinned
@@ -260,13 +260,13 @@ static void build_layout(mf_t *m) {
     for (auto &b : m->boxes) {
         FabInfo f{};
         for (int d = 0; d < 3; ++d) { f.n[d] = b.len(d); f.lo[d] = b.lo[d]; }
-        // valid x = 0 of every row starts a 128-byte line and the row pitch is a whole number of
-        // lines: the valid cells of a row are whole sectors (no partial-sector writes, no ghost
-        // sector fetched with them), and a TMA plane load that starts a 16-byte chunk left of a
-        // tile is aligned too
-        const int AL = 128 / S;
-        const int fpad = (AL - g % AL) % AL;
-        f.px = (int)(((long long)fpad + f.n[0] + 2 * g + AL - 1) / AL * AL);
+        // a row starts at its first ghost cell (x = -g) on a 32-byte sector boundary and its pitch
+        // is a whole number of sectors: rows lie back to back with little padding (DRAM pages
+        // stay dense), a whole-row TMA load starts aligned, and whole rows are written in whole
+        // sectors
+        const int AS = 32 / S;
+        const int fpad = 0;
+        f.px = (int)(((long long)f.n[0] + 2 * g + AS - 1) / AS * AS);
         const long long py = f.n[1] + 2 * g, nzg = f.n[2] + 2 * g;
         f.plane = (long long)f.px * py;
         f.cstride = f.plane * nzg;
@@ -858,35 +858,22 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // Plane geometry of every FArrayBox for the current tile shape and radius R; false when a
 // box needs a plane wider than the TMA box limit (256 per dimension) or more cells per
 // thread than the kernel keeps in registers.
-static bool tma_geometry(mf_t *m, int R, const std::vector<TileStrip> &st, std::vector<TmaFab> &tf, int &slot_bytes,
-                         int &gpt) {
-    const int S = m->esize, A = 16 / S, g = m->ngrow, AL = 128 / S;
-    const int XH = (R + A - 1) / A * A;  // x halo columns loaded on each side
+static bool tma_geometry(mf_t *m, int R, std::vector<TmaFab> &tf, int &slot_bytes, int &gpt) {
+    const int S = m->esize, A = 16 / S, g = m->ngrow;
     tf.assign(m->fabs.size(), TmaFab{});
     int maxplane = 0, maxgroups = 0;
     for (auto &t : m->tiles) {
-        if (t.x0 % A) return false;  // a plane load must start on a 16-byte boundary
-        maxgroups = std::max(maxgroups, ((int)t.tx + A - 1) / A * (int)t.ty);
-    }
-    std::vector<char> narrow(m->fabs.size(), 1);
-    for (size_t w = 0; w < m->tiles.size(); ++w) {
-        const Tile &t = m->tiles[w];
-        // only the valid columns are loaded when every tile spans the box and takes both x
-        // halos from the neighbours' strips
-        if (!(t.x0 == 0 && t.tx == m->fabs[t.fab].n[0] && st[w].lfab >= 0 && st[w].rfab >= 0)) narrow[t.fab] = 0;
+        // the TMA kernel streams whole rows (x = -g .. n0 + g and padding) of every plane
+        if (t.x0 != 0 || t.tx != m->fabs[t.fab].n[0]) return false;
+        maxgroups = std::max(maxgroups, m->fabs[t.fab].px / A * (int)t.ty);
     }
     for (size_t b = 0; b < m->fabs.size(); ++b) {
-        int tx = 1, ty = 1;
-        for (auto &t : m->tiles) {
-            if (t.fab != (int)b || t.comp != 0) continue;
-            tx = std::max(tx, (int)t.tx);
-            ty = std::max(ty, (int)t.ty);
-        }
-        tf[b].xs = narrow[b] ? 0 : XH;
-        tf[b].bx = tf[b].xs + (tx + A - 1) / A * A + tf[b].xs;
+        int ty = 1;
+        for (auto &t : m->tiles)
+            if (t.fab == (int)b && t.comp == 0) ty = std::max(ty, (int)t.ty);
+        tf[b].bx = m->fabs[b].px;
         tf[b].by = ty + 2 * R;
         tf[b].ngrow = g;
-        tf[b].xv = (g + AL - 1) / AL * AL;  // fpad + g: row element of valid x = 0
         if (tf[b].bx > 256 || tf[b].by > 256) return false;
         maxplane = std::max(maxplane, tf[b].bx * tf[b].by * S);
     }
@@ -899,12 +886,11 @@ static bool tma_geometry(mf_t *m, int R, const std::vector<TileStrip> &st, std::
 
 // x-halo strips: for a tile whose x halo leaves its box on the low (high) side, the box
 // owning the column just outside that face over all the tile's rows and planes, when one box
-// owns all of it.  The strip holds that box's XH valid columns next to the face.
+// owns all of it.  The strip holds that box's R valid cells next to the face.
 static void find_strips(mf_t *m, int R, std::vector<TileStrip> &st, std::vector<char> &served) {
     const int S = m->esize, A = 16 / S, g = m->ngrow;
-    const int XH = (R + A - 1) / A * A;
     const int nb = (int)m->boxes.size();
-    st.assign(m->tiles.size(), TileStrip{-1, -1, 0, 0, 0, 0, 0, 0});
+    st.assign(m->tiles.size(), TileStrip{-1, -1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0});
     // served[2b + side]: every tile on that face pulls its halo from a neighbour
     served.assign(2 * (size_t)nb, 1);
     std::vector<char> touched(2 * (size_t)nb, 0);
@@ -937,18 +923,24 @@ static void find_strips(mf_t *m, int R, std::vector<TileStrip> &st, std::vector<
                 for (int d = 0; d < 3; ++d) in = in && Ab.lo[d] <= q.lo[d] && q.hi[d] <= Ab.hi[d];
                 if (in) { owner = a; break; }
             }
-            const bool ok = owner >= 0 && m->boxes[owner].len(0) >= XH && m->boxes[owner].len(0) % A == 0;
+            const bool ok = owner >= 0 && m->boxes[owner].len(0) >= R;
             if (!ok) {
                 served[2 * t.fab + side] = 0;
                 continue;
             }
             const Box &Ab = m->boxes[owner];
-            const int AL = 128 / S;
-            const int xvA = (g + AL - 1) / AL * AL;
-            const int x = side == 0 ? xvA + Ab.len(0) - XH : xvA;
+            const int nA = Ab.len(0);
+            // strip: XW elements of the owner's rows, starting 16-byte aligned at or before the R
+            // cells next to the face (row element of cell x is g + x)
+            const int start = side == 0 ? (g + nA - R) / A * A : g / A * A;
             const int y = g + q.lo[1] - Ab.lo[1], z = g + q.lo[2] - Ab.lo[2];
-            if (side == 0) { st[w].lfab = owner; st[w].lx = x; st[w].ly = y; st[w].lz = z; }
-            else { st[w].rfab = owner; st[w].rx = x; st[w].ry = y; st[w].rz = z; }
+            if (side == 0) {
+                st[w].lfab = owner; st[w].lx = start; st[w].ly = y; st[w].lz = z;
+                st[w].lidx0 = g + nA - start;
+            } else {
+                st[w].rfab = owner; st[w].rx = start; st[w].ry = y; st[w].rz = z;
+                st[w].ridx0 = g - start;
+            }
         }
     }
     for (size_t i = 0; i < served.size(); ++i) served[i] = served[i] && touched[i];
@@ -966,16 +958,16 @@ static int build_tma(mf_t *m, int R) {
     m->tma_R = R;
     if (!m->use_tma) return 0;
     const int S = m->esize, A = 16 / S;
-    const int XH = (R + A - 1) / A * A;
+    const int XW = (R + A - 1 + A - 1) / A * A;  // strip width: R cells from any 16-byte start
     int srows = 1;
     for (auto &t : m->tiles) srows = std::max(srows, (int)t.ty);
+    std::vector<TmaFab> tf;
+    int main_slot = 0, gpt = 0;
+    if (!tma_geometry(m, R, tf, main_slot, gpt)) return 0;
     std::vector<TileStrip> strips;
     std::vector<char> served;
     find_strips(m, R, strips, served);
-    std::vector<TmaFab> tf;
-    int main_slot = 0, gpt = 0;
-    if (!tma_geometry(m, R, strips, tf, main_slot, gpt)) return 0;
-    const int strip_bytes = XH * srows * S;
+    const int strip_bytes = XW * srows * S;
     const int strip_pitch = (strip_bytes + 127) / 128 * 128;
     const int slot = main_slot + 2 * strip_pitch;
     int ns = R == 4 ? 16 : 8;  // ring slots (power of two)
@@ -996,7 +988,7 @@ static int build_tma(mf_t *m, int R) {
                                   (cuuint64_t)m->ncomp};
             cuuint64_t strides[3] = {(cuuint64_t)f.px * S, (cuuint64_t)f.plane * S, (cuuint64_t)f.cstride * S};
             cuuint32_t box[4] = {(cuuint32_t)tf[b].bx, (cuuint32_t)tf[b].by, 1, 1};
-            cuuint32_t sbox[4] = {(cuuint32_t)XH, (cuuint32_t)srows, 1, 1};
+            cuuint32_t sbox[4] = {(cuuint32_t)XW, (cuuint32_t)srows, 1, 1};
             cuuint32_t estr[4] = {1, 1, 1, 1};
             void *gaddr = (char *)m->level_ptr(which) + (size_t)m->fab_start[b] * S;
             CUresult r = encode(&maps[(size_t)which * nf + b], dt, 4, gaddr, dims, strides, box, estr,
@@ -1047,8 +1039,12 @@ static int build_tma(mf_t *m, int R) {
                 pp.dfab = en.dfab;
                 pp.x0 = lo[0] - tlo[0]; pp.y0 = lo[1] - tlo[1]; pp.z0 = lo[2] - tlo[2];
                 pp.nx = hi[0] - lo[0] + 1; pp.ny = hi[1] - lo[1] + 1; pp.nz = hi[2] - lo[2] + 1;
-                pp.dst = elem_at(m->fabs[en.dfab], cr[0] + (lo[0] - cr[3]), cr[1] + (lo[1] - cr[4]),
-                                 cr[2] + (lo[2] - cr[5]));
+                const int dx = cr[0] + (lo[0] - cr[3]);
+                pp.dst = elem_at(m->fabs[en.dfab], dx, cr[1] + (lo[1] - cr[4]), cr[2] + (lo[2] - cr[5]));
+                // the destination rows are laid out exactly like the tile's rows: whole 16-byte
+                // groups (don't-care values in ghost / padding positions included) may be stored
+                pp.full_row = pp.x0 == 0 && pp.nx == t.tx && dx == m->boxes[en.dfab].lo[0] &&
+                              m->boxes[en.dfab].len(0) == t.tx;
                 pieces.push_back(pp);
             }
             strips[w].pcount = (int)pieces.size() - strips[w].pfirst;
@@ -1077,6 +1073,7 @@ static int build_tma(mf_t *m, int R) {
     m->tma_strip_rows = srows;
     m->tma_strip_bytes = strip_bytes;
     m->tma_strip_pitch = strip_pitch;
+    m->tma_strip_w = XW;
     m->tma_ok = true;
     m->tma_strips = true;
     m->tma_push = push_ok;
@@ -1140,6 +1137,7 @@ static int enqueue_stencil(mf_t *m, int from, int R, bool fp64diff, const double
         p.strip_off = m->tma_main_slot;
         p.strip_bytes = m->tma_strip_bytes;
         p.strip_pitch = m->tma_strip_pitch;
+        p.strip_w = m->tma_strip_w;
         p.push = (push && m->tma_push) ? (const PushPiece *)m->d_push.p : nullptr;
         for (int c = 0; c < m->ncomp; ++c) p.lam[0][c] = lam[c];
         CU(launch_stencil_tma(m->dtype, R, fp64diff, m->cta_threads, m->tma_cpt, p, 0, s));

@@ -106,10 +106,8 @@ constexpr int kMaxStages = 16;
 constexpr int kMaxPush = 16;  // ghost-push pieces per tile
 
 struct TmaFab {
-    int bx, by;   // box of one plane load: bx elements along x (multiple of 16 bytes), by rows
+    int bx, by;   // box of one plane load: the whole row (bx elements from x = -g), by rows
     int ngrow;
-    int xv;       // row element of valid x = 0 (128-byte aligned)
-    int xs;       // columns loaded left of the tile (0 when both x halos come from strips)
     int pad_;
 };
 
@@ -120,6 +118,7 @@ struct TileStrip {
     int lfab, rfab;
     int lx, ly, lz;
     int rx, ry, rz;
+    int lidx0, ridx0;    // strip column of the neighbour cell next to the face (x = -1 and x = n0, plus 1)
     int pfirst, pcount;  // this tile's ghost-push pieces
 };
 
@@ -129,6 +128,8 @@ struct PushPiece {
     long long dst;
     int x0, y0, z0, nx, ny, nz;
     int dfab;
+    int full_row;  // the piece spans the tile's whole row and the destination rows match it
+    int pad_;
 };
 
 struct StencilTmaParams {
@@ -139,6 +140,7 @@ struct StencilTmaParams {
     int strip_off;             // byte offset of the left strip in a slot; right strip follows
     int strip_bytes;           // bytes of one strip load (right strip at strip_off + strip_pitch)
     int strip_pitch;
+    int strip_w;               // elements per strip row
     const TmaFab *tfab;
     const FabInfo *ftab;
     const Tile *tiles;

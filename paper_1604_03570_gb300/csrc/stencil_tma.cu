@@ -112,21 +112,20 @@ template <> struct V16<__nv_bfloat16> {
 
 template <typename S, typename A, int R, int GPT, int NT>
 __global__ void __launch_bounds__(NT) k_stencil_tma(const __grid_constant__ StencilTmaParams p) {
-    constexpr int VX = V16<S>::n;                   // cells per group: one 16-byte vector
-    constexpr int XH = ((R + VX - 1) / VX) * VX;    // x halo loaded on each side (16-byte multiple)
+    constexpr int VX = V16<S>::n;  // cells per group: one 16-byte vector of a row
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bars[kMaxStages];
     __shared__ int abort_flag;
     struct SPiece {
         S *base;           // destination of the piece's first cell, this tile's component
         long long plane;
-        int px, x0, y0, z0, nx, ny, nz, full_z;
+        int px, x0, y0, z0, nx, ny, nz, full_z, full_row;
     };
     __shared__ SPiece spc[kMaxPush];
     unsigned char *slots = (unsigned char *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
-    const int NS = p.nstages;                       // power of two
+    const int NS = p.nstages;  // power of two
     const int tid = threadIdx.x;
-    if (*(volatile int *)p.err) return;             // an earlier launch already failed: do nothing
+    if (*(volatile int *)p.err) return;  // an earlier launch already failed: do nothing
 
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
@@ -142,12 +141,11 @@ __global__ void __launch_bounds__(NT) k_stencil_tma(const __grid_constant__ Sten
         const TmaFab tf = p.tfab[t.fab];
         const FabInfo f = p.ftab[t.fab];
         const CUtensorMap *map = p.maps + t.fab;
-        const int bx = tf.bx;                       // smem row length (elements)
-        const int ntot = t.tz + 2 * R;              // planes of this tile, halo included
+        const int g = tf.ngrow;
+        const int bx = tf.bx;                // whole row: x = -g at element 0
+        const int ntot = t.tz + 2 * R;       // planes of this tile, halo included
         const uint32_t plane_bytes = (uint32_t)(tf.bx * tf.by * (int)sizeof(S));
-        const int xcoord = tf.xv + t.x0 - tf.xs;    // 16-byte aligned row element of the first loaded column
-        const int ycoord = tf.ngrow + t.y0 - R, zcoord = tf.ngrow + t.z0 - R;
-
+        const int ycoord = g + t.y0 - R, zcoord = g + t.z0 - R;
         TileStrip ts;
         ts.lfab = ts.rfab = -1;
         ts.pcount = 0;
@@ -163,6 +161,7 @@ __global__ void __launch_bounds__(NT) k_stencil_tma(const __grid_constant__ Sten
             sp.x0 = pp.x0; sp.y0 = pp.y0; sp.z0 = pp.z0;
             sp.nx = pp.nx; sp.ny = pp.ny; sp.nz = pp.nz;
             sp.full_z = pp.z0 == 0 && pp.nz == t.tz;
+            sp.full_row = pp.full_row;
             spc[tid] = sp;
         }
         auto slot_of = [&](int pl) -> uint32_t { return (seq + (uint32_t)pl) & (uint32_t)(NS - 1); };
@@ -173,7 +172,7 @@ __global__ void __launch_bounds__(NT) k_stencil_tma(const __grid_constant__ Sten
             const bool centre = pl >= R && pl < R + t.tz;
             const bool ls = centre && ts.lfab >= 0, rs = centre && ts.rfab >= 0;
             mbar_expect_tx(&bars[sl], plane_bytes + (ls ? p.strip_bytes : 0) + (rs ? p.strip_bytes : 0));
-            tma_load_4d(sp, map, &bars[sl], xcoord, ycoord, zcoord + pl, t.comp);
+            tma_load_4d(sp, map, &bars[sl], 0, ycoord, zcoord + pl, t.comp);
             if (ls) tma_load_4d(sp + p.strip_off, p.smaps + ts.lfab, &bars[sl], ts.lx, ts.ly, ts.lz + pl - R, t.comp);
             if (rs)
                 tma_load_4d(sp + p.strip_off + p.strip_pitch, p.smaps + ts.rfab, &bars[sl], ts.rx, ts.ry,
@@ -190,18 +189,18 @@ __global__ void __launch_bounds__(NT) k_stencil_tma(const __grid_constant__ Sten
             for (int pl = 0; pl < issued0; ++pl) issue(pl);
         int issued = issued0;
 
-        // groups of VX consecutive x cells owned by this thread
-        const int ngx = (t.tx + VX - 1) / VX;
+        // groups: 16-byte pieces of a row, element e = VX * gx of row gy, cells x = e - g + c
+        const int ngx = bx / VX;
         const int ngroups = ngx * t.ty;
-        int soff[GPT], gx0[GPT], gy[GPT];
+        int soff[GPT], ge[GPT], gy[GPT];
         bool act[GPT];
 #pragma unroll
         for (int j = 0; j < GPT; ++j) {
             const int gi = tid + j * NT;
             act[j] = gi < ngroups;
-            gx0[j] = act[j] ? (gi % ngx) * VX : 0;
+            ge[j] = act[j] ? (gi % ngx) * VX : 0;
             gy[j] = act[j] ? gi / ngx : 0;
-            soff[j] = (gy[j] + R) * bx + tf.xs + gx0[j];  // smem offset of the group's first cell
+            soff[j] = (gy[j] + R) * bx + ge[j];  // smem offset of the group's first element
         }
         A q[GPT][VX][2 * R + 1];  // z queue per cell: q[..][..][i] = u(z - R + i)
         A fzm[GPT][VX];
@@ -247,8 +246,9 @@ __global__ void __launch_bounds__(NT) k_stencil_tma(const __grid_constant__ Sten
             }
 #pragma unroll
             for (int j = 0; j < GPT; ++j) {
-                const bool hit = act[j] && gy[j] >= sp.y0 && gy[j] < sp.y0 + sp.ny && gx0[j] < sp.x0 + sp.nx &&
-                                 gx0[j] + VX > sp.x0;
+                const int x0c = ge[j] - g;  // cell of the group's first element
+                const bool hit = act[j] && gy[j] >= sp.y0 && gy[j] < sp.y0 + sp.ny &&
+                                 (sp.full_row || (x0c < sp.x0 + sp.nx && x0c + VX > sp.x0));
                 if (hit) {
                     if (sp.full_z) pmask_full[j] |= 1u << pi;
                     else pmask_part[j] |= 1u << pi;
@@ -257,24 +257,43 @@ __global__ void __launch_bounds__(NT) k_stencil_tma(const __grid_constant__ Sten
         }
 
         const A lam = (A)p.lam[f.level][t.comp];
-        // per group, fixed for the tile: output pointer (advanced one plane per step), whether
-        // the 16-byte store is whole, and the shared-memory element offset (from the slot base)
-        // of every x-halo cell: the loaded row, or the neighbour strip outside the box
+        // per group, fixed for the tile: output pointer (advanced one plane per step) and the
+        // shared-memory offset of every x-halo cell -- the loaded row for cells of the box (and
+        // for filled ghost columns), the neighbour strip outside a strip-served face; cells
+        // that only feed don't-care outputs (ghost and padding positions) read their own row
         S *op[GPT];
-        bool vst[GPT];
         int hl[GPT][R], hr[GPT][R];
+        int co[GPT][VX];      // strip offsets for ghost cells inside the group next to a served face
+        uint32_t cov[GPT];    // bit c: cell c of the group takes its value from a strip
         {
-            S *dst = (S *)p.dst[f.level] + f.org + t.comp * f.cstride + (long long)t.z0 * f.plane;
+            S *rowbase = (S *)p.dst[f.level] + f.org - g + t.comp * f.cstride + (long long)t.z0 * f.plane;
             const int lso = p.strip_off / (int)sizeof(S), rso = (p.strip_off + p.strip_pitch) / (int)sizeof(S);
+            const int xw = p.strip_w;
+            const int n0 = f.n[0];
 #pragma unroll
             for (int j = 0; j < GPT; ++j) {
-                op[j] = dst + (long long)(t.y0 + gy[j]) * f.px + (t.x0 + gx0[j]);
-                vst[j] = (t.x0 % VX) == 0 && gx0[j] + VX <= t.tx;
+                op[j] = rowbase + (long long)(t.y0 + gy[j]) * f.px + ge[j];
+                const int rowo = (gy[j] + R) * bx;
 #pragma unroll
-                for (int i = 0; i < R; ++i) {
-                    const int xl = t.x0 + gx0[j] - R + i, xr = t.x0 + gx0[j] + VX + i;
-                    hl[j][i] = (xl < 0 && ts.lfab >= 0) ? lso + gy[j] * XH + XH + xl : soff[j] - R + i;
-                    hr[j][i] = (xr >= f.n[0] && ts.rfab >= 0) ? rso + gy[j] * XH + (xr - f.n[0]) : soff[j] + VX + i;
+                for (int i = 0; i < 2 * R; ++i) {
+                    const int x = (i < R) ? ge[j] - g - R + i : ge[j] - g + VX + (i - R);
+                    int o;
+                    if (x < 0 && x >= -R && ts.lfab >= 0) o = lso + gy[j] * xw + ts.lidx0 + x;
+                    else if (x >= n0 && x < n0 + R && ts.rfab >= 0) o = rso + gy[j] * xw + ts.ridx0 + (x - n0);
+                    else o = rowo + min(max(x + g, 0), bx - 1);
+                    if (i < R) hl[j][i] = o;
+                    else hr[j][i - R] = o;
+                }
+                cov[j] = 0;
+#pragma unroll
+                for (int c = 0; c < VX; ++c) {
+                    const int x = ge[j] - g + c;
+                    co[j][c] = 0;
+                    if (x < 0 && x >= -R && ts.lfab >= 0) { co[j][c] = lso + gy[j] * xw + ts.lidx0 + x; cov[j] |= 1u << c; }
+                    if (x >= n0 && x < n0 + R && ts.rfab >= 0) {
+                        co[j][c] = rso + gy[j] * xw + ts.ridx0 + (x - n0);
+                        cov[j] |= 1u << c;
+                    }
                 }
             }
         }
@@ -299,6 +318,11 @@ __global__ void __launch_bounds__(NT) k_stencil_tma(const __grid_constant__ Sten
                 }
 #pragma unroll
                 for (int c = 0; c < VX; ++c) wx[R + c] = q[j][c][R];
+                if (cov[j]) {  // the box face is inside this group: x neighbours from the strips
+#pragma unroll
+                    for (int c = 0; c < VX; ++c)
+                        if (cov[j] & (1u << c)) wx[R + c] = ld_smem<S, A>(cp + co[j][c]);
+                }
                 // y rows: ry[m][c] = u(x + c, y - R + m), m != R
                 A ry[2 * R + 1][VX];
                 const S *cc = cp + soff[j];
@@ -325,13 +349,9 @@ __global__ void __launch_bounds__(NT) k_stencil_tma(const __grid_constant__ Sten
                 S *o = op[j];
                 op[j] += f.plane;
                 if (!act[j]) continue;
-                if (vst[j]) {
-                    V16<S>::st(o, out);
-                } else {
-#pragma unroll
-                    for (int c = 0; c < VX; ++c)
-                        if (gx0[j] + c < t.tx) st(o + c, out[c]);
-                }
+                // whole 16-byte group: valid cells plus don't-care values in ghost / padding
+                // positions, so the row is written in whole sectors
+                V16<S>::st(o, out);
                 // ghost push: the same values into the neighbour boxes whose ghost faces hold them
                 uint32_t pm = pmask_full[j] | ((k >= kpart_lo && k <= kpart_hi) ? pmask_part[j] : 0u);
                 while (pm) {
@@ -339,16 +359,16 @@ __global__ void __launch_bounds__(NT) k_stencil_tma(const __grid_constant__ Sten
                     pm &= pm - 1;
                     const SPiece &sp = spc[pi];
                     if (k < sp.z0 || k >= sp.z0 + sp.nz) continue;
+                    const int x0c = ge[j] - g;
                     S *gp = sp.base + (long long)(k - sp.z0) * sp.plane + (long long)(gy[j] - sp.y0) * sp.px +
-                            (gx0[j] - sp.x0);
-                    if (gx0[j] >= sp.x0 && gx0[j] + VX <= sp.x0 + sp.nx && gx0[j] + VX <= t.tx &&
-                        ((uintptr_t)gp & 15) == 0) {
+                            (x0c - sp.x0);
+                    if (sp.full_row && ((uintptr_t)gp & 15) == 0) {
                         V16<S>::st(gp, out);
                     } else {
 #pragma unroll
                         for (int c = 0; c < VX; ++c) {
-                            const int x = gx0[j] + c;
-                            if (x >= sp.x0 && x < sp.x0 + sp.nx && x < t.tx) st(gp + c, out[c]);
+                            const int x = x0c + c;
+                            if (x >= sp.x0 && x < sp.x0 + sp.nx) st(gp + c, out[c]);
                         }
                     }
                 }
