@@ -226,10 +226,9 @@ struct mf {
     bool tma_strips = false;  // x halos pulled from neighbour boxes (fill skips x faces)
     int tma_R = 0;            // radius the maps were encoded for (0 = none)
     bool tma_ok = false;      // current tile shape fits the TMA kernel
-    int tma_cpt = 1, tma_slot = 0, tma_ns = 0;
+    int tma_cpt = 32, tma_slot = 0, tma_ns = 0;  // tma_cpt: CTA threads of the TMA stencil
     int tma_main_slot = 0, tma_strip_rows = 0, tma_strip_bytes = 0, tma_strip_pitch = 0, tma_strip_w = 0;
     bool use_tma = true;
-    int cta_threads = 256;    // TMA stencil CTA size (128 or 256), picked by the autotuner
     double *h_sum = nullptr;       // pinned
     size_t tile_capacity = 0;
     std::map<std::string, std::unique_ptr<GraphExec>> graphs;
@@ -675,11 +674,6 @@ extern "C" int mf_set_tile(mf_t *m, const int tile[3]) {
     m->tile_auto = false;
     int rc = set_tiles(m, tile);
     if (rc) return rc;
-    // CTA size for a user tile: the smaller one when a tile has at most 128 16-byte groups
-    int maxgroups = 0;
-    const int A = 16 / m->esize;
-    for (auto &t : m->tiles) maxgroups = std::max(maxgroups, ((int)t.tx + A - 1) / A * (int)t.ty);
-    m->cta_threads = maxgroups <= 128 ? 128 : 256;
     m->tma_R = 0;
     return 0;
 }
@@ -865,7 +859,7 @@ static bool tma_geometry(mf_t *m, int R, std::vector<TmaFab> &tf, int &slot_byte
     for (auto &t : m->tiles) {
         // the TMA kernel streams whole rows (x = -g .. n0 + g and padding) of every plane
         if (t.x0 != 0 || t.tx != m->fabs[t.fab].n[0]) return false;
-        maxgroups = std::max(maxgroups, m->fabs[t.fab].px / A * (int)t.ty);
+        maxgroups = std::max(maxgroups, (m->fabs[t.fab].n[0] + 2 * g + A - 1) / A * (int)t.ty);
     }
     for (size_t b = 0; b < m->fabs.size(); ++b) {
         int ty = 1;
@@ -877,9 +871,9 @@ static bool tma_geometry(mf_t *m, int R, std::vector<TmaFab> &tf, int &slot_byte
         if (tf[b].bx > 256 || tf[b].by > 256) return false;
         maxplane = std::max(maxplane, tf[b].bx * tf[b].by * S);
     }
-    const int nt = m->cta_threads;
-    gpt = maxgroups <= nt ? 1 : maxgroups <= 2 * nt ? 2 : maxgroups <= 4 * nt ? 4 : 0;
-    if (gpt == 0 || (R == 4 && gpt > 2)) return false;
+    // one thread per group: the CTA is the largest tile's group count rounded up to a warp
+    gpt = (maxgroups + 31) / 32 * 32;
+    if (gpt > tma_max_threads(R)) return false;
     slot_bytes = (maxplane + 127) / 128 * 128;
     return true;
 }
@@ -1140,7 +1134,7 @@ static int enqueue_stencil(mf_t *m, int from, int R, bool fp64diff, const double
         p.strip_w = m->tma_strip_w;
         p.push = (push && m->tma_push) ? (const PushPiece *)m->d_push.p : nullptr;
         for (int c = 0; c < m->ncomp; ++c) p.lam[0][c] = lam[c];
-        CU(launch_stencil_tma(m->dtype, R, fp64diff, m->cta_threads, m->tma_cpt, p, 0, s));
+        CU(launch_stencil_tma(m->dtype, R, fp64diff, m->tma_cpt, p, 0, s));
         return 0;
     }
     StencilParams p = stencil_params(m, from, lam);
@@ -1184,29 +1178,23 @@ static int autotune(mf_t *m, int R, bool fp64diff, const double *lam) {
     CU(cudaEventCreate(&e1));
     float best = 1e30f;
     std::array<int, 3> best_t = {0, 0, 0};
-    int best_nt = 256;
-    const int nts[2] = {128, 256};
-    for (auto &t : cands)
-        for (int nt : nts) {
-            if (!m->use_tma && nt != 256) continue;
-            m->cta_threads = nt;
-            int rc = set_tiles(m, t.data());
-            if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
-            // warm-up (also encodes the tensor maps), then 3 timed launches
+    for (auto &t : cands) {
+        int rc = set_tiles(m, t.data());
+        if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
+        // warm-up (also encodes the tensor maps), then 3 timed launches
+        if ((rc = enqueue_stencil(m, m->cur, R, fp64diff, lam, m->stream))) return rc;
+        CU(cudaEventRecord(e0, m->stream));
+        for (int i = 0; i < 3; ++i)
             if ((rc = enqueue_stencil(m, m->cur, R, fp64diff, lam, m->stream))) return rc;
-            CU(cudaEventRecord(e0, m->stream));
-            for (int i = 0; i < 3; ++i)
-                if ((rc = enqueue_stencil(m, m->cur, R, fp64diff, lam, m->stream))) return rc;
-            CU(cudaEventRecord(e1, m->stream));
-            CU(cudaEventSynchronize(e1));
-            float ms = 0;
-            CU(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best) { best = ms; best_t = t; best_nt = nt; }
-        }
+        CU(cudaEventRecord(e1, m->stream));
+        CU(cudaEventSynchronize(e1));
+        float ms = 0;
+        CU(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) { best = ms; best_t = t; }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     m->tile_auto = false;
-    m->cta_threads = best_nt;
     return set_tiles(m, best_t.data());
 }
 

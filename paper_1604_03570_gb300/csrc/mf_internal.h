@@ -101,7 +101,7 @@ struct StencilParams {
 };
 
 // TMA-staged stencil: per FArrayBox, the shared-memory plane geometry of its tensor map.
-constexpr int kTmaThreadsMax = 256;  // CTA sizes 128 or 256
+
 constexpr int kMaxStages = 16;
 constexpr int kMaxPush = 16;  // ghost-push pieces per tile
 
@@ -155,8 +155,9 @@ struct StencilTmaParams {
 };
 
 // ---- launchers (mf_kernels.cu, stencil_tma.cu); all asynchronous on `s`
-cudaError_t launch_stencil_tma(int dtype, int R, bool fp64diff, int nt, int gpt, const StencilTmaParams &p, int grid,
+cudaError_t launch_stencil_tma(int dtype, int R, bool fp64diff, int nt, const StencilTmaParams &p, int grid,
                                cudaStream_t s);
+int tma_max_threads(int R);  // largest CTA of the TMA stencil for radius R
 cudaError_t launch_fill(int dtype, const LevelPtrs &lv, const FbTask *tasks, int ntasks, int grid, cudaStream_t s);
 cudaError_t launch_stencil(int dtype, int R, bool fp64diff, const StencilParams &p, int bx, int by, int grid,
                            cudaStream_t s);

@@ -110,9 +110,14 @@ template <> struct V16<__nv_bfloat16> {
     }
 };
 
-template <typename S, typename A, int R, int GPT, int NT>
-__global__ void __launch_bounds__(NT) k_stencil_tma(const __grid_constant__ StencilTmaParams p) {
+// One thread per 16-byte group; the CTA has as many threads as the tile has groups (rounded
+// up to a warp), so its size is a launch parameter bounded per radius.
+template <int R> struct TmaBounds { static constexpr int threads = R == 1 ? 1024 : R == 2 ? 768 : 512; };
+
+template <typename S, typename A, int R>
+__global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __grid_constant__ StencilTmaParams p) {
     constexpr int VX = V16<S>::n;  // cells per group: one 16-byte vector of a row
+    constexpr int GPT = 1;
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bars[kMaxStages];
     __shared__ int abort_flag;
@@ -189,14 +194,15 @@ __global__ void __launch_bounds__(NT) k_stencil_tma(const __grid_constant__ Sten
             for (int pl = 0; pl < issued0; ++pl) issue(pl);
         int issued = issued0;
 
-        // groups: 16-byte pieces of a row, element e = VX * gx of row gy, cells x = e - g + c
-        const int ngx = bx / VX;
+        // groups: 16-byte pieces of a row, element e = VX * gx of row gy, cells x = e - g + c;
+        // groups holding nothing but padding are skipped
+        const int ngx = (f.n[0] + 2 * g + VX - 1) / VX;
         const int ngroups = ngx * t.ty;
         int soff[GPT], ge[GPT], gy[GPT];
         bool act[GPT];
 #pragma unroll
         for (int j = 0; j < GPT; ++j) {
-            const int gi = tid + j * NT;
+            const int gi = tid + j * (int)blockDim.x;
             act[j] = gi < ngroups;
             ge[j] = act[j] ? (gi % ngx) * VX : 0;
             gy[j] = act[j] ? gi / ngx : 0;
@@ -389,10 +395,11 @@ __global__ void __launch_bounds__(NT) k_stencil_tma(const __grid_constant__ Sten
     }
 }
 
-template <typename S, typename A, int R, int GPT, int NT>
-static cudaError_t tma_t(const StencilTmaParams &p, int grid, cudaStream_t s) {
+template <typename S, typename A, int R>
+static cudaError_t tma_t(int nt, const StencilTmaParams &p, int grid, cudaStream_t s) {
+    if (nt < 32 || nt > TmaBounds<R>::threads || nt % 32) return cudaErrorInvalidValue;
     const int smem = p.nstages * p.slot_bytes + 128;
-    auto kern = k_stencil_tma<S, A, R, GPT, NT>;
+    auto kern = k_stencil_tma<S, A, R>;
     static int configured = 0;
     if (smem > configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -402,56 +409,38 @@ static cudaError_t tma_t(const StencilTmaParams &p, int grid, cudaStream_t s) {
     int g = grid;
     if (g <= 0) {
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem) != cudaSuccess || per_sm < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem) != cudaSuccess || per_sm < 1)
             per_sm = 1;
         long long gg = (long long)per_sm * sm_count();
         g = (int)(gg < p.ntiles ? gg : p.ntiles);
         if (g < 1) g = 1;
     }
-    kern<<<g, NT, smem, s>>>(p);
+    kern<<<g, nt, smem, s>>>(p);
     return cudaGetLastError();
 }
 
-template <typename S, typename A, int R, int NT>
-static cudaError_t tma_c(int gpt, const StencilTmaParams &p, int grid, cudaStream_t s) {
-    switch (gpt) {
-        case 1: return tma_t<S, A, R, 1, NT>(p, grid, s);
-        case 2: return tma_t<S, A, R, 2, NT>(p, grid, s);
-        case 4:
-            if constexpr (R < 4) return tma_t<S, A, R, 4, NT>(p, grid, s);  // radius 4 keeps <= 2 groups per thread
-            break;
-    }
-    return cudaErrorInvalidValue;
-}
-
-template <typename S, typename A, int R>
-static cudaError_t tma_n(int nt, int gpt, const StencilTmaParams &p, int grid, cudaStream_t s) {
-    if (nt == 128) return tma_c<S, A, R, 128>(gpt, p, grid, s);
-    if (nt == 256) return tma_c<S, A, R, 256>(gpt, p, grid, s);
-    return cudaErrorInvalidValue;
-}
-
 template <typename S, typename A>
-static cudaError_t tma_r(int R, int nt, int gpt, const StencilTmaParams &p, int grid, cudaStream_t s) {
+static cudaError_t tma_r(int R, int nt, const StencilTmaParams &p, int grid, cudaStream_t s) {
     switch (R) {
-        case 1: return tma_n<S, A, 1>(nt, gpt, p, grid, s);
-        case 2: return tma_n<S, A, 2>(nt, gpt, p, grid, s);
-        case 4: return tma_n<S, A, 4>(nt, gpt, p, grid, s);
+        case 1: return tma_t<S, A, 1>(nt, p, grid, s);
+        case 2: return tma_t<S, A, 2>(nt, p, grid, s);
+        case 4: return tma_t<S, A, 4>(nt, p, grid, s);
     }
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_stencil_tma(int dtype, int R, bool fp64diff, int nt, int gpt, const StencilTmaParams &p, int grid,
+int tma_max_threads(int R) { return R == 1 ? TmaBounds<1>::threads : R == 2 ? TmaBounds<2>::threads : TmaBounds<4>::threads; }
+
+cudaError_t launch_stencil_tma(int dtype, int R, bool fp64diff, int nt, const StencilTmaParams &p, int grid,
                                cudaStream_t s) {
     if (p.ntiles == 0) return cudaSuccess;
     if (p.nstages > kMaxStages || p.nstages < R + 2 || (p.nstages & (p.nstages - 1))) return cudaErrorInvalidValue;
     switch (dtype) {
-        case F64: return tma_r<double, double>(R, nt, gpt, p, grid, s);
-        case F32:
-            return fp64diff ? tma_r<float, double>(R, nt, gpt, p, grid, s) : tma_r<float, float>(R, nt, gpt, p, grid, s);
+        case F64: return tma_r<double, double>(R, nt, p, grid, s);
+        case F32: return fp64diff ? tma_r<float, double>(R, nt, p, grid, s) : tma_r<float, float>(R, nt, p, grid, s);
         case BF16:
-            return fp64diff ? tma_r<__nv_bfloat16, double>(R, nt, gpt, p, grid, s)
-                            : tma_r<__nv_bfloat16, float>(R, nt, gpt, p, grid, s);
+            return fp64diff ? tma_r<__nv_bfloat16, double>(R, nt, p, grid, s)
+                            : tma_r<__nv_bfloat16, float>(R, nt, p, grid, s);
     }
     return cudaErrorInvalidValue;
 }
