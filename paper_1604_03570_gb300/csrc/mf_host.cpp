@@ -857,9 +857,10 @@ static bool tma_geometry(mf_t *m, int R, std::vector<TmaFab> &tf, int &slot_byte
     tf.assign(m->fabs.size(), TmaFab{});
     int maxplane = 0, maxgroups = 0;
     for (auto &t : m->tiles) {
-        // the TMA kernel streams whole rows (x = -g .. n0 + g and padding) of every plane
+        // the TMA kernel streams whole rows (x = -g .. n0 + g and padding) of every plane; a thread
+        // owns one 16-byte group in two consecutive rows
         if (t.x0 != 0 || t.tx != m->fabs[t.fab].n[0]) return false;
-        maxgroups = std::max(maxgroups, (m->fabs[t.fab].n[0] + 2 * g + A - 1) / A * (int)t.ty);
+        maxgroups = std::max(maxgroups, (m->fabs[t.fab].n[0] + 2 * g + A - 1) / A * (((int)t.ty + 1) / 2));
     }
     for (size_t b = 0; b < m->fabs.size(); ++b) {
         int ty = 1;
@@ -1122,6 +1123,8 @@ static int enqueue_stencil(mf_t *m, int from, int R, bool fp64diff, const double
         p.tiles = (const Tile *)m->d_tiles.p;
         p.ntiles = (int)m->tiles.size();
         p.nstages = m->tma_ns;
+        p.nstages_log2 = 0;
+        while ((1 << p.nstages_log2) < m->tma_ns) ++p.nstages_log2;
         p.slot_bytes = m->tma_slot;
         p.dst[0] = m->level_ptr(1 - from);
         p.err = (int *)m->d_err.p;

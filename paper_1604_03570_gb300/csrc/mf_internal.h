@@ -145,7 +145,8 @@ struct StencilTmaParams {
     const FabInfo *ftab;
     const Tile *tiles;
     int ntiles;
-    int nstages;               // shared-memory ring slots
+    int nstages;               // shared-memory ring slots (power of two)
+    int nstages_log2;
     int slot_bytes;            // bytes per slot (multiple of 128)
     int pad_;
     void *dst[kMaxLev];

@@ -107,4 +107,11 @@ __device__ __forceinline__ A update_cell_fx(A fxp, A fxm, const A *qy, A fzm, A 
     return Ar<A>::fma(lam, div, u);
 }
 
+// The same update with every face flux given: (Dx + Dy) + Dz, then u + lam * div.
+template <typename A>
+__device__ __forceinline__ A update_cell_f(A fxp, A fxm, A fyp, A fym, A fzp, A fzm, A u, A lam) {
+    A div = Ar<A>::add(Ar<A>::add(Ar<A>::sub(fxp, fxm), Ar<A>::sub(fyp, fym)), Ar<A>::sub(fzp, fzm));
+    return Ar<A>::fma(lam, div, u);
+}
+
 }  // namespace mfk

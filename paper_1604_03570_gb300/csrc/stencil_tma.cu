@@ -112,12 +112,11 @@ template <> struct V16<__nv_bfloat16> {
 
 // One thread per 16-byte group; the CTA has as many threads as the tile has groups (rounded
 // up to a warp), so its size is a launch parameter bounded per radius.
-template <int R> struct TmaBounds { static constexpr int threads = R == 1 ? 1024 : R == 2 ? 768 : 512; };
+template <int R> struct TmaBounds { static constexpr int threads = R == 4 ? 384 : 512; };
 
 template <typename S, typename A, int R>
 __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __grid_constant__ StencilTmaParams p) {
     constexpr int VX = V16<S>::n;  // cells per group: one 16-byte vector of a row
-    constexpr int GPT = 1;
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bars[kMaxStages];
     __shared__ int abort_flag;
@@ -185,7 +184,7 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
         };
         auto wait_plane = [&](int pl) -> bool {
             const uint32_t sq = seq + (uint32_t)pl;
-            return mbar_wait(&bars[sq & (uint32_t)(NS - 1)], (sq / (uint32_t)NS) & 1u);
+            return mbar_wait(&bars[sq & (uint32_t)(NS - 1)], (sq >> p.nstages_log2) & 1u);
         };
         auto plane_ptr = [&](int pl) -> const S * { return (const S *)(slots + (size_t)slot_of(pl) * p.slot_bytes); };
 
@@ -194,39 +193,36 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
             for (int pl = 0; pl < issued0; ++pl) issue(pl);
         int issued = issued0;
 
-        // groups: 16-byte pieces of a row, element e = VX * gx of row gy, cells x = e - g + c;
-        // groups holding nothing but padding are skipped
+        // work unit of a thread: a 16-byte group (element e = VX * gx, cells x = e - g + c) in two
+        // consecutive rows y0 = 2 * gp and y0 + 1 of the tile; the face flux between the two rows is
+        // shared.  Groups holding nothing but padding are skipped.
         const int ngx = (f.n[0] + 2 * g + VX - 1) / VX;
-        const int ngroups = ngx * t.ty;
-        int soff[GPT], ge[GPT], gy[GPT];
-        bool act[GPT];
-#pragma unroll
-        for (int j = 0; j < GPT; ++j) {
-            const int gi = tid + j * (int)blockDim.x;
-            act[j] = gi < ngroups;
-            ge[j] = act[j] ? (gi % ngx) * VX : 0;
-            gy[j] = act[j] ? gi / ngx : 0;
-            soff[j] = (gy[j] + R) * bx + ge[j];  // smem offset of the group's first element
-        }
-        A q[GPT][VX][2 * R + 1];  // z queue per cell: q[..][..][i] = u(z - R + i)
-        A fzm[GPT][VX];
+        const int npair = (t.ty + 1) >> 1;
+        const int gi = tid;
+        const bool act = gi < ngx * npair;
+        const int ge = act ? (gi % ngx) * VX : 0;
+        const int y0 = act ? 2 * (gi / ngx) : 0;
+        const bool act1 = act && y0 + 1 < t.ty;  // the second row exists
+        const int soff = (y0 + R) * bx + ge;     // smem offset of the first row's group
+        A q[2][VX][2 * R + 1];                   // z queue per cell: q[r][c][i] = u(z - R + i)
+        A fzm[2][VX];
         bool ok = true;
 #pragma unroll
         for (int pl = 0; pl < 2 * R; ++pl) {
             ok = ok && wait_plane(pl);
             const S *sp = plane_ptr(pl);
 #pragma unroll
-            for (int j = 0; j < GPT; ++j) {
+            for (int r = 0; r < 2; ++r) {
                 A v[VX];
-                V16<S>::ld(sp + soff[j], v);
+                V16<S>::ld(sp + soff + r * bx, v);
 #pragma unroll
-                for (int c = 0; c < VX; ++c) q[j][c][pl] = v[c];
+                for (int c = 0; c < VX; ++c) q[r][c][pl] = v[c];
             }
         }
 #pragma unroll
-        for (int j = 0; j < GPT; ++j)
+        for (int r = 0; r < 2; ++r)
 #pragma unroll
-            for (int c = 0; c < VX; ++c) fzm[j][c] = face_flux<A, R>(q[j][c], R - 1);
+            for (int c = 0; c < VX; ++c) fzm[r][c] = face_flux<A, R>(q[r][c], R - 1);
         if (!ok) { abort_flag = 1; atomicOr(p.err, 1); }
         __syncthreads();
         int waited = 2 * R;  // planes [0, waited) have completed
@@ -238,69 +234,64 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
         // planes 0 .. R-1 are no longer needed: refill their slots
         if (tid == 0)
             for (int pl = 0; pl < R && issued < ntot; ++pl) issue(issued++);
-        // push masks per group: pieces spanning the whole tile in z (checked every plane) and
-        // the others (checked only inside their planes)
-        uint32_t pmask_full[GPT], pmask_part[GPT];
+        // push masks per row: pieces spanning the whole tile in z (checked every plane) and the
+        // others (checked only inside their planes)
+        uint32_t pmask_full[2] = {0u, 0u}, pmask_part[2] = {0u, 0u};
         int kpart_lo = 0x7fffffff, kpart_hi = -1;  // planes where some partial piece applies
-#pragma unroll
-        for (int j = 0; j < GPT; ++j) { pmask_full[j] = 0; pmask_part[j] = 0; }
         for (int pi = 0; pi < ts.pcount; ++pi) {
             const SPiece &sp = spc[pi];
             if (!sp.full_z) {
                 kpart_lo = min(kpart_lo, sp.z0);
                 kpart_hi = max(kpart_hi, sp.z0 + sp.nz - 1);
             }
+            const int x0c = ge - g;  // cell of the group's first element
 #pragma unroll
-            for (int j = 0; j < GPT; ++j) {
-                const int x0c = ge[j] - g;  // cell of the group's first element
-                const bool hit = act[j] && gy[j] >= sp.y0 && gy[j] < sp.y0 + sp.ny &&
+            for (int r = 0; r < 2; ++r) {
+                const bool hit = (r == 0 ? act : act1) && y0 + r >= sp.y0 && y0 + r < sp.y0 + sp.ny &&
                                  (sp.full_row || (x0c < sp.x0 + sp.nx && x0c + VX > sp.x0));
                 if (hit) {
-                    if (sp.full_z) pmask_full[j] |= 1u << pi;
-                    else pmask_part[j] |= 1u << pi;
+                    if (sp.full_z) pmask_full[r] |= 1u << pi;
+                    else pmask_part[r] |= 1u << pi;
                 }
             }
         }
 
         const A lam = (A)p.lam[f.level][t.comp];
-        // per group, fixed for the tile: output pointer (advanced one plane per step) and the
-        // shared-memory offset of every x-halo cell -- the loaded row for cells of the box (and
-        // for filled ghost columns), the neighbour strip outside a strip-served face; cells
-        // that only feed don't-care outputs (ghost and padding positions) read their own row
-        S *op[GPT];
-        int hl[GPT][R], hr[GPT][R];
-        int co[GPT][VX];      // strip offsets for ghost cells inside the group next to a served face
-        uint32_t cov[GPT];    // bit c: cell c of the group takes its value from a strip
+        // fixed for the tile: output pointer (advanced one plane per step) and the shared-memory
+        // offset of every x-halo cell -- the loaded row for cells of the box (and for filled ghost
+        // columns), the neighbour strip outside a strip-served face; cells that only feed
+        // don't-care outputs (ghost and padding positions) read their own row
+        S *op;
+        int hl[2][R], hr[2][R];
+        int co[2][VX];   // strip offsets for ghost cells inside the group next to a served face
+        uint32_t cov;    // bit c: cell c of the group takes its value from a strip (both rows)
         {
-            S *rowbase = (S *)p.dst[f.level] + f.org - g + t.comp * f.cstride + (long long)t.z0 * f.plane;
+            op = (S *)p.dst[f.level] + f.org - g + t.comp * f.cstride + (long long)t.z0 * f.plane +
+                 (long long)(t.y0 + y0) * f.px + ge;
             const int lso = p.strip_off / (int)sizeof(S), rso = (p.strip_off + p.strip_pitch) / (int)sizeof(S);
             const int xw = p.strip_w;
             const int n0 = f.n[0];
+            auto src = [&](int x, int r) -> int {
+                if (x < 0 && x >= -R && ts.lfab >= 0) return lso + (y0 + r) * xw + ts.lidx0 + x;
+                if (x >= n0 && x < n0 + R && ts.rfab >= 0) return rso + (y0 + r) * xw + ts.ridx0 + (x - n0);
+                return (y0 + r + R) * bx + min(max(x + g, 0), bx - 1);
+            };
 #pragma unroll
-            for (int j = 0; j < GPT; ++j) {
-                op[j] = rowbase + (long long)(t.y0 + gy[j]) * f.px + ge[j];
-                const int rowo = (gy[j] + R) * bx;
+            for (int r = 0; r < 2; ++r) {
 #pragma unroll
-                for (int i = 0; i < 2 * R; ++i) {
-                    const int x = (i < R) ? ge[j] - g - R + i : ge[j] - g + VX + (i - R);
-                    int o;
-                    if (x < 0 && x >= -R && ts.lfab >= 0) o = lso + gy[j] * xw + ts.lidx0 + x;
-                    else if (x >= n0 && x < n0 + R && ts.rfab >= 0) o = rso + gy[j] * xw + ts.ridx0 + (x - n0);
-                    else o = rowo + min(max(x + g, 0), bx - 1);
-                    if (i < R) hl[j][i] = o;
-                    else hr[j][i - R] = o;
+                for (int i = 0; i < R; ++i) {
+                    hl[r][i] = src(ge - g - R + i, r);
+                    hr[r][i] = src(ge - g + VX + i, r);
                 }
-                cov[j] = 0;
+            }
+            cov = 0;
 #pragma unroll
-                for (int c = 0; c < VX; ++c) {
-                    const int x = ge[j] - g + c;
-                    co[j][c] = 0;
-                    if (x < 0 && x >= -R && ts.lfab >= 0) { co[j][c] = lso + gy[j] * xw + ts.lidx0 + x; cov[j] |= 1u << c; }
-                    if (x >= n0 && x < n0 + R && ts.rfab >= 0) {
-                        co[j][c] = rso + gy[j] * xw + ts.ridx0 + (x - n0);
-                        cov[j] |= 1u << c;
-                    }
-                }
+            for (int c = 0; c < VX; ++c) {
+                const int x = ge - g + c;
+                const bool strip = (x < 0 && x >= -R && ts.lfab >= 0) || (x >= n0 && x < n0 + R && ts.rfab >= 0);
+                co[0][c] = src(x, 0);
+                co[1][c] = src(x, 1);
+                if (strip) cov |= 1u << c;
             }
         }
         for (int k = 0; k < t.tz; ++k) {
@@ -308,73 +299,91 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
             const S *newp = plane_ptr(k + 2 * R);
             const S *cp = plane_ptr(k + R);
 #pragma unroll
-            for (int j = 0; j < GPT; ++j) {
-                {
-                    A v[VX];
-                    V16<S>::ld(newp + soff[j], v);
+            for (int r = 0; r < 2; ++r) {
+                A v[VX];
+                V16<S>::ld(newp + soff + r * bx, v);
 #pragma unroll
-                    for (int c = 0; c < VX; ++c) q[j][c][2 * R] = v[c];
-                }
+                for (int c = 0; c < VX; ++c) q[r][c][2 * R] = v[c];
+            }
+            // y window per column: wy[m][c] = u(x + c, y0 - R + m), m = 0 .. 2R+1 (rows y0, y0+1 from
+            // the queues, the rest from the centre plane)
+            A wy[2 * R + 2][VX];
+            const S *cc = cp + soff;
+#pragma unroll
+            for (int m = 0; m < 2 * R + 2; ++m) {
+                if (m == R || m == R + 1) continue;
+                V16<S>::ld(cc + (m - R) * bx, wy[m]);
+            }
+#pragma unroll
+            for (int c = 0; c < VX; ++c) { wy[R][c] = q[0][c][R]; wy[R + 1][c] = q[1][c][R]; }
+            // y-face fluxes at y0 - 1/2, y0 + 1/2 (shared), y0 + 3/2
+            A fy[3][VX];
+#pragma unroll
+            for (int c = 0; c < VX; ++c) {
+                A col[2 * R + 2];
+#pragma unroll
+                for (int m = 0; m < 2 * R + 2; ++m) col[m] = wy[m][c];
+                fy[0][c] = face_flux<A, R>(col, R - 1);
+                fy[1][c] = face_flux<A, R>(col, R);
+                fy[2][c] = face_flux<A, R>(col, R + 1);
+            }
+            A out[2][VX];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
                 // x window: w[i] = u(x0 - R + i), i = 0 .. VX + 2R - 1
                 A wx[VX + 2 * R];
 #pragma unroll
                 for (int i = 0; i < R; ++i) {
-                    wx[i] = ld_smem<S, A>(cp + hl[j][i]);
-                    wx[R + VX + i] = ld_smem<S, A>(cp + hr[j][i]);
+                    wx[i] = ld_smem<S, A>(cp + hl[r][i]);
+                    wx[R + VX + i] = ld_smem<S, A>(cp + hr[r][i]);
                 }
 #pragma unroll
-                for (int c = 0; c < VX; ++c) wx[R + c] = q[j][c][R];
-                if (cov[j]) {  // the box face is inside this group: x neighbours from the strips
+                for (int c = 0; c < VX; ++c) wx[R + c] = q[r][c][R];
+                if (cov) {  // the box face is inside this group: x neighbours from the strips
 #pragma unroll
                     for (int c = 0; c < VX; ++c)
-                        if (cov[j] & (1u << c)) wx[R + c] = ld_smem<S, A>(cp + co[j][c]);
-                }
-                // y rows: ry[m][c] = u(x + c, y - R + m), m != R
-                A ry[2 * R + 1][VX];
-                const S *cc = cp + soff[j];
-#pragma unroll
-                for (int m = 0; m < 2 * R + 1; ++m) {
-                    if (m == R) continue;
-                    V16<S>::ld(cc + (m - R) * bx, ry[m]);
+                        if (cov & (1u << c)) wx[R + c] = ld_smem<S, A>(cp + co[r][c]);
                 }
                 A fx[VX + 1];  // x-face fluxes: fx[c] is the face left of cell c
 #pragma unroll
                 for (int c = 0; c <= VX; ++c) fx[c] = face_flux<A, R>(wx, c + R - 1);
-                A out[VX];
 #pragma unroll
                 for (int c = 0; c < VX; ++c) {
-                    A qy[2 * R + 1];
+                    const A fzp = face_flux<A, R>(q[r][c], R);
+                    out[r][c] = update_cell_f<A>(fx[c + 1], fx[c], fy[r + 1][c], fy[r][c], fzp, fzm[r][c],
+                                                 q[r][c][R], lam);
+                    fzm[r][c] = fzp;
 #pragma unroll
-                    for (int m = 0; m < 2 * R + 1; ++m) qy[m] = (m == R) ? q[j][c][R] : ry[m][c];
-                    const A fzp = face_flux<A, R>(q[j][c], R);
-                    out[c] = update_cell_fx<A, R>(fx[c + 1], fx[c], qy, fzm[j][c], fzp, q[j][c][R], lam);
-                    fzm[j][c] = fzp;
-#pragma unroll
-                    for (int i = 0; i < 2 * R; ++i) q[j][c][i] = q[j][c][i + 1];
+                    for (int i = 0; i < 2 * R; ++i) q[r][c][i] = q[r][c][i + 1];
                 }
-                S *o = op[j];
-                op[j] += f.plane;
-                if (!act[j]) continue;
-                // whole 16-byte group: valid cells plus don't-care values in ghost / padding
-                // positions, so the row is written in whole sectors
-                V16<S>::st(o, out);
+            }
+            S *o = op;
+            op += f.plane;
+            if (act) {
+                // whole 16-byte groups: valid cells plus don't-care values in ghost / padding
+                // positions, so rows are written in whole sectors
+                V16<S>::st(o, out[0]);
+                if (act1) V16<S>::st(o + f.px, out[1]);
                 // ghost push: the same values into the neighbour boxes whose ghost faces hold them
-                uint32_t pm = pmask_full[j] | ((k >= kpart_lo && k <= kpart_hi) ? pmask_part[j] : 0u);
-                while (pm) {
-                    const int pi = __ffs(pm) - 1;
-                    pm &= pm - 1;
-                    const SPiece &sp = spc[pi];
-                    if (k < sp.z0 || k >= sp.z0 + sp.nz) continue;
-                    const int x0c = ge[j] - g;
-                    S *gp = sp.base + (long long)(k - sp.z0) * sp.plane + (long long)(gy[j] - sp.y0) * sp.px +
-                            (x0c - sp.x0);
-                    if (sp.full_row && ((uintptr_t)gp & 15) == 0) {
-                        V16<S>::st(gp, out);
-                    } else {
 #pragma unroll
-                        for (int c = 0; c < VX; ++c) {
-                            const int x = x0c + c;
-                            if (x >= sp.x0 && x < sp.x0 + sp.nx) st(gp + c, out[c]);
+                for (int r = 0; r < 2; ++r) {
+                    uint32_t pm = pmask_full[r] | ((k >= kpart_lo && k <= kpart_hi) ? pmask_part[r] : 0u);
+                    while (pm) {
+                        const int pi = __ffs(pm) - 1;
+                        pm &= pm - 1;
+                        const SPiece &sp = spc[pi];
+                        if (k < sp.z0 || k >= sp.z0 + sp.nz) continue;
+                        const int x0c = ge - g;
+                        S *gp = sp.base + (long long)(k - sp.z0) * sp.plane + (long long)(y0 + r - sp.y0) * sp.px +
+                                (x0c - sp.x0);
+                        if (sp.full_row && ((uintptr_t)gp & 15) == 0) {
+                            V16<S>::st(gp, out[r]);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < VX; ++c) {
+                                const int x = x0c + c;
+                                if (x >= sp.x0 && x < sp.x0 + sp.nx) st(gp + c, out[r][c]);
+                            }
                         }
                     }
                 }
