@@ -860,7 +860,8 @@ static bool tma_geometry(mf_t *m, int R, std::vector<TmaFab> &tf, int &slot_byte
         // the TMA kernel streams whole rows (x = -g .. n0 + g and padding) of every plane; a thread
         // owns one 16-byte group in two consecutive rows
         if (t.x0 != 0 || t.tx != m->fabs[t.fab].n[0]) return false;
-        maxgroups = std::max(maxgroups, (m->fabs[t.fab].n[0] + 2 * g + A - 1) / A * (((int)t.ty + 1) / 2));
+        const int rows = tma_rows_per_thread(R);
+        maxgroups = std::max(maxgroups, (m->fabs[t.fab].n[0] + 2 * g + A - 1) / A * (((int)t.ty + rows - 1) / rows));
     }
     for (size_t b = 0; b < m->fabs.size(); ++b) {
         int ty = 1;

@@ -114,7 +114,7 @@ template <> struct V16<__nv_bfloat16> {
 // up to a warp), so its size is a launch parameter bounded per radius.
 template <int R> struct TmaBounds { static constexpr int threads = R == 4 ? 384 : 512; };
 
-template <typename S, typename A, int R>
+template <typename S, typename A, int R, int ROWS>
 __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __grid_constant__ StencilTmaParams p) {
     constexpr int VX = V16<S>::n;  // cells per group: one 16-byte vector of a row
     extern __shared__ unsigned char smem_raw[];
@@ -193,26 +193,26 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
             for (int pl = 0; pl < issued0; ++pl) issue(pl);
         int issued = issued0;
 
-        // work unit of a thread: a 16-byte group (element e = VX * gx, cells x = e - g + c) in two
-        // consecutive rows y0 = 2 * gp and y0 + 1 of the tile; the face flux between the two rows is
+        // work unit of a thread: a 16-byte group (element e = VX * gx, cells x = e - g + c) in ROWS
+        // consecutive rows y0 .. y0 + ROWS - 1 of the tile; the face fluxes between those rows are
         // shared.  Groups holding nothing but padding are skipped.
         const int ngx = (f.n[0] + 2 * g + VX - 1) / VX;
-        const int npair = (t.ty + 1) >> 1;
+        const int nset = (t.ty + ROWS - 1) / ROWS;
         const int gi = tid;
-        const bool act = gi < ngx * npair;
+        const bool act = gi < ngx * nset;
         const int ge = act ? (gi % ngx) * VX : 0;
-        const int y0 = act ? 2 * (gi / ngx) : 0;
-        const bool act1 = act && y0 + 1 < t.ty;  // the second row exists
+        const int y0 = act ? ROWS * (gi / ngx) : 0;
+        const int nrow = act ? min(ROWS, t.ty - y0) : 0;  // rows of the set that exist
         const int soff = (y0 + R) * bx + ge;     // smem offset of the first row's group
-        A q[2][VX][2 * R + 1];                   // z queue per cell: q[r][c][i] = u(z - R + i)
-        A fzm[2][VX];
+        A q[ROWS][VX][2 * R + 1];                // z queue per cell: q[r][c][i] = u(z - R + i)
+        A fzm[ROWS][VX];
         bool ok = true;
 #pragma unroll
         for (int pl = 0; pl < 2 * R; ++pl) {
             ok = ok && wait_plane(pl);
             const S *sp = plane_ptr(pl);
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
+            for (int r = 0; r < ROWS; ++r) {
                 A v[VX];
                 V16<S>::ld(sp + soff + r * bx, v);
 #pragma unroll
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
             }
         }
 #pragma unroll
-        for (int r = 0; r < 2; ++r)
+        for (int r = 0; r < ROWS; ++r)
 #pragma unroll
             for (int c = 0; c < VX; ++c) fzm[r][c] = face_flux<A, R>(q[r][c], R - 1);
         if (!ok) { abort_flag = 1; atomicOr(p.err, 1); }
@@ -236,7 +236,9 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
             for (int pl = 0; pl < R && issued < ntot; ++pl) issue(issued++);
         // push masks per row: pieces spanning the whole tile in z (checked every plane) and the
         // others (checked only inside their planes)
-        uint32_t pmask_full[2] = {0u, 0u}, pmask_part[2] = {0u, 0u};
+        uint32_t pmask_full[ROWS], pmask_part[ROWS];
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) { pmask_full[r] = 0u; pmask_part[r] = 0u; }
         int kpart_lo = 0x7fffffff, kpart_hi = -1;  // planes where some partial piece applies
         for (int pi = 0; pi < ts.pcount; ++pi) {
             const SPiece &sp = spc[pi];
@@ -246,8 +248,8 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
             }
             const int x0c = ge - g;  // cell of the group's first element
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                const bool hit = (r == 0 ? act : act1) && y0 + r >= sp.y0 && y0 + r < sp.y0 + sp.ny &&
+            for (int r = 0; r < ROWS; ++r) {
+                const bool hit = r < nrow && y0 + r >= sp.y0 && y0 + r < sp.y0 + sp.ny &&
                                  (sp.full_row || (x0c < sp.x0 + sp.nx && x0c + VX > sp.x0));
                 if (hit) {
                     if (sp.full_z) pmask_full[r] |= 1u << pi;
@@ -256,15 +258,18 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
             }
         }
 
+        bool has_push = false;
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) has_push = has_push || (pmask_full[r] | pmask_part[r]) != 0u;
         const A lam = (A)p.lam[f.level][t.comp];
         // fixed for the tile: output pointer (advanced one plane per step) and the shared-memory
         // offset of every x-halo cell -- the loaded row for cells of the box (and for filled ghost
         // columns), the neighbour strip outside a strip-served face; cells that only feed
         // don't-care outputs (ghost and padding positions) read their own row
         S *op;
-        int hl[2][R], hr[2][R];
-        int co[2][VX];   // strip offsets for ghost cells inside the group next to a served face
-        uint32_t cov;    // bit c: cell c of the group takes its value from a strip (both rows)
+        int hl[ROWS][R], hr[ROWS][R];
+        int co[ROWS][VX];  // strip offsets for ghost cells inside the group next to a served face
+        uint32_t cov;      // bit c: cell c of the group takes its value from a strip (every row)
         {
             op = (S *)p.dst[f.level] + f.org - g + t.comp * f.cstride + (long long)t.z0 * f.plane +
                  (long long)(t.y0 + y0) * f.px + ge;
@@ -277,7 +282,7 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
                 return (y0 + r + R) * bx + min(max(x + g, 0), bx - 1);
             };
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
+            for (int r = 0; r < ROWS; ++r) {
 #pragma unroll
                 for (int i = 0; i < R; ++i) {
                     hl[r][i] = src(ge - g - R + i, r);
@@ -289,8 +294,8 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
             for (int c = 0; c < VX; ++c) {
                 const int x = ge - g + c;
                 const bool strip = (x < 0 && x >= -R && ts.lfab >= 0) || (x >= n0 && x < n0 + R && ts.rfab >= 0);
-                co[0][c] = src(x, 0);
-                co[1][c] = src(x, 1);
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) co[r][c] = src(x, r);
                 if (strip) cov |= 1u << c;
             }
         }
@@ -299,37 +304,38 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
             const S *newp = plane_ptr(k + 2 * R);
             const S *cp = plane_ptr(k + R);
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
+            for (int r = 0; r < ROWS; ++r) {
                 A v[VX];
                 V16<S>::ld(newp + soff + r * bx, v);
 #pragma unroll
                 for (int c = 0; c < VX; ++c) q[r][c][2 * R] = v[c];
             }
-            // y window per column: wy[m][c] = u(x + c, y0 - R + m), m = 0 .. 2R+1 (rows y0, y0+1 from
-            // the queues, the rest from the centre plane)
-            A wy[2 * R + 2][VX];
+            // y window per column: wy[m][c] = u(x + c, y0 - R + m), m = 0 .. 2R+ROWS-1 (the set's own
+            // rows from the queues, the rest from the centre plane)
+            A wy[2 * R + ROWS][VX];
             const S *cc = cp + soff;
 #pragma unroll
-            for (int m = 0; m < 2 * R + 2; ++m) {
-                if (m == R || m == R + 1) continue;
+            for (int m = 0; m < 2 * R + ROWS; ++m) {
+                if (m >= R && m < R + ROWS) continue;
                 V16<S>::ld(cc + (m - R) * bx, wy[m]);
             }
 #pragma unroll
-            for (int c = 0; c < VX; ++c) { wy[R][c] = q[0][c][R]; wy[R + 1][c] = q[1][c][R]; }
-            // y-face fluxes at y0 - 1/2, y0 + 1/2 (shared), y0 + 3/2
-            A fy[3][VX];
+            for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+                for (int c = 0; c < VX; ++c) wy[R + r][c] = q[r][c][R];
+            // y-face fluxes at y0 - 1/2 + r, r = 0 .. ROWS (inner faces shared by two rows)
+            A fy[ROWS + 1][VX];
 #pragma unroll
             for (int c = 0; c < VX; ++c) {
-                A col[2 * R + 2];
+                A col[2 * R + ROWS];
 #pragma unroll
-                for (int m = 0; m < 2 * R + 2; ++m) col[m] = wy[m][c];
-                fy[0][c] = face_flux<A, R>(col, R - 1);
-                fy[1][c] = face_flux<A, R>(col, R);
-                fy[2][c] = face_flux<A, R>(col, R + 1);
+                for (int m = 0; m < 2 * R + ROWS; ++m) col[m] = wy[m][c];
+#pragma unroll
+                for (int r = 0; r <= ROWS; ++r) fy[r][c] = face_flux<A, R>(col, R - 1 + r);
             }
-            A out[2][VX];
+            A out[ROWS][VX];
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
+            for (int r = 0; r < ROWS; ++r) {
                 // x window: w[i] = u(x0 - R + i), i = 0 .. VX + 2R - 1
                 A wx[VX + 2 * R];
 #pragma unroll
@@ -362,11 +368,14 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
             if (act) {
                 // whole 16-byte groups: valid cells plus don't-care values in ghost / padding
                 // positions, so rows are written in whole sectors
-                V16<S>::st(o, out[0]);
-                if (act1) V16<S>::st(o + f.px, out[1]);
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r)
+                    if (r < nrow) V16<S>::st(o + r * f.px, out[r]);
+            }
+            if (has_push) {
                 // ghost push: the same values into the neighbour boxes whose ghost faces hold them
 #pragma unroll
-                for (int r = 0; r < 2; ++r) {
+                for (int r = 0; r < ROWS; ++r) {
                     uint32_t pm = pmask_full[r] | ((k >= kpart_lo && k <= kpart_hi) ? pmask_part[r] : 0u);
                     while (pm) {
                         const int pi = __ffs(pm) - 1;
@@ -404,11 +413,13 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
     }
 }
 
+template <int R> struct TmaRows { static constexpr int rows = R == 1 ? 4 : 2; };
+
 template <typename S, typename A, int R>
 static cudaError_t tma_t(int nt, const StencilTmaParams &p, int grid, cudaStream_t s) {
     if (nt < 32 || nt > TmaBounds<R>::threads || nt % 32) return cudaErrorInvalidValue;
     const int smem = p.nstages * p.slot_bytes + 128;
-    auto kern = k_stencil_tma<S, A, R>;
+    auto kern = k_stencil_tma<S, A, R, TmaRows<R>::rows>;
     static int configured = 0;
     if (smem > configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -439,6 +450,7 @@ static cudaError_t tma_r(int R, int nt, const StencilTmaParams &p, int grid, cud
 }
 
 int tma_max_threads(int R) { return R == 1 ? TmaBounds<1>::threads : R == 2 ? TmaBounds<2>::threads : TmaBounds<4>::threads; }
+int tma_rows_per_thread(int R) { return R == 1 ? TmaRows<1>::rows : R == 2 ? TmaRows<2>::rows : TmaRows<4>::rows; }
 
 cudaError_t launch_stencil_tma(int dtype, int R, bool fp64diff, int nt, const StencilTmaParams &p, int grid,
                                cudaStream_t s) {
