@@ -873,8 +873,8 @@ static bool tma_geometry(mf_t *m, int R, std::vector<TmaFab> &tf, int &slot_byte
         if (tf[b].bx > 256 || tf[b].by > 256) return false;
         maxplane = std::max(maxplane, tf[b].bx * tf[b].by * S);
     }
-    // one thread per group: the CTA is the largest tile's group count rounded up to a warp
-    gpt = (maxgroups + 31) / 32 * 32;
+    // a producer warp plus one consumer thread per group, rounded up to a warp
+    gpt = 32 + (maxgroups + 31) / 32 * 32;
     if (gpt > tma_max_threads(R)) return false;
     slot_bytes = (maxplane + 127) / 128 * 128;
     return true;
@@ -968,7 +968,7 @@ static int build_tma(mf_t *m, int R) {
     const int slot = main_slot + 2 * strip_pitch;
     int ns = R == 4 ? 16 : 8;  // ring slots (power of two)
     while (ns > 8 && (long long)ns * slot + 128 > 160 * 1024) ns /= 2;
-    if (ns < 2 * R || (long long)ns * slot + 128 > 200 * 1024) return 0;
+    if (ns < 2 * R + 1 || (long long)ns * slot + 128 > 200 * 1024) return 0;
     auto encode = tensor_map_encoder();
     if (!encode) return 0;
     const int nf = (int)m->fabs.size();

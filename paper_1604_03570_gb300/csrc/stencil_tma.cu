@@ -110,169 +110,133 @@ template <> struct V16<__nv_bfloat16> {
     }
 };
 
-// One thread per 16-byte group; the CTA has as many threads as the tile has groups (rounded
-// up to a warp), so its size is a launch parameter bounded per radius.
-template <int R> struct TmaBounds { static constexpr int threads = R == 4 ? 384 : 512; };
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Warp 0 is the producer: its first lane issues the TMA loads of every plane of every tile of
+// this CTA, in order, into the ring of NS slots, each time waiting for the slot's "empty"
+// barrier (all consumer warps done with the plane that last used it).  The other warps are
+// consumers: each thread owns one 16-byte group (element e = VX * gx, cells x = e - g + c) in
+// ROWS consecutive rows of the tile and marches it along z with a register queue.  There is
+// no CTA-wide barrier inside the loop, so consumers run ahead as far as the loaded planes
+// allow, and the producer starts on the next tile while the consumers finish this one.
+// The CTA has 32 + (consumer groups rounded up to a warp) threads.
+template <int R> struct TmaBounds { static constexpr int threads = R == 4 ? 416 : 544; };
 
 template <typename S, typename A, int R, int ROWS>
 __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __grid_constant__ StencilTmaParams p) {
     constexpr int VX = V16<S>::n;  // cells per group: one 16-byte vector of a row
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bars[kMaxStages];
-    __shared__ int abort_flag;
-    struct SPiece {
-        S *base;           // destination of the piece's first cell, this tile's component
-        long long plane;
-        int px, x0, y0, z0, nx, ny, nz, full_z, full_row;
-    };
-    __shared__ SPiece spc[kMaxPush];
+    __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];
     unsigned char *slots = (unsigned char *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     const int NS = p.nstages;  // power of two
     const int tid = threadIdx.x;
-    if (*(volatile int *)p.err) return;  // an earlier launch already failed: do nothing
-
+    const int ncw = (int)(blockDim.x >> 5) - 1;  // consumer warps
+    if (*(volatile int *)p.err) return;          // an earlier launch already failed: do nothing
     if (tid == 0) {
-        for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
-        abort_flag = 0;
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], (uint32_t)ncw);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
 
-    uint32_t seq = 0;  // planes issued by this CTA so far; plane seq+i lives in slot (seq+i) % NS
+    if (tid < 32) {
+        // ------------------------------------------------------------------ producer
+        if (tid != 0) return;
+        uint32_t seq = 0;
+        for (int w = blockIdx.x; w < p.ntiles; w += gridDim.x) {
+            const Tile t = p.tiles[w];
+            const TmaFab tf = p.tfab[t.fab];
+            TileStrip ts;
+            ts.lfab = ts.rfab = -1;
+            if (p.strips) ts = p.strips[w];
+            const CUtensorMap *map = p.maps + t.fab;
+            const uint32_t plane_bytes = (uint32_t)(tf.bx * tf.by * (int)sizeof(S));
+            const int ycoord = tf.ngrow + t.y0 - R, zcoord = tf.ngrow + t.z0 - R;
+            const int ntot = t.tz + 2 * R;
+            for (int pl = 0; pl < ntot; ++pl, ++seq) {
+                const uint32_t sl = seq & (uint32_t)(NS - 1);
+                if (seq >= (uint32_t)NS && !mbar_wait(&empty[sl], ((seq >> p.nstages_log2) - 1) & 1u)) {
+                    atomicOr(p.err, 1);
+                    return;  // consumers give up on their own bounded waits
+                }
+                unsigned char *sp = slots + (size_t)sl * p.slot_bytes;
+                // centre planes (the x neighbours of the tile's cells) also take the x halo strips
+                const bool centre = pl >= R && pl < R + t.tz;
+                const bool ls = centre && ts.lfab >= 0, rs = centre && ts.rfab >= 0;
+                mbar_expect_tx(&full[sl], plane_bytes + (ls ? p.strip_bytes : 0) + (rs ? p.strip_bytes : 0));
+                tma_load_4d(sp, map, &full[sl], 0, ycoord, zcoord + pl, t.comp);
+                if (ls) tma_load_4d(sp + p.strip_off, p.smaps + ts.lfab, &full[sl], ts.lx, ts.ly, ts.lz + pl - R, t.comp);
+                if (rs)
+                    tma_load_4d(sp + p.strip_off + p.strip_pitch, p.smaps + ts.rfab, &full[sl], ts.rx, ts.ry,
+                                ts.rz + pl - R, t.comp);
+            }
+        }
+        // drain: the last NS planes must have landed before the CTA may exit
+        for (uint32_t k = seq > (uint32_t)NS ? seq - NS : 0; k < seq; ++k)
+            if (!mbar_wait(&full[k & (uint32_t)(NS - 1)], (k >> p.nstages_log2) & 1u)) {
+                atomicOr(p.err, 1);
+                return;
+            }
+        return;
+    }
+
+    // ------------------------------------------------------------------ consumers
+    const int ctid = tid - 32;
+    const int lane = tid & 31;
+    uint32_t seq = 0;
+    auto wait_seq = [&](uint32_t sq) -> bool {
+        return mbar_wait(&full[sq & (uint32_t)(NS - 1)], (sq >> p.nstages_log2) & 1u);
+    };
+    auto slot_ptr = [&](uint32_t sq) -> const S * {
+        return (const S *)(slots + (size_t)(sq & (uint32_t)(NS - 1)) * p.slot_bytes);
+    };
+    auto release = [&](uint32_t sq) {  // this warp is done with plane sq
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[sq & (uint32_t)(NS - 1)]);
+    };
     for (int w = blockIdx.x; w < p.ntiles; w += gridDim.x) {
         const Tile t = p.tiles[w];
         const TmaFab tf = p.tfab[t.fab];
         const FabInfo f = p.ftab[t.fab];
-        const CUtensorMap *map = p.maps + t.fab;
         const int g = tf.ngrow;
-        const int bx = tf.bx;                // whole row: x = -g at element 0
-        const int ntot = t.tz + 2 * R;       // planes of this tile, halo included
-        const uint32_t plane_bytes = (uint32_t)(tf.bx * tf.by * (int)sizeof(S));
-        const int ycoord = g + t.y0 - R, zcoord = g + t.z0 - R;
+        const int bx = tf.bx;  // whole row: x = -g at element 0
         TileStrip ts;
         ts.lfab = ts.rfab = -1;
         ts.pcount = 0;
         if (p.strips) ts = p.strips[w];
         if (!p.push) ts.pcount = 0;
-        if (tid < ts.pcount) {  // ghost-push pieces of the tile, resolved once
-            const PushPiece pp = p.push[ts.pfirst + tid];
-            const FabInfo &df = p.ftab[pp.dfab];
-            SPiece sp;
-            sp.base = (S *)p.dst[df.level] + pp.dst + t.comp * df.cstride;
-            sp.plane = df.plane;
-            sp.px = df.px;
-            sp.x0 = pp.x0; sp.y0 = pp.y0; sp.z0 = pp.z0;
-            sp.nx = pp.nx; sp.ny = pp.ny; sp.nz = pp.nz;
-            sp.full_z = pp.z0 == 0 && pp.nz == t.tz;
-            sp.full_row = pp.full_row;
-            spc[tid] = sp;
-        }
-        auto slot_of = [&](int pl) -> uint32_t { return (seq + (uint32_t)pl) & (uint32_t)(NS - 1); };
-        auto issue = [&](int pl) {
-            const uint32_t sl = slot_of(pl);
-            unsigned char *sp = slots + (size_t)sl * p.slot_bytes;
-            // centre planes (the x neighbours of the tile's cells) also take the x halo strips
-            const bool centre = pl >= R && pl < R + t.tz;
-            const bool ls = centre && ts.lfab >= 0, rs = centre && ts.rfab >= 0;
-            mbar_expect_tx(&bars[sl], plane_bytes + (ls ? p.strip_bytes : 0) + (rs ? p.strip_bytes : 0));
-            tma_load_4d(sp, map, &bars[sl], 0, ycoord, zcoord + pl, t.comp);
-            if (ls) tma_load_4d(sp + p.strip_off, p.smaps + ts.lfab, &bars[sl], ts.lx, ts.ly, ts.lz + pl - R, t.comp);
-            if (rs)
-                tma_load_4d(sp + p.strip_off + p.strip_pitch, p.smaps + ts.rfab, &bars[sl], ts.rx, ts.ry,
-                            ts.rz + pl - R, t.comp);
-        };
-        auto wait_plane = [&](int pl) -> bool {
-            const uint32_t sq = seq + (uint32_t)pl;
-            return mbar_wait(&bars[sq & (uint32_t)(NS - 1)], (sq >> p.nstages_log2) & 1u);
-        };
-        auto plane_ptr = [&](int pl) -> const S * { return (const S *)(slots + (size_t)slot_of(pl) * p.slot_bytes); };
 
-        const int issued0 = ntot < NS ? ntot : NS;
-        if (tid == 0)
-            for (int pl = 0; pl < issued0; ++pl) issue(pl);
-        int issued = issued0;
-
-        // work unit of a thread: a 16-byte group (element e = VX * gx, cells x = e - g + c) in ROWS
-        // consecutive rows y0 .. y0 + ROWS - 1 of the tile; the face fluxes between those rows are
-        // shared.  Groups holding nothing but padding are skipped.
         const int ngx = (f.n[0] + 2 * g + VX - 1) / VX;
         const int nset = (t.ty + ROWS - 1) / ROWS;
-        const int gi = tid;
-        const bool act = gi < ngx * nset;
-        const int ge = act ? (gi % ngx) * VX : 0;
-        const int y0 = act ? ROWS * (gi / ngx) : 0;
+        const bool act = ctid < ngx * nset;
+        const int ge = act ? (ctid % ngx) * VX : 0;
+        const int y0 = act ? ROWS * (ctid / ngx) : 0;
         const int nrow = act ? min(ROWS, t.ty - y0) : 0;  // rows of the set that exist
-        const int soff = (y0 + R) * bx + ge;     // smem offset of the first row's group
-        A q[ROWS][VX][2 * R + 1];                // z queue per cell: q[r][c][i] = u(z - R + i)
-        A fzm[ROWS][VX];
-        bool ok = true;
-#pragma unroll
-        for (int pl = 0; pl < 2 * R; ++pl) {
-            ok = ok && wait_plane(pl);
-            const S *sp = plane_ptr(pl);
-#pragma unroll
-            for (int r = 0; r < ROWS; ++r) {
-                A v[VX];
-                V16<S>::ld(sp + soff + r * bx, v);
-#pragma unroll
-                for (int c = 0; c < VX; ++c) q[r][c][pl] = v[c];
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < ROWS; ++r)
-#pragma unroll
-            for (int c = 0; c < VX; ++c) fzm[r][c] = face_flux<A, R>(q[r][c], R - 1);
-        if (!ok) { abort_flag = 1; atomicOr(p.err, 1); }
-        __syncthreads();
-        int waited = 2 * R;  // planes [0, waited) have completed
-        if (abort_flag) {
-            if (tid == 0)
-                for (int pl = waited; pl < issued; ++pl) wait_plane(pl);
-            break;
-        }
-        // planes 0 .. R-1 are no longer needed: refill their slots
-        if (tid == 0)
-            for (int pl = 0; pl < R && issued < ntot; ++pl) issue(issued++);
-        // push masks per row: pieces spanning the whole tile in z (checked every plane) and the
-        // others (checked only inside their planes)
-        uint32_t pmask_full[ROWS], pmask_part[ROWS];
-#pragma unroll
-        for (int r = 0; r < ROWS; ++r) { pmask_full[r] = 0u; pmask_part[r] = 0u; }
-        int kpart_lo = 0x7fffffff, kpart_hi = -1;  // planes where some partial piece applies
+        const int soff = (y0 + R) * bx + ge;             // smem offset of the first row's group
+
+        // ghost-push pieces touching this thread's rows
+        uint32_t pmask = 0u;
         for (int pi = 0; pi < ts.pcount; ++pi) {
-            const SPiece &sp = spc[pi];
-            if (!sp.full_z) {
-                kpart_lo = min(kpart_lo, sp.z0);
-                kpart_hi = max(kpart_hi, sp.z0 + sp.nz - 1);
-            }
-            const int x0c = ge - g;  // cell of the group's first element
-#pragma unroll
-            for (int r = 0; r < ROWS; ++r) {
-                const bool hit = r < nrow && y0 + r >= sp.y0 && y0 + r < sp.y0 + sp.ny &&
-                                 (sp.full_row || (x0c < sp.x0 + sp.nx && x0c + VX > sp.x0));
-                if (hit) {
-                    if (sp.full_z) pmask_full[r] |= 1u << pi;
-                    else pmask_part[r] |= 1u << pi;
-                }
-            }
+            const PushPiece pp = p.push[ts.pfirst + pi];
+            const int x0c = ge - g;
+            const bool hit = act && y0 + nrow > pp.y0 && y0 < pp.y0 + pp.ny &&
+                             (pp.full_row || (x0c < pp.x0 + pp.nx && x0c + VX > pp.x0));
+            if (hit) pmask |= 1u << pi;
         }
 
-        bool has_push = false;
-#pragma unroll
-        for (int r = 0; r < ROWS; ++r) has_push = has_push || (pmask_full[r] | pmask_part[r]) != 0u;
-        const A lam = (A)p.lam[f.level][t.comp];
         // fixed for the tile: output pointer (advanced one plane per step) and the shared-memory
-        // offset of every x-halo cell -- the loaded row for cells of the box (and for filled ghost
-        // columns), the neighbour strip outside a strip-served face; cells that only feed
+        // offset of every x-halo cell -- the loaded row for cells of the box (and for filled
+        // ghost columns), the neighbour strip outside a strip-served face; cells that only feed
         // don't-care outputs (ghost and padding positions) read their own row
-        S *op;
         int hl[ROWS][R], hr[ROWS][R];
         int co[ROWS][VX];  // strip offsets for ghost cells inside the group next to a served face
-        uint32_t cov;      // bit c: cell c of the group takes its value from a strip (every row)
+        uint32_t cov = 0;  // bit c: cell c of the group takes its value from a strip (every row)
         {
-            op = (S *)p.dst[f.level] + f.org - g + t.comp * f.cstride + (long long)t.z0 * f.plane +
-                 (long long)(t.y0 + y0) * f.px + ge;
             const int lso = p.strip_off / (int)sizeof(S), rso = (p.strip_off + p.strip_pitch) / (int)sizeof(S);
             const int xw = p.strip_w;
             const int n0 = f.n[0];
@@ -289,7 +253,6 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
                     hr[r][i] = src(ge - g + VX + i, r);
                 }
             }
-            cov = 0;
 #pragma unroll
             for (int c = 0; c < VX; ++c) {
                 const int x = ge - g + c;
@@ -299,10 +262,42 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
                 if (strip) cov |= 1u << c;
             }
         }
+        S *op = (S *)p.dst[f.level] + f.org - g + t.comp * f.cstride + (long long)t.z0 * f.plane +
+                (long long)(t.y0 + y0) * f.px + ge;
+        const A lam = (A)p.lam[f.level][t.comp];
+
+        A q[ROWS][VX][2 * R + 1];  // z queue per cell: q[r][c][i] = u(z - R + i)
+        A fzm[ROWS][VX];
+        bool ok = true;
+#pragma unroll
+        for (int pl = 0; pl < 2 * R; ++pl) {
+            ok = ok && wait_seq(seq + pl);
+            const S *sp = slot_ptr(seq + pl);
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+                A v[VX];
+                V16<S>::ld(sp + soff + r * bx, v);
+#pragma unroll
+                for (int c = 0; c < VX; ++c) q[r][c][pl] = v[c];
+            }
+        }
+        if (!__all_sync(0xffffffffu, ok)) {  // the whole warp leaves together
+            if (lane == 0) atomicOr(p.err, 1);
+            return;
+        }
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+            for (int c = 0; c < VX; ++c) fzm[r][c] = face_flux<A, R>(q[r][c], R - 1);
+        for (int pl = 0; pl < R; ++pl) release(seq + pl);  // planes 0 .. R-1: in the queues only
+
         for (int k = 0; k < t.tz; ++k) {
-            ok = wait_plane(k + 2 * R);
-            const S *newp = plane_ptr(k + 2 * R);
-            const S *cp = plane_ptr(k + R);
+            if (!__all_sync(0xffffffffu, wait_seq(seq + k + 2 * R))) {
+                if (lane == 0) atomicOr(p.err, 1);
+                return;
+            }
+            const S *newp = slot_ptr(seq + k + 2 * R);
+            const S *cp = slot_ptr(seq + k + R);
 #pragma unroll
             for (int r = 0; r < ROWS; ++r) {
                 A v[VX];
@@ -363,6 +358,9 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
                     for (int i = 0; i < 2 * R; ++i) q[r][c][i] = q[r][c][i + 1];
                 }
             }
+            // every read of the centre plane (and of the last R planes) is done
+            release(seq + k + R);
+            if (k >= t.tz - R) release(seq + k + 2 * R);
             S *o = op;
             op += f.plane;
             if (act) {
@@ -372,48 +370,40 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
                 for (int r = 0; r < ROWS; ++r)
                     if (r < nrow) V16<S>::st(o + r * f.px, out[r]);
             }
-            if (has_push) {
+            if (pmask) {
                 // ghost push: the same values into the neighbour boxes whose ghost faces hold them
+                uint32_t pm = pmask;
+                while (pm) {
+                    const int pi = __ffs(pm) - 1;
+                    pm &= pm - 1;
+                    const PushPiece pp = p.push[ts.pfirst + pi];
+                    if (k < pp.z0 || k >= pp.z0 + pp.nz) continue;
+                    const FabInfo &df = p.ftab[pp.dfab];
+                    S *base = (S *)p.dst[df.level] + pp.dst + t.comp * df.cstride + (long long)(k - pp.z0) * df.plane;
+                    const int x0c = ge - g;
 #pragma unroll
-                for (int r = 0; r < ROWS; ++r) {
-                    uint32_t pm = pmask_full[r] | ((k >= kpart_lo && k <= kpart_hi) ? pmask_part[r] : 0u);
-                    while (pm) {
-                        const int pi = __ffs(pm) - 1;
-                        pm &= pm - 1;
-                        const SPiece &sp = spc[pi];
-                        if (k < sp.z0 || k >= sp.z0 + sp.nz) continue;
-                        const int x0c = ge - g;
-                        S *gp = sp.base + (long long)(k - sp.z0) * sp.plane + (long long)(y0 + r - sp.y0) * sp.px +
-                                (x0c - sp.x0);
-                        if (sp.full_row && ((uintptr_t)gp & 15) == 0) {
+                    for (int r = 0; r < ROWS; ++r) {
+                        const int yy = y0 + r;
+                        if (r >= nrow || yy < pp.y0 || yy >= pp.y0 + pp.ny) continue;
+                        S *gp = base + (long long)(yy - pp.y0) * df.px + (x0c - pp.x0);
+                        if (pp.full_row && ((uintptr_t)gp & 15) == 0) {
                             V16<S>::st(gp, out[r]);
                         } else {
 #pragma unroll
                             for (int c = 0; c < VX; ++c) {
                                 const int x = x0c + c;
-                                if (x >= sp.x0 && x < sp.x0 + sp.nx) st(gp + c, out[r][c]);
+                                if (x >= pp.x0 && x < pp.x0 + pp.nx) st(gp + c, out[r][c]);
                             }
                         }
                     }
                 }
             }
-            if (!ok) { abort_flag = 1; atomicOr(p.err, 1); }
-            __syncthreads();  // every thread is done with the centre plane k + R
-            waited = k + 2 * R + 1;
-            if (abort_flag) break;
-            if (tid == 0 && issued < ntot) issue(issued++);
         }
-        if (abort_flag) {
-            // drain the copies this CTA issued for the tile (bounded waits), then stop
-            if (tid == 0)
-                for (int pl = waited; pl < issued; ++pl) wait_plane(pl);
-            break;
-        }
-        seq += (uint32_t)ntot;
+        seq += (uint32_t)(t.tz + 2 * R);
     }
 }
 
-template <int R> struct TmaRows { static constexpr int rows = R == 1 ? 4 : 2; };
+template <int R> struct TmaRows { static constexpr int rows = R == 4 ? 1 : 2; };
 
 template <typename S, typename A, int R>
 static cudaError_t tma_t(int nt, const StencilTmaParams &p, int grid, cudaStream_t s) {
