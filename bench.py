@@ -315,7 +315,7 @@ def run_ours(args, cfg, ws, rank, local):
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
            "config": workload_config(cfg), "roofline": roof, "gpu_launches": 2 * nsteps * args.steps,
-           "tile": list(tile)}
+           "tile": list(tile), "schedule": mf.mf_get_schedule(head.h)}
     out["config"]["l2"] = out["config"]["l2"] % (2 * mf.mf_bytes(head.h) / 2 / 1e6)
     out["clocks"] = clk.summary()
 

@@ -121,6 +121,10 @@ int mf_get_tile(const mf_t *mf, int tile[3]);
 enum { MF_KERNEL_TMA = 0, MF_KERNEL_GLOBAL = 1 };
 int mf_set_kernel(mf_t *mf, int variant);
 
+/* The schedule in use (after the autotuner, if it ran): {tile x, y, z, rows per thread, ring
+ * slots, kernel variant in use (MF_KERNEL_*)}. */
+int mf_get_schedule(const mf_t *mf, int out[6]);
+
 /*
  * Dense host arrays are (ncomp, Nz, Ny, Nx) doubles over the whole domain, x fastest.
  * mf_copy_from_host writes the valid cells of every box of the current time level

@@ -28,7 +28,7 @@ EXPORTS = [
     "mf_get_fb_regions", "mf_attach", "mf_set_tile", "mf_get_tile", "mf_copy_from_host", "mf_copy_to_host",
     "mf_copy_fab_to_host", "mf_copy_fab_from_host", "mf_fill_boundary", "mf_interp_cf", "mf_average_down",
     "mf_advance", "mf_amr_advance", "mf_sum", "mf_step_bytes", "mf_current", "mf_last_error", "mf_set_timing",
-    "mf_phase_ms", "mf_set_kernel", "mf_sum_strided_noalloc",
+    "mf_phase_ms", "mf_set_kernel", "mf_sum_strided_noalloc", "mf_get_schedule",
 ]
 
 
@@ -77,6 +77,7 @@ def _load():
         "mf_set_timing": (I, [P, I]),
         "mf_phase_ms": (I, [P, P]),
         "mf_set_kernel": (I, [P, I]),
+        "mf_get_schedule": (I, [P, P]),
         "mf_sum_strided_noalloc": (I, [P, I, I, I, I, LL, LL, ctypes.POINTER(D), P]),
     }
     for name, (res, args) in sig.items():
@@ -246,6 +247,13 @@ def mf_current(h):
 
 def mf_set_kernel(h, variant):
     _check(lib.mf_set_kernel(h, int(variant)))
+
+
+def mf_get_schedule(h):
+    out = np.zeros(6, dtype=np.int32)
+    _check(lib.mf_get_schedule(h, _ptr(out)))
+    return {"tile": tuple(int(v) for v in out[:3]), "rows": int(out[3]), "stages": int(out[4]),
+            "kernel": "tma" if out[5] == MF_KERNEL_TMA else "global"}
 
 
 def mf_set_timing(h, on):

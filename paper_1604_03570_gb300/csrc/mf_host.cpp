@@ -227,6 +227,8 @@ struct mf {
     int tma_R = 0;            // radius the maps were encoded for (0 = none)
     bool tma_ok = false;      // current tile shape fits the TMA kernel
     int tma_cpt = 32, tma_slot = 0, tma_ns = 0;  // tma_cpt: CTA threads of the TMA stencil
+    int tma_rows = 2;     // rows per consumer thread (autotuned; clipped to what the radius allows)
+    int tma_ns_pref = 0;  // ring slots (0: by radius; autotuned)
     int tma_main_slot = 0, tma_strip_rows = 0, tma_strip_bytes = 0, tma_strip_pitch = 0, tma_strip_w = 0;
     bool use_tma = true;
     double *h_sum = nullptr;       // pinned
@@ -860,7 +862,7 @@ static bool tma_geometry(mf_t *m, int R, std::vector<TmaFab> &tf, int &slot_byte
         // the TMA kernel streams whole rows (x = -g .. n0 + g and padding) of every plane; a thread
         // owns one 16-byte group in two consecutive rows
         if (t.x0 != 0 || t.tx != m->fabs[t.fab].n[0]) return false;
-        const int rows = tma_rows_per_thread(R);
+        const int rows = std::min(m->tma_rows, tma_max_rows(R));
         maxgroups = std::max(maxgroups, (m->fabs[t.fab].n[0] + 2 * g + A - 1) / A * (((int)t.ty + rows - 1) / rows));
     }
     for (size_t b = 0; b < m->fabs.size(); ++b) {
@@ -966,7 +968,8 @@ static int build_tma(mf_t *m, int R) {
     const int strip_bytes = XW * srows * S;
     const int strip_pitch = (strip_bytes + 127) / 128 * 128;
     const int slot = main_slot + 2 * strip_pitch;
-    int ns = R == 4 ? 16 : 8;  // ring slots (power of two)
+    int ns = m->tma_ns_pref ? m->tma_ns_pref : (R == 4 ? 16 : 8);  // ring slots (power of two)
+    if (ns < 2 * R + 1) ns = R == 4 ? 16 : 8;
     while (ns > 8 && (long long)ns * slot + 128 > 160 * 1024) ns /= 2;
     if (ns < 2 * R + 1 || (long long)ns * slot + 128 > 200 * 1024) return 0;
     auto encode = tensor_map_encoder();
@@ -1138,7 +1141,7 @@ static int enqueue_stencil(mf_t *m, int from, int R, bool fp64diff, const double
         p.strip_w = m->tma_strip_w;
         p.push = (push && m->tma_push) ? (const PushPiece *)m->d_push.p : nullptr;
         for (int c = 0; c < m->ncomp; ++c) p.lam[0][c] = lam[c];
-        CU(launch_stencil_tma(m->dtype, R, fp64diff, m->tma_cpt, p, 0, s));
+        CU(launch_stencil_tma(m->dtype, R, fp64diff, std::min(m->tma_rows, tma_max_rows(R)), m->tma_cpt, p, 0, s));
         return 0;
     }
     StencilParams p = stencil_params(m, from, lam);
@@ -1175,15 +1178,31 @@ static int check_stencil(const mf_t *m, const mf_stencil *st, double dt, double 
 
 // Autotune: time every candidate tile shape on the live data (current -> other level, which
 // is scratch at this point) and keep the fastest.  Synchronous; runs once per handle.
+// Autotune: time every candidate schedule -- tile shape, and for the TMA kernel rows per
+// thread and ring depth -- on the live data (current -> other level, which is scratch at this
+// point) and keep the fastest.  Synchronous; runs once per handle.
 static int autotune(mf_t *m, int R, bool fp64diff, const double *lam) {
-    auto cands = tile_candidates(m);
+    auto tiles = tile_candidates(m);
+    struct Cand { std::array<int, 3> t; int rows, ns; };
+    std::vector<Cand> cands;
+    for (auto &t : tiles) {
+        if (m->use_tma && t[0] == 0) {
+            for (int rows = 1; rows <= tma_max_rows(R); ++rows)
+                for (int ns : {4, 8, 16})
+                    if (ns >= 2 * R + 1) cands.push_back({t, rows, ns});
+        } else {
+            cands.push_back({t, 2, 0});
+        }
+    }
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
     float best = 1e30f;
-    std::array<int, 3> best_t = {0, 0, 0};
-    for (auto &t : cands) {
-        int rc = set_tiles(m, t.data());
+    Cand bc = cands.front();
+    for (auto &c : cands) {
+        m->tma_rows = c.rows;
+        m->tma_ns_pref = c.ns;
+        int rc = set_tiles(m, c.t.data());
         if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
         // warm-up (also encodes the tensor maps), then 3 timed launches
         if ((rc = enqueue_stencil(m, m->cur, R, fp64diff, lam, m->stream))) return rc;
@@ -1194,12 +1213,23 @@ static int autotune(mf_t *m, int R, bool fp64diff, const double *lam) {
         CU(cudaEventSynchronize(e1));
         float ms = 0;
         CU(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) { best = ms; best_t = t; }
+        if (ms < best) { best = ms; bc = c; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     m->tile_auto = false;
-    return set_tiles(m, best_t.data());
+    m->tma_rows = bc.rows;
+    m->tma_ns_pref = bc.ns;
+    return set_tiles(m, bc.t.data());
+}
+
+extern "C" int mf_get_schedule(const mf_t *m, int out[6]) {
+    if (!m || !out) return fail(MF_EINVAL, "null argument");
+    for (int d = 0; d < 3; ++d) out[d] = m->tile[d];
+    out[3] = m->tma_rows;
+    out[4] = m->tma_ns;
+    out[5] = (m->use_tma && m->tma_ok) ? MF_KERNEL_TMA : MF_KERNEL_GLOBAL;
+    return 0;
 }
 
 static std::string graph_key(const char *what, int R, bool fp64diff, const double *lam, int nc, int nsteps, int from) {

@@ -156,10 +156,10 @@ struct StencilTmaParams {
 };
 
 // ---- launchers (mf_kernels.cu, stencil_tma.cu); all asynchronous on `s`
-cudaError_t launch_stencil_tma(int dtype, int R, bool fp64diff, int nt, const StencilTmaParams &p, int grid,
+cudaError_t launch_stencil_tma(int dtype, int R, bool fp64diff, int rows, int nt, const StencilTmaParams &p, int grid,
                                cudaStream_t s);
 int tma_max_threads(int R);      // largest CTA of the TMA stencil for radius R
-int tma_rows_per_thread(int R);  // rows of one 16-byte group a TMA stencil thread computes
+int tma_max_rows(int R);         // most rows of one 16-byte group a TMA stencil thread may compute
 cudaError_t launch_fill(int dtype, const LevelPtrs &lv, const FbTask *tasks, int ntasks, int grid, cudaStream_t s);
 cudaError_t launch_stencil(int dtype, int R, bool fp64diff, const StencilParams &p, int bx, int by, int grid,
                            cudaStream_t s);

@@ -403,13 +403,11 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
     }
 }
 
-template <int R> struct TmaRows { static constexpr int rows = R == 4 ? 1 : 2; };
-
-template <typename S, typename A, int R>
+template <typename S, typename A, int R, int ROWS>
 static cudaError_t tma_t(int nt, const StencilTmaParams &p, int grid, cudaStream_t s) {
-    if (nt < 32 || nt > TmaBounds<R>::threads || nt % 32) return cudaErrorInvalidValue;
+    if (nt < 64 || nt > TmaBounds<R>::threads || nt % 32) return cudaErrorInvalidValue;
     const int smem = p.nstages * p.slot_bytes + 128;
-    auto kern = k_stencil_tma<S, A, R, TmaRows<R>::rows>;
+    auto kern = k_stencil_tma<S, A, R, ROWS>;
     static int configured = 0;
     if (smem > configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -430,28 +428,32 @@ static cudaError_t tma_t(int nt, const StencilTmaParams &p, int grid, cudaStream
 }
 
 template <typename S, typename A>
-static cudaError_t tma_r(int R, int nt, const StencilTmaParams &p, int grid, cudaStream_t s) {
-    switch (R) {
-        case 1: return tma_t<S, A, 1>(nt, p, grid, s);
-        case 2: return tma_t<S, A, 2>(nt, p, grid, s);
-        case 4: return tma_t<S, A, 4>(nt, p, grid, s);
+static cudaError_t tma_r(int R, int rows, int nt, const StencilTmaParams &p, int grid, cudaStream_t s) {
+    switch (R * 4 + rows) {
+        case 1 * 4 + 1: return tma_t<S, A, 1, 1>(nt, p, grid, s);
+        case 1 * 4 + 2: return tma_t<S, A, 1, 2>(nt, p, grid, s);
+        case 2 * 4 + 1: return tma_t<S, A, 2, 1>(nt, p, grid, s);
+        case 2 * 4 + 2: return tma_t<S, A, 2, 2>(nt, p, grid, s);
+        case 4 * 4 + 1: return tma_t<S, A, 4, 1>(nt, p, grid, s);
     }
     return cudaErrorInvalidValue;
 }
 
 int tma_max_threads(int R) { return R == 1 ? TmaBounds<1>::threads : R == 2 ? TmaBounds<2>::threads : TmaBounds<4>::threads; }
-int tma_rows_per_thread(int R) { return R == 1 ? TmaRows<1>::rows : R == 2 ? TmaRows<2>::rows : TmaRows<4>::rows; }
+int tma_max_rows(int R) { return R == 4 ? 1 : 2; }
 
-cudaError_t launch_stencil_tma(int dtype, int R, bool fp64diff, int nt, const StencilTmaParams &p, int grid,
+cudaError_t launch_stencil_tma(int dtype, int R, bool fp64diff, int rows, int nt, const StencilTmaParams &p, int grid,
                                cudaStream_t s) {
     if (p.ntiles == 0) return cudaSuccess;
-    if (p.nstages > kMaxStages || p.nstages < R + 2 || (p.nstages & (p.nstages - 1))) return cudaErrorInvalidValue;
+    if (p.nstages > kMaxStages || p.nstages < 2 * R + 1 || (p.nstages & (p.nstages - 1))) return cudaErrorInvalidValue;
+    if (rows < 1 || rows > tma_max_rows(R)) return cudaErrorInvalidValue;
     switch (dtype) {
-        case F64: return tma_r<double, double>(R, nt, p, grid, s);
-        case F32: return fp64diff ? tma_r<float, double>(R, nt, p, grid, s) : tma_r<float, float>(R, nt, p, grid, s);
+        case F64: return tma_r<double, double>(R, rows, nt, p, grid, s);
+        case F32:
+            return fp64diff ? tma_r<float, double>(R, rows, nt, p, grid, s) : tma_r<float, float>(R, rows, nt, p, grid, s);
         case BF16:
-            return fp64diff ? tma_r<__nv_bfloat16, double>(R, nt, p, grid, s)
-                            : tma_r<__nv_bfloat16, float>(R, nt, p, grid, s);
+            return fp64diff ? tma_r<__nv_bfloat16, double>(R, rows, nt, p, grid, s)
+                            : tma_r<__nv_bfloat16, float>(R, rows, nt, p, grid, s);
     }
     return cudaErrorInvalidValue;
 }
