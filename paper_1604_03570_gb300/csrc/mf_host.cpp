@@ -261,13 +261,12 @@ static void build_layout(mf_t *m) {
     for (auto &b : m->boxes) {
         FabInfo f{};
         for (int d = 0; d < 3; ++d) { f.n[d] = b.len(d); f.lo[d] = b.lo[d]; }
-        // a row starts at its first ghost cell (x = -g) on a 32-byte sector boundary and its pitch
-        // is a whole number of sectors: rows lie back to back with little padding (DRAM pages
-        // stay dense), a whole-row TMA load starts aligned, and whole rows are written in whole
-        // sectors
-        const int AS = 32 / S;
-        const int fpad = 0;
-        f.px = (int)(((long long)f.n[0] + 2 * g + AS - 1) / AS * AS);
+        // rows lie back to back at a pitch of whole 32-byte sectors (dense DRAM pages, aligned
+        // whole-row TMA loads); the left ghost cells are padded to a whole 16-byte chunk so that
+        // valid x = 0 sits on a 16-byte boundary (aligned vector access of the valid cells)
+        const int AS = 32 / S, A16 = 16 / S;
+        const int fpad = (A16 - g % A16) % A16;
+        f.px = (int)(((long long)fpad + f.n[0] + 2 * g + AS - 1) / AS * AS);
         const long long py = f.n[1] + 2 * g, nzg = f.n[2] + 2 * g;
         f.plane = (long long)f.px * py;
         f.cstride = f.plane * nzg;
@@ -863,7 +862,7 @@ static bool tma_geometry(mf_t *m, int R, std::vector<TmaFab> &tf, int &slot_byte
         // owns one 16-byte group in two consecutive rows
         if (t.x0 != 0 || t.tx != m->fabs[t.fab].n[0]) return false;
         const int rows = std::min(m->tma_rows, tma_max_rows(R));
-        maxgroups = std::max(maxgroups, (m->fabs[t.fab].n[0] + 2 * g + A - 1) / A * (((int)t.ty + rows - 1) / rows));
+        maxgroups = std::max(maxgroups, (m->fabs[t.fab].n[0] + A - 1) / A * (((int)t.ty + rows - 1) / rows));
     }
     for (size_t b = 0; b < m->fabs.size(); ++b) {
         int ty = 1;
@@ -872,6 +871,7 @@ static bool tma_geometry(mf_t *m, int R, std::vector<TmaFab> &tf, int &slot_byte
         tf[b].bx = m->fabs[b].px;
         tf[b].by = ty + 2 * R;
         tf[b].ngrow = g;
+        tf[b].xv = (g + A - 1) / A * A;  // row element of valid x = 0
         if (tf[b].bx > 256 || tf[b].by > 256) return false;
         maxplane = std::max(maxplane, tf[b].bx * tf[b].by * S);
     }
@@ -929,15 +929,16 @@ static void find_strips(mf_t *m, int R, std::vector<TileStrip> &st, std::vector<
             const Box &Ab = m->boxes[owner];
             const int nA = Ab.len(0);
             // strip: XW elements of the owner's rows, starting 16-byte aligned at or before the R
-            // cells next to the face (row element of cell x is g + x)
-            const int start = side == 0 ? (g + nA - R) / A * A : g / A * A;
+            // cells next to the face (row element of cell x is xv + x)
+            const int xvA = (g + A - 1) / A * A;
+            const int start = side == 0 ? (xvA + nA - R) / A * A : xvA;
             const int y = g + q.lo[1] - Ab.lo[1], z = g + q.lo[2] - Ab.lo[2];
             if (side == 0) {
                 st[w].lfab = owner; st[w].lx = start; st[w].ly = y; st[w].lz = z;
-                st[w].lidx0 = g + nA - start;
+                st[w].lidx0 = xvA + nA - start;
             } else {
                 st[w].rfab = owner; st[w].rx = start; st[w].ry = y; st[w].rz = z;
-                st[w].ridx0 = g - start;
+                st[w].ridx0 = xvA - start;
             }
         }
     }

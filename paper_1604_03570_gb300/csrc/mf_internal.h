@@ -106,9 +106,9 @@ constexpr int kMaxStages = 16;
 constexpr int kMaxPush = 16;  // ghost-push pieces per tile
 
 struct TmaFab {
-    int bx, by;   // box of one plane load: the whole row (bx elements from x = -g), by rows
+    int bx, by;   // box of one plane load: the whole row (bx elements, the row pitch), by rows
     int ngrow;
-    int pad_;
+    int xv;       // row element of valid x = 0 (16-byte aligned)
 };
 
 // x halo of a tile taken straight from the neighbouring box (its valid cells), or -1 when

@@ -203,27 +203,27 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
         const Tile t = p.tiles[w];
         const TmaFab tf = p.tfab[t.fab];
         const FabInfo f = p.ftab[t.fab];
-        const int g = tf.ngrow;
-        const int bx = tf.bx;  // whole row: x = -g at element 0
+        const int xv = tf.xv;  // row element of valid x = 0
+        const int bx = tf.bx;  // whole row
         TileStrip ts;
         ts.lfab = ts.rfab = -1;
         ts.pcount = 0;
         if (p.strips) ts = p.strips[w];
         if (!p.push) ts.pcount = 0;
 
-        const int ngx = (f.n[0] + 2 * g + VX - 1) / VX;
+        // groups of valid cells: x0c = VX * gx .. + VX - 1 at row element xv + x0c
+        const int ngx = (f.n[0] + VX - 1) / VX;
         const int nset = (t.ty + ROWS - 1) / ROWS;
         const bool act = ctid < ngx * nset;
-        const int ge = act ? (ctid % ngx) * VX : 0;
+        const int x0c = act ? (ctid % ngx) * VX : 0;
         const int y0 = act ? ROWS * (ctid / ngx) : 0;
         const int nrow = act ? min(ROWS, t.ty - y0) : 0;  // rows of the set that exist
-        const int soff = (y0 + R) * bx + ge;             // smem offset of the first row's group
+        const int soff = (y0 + R) * bx + xv + x0c;       // smem offset of the first row's group
 
         // ghost-push pieces touching this thread's rows
         uint32_t pmask = 0u;
         for (int pi = 0; pi < ts.pcount; ++pi) {
             const PushPiece pp = p.push[ts.pfirst + pi];
-            const int x0c = ge - g;
             const bool hit = act && y0 + nrow > pp.y0 && y0 < pp.y0 + pp.ny &&
                              (pp.full_row || (x0c < pp.x0 + pp.nx && x0c + VX > pp.x0));
             if (hit) pmask |= 1u << pi;
@@ -243,27 +243,32 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
             auto src = [&](int x, int r) -> int {
                 if (x < 0 && x >= -R && ts.lfab >= 0) return lso + (y0 + r) * xw + ts.lidx0 + x;
                 if (x >= n0 && x < n0 + R && ts.rfab >= 0) return rso + (y0 + r) * xw + ts.ridx0 + (x - n0);
-                return (y0 + r + R) * bx + min(max(x + g, 0), bx - 1);
+                return (y0 + r + R) * bx + min(max(x + xv, 0), bx - 1);
             };
 #pragma unroll
             for (int r = 0; r < ROWS; ++r) {
 #pragma unroll
                 for (int i = 0; i < R; ++i) {
-                    hl[r][i] = src(ge - g - R + i, r);
-                    hr[r][i] = src(ge - g + VX + i, r);
+                    hl[r][i] = src(x0c - R + i, r);
+                    hr[r][i] = src(x0c + VX + i, r);
                 }
             }
 #pragma unroll
             for (int c = 0; c < VX; ++c) {
-                const int x = ge - g + c;
+                const int x = x0c + c;
                 const bool strip = (x < 0 && x >= -R && ts.lfab >= 0) || (x >= n0 && x < n0 + R && ts.rfab >= 0);
 #pragma unroll
                 for (int r = 0; r < ROWS; ++r) co[r][c] = src(x, r);
                 if (strip) cov |= 1u << c;
             }
         }
-        S *op = (S *)p.dst[f.level] + f.org - g + t.comp * f.cstride + (long long)t.z0 * f.plane +
-                (long long)(t.y0 + y0) * f.px + ge;
+        S *op = (S *)p.dst[f.level] + f.org + t.comp * f.cstride + (long long)t.z0 * f.plane +
+                (long long)(t.y0 + y0) * f.px + x0c;
+        // the groups at the row ends also complete the sectors they share with ghost / padding
+        // cells, writing don't-care values there (strips, not those cells, feed the stencil)
+        const bool full = x0c + VX <= f.n[0];
+        const bool lpad = act && x0c == 0 && xv >= VX && ((f.org - xv) * (long long)sizeof(S)) % 32 == 0;
+        const bool rpad = act && full && x0c + VX == f.n[0] && xv + f.n[0] + VX <= f.px;
         const A lam = (A)p.lam[f.level][t.comp];
 
         A q[ROWS][VX][2 * R + 1];  // z queue per cell: q[r][c][i] = u(z - R + i)
@@ -364,11 +369,20 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
             S *o = op;
             op += f.plane;
             if (act) {
-                // whole 16-byte groups: valid cells plus don't-care values in ghost / padding
-                // positions, so rows are written in whole sectors
 #pragma unroll
-                for (int r = 0; r < ROWS; ++r)
-                    if (r < nrow) V16<S>::st(o + r * f.px, out[r]);
+                for (int r = 0; r < ROWS; ++r) {
+                    if (r >= nrow) continue;
+                    S *orow = o + r * f.px;
+                    if (full) {
+                        V16<S>::st(orow, out[r]);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < VX; ++c)
+                            if (x0c + c < f.n[0]) st(orow + c, out[r][c]);
+                    }
+                    if (lpad) V16<S>::st(orow - VX, out[r]);
+                    if (rpad) V16<S>::st(orow + VX, out[r]);
+                }
             }
             if (pmask) {
                 // ghost push: the same values into the neighbour boxes whose ghost faces hold them
@@ -380,13 +394,12 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
                     if (k < pp.z0 || k >= pp.z0 + pp.nz) continue;
                     const FabInfo &df = p.ftab[pp.dfab];
                     S *base = (S *)p.dst[df.level] + pp.dst + t.comp * df.cstride + (long long)(k - pp.z0) * df.plane;
-                    const int x0c = ge - g;
 #pragma unroll
                     for (int r = 0; r < ROWS; ++r) {
                         const int yy = y0 + r;
                         if (r >= nrow || yy < pp.y0 || yy >= pp.y0 + pp.ny) continue;
                         S *gp = base + (long long)(yy - pp.y0) * df.px + (x0c - pp.x0);
-                        if (pp.full_row && ((uintptr_t)gp & 15) == 0) {
+                        if (pp.full_row && full && ((uintptr_t)gp & 15) == 0) {
                             V16<S>::st(gp, out[r]);
                         } else {
 #pragma unroll
