@@ -121,8 +121,20 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 // ROWS consecutive rows of the tile and marches it along z with a register queue.  There is
 // no CTA-wide barrier inside the loop, so consumers run ahead as far as the loaded planes
 // allow, and the producer starts on the next tile while the consumers finish this one.
+// Where the tile's new values are also ghost cells of neighbouring boxes (ghost push), each
+// consumer warp keeps the tile's push pieces in a small shared-memory table, written once per
+// tile, and tests a piece's z range before touching it.
 // The CTA has 32 + (consumer groups rounded up to a warp) threads.
 template <int R> struct TmaBounds { static constexpr int threads = R == 4 ? 416 : 544; };
+
+// One ghost-push piece as a consumer warp keeps it (see the tile prologue).
+struct PushRec {
+    unsigned long long base;  // byte address of tile cell (0, 0, 0) in the destination
+    long long plane;          // destination plane stride (elements)
+    int px;                   // destination row pitch (elements)
+    uint32_t zr, yr, xr;      // [lo, hi) ranges relative to the tile, packed lo | hi << 16
+};
+
 
 template <typename S, typename A, int R, int ROWS>
 __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __grid_constant__ StencilTmaParams p) {
@@ -133,6 +145,7 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
     const int NS = p.nstages;  // power of two
     const int tid = threadIdx.x;
     const int ncw = (int)(blockDim.x >> 5) - 1;  // consumer warps
+    __shared__ PushRec ptab[TmaBounds<R>::threads / 32 - 1][kMaxPush];  // per consumer warp
     if (*(volatile int *)p.err) return;          // an earlier launch already failed: do nothing
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
@@ -187,6 +200,7 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
 
     // ------------------------------------------------------------------ consumers
     const int ctid = tid - 32;
+    const int cw = ctid >> 5;  // consumer warp
     const int lane = tid & 31;
     uint32_t seq = 0;
     auto wait_seq = [&](uint32_t sq) -> bool {
@@ -220,22 +234,46 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
         const int nrow = act ? min(ROWS, t.ty - y0) : 0;  // rows of the set that exist
         const int soff = (y0 + R) * bx + xv + x0c;       // smem offset of the first row's group
 
-        // ghost-push pieces touching this thread's rows
+        // Ghost-push pieces of the tile, in the warp's own table: lane i writes piece i
+        // (destination address of tile cell (0, 0, 0), plane stride, row pitch, and the piece's
+        // z, y and x ranges relative to the tile, x packed with the full-row flag in bit 31).
+        // pmask: the pieces touching this thread's cells, wm: the union over the warp.
+        PushRec *ptw = ptab[cw];
+        __syncwarp();  // the warp's previous tile is done with the table
+        if (lane < ts.pcount) {
+            const PushPiece pp = p.push[ts.pfirst + lane];
+            const FabInfo df = p.ftab[pp.dfab];
+            const long long off = pp.dst + t.comp * df.cstride - pp.z0 * df.plane - pp.y0 * (long long)df.px - pp.x0;
+            PushRec pr;
+            pr.base = (unsigned long long)(uintptr_t)p.dst[df.level] + (unsigned long long)off * sizeof(S);
+            pr.plane = df.plane;
+            pr.px = df.px;
+            pr.zr = (uint32_t)pp.z0 | (uint32_t)(pp.z0 + pp.nz) << 16;
+            pr.yr = (uint32_t)pp.y0 | (uint32_t)(pp.y0 + pp.ny) << 16;
+            pr.xr = (uint32_t)pp.x0 | (uint32_t)(pp.x0 + pp.nx) << 16 | (pp.full_row ? 0x80000000u : 0u);
+            ptw[lane] = pr;
+        }
+        __syncwarp();
         uint32_t pmask = 0u;
         for (int pi = 0; pi < ts.pcount; ++pi) {
-            const PushPiece pp = p.push[ts.pfirst + pi];
-            const bool hit = act && y0 + nrow > pp.y0 && y0 < pp.y0 + pp.ny &&
-                             (pp.full_row || (x0c < pp.x0 + pp.nx && x0c + VX > pp.x0));
+            const uint32_t yr = ptw[pi].yr, xr = ptw[pi].xr;
+            const int py0 = (int)(yr & 0xffffu), py1 = (int)(yr >> 16);
+            const int px0 = (int)(xr & 0xffffu), px1 = (int)((xr >> 16) & 0x7fffu);
+            const bool hit = act && y0 + nrow > py0 && y0 < py1 && ((xr >> 31) || (x0c < px1 && x0c + VX > px0));
             if (hit) pmask |= 1u << pi;
         }
+        const uint32_t wm = __reduce_or_sync(0xffffffffu, pmask);
 
         // fixed for the tile: output pointer (advanced one plane per step) and the shared-memory
         // offset of every x-halo cell -- the loaded row for cells of the box (and for filled
         // ghost columns), the neighbour strip outside a strip-served face; cells that only feed
         // don't-care outputs (ghost and padding positions) read their own row
         int hl[ROWS][R], hr[ROWS][R];
-        int co[ROWS][VX];  // strip offsets for ghost cells inside the group next to a served face
+        // Groups start at valid x >= 0, so only cells past the right face (x >= n0) can sit in a
+        // group; where that face is strip-served, cell c of row r reads strip offset
+        // cob + r * strip_w + c instead of its own row.
         uint32_t cov = 0;  // bit c: cell c of the group takes its value from a strip (every row)
+        int cob = 0;
         {
             const int lso = p.strip_off / (int)sizeof(S), rso = (p.strip_off + p.strip_pitch) / (int)sizeof(S);
             const int xw = p.strip_w;
@@ -256,11 +294,9 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
 #pragma unroll
             for (int c = 0; c < VX; ++c) {
                 const int x = x0c + c;
-                const bool strip = (x < 0 && x >= -R && ts.lfab >= 0) || (x >= n0 && x < n0 + R && ts.rfab >= 0);
-#pragma unroll
-                for (int r = 0; r < ROWS; ++r) co[r][c] = src(x, r);
-                if (strip) cov |= 1u << c;
+                if (x >= n0 && x < n0 + R && ts.rfab >= 0) cov |= 1u << c;
             }
+            cob = rso + y0 * xw + ts.ridx0 + x0c - n0;
         }
         S *op = (S *)p.dst[f.level] + f.org + t.comp * f.cstride + (long long)t.z0 * f.plane +
                 (long long)(t.y0 + y0) * f.px + x0c;
@@ -269,6 +305,8 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
         const bool full = x0c + VX <= f.n[0];
         const bool lpad = act && x0c == 0 && xv >= VX && ((f.org - xv) * (long long)sizeof(S)) % 32 == 0;
         const bool rpad = act && full && x0c + VX == f.n[0] && xv + f.n[0] + VX <= f.px;
+        const int xo = lpad ? -VX : VX;  // the extra store of a row-end group
+        const bool both = __any_sync(0xffffffffu, lpad && rpad);  // one group spans the whole row
         const A lam = (A)p.lam[f.level][t.comp];
 
         A q[ROWS][VX][2 * R + 1];  // z queue per cell: q[r][c][i] = u(z - R + i)
@@ -310,8 +348,8 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
 #pragma unroll
                 for (int c = 0; c < VX; ++c) q[r][c][2 * R] = v[c];
             }
-            // y window per column: wy[m][c] = u(x + c, y0 - R + m), m = 0 .. 2R+ROWS-1 (the set's own
-            // rows from the queues, the rest from the centre plane)
+            // y window per column: wy[m][c] = u(x + c, y0 - R + m), m = 0 .. 2R+ROWS-1 (the set's
+            // own rows from the queues, the rest from the centre plane)
             A wy[2 * R + ROWS][VX];
             const S *cc = cp + soff;
 #pragma unroll
@@ -348,7 +386,7 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
                 if (cov) {  // the box face is inside this group: x neighbours from the strips
 #pragma unroll
                     for (int c = 0; c < VX; ++c)
-                        if (cov & (1u << c)) wx[R + c] = ld_smem<S, A>(cp + co[r][c]);
+                        if (cov & (1u << c)) wx[R + c] = ld_smem<S, A>(cp + cob + r * p.strip_w + c);
                 }
                 A fx[VX + 1];  // x-face fluxes: fx[c] is the face left of cell c
 #pragma unroll
@@ -380,32 +418,37 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
                         for (int c = 0; c < VX; ++c)
                             if (x0c + c < f.n[0]) st(orow + c, out[r][c]);
                     }
-                    if (lpad) V16<S>::st(orow - VX, out[r]);
-                    if (rpad) V16<S>::st(orow + VX, out[r]);
+                    if (lpad || rpad) V16<S>::st(orow + xo, out[r]);
+                    if (both && lpad && rpad) V16<S>::st(orow + VX, out[r]);
                 }
             }
-            if (pmask) {
+            if (wm) {
                 // ghost push: the same values into the neighbour boxes whose ghost faces hold them
-                uint32_t pm = pmask;
-                while (pm) {
-                    const int pi = __ffs(pm) - 1;
-                    pm &= pm - 1;
-                    const PushPiece pp = p.push[ts.pfirst + pi];
-                    if (k < pp.z0 || k >= pp.z0 + pp.nz) continue;
-                    const FabInfo &df = p.ftab[pp.dfab];
-                    S *base = (S *)p.dst[df.level] + pp.dst + t.comp * df.cstride + (long long)(k - pp.z0) * df.plane;
+                uint32_t m = wm;
+                while (m) {
+                    const int pi = __ffs(m) - 1;
+                    m &= m - 1;
+                    const uint32_t zr = ptw[pi].zr;
+                    if (k < (int)(zr & 0xffffu) || k >= (int)(zr >> 16) || !(pmask & (1u << pi))) continue;
+                    const unsigned long long b = ptw[pi].base;
+                    const long long dplane = ptw[pi].plane;
+                    const int dpx = ptw[pi].px;
+                    const uint32_t yr = ptw[pi].yr, xr = ptw[pi].xr;
+                    const int py0 = (int)(yr & 0xffffu), py1 = (int)(yr >> 16);
+                    const int px0 = (int)(xr & 0xffffu), px1 = (int)((xr >> 16) & 0x7fffu);
 #pragma unroll
                     for (int r = 0; r < ROWS; ++r) {
                         const int yy = y0 + r;
-                        if (r >= nrow || yy < pp.y0 || yy >= pp.y0 + pp.ny) continue;
-                        S *gp = base + (long long)(yy - pp.y0) * df.px + (x0c - pp.x0);
-                        if (pp.full_row && full && ((uintptr_t)gp & 15) == 0) {
+                        if (r >= nrow || yy < py0 || yy >= py1) continue;
+                        S *gp = (S *)(uintptr_t)(b + (unsigned long long)(k * dplane + (long long)yy * dpx + x0c) *
+                                                         sizeof(S));
+                        if ((xr >> 31) && full && ((uintptr_t)gp & 15) == 0) {
                             V16<S>::st(gp, out[r]);
                         } else {
 #pragma unroll
                             for (int c = 0; c < VX; ++c) {
                                 const int x = x0c + c;
-                                if (x >= pp.x0 && x < pp.x0 + pp.nx) st(gp + c, out[r][c]);
+                                if (x >= px0 && x < px1) st(gp + c, out[r][c]);
                             }
                         }
                     }
