@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -231,6 +232,12 @@ struct mf {
     int tma_ns_pref = 0;  // ring slots (0: by radius; autotuned)
     int tma_main_slot = 0, tma_strip_rows = 0, tma_strip_bytes = 0, tma_strip_pitch = 0, tma_strip_w = 0;
     bool use_tma = true;
+    // balanced schedule (tile z extent 0): CTA b of exactly tma_grid CTAs takes tiles
+    // [cta_tiles[b], cta_tiles[b + 1])
+    std::vector<int> cta_tiles;
+    DevBuf d_cta;
+    int tma_grid = 0;
+    unsigned long long gen = 0;    // changes whenever state baked into a captured graph changes
     double *h_sum = nullptr;       // pinned
     size_t tile_capacity = 0;
     std::map<std::string, std::unique_ptr<GraphExec>> graphs;
@@ -589,7 +596,14 @@ extern "C" double mf_step_bytes(const mf_t *m, int R) {
 
 // ------------------------------------------------------------------ attach
 
-static void invalidate_graphs(mf_t *m) { m->graphs.clear(); }
+// Graphs bake in kernel parameters (buffer addresses, ring geometry, tile counts).  Every
+// change of that state drops the handle's own graphs and takes a new generation number, which
+// is part of every graph key -- also of the two-level graphs another handle keeps.
+static std::atomic<unsigned long long> g_generation{0};
+static void invalidate_graphs(mf_t *m) {
+    m->graphs.clear();
+    m->gen = ++g_generation;
+}
 
 extern "C" int mf_attach(mf_t *m, void *dev_ptr, size_t bytes, void *stream) {
     if (!m) return fail(MF_EINVAL, "null handle");
@@ -950,11 +964,46 @@ static void find_strips(mf_t *m, int R, std::vector<TileStrip> &st, std::vector<
     }
 }
 
+// Balanced schedule for G CTAs: the tile shape's columns (its x and y extents, every plane of
+// the box) in order, each plane weighted by its cells, cut into G runs of equal weight; CTA b
+// takes the planes whose midpoints fall into run b, as one tile per column it touches.
+static void balance_tiles(const mf_t *m, int G, std::vector<Tile> &out, std::vector<int> &first) {
+    std::vector<Tile> cols;
+    const int shape[3] = {m->tile[0], m->tile[1], 0};
+    make_tiles(m, shape, cols);
+    double total = 0;
+    for (auto &c : cols) total += (double)c.tx * c.ty * c.tz;
+    out.clear();
+    first.assign((size_t)G + 1, 0);
+    double acc = 0;
+    int cur = 0;  // CTA of the last tile emitted
+    auto owner = [&](double at) { return std::min(G - 1, (int)(at * G / total)); };
+    for (auto &c : cols) {
+        const double a = (double)c.tx * c.ty;
+        for (int k = 0; k < c.tz;) {
+            const int b = owner(acc + (k + 0.5) * a);
+            int k1 = k + 1;
+            while (k1 < c.tz && owner(acc + (k1 + 0.5) * a) == b) ++k1;
+            while (cur < b) first[++cur] = (int)out.size();
+            Tile t = c;
+            t.z0 = (short)(c.z0 + k);
+            t.tz = (short)(k1 - k);
+            out.push_back(t);
+            k = k1;
+        }
+        acc += a * c.tz;
+    }
+    while (cur < G) first[++cur] = (int)out.size();
+}
+
 static int build_tma(mf_t *m, int R) {
+    invalidate_graphs(m);
     m->tma_ok = false;
     m->tma_strips = false;
     m->tma_push = false;
     m->tma_R = R;
+    m->tma_grid = 0;
+    m->cta_tiles.clear();
     if (!m->use_tma) return 0;
     const int S = m->esize, A = 16 / S;
     const int XW = (R + A - 1 + A - 1) / A * A;  // strip width: R cells from any 16-byte start
@@ -963,9 +1012,6 @@ static int build_tma(mf_t *m, int R) {
     std::vector<TmaFab> tf;
     int main_slot = 0, gpt = 0;
     if (!tma_geometry(m, R, tf, main_slot, gpt)) return 0;
-    std::vector<TileStrip> strips;
-    std::vector<char> served;
-    find_strips(m, R, strips, served);
     const int strip_bytes = XW * srows * S;
     const int strip_pitch = (strip_bytes + 127) / 128 * 128;
     const int slot = main_slot + 2 * strip_pitch;
@@ -973,6 +1019,27 @@ static int build_tma(mf_t *m, int R) {
     if (ns < 2 * R + 1) ns = R == 4 ? 16 : 8;
     while (ns > 8 && (long long)ns * slot + 128 > 160 * 1024) ns /= 2;
     if (ns < 2 * R + 1 || (long long)ns * slot + 128 > 200 * 1024) return 0;
+    if (m->tile[2] <= 0) {
+        // whole-box z extent: split the columns over exactly one wave of CTAs
+        const int rows = std::min(m->tma_rows, tma_max_rows(R));
+        const int per_sm = tma_ctas_per_sm(m->dtype, R, rows, gpt, ns * slot + 128);
+        if (per_sm < 1) return 0;
+        const int G = per_sm * sm_count();
+        balance_tiles(m, G, m->tiles, m->cta_tiles);
+        if (m->tiles.size() > m->tile_capacity) {
+            int rc = m->d_tiles.ensure(m->tiles.size() * sizeof(Tile));
+            if (rc) return rc;
+            m->tile_capacity = m->tiles.size();
+        }
+        CU(cudaMemcpyAsync(m->d_tiles.p, m->tiles.data(), m->tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice,
+                           m->stream));
+        int rc = m->d_cta.upload(m->cta_tiles, m->stream);
+        if (rc) return rc;
+        m->tma_grid = G;
+    }
+    std::vector<TileStrip> strips;
+    std::vector<char> served;
+    find_strips(m, R, strips, served);
     auto encode = tensor_map_encoder();
     if (!encode) return 0;
     const int nf = (int)m->fabs.size();
@@ -1141,8 +1208,10 @@ static int enqueue_stencil(mf_t *m, int from, int R, bool fp64diff, const double
         p.strip_pitch = m->tma_strip_pitch;
         p.strip_w = m->tma_strip_w;
         p.push = (push && m->tma_push) ? (const PushPiece *)m->d_push.p : nullptr;
+        p.cta_tiles = m->tma_grid ? (const int *)m->d_cta.p : nullptr;
         for (int c = 0; c < m->ncomp; ++c) p.lam[0][c] = lam[c];
-        CU(launch_stencil_tma(m->dtype, R, fp64diff, std::min(m->tma_rows, tma_max_rows(R)), m->tma_cpt, p, 0, s));
+        CU(launch_stencil_tma(m->dtype, R, fp64diff, std::min(m->tma_rows, tma_max_rows(R)), m->tma_cpt, p,
+                              m->tma_grid, s));
         return 0;
     }
     StencilParams p = stencil_params(m, from, lam);
@@ -1337,7 +1406,9 @@ extern "C" int mf_advance(mf_t *m, const mf_stencil *st, double dt, int nsteps) 
     }
     if (m->tile_auto && (rc = autotune(m, R, fp64diff, lam))) return rc;
     if (m->use_tma && m->tma_R != R && (rc = build_tma(m, R))) return rc;  // never inside a capture
-    const std::string key = graph_key(m->timing ? "advT" : "adv", R, fp64diff, lam, m->ncomp, nsteps, m->cur);
+    char kb[48];
+    snprintf(kb, sizeof kb, "%s|g%llu", m->timing ? "advT" : "adv", m->gen);
+    const std::string key = graph_key(kb, R, fp64diff, lam, m->ncomp, nsteps, m->cur);
     auto it = m->graphs.find(key);
     if (it == m->graphs.end()) {
         if (m->timing && (rc = ensure_events(m, 2 * nsteps + 1))) return rc;
@@ -1590,8 +1661,9 @@ extern "C" int mf_amr_advance(mf_t *crse, mf_t *fine, const mf_stencil *st, doub
     if (fine->use_tma && fine->tma_R != R && (rc = build_tma(fine, R))) return rc;
     // the coarse stream orders everything; the fine stream waits for nothing else (same
     // stream expected); capture the whole advance into one graph
-    char buf[96];
-    snprintf(buf, sizeof buf, "amr|%p|s%d|r%d|fc%d", (void *)fine, nsub, ratio, fine->cur);
+    char buf[160];
+    snprintf(buf, sizeof buf, "amr|%p|g%llu|g%llu|s%d|r%d|fc%d", (void *)fine, crse->gen, fine->gen, nsub, ratio,
+             fine->cur);
     const std::string key = graph_key(buf, R, fp64diff, lam_c, crse->ncomp, ncrse_steps, crse->cur);
     auto it = crse->graphs.find(key);
     if (it == crse->graphs.end()) {

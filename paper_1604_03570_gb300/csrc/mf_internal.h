@@ -144,6 +144,7 @@ struct StencilTmaParams {
     const TmaFab *tfab;
     const FabInfo *ftab;
     const Tile *tiles;
+    const int *cta_tiles;      // CTA b takes tiles [cta_tiles[b], cta_tiles[b+1]); nullptr: tiles b, b + grid, ...
     int ntiles;
     int nstages;               // shared-memory ring slots (power of two)
     int nstages_log2;
@@ -160,6 +161,8 @@ cudaError_t launch_stencil_tma(int dtype, int R, bool fp64diff, int rows, int nt
                                cudaStream_t s);
 int tma_max_threads(int R);      // largest CTA of the TMA stencil for radius R
 int tma_max_rows(int R);         // most rows of one 16-byte group a TMA stencil thread may compute
+// resident CTAs per SM of the TMA stencil with nt threads and smem dynamic shared bytes (0: none)
+int tma_ctas_per_sm(int dtype, int R, int rows, int nt, int smem);
 cudaError_t launch_fill(int dtype, const LevelPtrs &lv, const FbTask *tasks, int ntasks, int grid, cudaStream_t s);
 cudaError_t launch_stencil(int dtype, int R, bool fp64diff, const StencilParams &p, int bx, int by, int grid,
                            cudaStream_t s);

@@ -18,6 +18,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "mf_internal.h"
@@ -156,12 +157,19 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
+    // this CTA's tiles: its own range of a balanced schedule, else every gridDim.x-th tile
+    int w0 = blockIdx.x, w1 = p.ntiles, ws = gridDim.x;
+    if (p.cta_tiles) {
+        w0 = p.cta_tiles[blockIdx.x];
+        w1 = p.cta_tiles[blockIdx.x + 1];
+        ws = 1;
+    }
 
     if (tid < 32) {
         // ------------------------------------------------------------------ producer
         if (tid != 0) return;
         uint32_t seq = 0;
-        for (int w = blockIdx.x; w < p.ntiles; w += gridDim.x) {
+        for (int w = w0; w < w1; w += ws) {
             const Tile t = p.tiles[w];
             const TmaFab tf = p.tfab[t.fab];
             TileStrip ts;
@@ -213,7 +221,7 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[sq & (uint32_t)(NS - 1)]);
     };
-    for (int w = blockIdx.x; w < p.ntiles; w += gridDim.x) {
+    for (int w = w0; w < w1; w += ws) {
         const Tile t = p.tiles[w];
         const TmaFab tf = p.tfab[t.fab];
         const FabInfo f = p.ftab[t.fab];
@@ -332,7 +340,10 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
         for (int r = 0; r < ROWS; ++r)
 #pragma unroll
             for (int c = 0; c < VX; ++c) fzm[r][c] = face_flux<A, R>(q[r][c], R - 1);
-        for (int pl = 0; pl < R; ++pl) release(seq + pl);  // planes 0 .. R-1: in the queues only
+        // planes 0 .. R-1 live on in the queues only; so do planes tz + R .. 2R - 1 of a tile
+        // thinner than R (never a centre plane, and below the planes the z loop releases)
+        for (int pl = 0; pl < 2 * R; ++pl)
+            if (pl < R || pl >= t.tz + R) release(seq + pl);
 
         for (int k = 0; k < t.tz; ++k) {
             if (!__all_sync(0xffffffffu, wait_seq(seq + k + 2 * R))) {
@@ -459,17 +470,26 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
     }
 }
 
+// Raise the kernel's dynamic shared-memory limit to at least smem (never lowers it).
+template <typename S, typename A, int R, int ROWS>
+static cudaError_t tma_configure(int smem) {
+    static int configured = 0;
+    if (smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_stencil_tma<S, A, R, ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    return cudaSuccess;
+}
+
 template <typename S, typename A, int R, int ROWS>
 static cudaError_t tma_t(int nt, const StencilTmaParams &p, int grid, cudaStream_t s) {
     if (nt < 64 || nt > TmaBounds<R>::threads || nt % 32) return cudaErrorInvalidValue;
     const int smem = p.nstages * p.slot_bytes + 128;
     auto kern = k_stencil_tma<S, A, R, ROWS>;
-    static int configured = 0;
-    if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        configured = smem;
-    }
+    cudaError_t e = tma_configure<S, A, R, ROWS>(smem);
+    if (e != cudaSuccess) return e;
     int g = grid;
     if (g <= 0) {
         int per_sm = 0;
@@ -493,6 +513,47 @@ static cudaError_t tma_r(int R, int rows, int nt, const StencilTmaParams &p, int
         case 4 * 4 + 1: return tma_t<S, A, 4, 1>(nt, p, grid, s);
     }
     return cudaErrorInvalidValue;
+}
+
+template <typename S, typename A, int R, int ROWS>
+static int tma_occ(int nt, int smem) {
+    if (nt < 64 || nt > TmaBounds<R>::threads || nt % 32) return 0;
+    if (tma_configure<S, A, R, ROWS>(smem) != cudaSuccess) return 0;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stencil_tma<S, A, R, ROWS>, nt, smem) != cudaSuccess)
+        return 0;
+    return per_sm;
+}
+
+// Residency of the storage type's two instantiations (FP64 differences or not): the smaller,
+// so that one schedule fits both in one wave.
+template <typename S> struct NativeArith { using T = S; };  // bf16 values compute in FP32
+template <> struct NativeArith<__nv_bfloat16> { using T = float; };
+
+template <typename S, int R, int ROWS>
+static int tma_occ2(int nt, int smem) {
+    return std::min(tma_occ<S, typename NativeArith<S>::T, R, ROWS>(nt, smem), tma_occ<S, double, R, ROWS>(nt, smem));
+}
+
+template <typename S>
+static int tma_occ_r(int R, int rows, int nt, int smem) {
+    switch (R * 4 + rows) {
+        case 1 * 4 + 1: return tma_occ2<S, 1, 1>(nt, smem);
+        case 1 * 4 + 2: return tma_occ2<S, 1, 2>(nt, smem);
+        case 2 * 4 + 1: return tma_occ2<S, 2, 1>(nt, smem);
+        case 2 * 4 + 2: return tma_occ2<S, 2, 2>(nt, smem);
+        case 4 * 4 + 1: return tma_occ2<S, 4, 1>(nt, smem);
+    }
+    return 0;
+}
+
+int tma_ctas_per_sm(int dtype, int R, int rows, int nt, int smem) {
+    switch (dtype) {
+        case F64: return tma_occ_r<double>(R, rows, nt, smem);
+        case F32: return tma_occ_r<float>(R, rows, nt, smem);
+        case BF16: return tma_occ_r<__nv_bfloat16>(R, rows, nt, smem);
+    }
+    return 0;
 }
 
 int tma_max_threads(int R) { return R == 1 ? TmaBounds<1>::threads : R == 2 ? TmaBounds<2>::threads : TmaBounds<4>::threads; }
