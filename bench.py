@@ -180,11 +180,17 @@ def cpu_baseline(cfg, budget_s=15.0):
 
 # ------------------------------------------------------------------ our arm
 
-def src_hash():
+KERNEL_SOURCES = {
+    "k_stencil_tma": ["stencil_tma.cu", "stencil_common.cuh", "mf_internal.h"],
+    "k_stencil": ["mf_kernels.cu", "stencil_common.cuh", "mf_internal.h"],
+}
+
+
+def src_hash(kernel):
     h = hashlib.sha256()
-    p = os.path.join(ROOT, "paper_1604_03570_gb300", "csrc", "mf_kernels.cu")
-    with open(p, "rb") as f:
-        h.update(f.read())
+    for name in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_1604_03570_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
@@ -198,7 +204,7 @@ def traffic_for(kernel, workload_key, dtype):
     except (OSError, ValueError):
         return None
     rec = t.get("%s|%s|%s" % (kernel, workload_key, dtype))
-    if not rec or rec.get("src_sha") != src_hash():
+    if not rec or rec.get("src_sha") != src_hash(kernel):
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -209,6 +215,18 @@ def measured_peaks():
             return json.load(f), "measured"
     except (OSError, ValueError):
         return {"hbm_gbs": 6800.0}, "fallback"
+
+
+# floating-point operations per cell of one flux-form update: 3 face fluxes per cell (each face
+# is shared by two cells; radius 1: one subtraction, radius R > 1: R subtractions, R
+# multiplications, R - 1 additions), 5 additions for the divergence, one multiply-add
+FLOPS_PER_CELL = {1: 3 * 1 + 5 + 2, 2: 3 * (3 * 2 - 1) + 5 + 2, 4: 3 * (3 * 4 - 1) + 5 + 2}
+
+
+def fp64_peak_tflops():
+    """FP64 FMA throughput of this GPU, measured by the library's DFMA loop."""
+    import paper_1604_03570_gb300 as mf
+    return mf.mf_fp64_fma_rate()
 
 
 def time_advances(mfab, R, D, dt, nsteps, K, flush, flags=0):
@@ -276,7 +294,12 @@ def run_ours(args, cfg, ws, rank, local):
     value = ws * V * nsteps * args.steps / (total_ms * 1e-3)
     tile, _ = mf.mf_get_tile(head.h)
 
-    # ---- roofline of the dominant kernel (stencil) from events inside the graph
+    launches = mf.mf_launch_count(head.h)  # of one mf_advance (the graph replayed every bench step)
+    sched = mf.mf_get_schedule(head.h)
+    kname = "k_stencil_tma" if sched["kernel"] == "tma" else "k_stencil"
+
+    # ---- roofline of the dominant kernel (stencil): events inside the graph wherever the kind
+    # of launch changes, so the back-to-back stencil launches are timed without nodes between
     mf.mf_set_timing(head.h, 1)
     for _ in range(2):
         mf.mf_advance(head.h, R, D, dt, nsteps)
@@ -288,34 +311,70 @@ def run_ours(args, cfg, ws, rank, local):
         fill_ms += a
         st_ms += b
     mf.mf_set_timing(head.h, 0)
-    launches = args.steps * nsteps
-    st_avg_s = st_ms * 1e-3 / launches
-    fill_avg_s = fill_ms * 1e-3 / launches
+    st_avg_s = st_ms * 1e-3 / (launches["stencil"] * args.steps)
     S = {"f64": 8, "f32": 4, "bf16": 2}[args.dtype]
     nbox = (N // cfg["max_grid_size"]) ** 3
     b = cfg["max_grid_size"]
     G = mf.mf_fb_regions(head.h)[1]
-    st_bytes = S * cfg["ncomp"] * (2 * V + nbox * 6 * R * b * b)
-    fill_bytes = S * cfg["ncomp"] * 2 * G
+    C = cfg["ncomp"]
+    # compulsory bytes of one stencil launch: every valid cell read and written once, plus the
+    # face halo of radius R of every box (the ghost push into neighbouring boxes is not counted)
+    st_bytes = S * C * (2 * V + nbox * 6 * R * b * b)
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
     achieved = st_bytes / st_avg_s / 1e9
-    roof = {"bound": "hbm", "kernel": "k_stencil<%s,R=%d>" % (args.dtype, R), "achieved": achieved, "peak": hbm,
-            "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,
-            "traffic": traffic_for("k_stencil", WORKLOAD, args.dtype),
+    step_bytes = mf.mf_step_bytes(head.h, R)
+    roof = {"bound": "hbm", "kernel": "%s<%s,R=%d>" % (kname, args.dtype, R), "achieved": achieved, "peak": hbm,
+            "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind + " (STREAM-style copy)",
+            "traffic": traffic_for(kname, WORKLOAD, args.dtype),
             "algorithmic_bytes_per_launch": st_bytes, "avg_launch_us": st_avg_s * 1e6,
-            "fill_kernel": {"achieved": fill_bytes / fill_avg_s / 1e9, "algorithmic_bytes_per_launch": fill_bytes,
-                            "avg_launch_us": fill_avg_s * 1e6},
-            "step_bytes": mf.mf_step_bytes(head.h, R),
-            "step_frac": mf.mf_step_bytes(head.h, R) * nsteps * args.steps / (total_ms * 1e-3) / 1e9 / hbm,
-            "fill_fraction": fill_ms / (fill_ms + st_ms),
+            "stencil_launches_per_bench_step": launches["stencil"],
+            "fill_launches_per_bench_step": launches["fill"],
+            "fill_phase_us_per_bench_step": fill_ms * 1e3 / args.steps,
+            "step_bytes": step_bytes,
+            "step_frac": step_bytes * nsteps * args.steps / (total_ms * 1e-3) / 1e9 / hbm,
+            "step_frac_of_8tbs": step_bytes * nsteps * args.steps / (total_ms * 1e-3) / 1e9 / 8000.0,
             "timed_with_events_ms_per_step": sum(t_timed) / len(t_timed)}
+
+    # ---- the full FillBoundary kernel alone (every ghost cell, edges and corners included)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for _ in range(3):
+        mf.mf_fill_boundary(head.h)
+    fb_us = []
+    for _ in range(args.steps):
+        flush()
+        ev[0].record(head.stream)
+        mf.mf_fill_boundary(head.h)
+        ev[1].record(head.stream)
+        torch.cuda.synchronize()
+        fb_us.append(ev[0].elapsed_time(ev[1]) * 1e3)
+    fb_bytes = 2 * S * C * G
+    fb_avg = statistics.median(fb_us)
+    roof["fill_kernel"] = {"kernel": "k_fill<%s>" % args.dtype, "achieved": fb_bytes / fb_avg / 1e3, "unit": "GB/s",
+                           "frac": fb_bytes / fb_avg / 1e3 / hbm, "algorithmic_bytes_per_launch": fb_bytes,
+                           "avg_launch_us": fb_avg, "ghost_cells": G}
+    # ---- the compensated domain sum (kernels + the 8-byte read-back)
+    for _ in range(2):
+        mf.mf_sum(head.h, 0)
+    sm_us = []
+    for _ in range(args.steps):
+        flush()
+        ev[0].record(head.stream)
+        mf.mf_sum(head.h, 0)
+        ev[1].record(head.stream)
+        torch.cuda.synchronize()
+        sm_us.append(ev[0].elapsed_time(ev[1]) * 1e3)
+    sm_avg = statistics.median(sm_us)
+    roof["sum_kernel"] = {"kernel": "k_sum_partial+k_sum_final", "achieved": S * V / sm_avg / 1e3, "unit": "GB/s",
+                          "frac": S * V / sm_avg / 1e3 / hbm, "algorithmic_bytes_per_launch": S * V,
+                          "avg_call_us": sm_avg}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-           "config": workload_config(cfg), "roofline": roof, "gpu_launches": 2 * nsteps * args.steps,
-           "tile": list(tile), "schedule": mf.mf_get_schedule(head.h)}
+           "config": workload_config(cfg), "roofline": roof,
+           "gpu_launches": (launches["fill"] + launches["stencil"]) * args.steps,
+           "tile": list(tile), "schedule": sched}
     out["config"]["l2"] = out["config"]["l2"] % (2 * mf.mf_bytes(head.h) / 2 / 1e6)
     out["clocks"] = clk.summary()
 
@@ -355,9 +414,15 @@ def run_ours(args, cfg, ws, rank, local):
         tp = time_advances(plain, R, D, dt, nsteps, 2, flush, mf.MF_PLAIN_PER_BOX)
         vplain = V * nsteps * 2 / (sum(tp) * 1e-3)
         del plain
+        dpk = fp64_peak_tflops()
+        flops = FLOPS_PER_CELL[R] * V * nsteps * k2 / (sum(t64) * 1e-3) / 1e12
         out["fp64_batched"] = {"value": v64, "unit": UNIT, "tile": list(tile64),
-                               "frac_of_hbm": (8 * (2 * V + 2 * G) + 8 * nbox * 6 * b * b) * nsteps * k2
-                               / (sum(t64) * 1e-3) / 1e9 / hbm}
+                               "frac_of_hbm": 8 * C * (2 * V + 2 * G + nbox * 6 * b * b) * nsteps * k2
+                               / (sum(t64) * 1e-3) / 1e9 / hbm,
+                               "roofline": {"bound": "alu", "achieved": flops, "peak": dpk, "unit": "TFLOP/s",
+                                            "frac": flops / dpk if dpk else None,
+                                            "peak_kind": "measured: mf_fp64_fma_rate (DFMA chains, best of 3)",
+                                            "flops_per_cell": FLOPS_PER_CELL[R]}}
         out["fp64_plain_per_box"] = {"value": vplain, "unit": UNIT,
                                      "launches_per_time_step": 2 * nbox}
         out["speedup_batched_vs_fp64_plain_per_box"] = value / vplain

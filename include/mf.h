@@ -191,11 +191,25 @@ int mf_sum(mf_t *mf, int comp, double *out);
 double mf_step_bytes(const mf_t *mf, int R);
 
 /* Phase timing (Sec. 4.1 times the ghost fill and the kernel separately): when on, the
- * graph of mf_advance also records CUDA events between the launches; mf_phase_ms then
- * returns the summed device time of the FillBoundary launches (out[0]) and of the stencil
- * launches (out[1]) of the last mf_advance, waiting for it to finish. */
+ * graph of mf_advance also records a CUDA event wherever the kind of launch changes (fill to
+ * stencil or back; consecutive stencil launches have no event between them).  mf_phase_ms
+ * then returns the summed device time of the FillBoundary phases (out[0]) and of the stencil
+ * phases (out[1]) of the last mf_advance on this handle, waiting for it to finish;
+ * MF_ESTATE when that advance was not timed. */
 int mf_set_timing(mf_t *mf, int on);
 int mf_phase_ms(mf_t *mf, double out[2]);
+
+/* Kernel launches of the last mf_advance (or, on the coarse handle, mf_amr_advance) call:
+ * out[0] ghost-fill, out[1] stencil, out[2] coarse-fine interpolation, out[3] average-down
+ * launches.  Launches whose work list is empty are not made and not counted. */
+int mf_launch_count(const mf_t *mf, int out[4]);
+
+/* Measured FP64 fused multiply-add throughput of the current GPU in TFLOP/s (2 flops per
+ * FMA): 8 independent FMA chains per thread, 8 CTAs of 256 threads per SM, best of three
+ * timed launches on `stream` (cudaStream_t; NULL = legacy stream).  The ceiling of the FP64
+ * sweep on parts whose FP64 rate is low next to their memory bandwidth.  Measurement support,
+ * not part of the method; allocates and frees 8 bytes of device memory and synchronises. */
+int mf_fp64_fma_rate(double *tflops, void *stream);
 
 /* Which time level (0 or 1) is current. */
 int mf_current(const mf_t *mf);

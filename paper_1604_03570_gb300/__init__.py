@@ -28,7 +28,8 @@ EXPORTS = [
     "mf_get_fb_regions", "mf_attach", "mf_set_tile", "mf_get_tile", "mf_copy_from_host", "mf_copy_to_host",
     "mf_copy_fab_to_host", "mf_copy_fab_from_host", "mf_fill_boundary", "mf_interp_cf", "mf_average_down",
     "mf_advance", "mf_amr_advance", "mf_sum", "mf_step_bytes", "mf_current", "mf_last_error", "mf_set_timing",
-    "mf_phase_ms", "mf_set_kernel", "mf_sum_strided_noalloc", "mf_get_schedule",
+    "mf_phase_ms", "mf_set_kernel", "mf_sum_strided_noalloc", "mf_get_schedule", "mf_launch_count",
+    "mf_fp64_fma_rate",
 ]
 
 
@@ -78,6 +79,8 @@ def _load():
         "mf_phase_ms": (I, [P, P]),
         "mf_set_kernel": (I, [P, I]),
         "mf_get_schedule": (I, [P, P]),
+        "mf_launch_count": (I, [P, P]),
+        "mf_fp64_fma_rate": (I, [ctypes.POINTER(D), P]),
         "mf_sum_strided_noalloc": (I, [P, I, I, I, I, LL, LL, ctypes.POINTER(D), P]),
     }
     for name, (res, args) in sig.items():
@@ -264,6 +267,20 @@ def mf_phase_ms(h):
     out = np.zeros(2, dtype=np.float64)
     _check(lib.mf_phase_ms(h, _ptr(out)))
     return float(out[0]), float(out[1])
+
+
+def mf_launch_count(h):
+    """Kernel launches of the last advance: fill, stencil, interp, average-down."""
+    out = np.zeros(4, dtype=np.int32)
+    _check(lib.mf_launch_count(h, _ptr(out)))
+    return {"fill": int(out[0]), "stencil": int(out[1]), "interp": int(out[2]), "avgdown": int(out[3])}
+
+
+def mf_fp64_fma_rate(stream=0):
+    """Measured FP64 FMA throughput (TFLOP/s) of the current GPU."""
+    out = ctypes.c_double()
+    _check(lib.mf_fp64_fma_rate(ctypes.byref(out), ctypes.c_void_p(int(stream or 0))))
+    return out.value
 
 
 def mf_sum_strided_noalloc(data_ptr, dtype, nx, ny, nz, sy, sz, stream=0):

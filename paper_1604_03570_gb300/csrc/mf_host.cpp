@@ -171,6 +171,9 @@ struct DevBuf {
 
 struct GraphExec {
     cudaGraphExec_t exec = nullptr;
+    int launches[4] = {0, 0, 0, 0};  // ghost fill, stencil, coarse-fine interp, average-down kernels
+    int nev = 0;                     // timing events recorded by the graph (0: untimed)
+    std::vector<char> kinds;         // kinds[i]: phase between events i-1 and i (0 fill, 1 stencil, 2 other)
     ~GraphExec() { if (exec) cudaGraphExecDestroy(exec); }
 };
 
@@ -245,6 +248,8 @@ struct mf {
     bool timing = false;
     std::vector<cudaEvent_t> ev;   // 2*nsteps+1 of the last timed advance
     int ev_used = 0;
+    std::vector<char> ev_kinds;    // phase of each interval of the last timed advance
+    int launches[4] = {0, 0, 0, 0};  // kernel launches of the last advance (see GraphExec)
     std::vector<std::unique_ptr<InterpPlan>> interp;
     std::vector<std::unique_ptr<AvgPlan>> avg;
     ~mf() {
@@ -1163,6 +1168,10 @@ static int enqueue_fill(mf_t *m, int which, cudaStream_t s) {
 // The ghost exchange a time step needs: with the TMA stencil, only the face regions it reads
 // from ghost cells (edges and corners are never read by a star stencil; x faces whose tiles
 // take their halo from the neighbour box are skipped).
+static size_t fill_step_tasks(const mf_t *m) {
+    return (m->use_tma && m->tma_ok && m->tma_strips) ? m->fbtasks_adv.size() : m->fbtasks.size();
+}
+
 static int enqueue_fill_step(mf_t *m, int which, cudaStream_t s) {
     if (!(m->use_tma && m->tma_ok && m->tma_strips)) return enqueue_fill(m, which, s);
     CU(launch_fill(m->dtype, level_ptrs(m, which), (const FbTask *)m->d_fbtasks_adv.p, (int)m->fbtasks_adv.size(), 0,
@@ -1349,6 +1358,61 @@ static int record(mf_t *m, int i) {
     return 0;
 }
 
+// Launch bookkeeping while capturing an advance: counts the kernels of each kind and, when
+// timing, records an event wherever the kind of work changes (so back-to-back stencil
+// launches run without event nodes between them).
+struct PhaseLog {
+    mf_t *m;
+    bool timing;
+    int nev = 0;
+    int open = -1;  // kind of the interval since the last event (-1: none yet)
+    int launches[4] = {0, 0, 0, 0};
+    std::vector<char> kinds;
+    int start() {
+        if (!timing) return 0;
+        kinds.push_back(-1);
+        return record(m, nev++);
+    }
+    // call before enqueueing a kernel of kind k (0 fill, 1 stencil, 2 interp, 3 average-down);
+    // real = false: the launcher will find an empty list and launch nothing
+    int before(int k, bool real = true) {
+        if (!real) return 0;
+        ++launches[k];
+        const int phase = k < 2 ? k : 2;
+        if (!timing || open == phase) { open = phase; return 0; }
+        int rc = 0;
+        if (open >= 0) {
+            kinds.push_back((char)open);
+            rc = record(m, nev++);
+        }
+        open = phase;
+        return rc;
+    }
+    int finish() {
+        if (!timing || open < 0) return 0;
+        kinds.push_back((char)open);
+        return record(m, nev++);
+    }
+    void store(GraphExec &g) const {
+        for (int i = 0; i < 4; ++i) g.launches[i] = launches[i];
+        g.nev = timing ? nev : 0;
+        g.kinds = kinds;
+    }
+};
+
+// The state mf_phase_ms and mf_launch_count report, from the graph just launched.
+static void note_launch(mf_t *m, const GraphExec &g) {
+    for (int i = 0; i < 4; ++i) m->launches[i] = g.launches[i];
+    m->ev_used = g.nev;
+    m->ev_kinds = g.kinds;
+}
+
+extern "C" int mf_launch_count(const mf_t *m, int out[4]) {
+    if (!m || !out) return fail(MF_EINVAL, "null argument");
+    for (int i = 0; i < 4; ++i) out[i] = m->launches[i];
+    return 0;
+}
+
 extern "C" int mf_set_timing(mf_t *m, int on) {
     if (!m) return fail(MF_EINVAL, "null handle");
     m->timing = on != 0;
@@ -1358,14 +1422,13 @@ extern "C" int mf_set_timing(mf_t *m, int on) {
 extern "C" int mf_phase_ms(mf_t *m, double out[2]) {
     if (!m || !out) return fail(MF_EINVAL, "null argument");
     out[0] = out[1] = 0.0;
-    if (m->ev_used < 3) return fail(MF_ESTATE, "no timed advance recorded");
+    if (m->ev_used < 2) return fail(MF_ESTATE, "no timed advance recorded");
     CU(cudaEventSynchronize(m->ev[m->ev_used - 1]));
-    for (int i = 0; 2 * i + 2 < m->ev_used; ++i) {
-        float a = 0, b = 0;
-        CU(cudaEventElapsedTime(&a, m->ev[2 * i], m->ev[2 * i + 1]));
-        CU(cudaEventElapsedTime(&b, m->ev[2 * i + 1], m->ev[2 * i + 2]));
-        out[0] += a;
-        out[1] += b;
+    for (int i = 1; i < m->ev_used; ++i) {
+        float a = 0;
+        CU(cudaEventElapsedTime(&a, m->ev[i - 1], m->ev[i]));
+        if (m->ev_kinds[i] == 0) out[0] += a;
+        if (m->ev_kinds[i] == 1) out[1] += a;
     }
     return 0;
 }
@@ -1414,28 +1477,30 @@ extern "C" int mf_advance(mf_t *m, const mf_stencil *st, double dt, int nsteps) 
         if (m->timing && (rc = ensure_events(m, 2 * nsteps + 1))) return rc;
         if ((rc = capture_begin(m))) return rc;
         int body = 0, from = m->cur;
-        if (m->timing) body = record(m, 0);
+        PhaseLog log{m, m->timing};
+        body = log.start();
         const bool push = m->use_tma && m->tma_ok && m->tma_push;
         for (int s = 0; s < nsteps && !body; ++s) {
             if (push && s > 0) {
                 // the previous stencil launch pushed the face ghosts; fill what is left
-                if (!m->fbtasks_res.empty())
+                if (!m->fbtasks_res.empty() && !(body = log.before(0)))
                     body = launch_fill(m->dtype, level_ptrs(m, from), (const FbTask *)m->d_fbtasks_res.p,
                                        (int)m->fbtasks_res.size(), 0, m->cap) == cudaSuccess
                                ? 0
                                : fail(MF_ECUDA, "fill launch failed");
-            } else {
+            } else if (!(body = log.before(0, fill_step_tasks(m) > 0))) {
                 body = enqueue_fill_step(m, from, m->cap);
             }
-            if (!body && m->timing) body = record(m, 2 * s + 1);
+            if (!body) body = log.before(1);
             if (!body) body = enqueue_stencil(m, from, R, fp64diff, lam, m->cap, push);
-            if (!body && m->timing) body = record(m, 2 * s + 2);
             from = 1 - from;
         }
+        if (!body) body = log.finish();
         if ((rc = capture_end(m, key, body))) return rc;
         it = m->graphs.find(key);
+        log.store(*it->second);
     }
-    m->ev_used = m->timing ? 2 * nsteps + 1 : 0;
+    note_launch(m, *it->second);
     CU(cudaGraphLaunch(it->second->exec, m->stream));
     if (nsteps & 1) m->cur = 1 - m->cur;
     return 0;
@@ -1670,24 +1735,29 @@ extern "C" int mf_amr_advance(mf_t *crse, mf_t *fine, const mf_stencil *st, doub
         if ((rc = capture_begin(crse))) return rc;
         cudaStream_t s = crse->cap;
         int body = 0, c = crse->cur, f = fine->cur;
+        PhaseLog log{crse, false};
         for (int step = 0; step < ncrse_steps && !body; ++step) {
             // full exchange: the coarse-fine interpolation reads coarse edge and corner ghosts
-            body = enqueue_fill(crse, c, s);
-            if (!body) body = enqueue_stencil(crse, c, R, fp64diff, lam_c, s);
-            if (!body) body = enqueue_fill(crse, 1 - c, s);
+            const bool cf = !crse->fbtasks.empty();
+            if (!(body = log.before(0, cf))) body = enqueue_fill(crse, c, s);
+            if (!body && !(body = log.before(1))) body = enqueue_stencil(crse, c, R, fp64diff, lam_c, s);
+            if (!body && !(body = log.before(0, cf))) body = enqueue_fill(crse, 1 - c, s);
             for (int sub = 0; sub < nsub && !body; ++sub) {
-                body = enqueue_fill_step(fine, f, s);
-                if (!body)
+                if (!(body = log.before(0, fill_step_tasks(fine) > 0))) body = enqueue_fill_step(fine, f, s);
+                if (!body && !(body = log.before(2, !ip->runs.empty())))
                     body = enqueue_interp(fine, f, crse, c, crse, 1 - c, ip, ratio, (double)sub / (double)nsub, s);
-                if (!body) body = enqueue_stencil(fine, f, R, fp64diff, lam_f, s);
+                if (!body && !(body = log.before(1))) body = enqueue_stencil(fine, f, R, fp64diff, lam_f, s);
                 f = 1 - f;
             }
-            if (!body) body = enqueue_avg(fine, f, crse, 1 - c, ap, ratio, s);
+            if (!body && !(body = log.before(3, !ap->regs.empty())))
+                body = enqueue_avg(fine, f, crse, 1 - c, ap, ratio, s);
             c = 1 - c;
         }
         if ((rc = capture_end(crse, key, body))) return rc;
         it = crse->graphs.find(key);
+        log.store(*it->second);
     }
+    note_launch(crse, *it->second);
     CU(cudaGraphLaunch(it->second->exec, crse->stream));
     if (ncrse_steps & 1) crse->cur = 1 - crse->cur;
     if ((ncrse_steps * nsub) & 1) fine->cur = 1 - fine->cur;

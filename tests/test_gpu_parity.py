@@ -369,3 +369,20 @@ def test_phase_timing_reports_both_phases():
     g.advance(1, [1.0], 0.1 / 4096, 6)
     fill_ms, st_ms = mf.mf_phase_ms(g.h)
     assert fill_ms > 0 and st_ms > 0
+    n = mf.mf_launch_count(g.h)
+    assert n["stencil"] == 6 and 1 <= n["fill"] <= 6 and n["interp"] == 0 and n["avgdown"] == 0
+
+
+def test_launch_count_without_ghost_push():
+    """The global-memory kernel fills every step: one fill and one stencil launch per step."""
+    g = gpu_level([0, 0, 0], [31, 31, 31], mgs=16, ngrow=1, dtype="f32")
+    g.from_host(rand_field((1, 32, 32, 32), 17, "f32"))
+    mf.mf_set_kernel(g.h, mf.MF_KERNEL_GLOBAL)
+    g.advance(1, [1.0], 0.1 / 1024, 5)
+    assert mf.mf_launch_count(g.h) == {"fill": 5, "stencil": 5, "interp": 0, "avgdown": 0}
+
+
+def test_fp64_fma_rate_is_plausible():
+    """The DFMA throughput probe returns a rate between 0.1 and 200 TFLOP/s."""
+    r = mf.mf_fp64_fma_rate()
+    assert 0.1 < r < 200.0, r
