@@ -66,8 +66,8 @@ def workload_config(cfg):
             "domain": N, "max_grid_size": cfg["max_grid_size"], "ngrow": cfg["ngrow"], "ncomp": cfg["ncomp"],
             "stencil_radius": cfg["R"], "time_steps_per_bench_step": cfg["nsteps"],
             "initial_data": "8 seeded sine modes, |k_d| in 1..16",
-            "l2": "flushed (512 MB write) before every timed bench step; per-step working set "
-                  "(two time levels incl. ghosts) %.0f MB (FP32)"}
+            "l2": "flushed (512 MB write, then 512 MB read) before every timed bench step; per-step working "
+                  "set (two time levels incl. ghosts) %.0f MB, larger than the 129 MB L2"}
 
 
 # ------------------------------------------------------------------ clocks
@@ -261,9 +261,13 @@ def run_ours(args, cfg, ws, rank, local):
     V = N ** 3
     dense = synth.initial_field(cfg)
     flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    flush_rd = torch.ones(512 << 20, dtype=torch.uint8, device=dev)
 
     def flush():
+        # write a buffer four times the L2, then read another: the timed region starts with no
+        # line of its own data in L2 and no dirty line of the flush left to write back
         flush_buf.fill_(1)
+        flush_rd.max()
 
     def level(dtype):
         m = mf.MultiFab(lo, hi, max_grid_size=cfg["max_grid_size"], ncomp=cfg["ncomp"], ngrow=cfg["ngrow"],
@@ -353,21 +357,21 @@ def run_ours(args, cfg, ws, rank, local):
     roof["fill_kernel"] = {"kernel": "k_fill<%s>" % args.dtype, "achieved": fb_bytes / fb_avg / 1e3, "unit": "GB/s",
                            "frac": fb_bytes / fb_avg / 1e3 / hbm, "algorithmic_bytes_per_launch": fb_bytes,
                            "avg_launch_us": fb_avg, "ghost_cells": G}
-    # ---- the compensated domain sum (kernels + the 8-byte read-back)
+    # ---- the compensated domain sum: mf_sum synchronises, so this is the host-visible call
+    # latency (kernels, the 8-byte read-back and the wake-up of the calling thread)
     for _ in range(2):
         mf.mf_sum(head.h, 0)
     sm_us = []
     for _ in range(args.steps):
         flush()
-        ev[0].record(head.stream)
-        mf.mf_sum(head.h, 0)
-        ev[1].record(head.stream)
         torch.cuda.synchronize()
-        sm_us.append(ev[0].elapsed_time(ev[1]) * 1e3)
+        t0 = time.perf_counter()
+        mf.mf_sum(head.h, 0)
+        sm_us.append((time.perf_counter() - t0) * 1e6)
     sm_avg = statistics.median(sm_us)
-    roof["sum_kernel"] = {"kernel": "k_sum_partial+k_sum_final", "achieved": S * V / sm_avg / 1e3, "unit": "GB/s",
-                          "frac": S * V / sm_avg / 1e3 / hbm, "algorithmic_bytes_per_launch": S * V,
-                          "avg_call_us": sm_avg}
+    roof["sum_call"] = {"kernels": "k_sum_partial+k_sum_final", "achieved": S * V / sm_avg / 1e3, "unit": "GB/s",
+                        "frac": S * V / sm_avg / 1e3 / hbm, "algorithmic_bytes_per_call": S * V,
+                        "median_call_us": sm_avg}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,

@@ -1255,8 +1255,6 @@ static int check_stencil(const mf_t *m, const mf_stencil *st, double dt, double 
     return 0;
 }
 
-// Autotune: time every candidate tile shape on the live data (current -> other level, which
-// is scratch at this point) and keep the fastest.  Synchronous; runs once per handle.
 // Autotune: time every candidate schedule -- tile shape, and for the TMA kernel rows per
 // thread and ring depth -- on the live data (current -> other level, which is scratch at this
 // point) and keep the fastest.  Synchronous; runs once per handle.
@@ -1276,23 +1274,38 @@ static int autotune(mf_t *m, int R, bool fp64diff, const double *lam) {
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
-    float best = 1e30f;
-    Cand bc = cands.front();
-    for (auto &c : cands) {
+    // time one candidate: a warm-up launch (also encodes the tensor maps), then n launches
+    auto time_cand = [&](const Cand &c, int n, float *ms) -> int {
         m->tma_rows = c.rows;
         m->tma_ns_pref = c.ns;
         int rc = set_tiles(m, c.t.data());
-        if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
-        // warm-up (also encodes the tensor maps), then 3 timed launches
+        if (rc) return rc;
         if ((rc = enqueue_stencil(m, m->cur, R, fp64diff, lam, m->stream))) return rc;
         CU(cudaEventRecord(e0, m->stream));
-        for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < n; ++i)
             if ((rc = enqueue_stencil(m, m->cur, R, fp64diff, lam, m->stream))) return rc;
         CU(cudaEventRecord(e1, m->stream));
         CU(cudaEventSynchronize(e1));
+        CU(cudaEventElapsedTime(ms, e0, e1));
+        *ms /= (float)n;
+        return 0;
+    };
+    // round 1: every candidate, 3 launches; round 2: the four fastest again, 12 launches each
+    std::vector<std::pair<float, size_t>> r1;
+    for (size_t i = 0; i < cands.size(); ++i) {
         float ms = 0;
-        CU(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) { best = ms; bc = c; }
+        int rc = time_cand(cands[i], 3, &ms);
+        if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
+        r1.push_back({ms, i});
+    }
+    std::sort(r1.begin(), r1.end());
+    float best = 1e30f;
+    Cand bc = cands[r1.front().second];
+    for (size_t j = 0; j < r1.size() && j < 4; ++j) {
+        float ms = 0;
+        int rc = time_cand(cands[r1[j].second], 12, &ms);
+        if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
+        if (ms < best) { best = ms; bc = cands[r1[j].second]; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
