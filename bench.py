@@ -243,6 +243,22 @@ def time_advances(mfab, R, D, dt, nsteps, K, flush, flags=0):
     return [a.elapsed_time(b) for a, b in ev]
 
 
+def max_over_ranks(x, dist, device):
+    """The largest x over all ranks (x itself on one rank)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(ws, units_per_rank, seconds):
+    """Units all ranks processed per second of the slowest rank (weak scaling: every rank
+    processes the same units)."""
+    return ws * units_per_rank / seconds
+
+
 def run_ours(args, cfg, ws, rank, local):
     import torch
     import paper_1604_03570_gb300 as mf
@@ -289,13 +305,10 @@ def run_ours(args, cfg, ws, rank, local):
     with ClockSampler(local) as clk:
         times = time_advances(head, R, D, dt, nsteps, args.steps, flush)
     torch.cuda.synchronize()
-    total_ms = sum(times)
+    total_ms = max_over_ranks(sum(times), dist, dev)
     if dist:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
-    value = ws * V * nsteps * args.steps / (total_ms * 1e-3)
+    value = whole_job_rate(ws, V * nsteps * args.steps, total_ms * 1e-3)
     tile, _ = mf.mf_get_tile(head.h)
 
     launches = mf.mf_launch_count(head.h)  # of one mf_advance (the graph replayed every bench step)
@@ -396,12 +409,8 @@ def run_ours(args, cfg, ws, rank, local):
             t1 = time.perf_counter()
             if k >= args.warmup:
                 e2e_t.append(t1 - t0)
-        e2e_s = sum(e2e_t)
-        if dist:
-            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        out["e2e"] = {"value": ws * V * nsteps * args.steps / e2e_s, "unit": UNIT,
+        e2e_s = max_over_ranks(sum(e2e_t), dist, dev)
+        out["e2e"] = {"value": whole_job_rate(ws, V * nsteps * args.steps, e2e_s), "unit": UNIT,
                       "h2d_bytes_per_step": int(dense.nbytes), "d2h_bytes_per_step": int(dense.nbytes)}
         del head
         # ---- FP64 batched and FP64 plain per box

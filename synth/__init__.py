@@ -139,7 +139,13 @@ def uneven_boxes(N, target, seed=BOX_SEED, base=32, quantum=8):
     if target < len(boxes):
         raise ValueError("target below the base box count")
     rng = Rng(seed, 7)
-    splittable = [i for i, b in enumerate(boxes) if max(b[3] - b[0], b[4] - b[1], b[5] - b[2]) + 1 >= 2 * quantum]
+
+    def can_split(bb):
+        return max(bb[3] - bb[0], bb[4] - bb[1], bb[5] - bb[2]) + 1 >= 2 * quantum
+
+    # indices of the splittable boxes in increasing order: a split changes box i in place (it
+    # stays at its position or leaves the list) and appends the new box (largest index)
+    splittable = [i for i, b in enumerate(boxes) if can_split(b)]
     while len(boxes) < target:
         if not splittable:
             raise ValueError("cannot reach target")
@@ -156,8 +162,10 @@ def uneven_boxes(N, target, seed=BOX_SEED, base=32, quantum=8):
         c[d] = b[d] + cut
         boxes[i] = a
         boxes.append(c)
-        splittable = [j for j, bb in enumerate(boxes)
-                      if max(bb[3] - bb[0], bb[4] - bb[1], bb[5] - bb[2]) + 1 >= 2 * quantum]
+        if not can_split(a):
+            splittable.pop(pick)
+        if can_split(c):
+            splittable.append(len(boxes) - 1)
     return np.asarray(boxes, dtype=np.int32)
 
 

@@ -386,3 +386,46 @@ def test_fp64_fma_rate_is_plausible():
     """The DFMA throughput probe returns a rate between 0.1 and 200 TFLOP/s."""
     r = mf.mf_fp64_fma_rate()
     assert 0.1 < r < 200.0, r
+
+
+# --------------------------------------------------------------------------- degenerate layouts
+
+THIN_DOM = ([0, 0, 0], [15, 11, 9])
+THIN = np.array([[x0, 0, z0, x1, 11, z1] for (x0, x1) in ((0, 0), (1, 2), (3, 5), (6, 15))
+                 for (z0, z1) in ((0, 1), (2, 9))], dtype=np.int32)
+
+
+@pytest.mark.parametrize("R", [1, 2])
+def test_advance_fp64_thin_boxes_matches_oracle(R):
+    """Boxes 1, 2 and 3 cells thick (thinner than the ghost width and the stencil radius)."""
+    lo, hi = THIN_DOM
+    dense = rand_field((1, 10, 12, 16), 40 + R)
+    dt = 0.1 / (16 * 16)
+    lam = 1.0 * dt * 256.0
+    g = gpu_level(lo, hi, boxes=THIN, ngrow=R)
+    g.from_host(dense)
+    g.advance(R, [1.0], dt, 5)
+    assert rel_err(g.to_host(), _oracle_advance(THIN, lo, hi, R, 1, R, lam, 5, dense)) <= FP64_TOL
+
+
+def test_row_wider_than_a_tma_box_uses_the_global_kernel():
+    """A row of more than 256 elements cannot be one TMA box row: the schedule falls back to
+    the global-memory kernel, with the same results."""
+    lo, hi = [0, 0, 0], [299, 7, 5]
+    dense = rand_field((1, 6, 8, 300), 44)
+    dt = 0.1 / (300 * 300)
+    g = gpu_level(lo, hi, mgs=300, ngrow=1)
+    g.from_host(dense)
+    g.advance(1, [1.0], dt, 3)
+    assert mf.mf_get_schedule(g.h)["kernel"] == "global"
+    ref = _oracle_advance(np.array([[0, 0, 0, 299, 7, 5]], dtype=np.int32), lo, hi, 1, 1, 1, dt * 300 * 300, 3,
+                          dense)
+    assert rel_err(g.to_host(), ref) <= FP64_TOL
+
+
+def test_zero_steps_is_a_no_op():
+    g = gpu_level([0, 0, 0], [15, 15, 15], mgs=8, ngrow=1)
+    dense = rand_field((1, 16, 16, 16), 45)
+    g.from_host(dense)
+    g.advance(1, [1.0], 0.1 / 256, 0)
+    np.testing.assert_array_equal(g.to_host(), dense)
