@@ -301,32 +301,39 @@ static long long elem_at(const FabInfo &f, int i, int j, int k) {  // global (i,
 
 // FillBoundary tasks for the entries selected by `use`: CTA-sized pieces (256 threads x 4 cells).
 static void make_fill_tasks(const mf_t *m, const std::vector<char> &use, std::vector<FbTask> &out) {
-    const int kTask = 1024;
+    const int kTask = 256;  // one warp of the fill kernel: 32 lanes x 8 cells (or vectors)
+    const long long V = 16 / m->esize;  // elements per 16-byte vector
     out.clear();
     for (int e = 0; e < (int)m->fb.size(); ++e) {
         if (!use[e]) continue;
         const FbEntry &en = m->fb[e];
         const FabInfo &sf = m->fabs[en.sfab], &df = m->fabs[en.dfab];
-        const long long cells = (long long)en.n[0] * en.n[1] * en.n[2] * m->ncomp;
+        // rows that start and end on 16-byte boundaries on both sides copy as 16-byte vectors
+        // (pitches, planes and component strides are whole 32-byte sectors by construction)
+        const bool vec = en.n[0] % V == 0 && en.src % V == 0 && en.dst % V == 0;
+        const long long u = vec ? V : 1;
+        const int n0 = (int)(en.n[0] / u);
+        const long long cells = (long long)n0 * en.n[1] * en.n[2] * m->ncomp;
         for (long long f = 0; f < cells; f += kTask) {
             FbTask t{};
-            t.src = en.src;
-            t.dst = en.dst;
-            t.s_pl = sf.plane;
-            t.d_pl = df.plane;
-            t.s_cs = sf.cstride;
-            t.d_cs = df.cstride;
-            t.s_px = sf.px;
-            t.d_px = df.px;
-            t.n0 = en.n[0];
+            t.src = en.src / u;
+            t.dst = en.dst / u;
+            t.s_pl = (int)(sf.plane / u);
+            t.d_pl = (int)(df.plane / u);
+            t.s_cs = (int)(sf.cstride / u);
+            t.d_cs = (int)(df.cstride / u);
+            t.s_px = (int)(sf.px / u);
+            t.d_px = (int)(df.px / u);
+            t.n0 = n0;
             t.n1 = en.n[1];
             t.n2 = en.n[2];
             t.first = (int)f;
             t.count = (int)std::min<long long>(kTask, cells - f);
             t.level = en.level;
-            t.f0 = make_fastdiv((uint32_t)en.n[0]);
+            t.f0 = make_fastdiv((uint32_t)n0);
             t.f1 = make_fastdiv((uint32_t)en.n[1]);
             t.f2 = make_fastdiv((uint32_t)en.n[2]);
+            t.vec = vec ? 1 : 0;
             out.push_back(t);
         }
     }
@@ -465,6 +472,8 @@ static int check_create(const int dlo[3], const int dhi[3], int ncomp, int ngrow
 
 static int finish_create(mf_t *m) {
     build_layout(m);
+    for (auto &f : m->fabs)  // offsets within one FArrayBox are 32-bit in the kernels
+        if (f.cstride * m->ncomp >= (1LL << 31)) return fail(MF_EINVAL, "an FArrayBox of 2^31 or more elements");
     int rc = build_fb(m);
     if (rc) return rc;
     make_tiles(m, m->tile, m->tiles);

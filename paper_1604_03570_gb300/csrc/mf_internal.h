@@ -48,17 +48,21 @@ inline FastDiv make_fastdiv(uint32_t d) {
     return FastDiv{(uint32_t)(((1ull << 32) * ((1ull << s) - d)) / d + 1), s};
 }
 
-// Work unit of the fill kernel, self-contained so that a CTA needs one load to start:
+// Work unit of the fill kernel (one warp), self-contained so that a warp needs one load to start:
 // cells [first, first + count) of one copy region in the linear order (comp, z, y, x).
+// With vec != 0 every offset, stride and the x extent n0 count 16-byte vectors instead of
+// elements (a region whose rows start and end on 16-byte boundaries on both sides).
 struct FbTask {
-    long long src, dst;    // element offsets of the region's first cell, comp 0
-    long long s_pl, d_pl;  // plane strides
-    long long s_cs, d_cs;  // component strides
+    long long src, dst;    // offsets of the region's first cell, comp 0
+    int s_pl, d_pl;        // plane strides (an FArrayBox has fewer than 2^31 elements)
+    int s_cs, d_cs;        // component strides
     int s_px, d_px;        // row pitches
     int n0, n1, n2;        // region extents
     int first, count;
     int level;
     FastDiv f0, f1, f2;    // division by n0, n1, n2
+    int vec;               // units: 0 elements, 1 16-byte vectors
+    int pad_;
 };
 static_assert(sizeof(FbTask) % 8 == 0, "the fill kernel copies its task header in 8-byte words");
 

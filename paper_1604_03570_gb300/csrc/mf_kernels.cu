@@ -32,35 +32,57 @@ namespace mfk {
 
 __device__ __forceinline__ uint32_t fdiv(uint32_t n, FastDiv d) { return (__umulhi(n, d.m) + n) >> d.s; }
 
+// A warp copies one task of 256 cells or 16-byte vectors (8 per lane, every load issued
+// before the stores).  Lanes 0..11 load one 8-byte word of the 96-byte task header each and
+// the warp shares them by shuffle, so warps never wait for one another.
+constexpr int kFillCellsPerLane = 8;
+union FbTaskWords {
+    FbTask t;
+    unsigned long long w[sizeof(FbTask) / 8];
+};
+
+// Cells off + lane + 32 u, u < U, of the task.
+template <typename E, int U>
+__device__ __forceinline__ void fill_copy(E *base, const FbTask &tk, int lane, int off) {
+    const E *sb = base + tk.src;
+    E *db = base + tk.dst;
+    E v[U];
+    uint32_t dof[U];  // offsets within the destination FArrayBox
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int i = off + lane + 32 * u;
+        const uint32_t l = (uint32_t)(tk.first + i);
+        const uint32_t r0 = fdiv(l, tk.f0);
+        const uint32_t x = l - r0 * (uint32_t)tk.n0;
+        const uint32_t r1 = fdiv(r0, tk.f1);
+        const uint32_t y = r0 - r1 * (uint32_t)tk.n1;
+        const uint32_t c = fdiv(r1, tk.f2);
+        const uint32_t z = r1 - c * (uint32_t)tk.n2;
+        dof[u] = c * (uint32_t)tk.d_cs + z * (uint32_t)tk.d_pl + y * (uint32_t)tk.d_px + x;
+        if (i < tk.count) v[u] = __ldg(sb + (c * (uint32_t)tk.s_cs + z * (uint32_t)tk.s_pl + y * (uint32_t)tk.s_px + x));
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+        if (off + lane + 32 * u < tk.count) db[dof[u]] = v[u];
+}
+
 template <typename E>
 __global__ void __launch_bounds__(256) k_fill(LevelPtrs lv, const FbTask *__restrict__ tasks, int ntasks) {
-    constexpr int U = 4;  // cells per thread per task: all loads issued before the stores
-    __shared__ FbTask sh;
-    for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
-        __syncthreads();  // the previous task's header is no longer read
-        if (threadIdx.x < (int)(sizeof(FbTask) / 8))
-            ((unsigned long long *)&sh)[threadIdx.x] = __ldg((const unsigned long long *)(tasks + t) + threadIdx.x);
-        __syncthreads();
-        const FbTask &tk = sh;
-        E *base = (E *)lv.base[tk.level];
-        E v[U];
-        long long dof[U];
+    constexpr int W = (int)(sizeof(FbTask) / 8);
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); t < ntasks; t += nwarps) {
+        unsigned long long word = 0;
+        if (lane < W) word = __ldg((const unsigned long long *)(tasks + t) + lane);
+        FbTaskWords h;
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int i = threadIdx.x + u * (int)blockDim.x;
-            const uint32_t l = (uint32_t)(tk.first + i);
-            const uint32_t r0 = fdiv(l, tk.f0);
-            const uint32_t x = l - r0 * (uint32_t)tk.n0;
-            const uint32_t r1 = fdiv(r0, tk.f1);
-            const uint32_t y = r0 - r1 * (uint32_t)tk.n1;
-            const uint32_t c = fdiv(r1, tk.f2);
-            const uint32_t z = r1 - c * (uint32_t)tk.n2;
-            dof[u] = tk.dst + c * tk.d_cs + z * tk.d_pl + (long long)y * tk.d_px + x;
-            if (i < tk.count) v[u] = __ldg(base + tk.src + c * tk.s_cs + z * tk.s_pl + (long long)y * tk.s_px + x);
+        for (int i = 0; i < W; ++i) h.w[i] = __shfl_sync(0xffffffffu, word, i);
+        if (h.t.vec) {  // two halves of 4 vectors per lane (registers)
+            fill_copy<uint4, kFillCellsPerLane / 2>((uint4 *)lv.base[h.t.level], h.t, lane, 0);
+            fill_copy<uint4, kFillCellsPerLane / 2>((uint4 *)lv.base[h.t.level], h.t, lane, 16 * kFillCellsPerLane);
+        } else {
+            fill_copy<E, kFillCellsPerLane>((E *)lv.base[h.t.level], h.t, lane, 0);
         }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (threadIdx.x + u * (int)blockDim.x < tk.count) base[dof[u]] = v[u];
     }
 }
 
@@ -334,17 +356,17 @@ cudaError_t launch_fill(int dtype, const LevelPtrs &lv, const FbTask *tasks, int
     if (ntasks == 0) return cudaSuccess;
     switch (dtype_size(dtype)) {
         case 8: {
-            int g = grid > 0 ? grid : persistent_grid(k_fill<unsigned long long>, 256, ntasks);
+            int g = grid > 0 ? grid : persistent_grid(k_fill<unsigned long long>, 256, (ntasks + 7) / 8);
             k_fill<unsigned long long><<<g, 256, 0, s>>>(lv, tasks, ntasks);
             break;
         }
         case 4: {
-            int g = grid > 0 ? grid : persistent_grid(k_fill<unsigned int>, 256, ntasks);
+            int g = grid > 0 ? grid : persistent_grid(k_fill<unsigned int>, 256, (ntasks + 7) / 8);
             k_fill<unsigned int><<<g, 256, 0, s>>>(lv, tasks, ntasks);
             break;
         }
         default: {
-            int g = grid > 0 ? grid : persistent_grid(k_fill<unsigned short>, 256, ntasks);
+            int g = grid > 0 ? grid : persistent_grid(k_fill<unsigned short>, 256, (ntasks + 7) / 8);
             k_fill<unsigned short><<<g, 256, 0, s>>>(lv, tasks, ntasks);
         }
     }

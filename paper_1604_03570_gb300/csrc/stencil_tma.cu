@@ -147,7 +147,6 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
     const int tid = threadIdx.x;
     const int ncw = (int)(blockDim.x >> 5) - 1;  // consumer warps
     __shared__ PushRec ptab[TmaBounds<R>::threads / 32 - 1][kMaxPush];  // per consumer warp
-    if (*(volatile int *)p.err) return;          // an earlier launch already failed: do nothing
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(&full[s], 1);
@@ -157,6 +156,13 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
+    // Programmatic dependent launch: the next launch in the stream may start its CTAs (which
+    // only find room as this grid's CTAs exit) and set up; before touching level data or the
+    // error word every thread waits for the previous grid to complete.  Both are no-ops for a
+    // launch without the attribute.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (*(volatile int *)p.err) return;  // an earlier launch already failed: do nothing
     // this CTA's tiles: its own range of a balanced schedule, else every gridDim.x-th tile
     int w0 = blockIdx.x, w1 = p.ntiles, ws = gridDim.x;
     if (p.cta_tiles) {
@@ -499,8 +505,17 @@ static cudaError_t tma_t(int nt, const StencilTmaParams &p, int grid, cudaStream
         g = (int)(gg < p.ntiles ? gg : p.ntiles);
         if (g < 1) g = 1;
     }
-    kern<<<g, nt, smem, s>>>(p);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)g);
+    cfg.blockDim = dim3((unsigned)nt);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, p);
 }
 
 template <typename S, typename A>
