@@ -274,10 +274,11 @@ static void build_layout(mf_t *m) {
         FabInfo f{};
         for (int d = 0; d < 3; ++d) { f.n[d] = b.len(d); f.lo[d] = b.lo[d]; }
         // rows lie back to back at a pitch of whole 32-byte sectors (dense DRAM pages, aligned
-        // whole-row TMA loads); the left ghost cells are padded to a whole 16-byte chunk so that
-        // valid x = 0 sits on a 16-byte boundary (aligned vector access of the valid cells)
-        const int AS = 32 / S, A16 = 16 / S;
-        const int fpad = (A16 - g % A16) % A16;
+        // whole-row TMA loads); the left ghost cells are padded so that valid x = 0 starts a
+        // 32-byte sector: a row of valid cells is whole sectors, read and written without
+        // partial sectors
+        const int AS = 32 / S;
+        const int fpad = (AS - g % AS) % AS;
         f.px = (int)(((long long)fpad + f.n[0] + 2 * g + AS - 1) / AS * AS);
         const long long py = f.n[1] + 2 * g, nzg = f.n[2] + 2 * g;
         f.plane = (long long)f.px * py;
@@ -291,6 +292,12 @@ static void build_layout(mf_t *m) {
     }
     off = (off + align - 1) / align * align;
     m->level_elems = (size_t)off;
+}
+
+// Row element of valid x = 0 in every FArrayBox (the layout's left padding plus the ghosts).
+static int valid_x_elem(const mf_t *m) {
+    const int AS = 32 / m->esize, g = m->ngrow;
+    return (g + AS - 1) / AS * AS;
 }
 
 static long long elem_at(const FabInfo &f, int i, int j, int k) {  // global (i,j,k), comp 0
@@ -880,14 +887,17 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 // Plane geometry of every FArrayBox for the current tile shape and radius R; false when a
 // box needs a plane wider than the TMA box limit (256 per dimension) or more cells per
-// thread than the kernel keeps in registers.
-static bool tma_geometry(mf_t *m, int R, std::vector<TmaFab> &tf, int &slot_bytes, int &gpt) {
+// thread than the kernel keeps in registers.  A box whose two x faces are served by strips
+// (served[2b], served[2b+1]) loads only its valid cells of each row, rounded up to 16 bytes;
+// the others load the whole row, ghost columns and padding included.
+static bool tma_geometry(mf_t *m, int R, const std::vector<char> &served, std::vector<TmaFab> &tf, int &slot_bytes,
+                         int &gpt) {
     const int S = m->esize, A = 16 / S, g = m->ngrow;
     tf.assign(m->fabs.size(), TmaFab{});
     int maxplane = 0, maxgroups = 0;
     for (auto &t : m->tiles) {
-        // the TMA kernel streams whole rows (x = -g .. n0 + g and padding) of every plane; a thread
-        // owns one 16-byte group in two consecutive rows
+        // the TMA kernel streams whole rows of every plane; a thread owns one 16-byte group in
+        // ROWS consecutive rows
         if (t.x0 != 0 || t.tx != m->fabs[t.fab].n[0]) return false;
         const int rows = std::min(m->tma_rows, tma_max_rows(R));
         maxgroups = std::max(maxgroups, (m->fabs[t.fab].n[0] + A - 1) / A * (((int)t.ty + rows - 1) / rows));
@@ -896,10 +906,13 @@ static bool tma_geometry(mf_t *m, int R, std::vector<TmaFab> &tf, int &slot_byte
         int ty = 1;
         for (auto &t : m->tiles)
             if (t.fab == (int)b && t.comp == 0) ty = std::max(ty, (int)t.ty);
-        tf[b].bx = m->fabs[b].px;
+        const int xvg = valid_x_elem(m);
+        const bool narrow = !served.empty() && served[2 * b] && served[2 * b + 1];
+        tf[b].bx = narrow ? (m->fabs[b].n[0] + A - 1) / A * A : m->fabs[b].px;
         tf[b].by = ty + 2 * R;
         tf[b].ngrow = g;
-        tf[b].xv = (g + A - 1) / A * A;  // row element of valid x = 0
+        tf[b].xs = narrow ? xvg : 0;
+        tf[b].xv = xvg - tf[b].xs;
         if (tf[b].bx > 256 || tf[b].by > 256) return false;
         maxplane = std::max(maxplane, tf[b].bx * tf[b].by * S);
     }
@@ -958,7 +971,7 @@ static void find_strips(mf_t *m, int R, std::vector<TileStrip> &st, std::vector<
             const int nA = Ab.len(0);
             // strip: XW elements of the owner's rows, starting 16-byte aligned at or before the R
             // cells next to the face (row element of cell x is xv + x)
-            const int xvA = (g + A - 1) / A * A;
+            const int xvA = valid_x_elem(m);
             const int start = side == 0 ? (xvA + nA - R) / A * A : xvA;
             const int y = g + q.lo[1] - Ab.lo[1], z = g + q.lo[2] - Ab.lo[2];
             if (side == 0) {
@@ -1025,7 +1038,14 @@ static int build_tma(mf_t *m, int R) {
     for (auto &t : m->tiles) srows = std::max(srows, (int)t.ty);
     std::vector<TmaFab> tf;
     int main_slot = 0, gpt = 0;
-    if (!tma_geometry(m, R, tf, main_slot, gpt)) return 0;
+    {
+        // faces served by strips for whole-box z extents stay served for any z split of them,
+        // so they fix the plane geometry before the balanced schedule is made
+        std::vector<TileStrip> st0;
+        std::vector<char> served0;
+        find_strips(m, R, st0, served0);
+        if (!tma_geometry(m, R, served0, tf, main_slot, gpt)) return 0;
+    }
     const int strip_bytes = XW * srows * S;
     const int strip_pitch = (strip_bytes + 127) / 128 * 128;
     const int slot = main_slot + 2 * strip_pitch;

@@ -110,9 +110,12 @@ constexpr int kMaxStages = 16;
 constexpr int kMaxPush = 16;  // ghost-push pieces per tile
 
 struct TmaFab {
-    int bx, by;   // box of one plane load: the whole row (bx elements, the row pitch), by rows
+    int bx, by;   // box of one plane load: bx elements of each of by rows
     int ngrow;
-    int xv;       // row element of valid x = 0 (16-byte aligned)
+    int xv;       // element of valid x = 0 within the loaded row
+    int xs;       // row element where the loaded row starts (16-byte aligned): 0 for the whole
+                  // row, or valid x = 0 when strips serve both x faces (valid cells only)
+    int pad_;
 };
 
 // x halo of a tile taken straight from the neighbouring box (its valid cells), or -1 when

@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
                 const bool centre = pl >= R && pl < R + t.tz;
                 const bool ls = centre && ts.lfab >= 0, rs = centre && ts.rfab >= 0;
                 mbar_expect_tx(&full[sl], plane_bytes + (ls ? p.strip_bytes : 0) + (rs ? p.strip_bytes : 0));
-                tma_load_4d(sp, map, &full[sl], 0, ycoord, zcoord + pl, t.comp);
+                tma_load_4d(sp, map, &full[sl], tf.xs, ycoord, zcoord + pl, t.comp);
                 if (ls) tma_load_4d(sp + p.strip_off, p.smaps + ts.lfab, &full[sl], ts.lx, ts.ly, ts.lz + pl - R, t.comp);
                 if (rs)
                     tma_load_4d(sp + p.strip_off + p.strip_pitch, p.smaps + ts.rfab, &full[sl], ts.rx, ts.ry,
@@ -231,8 +231,9 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
         const Tile t = p.tiles[w];
         const TmaFab tf = p.tfab[t.fab];
         const FabInfo f = p.ftab[t.fab];
-        const int xv = tf.xv;  // row element of valid x = 0
-        const int bx = tf.bx;  // whole row
+        const int xv = tf.xv;   // element of valid x = 0 in a loaded row
+        const int bx = tf.bx;   // elements of a loaded row
+        const int xvg = xv + tf.xs;  // row element of valid x = 0 in the FArrayBox
         TileStrip ts;
         ts.lfab = ts.rfab = -1;
         ts.pcount = 0;
@@ -314,11 +315,13 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
         }
         S *op = (S *)p.dst[f.level] + f.org + t.comp * f.cstride + (long long)t.z0 * f.plane +
                 (long long)(t.y0 + y0) * f.px + x0c;
-        // the groups at the row ends also complete the sectors they share with ghost / padding
-        // cells, writing don't-care values there (strips, not those cells, feed the stencil)
+        // a group at a row end that fills only half of a 32-byte sector also writes the other
+        // half (ghost / padding cells, don't-care values there: strips, not those cells, feed
+        // the stencil), so that no sector is written in part
         const bool full = x0c + VX <= f.n[0];
-        const bool lpad = act && x0c == 0 && xv >= VX && ((f.org - xv) * (long long)sizeof(S)) % 32 == 0;
-        const bool rpad = act && full && x0c + VX == f.n[0] && xv + f.n[0] + VX <= f.px;
+        const bool lpad = act && x0c == 0 && xvg >= VX && (f.org * (long long)sizeof(S)) % 32 == 16;
+        const bool rpad = act && full && x0c + VX == f.n[0] && xvg + f.n[0] + VX <= f.px &&
+                          ((f.org + f.n[0]) * (long long)sizeof(S)) % 32 == 16;
         const int xo = lpad ? -VX : VX;  // the extra store of a row-end group
         const bool both = __any_sync(0xffffffffu, lpad && rpad);  // one group spans the whole row
         const A lam = (A)p.lam[f.level][t.comp];
