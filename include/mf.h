@@ -121,9 +121,19 @@ int mf_get_tile(const mf_t *mf, int tile[3]);
 enum { MF_KERNEL_TMA = 0, MF_KERNEL_GLOBAL = 1 };
 int mf_set_kernel(mf_t *mf, int variant);
 
+/* Schedule of the TMA stencil besides the tile shape: in[0] rows per thread (1 or 2; 0 = 2),
+ * in[1] shared-memory ring slots (a power of two up to 16; 0 = by radius), in[2] bytes per
+ * row group of a thread (16 or 32; 0 = 16).  Where a radius or storage type lacks the
+ * combination the launch falls back to 16-byte groups and the rows the radius allows.
+ * Results do not depend on the schedule (identical bits).  The autotuner, when on, overrides
+ * it; MF_EINVAL for values out of range. */
+int mf_set_schedule(mf_t *mf, const int in[3]);
+
 /* The schedule in use (after the autotuner, if it ran): {tile x, y, z, rows per thread, ring
- * slots, kernel variant in use (MF_KERNEL_*)}. */
-int mf_get_schedule(const mf_t *mf, int out[6]);
+ * slots, kernel variant in use (MF_KERNEL_*), bytes per row group of a thread (16 or 32)}.
+ * A tile z extent of 0 means whole boxes, which the TMA kernel splits in z evenly over one
+ * wave of CTAs. */
+int mf_get_schedule(const mf_t *mf, int out[7]);
 
 /*
  * Dense host arrays are (ncomp, Nz, Ny, Nx) doubles over the whole domain, x fastest.

@@ -29,7 +29,7 @@ EXPORTS = [
     "mf_copy_fab_to_host", "mf_copy_fab_from_host", "mf_fill_boundary", "mf_interp_cf", "mf_average_down",
     "mf_advance", "mf_amr_advance", "mf_sum", "mf_step_bytes", "mf_current", "mf_last_error", "mf_set_timing",
     "mf_phase_ms", "mf_set_kernel", "mf_sum_strided_noalloc", "mf_get_schedule", "mf_launch_count",
-    "mf_fp64_fma_rate",
+    "mf_fp64_fma_rate", "mf_set_schedule",
 ]
 
 
@@ -81,6 +81,7 @@ def _load():
         "mf_get_schedule": (I, [P, P]),
         "mf_launch_count": (I, [P, P]),
         "mf_fp64_fma_rate": (I, [ctypes.POINTER(D), P]),
+        "mf_set_schedule": (I, [P, P]),
         "mf_sum_strided_noalloc": (I, [P, I, I, I, I, LL, LL, ctypes.POINTER(D), P]),
     }
     for name, (res, args) in sig.items():
@@ -252,11 +253,15 @@ def mf_set_kernel(h, variant):
     _check(lib.mf_set_kernel(h, int(variant)))
 
 
+def mf_set_schedule(h, rows=0, stages=0, group_bytes=0):
+    _check(lib.mf_set_schedule(h, _ptr(np.array([rows, stages, group_bytes], dtype=np.int32))))
+
+
 def mf_get_schedule(h):
-    out = np.zeros(6, dtype=np.int32)
+    out = np.zeros(7, dtype=np.int32)
     _check(lib.mf_get_schedule(h, _ptr(out)))
     return {"tile": tuple(int(v) for v in out[:3]), "rows": int(out[3]), "stages": int(out[4]),
-            "kernel": "tma" if out[5] == MF_KERNEL_TMA else "global"}
+            "kernel": "tma" if out[5] == MF_KERNEL_TMA else "global", "group_bytes": int(out[6])}
 
 
 def mf_set_timing(h, on):

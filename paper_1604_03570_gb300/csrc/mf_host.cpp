@@ -232,6 +232,7 @@ struct mf {
     bool tma_ok = false;      // current tile shape fits the TMA kernel
     int tma_cpt = 32, tma_slot = 0, tma_ns = 0;  // tma_cpt: CTA threads of the TMA stencil
     int tma_rows = 2;     // rows per consumer thread (autotuned; clipped to what the radius allows)
+    int tma_gb = 16;      // bytes per row group of a consumer thread, 16 or 32 (autotuned)
     int tma_ns_pref = 0;  // ring slots (0: by radius; autotuned)
     int tma_main_slot = 0, tma_strip_rows = 0, tma_strip_bytes = 0, tma_strip_pitch = 0, tma_strip_w = 0;
     bool use_tma = true;
@@ -885,6 +886,13 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
+// The schedule a radius-R launch uses: rows per thread clipped to what R allows; 32-byte
+// groups only where that variant exists, else 16-byte groups.
+static int eff_rows(const mf_t *m, int R) { return std::min(m->tma_rows, tma_max_rows(R)); }
+static int eff_gb(const mf_t *m, int R) {
+    return tma_has_group(m->dtype, R, eff_rows(m, R), m->tma_gb) ? m->tma_gb : 16;
+}
+
 // Plane geometry of every FArrayBox for the current tile shape and radius R; false when a
 // box needs a plane wider than the TMA box limit (256 per dimension) or more cells per
 // thread than the kernel keeps in registers.  A box whose two x faces are served by strips
@@ -895,12 +903,13 @@ static bool tma_geometry(mf_t *m, int R, const std::vector<char> &served, std::v
     const int S = m->esize, A = 16 / S, g = m->ngrow;
     tf.assign(m->fabs.size(), TmaFab{});
     int maxplane = 0, maxgroups = 0;
+    const int VXg = eff_gb(m, R) / S;  // cells per group
     for (auto &t : m->tiles) {
-        // the TMA kernel streams whole rows of every plane; a thread owns one 16-byte group in
-        // ROWS consecutive rows
+        // the TMA kernel streams whole rows of every plane; a thread owns one group in ROWS
+        // consecutive rows
         if (t.x0 != 0 || t.tx != m->fabs[t.fab].n[0]) return false;
-        const int rows = std::min(m->tma_rows, tma_max_rows(R));
-        maxgroups = std::max(maxgroups, (m->fabs[t.fab].n[0] + A - 1) / A * (((int)t.ty + rows - 1) / rows));
+        const int rows = eff_rows(m, R);
+        maxgroups = std::max(maxgroups, (m->fabs[t.fab].n[0] + VXg - 1) / VXg * (((int)t.ty + rows - 1) / rows));
     }
     for (size_t b = 0; b < m->fabs.size(); ++b) {
         int ty = 1;
@@ -1055,8 +1064,7 @@ static int build_tma(mf_t *m, int R) {
     if (ns < 2 * R + 1 || (long long)ns * slot + 128 > 200 * 1024) return 0;
     if (m->tile[2] <= 0) {
         // whole-box z extent: split the columns over exactly one wave of CTAs
-        const int rows = std::min(m->tma_rows, tma_max_rows(R));
-        const int per_sm = tma_ctas_per_sm(m->dtype, R, rows, gpt, ns * slot + 128);
+        const int per_sm = tma_ctas_per_sm(m->dtype, R, eff_rows(m, R), eff_gb(m, R), gpt, ns * slot + 128);
         if (per_sm < 1) return 0;
         const int G = per_sm * sm_count();
         balance_tiles(m, G, m->tiles, m->cta_tiles);
@@ -1248,8 +1256,7 @@ static int enqueue_stencil(mf_t *m, int from, int R, bool fp64diff, const double
         p.push = (push && m->tma_push) ? (const PushPiece *)m->d_push.p : nullptr;
         p.cta_tiles = m->tma_grid ? (const int *)m->d_cta.p : nullptr;
         for (int c = 0; c < m->ncomp; ++c) p.lam[0][c] = lam[c];
-        CU(launch_stencil_tma(m->dtype, R, fp64diff, std::min(m->tma_rows, tma_max_rows(R)), m->tma_cpt, p,
-                              m->tma_grid, s));
+        CU(launch_stencil_tma(m->dtype, R, fp64diff, eff_rows(m, R), eff_gb(m, R), m->tma_cpt, p, m->tma_grid, s));
         return 0;
     }
     StencilParams p = stencil_params(m, from, lam);
@@ -1289,15 +1296,17 @@ static int check_stencil(const mf_t *m, const mf_stencil *st, double dt, double 
 // point) and keep the fastest.  Synchronous; runs once per handle.
 static int autotune(mf_t *m, int R, bool fp64diff, const double *lam) {
     auto tiles = tile_candidates(m);
-    struct Cand { std::array<int, 3> t; int rows, ns; };
+    struct Cand { std::array<int, 3> t; int rows, ns, gb; };
     std::vector<Cand> cands;
     for (auto &t : tiles) {
         if (m->use_tma && t[0] == 0) {
             for (int rows = 1; rows <= tma_max_rows(R); ++rows)
-                for (int ns : {4, 8, 16})
-                    if (ns >= 2 * R + 1) cands.push_back({t, rows, ns});
+                for (int gb : {16, 32})
+                    if (tma_has_group(m->dtype, R, rows, gb))
+                        for (int ns : {4, 8, 16})
+                            if (ns >= 2 * R + 1) cands.push_back({t, rows, ns, gb});
         } else {
-            cands.push_back({t, 2, 0});
+            cands.push_back({t, 2, 0, 16});
         }
     }
     cudaEvent_t e0, e1;
@@ -1308,6 +1317,7 @@ static int autotune(mf_t *m, int R, bool fp64diff, const double *lam) {
     auto time_cand = [&](const Cand &c, int n, float *ms) -> int {
         m->tma_rows = c.rows;
         m->tma_ns_pref = c.ns;
+        m->tma_gb = c.gb;
         int rc = set_tiles(m, c.t.data());
         if (rc) return rc;
         if ((rc = enqueue_stencil(m, m->cur, R, fp64diff, lam, m->stream, true))) return rc;
@@ -1345,15 +1355,32 @@ static int autotune(mf_t *m, int R, bool fp64diff, const double *lam) {
     m->tile_auto = false;
     m->tma_rows = bc.rows;
     m->tma_ns_pref = bc.ns;
+    m->tma_gb = bc.gb;
     return set_tiles(m, bc.t.data());
 }
 
-extern "C" int mf_get_schedule(const mf_t *m, int out[6]) {
+extern "C" int mf_set_schedule(mf_t *m, const int in[3]) {
+    if (!m || !in) return fail(MF_EINVAL, "null argument");
+    const int rows = in[0] ? in[0] : 2, ns = in[1], gb = in[2] ? in[2] : 16;
+    if (rows < 1 || rows > 2) return fail(MF_EINVAL, "rows per thread must be 1 or 2");
+    if (ns != 0 && (ns < 2 || ns > kMaxStages || (ns & (ns - 1)))) return fail(MF_EINVAL, "ring slots: a power of two <= %d", kMaxStages);
+    if (gb != 16 && gb != 32) return fail(MF_EINVAL, "group bytes must be 16 or 32");
+    m->tma_rows = rows;
+    m->tma_ns_pref = ns;
+    m->tma_gb = gb;
+    m->tma_R = 0;  // rebuilt (and graphs dropped) at the next launch
+    invalidate_graphs(m);
+    return 0;
+}
+
+extern "C" int mf_get_schedule(const mf_t *m, int out[7]) {
     if (!m || !out) return fail(MF_EINVAL, "null argument");
     for (int d = 0; d < 3; ++d) out[d] = m->tile[d];
-    out[3] = m->tma_rows;
+    const int R = m->tma_R ? m->tma_R : 1;
+    out[3] = eff_rows(m, R);
     out[4] = m->tma_ns;
     out[5] = (m->use_tma && m->tma_ok) ? MF_KERNEL_TMA : MF_KERNEL_GLOBAL;
+    out[6] = eff_gb(m, R);
     return 0;
 }
 

@@ -164,12 +164,14 @@ struct StencilTmaParams {
 };
 
 // ---- launchers (mf_kernels.cu, stencil_tma.cu); all asynchronous on `s`
-cudaError_t launch_stencil_tma(int dtype, int R, bool fp64diff, int rows, int nt, const StencilTmaParams &p, int grid,
-                               cudaStream_t s);
+cudaError_t launch_stencil_tma(int dtype, int R, bool fp64diff, int rows, int gb, int nt, const StencilTmaParams &p,
+                               int grid, cudaStream_t s);
+// whether the TMA stencil has a schedule with rows rows of gb-byte groups per thread
+bool tma_has_group(int dtype, int R, int rows, int gb);
 int tma_max_threads(int R);      // largest CTA of the TMA stencil for radius R
-int tma_max_rows(int R);         // most rows of one 16-byte group a TMA stencil thread may compute
+int tma_max_rows(int R);         // most rows of 16-byte groups a TMA stencil thread may compute
 // resident CTAs per SM of the TMA stencil with nt threads and smem dynamic shared bytes (0: none)
-int tma_ctas_per_sm(int dtype, int R, int rows, int nt, int smem);
+int tma_ctas_per_sm(int dtype, int R, int rows, int gb, int nt, int smem);
 cudaError_t launch_fill(int dtype, const LevelPtrs &lv, const FbTask *tasks, int ntasks, int grid, cudaStream_t s);
 cudaError_t launch_stencil(int dtype, int R, bool fp64diff, const StencilParams &p, int bx, int by, int grid,
                            cudaStream_t s);

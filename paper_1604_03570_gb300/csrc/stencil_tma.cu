@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "mf_internal.h"
 #include "stencil_common.cuh"
@@ -111,6 +112,42 @@ template <> struct V16<__nv_bfloat16> {
     }
 };
 
+// Groups of a thread's row: GB = 16 bytes (V16), or GB = 32 bytes -- one whole 32-byte
+// sector, stored with one 256-bit store -- for FP32 and FP64 storage.
+template <typename S, int GB> struct VG;
+template <typename S> struct VG<S, 16> : V16<S> {};
+template <> struct VG<float, 32> {
+    static constexpr int n = 8;
+    template <typename A> static __device__ __forceinline__ void ld(const float *p, A *o) {
+        V16<float>::ld(p, o);
+        V16<float>::ld(p + 4, o + 4);
+    }
+    static __device__ __forceinline__ void st8(float *p, float a0, float a1, float a2, float a3, float a4, float a5,
+                                               float a6, float a7) {
+        asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(a0), "f"(a1), "f"(a2),
+                     "f"(a3), "f"(a4), "f"(a5), "f"(a6), "f"(a7)
+                     : "memory");
+    }
+    static __device__ __forceinline__ void st(float *p, const float *v) {
+        st8(p, v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7]);
+    }
+    static __device__ __forceinline__ void st(float *p, const double *v) {
+        st8(p, __double2float_rn(v[0]), __double2float_rn(v[1]), __double2float_rn(v[2]), __double2float_rn(v[3]),
+            __double2float_rn(v[4]), __double2float_rn(v[5]), __double2float_rn(v[6]), __double2float_rn(v[7]));
+    }
+};
+template <> struct VG<double, 32> {
+    static constexpr int n = 4;
+    template <typename A> static __device__ __forceinline__ void ld(const double *p, A *o) {
+        V16<double>::ld(p, o);
+        V16<double>::ld(p + 2, o + 2);
+    }
+    static __device__ __forceinline__ void st(double *p, const double *v) {
+        asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(p), "d"(v[0]), "d"(v[1]), "d"(v[2]), "d"(v[3])
+                     : "memory");
+    }
+};
+
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -137,9 +174,10 @@ struct PushRec {
 };
 
 
-template <typename S, typename A, int R, int ROWS>
+template <typename S, typename A, int R, int ROWS, int GB>
 __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __grid_constant__ StencilTmaParams p) {
-    constexpr int VX = V16<S>::n;  // cells per group: one 16-byte vector of a row
+    using V = VG<S, GB>;
+    constexpr int VX = V::n;  // cells per group: one GB-byte vector of a row
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];
     unsigned char *slots = (unsigned char *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
@@ -336,7 +374,7 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
 #pragma unroll
             for (int r = 0; r < ROWS; ++r) {
                 A v[VX];
-                V16<S>::ld(sp + soff + r * bx, v);
+                V::ld(sp + soff + r * bx, v);
 #pragma unroll
                 for (int c = 0; c < VX; ++c) q[r][c][pl] = v[c];
             }
@@ -364,7 +402,7 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
 #pragma unroll
             for (int r = 0; r < ROWS; ++r) {
                 A v[VX];
-                V16<S>::ld(newp + soff + r * bx, v);
+                V::ld(newp + soff + r * bx, v);
 #pragma unroll
                 for (int c = 0; c < VX; ++c) q[r][c][2 * R] = v[c];
             }
@@ -375,7 +413,7 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
 #pragma unroll
             for (int m = 0; m < 2 * R + ROWS; ++m) {
                 if (m >= R && m < R + ROWS) continue;
-                V16<S>::ld(cc + (m - R) * bx, wy[m]);
+                V::ld(cc + (m - R) * bx, wy[m]);
             }
 #pragma unroll
             for (int r = 0; r < ROWS; ++r)
@@ -432,14 +470,14 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
                     if (r >= nrow) continue;
                     S *orow = o + r * f.px;
                     if (full) {
-                        V16<S>::st(orow, out[r]);
+                        V::st(orow, out[r]);
                     } else {
 #pragma unroll
                         for (int c = 0; c < VX; ++c)
                             if (x0c + c < f.n[0]) st(orow + c, out[r][c]);
                     }
-                    if (lpad || rpad) V16<S>::st(orow + xo, out[r]);
-                    if (both && lpad && rpad) V16<S>::st(orow + VX, out[r]);
+                    if (lpad || rpad) V::st(orow + xo, out[r]);
+                    if (both && lpad && rpad) V::st(orow + VX, out[r]);
                 }
             }
             if (wm) {
@@ -462,8 +500,8 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
                         if (r >= nrow || yy < py0 || yy >= py1) continue;
                         S *gp = (S *)(uintptr_t)(b + (unsigned long long)(k * dplane + (long long)yy * dpx + x0c) *
                                                          sizeof(S));
-                        if ((xr >> 31) && full && ((uintptr_t)gp & 15) == 0) {
-                            V16<S>::st(gp, out[r]);
+                        if ((xr >> 31) && full && ((uintptr_t)gp & (GB - 1)) == 0) {
+                            V::st(gp, out[r]);
                         } else {
 #pragma unroll
                             for (int c = 0; c < VX; ++c) {
@@ -480,24 +518,24 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
 }
 
 // Raise the kernel's dynamic shared-memory limit to at least smem (never lowers it).
-template <typename S, typename A, int R, int ROWS>
+template <typename S, typename A, int R, int ROWS, int GB>
 static cudaError_t tma_configure(int smem) {
     static int configured = 0;
     if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_stencil_tma<S, A, R, ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             smem);
+        cudaError_t e = cudaFuncSetAttribute(k_stencil_tma<S, A, R, ROWS, GB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         configured = smem;
     }
     return cudaSuccess;
 }
 
-template <typename S, typename A, int R, int ROWS>
+template <typename S, typename A, int R, int ROWS, int GB>
 static cudaError_t tma_t(int nt, const StencilTmaParams &p, int grid, cudaStream_t s) {
     if (nt < 64 || nt > TmaBounds<R>::threads || nt % 32) return cudaErrorInvalidValue;
     const int smem = p.nstages * p.slot_bytes + 128;
-    auto kern = k_stencil_tma<S, A, R, ROWS>;
-    cudaError_t e = tma_configure<S, A, R, ROWS>(smem);
+    auto kern = k_stencil_tma<S, A, R, ROWS, GB>;
+    cudaError_t e = tma_configure<S, A, R, ROWS, GB>(smem);
     if (e != cudaSuccess) return e;
     int g = grid;
     if (g <= 0) {
@@ -521,74 +559,94 @@ static cudaError_t tma_t(int nt, const StencilTmaParams &p, int grid, cudaStream
     return cudaLaunchKernelEx(&cfg, kern, p);
 }
 
-template <typename S, typename A>
-static cudaError_t tma_r(int R, int rows, int nt, const StencilTmaParams &p, int grid, cudaStream_t s) {
-    switch (R * 4 + rows) {
-        case 1 * 4 + 1: return tma_t<S, A, 1, 1>(nt, p, grid, s);
-        case 1 * 4 + 2: return tma_t<S, A, 1, 2>(nt, p, grid, s);
-        case 2 * 4 + 1: return tma_t<S, A, 2, 1>(nt, p, grid, s);
-        case 2 * 4 + 2: return tma_t<S, A, 2, 2>(nt, p, grid, s);
-        case 4 * 4 + 1: return tma_t<S, A, 4, 1>(nt, p, grid, s);
-    }
-    return cudaErrorInvalidValue;
-}
-
-template <typename S, typename A, int R, int ROWS>
+template <typename S, typename A, int R, int ROWS, int GB>
 static int tma_occ(int nt, int smem) {
     if (nt < 64 || nt > TmaBounds<R>::threads || nt % 32) return 0;
-    if (tma_configure<S, A, R, ROWS>(smem) != cudaSuccess) return 0;
+    if (tma_configure<S, A, R, ROWS, GB>(smem) != cudaSuccess) return 0;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stencil_tma<S, A, R, ROWS>, nt, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stencil_tma<S, A, R, ROWS, GB>, nt, smem) !=
+        cudaSuccess)
         return 0;
     return per_sm;
 }
 
-// Residency of the storage type's two instantiations (FP64 differences or not): the smaller,
-// so that one schedule fits both in one wave.
 template <typename S> struct NativeArith { using T = S; };  // bf16 values compute in FP32
 template <> struct NativeArith<__nv_bfloat16> { using T = float; };
 
-template <typename S, int R, int ROWS>
-static int tma_occ2(int nt, int smem) {
-    return std::min(tma_occ<S, typename NativeArith<S>::T, R, ROWS>(nt, smem), tma_occ<S, double, R, ROWS>(nt, smem));
-}
+// The instantiated schedules: (R, rows, group bytes).  32-byte groups exist for FP32 and FP64
+// storage with one row per thread and R <= 2 (registers).
+template <typename S> constexpr bool kHasWide = !std::is_same<S, __nv_bfloat16>::value;
 
-template <typename S>
-static int tma_occ_r(int R, int rows, int nt, int smem) {
-    switch (R * 4 + rows) {
-        case 1 * 4 + 1: return tma_occ2<S, 1, 1>(nt, smem);
-        case 1 * 4 + 2: return tma_occ2<S, 1, 2>(nt, smem);
-        case 2 * 4 + 1: return tma_occ2<S, 2, 1>(nt, smem);
-        case 2 * 4 + 2: return tma_occ2<S, 2, 2>(nt, smem);
-        case 4 * 4 + 1: return tma_occ2<S, 4, 1>(nt, smem);
+// Calls f.template run<R, ROWS, GB>() for the instantiated schedule, else returns fallback.
+template <typename S, typename F, typename T>
+static T tma_dispatch(int R, int rows, int gb, F &&f, T fallback) {
+    switch ((R * 4 + rows) * 2 + (gb == 32 ? 1 : 0)) {
+        case (1 * 4 + 1) * 2: return f.template run<1, 1, 16>();
+        case (1 * 4 + 2) * 2: return f.template run<1, 2, 16>();
+        case (2 * 4 + 1) * 2: return f.template run<2, 1, 16>();
+        case (2 * 4 + 2) * 2: return f.template run<2, 2, 16>();
+        case (4 * 4 + 1) * 2: return f.template run<4, 1, 16>();
+        case (1 * 4 + 1) * 2 + 1:
+            if constexpr (kHasWide<S>) return f.template run<1, 1, 32>();
+            break;
+        case (2 * 4 + 1) * 2 + 1:
+            if constexpr (kHasWide<S>) return f.template run<2, 1, 32>();
+            break;
     }
-    return 0;
+    return fallback;
 }
 
-int tma_ctas_per_sm(int dtype, int R, int rows, int nt, int smem) {
+template <typename S, typename A>
+struct LaunchF {
+    int nt;
+    const StencilTmaParams &p;
+    int grid;
+    cudaStream_t s;
+    template <int R, int ROWS, int GB> cudaError_t run() { return tma_t<S, A, R, ROWS, GB>(nt, p, grid, s); }
+};
+
+// Residency of the storage type's two instantiations (FP64 differences or not): the smaller,
+// so that one schedule fits both in one wave.
+template <typename S>
+struct OccF {
+    int nt, smem;
+    template <int R, int ROWS, int GB> int run() {
+        return std::min(tma_occ<S, typename NativeArith<S>::T, R, ROWS, GB>(nt, smem),
+                        tma_occ<S, double, R, ROWS, GB>(nt, smem));
+    }
+};
+
+int tma_ctas_per_sm(int dtype, int R, int rows, int gb, int nt, int smem) {
     switch (dtype) {
-        case F64: return tma_occ_r<double>(R, rows, nt, smem);
-        case F32: return tma_occ_r<float>(R, rows, nt, smem);
-        case BF16: return tma_occ_r<__nv_bfloat16>(R, rows, nt, smem);
+        case F64: return tma_dispatch<double>(R, rows, gb, OccF<double>{nt, smem}, 0);
+        case F32: return tma_dispatch<float>(R, rows, gb, OccF<float>{nt, smem}, 0);
+        case BF16: return tma_dispatch<__nv_bfloat16>(R, rows, gb, OccF<__nv_bfloat16>{nt, smem}, 0);
     }
     return 0;
 }
 
 int tma_max_threads(int R) { return R == 1 ? TmaBounds<1>::threads : R == 2 ? TmaBounds<2>::threads : TmaBounds<4>::threads; }
 int tma_max_rows(int R) { return R == 4 ? 1 : 2; }
+bool tma_has_group(int dtype, int R, int rows, int gb) {
+    if (gb == 16) return rows >= 1 && rows <= tma_max_rows(R);
+    return gb == 32 && dtype != BF16 && R <= 2 && rows == 1;
+}
 
-cudaError_t launch_stencil_tma(int dtype, int R, bool fp64diff, int rows, int nt, const StencilTmaParams &p, int grid,
-                               cudaStream_t s) {
+cudaError_t launch_stencil_tma(int dtype, int R, bool fp64diff, int rows, int gb, int nt, const StencilTmaParams &p,
+                               int grid, cudaStream_t s) {
     if (p.ntiles == 0) return cudaSuccess;
     if (p.nstages > kMaxStages || p.nstages < 2 * R + 1 || (p.nstages & (p.nstages - 1))) return cudaErrorInvalidValue;
-    if (rows < 1 || rows > tma_max_rows(R)) return cudaErrorInvalidValue;
+    if (!tma_has_group(dtype, R, rows, gb)) return cudaErrorInvalidValue;
     switch (dtype) {
-        case F64: return tma_r<double, double>(R, rows, nt, p, grid, s);
+        case F64: return tma_dispatch<double>(R, rows, gb, LaunchF<double, double>{nt, p, grid, s}, cudaErrorInvalidValue);
         case F32:
-            return fp64diff ? tma_r<float, double>(R, rows, nt, p, grid, s) : tma_r<float, float>(R, rows, nt, p, grid, s);
+            return fp64diff ? tma_dispatch<float>(R, rows, gb, LaunchF<float, double>{nt, p, grid, s}, cudaErrorInvalidValue)
+                            : tma_dispatch<float>(R, rows, gb, LaunchF<float, float>{nt, p, grid, s}, cudaErrorInvalidValue);
         case BF16:
-            return fp64diff ? tma_r<__nv_bfloat16, double>(R, rows, nt, p, grid, s)
-                            : tma_r<__nv_bfloat16, float>(R, rows, nt, p, grid, s);
+            return fp64diff ? tma_dispatch<__nv_bfloat16>(R, rows, gb, LaunchF<__nv_bfloat16, double>{nt, p, grid, s},
+                                                          cudaErrorInvalidValue)
+                            : tma_dispatch<__nv_bfloat16>(R, rows, gb, LaunchF<__nv_bfloat16, float>{nt, p, grid, s},
+                                                          cudaErrorInvalidValue);
     }
     return cudaErrorInvalidValue;
 }

@@ -226,6 +226,34 @@ def test_layout_and_tile_invariance_bitwise(dtype, R):
         np.testing.assert_array_equal(o, outs[0])
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("R", [1, 2])
+def test_schedule_invariance_bitwise_and_parity(dtype, R):
+    """Rows per thread, ring depth and 16- or 32-byte row groups change how the TMA kernel
+    walks the tile, not the arithmetic: identical bits, FP64 within the oracle tolerance.
+    Includes a row of 60 cells (a partial last 32-byte group) and thin boxes."""
+    lo, hi = [0, 0, 0], [59, 23, 19]
+    boxes = np.array([[0, 0, 0, 59, 11, 19], [0, 12, 0, 27, 23, 9], [28, 12, 0, 59, 23, 9],
+                      [0, 12, 10, 59, 23, 19]], dtype=np.int32)
+    dense = rand_field((2, 20, 24, 60), 50 + R, dtype)
+    dt = {1: 0.15, 2: 0.1125}[R] / (60 * 60)
+    outs, scheds = [], []
+    for rows, stages, gb in [(2, 8, 16), (1, 4, 16), (1, 8, 32), (1, 16, 32), (2, 0, 32)]:
+        g = gpu_level(lo, hi, boxes=boxes, ncomp=2, ngrow=R, dtype=dtype)
+        g.set_tile((0, 8, 0))
+        mf.mf_set_schedule(g.h, rows, stages, gb)
+        g.from_host(dense)
+        g.advance(R, [1.0, 0.5], dt, 7)
+        outs.append(g.to_host())
+        scheds.append(mf.mf_get_schedule(g.h))
+    assert scheds[2]["group_bytes"] == (16 if dtype == "bf16" else 32) and scheds[2]["kernel"] == "tma"
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o, outs[0])
+    if dtype == "f64":
+        ref = _oracle_advance(boxes, lo, hi, R, 2, R, np.array([1.0, 0.5]) * dt * 3600.0, 7, dense)
+        assert rel_err(outs[0], ref) <= FP64_TOL
+
+
 # --------------------------------------------------------------------------- reduced precision
 
 @pytest.mark.parametrize("dtype,bound", [("f32", 2e-6), ("bf16", 3e-2)])
