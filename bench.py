@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="headline only (no FP64, e2e, CPU baseline)")
     p.add_argument("--tile", default=None, help="fixed tile 'x,y,z' instead of the autotuner (0 = whole box)")
     p.add_argument("--kernel", default="tma", choices=["tma", "global"], help="stencil kernel variant")
+    p.add_argument("--schedule", default=None,
+                   help="fixed schedule 'x,y,z,rows,stages,group_bytes' instead of the autotuner")
     return p.parse_args()
 
 
@@ -295,6 +297,10 @@ def run_ours(args, cfg, ws, rank, local):
     head = level(args.dtype)
     if args.tile:
         head.set_tile(tuple(int(v) for v in args.tile.split(",")))
+    if args.schedule:
+        v = [int(x) for x in args.schedule.split(",")]
+        head.set_tile(tuple(v[:3]))
+        mf.mf_set_schedule(head.h, *v[3:6])
     mf.mf_set_kernel(head.h, mf.MF_KERNEL_TMA if args.kernel == "tma" else mf.MF_KERNEL_GLOBAL)
     for _ in range(args.warmup):
         mf.mf_advance(head.h, R, D, dt, nsteps)
