@@ -315,7 +315,6 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
             const bool hit = act && y0 + nrow > py0 && y0 < py1 && ((xr >> 31) || (x0c < px1 && x0c + VX > px0));
             if (hit) pmask |= 1u << pi;
         }
-        const uint32_t wm = __reduce_or_sync(0xffffffffu, pmask);
 
         // fixed for the tile: output pointer (advanced one plane per step) and the shared-memory
         // offset of every x-halo cell -- the loaded row for cells of the box (and for filled
@@ -363,6 +362,46 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
         const int xo = lpad ? -VX : VX;  // the extra store of a row-end group
         const bool both = __any_sync(0xffffffffu, lpad && rpad);  // one group spans the whole row
         const A lam = (A)p.lam[f.level][t.comp];
+
+        // Pieces that cover every plane of the tile and whole rows (the y faces) become one
+        // destination pointer per row of this thread, advanced a plane per step; the rest (z faces,
+        // one or two planes per tile, and irregular pieces) take the general loop below.
+        S *fyp[ROWS];
+        uint32_t fmask = 0u;  // bit r: row r is also stored at fyp[r]
+        long long fdp = 0;    // their common plane stride
+        uint32_t slow = pmask;
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) fyp[r] = nullptr;
+        for (int pi = 0; pi < ts.pcount; ++pi) {
+            if (!(pmask & (1u << pi))) continue;
+            const uint32_t zr = ptw[pi].zr, yr = ptw[pi].yr, xr = ptw[pi].xr;
+            const long long dplane = ptw[pi].plane;
+            if ((zr & 0xffffu) != 0u || (int)(zr >> 16) < t.tz || !(xr >> 31) || !full) continue;
+            if (fdp != 0 && fdp != dplane) continue;
+            const int py0 = (int)(yr & 0xffffu), py1 = (int)(yr >> 16);
+            const unsigned long long b = ptw[pi].base;
+            const int dpx = ptw[pi].px;
+            bool ok = true;
+            uint32_t take = 0u;
+            S *gp[ROWS];
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+                const int yy = y0 + r;
+                gp[r] = nullptr;
+                if (r >= nrow || yy < py0 || yy >= py1) continue;
+                gp[r] = (S *)(uintptr_t)(b + (unsigned long long)((long long)yy * dpx + x0c) * sizeof(S));
+                if ((fmask & (1u << r)) || ((uintptr_t)gp[r] & (GB - 1)) != 0) ok = false;
+                take |= 1u << r;
+            }
+            if (!ok || !take) continue;
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r)
+                if (take & (1u << r)) fyp[r] = gp[r];
+            fmask |= take;
+            fdp = dplane;
+            slow &= ~(1u << pi);
+        }
+        const uint32_t wm = __reduce_or_sync(0xffffffffu, slow);
 
         A q[ROWS][VX][2 * R + 1];  // z queue per cell: q[r][c][i] = u(z - R + i)
         A fzm[ROWS][VX];
@@ -480,14 +519,21 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
                     if (both && lpad && rpad) V::st(orow + VX, out[r]);
                 }
             }
+            // ghost push: the same values into the neighbour boxes whose ghost faces hold them
+            if (fmask) {
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) {
+                    if (fmask & (1u << r)) V::st(fyp[r], out[r]);
+                    fyp[r] += fdp;
+                }
+            }
             if (wm) {
-                // ghost push: the same values into the neighbour boxes whose ghost faces hold them
                 uint32_t m = wm;
                 while (m) {
                     const int pi = __ffs(m) - 1;
                     m &= m - 1;
                     const uint32_t zr = ptw[pi].zr;
-                    if (k < (int)(zr & 0xffffu) || k >= (int)(zr >> 16) || !(pmask & (1u << pi))) continue;
+                    if (k < (int)(zr & 0xffffu) || k >= (int)(zr >> 16) || !(slow & (1u << pi))) continue;
                     const unsigned long long b = ptw[pi].base;
                     const long long dplane = ptw[pi].plane;
                     const int dpx = ptw[pi].px;
