@@ -196,6 +196,21 @@ int mf_amr_advance(mf_t *crse, mf_t *fine, const mf_stencil *st, double dt_crse,
  * reduction (the paper's example is mf.max(0)). */
 int mf_sum(mf_t *mf, int comp, double *out);
 
+/* mf_reduce -- whole-level reduction of component comp over all valid cells of the current time
+ * level (Sec. 3.1: a MultiFab answers sum, max and norm queries; the paper's example is
+ * mf.max(0)); synchronises the stream and writes the result to *out.
+ *   MF_RED_SUM    sum of u            (FP64, Neumaier-compensated; = mf_sum)
+ *   MF_RED_MAX    max u               (exact)
+ *   MF_RED_MIN    min u               (exact)
+ *   MF_RED_NORM0  max |u|             (exact)
+ *   MF_RED_NORM1  sum |u|             (FP64, compensated)
+ *   MF_RED_NORM2  sqrt(sum u^2)       (squares rounded to FP64, sum compensated, then sqrt)
+ * NaN values are skipped by MAX, MIN and NORM0.  The rows of the boxes are reduced in a fixed
+ * order and tree, so the bits depend only on the box layout.  MF_EINVAL for a bad component or
+ * operation, MF_ESTATE before mf_attach. */
+enum { MF_RED_SUM = 0, MF_RED_MAX = 1, MF_RED_MIN = 2, MF_RED_NORM0 = 3, MF_RED_NORM1 = 4, MF_RED_NORM2 = 5 };
+int mf_reduce(mf_t *mf, int comp, int op, double *out);
+
 /* Algorithmic bytes per step of the sweep: S*C*(2V + 2G + G_face) (valid cells read and
  * written, ghost cells copied, face ghosts read by the stencil of radius R). */
 double mf_step_bytes(const mf_t *mf, int R);

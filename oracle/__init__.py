@@ -19,6 +19,8 @@ What each function follows (section of arXiv 1604.03570):
 * ``domain_sum``      -- the whole-level reduction (Sec. 3.1, mf.max(0) is the example), here
                          the sum of one component over the valid cells, correctly rounded
                          (Shewchuk's exact summation as implemented by ``math.fsum``).
+* ``reduce``          -- the other MultiFab reductions of Sec. 3.1 by their definitions: max,
+                         min, max |u|, sum |u| (correctly rounded), and the 2-norm.
 * ``interp_cf`` / ``average_down`` / ``amr_advance`` -- the inter-level operations of a
                          refined level (Sec. 3, ratio 2 or 4); the paper gives no formula, the
                          readings are trilinear space / linear time interpolation of uncovered
@@ -189,6 +191,39 @@ def domain_sum(level, data, comp=0):
         nz, ny, nx = f.shape
         parts.append(f[g:nz - g, g:ny - g, g:nx - g].ravel())
     return math.fsum(np.concatenate(parts).tolist()) if parts else 0.0
+
+
+def _valid_cells(level, data, comp):
+    g = level.g
+    parts = []
+    for b in range(level.nbox):
+        f = level.fab(data, b)[comp]
+        nz, ny, nx = f.shape
+        parts.append(f[g:nz - g, g:ny - g, g:nx - g].ravel())
+    return np.concatenate(parts)
+
+
+def reduce(level, data, op, comp=0):
+    """The MultiFab reductions of Sec. 3.1 (mf.max(0) is the paper's example) over the valid
+    cells of component comp, each by its definition: "sum" (correctly rounded, math.fsum),
+    "max", "min", "norm0" (max |u|), "norm1" (sum |u|, correctly rounded) and "norm2"
+    (square root of the correctly rounded sum of the FP64 squares).  NaN values are skipped by
+    the max-type reductions."""
+    v = _valid_cells(level, data, comp)
+    if op == "sum":
+        return math.fsum(v.tolist())
+    if op == "norm1":
+        return math.fsum(np.abs(v).tolist())
+    if op == "norm2":
+        return math.sqrt(math.fsum((v * v).tolist()))
+    v = v[~np.isnan(v)]
+    if op == "max":
+        return float(np.max(v))
+    if op == "min":
+        return float(np.min(v))
+    if op == "norm0":
+        return float(np.max(np.abs(v)))
+    raise ValueError("unknown reduction %r" % (op,))
 
 
 def interp_cf(fine, crse, ratio, alpha, c_old, c_new, fdata):

@@ -21,6 +21,9 @@ DTYPES = {"f64": MF_F64, "f32": MF_F32, "bf16": MF_BF16}
 MF_LAP2_7PT, MF_LAP4_13PT, MF_LAP8_25PT = 1, 2, 4
 MF_FP64_DIFF, MF_PLAIN_PER_BOX = 1, 2
 MF_KERNEL_TMA, MF_KERNEL_GLOBAL = 0, 1
+MF_RED_SUM, MF_RED_MAX, MF_RED_MIN, MF_RED_NORM0, MF_RED_NORM1, MF_RED_NORM2 = 0, 1, 2, 3, 4, 5
+REDUCTIONS = {"sum": MF_RED_SUM, "max": MF_RED_MAX, "min": MF_RED_MIN, "norm0": MF_RED_NORM0,
+              "norm1": MF_RED_NORM1, "norm2": MF_RED_NORM2}
 MF_EINVAL, MF_ENOMEM, MF_ECUDA, MF_EUNSTABLE, MF_EALIGN, MF_ESTATE = -1, -2, -3, -4, -5, -6
 
 EXPORTS = [
@@ -29,7 +32,7 @@ EXPORTS = [
     "mf_copy_fab_to_host", "mf_copy_fab_from_host", "mf_fill_boundary", "mf_interp_cf", "mf_average_down",
     "mf_advance", "mf_amr_advance", "mf_sum", "mf_step_bytes", "mf_current", "mf_last_error", "mf_set_timing",
     "mf_phase_ms", "mf_set_kernel", "mf_sum_strided_noalloc", "mf_get_schedule", "mf_launch_count",
-    "mf_fp64_fma_rate", "mf_set_schedule",
+    "mf_fp64_fma_rate", "mf_set_schedule", "mf_reduce",
 ]
 
 
@@ -82,6 +85,7 @@ def _load():
         "mf_launch_count": (I, [P, P]),
         "mf_fp64_fma_rate": (I, [ctypes.POINTER(D), P]),
         "mf_set_schedule": (I, [P, P]),
+        "mf_reduce": (I, [P, I, I, ctypes.POINTER(D)]),
         "mf_sum_strided_noalloc": (I, [P, I, I, I, I, LL, LL, ctypes.POINTER(D), P]),
     }
     for name, (res, args) in sig.items():
@@ -274,6 +278,14 @@ def mf_phase_ms(h):
     return float(out[0]), float(out[1])
 
 
+def mf_reduce(h, comp, op):
+    """Whole-level reduction of one component; op is a name of REDUCTIONS or an MF_RED_* code."""
+    out = ctypes.c_double()
+    code = REDUCTIONS[op] if isinstance(op, str) else int(op)
+    _check(lib.mf_reduce(h, int(comp), code, ctypes.byref(out)))
+    return out.value
+
+
 def mf_launch_count(h):
     """Kernel launches of the last advance: fill, stencil, interp, average-down."""
     out = np.zeros(4, dtype=np.int32)
@@ -357,6 +369,9 @@ class MultiFab:
 
     def sum(self, comp=0):
         return mf_sum(self.h, comp)
+
+    def reduce(self, op, comp=0):
+        return mf_reduce(self.h, comp, op)
 
     def set_tile(self, tile):
         mf_set_tile(self.h, tile)

@@ -223,6 +223,7 @@ struct mf {
     int cur = 0;
     bool attached = false;
     DevBuf d_fabs, d_fb, d_fbtasks, d_tiles, d_cbeg, d_partials, d_sumout;
+    DevBuf d_rowpre;  // first valid row (y, z) of every FArrayBox in the reductions' row list
     // TMA-staged stencil: tensor maps of every FArrayBox over each time level, plane geometry
     DevBuf d_maps, d_tfab, d_err, d_smaps, d_strips, d_fbtasks_adv, d_push, d_fbtasks_res;
     std::vector<FbTask> fbtasks_res;  // the fill left once the stencil pushes face ghosts
@@ -643,6 +644,12 @@ extern "C" int mf_attach(mf_t *m, void *dev_ptr, size_t bytes, void *stream) {
     if ((rc = m->d_fb.upload(m->fb, m->stream))) return rc;
     if ((rc = m->d_fbtasks.upload(m->fbtasks, m->stream))) return rc;
     if ((rc = m->d_cbeg.upload(m->fb_cbeg, m->stream))) return rc;
+    {
+        std::vector<long long> rowpre(m->fabs.size() + 1, 0);
+        for (size_t b = 0; b < m->fabs.size(); ++b)
+            rowpre[b + 1] = rowpre[b] + (long long)m->fabs[b].n[1] * m->fabs[b].n[2];
+        if ((rc = m->d_rowpre.upload(rowpre, m->stream))) return rc;
+    }
     // tile buffer large enough for every autotune candidate
     size_t cap = m->tiles.size();
     std::vector<Tile> tmp;
@@ -1581,19 +1588,23 @@ extern "C" int mf_advance(mf_t *m, const mf_stencil *st, double dt, int nsteps) 
 
 // ------------------------------------------------------------------ reduction
 
-extern "C" int mf_sum(mf_t *m, int comp, double *out) {
+extern "C" int mf_reduce(mf_t *m, int comp, int op, double *out) {
     int rc = need_attached(m);
     if (rc) return rc;
     if (comp < 0 || comp >= m->ncomp || !out) return fail(MF_EINVAL, "bad component or null out");
+    if (op < MF_RED_SUM || op > MF_RED_NORM2) return fail(MF_EINVAL, "unknown reduction %d", op);
     const int grid = 304;  // fixed: the reduction tree, hence the bits, do not depend on the GPU
-    CU(launch_sum(m->dtype, m->level_ptr(m->cur), (const FabInfo *)m->d_fabs.p, (const Tile *)m->d_tiles.p,
-                  (int)m->tiles.size(), comp, (double2 *)m->d_partials.p, grid, (double *)m->d_sumout.p, m->stream));
+    CU(launch_reduce(m->dtype, op, m->level_ptr(m->cur), (const FabInfo *)m->d_fabs.p,
+                     (const long long *)m->d_rowpre.p, (int)m->fabs.size(), comp, (double2 *)m->d_partials.p, grid,
+                     (double *)m->d_sumout.p, m->stream));
     CU(cudaMemcpyAsync(m->h_sum, m->d_sumout.p, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
     CU(cudaStreamSynchronize(m->stream));
     if ((rc = check_device_error(m))) return rc;
     *out = *m->h_sum;
     return 0;
 }
+
+extern "C" int mf_sum(mf_t *m, int comp, double *out) { return mf_reduce(m, comp, MF_RED_SUM, out); }
 
 // ------------------------------------------------------------------ AMR
 

@@ -180,8 +180,10 @@ cudaError_t launch_stencil_plain(int dtype, int R, const void *src, void *dst, c
                                  int comp, cudaStream_t s);
 cudaError_t launch_fill_plain(int dtype, void *base, const FabInfo *ftab, const FbEntry *ent, int count,
                               long long total, const int *cbeg, cudaStream_t s);
-cudaError_t launch_sum(int dtype, const void *base, const FabInfo *ftab, const Tile *tiles, int ntiles, int comp,
-                       double2 *partials, int grid, double *out_dev, cudaStream_t s);
+// whole-level reduction of one component (RED_*), result written to out_dev (device)
+enum { RED_SUM = 0, RED_MAX = 1, RED_MIN = 2, RED_NORM0 = 3, RED_NORM1 = 4, RED_NORM2 = 5 };
+cudaError_t launch_reduce(int dtype, int op, const void *base, const FabInfo *ftab, const long long *rowpre, int nfab,
+                          int comp, double2 *partials, int grid, double *out_dev, cudaStream_t s);
 cudaError_t launch_scatter_dense(int dtype, void *base, const FabInfo *ftab, int nfab, const double *stage,
                                  const int dlo[3], const int dn[3], int z0, int z1, int comp, int ncomp_chunk,
                                  cudaStream_t s);

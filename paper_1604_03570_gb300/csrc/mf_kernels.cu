@@ -9,9 +9,9 @@
 //                   a register queue of 2R+1 values, so the z-face flux of the previous
 //                   cell is reused; x and y neighbours come through L1.
 //   k_stencil_plain the untiled per-box baseline of Sec. 3.1 (one launch per box).
-//   k_sum_*         whole-level reduction (Sec. 3.1 mf.max(0) analogue): FP64 Neumaier
-//                   compensated sums, fixed reduction tree, so the result does not depend
-//                   on timing.
+//   k_reduce_*      whole-level reductions (Sec. 3.1: the sum, mf.max(0) and norms): FP64
+//                   Neumaier-compensated sums, exact max / min, a fixed reduction tree over
+//                   the box layout's rows, so the result depends on neither tiles nor timing.
 //   k_interp / k_avgdown   inter-level operations of a refined level (Sec. 3).
 //   k_scatter / k_gather   dense host layout <-> FArrayBoxes with dtype conversion.
 //
@@ -181,31 +181,110 @@ __global__ void k_stencil_plain(const S *__restrict__ src, S *__restrict__ dst, 
 
 // ------------------------------------------------------------------ reduction
 
-template <typename S>
-__global__ void __launch_bounds__(256) k_sum_partial(const S *__restrict__ base, const FabInfo *__restrict__ ftab,
-                                                     const Tile *__restrict__ tiles, int ntiles, int comp,
-                                                     double2 *partials) {
-    double s = 0.0, c = 0.0;
-    for (int w = blockIdx.x; w < ntiles; w += gridDim.x) {
-        const Tile t = tiles[w];
-        if (t.comp != comp) continue;
-        const FabInfo f = ftab[t.fab];
-        const S *p = base + f.org + comp * f.cstride;
-        const int cells = t.tx * t.ty * t.tz;
-        for (int i = threadIdx.x; i < cells; i += blockDim.x) {
-            int x = i % t.tx, r = i / t.tx, y = r % t.ty, z = r / t.ty;
-            neu_add(s, c, to_f64(p[(long long)(t.z0 + z) * f.plane + (long long)(t.y0 + y) * f.px + t.x0 + x]));
+// Whole-level reductions of one component (Sec. 3.1: the MultiFab's sum, max and norms).  The
+// valid rows of all FArrayBoxes form one list (rowpre[b] = first row of box b); warp w of the
+// grid takes rows w, w + warps, ... with its lanes along x, so the accumulation order, hence the
+// bits, depends only on the box layout and the fixed grid -- not on tiles or timing.
+// Sums (sum, sum |u|, sum u^2) accumulate in FP64 with Neumaier compensation; max, min and
+// max |u| are exact (FP64 holds every stored value; NaN values are skipped).
+template <int OP> struct RedOp;
+template <> struct RedOp<RED_SUM> {
+    static constexpr bool sum = true;
+    static __device__ __forceinline__ double val(double x) { return x; }
+};
+template <> struct RedOp<RED_NORM1> {
+    static constexpr bool sum = true;
+    static __device__ __forceinline__ double val(double x) { return ::fabs(x); }
+};
+template <> struct RedOp<RED_NORM2> {
+    static constexpr bool sum = true;
+    static __device__ __forceinline__ double val(double x) { return __dmul_rn(x, x); }
+};
+template <> struct RedOp<RED_MAX> {
+    static constexpr bool sum = false;
+    static constexpr double init = -__builtin_huge_val();
+    static __device__ __forceinline__ double val(double x) { return x; }
+    static __device__ __forceinline__ double pick(double a, double b) { return ::fmax(a, b); }
+};
+template <> struct RedOp<RED_MIN> {
+    static constexpr bool sum = false;
+    static constexpr double init = __builtin_huge_val();
+    static __device__ __forceinline__ double val(double x) { return x; }
+    static __device__ __forceinline__ double pick(double a, double b) { return ::fmin(a, b); }
+};
+template <> struct RedOp<RED_NORM0> {
+    static constexpr bool sum = false;
+    static constexpr double init = 0.0;
+    static __device__ __forceinline__ double val(double x) { return ::fabs(x); }
+    static __device__ __forceinline__ double pick(double a, double b) { return ::fmax(a, b); }
+};
+
+__device__ __forceinline__ double block_pick_max(double m, bool is_min) {
+    for (int off = 16; off > 0; off >>= 1) {
+        const double o = __shfl_down_sync(0xffffffffu, m, off);
+        m = is_min ? ::fmin(m, o) : ::fmax(m, o);
+    }
+    __shared__ double sm[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) sm[wid] = m;
+    __syncthreads();
+    if (wid == 0) {
+        m = lane < nw ? sm[lane] : sm[0];
+        for (int off = 16; off > 0; off >>= 1) {
+            const double o = __shfl_down_sync(0xffffffffu, m, off);
+            m = is_min ? ::fmin(m, o) : ::fmax(m, o);
         }
     }
-    block_reduce(s, c);
+    return m;
+}
+
+template <typename S, int OP>
+__global__ void __launch_bounds__(256) k_reduce_partial(const S *__restrict__ base, const FabInfo *__restrict__ ftab,
+                                                        const long long *__restrict__ rowpre, int nfab, int comp,
+                                                        double2 *partials) {
+    using O = RedOp<OP>;
+    const int lane = threadIdx.x & 31;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long nrows = rowpre[nfab];
+    double s, c = 0.0;
+    if constexpr (O::sum) s = 0.0; else s = O::init;
+    for (long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrows; r += nw) {
+        int lo = 0, hi = nfab - 1;  // the box holding row r: last lo with rowpre[lo] <= r
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (rowpre[mid] <= r) lo = mid; else hi = mid - 1;
+        }
+        const FabInfo f = ftab[lo];
+        const int rr = (int)(r - rowpre[lo]);
+        const int y = rr % f.n[1], z = rr / f.n[1];
+        const S *p = base + f.org + comp * f.cstride + (long long)z * f.plane + (long long)y * f.px;
+        for (int x = lane; x < f.n[0]; x += 32) {
+            const double v = O::val(to_f64(p[x]));
+            if constexpr (O::sum) neu_add(s, c, v); else s = O::pick(s, v);
+        }
+    }
+    if constexpr (O::sum) {
+        block_reduce(s, c);
+    } else {
+        s = block_pick_max(s, OP == RED_MIN);
+    }
     if (threadIdx.x == 0) partials[blockIdx.x] = make_double2(s, c);
 }
 
-__global__ void __launch_bounds__(256) k_sum_final(const double2 *partials, int n, double *out) {
-    double s = 0.0, c = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) neu_merge(s, c, partials[i].x, partials[i].y);
-    block_reduce(s, c);
-    if (threadIdx.x == 0) out[0] = __dadd_rn(s, c);
+template <int OP>
+__global__ void __launch_bounds__(256) k_reduce_final(const double2 *partials, int n, double *out) {
+    using O = RedOp<OP>;
+    if constexpr (O::sum) {
+        double s = 0.0, c = 0.0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) neu_merge(s, c, partials[i].x, partials[i].y);
+        block_reduce(s, c);
+        if (threadIdx.x == 0) out[0] = OP == RED_NORM2 ? __dsqrt_rn(__dadd_rn(s, c)) : __dadd_rn(s, c);
+    } else {
+        double m = O::init;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) m = O::pick(m, partials[i].x);
+        m = block_pick_max(m, OP == RED_MIN);
+        if (threadIdx.x == 0) out[0] = m;
+    }
 }
 
 // ------------------------------------------------------------------ dense staging
@@ -447,18 +526,38 @@ cudaError_t launch_stencil_plain(int dtype, int R, const void *src, void *dst, c
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_sum(int dtype, const void *base, const FabInfo *ftab, const Tile *tiles, int ntiles, int comp,
-                       double2 *partials, int grid, double *out_dev, cudaStream_t s) {
-    switch (dtype) {
-        case F64: k_sum_partial<<<grid, 256, 0, s>>>((const double *)base, ftab, tiles, ntiles, comp, partials); break;
-        case F32: k_sum_partial<<<grid, 256, 0, s>>>((const float *)base, ftab, tiles, ntiles, comp, partials); break;
-        default:
-            k_sum_partial<<<grid, 256, 0, s>>>((const __nv_bfloat16 *)base, ftab, tiles, ntiles, comp, partials);
-    }
+template <typename S, int OP>
+static cudaError_t reduce_t(const void *base, const FabInfo *ftab, const long long *rowpre, int nfab, int comp,
+                            double2 *partials, int grid, double *out_dev, cudaStream_t s) {
+    k_reduce_partial<S, OP><<<grid, 256, 0, s>>>((const S *)base, ftab, rowpre, nfab, comp, partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_sum_final<<<1, 256, 0, s>>>(partials, grid, out_dev);
+    k_reduce_final<OP><<<1, 256, 0, s>>>(partials, grid, out_dev);
     return cudaGetLastError();
+}
+
+template <typename S>
+static cudaError_t reduce_s(int op, const void *base, const FabInfo *ftab, const long long *rowpre, int nfab,
+                            int comp, double2 *partials, int grid, double *out_dev, cudaStream_t s) {
+    switch (op) {
+        case RED_SUM: return reduce_t<S, RED_SUM>(base, ftab, rowpre, nfab, comp, partials, grid, out_dev, s);
+        case RED_MAX: return reduce_t<S, RED_MAX>(base, ftab, rowpre, nfab, comp, partials, grid, out_dev, s);
+        case RED_MIN: return reduce_t<S, RED_MIN>(base, ftab, rowpre, nfab, comp, partials, grid, out_dev, s);
+        case RED_NORM0: return reduce_t<S, RED_NORM0>(base, ftab, rowpre, nfab, comp, partials, grid, out_dev, s);
+        case RED_NORM1: return reduce_t<S, RED_NORM1>(base, ftab, rowpre, nfab, comp, partials, grid, out_dev, s);
+        case RED_NORM2: return reduce_t<S, RED_NORM2>(base, ftab, rowpre, nfab, comp, partials, grid, out_dev, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_reduce(int dtype, int op, const void *base, const FabInfo *ftab, const long long *rowpre, int nfab,
+                          int comp, double2 *partials, int grid, double *out_dev, cudaStream_t s) {
+    switch (dtype) {
+        case F64: return reduce_s<double>(op, base, ftab, rowpre, nfab, comp, partials, grid, out_dev, s);
+        case F32: return reduce_s<float>(op, base, ftab, rowpre, nfab, comp, partials, grid, out_dev, s);
+        case BF16: return reduce_s<__nv_bfloat16>(op, base, ftab, rowpre, nfab, comp, partials, grid, out_dev, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 static cudaError_t dense_common(bool scatter, int dtype, void *base, const FabInfo *ftab, int nfab, double *stage,

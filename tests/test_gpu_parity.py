@@ -457,3 +457,38 @@ def test_zero_steps_is_a_no_op():
     g.from_host(dense)
     g.advance(1, [1.0], 0.1 / 256, 0)
     np.testing.assert_array_equal(g.to_host(), dense)
+
+
+# --------------------------------------------------------------------------- other reductions
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+def test_reductions_match_oracle(dtype):
+    """mf_reduce against the oracle's definitions: max, min, max|u| exact; sum, sum|u| and the
+    2-norm within 2 ulp (compensated FP64 against correctly rounded)."""
+    lo, hi = UNEVEN_DOM
+    dense = rand_field((2, 20, 16, 24), 60, dtype)
+    dense[1, 7, 3, 20] = round_to(np.array([9.75]), dtype)[0]
+    dense[1, 2, 14, 1] = round_to(np.array([-11.5]), dtype)[0]
+    g = gpu_level(lo, hi, boxes=UNEVEN, ncomp=2, ngrow=2, dtype=dtype)
+    g.from_host(dense)
+    L = oracle.Level(UNEVEN, lo, hi, 2, 2)
+    u = L.from_dense(dense)
+    for comp in range(2):
+        for op in ("max", "min", "norm0"):
+            assert g.reduce(op, comp) == oracle.reduce(L, u, op, comp), (op, comp)
+        for op in ("sum", "norm1", "norm2"):
+            got, ref = g.reduce(op, comp), oracle.reduce(L, u, op, comp)
+            assert abs(got - ref) <= 2 * math.ulp(abs(ref)), (op, comp, got, ref)
+    assert g.reduce("max", 1) == 9.75 and g.reduce("norm0", 1) == 11.5
+
+
+def test_reductions_do_not_depend_on_the_schedule():
+    lo, hi = [0, 0, 0], [31, 31, 31]
+    dense = rand_field((1, 32, 32, 32), 61)
+    outs = []
+    for tile in [(0, 0, 0), (16, 4, 4), (32, 8, 16)]:
+        g = gpu_level(lo, hi, mgs=16, ngrow=1)
+        g.set_tile(tile)
+        g.from_host(dense)
+        outs.append([g.reduce(op) for op in ("sum", "max", "min", "norm0", "norm1", "norm2")])
+    assert outs[0] == outs[1] == outs[2]

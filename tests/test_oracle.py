@@ -206,6 +206,65 @@ def test_domain_sum_is_correctly_rounded():
     assert oracle.domain_sum(L, u) == 2.0
 
 
+# --------------------------------------------------------------------------- other reductions
+
+def _uneven_16():
+    lo, hi = [0, 0, 0], [15, 15, 15]
+    boxes = [[0, 0, 0, 9, 15, 15], [10, 0, 0, 15, 6, 15], [10, 7, 0, 15, 15, 15]]
+    return oracle.Level(boxes, lo, hi, 2, 2)
+
+
+def test_reductions_see_valid_cells_only_planted_extremes():
+    """max / min / max|u| of a field in [0, 1) with a planted 2.5 and -3.25; the ghost cells
+    hold +-100, which must not show (a reduction over the grown boxes would see them)."""
+    L = _uneven_16()
+    dense = np.random.default_rng(3).random((2, 16, 16, 16))
+    dense[1, 3, 12, 14] = 2.5
+    dense[1, 9, 1, 2] = -3.25
+    u = L.from_dense(dense)
+    for b in range(L.nbox):  # ghosts: +-100
+        f = L.fab(u, b)
+        g = L.g
+        inner = f[:, g:-g, g:-g, g:-g].copy()
+        f[:, :, :, :] = np.where(np.arange(f.shape[3]) % 2 == 0, 100.0, -100.0)
+        f[:, g:-g, g:-g, g:-g] = inner
+    assert oracle.reduce(L, u, "max", 1) == 2.5
+    assert oracle.reduce(L, u, "min", 1) == -3.25
+    assert oracle.reduce(L, u, "norm0", 1) == 3.25
+    assert 0.0 <= oracle.reduce(L, u, "min", 0) and oracle.reduce(L, u, "max", 0) < 1.0
+
+
+def test_norms_of_closed_form_fields():
+    """2-norm of a constant c on 16^3 cells is 64 |c| exactly; the +-1 checkerboard has
+    1-norm 4096, 2-norm 64, sum 0; a single nonzero cell v has every norm |v|."""
+    L = _uneven_16()
+    i = np.arange(16)
+    cb = (-1.0) ** (i[:, None, None] + i[None, :, None] + i[None, None, :])
+    dense = np.stack([np.full((16, 16, 16), -0.375), cb])
+    u = L.from_dense(dense)
+    assert oracle.reduce(L, u, "norm2", 0) == 24.0
+    assert oracle.reduce(L, u, "norm1", 0) == 1536.0
+    assert oracle.reduce(L, u, "sum", 0) == -1536.0
+    assert oracle.reduce(L, u, "norm1", 1) == 4096.0
+    assert oracle.reduce(L, u, "norm2", 1) == 64.0
+    assert oracle.reduce(L, u, "sum", 1) == 0.0
+    one = np.zeros((2, 16, 16, 16))
+    one[0, 5, 11, 13] = -7.5
+    u1 = L.from_dense(one)
+    for op in ("norm0", "norm1", "norm2"):
+        assert oracle.reduce(L, u1, op, 0) == 7.5
+    assert oracle.reduce(L, u1, "min", 0) == -7.5 and oracle.reduce(L, u1, "max", 0) == 0.0
+
+
+def test_max_type_reductions_skip_nan():
+    L = _uneven_16()
+    dense = np.zeros((2, 16, 16, 16))
+    dense[0, 0, 0, 0] = np.nan
+    dense[0, 15, 15, 15] = 1.25
+    u = L.from_dense(dense)
+    assert oracle.reduce(L, u, "max", 0) == 1.25 and oracle.reduce(L, u, "norm0", 0) == 1.25
+
+
 # --------------------------------------------------------------------------- layout invariance
 
 @pytest.mark.parametrize("R", [1, 2])
