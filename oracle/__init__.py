@@ -16,6 +16,9 @@ What each function follows (section of arXiv 1604.03570):
                          is the paper's second-order scheme, R = 4 the 9-cell-wide 8th-order
                          stencil of Sec. 4.2.  ``form="direct"`` is a cross-check only.
 * ``advance``         -- nsteps x (FillBoundary, stencil, swap) (Sec. 4.1).
+* ``rk3_advance``     -- the third-order Runge-Kutta integration of Sec. 4.2 (SMC), read as the
+                         three-stage SSP scheme: each stage a FillBoundary and a forward-Euler
+                         stencil step, combined with the state at the start of the step.
 * ``domain_sum``      -- the whole-level reduction (Sec. 3.1, mf.max(0) is the example), here
                          the sum of one component over the valid cells, correctly rounded
                          (Shewchuk's exact summation as implemented by ``math.fsum``).
@@ -180,6 +183,29 @@ def advance(level, data, R, lam, nsteps):
     which = lib().orc_advance(level.nbox, _p(level.boxes), _p(level.dlo), _p(level.dhi), level.g, level.C, int(R),
                               _p(b), _p(lam), int(nsteps), _p(a), _p(other))
     return a if which == 0 else other
+
+
+# Stage weights of the three-stage SSP Runge-Kutta scheme: stage s returns
+# a_s * u + b_s * E(v_s), E the forward-Euler step, u the state at the start of the step.
+RK3_STAGES = ((0.0, 1.0), (0.75, 0.25), (1.0 / 3.0, 2.0 / 3.0))
+
+
+def rk3_advance(level, data, R, lam, nsteps):
+    """nsteps of the third-order Runge-Kutta time integration of Sec. 4.2, read as the
+    three-stage strong-stability-preserving scheme of Shu and Osher (1988):
+        u1 = E(u),  u2 = 3/4 u + 1/4 E(u1),  u_new = 1/3 u + 2/3 E(u2),
+    where E(v) = v + lam * div F(v) is one forward-Euler flux-form step (``stencil``) after a
+    FillBoundary of v.  Returns the new FArrayBox storage (valid cells defined)."""
+    u = np.array(data, dtype=np.float64, copy=True)
+    e = level.alloc()
+    for _ in range(nsteps):
+        v = u
+        for a, b in RK3_STAGES:
+            fill_boundary(level, v)
+            stencil(level, R, lam, v, e)
+            v = e.copy() if a == 0.0 else a * u + b * e
+        u = v
+    return u
 
 
 def domain_sum(level, data, comp=0):

@@ -206,6 +206,35 @@ def test_domain_sum_is_correctly_rounded():
     assert oracle.domain_sum(L, u) == 2.0
 
 
+# --------------------------------------------------------------------------- RK3 (Sec. 4.2)
+
+@pytest.mark.parametrize("R,k", [(1, (1, 2, 1)), (2, (3, 1, 2)), (4, (2, 2, 3))])
+def test_rk3_single_mode_decays_by_the_stability_polynomial(R, k):
+    """For the linear operator one SSP-RK3 step maps a Fourier mode to P(z) times itself,
+    P(z) = 1 + z + z^2/2 + z^3/6, z = lam * sum_d sigma_R(2 pi k_d / N) (the scheme is exact
+    for linear autonomous problems up to third order)."""
+    N = (12, 10, 8)
+    lo, hi = whole_domain(N)
+    L = oracle.Level(oracle.chop(lo, hi, 5), lo, hi, R, 1)
+    u0 = synth.single_mode((N[2], N[1], N[0]), k)[None]
+    lam = 0.12
+    z = lam * sum(coeffs.symbol(R, 2 * math.pi * kd / n) for kd, n in zip(k, N))
+    P = 1 + z + z * z / 2 + z ** 3 / 6
+    nsteps = 4
+    out = L.to_dense(oracle.rk3_advance(L, L.from_dense(u0), R, lam, nsteps))
+    assert rel_err(out, P ** nsteps * u0) <= 1e-12
+
+
+def test_rk3_conserves_the_sum():
+    lo, hi = whole_domain((16, 12, 10))
+    boxes = [[0, 0, 0, 9, 11, 9], [10, 0, 0, 15, 5, 9], [10, 6, 0, 15, 11, 9]]
+    L = oracle.Level(boxes, lo, hi, 2, 1)
+    u0 = np.random.default_rng(7).random((1, 10, 12, 16))
+    u = oracle.rk3_advance(L, L.from_dense(u0), 2, 0.1, 3)
+    s0, s1 = math.fsum(u0.ravel().tolist()), oracle.domain_sum(L, u)
+    assert abs(s1 - s0) <= 3 * 3 * 1e-15 * float(np.sum(np.abs(u0)))
+
+
 # --------------------------------------------------------------------------- other reductions
 
 def _uneven_16():
