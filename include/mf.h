@@ -191,6 +191,21 @@ int mf_advance(mf_t *mf, const mf_stencil *st, double dt, int nsteps);
 int mf_amr_advance(mf_t *crse, mf_t *fine, const mf_stencil *st, double dt_crse, int ncrse_steps, int nsub,
                    int ratio);
 
+/* Runge-Kutta advance (Sec. 4.2: SMC integrates its 8th-order operator with a third-order
+ * Runge-Kutta method; read as the three-stage SSP scheme of Shu and Osher):
+ *   u1 = E(u),  u2 = 3/4 u + 1/4 E(u1),  u_new = 1/3 u + 2/3 E(u2),
+ * E(v) = v + lam * div F(v) being one FillBoundary + forward-Euler flux-form step (mf_advance).
+ * The stages need a third level of the handle's layout: mf_stage_bytes() bytes of device
+ * memory, 256-byte aligned, owned by the caller and attached once with mf_attach_stage (it must
+ * outlive the handle; MF_EALIGN if misaligned or too small, MF_ESTATE before mf_attach).
+ * mf_rk3_advance runs nsteps steps (3 stencil launches each) as one CUDA graph on the attached
+ * stream, asynchronously; the result is the current level.  Same stencils, flags (except
+ * MF_PLAIN_PER_BOX: MF_EINVAL) and stability check as mf_advance; MF_ESTATE without a stage
+ * level. */
+size_t mf_stage_bytes(const mf_t *mf);
+int mf_attach_stage(mf_t *mf, void *dev_ptr, size_t bytes);
+int mf_rk3_advance(mf_t *mf, const mf_stencil *st, double dt, int nsteps);
+
 /* mf_sum -- sum of component comp over all valid cells of the current time level, FP64 with
  * compensated (Neumaier) accumulation; synchronises the stream.  Sec. 3.1 whole-level
  * reduction (the paper's example is mf.max(0)). */

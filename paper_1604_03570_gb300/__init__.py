@@ -32,7 +32,8 @@ EXPORTS = [
     "mf_copy_fab_to_host", "mf_copy_fab_from_host", "mf_fill_boundary", "mf_interp_cf", "mf_average_down",
     "mf_advance", "mf_amr_advance", "mf_sum", "mf_step_bytes", "mf_current", "mf_last_error", "mf_set_timing",
     "mf_phase_ms", "mf_set_kernel", "mf_sum_strided_noalloc", "mf_get_schedule", "mf_launch_count",
-    "mf_fp64_fma_rate", "mf_set_schedule", "mf_reduce",
+    "mf_fp64_fma_rate", "mf_set_schedule", "mf_reduce", "mf_stage_bytes", "mf_attach_stage",
+    "mf_rk3_advance",
 ]
 
 
@@ -86,6 +87,9 @@ def _load():
         "mf_fp64_fma_rate": (I, [ctypes.POINTER(D), P]),
         "mf_set_schedule": (I, [P, P]),
         "mf_reduce": (I, [P, I, I, ctypes.POINTER(D)]),
+        "mf_stage_bytes": (SZ, [P]),
+        "mf_attach_stage": (I, [P, P, SZ]),
+        "mf_rk3_advance": (I, [P, ctypes.POINTER(mf_stencil), D, I]),
         "mf_sum_strided_noalloc": (I, [P, I, I, I, I, LL, LL, ctypes.POINTER(D), P]),
     }
     for name, (res, args) in sig.items():
@@ -233,6 +237,20 @@ def mf_advance(h, kind, diffusivity, dt, nsteps, flags=0):
     del keep
 
 
+def mf_stage_bytes(h):
+    return int(lib.mf_stage_bytes(h))
+
+
+def mf_attach_stage(h, dev_ptr, nbytes):
+    _check(lib.mf_attach_stage(h, ctypes.c_void_p(int(dev_ptr)), ctypes.c_size_t(int(nbytes))))
+
+
+def mf_rk3_advance(h, kind, diffusivity, dt, nsteps, flags=0):
+    st, keep = _stencil(kind, diffusivity, flags)
+    _check(lib.mf_rk3_advance(h, ctypes.byref(st), float(dt), int(nsteps)))
+    del keep
+
+
 def mf_amr_advance(crse, fine, kind, diffusivity, dt_crse, ncrse_steps, nsub=2, ratio=2, flags=0):
     st, keep = _stencil(kind, diffusivity, flags)
     _check(lib.mf_amr_advance(crse, fine, ctypes.byref(st), float(dt_crse), int(ncrse_steps), int(nsub), int(ratio)))
@@ -366,6 +384,15 @@ class MultiFab:
 
     def advance(self, kind, diffusivity, dt, nsteps, flags=0):
         mf_advance(self.h, kind, diffusivity, dt, nsteps, flags)
+
+    def rk3_advance(self, kind, diffusivity, dt, nsteps, flags=0):
+        """Third-order SSP Runge-Kutta steps; allocates and attaches the stage level once."""
+        if getattr(self, "stage_buf", None) is None:
+            import torch
+            nb = mf_stage_bytes(self.h)
+            self.stage_buf = torch.empty(nb, dtype=torch.uint8, device=self.buf.device)
+            mf_attach_stage(self.h, self.stage_buf.data_ptr(), nb)
+        mf_rk3_advance(self.h, kind, diffusivity, dt, nsteps, flags)
 
     def sum(self, comp=0):
         return mf_sum(self.h, comp)

@@ -260,7 +260,11 @@ struct mf {
         if (cap) cudaStreamDestroy(cap);
         if (h_sum) cudaFreeHost(h_sum);
     }
-    void *level_ptr(int which) const { return base + (size_t)which * level_elems * esize; }
+    // Runge-Kutta stage level (slot 2), caller-owned like the two time levels
+    char *stage = nullptr;
+    void *level_ptr(int which) const {
+        return which == 2 ? (void *)stage : (void *)(base + (size_t)which * level_elems * esize);
+    }
 };
 
 // ------------------------------------------------------------------ layout
@@ -661,7 +665,7 @@ extern "C" int mf_attach(mf_t *m, void *dev_ptr, size_t bytes, void *stream) {
     if ((rc = m->d_tiles.ensure(cap * sizeof(Tile)))) return rc;
     CU(cudaMemcpyAsync(m->d_tiles.p, m->tiles.data(), m->tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice, m->stream));
     if ((rc = m->d_partials.ensure(512 * sizeof(double2)))) return rc;
-    if ((rc = m->d_maps.ensure(2 * m->fabs.size() * sizeof(CUtensorMap)))) return rc;
+    if ((rc = m->d_maps.ensure(3 * m->fabs.size() * sizeof(CUtensorMap)))) return rc;  // two levels + stage
     if ((rc = m->d_tfab.ensure(m->fabs.size() * sizeof(TmaFab)))) return rc;
     if ((rc = m->d_err.ensure(sizeof(int)))) return rc;
     CU(cudaMemsetAsync(m->d_err.p, 0, sizeof(int), m->stream));
@@ -1092,11 +1096,11 @@ static int build_tma(mf_t *m, int R) {
     auto encode = tensor_map_encoder();
     if (!encode) return 0;
     const int nf = (int)m->fabs.size();
-    std::vector<CUtensorMap> maps(2 * (size_t)nf), smaps(2 * (size_t)nf);
+    std::vector<CUtensorMap> maps(3 * (size_t)nf), smaps(3 * (size_t)nf);  // levels 0, 1 and the stage level
     const CUtensorMapDataType dt = m->dtype == F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
                                    : m->dtype == F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                                      : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    for (int which = 0; which < 2; ++which)
+    for (int which = 0; which < (m->stage ? 3 : 2); ++which)
         for (int b = 0; b < nf; ++b) {
             const FabInfo &f = m->fabs[b];
             const int g = m->ngrow;
@@ -1223,10 +1227,21 @@ static int enqueue_fill_step(mf_t *m, int which, cudaStream_t s) {
     return 0;
 }
 
-static StencilParams stencil_params(const mf_t *m, int from, const double *lam) {
+// One stencil launch: level `from` (ghosts filled) -> level `to` (default: the other time
+// level).  With u0 >= 0 the launch is a Runge-Kutta stage and writes
+// rk_a * (level u0) + rk_b * (forward-Euler value).
+struct StageArgs {
+    int to = -1, u0 = -1;
+    double rk_a = 0.0, rk_b = 1.0;
+};
+
+static StencilParams stencil_params(const mf_t *m, int from, const double *lam, const StageArgs &sa = StageArgs{}) {
     StencilParams p{};
     p.src[0] = m->level_ptr(from);
-    p.dst[0] = m->level_ptr(1 - from);
+    p.dst[0] = m->level_ptr(sa.to >= 0 ? sa.to : 1 - from);
+    p.u0[0] = sa.u0 >= 0 ? m->level_ptr(sa.u0) : nullptr;
+    p.rk_a = sa.rk_a;
+    p.rk_b = sa.rk_b;
     p.ftab = (const FabInfo *)m->d_fabs.p;
     p.tiles = (const Tile *)m->d_tiles.p;
     p.ntiles = (int)m->tiles.size();
@@ -1235,7 +1250,7 @@ static StencilParams stencil_params(const mf_t *m, int from, const double *lam) 
 }
 
 static int enqueue_stencil(mf_t *m, int from, int R, bool fp64diff, const double *lam, cudaStream_t s,
-                           bool push = false) {
+                           bool push = false, const StageArgs &sa = StageArgs{}) {
     if (m->use_tma && m->tma_R != R) {
         int rc = build_tma(m, R);
         if (rc) return rc;
@@ -1251,7 +1266,10 @@ static int enqueue_stencil(mf_t *m, int from, int R, bool fp64diff, const double
         p.nstages_log2 = 0;
         while ((1 << p.nstages_log2) < m->tma_ns) ++p.nstages_log2;
         p.slot_bytes = m->tma_slot;
-        p.dst[0] = m->level_ptr(1 - from);
+        p.dst[0] = m->level_ptr(sa.to >= 0 ? sa.to : 1 - from);
+        p.u0[0] = sa.u0 >= 0 ? m->level_ptr(sa.u0) : nullptr;
+        p.rk_a = sa.rk_a;
+        p.rk_b = sa.rk_b;
         p.err = (int *)m->d_err.p;
         p.smaps = (const CUtensorMap *)m->d_smaps.p + (size_t)from * m->fabs.size();
         p.strips = (const TileStrip *)m->d_strips.p;
@@ -1266,7 +1284,7 @@ static int enqueue_stencil(mf_t *m, int from, int R, bool fp64diff, const double
         CU(launch_stencil_tma(m->dtype, R, fp64diff, eff_rows(m, R), eff_gb(m, R), m->tma_cpt, p, m->tma_grid, s));
         return 0;
     }
-    StencilParams p = stencil_params(m, from, lam);
+    StencilParams p = stencil_params(m, from, lam, sa);
     CU(launch_stencil(m->dtype, R, fp64diff, p, m->block[0], m->block[1], 0, s));
     return 0;
 }
@@ -1574,6 +1592,90 @@ extern "C" int mf_advance(mf_t *m, const mf_stencil *st, double dt, int nsteps) 
             if (!body) body = log.before(1);
             if (!body) body = enqueue_stencil(m, from, R, fp64diff, lam, m->cap, push);
             from = 1 - from;
+        }
+        if (!body) body = log.finish();
+        if ((rc = capture_end(m, key, body))) return rc;
+        it = m->graphs.find(key);
+        log.store(*it->second);
+    }
+    note_launch(m, *it->second);
+    CU(cudaGraphLaunch(it->second->exec, m->stream));
+    if (nsteps & 1) m->cur = 1 - m->cur;
+    return 0;
+}
+
+// ------------------------------------------------------------------ Runge-Kutta (Sec. 4.2)
+
+extern "C" size_t mf_stage_bytes(const mf_t *m) { return m ? m->level_elems * m->esize : 0; }
+
+extern "C" int mf_attach_stage(mf_t *m, void *dev_ptr, size_t bytes) {
+    int rc = need_attached(m);
+    if (rc) return rc;
+    if (!dev_ptr || ((uintptr_t)dev_ptr & 255)) return fail(MF_EALIGN, "stage pointer must be 256-byte aligned");
+    if (bytes < mf_stage_bytes(m)) return fail(MF_EALIGN, "stage buffer of %zu bytes, need %zu", bytes, mf_stage_bytes(m));
+    m->stage = (char *)dev_ptr;
+    m->tma_R = 0;  // the tensor maps of the stage level are encoded at the next launch
+    invalidate_graphs(m);
+    return 0;
+}
+
+// Stage weights of the three-stage SSP Runge-Kutta scheme (the reading of Sec. 4.2's third-order
+// Runge-Kutta integration): stage k writes W[k][0] * u + W[k][1] * E(v_k), u the state at the
+// start of the step, E one forward-Euler flux-form step.
+static const double kRk3[3][2] = {{0.0, 1.0}, {0.75, 0.25}, {1.0 / 3.0, 2.0 / 3.0}};
+
+extern "C" int mf_rk3_advance(mf_t *m, const mf_stencil *st, double dt, int nsteps) {
+    int rc = need_attached(m);
+    if (rc) return rc;
+    if (!m->stage) return fail(MF_ESTATE, "no stage level attached (mf_attach_stage)");
+    double lam[kMaxComp];
+    if ((rc = check_stencil(m, st, dt, lam, 1.0))) return rc;
+    if (nsteps < 0) return fail(MF_EINVAL, "nsteps must be >= 0");
+    if (st->flags & MF_PLAIN_PER_BOX) return fail(MF_EINVAL, "MF_PLAIN_PER_BOX does not apply to mf_rk3_advance");
+    if (nsteps == 0) return 0;
+    const int R = st->kind;
+    const bool fp64diff = (st->flags & MF_FP64_DIFF) && m->dtype != F64;
+    if (m->tile_auto && (rc = autotune(m, R, fp64diff, lam))) return rc;
+    if (m->use_tma && m->tma_R != R && (rc = build_tma(m, R))) return rc;  // never inside a capture
+    char kb[48];
+    snprintf(kb, sizeof kb, "%s|g%llu", m->timing ? "rk3T" : "rk3", m->gen);
+    const std::string key = graph_key(kb, R, fp64diff, lam, m->ncomp, nsteps, m->cur);
+    auto it = m->graphs.find(key);
+    if (it == m->graphs.end()) {
+        if (m->timing && (rc = ensure_events(m, 6 * nsteps + 1))) return rc;
+        if ((rc = capture_begin(m))) return rc;
+        int body = 0, a = m->cur;
+        PhaseLog log{m, m->timing};
+        body = log.start();
+        const bool push = m->use_tma && m->tma_ok && m->tma_push;
+        // pushed[l]: the launch that last wrote level l also wrote its face ghosts
+        bool pushed[3] = {false, false, false};
+        for (int step = 0; step < nsteps && !body; ++step) {
+            const int b = 1 - a;
+            const int in[3] = {a, b, 2}, out[3] = {b, 2, b};  // u -> u1 (b) -> u2 (stage) -> new u (b)
+            for (int k = 0; k < 3 && !body; ++k) {
+                const int v = in[k];
+                if (pushed[v]) {
+                    if (!m->fbtasks_res.empty() && !(body = log.before(0)))
+                        body = launch_fill(m->dtype, level_ptrs(m, v), (const FbTask *)m->d_fbtasks_res.p,
+                                           (int)m->fbtasks_res.size(), 0, m->cap) == cudaSuccess
+                                   ? 0
+                                   : fail(MF_ECUDA, "fill launch failed");
+                } else if (!(body = log.before(0, fill_step_tasks(m) > 0))) {
+                    body = enqueue_fill_step(m, v, m->cap);
+                }
+                StageArgs sa;
+                sa.to = out[k];
+                if (k > 0) {
+                    sa.u0 = a;
+                    sa.rk_a = kRk3[k][0];
+                    sa.rk_b = kRk3[k][1];
+                }
+                if (!body) body = log.before(1);
+                if (!body) body = enqueue_stencil(m, v, R, fp64diff, lam, m->cap, push, sa);
+                pushed[out[k]] = push;
+            }
+            a = b;
         }
         if (!body) body = log.finish();
         if ((rc = capture_end(m, key, body))) return rc;

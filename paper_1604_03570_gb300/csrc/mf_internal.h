@@ -98,6 +98,8 @@ struct LevelPtrs {
 struct StencilParams {
     const void *src[kMaxLev];
     void *dst[kMaxLev];
+    const void *u0[kMaxLev];  // Runge-Kutta stage: state at the start of the step (nullptr: plain step)
+    double rk_a, rk_b;        // the stage writes rk_a * u0 + rk_b * (forward-Euler value)
     const FabInfo *ftab;
     const Tile *tiles;
     int ntiles;
@@ -160,12 +162,17 @@ struct StencilTmaParams {
     void *dst[kMaxLev];
     int *err;                  // set non-zero when a bounded wait expires
     const PushPiece *push;     // ghost-push pieces (nullptr: no push)
+    const void *u0[kMaxLev];   // Runge-Kutta stage: state at the start of the step (nullptr: plain step)
+    double rk_a, rk_b;         // the stage writes rk_a * u0 + rk_b * (forward-Euler value)
     double lam[kMaxLev][kMaxComp];
 };
 
 // ---- launchers (mf_kernels.cu, stencil_tma.cu); all asynchronous on `s`
 cudaError_t launch_stencil_tma(int dtype, int R, bool fp64diff, int rows, int gb, int nt, const StencilTmaParams &p,
                                int grid, cudaStream_t s);
+// the Runge-Kutta-stage variant (p.u0 set); launch_stencil_tma dispatches to it
+cudaError_t launch_stencil_tma_rk(int dtype, int R, bool fp64diff, int rows, int gb, int nt, const StencilTmaParams &p,
+                                  int grid, cudaStream_t s);
 // whether the TMA stencil has a schedule with rows rows of gb-byte groups per thread
 bool tma_has_group(int dtype, int R, int rows, int gb);
 int tma_max_threads(int R);      // largest CTA of the TMA stencil for radius R

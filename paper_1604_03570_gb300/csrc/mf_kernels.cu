@@ -122,7 +122,9 @@ __global__ void __launch_bounds__(256) k_stencil(StencilParams p) {
         const int px = f.px;
         const S *src = (const S *)p.src[f.level] + f.org + t.comp * f.cstride;
         S *dst = (S *)p.dst[f.level] + f.org + t.comp * f.cstride;
+        const S *u0 = p.u0[f.level] ? (const S *)p.u0[f.level] + f.org + t.comp * f.cstride : nullptr;
         const A lam = (A)p.lam[f.level][t.comp];
+        const A rka = (A)p.rk_a, rkb = (A)p.rk_b;
         for (int yy = threadIdx.y; yy < t.ty; yy += blockDim.y) {
             for (int xx = threadIdx.x; xx < t.tx; xx += blockDim.x) {
                 const int x = t.x0 + xx, y = t.y0 + yy;
@@ -143,7 +145,9 @@ __global__ void __launch_bounds__(256) k_stencil(StencilParams p) {
                         qy[j] = (j == R) ? q[R] : ld<S, A>(c0 + (long long)(j - R) * px);
                     }
                     const A fzp = face_flux<A, R>(q, R);
-                    st(ocol + (long long)z * pl, update_cell<A, R>(qx, qy, fzm, fzp, q[R], lam));
+                    A v = update_cell<A, R>(qx, qy, fzm, fzp, q[R], lam);
+                    if (u0) v = rk_combine<A>(v, ld<S, A>(u0 + (long long)z * pl + (long long)y * px + x), rka, rkb);
+                    st(ocol + (long long)z * pl, v);
                     fzm = fzp;
                     if (k + 1 < t.tz) {
 #pragma unroll

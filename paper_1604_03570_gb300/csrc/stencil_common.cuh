@@ -74,6 +74,12 @@ __device__ __forceinline__ A face_flux(const A *q, int c) {
     return f;
 }
 
+// Runge-Kutta stage combination a * u0 + b * e of the state at the start of the step (u0) and
+// the forward-Euler value e: one rounding of the product b * e, one of the fused multiply-add.
+template <typename A> __device__ __forceinline__ A rk_combine(A e, A u0, A a, A b) {
+    return Ar<A>::fma(a, u0, Ar<A>::mul(b, e));
+}
+
 template <typename S, typename A> __device__ __forceinline__ A ld_smem(const S *p);
 template <> __device__ __forceinline__ double ld_smem<double, double>(const double *p) { return *p; }
 template <> __device__ __forceinline__ float ld_smem<float, float>(const float *p) { return *p; }

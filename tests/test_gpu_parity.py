@@ -13,6 +13,7 @@ import pytest
 
 import oracle
 import synth
+from oracle.coeffs import symbol as coeffs_symbol
 
 torch = pytest.importorskip("torch")
 mf = pytest.importorskip("paper_1604_03570_gb300")
@@ -492,3 +493,60 @@ def test_reductions_do_not_depend_on_the_schedule():
         g.from_host(dense)
         outs.append([g.reduce(op) for op in ("sum", "max", "min", "norm0", "norm1", "norm2")])
     assert outs[0] == outs[1] == outs[2]
+
+
+# --------------------------------------------------------------------------- third-order Runge-Kutta (Sec. 4.2)
+
+@pytest.mark.parametrize("R", [1, 2, 4])
+def test_rk3_fp64_matches_oracle(R):
+    lo, hi = [0, 0, 0], [31, 31, 31]
+    C = 2
+    D = np.array([1.0, 0.5])
+    dt = {1: 0.15, 2: 0.1125, 4: 0.09}[R] / (32 * 32)
+    dense = np.stack([synth.eval_modes((32, 32, 32), synth.sine_modes(1604, 70 + c, 6, 6)) for c in range(C)])
+    dense += synth.noise(1604, 71, dense.shape, 1e-3)
+    g = gpu_level(lo, hi, boxes=CUBE_UNEVEN, ncomp=C, ngrow=R, dtype="f64")
+    g.from_host(dense)
+    g.rk3_advance(R, D, dt, 3)
+    L = oracle.Level(CUBE_UNEVEN, lo, hi, R, C)
+    ref = L.to_dense(oracle.rk3_advance(L, L.from_dense(dense), R, D * dt * 1024.0, 3))
+    assert rel_err(g.to_host(), ref) <= FP64_TOL
+    assert mf.mf_launch_count(g.h)["stencil"] == 9
+
+
+def test_rk3_single_mode_decays_by_the_stability_polynomial():
+    """64^3 in 8 boxes, the 25-point stencil, FP64: one mode times P(z)^n, P(z) = 1 + z + z^2/2 +
+    z^3/6, z = lam * sum_d sigma_4(2 pi k_d / N)."""
+    N, n, lam, k = 64, 10, 0.09, (3, 5, 2)
+    lo, hi = [0, 0, 0], [N - 1] * 3
+    u0 = synth.single_mode((N, N, N), k)[None]
+    z = lam * sum(coeffs_symbol(4, 2 * math.pi * kd / N) for kd in k)
+    P = 1 + z + z * z / 2 + z ** 3 / 6
+    g = gpu_level(lo, hi, mgs=32, ngrow=4, dtype="f64")
+    g.from_host(u0)
+    g.rk3_advance(4, [1.0], lam / (N * N), n)
+    assert rel_err(g.to_host(), P ** n * u0) <= FP64_TOL
+
+
+def test_rk3_kernel_variants_and_tiles_give_identical_bits():
+    lo, hi = [0, 0, 0], [31, 31, 31]
+    dense = rand_field((1, 32, 32, 32), 72, "f32")
+    outs = []
+    for boxes, tile, kern in [(oracle.chop(lo, hi, 16), (0, 0, 0), mf.MF_KERNEL_TMA),
+                              (oracle.chop(lo, hi, 16), (16, 4, 8), mf.MF_KERNEL_GLOBAL),
+                              (CUBE_UNEVEN, (0, 8, 16), mf.MF_KERNEL_TMA)]:
+        g = gpu_level(lo, hi, boxes=boxes, ngrow=2, dtype="f32")
+        g.set_tile(tile)
+        mf.mf_set_kernel(g.h, kern)
+        g.from_host(dense)
+        g.rk3_advance(2, [1.0], 0.1 / 1024, 4)
+        outs.append(g.to_host())
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o, outs[0])
+
+
+def test_rk3_without_a_stage_level_is_rejected():
+    g = gpu_level([0, 0, 0], [15, 15, 15], mgs=8, ngrow=1)
+    with pytest.raises(mf.MFError) as e:
+        mf.mf_rk3_advance(g.h, 1, [1.0], 0.1 / 256, 1)
+    assert e.value.code == mf.MF_ESTATE
