@@ -261,6 +261,42 @@ def whole_job_rate(ws, units_per_rank, seconds):
     return ws * units_per_rank / seconds
 
 
+RK3_CFG = dict(N=256, max_grid_size=64, ngrow=4, ncomp=1, R=4, nsteps=20, dtype="f32", nmodes=8, kmax=8)
+
+
+def rk3_line(mf, torch, flush, args, hbm):
+    """The third-order Runge-Kutta advance with the 25-point 8th-order stencil (Sec. 4.2's
+    integrator and operator): 256^3 in 64 boxes of 64^3, 4 ghost cells, FP32, 20 steps of 3
+    stencil launches per bench step."""
+    c = RK3_CFG
+    N, R, n = c["N"], c["R"], c["nsteps"]
+    dense = synth.eval_modes((N, N, N), synth.sine_modes(synth.FIELD_SEED, 300, c["nmodes"], c["kmax"]))[None]
+    m = mf.MultiFab([0, 0, 0], [N - 1] * 3, max_grid_size=c["max_grid_size"], ncomp=1, ngrow=c["ngrow"],
+                    dtype=c["dtype"])
+    m.from_host(dense)
+    dt = synth.heat_dt(N, R)
+    for _ in range(2):
+        m.rk3_advance(R, [1.0], dt, n)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush()
+        ev[k][0].record(m.stream)
+        mf.mf_rk3_advance(m.h, R, [1.0], dt, n)
+        ev[k][1].record(m.stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    V, nbox, b, S = N ** 3, (N // c["max_grid_size"]) ** 3, c["max_grid_size"], 4
+    # per step: 3 stencil launches (read V + face halo, write V) and 2 reads of u0
+    step_bytes = S * (3 * (2 * V + nbox * 6 * R * b * b) + 2 * V)
+    launches = mf.mf_launch_count(m.h)
+    return {"value": V * n / (ms * 1e-3), "unit": "cell-updates/s (RK3 steps)", "ms_per_bench_step": ms,
+            "workload": "rk3_8th256: periodic 256^3, 64 boxes of 64^3, ngrow 4, 25-point 8th-order stencil, "
+                        "3-stage SSP Runge-Kutta, FP32, %d steps per bench step" % n,
+            "step_bytes": step_bytes, "step_frac": step_bytes * n / (ms * 1e-3) / 1e9 / hbm,
+            "stencil_launches_per_bench_step": launches["stencil"], "fill_launches_per_bench_step": launches["fill"],
+            "schedule": mf.mf_get_schedule(m.h)}
+
+
 def run_ours(args, cfg, ws, rank, local):
     import torch
     import paper_1604_03570_gb300 as mf
@@ -455,6 +491,7 @@ def run_ours(args, cfg, ws, rank, local):
                                             "flops_per_cell": FLOPS_PER_CELL[R]}}
         out["fp64_plain_per_box"] = {"value": vplain, "unit": UNIT,
                                      "launches_per_time_step": 2 * nbox}
+        out["rk3_8th"] = rk3_line(mf, torch, flush, args, hbm)
         out["speedup_batched_vs_fp64_plain_per_box"] = value / vplain
         if rank == 0 and ws == 1:
             out["cpu_baseline"] = cpu_baseline(cfg)

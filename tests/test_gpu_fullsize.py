@@ -193,3 +193,29 @@ def test_amr2lev256_full_size_matches_oracle():
               % (dtype, ec, ef, tol, mf.mf_launch_count(gc.h)))
         assert ec <= tol and ef <= tol
         del gc, gf
+
+
+# --------------------------------------------------------------------------- RK3, 25-point, 256^3 (the benchmark's RK3 line)
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_rk3_8th256_full_size_matches_the_stability_polynomial(dtype):
+    """Sec. 4.2's integrator and operator at the benchmark's size: each mode of the initial data
+    is multiplied by P(z)^n, P(z) = 1 + z + z^2/2 + z^3/6, z = lam sum_d sigma_4(2 pi k_d / N)."""
+    N, R, n = 256, 4, 20
+    modes = synth.sine_modes(synth.FIELD_SEED, 300, 8, 8)
+    dense = synth.eval_modes((N, N, N), modes)[None]
+    dt = synth.heat_dt(N, R)
+    lam = dt * N * N
+
+    def P(k):
+        z = lam * sum(coeffs.symbol(R, 2.0 * math.pi * kd / N) for kd in k)
+        return 1.0 + z + z * z / 2.0 + z ** 3 / 6.0
+
+    exact = synth.eval_modes((N, N, N), [(k, a * P(k) ** n, ph) for k, a, ph in modes])[None]
+    g = level([0, 0, 0], [N - 1] * 3, dtype, max_grid_size=64, ngrow=4)
+    g.from_host(dense)
+    g.rk3_advance(R, [1.0], dt, n)
+    err = rel_err(g.to_host(), exact)
+    tol = FP64_TOL if dtype == "f64" else f32_tol(3 * n, R)
+    print("MEASURED rk3_8th256 %s rel_err %.3e (bound %.1e) schedule %s" % (dtype, err, tol, mf.mf_get_schedule(g.h)))
+    assert err <= tol
