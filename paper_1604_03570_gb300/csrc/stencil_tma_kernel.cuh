@@ -180,6 +180,8 @@ template <typename S, typename A, int R, int ROWS, int GB, bool RK>
 __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __grid_constant__ StencilTmaParams p) {
     using V = VG<S, GB>;
     constexpr int VX = V::n;  // cells per group: one GB-byte vector of a row
+    // FP32 arithmetic at radius 1: pairs of cells through the packed f32x2 instructions
+    constexpr bool kPair = std::is_same<A, float>::value && R == 1 && VX % 2 == 0;
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];
     unsigned char *slots = (unsigned char *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
@@ -464,13 +466,24 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
                 for (int c = 0; c < VX; ++c) wy[R + r][c] = q[r][c][R];
             // y-face fluxes at y0 - 1/2 + r, r = 0 .. ROWS (inner faces shared by two rows)
             A fy[ROWS + 1][VX];
+            if constexpr (kPair) {  // radius 1: the flux is a difference, two cells per instruction
 #pragma unroll
-            for (int c = 0; c < VX; ++c) {
-                A col[2 * R + ROWS];
+                for (int r = 0; r <= ROWS; ++r)
 #pragma unroll
-                for (int m = 0; m < 2 * R + ROWS; ++m) col[m] = wy[m][c];
+                    for (int c = 0; c < VX; c += 2) {
+                        const F2 d = sub2(F2{wy[r + 1][c], wy[r + 1][c + 1]}, F2{wy[r][c], wy[r][c + 1]});
+                        fy[r][c] = d.x;
+                        fy[r][c + 1] = d.y;
+                    }
+            } else {
 #pragma unroll
-                for (int r = 0; r <= ROWS; ++r) fy[r][c] = face_flux<A, R>(col, R - 1 + r);
+                for (int c = 0; c < VX; ++c) {
+                    A col[2 * R + ROWS];
+#pragma unroll
+                    for (int m = 0; m < 2 * R + ROWS; ++m) col[m] = wy[m][c];
+#pragma unroll
+                    for (int r = 0; r <= ROWS; ++r) fy[r][c] = face_flux<A, R>(col, R - 1 + r);
+                }
             }
             A out[ROWS][VX];
 #pragma unroll
@@ -492,14 +505,36 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
                 A fx[VX + 1];  // x-face fluxes: fx[c] is the face left of cell c
 #pragma unroll
                 for (int c = 0; c <= VX; ++c) fx[c] = face_flux<A, R>(wx, c + R - 1);
+                if constexpr (kPair) {
+                    // the same operations as update_cell_f in the same order, two cells at a time:
+                    // ((fxp - fxm) + (fyp - fym)) + (fzp - fzm), then u + lam * div
 #pragma unroll
-                for (int c = 0; c < VX; ++c) {
-                    const A fzp = face_flux<A, R>(q[r][c], R);
-                    out[r][c] = update_cell_f<A>(fx[c + 1], fx[c], fy[r + 1][c], fy[r][c], fzp, fzm[r][c],
-                                                 q[r][c][R], lam);
-                    fzm[r][c] = fzp;
+                    for (int c = 0; c < VX; c += 2) {
+                        const F2 u = F2{q[r][c][1], q[r][c + 1][1]};
+                        const F2 fzp = sub2(F2{q[r][c][2], q[r][c + 1][2]}, u);
+                        const F2 dx = F2{Ar<A>::sub(fx[c + 1], fx[c]), Ar<A>::sub(fx[c + 2], fx[c + 1])};
+                        const F2 dy = sub2(F2{fy[r + 1][c], fy[r + 1][c + 1]}, F2{fy[r][c], fy[r][c + 1]});
+                        const F2 dz = sub2(fzp, F2{fzm[r][c], fzm[r][c + 1]});
+                        const F2 o = fma2(F2{lam, lam}, add2(add2(dx, dy), dz), u);
+                        out[r][c] = o.x;
+                        out[r][c + 1] = o.y;
+                        fzm[r][c] = fzp.x;
+                        fzm[r][c + 1] = fzp.y;
+                        q[r][c][0] = q[r][c][1];
+                        q[r][c][1] = q[r][c][2];
+                        q[r][c + 1][0] = q[r][c + 1][1];
+                        q[r][c + 1][1] = q[r][c + 1][2];
+                    }
+                } else {
 #pragma unroll
-                    for (int i = 0; i < 2 * R; ++i) q[r][c][i] = q[r][c][i + 1];
+                    for (int c = 0; c < VX; ++c) {
+                        const A fzp = face_flux<A, R>(q[r][c], R);
+                        out[r][c] = update_cell_f<A>(fx[c + 1], fx[c], fy[r + 1][c], fy[r][c], fzp, fzm[r][c],
+                                                     q[r][c][R], lam);
+                        fzm[r][c] = fzp;
+#pragma unroll
+                        for (int i = 0; i < 2 * R; ++i) q[r][c][i] = q[r][c][i + 1];
+                    }
                 }
             }
             // every read of the centre plane (and of the last R planes) is done
