@@ -437,6 +437,7 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
         for (int pl = 0; pl < 2 * R; ++pl)
             if (pl < R || pl >= t.tz + R) release(seq + pl);
 
+#pragma unroll(kPair ? 2 : 1)
         for (int k = 0; k < t.tz; ++k) {
             if (!__all_sync(0xffffffffu, wait_seq(seq + k + 2 * R))) {
                 if (lane == 0) atomicOr(p.err, 1);
