@@ -367,6 +367,9 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
                           ((f.org + f.n[0]) * (long long)sizeof(S)) % 32 == 16;
         const int xo = lpad ? -VX : VX;  // the extra store of a row-end group
         const bool both = __any_sync(0xffffffffu, lpad && rpad);  // one group spans the whole row
+        // the common case for the whole warp: every thread active with all its rows, whole groups,
+        // no row-end completion store -- each plane is then ROWS vector stores
+        const bool plain_st = __all_sync(0xffffffffu, act && nrow == ROWS && full && !lpad && !rpad);
         const A lam = (A)p.lam[f.level][t.comp];
 
         // Pieces that cover every plane of the tile and whole rows (the y faces) become one
@@ -561,7 +564,10 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
                 }
                 u0p += f.plane;
             }
-            if (act) {
+            if (plain_st) {
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) V::st(o + r * f.px, out[r]);
+            } else if (act) {
 #pragma unroll
                 for (int r = 0; r < ROWS; ++r) {
                     if (r >= nrow) continue;
