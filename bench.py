@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="headline only (no FP64, e2e, CPU baseline)")
     p.add_argument("--tile", default=None, help="fixed tile 'x,y,z' instead of the autotuner (0 = whole box)")
     p.add_argument("--kernel", default="tma", choices=["tma", "global"], help="stencil kernel variant")
+    p.add_argument("--only", default=None, choices=["rk3_8th"],
+                   help="run only this secondary line (for profiling) and print it")
     p.add_argument("--schedule", default=None,
                    help="fixed schedule 'x,y,z,rows,stages,group_bytes' instead of the autotuner")
     return p.parse_args()
@@ -183,7 +185,7 @@ def cpu_baseline(cfg, budget_s=15.0):
 # ------------------------------------------------------------------ our arm
 
 KERNEL_SOURCES = {
-    "k_stencil_tma": ["stencil_tma.cu", "stencil_common.cuh", "mf_internal.h"],
+    "k_stencil_tma": ["stencil_tma_kernel.cuh", "stencil_tma.cu", "stencil_common.cuh", "mf_internal.h"],
     "k_stencil": ["mf_kernels.cu", "stencil_common.cuh", "mf_internal.h"],
 }
 
@@ -274,6 +276,10 @@ def rk3_line(mf, torch, flush, args, hbm):
     m = mf.MultiFab([0, 0, 0], [N - 1] * 3, max_grid_size=c["max_grid_size"], ncomp=1, ngrow=c["ngrow"],
                     dtype=c["dtype"])
     m.from_host(dense)
+    if args.only and args.schedule:
+        v = [int(x) for x in args.schedule.split(",")]
+        m.set_tile(tuple(v[:3]))
+        mf.mf_set_schedule(m.h, *v[3:6])
     dt = synth.heat_dt(N, R)
     for _ in range(2):
         m.rk3_advance(R, [1.0], dt, n)
@@ -510,6 +516,20 @@ def main():
         if rank != 0:
             return 0
         print(json.dumps(run_reference(args, cfg)))
+        return 0
+    if args.only == "rk3_8th":
+        import torch
+        import paper_1604_03570_gb300 as mf
+        torch.cuda.set_device(local)
+        flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+        flush_rd = torch.ones(512 << 20, dtype=torch.uint8, device="cuda")
+
+        def flush():
+            flush_buf.fill_(1)
+            flush_rd.max()
+
+        peaks, _ = measured_peaks()
+        print(json.dumps({"rk3_8th": rk3_line(mf, torch, flush, args, float(peaks["hbm_gbs"]))}))
         return 0
     out = run_ours(args, cfg, ws, rank, local)
     if out is not None:
