@@ -270,25 +270,158 @@ def average_down(fine, crse, ratio, fdata, cdata):
                                   fine.C, int(ratio), _p(fdata), _p(cdata))
 
 
-def amr_advance(crse, fine, R, lam_c, cdata, fdata, ncrse_steps, nsub=2, ratio=2):
+class CFFaces:
+    """The coarse-fine faces of a refined level, for refluxing (reading of the paper's
+    subcycling: Berger-Colella flux correction).  A fine face is a coarse-fine face when the
+    fine cell on its outside (periodic images included) lies in no fine box; the r^2 fine faces
+    on one face of an uncovered coarse cell C form one coarse face.  Fine boxes must consist of
+    whole coarse cells.
+
+    For each coarse face: the coarse cell C (global index), the direction d and sc = +1 when the
+    fine region is on C's high side in d (-1 on its low side).  For each fine box face: the
+    coarse-face id of every fine face (-1 where the outside is another fine box)."""
+
+    def __init__(self, crse, fine, ratio):
+        r = int(ratio)
+        flo, fhi = fine.dlo.astype(int), fine.dhi.astype(int)
+        Lf = fhi - flo + 1
+        clo = crse.dlo.astype(int)
+        cov = np.zeros((Lf[2], Lf[1], Lf[0]), dtype=bool)  # fine domain coverage, (z, y, x)
+        for b in fine.boxes:
+            if any((b[d] - flo[d]) % r or (b[3 + d] - flo[d] + 1) % r for d in range(3)):
+                raise ValueError("fine boxes must consist of whole coarse cells")
+            cov[b[2] - flo[2]:b[5] - flo[2] + 1, b[1] - flo[1]:b[4] - flo[1] + 1, b[0] - flo[0]:b[3] - flo[0] + 1] = True
+        keys = {}
+        self.slabs = []
+        for bi, b in enumerate(fine.boxes):
+            lo, hi = np.array(b[:3]), np.array(b[3:])
+            for d in range(3):
+                e = [a for a in range(3) if a != d]  # the two in-face directions, increasing
+                for s in (-1, 1):
+                    inside = hi[d] if s > 0 else lo[d]
+                    out = inside + s
+                    ga = np.arange(lo[e[0]], hi[e[0]] + 1)
+                    gb = np.arange(lo[e[1]], hi[e[1]] + 1)
+                    A, B = np.meshgrid(ga, gb, indexing="ij")  # (n_a, n_b) fine indices in the face
+                    P = [None, None, None]
+                    P[d] = np.full(A.shape, out)
+                    P[e[0]], P[e[1]] = A, B
+                    W = [(P[k] - flo[k]) % Lf[k] for k in range(3)]  # wrapped outside cell
+                    unc = ~cov[W[2], W[1], W[0]]
+                    cid = np.full(A.shape, -1, dtype=np.int64)
+                    if unc.any():
+                        Cg = [(W[k] // r) + clo[k] for k in range(3)]  # coarse cell outside (wrapped)
+                        for ia, ib in zip(*np.nonzero(unc)):
+                            key = (int(Cg[0][ia, ib]), int(Cg[1][ia, ib]), int(Cg[2][ia, ib]), d, -s)
+                            if key not in keys:
+                                keys[key] = len(keys)
+                            cid[ia, ib] = keys[key]
+                    self.slabs.append((bi, d, s, e, cid))
+        self.faces = np.array(sorted(keys, key=keys.get), dtype=np.int64).reshape(-1, 5)
+        self.r = r
+
+    @property
+    def n(self):
+        return self.faces.shape[0]
+
+
+def _line_flux(vals, b):
+    """F = sum_m b_m (v[R-1+m] - v[R-m]) over a line of 2R values (axis 0) across a face."""
+    R = len(b)
+    f = np.zeros(vals.shape[1:])
+    for m in range(1, R + 1):
+        f = f + b[m - 1] * (vals[R - 1 + m] - vals[R - m])
+    return f
+
+
+def cf_fine_flux(fine, cf, R, fdata):
+    """Per coarse face and component: the sum of the face fluxes F of its r^2 fine faces, each
+    from the fine box inside (its ghost cells hold the outside values); shape (C, nfaces)."""
+    b = [float(x) for x in coeffs.flux_coefficients(R)]
+    acc = np.zeros((fine.C, cf.n))
+    g = fine.g
+    for bi, d, s, e, cid in cf.slabs:
+        if not (cid >= 0).any():
+            continue
+        lo, hi = fine.boxes[bi, :3], fine.boxes[bi, 3:]
+        F = fine.fab(fdata, bi)  # (C, z, y, x) with ghosts
+        inside = (hi[d] if s > 0 else lo[d]) - lo[d] + g  # local index along d
+        low = inside if s > 0 else inside - 1  # lower cell of the face
+        vals = []
+        for k in range(-R + 1, R + 1):
+            sl = [slice(None)] * 4
+            sl[3 - d] = low + k
+            for a in e:
+                sl[3 - a] = slice(g, g + hi[a] - lo[a] + 1)
+            v = F[tuple(sl)]  # (C, n_e1, n_e0) in (z, y, x) order without the d axis
+            vals.append(np.transpose(v, (0, 2, 1)))  # (C, n_e0, n_e1) = (C, n_a, n_b)
+        fl = _line_flux(np.stack(vals), b)  # (C, n_a, n_b)
+        m = cid >= 0
+        for c in range(fine.C):
+            np.add.at(acc[c], cid[m], fl[c][m])
+    return acc
+
+
+def cf_coarse_flux(crse, cf, R, cdata):
+    """Per coarse face and component: the coarse face flux F, from the (periodic) coarse level."""
+    b = [float(x) for x in coeffs.flux_coefficients(R)]
+    dense = crse.to_dense(cdata)  # (C, z, y, x)
+    L = crse.dhi.astype(int) - crse.dlo.astype(int) + 1
+    clo = crse.dlo.astype(int)
+    out = np.zeros((crse.C, cf.n))
+    for i, (x, y, z, d, sc) in enumerate(cf.faces):
+        low = np.array([x, y, z]) - clo
+        if sc < 0:
+            low[d] -= 1
+        vals = []
+        for k in range(-R + 1, R + 1):
+            p = low.copy()
+            p[d] += k
+            p = p % L
+            vals.append(dense[:, p[2], p[1], p[0]])
+        out[:, i] = _line_flux(np.stack(vals), b)
+    return out
+
+
+def reflux(crse, cf, corr, cdata):
+    """Add corr[c, face] to the coarse cell of each coarse face (in place, valid cells)."""
+    dense = crse.to_dense(cdata)
+    clo = crse.dlo.astype(int)
+    for i, (x, y, z, d, sc) in enumerate(cf.faces):
+        dense[:, z - clo[2], y - clo[1], x - clo[0]] += corr[:, i]
+    cdata[:] = crse.from_dense(dense)
+
+
+def amr_advance(crse, fine, R, lam_c, cdata, fdata, ncrse_steps, nsub=2, ratio=2, reflux_faces=False):
     """Two-level step (reading of Sec. 3's subcycling): per coarse step, FillBoundary and
     stencil on the coarse level (lam_c); then nsub fine substeps, each FillBoundary, coarse-fine
     interpolation at alpha = s/nsub between the coarse old and new data, and the fine stencil
     with lam_f = lam_c * ratio^2 / nsub; then average-down onto the new coarse data.
-    No refluxing.  Returns (cdata, fdata) new arrays."""
+    With reflux_faces, every uncovered coarse cell next to a coarse-fine face then trades the
+    coarse face flux for the time- and area-average of the fine ones (Berger-Colella):
+    u_C += sc * (lam_f / r^3 * sum over substeps and the r^2 fine faces of F_f - lam_c * F_c).
+    Returns (cdata, fdata) new arrays."""
     lam_c = _lam_array(crse, lam_c)
     lam_f = lam_c * (ratio * ratio) / nsub
     c_cur = np.array(cdata, dtype=np.float64, copy=True)
     f_cur = np.array(fdata, dtype=np.float64, copy=True)
     c_new, f_new = crse.alloc(), fine.alloc()
+    cf = CFFaces(crse, fine, ratio) if reflux_faces else None
     for _ in range(ncrse_steps):
         fill_boundary(crse, c_cur)
+        if cf is not None:
+            fc = lam_c[:, None] * cf_coarse_flux(crse, cf, R, c_cur)
+            ff = np.zeros_like(fc)
         stencil(crse, R, lam_c, c_cur, c_new)
         for s in range(nsub):
             fill_boundary(fine, f_cur)
             interp_cf(fine, crse, ratio, s / nsub, c_cur, c_new, f_cur)
+            if cf is not None:
+                ff += (lam_f / ratio ** 3)[:, None] * cf_fine_flux(fine, cf, R, f_cur)
             stencil(fine, R, lam_f, f_cur, f_new)
             f_cur, f_new = f_new, f_cur
         average_down(fine, crse, ratio, f_cur, c_new)
+        if cf is not None:
+            reflux(crse, cf, cf.faces[:, 4][None, :] * (ff - fc), c_new)
         c_cur, c_new = c_new, c_cur
     return c_cur, f_cur

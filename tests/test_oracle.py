@@ -472,6 +472,75 @@ def test_amr_with_full_fine_cover_equals_fine_single_level():
     np.testing.assert_array_equal(crse.to_dense(c_out), crse.to_dense(c_ref))
 
 
+def _composite_sum(crse, fine, cdata, fdata, ratio=2, comp=0):
+    """sum of the fine cells plus r^3 times the coarse cells no fine box covers (fine-cell units)."""
+    cd, fd = crse.to_dense(cdata)[comp], fine.to_dense(fdata)[comp]
+    covered = np.zeros(cd.shape, dtype=bool)
+    for b in fine.boxes:
+        covered[b[2] // ratio:b[5] // ratio + 1, b[1] // ratio:b[4] // ratio + 1, b[0] // ratio:b[3] // ratio + 1] = True
+    vals = (ratio ** 3 * cd[~covered]).tolist() + fd[~np.isnan(fd)].tolist()
+    return math.fsum(vals), math.fsum(np.abs(vals).tolist())
+
+
+def _two_level_case(R, g):
+    Nc = 16
+    crse = oracle.Level(oracle.chop([0, 0, 0], [Nc - 1] * 3, 8), [0, 0, 0], [Nc - 1] * 3, g, 2)
+    fboxes = [[8, 8, 4, 15, 23, 19], [16, 8, 4, 23, 15, 11], [0, 24, 26, 5, 31, 31], [26, 24, 26, 31, 31, 31]]
+    fine = oracle.Level(fboxes, [0, 0, 0], [2 * Nc - 1] * 3, g, 2)
+    dense_f = _rand((2, 2 * Nc, 2 * Nc, 2 * Nc), seed=21)
+    fd = fine.from_dense(dense_f)
+    cd = crse.from_dense(_rand((2, Nc, Nc, Nc), seed=22))
+    oracle.average_down(fine, crse, 2, fd, cd)
+    return crse, fine, cd, fd
+
+
+@pytest.mark.parametrize("R,g", [(1, 1), (2, 2)])
+def test_reflux_conserves_the_composite_sum(R, g):
+    """With refluxing, the coarse flux at every coarse-fine face is replaced by the fine fluxes
+    through it, so the composite sum (fine cells plus r^3 times the uncovered coarse cells) is
+    invariant up to rounding; without it, it is not.  The fine boxes include a pair that meets
+    across the periodic boundary and one with a face on it."""
+    crse, fine, cd, fd = _two_level_case(R, g)
+    lam_c = {1: 0.075, 2: 0.05}[R]
+    for comp in range(2):
+        s0, a0 = _composite_sum(crse, fine, cd, fd, comp=comp)
+        c1, f1 = oracle.amr_advance(crse, fine, R, lam_c, cd, fd, 3, reflux_faces=True)
+        s1, _ = _composite_sum(crse, fine, c1, f1, comp=comp)
+        assert abs(s1 - s0) <= 3 * 2 * 1e-15 * a0, (comp, s1 - s0)
+        c2, f2 = oracle.amr_advance(crse, fine, R, lam_c, cd, fd, 3)
+        s2, _ = _composite_sum(crse, fine, c2, f2, comp=comp)
+        assert abs(s2 - s0) > 1e-6 * a0  # the test has teeth: no refluxing, no conservation
+
+
+def test_reflux_without_coarse_fine_faces_changes_nothing():
+    """A fine level covering the whole domain has no coarse-fine face."""
+    Nc = 8
+    crse = oracle.Level(oracle.chop([0, 0, 0], [Nc - 1] * 3, 4), [0, 0, 0], [Nc - 1] * 3, 1, 1)
+    fine = oracle.Level(oracle.chop([0, 0, 0], [2 * Nc - 1] * 3, 8), [0, 0, 0], [2 * Nc - 1] * 3, 1, 1)
+    fd = fine.from_dense(_rand((1, 2 * Nc, 2 * Nc, 2 * Nc), seed=23))
+    cd = crse.from_dense(np.zeros((1, Nc, Nc, Nc)))
+    oracle.average_down(fine, crse, 2, fd, cd)
+    assert oracle.CFFaces(crse, fine, 2).n == 0
+    a = oracle.amr_advance(crse, fine, 1, 0.075, cd, fd, 2, reflux_faces=True)
+    b = oracle.amr_advance(crse, fine, 1, 0.075, cd, fd, 2)
+    np.testing.assert_array_equal(crse.to_dense(a[0]), crse.to_dense(b[0]))
+
+
+def test_cf_faces_of_a_single_box_are_its_surface():
+    """One fine box of 4x6x8 coarse cells inside the domain: 2(4*6 + 4*8 + 6*8) coarse faces,
+    each on a distinct (coarse cell, direction, side)."""
+    Nc = 16
+    crse = oracle.Level(oracle.chop([0, 0, 0], [Nc - 1] * 3, 8), [0, 0, 0], [Nc - 1] * 3, 1, 1)
+    fine = oracle.Level([[4, 6, 8, 11, 17, 23]], [0, 0, 0], [2 * Nc - 1] * 3, 1, 1)
+    cf = oracle.CFFaces(crse, fine, 2)
+    assert cf.n == 2 * (4 * 6 + 4 * 8 + 6 * 8)
+    assert len({tuple(f) for f in cf.faces}) == cf.n
+    # every coarse cell named lies outside the box and next to it
+    for x, y, z, d, sc in cf.faces:
+        inside = 2 <= x <= 5 and 3 <= y <= 8 and 4 <= z <= 11
+        assert not inside
+
+
 def test_amr_keeps_constant_state():
     Nc = 8
     crse, fine = _fine_setup(Nc)
