@@ -46,14 +46,15 @@ typedef enum { MF_LAP2_7PT = 1, MF_LAP4_13PT = 2, MF_LAP8_25PT = 4 } mf_stencil_
 /* mf_stencil.flags */
 enum {
     MF_FP64_DIFF = 1,     /* FP32/BF16 storage: compute the flux differences in FP64 */
-    MF_PLAIN_PER_BOX = 2  /* the untiled baseline of Sec. 3.1: one launch per box per phase,
+    MF_PLAIN_PER_BOX = 2, /* the untiled baseline of Sec. 3.1: one launch per box per phase,
                              launched eagerly, no work list, no graph */
+    MF_REFLUX = 4         /* mf_amr_advance only: Berger-Colella refluxing (see there) */
 };
 
 typedef struct {
     int kind;                  /* mf_stencil_kind */
     const double *diffusivity; /* [ncomp] D_c > 0 */
-    int flags;                 /* MF_FP64_DIFF | MF_PLAIN_PER_BOX */
+    int flags;                 /* MF_FP64_DIFF | MF_PLAIN_PER_BOX | MF_REFLUX */
 } mf_stencil;
 
 /* Error codes */
@@ -186,7 +187,15 @@ int mf_advance(mf_t *mf, const mf_stencil *st, double dt, int nsteps);
  * mf_amr_advance -- two-level subcycled advance (fine = crse refined by ratio): per coarse step,
  * FillBoundary + stencil on the coarse level; then nsub fine substeps of dt/nsub, each
  * FillBoundary + coarse-fine interpolation at alpha = s/nsub + stencil; then average-down
- * onto the new coarse level.  Both levels must have the same dtype and ncomp.  No refluxing.
+ * onto the new coarse level.  Both levels must have the same dtype and ncomp.
+ * With MF_REFLUX in st->flags (Berger-Colella flux correction, which makes the two-level
+ * advance conservative): every coarse cell that lies in no fine box but shares a face with the
+ * fine region is corrected after the average-down by
+ *   sc * (lam_f / r^3 * sum over substeps and the r^2 fine faces of F_f - lam_c * F_c),
+ * F the face flux of the stencil (sum_m b_m (u_{i+m} - u_{i+1-m})), sc = +1 when the fine
+ * region is on the cell's high side, -1 on its low side; fluxes in FP64 from the coarse state at
+ * the start of the step and from each substep's fine state after its fill and interpolation.
+ * The fine boxes must consist of whole coarse cells (MF_EINVAL otherwise).
  */
 int mf_amr_advance(mf_t *crse, mf_t *fine, const mf_stencil *st, double dt_crse, int ncrse_steps, int nsub,
                    int ratio);
@@ -240,8 +249,8 @@ int mf_set_timing(mf_t *mf, int on);
 int mf_phase_ms(mf_t *mf, double out[2]);
 
 /* Kernel launches of the last mf_advance (or, on the coarse handle, mf_amr_advance) call:
- * out[0] ghost-fill, out[1] stencil, out[2] coarse-fine interpolation, out[3] average-down
- * launches.  Launches whose work list is empty are not made and not counted. */
+ * out[0] ghost-fill, out[1] stencil, out[2] coarse-fine interpolation and flux-register,
+ * out[3] average-down and reflux launches.  Launches whose work list is empty are not made and not counted. */
 int mf_launch_count(const mf_t *mf, int out[4]);
 
 /* Measured FP64 fused multiply-add throughput of the current GPU in TFLOP/s (2 flops per

@@ -185,6 +185,17 @@ struct InterpPlan {
     std::vector<InterpRun> runs;
     DevBuf d_runs;
 };
+
+// Refluxing plan of a (fine, coarse) level pair: the coarse faces of the coarse-fine interface,
+// their fine faces, the coarse cells to correct, and the FP64 flux registers.
+struct RefluxPlan {
+    const mf_t *crse = nullptr;
+    int ratio = 0;
+    std::vector<CFace> faces;
+    std::vector<FFace> ff;
+    std::vector<CCell> cells;
+    DevBuf d_faces, d_ff, d_cells, d_regc, d_regf;
+};
 struct AvgPlan {
     const mf_t *fine = nullptr;
     int ratio = 0;
@@ -253,6 +264,7 @@ struct mf {
     std::vector<char> ev_kinds;    // phase of each interval of the last timed advance
     int launches[4] = {0, 0, 0, 0};  // kernel launches of the last advance (see GraphExec)
     std::vector<std::unique_ptr<InterpPlan>> interp;
+    std::vector<std::unique_ptr<RefluxPlan>> reflux;
     std::vector<std::unique_ptr<AvgPlan>> avg;
     ~mf() {
         graphs.clear();
@@ -1561,6 +1573,7 @@ extern "C" int mf_advance(mf_t *m, const mf_stencil *st, double dt, int nsteps) 
     if (nsteps == 0) return 0;
     const int R = st->kind;
     const bool fp64diff = (st->flags & MF_FP64_DIFF) && m->dtype != F64;
+    if (st->flags & MF_REFLUX) return fail(MF_EINVAL, "MF_REFLUX applies to mf_amr_advance only");
     if (st->flags & MF_PLAIN_PER_BOX) {
         if (fp64diff) return fail(MF_EINVAL, "MF_PLAIN_PER_BOX does not combine with MF_FP64_DIFF");
         return advance_plain(m, R, lam, nsteps);
@@ -1631,7 +1644,7 @@ extern "C" int mf_rk3_advance(mf_t *m, const mf_stencil *st, double dt, int nste
     double lam[kMaxComp];
     if ((rc = check_stencil(m, st, dt, lam, 1.0))) return rc;
     if (nsteps < 0) return fail(MF_EINVAL, "nsteps must be >= 0");
-    if (st->flags & MF_PLAIN_PER_BOX) return fail(MF_EINVAL, "MF_PLAIN_PER_BOX does not apply to mf_rk3_advance");
+    if (st->flags & (MF_PLAIN_PER_BOX | MF_REFLUX)) return fail(MF_EINVAL, "MF_PLAIN_PER_BOX and MF_REFLUX do not apply to mf_rk3_advance");
     if (nsteps == 0) return 0;
     const int R = st->kind;
     const bool fp64diff = (st->flags & MF_FP64_DIFF) && m->dtype != F64;
@@ -1714,6 +1727,121 @@ static int wrap_idx(int i, int lo, int len) {
     int r = (i - lo) % len;
     if (r < 0) r += len;
     return lo + r;
+}
+
+// The coarse-fine interface of a refined level: for every face of every fine box, each group of
+// r x r fine faces whose outside coarse cell (periodic) lies in no fine box is one coarse face.
+// Fine boxes must consist of whole coarse cells, and the coarse level must cover its domain.
+static int build_reflux(const mf_t *fine, const mf_t *crse, int r, RefluxPlan &plan) {
+    const Box &fd = fine->domain, &cd = crse->domain;
+    int Lc[3];
+    for (int d = 0; d < 3; ++d) {
+        Lc[d] = cd.len(d);
+        if (fd.lo[d] != r * cd.lo[d] || fd.len(d) != r * Lc[d]) return fail(MF_EINVAL, "fine domain is not the refined coarse domain");
+    }
+    std::vector<unsigned char> cov((size_t)Lc[0] * Lc[1] * Lc[2], 0);  // coarse cells under fine boxes
+    for (auto &b : fine->boxes) {
+        for (int d = 0; d < 3; ++d)
+            if ((b.lo[d] - fd.lo[d]) % r || (b.hi[d] + 1 - fd.lo[d]) % r)
+                return fail(MF_EINVAL, "refluxing needs fine boxes made of whole coarse cells");
+        for (int z = floor_div(b.lo[2], r); z <= floor_div(b.hi[2], r); ++z)
+            for (int y = floor_div(b.lo[1], r); y <= floor_div(b.hi[1], r); ++y)
+                for (int x = floor_div(b.lo[0], r); x <= floor_div(b.hi[0], r); ++x)
+                    cov[((size_t)(z - cd.lo[2]) * Lc[1] + (y - cd.lo[1])) * Lc[0] + (x - cd.lo[0])] = 1;
+    }
+    BinHash hash;
+    hash.build(cd, crse->boxes);
+    std::vector<int> cand, stamp(crse->boxes.size(), -1);
+    int tag = 0;
+    struct Tmp { long long c_elem; CFace f; };
+    std::vector<Tmp> tmp;
+    plan.ff.clear();
+    for (size_t bf = 0; bf < fine->boxes.size(); ++bf) {
+        const Box &B = fine->boxes[bf];
+        const FabInfo &Ff = fine->fabs[bf];
+        for (int d = 0; d < 3; ++d) {
+            const int e0 = d == 0 ? 1 : 0, e1 = d == 2 ? 1 : 2;
+            const long long fds = d == 0 ? 1 : d == 1 ? (long long)Ff.px : Ff.plane;
+            for (int s = -1; s <= 1; s += 2) {
+                const int in = s > 0 ? B.hi[d] : B.lo[d];
+                const int outc = wrap_idx(((in + s) - fd.lo[d] + fd.len(d)) % fd.len(d) / r + cd.lo[d], cd.lo[d], Lc[d]);
+                for (int b1 = B.lo[e1]; b1 <= B.hi[e1]; b1 += r)
+                    for (int a0 = B.lo[e0]; a0 <= B.hi[e0]; a0 += r) {
+                        int C[3];
+                        C[d] = outc;
+                        C[e0] = wrap_idx(floor_div(a0, r), cd.lo[e0], Lc[e0]);
+                        C[e1] = wrap_idx(floor_div(b1, r), cd.lo[e1], Lc[e1]);
+                        if (cov[((size_t)(C[2] - cd.lo[2]) * Lc[1] + (C[1] - cd.lo[1])) * Lc[0] + (C[0] - cd.lo[0])])
+                            continue;  // the outside is another fine box
+                        Box q;
+                        for (int k = 0; k < 3; ++k) q.lo[k] = q.hi[k] = C[k];
+                        hash.query(q, cand, stamp, ++tag);
+                        int owner = -1;
+                        for (int a : cand)
+                            if (!intersect(crse->boxes[a], q).empty()) { owner = a; break; }
+                        if (owner < 0) return fail(MF_EINVAL, "coarse level does not cover its domain");
+                        const FabInfo &Fc = crse->fabs[owner];
+                        Tmp t;
+                        t.c_elem = elem_at(Fc, C[0], C[1], C[2]);
+                        int Lw[3] = {C[0], C[1], C[2]};
+                        if (-s < 0) Lw[d] -= 1;  // fine region on C's low side: the face's lower cell is C - e_d
+                        t.f.c_low = elem_at(Fc, Lw[0], Lw[1], Lw[2]);
+                        t.f.cstride = Fc.cstride;
+                        t.f.dstride = d == 0 ? 1 : d == 1 ? (long long)Fc.px : Fc.plane;
+                        t.f.sc = -s;
+                        t.f.ffirst = (int)plan.ff.size();
+                        for (int j1 = 0; j1 < r; ++j1)
+                            for (int j0 = 0; j0 < r; ++j0) {
+                                int P[3];
+                                P[d] = s > 0 ? in : in - 1;  // lower cell of the fine face
+                                P[e0] = a0 + j0;
+                                P[e1] = b1 + j1;
+                                FFace g;
+                                g.f_low = elem_at(Ff, P[0], P[1], P[2]);
+                                g.cstride = Ff.cstride;
+                                g.dstride = fds;
+                                plan.ff.push_back(g);
+                            }
+                        tmp.push_back(t);
+                    }
+            }
+        }
+    }
+    // group the faces by coarse cell (fixed order: cell, then the order found)
+    std::stable_sort(tmp.begin(), tmp.end(), [](const Tmp &a, const Tmp &b) { return a.c_elem < b.c_elem; });
+    plan.faces.clear();
+    plan.cells.clear();
+    for (size_t i = 0; i < tmp.size(); ++i) {
+        if (i == 0 || tmp[i].c_elem != tmp[i - 1].c_elem) {
+            CCell c;
+            c.c_elem = tmp[i].c_elem;
+            c.cstride = tmp[i].f.cstride;
+            c.efirst = (int)plan.faces.size();
+            c.ecount = 0;
+            plan.cells.push_back(c);
+        }
+        plan.faces.push_back(tmp[i].f);
+        plan.cells.back().ecount++;
+    }
+    return 0;
+}
+
+static RefluxPlan *get_reflux(mf_t *fine, const mf_t *crse, int ratio, int *rc) {
+    for (auto &p : fine->reflux)
+        if (p->crse == crse && p->ratio == ratio) { *rc = 0; return p.get(); }
+    auto p = std::make_unique<RefluxPlan>();
+    p->crse = crse;
+    p->ratio = ratio;
+    if ((*rc = build_reflux(fine, crse, ratio, *p))) return nullptr;
+    const size_t nreg = std::max<size_t>(1, p->faces.size() * (size_t)fine->ncomp) * sizeof(double);
+    if ((*rc = p->d_faces.upload(p->faces, fine->stream))) return nullptr;
+    if ((*rc = p->d_ff.upload(p->ff, fine->stream))) return nullptr;
+    if ((*rc = p->d_cells.upload(p->cells, fine->stream))) return nullptr;
+    if ((*rc = p->d_regc.ensure(nreg))) return nullptr;
+    if ((*rc = p->d_regf.ensure(nreg))) return nullptr;
+    if (cudaStreamSynchronize(fine->stream) != cudaSuccess) { *rc = fail(MF_ECUDA, "sync"); return nullptr; }
+    fine->reflux.push_back(std::move(p));
+    return fine->reflux.back().get();
 }
 
 static int build_interp(mf_t *fine, const mf_t *crse, int ratio, InterpPlan &plan) {
@@ -1906,6 +2034,17 @@ extern "C" int mf_amr_advance(mf_t *crse, mf_t *fine, const mf_stencil *st, doub
     if (!ip) return rc;
     AvgPlan *ap = get_avg(fine, crse, ratio, &rc);
     if (!ap) return rc;
+    const bool do_reflux = (st->flags & MF_REFLUX) != 0;
+    RefluxPlan *rp = nullptr;
+    RefluxW wc{}, wf{};
+    if (do_reflux) {
+        if (fine->ncomp != crse->ncomp) return fail(MF_EINVAL, "levels differ in components");
+        if (!(rp = get_reflux(fine, crse, ratio, &rc))) return rc;
+        for (int c = 0; c < crse->ncomp; ++c) {
+            wc.w[c] = lam_c[c];
+            wf.w[c] = lam_f[c] / ((double)ratio * ratio * ratio);
+        }
+    }
     if (crse->tile_auto && (rc = autotune(crse, R, fp64diff, lam_c))) return rc;
     if (fine->tile_auto && (rc = autotune(fine, R, fp64diff, lam_f))) return rc;
     if (crse->use_tma && crse->tma_R != R && (rc = build_tma(crse, R))) return rc;
@@ -1913,8 +2052,8 @@ extern "C" int mf_amr_advance(mf_t *crse, mf_t *fine, const mf_stencil *st, doub
     // the coarse stream orders everything; the fine stream waits for nothing else (same
     // stream expected); capture the whole advance into one graph
     char buf[160];
-    snprintf(buf, sizeof buf, "amr|%p|g%llu|g%llu|s%d|r%d|fc%d", (void *)fine, crse->gen, fine->gen, nsub, ratio,
-             fine->cur);
+    snprintf(buf, sizeof buf, "amr|%p|g%llu|g%llu|s%d|r%d|fc%d|x%d", (void *)fine, crse->gen, fine->gen, nsub, ratio,
+             fine->cur, (int)do_reflux);
     const std::string key = graph_key(buf, R, fp64diff, lam_c, crse->ncomp, ncrse_steps, crse->cur);
     auto it = crse->graphs.find(key);
     if (it == crse->graphs.end()) {
@@ -1925,18 +2064,36 @@ extern "C" int mf_amr_advance(mf_t *crse, mf_t *fine, const mf_stencil *st, doub
         for (int step = 0; step < ncrse_steps && !body; ++step) {
             // full exchange: the coarse-fine interpolation reads coarse edge and corner ghosts
             const bool cf = !crse->fbtasks.empty();
+            const int nface = rp ? (int)rp->faces.size() : 0;
             if (!(body = log.before(0, cf))) body = enqueue_fill(crse, c, s);
+            if (!body && rp && !(body = log.before(2, nface > 0)))  // coarse face fluxes at the interface
+                body = launch_cf_coarse_flux(crse->dtype, R, crse->level_ptr(c), (const CFace *)rp->d_faces.p, nface,
+                                             crse->ncomp, wc, (double *)rp->d_regc.p, s) == cudaSuccess
+                           ? 0
+                           : fail(MF_ECUDA, "flux register launch failed");
             if (!body && !(body = log.before(1))) body = enqueue_stencil(crse, c, R, fp64diff, lam_c, s);
             if (!body && !(body = log.before(0, cf))) body = enqueue_fill(crse, 1 - c, s);
             for (int sub = 0; sub < nsub && !body; ++sub) {
                 if (!(body = log.before(0, fill_step_tasks(fine) > 0))) body = enqueue_fill_step(fine, f, s);
                 if (!body && !(body = log.before(2, !ip->runs.empty())))
                     body = enqueue_interp(fine, f, crse, c, crse, 1 - c, ip, ratio, (double)sub / (double)nsub, s);
+                if (!body && rp && !(body = log.before(2, nface > 0)))  // fine face fluxes, this substep
+                    body = launch_cf_fine_flux(fine->dtype, R, fine->level_ptr(f), (const CFace *)rp->d_faces.p,
+                                               (const FFace *)rp->d_ff.p, nface, ratio * ratio, fine->ncomp, wf,
+                                               (double *)rp->d_regf.p, sub == 0, s) == cudaSuccess
+                               ? 0
+                               : fail(MF_ECUDA, "flux register launch failed");
                 if (!body && !(body = log.before(1))) body = enqueue_stencil(fine, f, R, fp64diff, lam_f, s);
                 f = 1 - f;
             }
             if (!body && !(body = log.before(3, !ap->regs.empty())))
                 body = enqueue_avg(fine, f, crse, 1 - c, ap, ratio, s);
+            if (!body && rp && !(body = log.before(3, !rp->cells.empty())))  // the flux correction
+                body = launch_reflux_apply(crse->dtype, crse->level_ptr(1 - c), (const CCell *)rp->d_cells.p,
+                                           (int)rp->cells.size(), (const CFace *)rp->d_faces.p, crse->ncomp,
+                                           (const double *)rp->d_regc.p, (const double *)rp->d_regf.p, s) == cudaSuccess
+                           ? 0
+                           : fail(MF_ECUDA, "reflux launch failed");
             c = 1 - c;
         }
         if ((rc = capture_end(crse, key, body))) return rc;

@@ -187,6 +187,38 @@ cudaError_t launch_stencil_plain(int dtype, int R, const void *src, void *dst, c
                                  int comp, cudaStream_t s);
 cudaError_t launch_fill_plain(int dtype, void *base, const FabInfo *ftab, const FbEntry *ent, int count,
                               long long total, const int *cbeg, cudaStream_t s);
+// Refluxing of the two-level advance (Berger-Colella flux correction).  A coarse face of the
+// coarse-fine interface: the coarse cell C next to it lies in no fine box; the fine region is on
+// C's high side (sc = +1) or low side (sc = -1) along direction d.
+struct CFace {
+    long long c_low;    // element offset (coarse level, comp 0) of the face's lower cell, in C's FArrayBox
+    long long cstride;  // component stride of that FArrayBox
+    long long dstride;  // its element stride along d
+    int ffirst;         // the face's r^2 fine faces: FFace[ffirst .. ffirst + r^2)
+    int sc;
+};
+// A fine face on the interface, seen from the fine box inside (its ghost cells hold the outside).
+struct FFace {
+    long long f_low;    // element offset (fine level, comp 0) of the face's lower cell
+    long long cstride;
+    long long dstride;
+};
+// An uncovered coarse cell next to the interface and its coarse faces CFace[efirst .. + ecount).
+struct CCell {
+    long long c_elem;
+    long long cstride;
+    int efirst, ecount;
+};
+struct RefluxW {
+    double w[kMaxComp];  // per component: lam_c (coarse fluxes) or lam_f / r^3 (fine fluxes)
+};
+cudaError_t launch_cf_coarse_flux(int dtype, int R, const void *base, const CFace *faces, int n, int ncomp,
+                                  const RefluxW &w, double *reg, cudaStream_t s);
+cudaError_t launch_cf_fine_flux(int dtype, int R, const void *base, const CFace *faces, const FFace *ff, int n,
+                                int nff, int ncomp, const RefluxW &w, double *reg, bool first, cudaStream_t s);
+cudaError_t launch_reflux_apply(int dtype, void *base, const CCell *cells, int ncell, const CFace *faces, int ncomp,
+                                const double *regc, const double *regf, cudaStream_t s);
+
 // whole-level reduction of one component (RED_*), result written to out_dev (device)
 enum { RED_SUM = 0, RED_MAX = 1, RED_MIN = 2, RED_NORM0 = 3, RED_NORM1 = 4, RED_NORM2 = 5 };
 cudaError_t launch_reduce(int dtype, int op, const void *base, const FabInfo *ftab, const long long *rowpre, int nfab,

@@ -20,6 +20,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "mf_internal.h"
@@ -184,6 +185,128 @@ __global__ void k_stencil_plain(const S *__restrict__ src, S *__restrict__ dst, 
 }
 
 // ------------------------------------------------------------------ reduction
+
+// ------------------------------------------------------------------ refluxing
+// Berger-Colella flux correction of the two-level advance, in FP64 whatever the storage:
+// reg_c = lam_c * F_c per coarse face, reg_f = sum over substeps of lam_f / r^3 * (sum of the
+// r^2 fine face fluxes), and every uncovered coarse cell next to the interface adds
+// sum over its faces of sc * (reg_f - reg_c).  One thread per (face or cell, component), the
+// sums in a fixed order.
+
+template <typename S, int R>
+__device__ __forceinline__ double line_flux(const S *low, long long dstride) {
+    double q[2 * R];  // q[j] = u(low + (j - R + 1) e_d)
+#pragma unroll
+    for (int j = 0; j < 2 * R; ++j) q[j] = to_f64(low[(long long)(j - R + 1) * dstride]);
+    return face_flux<double, R>(q, R - 1);
+}
+
+template <typename S, int R>
+__global__ void __launch_bounds__(256) k_cf_coarse_flux(const S *__restrict__ base, const CFace *__restrict__ faces,
+                                                        int n, int ncomp, RefluxW w, double *reg) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * ncomp; i += gridDim.x * blockDim.x) {
+        const int e = i / ncomp, c = i - e * ncomp;
+        const CFace f = faces[e];
+        reg[i] = __dmul_rn(w.w[c], line_flux<S, R>(base + f.c_low + c * f.cstride, f.dstride));
+    }
+}
+
+template <typename S, int R>
+__global__ void __launch_bounds__(256) k_cf_fine_flux(const S *__restrict__ base, const CFace *__restrict__ faces,
+                                                      const FFace *__restrict__ ff, int n, int nff, int ncomp,
+                                                      RefluxW w, double *reg, int first) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * ncomp; i += gridDim.x * blockDim.x) {
+        const int e = i / ncomp, c = i - e * ncomp;
+        const int f0 = faces[e].ffirst;
+        double sum = 0.0;
+        for (int k = 0; k < nff; ++k) {
+            const FFace g = ff[f0 + k];
+            sum = __dadd_rn(sum, line_flux<S, R>(base + g.f_low + c * g.cstride, g.dstride));
+        }
+        const double v = __dmul_rn(w.w[c], sum);
+        reg[i] = first ? v : __dadd_rn(reg[i], v);
+    }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256) k_reflux_apply(S *base, const CCell *__restrict__ cells, int ncell,
+                                                      const CFace *__restrict__ faces, int ncomp,
+                                                      const double *__restrict__ regc, const double *__restrict__ regf) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell * ncomp; i += gridDim.x * blockDim.x) {
+        const int j = i / ncomp, c = i - j * ncomp;
+        const CCell cl = cells[j];
+        double corr = 0.0;
+        for (int e = cl.efirst; e < cl.efirst + cl.ecount; ++e) {
+            const double d = __dsub_rn(regf[(long long)e * ncomp + c], regc[(long long)e * ncomp + c]);
+            corr = __dadd_rn(corr, faces[e].sc > 0 ? d : -d);
+        }
+        S *p = base + cl.c_elem + c * cl.cstride;
+        from_f64(p, __dadd_rn(to_f64(*p), corr));
+    }
+}
+
+static int blocks_for(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 65535)); }
+
+template <typename S>
+static cudaError_t cf_coarse_s(int R, const void *base, const CFace *faces, int n, int ncomp, const RefluxW &w,
+                               double *reg, cudaStream_t s) {
+    const int g = blocks_for((long long)n * ncomp);
+    switch (R) {
+        case 1: k_cf_coarse_flux<S, 1><<<g, 256, 0, s>>>((const S *)base, faces, n, ncomp, w, reg); break;
+        case 2: k_cf_coarse_flux<S, 2><<<g, 256, 0, s>>>((const S *)base, faces, n, ncomp, w, reg); break;
+        case 4: k_cf_coarse_flux<S, 4><<<g, 256, 0, s>>>((const S *)base, faces, n, ncomp, w, reg); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename S>
+static cudaError_t cf_fine_s(int R, const void *base, const CFace *faces, const FFace *ff, int n, int nff, int ncomp,
+                             const RefluxW &w, double *reg, bool first, cudaStream_t s) {
+    const int g = blocks_for((long long)n * ncomp);
+    switch (R) {
+        case 1: k_cf_fine_flux<S, 1><<<g, 256, 0, s>>>((const S *)base, faces, ff, n, nff, ncomp, w, reg, first); break;
+        case 2: k_cf_fine_flux<S, 2><<<g, 256, 0, s>>>((const S *)base, faces, ff, n, nff, ncomp, w, reg, first); break;
+        case 4: k_cf_fine_flux<S, 4><<<g, 256, 0, s>>>((const S *)base, faces, ff, n, nff, ncomp, w, reg, first); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cf_coarse_flux(int dtype, int R, const void *base, const CFace *faces, int n, int ncomp,
+                                  const RefluxW &w, double *reg, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    switch (dtype) {
+        case F64: return cf_coarse_s<double>(R, base, faces, n, ncomp, w, reg, s);
+        case F32: return cf_coarse_s<float>(R, base, faces, n, ncomp, w, reg, s);
+        case BF16: return cf_coarse_s<__nv_bfloat16>(R, base, faces, n, ncomp, w, reg, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_cf_fine_flux(int dtype, int R, const void *base, const CFace *faces, const FFace *ff, int n,
+                                int nff, int ncomp, const RefluxW &w, double *reg, bool first, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    switch (dtype) {
+        case F64: return cf_fine_s<double>(R, base, faces, ff, n, nff, ncomp, w, reg, first, s);
+        case F32: return cf_fine_s<float>(R, base, faces, ff, n, nff, ncomp, w, reg, first, s);
+        case BF16: return cf_fine_s<__nv_bfloat16>(R, base, faces, ff, n, nff, ncomp, w, reg, first, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_reflux_apply(int dtype, void *base, const CCell *cells, int ncell, const CFace *faces, int ncomp,
+                                const double *regc, const double *regf, cudaStream_t s) {
+    if (ncell == 0) return cudaSuccess;
+    const int g = blocks_for((long long)ncell * ncomp);
+    switch (dtype) {
+        case F64: k_reflux_apply<<<g, 256, 0, s>>>((double *)base, cells, ncell, faces, ncomp, regc, regf); break;
+        case F32: k_reflux_apply<<<g, 256, 0, s>>>((float *)base, cells, ncell, faces, ncomp, regc, regf); break;
+        case BF16: k_reflux_apply<<<g, 256, 0, s>>>((__nv_bfloat16 *)base, cells, ncell, faces, ncomp, regc, regf); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
 
 // Whole-level reductions of one component (Sec. 3.1: the MultiFab's sum, max and norms).  The
 // valid rows of all FArrayBoxes form one list (rowpre[b] = first row of box b); warp w of the

@@ -219,3 +219,52 @@ def test_rk3_8th256_full_size_matches_the_stability_polynomial(dtype):
     tol = FP64_TOL if dtype == "f64" else f32_tol(3 * n, R)
     print("MEASURED rk3_8th256 %s rel_err %.3e (bound %.1e) schedule %s" % (dtype, err, tol, mf.mf_get_schedule(g.h)))
     assert err <= tol
+
+
+def test_amr2lev256_reflux_full_size_matches_oracle_and_conserves():
+    """The two-level workload with refluxing (Berger-Colella): FP64 against the oracle over two
+    coarse steps, and the composite sum (fine cells plus 8 x the uncovered coarse cells)
+    conserved -- FP64 to rounding, FP32 to its own bound."""
+    cfg = synth.WORKLOADS["c4"]
+    Nc, r, nsub = cfg["N"], cfg["ratio"], cfg["nsub"]
+    steps = 2
+    fboxes = synth.sphere_fine_boxes(Nc, ratio=r)
+    cboxes = oracle.chop([0, 0, 0], [Nc - 1] * 3, cfg["max_grid_size"])
+    cden = synth.initial_field(cfg)
+    fden = synth.initial_field(cfg, N=r * Nc)
+    dt = synth.dt_for(cfg)
+    CL = oracle.Level(cboxes, [0, 0, 0], [Nc - 1] * 3, 1, 1)
+    FL = oracle.Level(fboxes, [0, 0, 0], [r * Nc - 1] * 3, 1, 1)
+    cd0, fd0 = CL.from_dense(cden), FL.from_dense(fden)
+    oracle.average_down(FL, CL, r, fd0, cd0)  # a consistent start: covered coarse = mean of fine
+    cden = CL.to_dense(cd0)
+    c_ref, f_ref = oracle.amr_advance(CL, FL, 1, dt * Nc * Nc, cd0, fd0, steps, nsub=nsub, ratio=r,
+                                      reflux_faces=True)
+    c_ref, f_ref = CL.to_dense(c_ref), FL.to_dense(f_ref)
+    covered = np.zeros((Nc, Nc, Nc), dtype=bool)
+    for b in fboxes:
+        covered[b[2] // r:b[5] // r + 1, b[1] // r:b[4] // r + 1, b[0] // r:b[3] // r + 1] = True
+
+    def composite(cd, fd):
+        vals = np.concatenate([r ** 3 * cd[0][~covered], fd[0][~np.isnan(fd[0])]])
+        return math.fsum(vals.tolist()), math.fsum(np.abs(vals).tolist())
+
+    s0, a0 = composite(cden, np.where(np.isnan(f_ref), np.nan, fden))
+    for dtype in ("f64", "f32"):
+        gc = level([0, 0, 0], [Nc - 1] * 3, dtype, boxes=cboxes, ngrow=1)
+        gf = level([0, 0, 0], [r * Nc - 1] * 3, dtype, boxes=fboxes, ngrow=1)
+        gc.from_host(cden)
+        gf.from_host(fden)
+        mf.mf_amr_advance(gc.h, gf.h, 1, [1.0], dt, steps, nsub, r, mf.MF_REFLUX)
+        co, fo = gc.to_host(), gf.to_host()
+        s1, _ = composite(co, fo)
+        drift = abs(s1 - s0) / a0
+        if dtype == "f64":
+            ec, ef = rel_err(co, c_ref), rel_err(fo, f_ref)
+            print("MEASURED amr2lev256 reflux f64 coarse %.3e fine %.3e composite drift %.3e" % (ec, ef, drift))
+            assert ec <= FP64_TOL and ef <= FP64_TOL
+            assert drift <= steps * (1 + nsub) * 1e-15
+        else:
+            print("MEASURED amr2lev256 reflux f32 composite drift %.3e" % drift)
+            assert drift <= steps * (1 + nsub) * 1e-7
+        del gc, gf

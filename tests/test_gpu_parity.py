@@ -550,3 +550,64 @@ def test_rk3_without_a_stage_level_is_rejected():
     with pytest.raises(mf.MFError) as e:
         mf.mf_rk3_advance(g.h, 1, [1.0], 0.1 / 256, 1)
     assert e.value.code == mf.MF_ESTATE
+
+
+# --------------------------------------------------------------------------- refluxing
+
+REFLUX_FINE = np.array([[8, 8, 4, 15, 23, 19], [16, 8, 4, 23, 15, 11], [0, 24, 26, 5, 31, 31],
+                        [26, 24, 26, 31, 31, 31]], dtype=np.int32)
+
+
+def _composite(cd, fd, fboxes, r=2):
+    covered = np.zeros(cd.shape[1:], dtype=bool)
+    for b in fboxes:
+        covered[b[2] // r:b[5] // r + 1, b[1] // r:b[4] // r + 1, b[0] // r:b[3] // r + 1] = True
+    out = []
+    for c in range(cd.shape[0]):
+        vals = (r ** 3 * cd[c][~covered]).tolist() + fd[c][~np.isnan(fd[c])].tolist()
+        out.append((math.fsum(vals), math.fsum(np.abs(vals).tolist())))
+    return out
+
+
+@pytest.mark.parametrize("R", [1, 2])
+def test_amr_reflux_fp64_matches_oracle_and_conserves(R):
+    Nc, C = 16, 2
+    clo, chi, flo, fhi = [0, 0, 0], [Nc - 1] * 3, [0, 0, 0], [2 * Nc - 1] * 3
+    cboxes = oracle.chop(clo, chi, 8)
+    rng = np.random.default_rng(80 + R)
+    fden = rng.standard_normal((C, 2 * Nc, 2 * Nc, 2 * Nc))
+    CL = oracle.Level(cboxes, clo, chi, R, C)
+    FL = oracle.Level(REFLUX_FINE, flo, fhi, R, C)
+    fd0 = FL.from_dense(fden)
+    cd0 = CL.from_dense(rng.standard_normal((C, Nc, Nc, Nc)))
+    oracle.average_down(FL, CL, 2, fd0, cd0)
+    cden, fden = CL.to_dense(cd0), FL.to_dense(fd0)
+    fden = np.where(np.isnan(fden), 0.0, fden)
+    lam_c = {1: 0.075, 2: 0.05}[R]
+    dt = lam_c / (Nc * Nc)
+    gc = gpu_level(clo, chi, boxes=cboxes, ncomp=C, ngrow=R)
+    gf = gpu_level(flo, fhi, boxes=REFLUX_FINE, ncomp=C, ngrow=R)
+    gc.from_host(cden)
+    gf.from_host(fden)
+    mf.mf_amr_advance(gc.h, gf.h, R, [1.0, 1.0], dt, 3, 2, 2, mf.MF_REFLUX)
+    c_ref, f_ref = oracle.amr_advance(CL, FL, R, lam_c, CL.from_dense(cden), FL.from_dense(fden), 3,
+                                      reflux_faces=True)
+    co, fo = gc.to_host(), gf.to_host()
+    cr, fr = CL.to_dense(c_ref), FL.to_dense(f_ref)
+    assert rel_err(co, cr) <= FP64_TOL
+    m = ~np.isnan(fr)
+    assert float(np.max(np.abs(fo[m] - fr[m])) / np.max(np.abs(fr[m]))) <= FP64_TOL
+    before = _composite(cden, np.where(m, fden, np.nan), REFLUX_FINE)
+    after = _composite(co, np.where(m, fo, np.nan), REFLUX_FINE)
+    for (s0, a0), (s1, _) in zip(before, after):
+        assert abs(s1 - s0) <= 3 * 2 * 1e-15 * a0
+    n = mf.mf_launch_count(gc.h)
+    # per coarse step: 2 interpolations + 2 fine and 1 coarse register launches; average-down + reflux
+    assert n["interp"] == 3 * 5 and n["avgdown"] == 3 * 2
+
+
+def test_reflux_flag_is_rejected_by_single_level_advances():
+    g = gpu_level([0, 0, 0], [15, 15, 15], mgs=8, ngrow=1)
+    with pytest.raises(mf.MFError) as e:
+        mf.mf_advance(g.h, 1, [1.0], 0.1 / 256, 1, mf.MF_REFLUX)
+    assert e.value.code == mf.MF_EINVAL
