@@ -47,7 +47,7 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="headline only (no FP64, e2e, CPU baseline)")
     p.add_argument("--tile", default=None, help="fixed tile 'x,y,z' instead of the autotuner (0 = whole box)")
     p.add_argument("--kernel", default="tma", choices=["tma", "global"], help="stencil kernel variant")
-    p.add_argument("--only", default=None, choices=["rk3_8th"],
+    p.add_argument("--only", default=None, choices=["rk3_8th", "amr2lev_reflux"],
                    help="run only this secondary line (for profiling) and print it")
     p.add_argument("--schedule", default=None,
                    help="fixed schedule 'x,y,z,rows,stages,group_bytes' instead of the autotuner")
@@ -303,6 +303,45 @@ def rk3_line(mf, torch, flush, args, hbm):
             "schedule": mf.mf_get_schedule(m.h)}
 
 
+def amr_line(mf, torch, flush, args):
+    """The two-level workload with refluxing: coarse 256^3 in 64 boxes of 64^3, a fine level at
+    ratio 2 on the seeded sphere boxes, 2 fine substeps per coarse step, FP32, 50 coarse steps
+    per bench step; cells counted once per coarse step on the coarse level and once per
+    substep on the fine level."""
+    cfg = synth.WORKLOADS["c4"]
+    Nc, r, nsub, n = cfg["N"], cfg["ratio"], cfg["nsub"], cfg["nsteps"]
+    fboxes = synth.sphere_fine_boxes(Nc, ratio=r)
+    modes = synth.sine_modes(synth.FIELD_SEED, 100, cfg["nmodes"], cfg["kmax"])
+    lo = fboxes[:, :3].min(axis=0)
+    hi = fboxes[:, 3:].max(axis=0)
+    fden = np.zeros((1, r * Nc, r * Nc, r * Nc))
+    fden[0, lo[2]:hi[2] + 1, lo[1]:hi[1] + 1, lo[0]:hi[0] + 1] = synth.eval_modes_box(
+        r * Nc, lo, tuple(int(v) for v in (hi - lo + 1)[::-1]), modes)
+    gc = mf.MultiFab([0, 0, 0], [Nc - 1] * 3, max_grid_size=cfg["max_grid_size"], ngrow=1, dtype="f32")
+    gf = mf.MultiFab([0, 0, 0], [r * Nc - 1] * 3, boxes=fboxes, ngrow=1, dtype="f32")
+    gc.from_host(synth.initial_field(cfg))
+    gf.from_host(fden)
+    mf.mf_average_down(gf.h, gc.h, r)
+    dt = synth.dt_for(cfg)
+    for _ in range(2):
+        mf.mf_amr_advance(gc.h, gf.h, 1, [1.0], dt, n, nsub, r, mf.MF_REFLUX)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush()
+        ev[k][0].record(gc.stream)
+        mf.mf_amr_advance(gc.h, gf.h, 1, [1.0], dt, n, nsub, r, mf.MF_REFLUX)
+        ev[k][1].record(gc.stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    Vc = Nc ** 3
+    Vf = int(((fboxes[:, 3:] - fboxes[:, :3] + 1).prod(axis=1)).sum())
+    return {"value": (Vc + nsub * Vf) * n / (ms * 1e-3), "unit": "cell-updates/s (coarse per step + fine per substep)",
+            "ms_per_bench_step": ms,
+            "workload": "amr2lev256_sphere: coarse 256^3 (64 boxes of 64^3) + %d fine boxes (%d cells) at ratio 2, "
+                        "2 substeps, refluxing, FP32, %d coarse steps per bench step" % (len(fboxes), Vf, n),
+            "launches_per_bench_step": mf.mf_launch_count(gc.h)}
+
+
 def run_ours(args, cfg, ws, rank, local):
     import torch
     import paper_1604_03570_gb300 as mf
@@ -498,6 +537,7 @@ def run_ours(args, cfg, ws, rank, local):
         out["fp64_plain_per_box"] = {"value": vplain, "unit": UNIT,
                                      "launches_per_time_step": 2 * nbox}
         out["rk3_8th"] = rk3_line(mf, torch, flush, args, hbm)
+        out["amr2lev_reflux"] = amr_line(mf, torch, flush, args)
         out["speedup_batched_vs_fp64_plain_per_box"] = value / vplain
         if rank == 0 and ws == 1:
             out["cpu_baseline"] = cpu_baseline(cfg)
@@ -517,7 +557,7 @@ def main():
             return 0
         print(json.dumps(run_reference(args, cfg)))
         return 0
-    if args.only == "rk3_8th":
+    if args.only:
         import torch
         import paper_1604_03570_gb300 as mf
         torch.cuda.set_device(local)
@@ -529,7 +569,9 @@ def main():
             flush_rd.max()
 
         peaks, _ = measured_peaks()
-        print(json.dumps({"rk3_8th": rk3_line(mf, torch, flush, args, float(peaks["hbm_gbs"]))}))
+        line = rk3_line(mf, torch, flush, args, float(peaks["hbm_gbs"])) if args.only == "rk3_8th" \
+            else amr_line(mf, torch, flush, args)
+        print(json.dumps({args.only: line}))
         return 0
     out = run_ours(args, cfg, ws, rank, local)
     if out is not None:

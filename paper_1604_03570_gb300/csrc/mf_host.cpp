@@ -179,10 +179,33 @@ struct GraphExec {
 
 // ------------------------------------------------------------------ the handle
 
+// A work list numbered cell by cell: segment q (a run or a region) holds cells
+// [start[q], start[q+1]); wfirst[w] is the segment holding cell 32 w.
+struct CellList {
+    std::vector<int> start, wfirst;
+    int ncells = 0;
+    DevBuf d_start, d_wfirst;
+    void finish() {
+        ncells = start.back();
+        wfirst.assign((size_t)((ncells + 31) / 32), 0);
+        size_t q = 0;
+        for (size_t w = 0; w < wfirst.size(); ++w) {
+            const int c = (int)(w * 32);
+            while (start[q + 1] <= c) ++q;
+            wfirst[w] = (int)q;
+        }
+    }
+    int upload(cudaStream_t s) {
+        int rc = d_start.upload(start, s);
+        return rc ? rc : d_wfirst.upload(wfirst, s);
+    }
+};
+
 struct InterpPlan {
     const mf_t *crse = nullptr;
     int ratio = 0;
     std::vector<InterpRun> runs;
+    CellList cells;
     DevBuf d_runs;
 };
 
@@ -199,7 +222,9 @@ struct RefluxPlan {
 struct AvgPlan {
     const mf_t *fine = nullptr;
     int ratio = 0;
+    bool vec = true;  // every fine offset and pitch a multiple of ratio: vector loads of children
     std::vector<AvgRegion> regs;
+    CellList cells;
     DevBuf d_regs;
 };
 
@@ -1863,57 +1888,76 @@ static int build_interp(mf_t *fine, const mf_t *crse, int ratio, InterpPlan &pla
         return -1;
     };
     plan.runs.clear();
+    plan.cells.start.assign(1, 0);
+    long long ncells = 0;
     for (int b = 0; b < (int)fine->boxes.size(); ++b) {
         const Box &B = fine->boxes[b];
         const Box gb = grow(B, g);
         const long long nx = gb.len(0), ny = gb.len(1), nz = gb.len(2);
-        std::vector<char> covered((size_t)(nx * ny * nz), 0);
+        // todo: ghost cells that neither the box nor a fine-fine fill covers, not yet in a run
+        std::vector<char> todo((size_t)(nx * ny * nz), 1);
+        auto at = [&](int i, int j, int k) -> char & {
+            return todo[(size_t)(((k - gb.lo[2]) * ny + (j - gb.lo[1])) * nx + (i - gb.lo[0]))];
+        };
         for (int k = B.lo[2]; k <= B.hi[2]; ++k)
             for (int j = B.lo[1]; j <= B.hi[1]; ++j)
-                for (int i = B.lo[0]; i <= B.hi[0]; ++i)
-                    covered[((k - gb.lo[2]) * ny + (j - gb.lo[1])) * nx + (i - gb.lo[0])] = 1;
+                for (int i = B.lo[0]; i <= B.hi[0]; ++i) at(i, j, k) = 0;
         const FabInfo &ff = fine->fabs[b];
         for (int e = fine->fb_group[b]; e < fine->fb_group[b + 1]; ++e) {
             const FbEntry &en = fine->fb[e];
-            const int c0 = fine->fb_corner[e][0] - B.lo[0], c1 = fine->fb_corner[e][1] - B.lo[1],
-                      c2 = fine->fb_corner[e][2] - B.lo[2];
+            const int *c = fine->fb_corner[e].data();
             for (int z = 0; z < en.n[2]; ++z)
                 for (int y = 0; y < en.n[1]; ++y)
-                    for (int x = 0; x < en.n[0]; ++x)
-                        covered[((c2 + z + g) * ny + (c1 + y + g)) * nx + (c0 + x + g)] = 1;
+                    for (int x = 0; x < en.n[0]; ++x) at(c[0] + x, c[1] + y, c[2] + z) = 0;
         }
         for (int k = gb.lo[2]; k <= gb.hi[2]; ++k)
-            for (int j = gb.lo[1]; j <= gb.hi[1]; ++j) {
-                int i = gb.lo[0];
-                while (i <= gb.hi[0]) {
-                    if (covered[((k - gb.lo[2]) * ny + (j - gb.lo[1])) * nx + (i - gb.lo[0])]) { ++i; continue; }
-                    // start a run: coarse owner and periodic shift of floor(I/r) per direction
-                    const int kj = floor_div(j, ratio), kk = floor_div(k, ratio);
-                    const int wj = wrap_idx(kj, crse->domain.lo[1], crse->domain.len(1));
-                    const int wk = wrap_idx(kk, crse->domain.lo[2], crse->domain.len(2));
-                    const int ki = floor_div(i, ratio);
-                    const int wi = wrap_idx(ki, crse->domain.lo[0], crse->domain.len(0));
-                    const int a = crse_owner(wi, wj, wk);
-                    if (a < 0) return fail(MF_EINVAL, "coarse level does not cover its domain");
-                    InterpRun run{};
-                    run.ffab = b;
-                    run.cfab = a;
-                    run.I = i; run.J = j; run.K = k;
-                    run.shift[0] = ki - wi; run.shift[1] = kj - wj; run.shift[2] = kk - wk;
-                    run.fdst = elem_at(ff, i, j, k);
-                    int len = 0;
-                    while (i <= gb.hi[0] && !covered[((k - gb.lo[2]) * ny + (j - gb.lo[1])) * nx + (i - gb.lo[0])]) {
-                        const int kx = floor_div(i, ratio);
-                        const int wx = wrap_idx(kx, crse->domain.lo[0], crse->domain.len(0));
-                        if (kx - wx != run.shift[0] || !crse->boxes[a].contains(wx, wj, wk)) break;
-                        ++len;
-                        ++i;
+            for (int j = gb.lo[1]; j <= gb.hi[1]; ++j)
+                for (int i = gb.lo[0]; i <= gb.hi[0]; ++i) {
+                    if (!at(i, j, k)) continue;
+                    // a run along the direction the ghost slab extends in: x where the cell lies
+                    // within the box's x range, else y, else z (corner cells: x)
+                    const int p0[3] = {i, j, k};
+                    bool in[3];
+                    for (int d = 0; d < 3; ++d) in[d] = B.lo[d] <= p0[d] && p0[d] <= B.hi[d];
+                    const int axis = in[0] ? 0 : in[1] ? 1 : in[2] ? 2 : 0;
+                    // coarse owner and periodic shift of the cell floor(i/r)
+                    int kc[3], wc[3];
+                    for (int d = 0; d < 3; ++d) {
+                        kc[d] = floor_div(p0[d], ratio);
+                        wc[d] = wrap_idx(kc[d], crse->domain.lo[d], crse->domain.len(d));
                     }
-                    run.len = len;
+                    const int a = crse_owner(wc[0], wc[1], wc[2]);
+                    if (a < 0) return fail(MF_EINVAL, "coarse level does not cover its domain");
+                    const FabInfo &cf = crse->fabs[a];
+                    InterpRun run{};
+                    run.I = i; run.J = j; run.K = k;
+                    run.axis = axis;
+                    run.fdst = elem_at(ff, i, j, k);
+                    run.fstep = axis == 0 ? 1 : axis == 1 ? ff.px : (int)ff.plane;
+                    run.fcs = (int)ff.cstride;
+                    run.ccs = (int)cf.cstride;
+                    run.cpx = cf.px;
+                    run.cplane = (int)cf.plane;
+                    run.cbase = cf.org - (long long)(kc[2] - wc[2] + cf.lo[2]) * cf.plane -
+                                (long long)(kc[1] - wc[1] + cf.lo[1]) * cf.px - (kc[0] - wc[0] + cf.lo[0]);
+                    int p[3] = {i, j, k}, len = 0;
+                    while (p[axis] <= gb.hi[axis] && at(p[0], p[1], p[2])) {
+                        const int kq = floor_div(p[axis], ratio);
+                        const int wq = wrap_idx(kq, crse->domain.lo[axis], crse->domain.len(axis));
+                        int w3[3] = {wc[0], wc[1], wc[2]};
+                        w3[axis] = wq;
+                        if (kq - wq != kc[axis] - wc[axis] || !crse->boxes[a].contains(w3[0], w3[1], w3[2])) break;
+                        at(p[0], p[1], p[2]) = 0;
+                        ++len;
+                        ++p[axis];
+                    }
+                    ncells += len;
+                    if (ncells > INT32_MAX - 64) return fail(MF_EINVAL, "too many ghost cells to interpolate");
                     plan.runs.push_back(run);
+                    plan.cells.start.push_back((int)ncells);
                 }
-            }
     }
+    plan.cells.finish();
     return 0;
 }
 
@@ -1925,6 +1969,7 @@ static InterpPlan *get_interp(mf_t *fine, const mf_t *crse, int ratio, int *rc) 
     p->ratio = ratio;
     if ((*rc = build_interp(fine, crse, ratio, *p))) return nullptr;
     if ((*rc = p->d_runs.upload(p->runs, fine->stream))) return nullptr;
+    if ((*rc = p->cells.upload(fine->stream))) return nullptr;
     if (cudaStreamSynchronize(fine->stream) != cudaSuccess) { *rc = fail(MF_ECUDA, "sync"); return nullptr; }
     fine->interp.push_back(std::move(p));
     return fine->interp.back().get();
@@ -1941,6 +1986,9 @@ static int build_avg(const mf_t *fine, mf_t *crse, int ratio, AvgPlan &plan) {
     std::vector<int> cand, stamp(crse->boxes.size(), -1);
     int tag = 0;
     plan.regs.clear();
+    plan.cells.start.assign(1, 0);
+    plan.vec = true;
+    long long ncells = 0;
     for (int f = 0; f < (int)fine->boxes.size(); ++f) {
         const Box &B = fine->boxes[f];
         for (int d = 0; d < 3; ++d)
@@ -1952,13 +2000,27 @@ static int build_avg(const mf_t *fine, mf_t *crse, int ratio, AvgPlan &plan) {
         for (int a : cand) {
             const Box r = intersect(cb, crse->boxes[a]);
             if (r.empty()) continue;
+            const FabInfo &ff = fine->fabs[f], &cf = crse->fabs[a];
             AvgRegion g{};
-            g.cfab = a;
-            g.ffab = f;
-            for (int d = 0; d < 3; ++d) { g.clo[d] = r.lo[d]; g.n[d] = r.len(d); }
+            g.fsrc = elem_at(ff, r.lo[0] * ratio, r.lo[1] * ratio, r.lo[2] * ratio);
+            g.cdst = elem_at(cf, r.lo[0], r.lo[1], r.lo[2]);
+            g.fpx = ff.px;
+            g.fplane = (int)ff.plane;
+            g.fcs = (int)ff.cstride;
+            g.cpx = cf.px;
+            g.cplane = (int)cf.plane;
+            g.ccs = (int)cf.cstride;
+            for (int d = 0; d < 3; ++d) g.n[d] = r.len(d);
+            if (g.fsrc % ratio || g.fpx % ratio || g.fplane % ratio || g.fcs % ratio) plan.vec = false;
+            ncells += (long long)g.n[0] * g.n[1] * g.n[2];
+            if (ncells > INT32_MAX - 64) return fail(MF_EINVAL, "too many coarse cells to average down");
             plan.regs.push_back(g);
+            plan.cells.start.push_back((int)ncells);
         }
     }
+    // the level allocation is 256-byte aligned: offsets that are multiples of ratio elements
+    // give vector loads aligned to their size
+    plan.cells.finish();
     return 0;
 }
 
@@ -1970,6 +2032,7 @@ static AvgPlan *get_avg(const mf_t *fine, mf_t *crse, int ratio, int *rc) {
     p->ratio = ratio;
     if ((*rc = build_avg(fine, crse, ratio, *p))) return nullptr;
     if ((*rc = p->d_regs.upload(p->regs, crse->stream))) return nullptr;
+    if ((*rc = p->cells.upload(crse->stream))) return nullptr;
     if (cudaStreamSynchronize(crse->stream) != cudaSuccess) { *rc = fail(MF_ECUDA, "sync"); return nullptr; }
     crse->avg.push_back(std::move(p));
     return crse->avg.back().get();
@@ -1977,17 +2040,18 @@ static AvgPlan *get_avg(const mf_t *fine, mf_t *crse, int ratio, int *rc) {
 
 static int enqueue_interp(mf_t *fine, int fwhich, const mf_t *cold, int cold_which, const mf_t *cnew, int cnew_which,
                           InterpPlan *plan, int ratio, double alpha, cudaStream_t s) {
-    CU(launch_interp(fine->dtype, fine->level_ptr(fwhich), (const FabInfo *)fine->d_fabs.p,
-                     cold->level_ptr(cold_which), cnew->level_ptr(cnew_which), (const FabInfo *)cold->d_fabs.p,
-                     (const InterpRun *)plan->d_runs.p, (int)plan->runs.size(), fine->ncomp, ratio, alpha, s));
+    CU(launch_interp(fine->dtype, fine->level_ptr(fwhich), cold->level_ptr(cold_which), cnew->level_ptr(cnew_which),
+                     (const InterpRun *)plan->d_runs.p, (const int *)plan->cells.d_start.p,
+                     (const int *)plan->cells.d_wfirst.p, (int)plan->runs.size(), plan->cells.ncells, fine->ncomp,
+                     ratio, alpha, s));
     return 0;
 }
 
 static int enqueue_avg(const mf_t *fine, int fwhich, mf_t *crse, int cwhich, AvgPlan *plan, int ratio,
                        cudaStream_t s) {
-    CU(launch_avgdown(fine->dtype, fine->level_ptr(fwhich), (const FabInfo *)fine->d_fabs.p, crse->level_ptr(cwhich),
-                      (const FabInfo *)crse->d_fabs.p, (const AvgRegion *)plan->d_regs.p, (int)plan->regs.size(),
-                      fine->ncomp, ratio, s));
+    CU(launch_avgdown(fine->dtype, fine->level_ptr(fwhich), crse->level_ptr(cwhich), (const AvgRegion *)plan->d_regs.p,
+                      (const int *)plan->cells.d_start.p, (const int *)plan->cells.d_wfirst.p, (int)plan->regs.size(),
+                      plan->cells.ncells, fine->ncomp, ratio, plan->vec, s));
     return 0;
 }
 

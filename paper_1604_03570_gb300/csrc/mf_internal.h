@@ -74,21 +74,32 @@ struct Tile {
     short tx, ty, tz;   // tile extents
 };
 
-// Coarse-fine interpolation: a run of fine ghost cells along x, all with the same coarse box.
+// Coarse-fine interpolation (Sec. 2.3, mf_interp_cf): a run of fine ghost cells along one
+// direction whose coarse cells floor(i/r) lie in one coarse box under one periodic shift.  The
+// cells of all runs are numbered in one sequence; run q holds cells [rstart[q], rstart[q+1]).
 struct InterpRun {
-    long long fdst;     // element offset of the first fine cell (comp 0)
-    int ffab;           // fine FArrayBox
-    int cfab;           // coarse FArrayBox containing floor(i_f / r) of every cell of the run
+    long long fdst;     // fine element offset of the first cell (comp 0) within a time level
+    long long cbase;    // element offset, in the owning coarse FAB, of global coarse index (0,0,0)
+                        // after the run's periodic shift (may lie outside the FAB; only
+                        // cbase + the offsets of the cells read are inside)
     int I, J, K;        // global fine index of the first cell
-    int len;
-    int shift[3];       // coarse index shift: coarse_local = floor-part - shift (periodic image)
+    int axis;           // direction the run advances in: 0 x, 1 y, 2 z
+    int fstep;          // fine element stride along axis
+    int fcs, ccs;       // component strides of the fine and coarse FABs (elements)
+    int cpx, cplane;    // coarse row and plane pitch (elements; a FAB holds < 2^31 elements)
 };
 
-// Average-down region: coarse valid cells [clo, clo + n) of coarse box cfab from fine box ffab.
+// Average-down region (Sec. 2.3): coarse valid cells [clo, clo + n) of one coarse FAB from one
+// fine FAB, with every offset and stride the kernel needs.  The cells of all regions are
+// numbered in one sequence, x fastest; region q holds cells [rstart[q], rstart[q+1]).
 struct AvgRegion {
-    int cfab, ffab;
-    int clo[3];         // global coarse index
+    long long fsrc;     // fine element offset of the first child of coarse cell clo (comp 0)
+    long long cdst;     // coarse element offset of cell clo (comp 0)
+    int fpx, fplane;    // fine row and plane pitch
+    int cpx, cplane;    // coarse row and plane pitch
+    int fcs, ccs;       // component strides
     int n[3];
+    int pad_;
 };
 
 struct LevelPtrs {
@@ -229,11 +240,14 @@ cudaError_t launch_scatter_dense(int dtype, void *base, const FabInfo *ftab, int
 cudaError_t launch_gather_dense(int dtype, const void *base, const FabInfo *ftab, int nfab, double *stage,
                                 const int dlo[3], const int dn[3], int z0, int z1, int comp, int ncomp_chunk,
                                 cudaStream_t s);
-cudaError_t launch_interp(int dtype, void *fbase, const FabInfo *ffabs, const void *cold, const void *cnew,
-                          const FabInfo *cfabs, const InterpRun *runs, int nruns, int ncomp, int ratio, double alpha,
-                          cudaStream_t s);
-cudaError_t launch_avgdown(int dtype, const void *fbase, const FabInfo *ffabs, void *cbase, const FabInfo *cfabs,
-                           const AvgRegion *regs, int nregs, int ncomp, int ratio, cudaStream_t s);
+// runs/rstart (nruns + 1 entries, rstart[nruns] = ncells)/wfirst (the run holding cell 32 w,
+// one entry per 32 cells): the interpolation work list.
+cudaError_t launch_interp(int dtype, void *fbase, const void *cold, const void *cnew, const InterpRun *runs,
+                          const int *rstart, const int *wfirst, int nruns, int ncells, int ncomp, int ratio,
+                          double alpha, cudaStream_t s);
+// vec: every region's fine offsets and pitches are multiples of ratio (vector loads of r children)
+cudaError_t launch_avgdown(int dtype, const void *fbase, void *cbase, const AvgRegion *regs, const int *rstart,
+                           const int *wfirst, int nregs, int ncells, int ncomp, int ratio, bool vec, cudaStream_t s);
 
 int sm_count();
 

@@ -22,6 +22,8 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
+#include <type_traits>
 
 #include "mf_internal.h"
 #include "stencil_common.cuh"
@@ -452,86 +454,149 @@ __global__ void k_dense(S *base, const FabInfo *__restrict__ ftab, double *stage
 
 // ------------------------------------------------------------------ AMR
 
+template <typename A, typename S> __device__ __forceinline__ A to_arith(S v) {
+    if constexpr (std::is_same<S, __nv_bfloat16>::value) return (A)__bfloat162float(v);
+    else return (A)v;
+}
+
+// Cells numbered 0..ncells-1 form consecutive non-empty segments (runs, regions); segment q
+// holds [start[q], start[q+1]) and start[nseg] = ncells.  first is the segment holding cell
+// c0 = 32 w.  For the calling lane's cell c0 + lane this returns its segment and its offset in
+// it, with one coalesced load and one warp reduction: the lanes mark, in a 32-bit mask, the
+// window positions where a segment starts; a lane's segment is first plus the number of marks
+// at or below it, less one.  Whole-warp call.
+__device__ __forceinline__ void warp_segment(const int *__restrict__ start, int first, int nseg, int ncells, int c0,
+                                             int &seg, int &off) {
+    const int lane = threadIdx.x & 31;
+    const int s = first + lane <= nseg ? __ldg(start + first + lane) : ncells;
+    const unsigned bit = lane == 0 ? 1u : (s - c0 < 32 ? 1u << (s - c0) : 0u);
+    const unsigned m = __reduce_or_sync(0xffffffffu, bit);
+    const unsigned le = m & (0xffffffffu >> (31 - lane));
+    const int k = __popc(le) - 1;
+    const int s0 = __shfl_sync(0xffffffffu, s, 0);
+    seg = first + k;
+    off = k == 0 ? c0 + lane - s0 : lane - (31 - __clz(le));
+}
+
 // Linear-interpolation stencil of fine index i at ratio r: coarse k0 and weight of k0+1
-// from the cell-centre position x = (2i + 1 - r) / (2r) in coarse index units.
-__device__ __forceinline__ void lin_w(int i, int r, int &k0, double &w1) {
+// from the cell-centre position x = (2i + 1 - r) / (2r) in coarse index units.  The weight
+// is a multiple of 1/(2r), exact in FP32 and FP64.
+template <typename A>
+__device__ __forceinline__ void lin_w(int i, int r, int &k0, A &w1) {
     const int num = 2 * i + 1 - r, den = 2 * r;
     int q = num / den;
     if (num % den != 0 && num < 0) --q;
     k0 = q;
-    w1 = (double)(num - den * q) / (double)den;
+    w1 = (A)(num - den * q) / (A)den;
 }
 
+// Coarse-to-fine ghost interpolation (Sec. 2.3): one thread per fine ghost cell of the work
+// list, trilinear in space and linear in time, (1 - alpha) cold + alpha cnew at each of the 8
+// coarse points, accumulated z, y, x ascending with the weight product (wz wy) wx -- the
+// arithmetic of the storage type's native precision (FP64 for FP64, FP32 otherwise).
 template <typename S>
-__global__ void __launch_bounds__(128) k_interp(S *fbase, const FabInfo *__restrict__ ffabs, const S *cold,
-                                                const S *cnew, const FabInfo *__restrict__ cfabs,
-                                                const InterpRun *__restrict__ runs, int nruns, int ncomp, int ratio,
-                                                double alpha) {
+__global__ void __launch_bounds__(256) k_interp(S *__restrict__ fbase, const S *__restrict__ cold,
+                                                const S *__restrict__ cnew, const InterpRun *__restrict__ runs,
+                                                const int *__restrict__ rstart, const int *__restrict__ wfirst,
+                                                int nruns, int ncells, int ncomp, int ratio, double alpha) {
+    using A = typename NativeArith<S>::T;
+    using O = Ar<A>;
+    const A a1 = (A)alpha, a0 = (A)(1.0 - alpha);
+    const int nw = (ncells + 31) >> 5;
     const int lane = threadIdx.x & 31;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int w = warp; w < nruns; w += nwarps) {
-        const InterpRun run = runs[w];
-        const FabInfo ff = ffabs[run.ffab];
-        const FabInfo cf = cfabs[run.cfab];
-        int ky, kz;
-        double wy1, wz1;
-        lin_w(run.J, ratio, ky, wy1);
-        lin_w(run.K, ratio, kz, wz1);
-        const int cy = ky - run.shift[1] - cf.lo[1], cz = kz - run.shift[2] - cf.lo[2];
-        const double wy[2] = {1.0 - wy1, wy1}, wz[2] = {1.0 - wz1, wz1};
-        for (int t = lane; t < run.len; t += 32) {
-            int kx;
-            double wx1;
-            lin_w(run.I + t, ratio, kx, wx1);
-            const int cx = kx - run.shift[0] - cf.lo[0];
-            const double wx[2] = {1.0 - wx1, wx1};
-            for (int c = 0; c < ncomp; ++c) {
-                double v = 0.0;
+    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw; w += (gridDim.x * blockDim.x) >> 5) {
+        int q, t;
+        warp_segment(rstart, __ldg(wfirst + w), nruns, ncells, w << 5, q, t);
+        if ((w << 5) + lane >= ncells) continue;
+        const InterpRun run = runs[q];
+        int ix[3] = {run.I, run.J, run.K};
+        ix[run.axis] += t;
+        int kx, ky, kz;
+        A wx1, wy1, wz1;
+        lin_w(ix[0], ratio, kx, wx1);
+        lin_w(ix[1], ratio, ky, wy1);
+        lin_w(ix[2], ratio, kz, wz1);
+        const A wx[2] = {O::sub((A)1, wx1), wx1}, wy[2] = {O::sub((A)1, wy1), wy1}, wz[2] = {O::sub((A)1, wz1), wz1};
+        const long long cb = run.cbase + (long long)kz * run.cplane + (long long)ky * run.cpx + kx;
+        S *fo = fbase + run.fdst + (long long)t * run.fstep;
+        for (int c = 0; c < ncomp; ++c) {
+            const S *po = cold + cb + (long long)c * run.ccs, *pn = cnew + cb + (long long)c * run.ccs;
+            A v = (A)0;
 #pragma unroll
-                for (int dz = 0; dz < 2; ++dz)
+            for (int dz = 0; dz < 2; ++dz)
 #pragma unroll
-                    for (int dy = 0; dy < 2; ++dy)
+                for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
-                        for (int dx = 0; dx < 2; ++dx) {
-                            const long long at = cf.org + c * cf.cstride + (long long)(cz + dz) * cf.plane +
-                                                 (long long)(cy + dy) * cf.px + (cx + dx);
-                            const double tv = __dadd_rn(__dmul_rn(1.0 - alpha, to_f64(cold[at])),
-                                                        __dmul_rn(alpha, to_f64(cnew[at])));
-                            v = __dadd_rn(v, __dmul_rn(__dmul_rn(__dmul_rn(wz[dz], wy[dy]), wx[dx]), tv));
-                        }
-                from_f64(fbase + run.fdst + c * ff.cstride + t, v);
-            }
+                    for (int dx = 0; dx < 2; ++dx) {
+                        const int o = dz * run.cplane + dy * run.cpx + dx;
+                        const A tv = O::add(O::mul(a0, ld<S, A>(po + o)), O::mul(a1, ld<S, A>(pn + o)));
+                        v = O::add(v, O::mul(O::mul(O::mul(wz[dz], wy[dy]), wx[dx]), tv));
+                    }
+            st(fo + (long long)c * run.fcs, v);
         }
     }
 }
 
-template <typename S>
-__global__ void __launch_bounds__(256) k_avgdown(const S *fbase, const FabInfo *__restrict__ ffabs, S *cbase,
-                                                 const FabInfo *__restrict__ cfabs, const AvgRegion *__restrict__ regs,
-                                                 int nregs, int ncomp, int ratio) {
-    const double inv = 1.0 / (double)(ratio * ratio * ratio);
-    for (int w = blockIdx.x; w < nregs; w += gridDim.x) {
-        const AvgRegion rg = regs[w];
-        const FabInfo ff = ffabs[rg.ffab];
-        const FabInfo cf = cfabs[rg.cfab];
-        const int cells = rg.n[0] * rg.n[1] * rg.n[2];
-        for (int i = threadIdx.x; i < cells * ncomp; i += blockDim.x) {
-            const int x = i % rg.n[0], y = (i / rg.n[0]) % rg.n[1], z = (i / (rg.n[0] * rg.n[1])) % rg.n[2];
-            const int c = i / cells;
-            const int I = rg.clo[0] + x, J = rg.clo[1] + y, K = rg.clo[2] + z;
-            const S *fp = fbase + ff.org + c * ff.cstride;
-            double s = 0.0;
-            for (int dz = 0; dz < ratio; ++dz)
-                for (int dy = 0; dy < ratio; ++dy)
-                    for (int dx = 0; dx < ratio; ++dx) {
-                        const int fx = I * ratio + dx - ff.lo[0], fy = J * ratio + dy - ff.lo[1],
-                                  fz = K * ratio + dz - ff.lo[2];
-                        s = __dadd_rn(s, to_f64(fp[(long long)fz * ff.plane + (long long)fy * ff.px + fx]));
-                    }
-            from_f64(cbase + cf.org + c * cf.cstride + (long long)(K - cf.lo[2]) * cf.plane +
-                         (long long)(J - cf.lo[1]) * cf.px + (I - cf.lo[0]),
-                     __dmul_rn(s, inv));
+// Vector load of the RR consecutive fine children along x (RR * sizeof(S) bytes, aligned to
+// that size, or to 16 bytes above it), or RR scalar loads.
+template <int B> struct LdVec;
+template <> struct LdVec<2> { using T = unsigned short; };
+template <> struct LdVec<4> { using T = unsigned int; };
+template <> struct LdVec<8> { using T = uint2; };
+template <> struct LdVec<16> { using T = uint4; };
+
+template <typename S, int RR, bool VEC>
+__device__ __forceinline__ void ld_children(const S *p, S (&v)[RR]) {
+    constexpr int B = RR * (int)sizeof(S);
+    if constexpr (!VEC) {
+#pragma unroll
+        for (int i = 0; i < RR; ++i) v[i] = __ldg(p + i);
+    } else if constexpr (B <= 16) {
+        const typename LdVec<B>::T t = __ldg(reinterpret_cast<const typename LdVec<B>::T *>(p));
+        memcpy(v, &t, B);
+    } else {
+        uint4 t[B / 16];
+#pragma unroll
+        for (int i = 0; i < B / 16; ++i) t[i] = __ldg(reinterpret_cast<const uint4 *>(p) + i);
+        memcpy(v, t, B);
+    }
+}
+
+// Average-down (Sec. 2.3): one thread per coarse cell of the work list, the mean of its RR^3
+// fine children summed z, y, x ascending, times 1/RR^3 (a power of two: the same value as
+// the division), in the storage type's native precision.  Consecutive lanes take consecutive
+// coarse x, so each fine row is read as one contiguous span per warp.
+template <typename S, int RR, bool VEC>
+__global__ void __launch_bounds__(256) k_avgdown(const S *__restrict__ fbase, S *__restrict__ cbase,
+                                                 const AvgRegion *__restrict__ regs, const int *__restrict__ rstart,
+                                                 const int *__restrict__ wfirst, int nregs, int ncells, int ncomp) {
+    using A = typename NativeArith<S>::T;
+    using O = Ar<A>;
+    const A inv = (A)(1.0 / (double)(RR * RR * RR));
+    const int nw = (ncells + 31) >> 5;
+    const int lane = threadIdx.x & 31;
+    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw; w += (gridDim.x * blockDim.x) >> 5) {
+        int q, t;
+        warp_segment(rstart, __ldg(wfirst + w), nregs, ncells, w << 5, q, t);
+        if ((w << 5) + lane >= ncells) continue;
+        const AvgRegion rg = regs[q];
+        const int x = t % rg.n[0], yz = t / rg.n[0];
+        const int y = yz % rg.n[1], z = yz / rg.n[1];
+        const S *fp = fbase + rg.fsrc + (long long)z * RR * rg.fplane + (long long)y * RR * rg.fpx + x * RR;
+        S *cp = cbase + rg.cdst + (long long)z * rg.cplane + (long long)y * rg.cpx + x;
+        for (int c = 0; c < ncomp; ++c) {
+            const S *fc = fp + (long long)c * rg.fcs;
+            A s = (A)0;
+#pragma unroll
+            for (int dz = 0; dz < RR; ++dz)
+#pragma unroll
+                for (int dy = 0; dy < RR; ++dy) {
+                    S v[RR];
+                    ld_children<S, RR, VEC>(fc + (long long)dz * rg.fplane + (long long)dy * rg.fpx, v);
+#pragma unroll
+                    for (int dx = 0; dx < RR; ++dx) s = O::add(s, to_arith<A>(v[dx]));
+                }
+            st(cp + (long long)c * rg.ccs, O::mul(s, inv));
         }
     }
 }
@@ -723,44 +788,63 @@ cudaError_t launch_gather_dense(int dtype, const void *base, const FabInfo *ftab
     return dense_common(false, dtype, const_cast<void *>(base), ftab, nfab, stage, dlo, dn, z0, z1, comp, nc, s);
 }
 
-cudaError_t launch_interp(int dtype, void *fbase, const FabInfo *ffabs, const void *cold, const void *cnew,
-                          const FabInfo *cfabs, const InterpRun *runs, int nruns, int ncomp, int ratio, double alpha,
-                          cudaStream_t s) {
-    if (nruns == 0) return cudaSuccess;
-    int grid = (nruns + 3) / 4;
-    if (grid > 8 * sm_count()) grid = 8 * sm_count();
+cudaError_t launch_interp(int dtype, void *fbase, const void *cold, const void *cnew, const InterpRun *runs,
+                          const int *rstart, const int *wfirst, int nruns, int ncells, int ncomp, int ratio,
+                          double alpha, cudaStream_t s) {
+    if (ncells == 0) return cudaSuccess;
+    const int blocks = (int)(((long long)ncells + 255) / 256);
     switch (dtype) {
-        case F64:
-            k_interp<<<grid, 128, 0, s>>>((double *)fbase, ffabs, (const double *)cold, (const double *)cnew, cfabs,
-                                          runs, nruns, ncomp, ratio, alpha);
+        case F64: {
+            const int g = persistent_grid(k_interp<double>, 256, blocks);
+            k_interp<<<g, 256, 0, s>>>((double *)fbase, (const double *)cold, (const double *)cnew, runs, rstart,
+                                       wfirst, nruns, ncells, ncomp, ratio, alpha);
             break;
-        case F32:
-            k_interp<<<grid, 128, 0, s>>>((float *)fbase, ffabs, (const float *)cold, (const float *)cnew, cfabs,
-                                          runs, nruns, ncomp, ratio, alpha);
+        }
+        case F32: {
+            const int g = persistent_grid(k_interp<float>, 256, blocks);
+            k_interp<<<g, 256, 0, s>>>((float *)fbase, (const float *)cold, (const float *)cnew, runs, rstart,
+                                       wfirst, nruns, ncells, ncomp, ratio, alpha);
             break;
-        default:
-            k_interp<<<grid, 128, 0, s>>>((__nv_bfloat16 *)fbase, ffabs, (const __nv_bfloat16 *)cold,
-                                          (const __nv_bfloat16 *)cnew, cfabs, runs, nruns, ncomp, ratio, alpha);
+        }
+        default: {
+            const int g = persistent_grid(k_interp<__nv_bfloat16>, 256, blocks);
+            k_interp<<<g, 256, 0, s>>>((__nv_bfloat16 *)fbase, (const __nv_bfloat16 *)cold,
+                                       (const __nv_bfloat16 *)cnew, runs, rstart, wfirst, nruns, ncells, ncomp, ratio,
+                                       alpha);
+        }
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_avgdown(int dtype, const void *fbase, const FabInfo *ffabs, void *cbase, const FabInfo *cfabs,
-                           const AvgRegion *regs, int nregs, int ncomp, int ratio, cudaStream_t s) {
-    if (nregs == 0) return cudaSuccess;
-    int grid = nregs < 4 * sm_count() ? nregs : 4 * sm_count();
+template <typename S, int RR, bool VEC>
+static void avgdown_t(const void *fbase, void *cbase, const AvgRegion *regs, const int *rstart, const int *wfirst,
+                      int nregs, int ncells, int ncomp, cudaStream_t s) {
+    const int blocks = (int)(((long long)ncells + 255) / 256);
+    const int g = persistent_grid(k_avgdown<S, RR, VEC>, 256, blocks);
+    k_avgdown<S, RR, VEC><<<g, 256, 0, s>>>((const S *)fbase, (S *)cbase, regs, rstart, wfirst, nregs, ncells, ncomp);
+}
+
+template <typename S>
+static void avgdown_s(const void *fbase, void *cbase, const AvgRegion *regs, const int *rstart, const int *wfirst,
+                      int nregs, int ncells, int ncomp, int ratio, bool vec, cudaStream_t s) {
+    if (ratio == 2) {
+        if (vec) avgdown_t<S, 2, true>(fbase, cbase, regs, rstart, wfirst, nregs, ncells, ncomp, s);
+        else avgdown_t<S, 2, false>(fbase, cbase, regs, rstart, wfirst, nregs, ncells, ncomp, s);
+    } else {
+        if (vec) avgdown_t<S, 4, true>(fbase, cbase, regs, rstart, wfirst, nregs, ncells, ncomp, s);
+        else avgdown_t<S, 4, false>(fbase, cbase, regs, rstart, wfirst, nregs, ncells, ncomp, s);
+    }
+}
+
+cudaError_t launch_avgdown(int dtype, const void *fbase, void *cbase, const AvgRegion *regs, const int *rstart,
+                           const int *wfirst, int nregs, int ncells, int ncomp, int ratio, bool vec, cudaStream_t s) {
+    if (ncells == 0) return cudaSuccess;
+    if (ratio != 2 && ratio != 4) return cudaErrorInvalidValue;
     switch (dtype) {
-        case F64:
-            k_avgdown<<<grid, 256, 0, s>>>((const double *)fbase, ffabs, (double *)cbase, cfabs, regs, nregs, ncomp,
-                                           ratio);
-            break;
-        case F32:
-            k_avgdown<<<grid, 256, 0, s>>>((const float *)fbase, ffabs, (float *)cbase, cfabs, regs, nregs, ncomp,
-                                           ratio);
-            break;
+        case F64: avgdown_s<double>(fbase, cbase, regs, rstart, wfirst, nregs, ncells, ncomp, ratio, vec, s); break;
+        case F32: avgdown_s<float>(fbase, cbase, regs, rstart, wfirst, nregs, ncells, ncomp, ratio, vec, s); break;
         default:
-            k_avgdown<<<grid, 256, 0, s>>>((const __nv_bfloat16 *)fbase, ffabs, (__nv_bfloat16 *)cbase, cfabs, regs,
-                                           nregs, ncomp, ratio);
+            avgdown_s<__nv_bfloat16>(fbase, cbase, regs, rstart, wfirst, nregs, ncells, ncomp, ratio, vec, s);
     }
     return cudaGetLastError();
 }

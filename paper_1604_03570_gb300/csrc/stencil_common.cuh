@@ -24,6 +24,11 @@ template <> struct Ar<float> {
     static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
 };
 
+// The arithmetic type of a storage type when the path computes natively: FP64 for FP64
+// storage, FP32 for FP32 and BF16 storage.
+template <typename S> struct NativeArith { using T = S; };
+template <> struct NativeArith<__nv_bfloat16> { using T = float; };
+
 template <typename S, typename A> __device__ __forceinline__ A ld(const S *p);
 template <> __device__ __forceinline__ double ld<double, double>(const double *p) { return __ldg(p); }
 template <> __device__ __forceinline__ float ld<float, float>(const float *p) { return __ldg(p); }

@@ -669,9 +669,6 @@ static cudaError_t tma_t(int nt, const StencilTmaParams &p, int grid, cudaStream
     return cudaLaunchKernelEx(&cfg, kern, p);
 }
 
-template <typename S> struct NativeArith { using T = S; };  // bf16 values compute in FP32
-template <> struct NativeArith<__nv_bfloat16> { using T = float; };
-
 // The instantiated schedules: (R, rows, group bytes).  32-byte groups exist for FP32 and FP64
 // storage with one row per thread and R <= 2 (registers).
 template <typename S> constexpr bool kHasWide = !std::is_same<S, __nv_bfloat16>::value;

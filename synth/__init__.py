@@ -104,6 +104,24 @@ def eval_modes(shape, modes, scale=None):
     return out
 
 
+def eval_modes_box(N, lo, shape, modes):
+    """eval_modes restricted to the cells lo .. lo + shape - 1 (x, y, z lower corner; shape in
+    (nz, ny, nx) order) of a periodic N^3 grid: the same values as the matching block of
+    eval_modes((N, N, N), modes)."""
+    nz, ny, nx = shape
+    out = np.zeros(shape, dtype=np.float64)
+    xs = [(lo[0] + np.arange(nx) + 0.5) / N, (lo[1] + np.arange(ny) + 0.5) / N, (lo[2] + np.arange(nz) + 0.5) / N]
+    for k, a, ph in modes:
+        ex = np.exp(2j * math.pi * k[0] * xs[0])
+        ey = np.exp(2j * math.pi * k[1] * xs[1])
+        ez = np.exp(2j * math.pi * k[2] * xs[2]) * np.exp(1j * ph)
+        for z0 in range(0, nz, 32):
+            z1 = min(nz, z0 + 32)
+            blk = ez[z0:z1, None, None] * (ey[None, :, None] * ex[None, None, :])
+            out[z0:z1] += a * blk.imag
+    return out
+
+
 def single_mode(shape, k, phase=0.3):
     """sin(2 pi k . x + phase) on the cell centres (the pure mode of the decay test)."""
     return eval_modes(shape, [(tuple(k), 1.0, phase)])

@@ -315,49 +315,85 @@ def test_conservation_fp64():
 
 # --------------------------------------------------------------------------- AMR
 
-def _two_level(dtype="f64", C=1):
+def _two_level(ratio=2):
+    """A 16^3 coarse level in 8 boxes and three fine boxes (whole coarse cells) at ratio r."""
     Nc = 16
     clo, chi = [0, 0, 0], [Nc - 1] * 3
-    fboxes = np.array([[8, 8, 8, 15, 23, 15], [16, 8, 8, 23, 15, 19], [0, 0, 24, 7, 7, 31]], dtype=np.int32)
-    flo, fhi = [0, 0, 0], [2 * Nc - 1] * 3
+    base = np.array([[4, 4, 4, 7, 11, 7], [8, 4, 4, 11, 7, 9], [0, 0, 12, 3, 3, 15]])  # coarse cells
+    fboxes = np.concatenate([base[:, :3] * ratio, (base[:, 3:] + 1) * ratio - 1], axis=1).astype(np.int32)
+    flo, fhi = [0, 0, 0], [ratio * Nc - 1] * 3
     return Nc, clo, chi, oracle.chop(clo, chi, 8), flo, fhi, fboxes
 
 
-def test_interp_cf_bit_exact_fp64():
-    Nc, clo, chi, cboxes, flo, fhi, fboxes = _two_level()
-    cold = rand_field((1, Nc, Nc, Nc), 11)
-    cnew = rand_field((1, Nc, Nc, Nc), 12)
-    gc_old = gpu_level(clo, chi, boxes=cboxes, ngrow=1)
-    gc_new = gpu_level(clo, chi, boxes=cboxes, ngrow=1)
-    gf = gpu_level(flo, fhi, boxes=fboxes, ngrow=2)
+# The FP32 and BF16 paths compute in FP32.  Interpolation: the time blend (3 roundings), the 8
+# weighted terms (weights exact, 1 rounding each) and 8 additions stay below 13 u max|c| with
+# u = 2^-24; average-down: 8 additions below 8 u max|f|.  BF16 adds its store rounding 2^-9.
+LOWP_BOUND = {"f32": 1e-6, "bf16": 4e-3}
+
+
+def _fabs_close(g, L, odata, bound):
+    scale = np.nanmax(np.abs(odata))
+    for b in range(L.nbox):
+        got, ref = g.fab_to_host(b), L.fab(odata, b)
+        np.testing.assert_array_equal(np.isnan(got), np.isnan(ref))
+        m = ~np.isnan(ref)
+        assert float(np.max(np.abs(got[m] - ref[m]))) <= bound * scale
+
+
+@pytest.mark.parametrize("dtype,ratio,C,alpha", [("f64", 2, 1, 0.5), ("f64", 4, 2, 0.25), ("f64", 2, 3, 0.0),
+                                                 ("f32", 2, 2, 0.5), ("f32", 4, 1, 0.75), ("bf16", 2, 1, 0.5)])
+def test_interp_cf_matches_oracle(dtype, ratio, C, alpha):
+    """FP64: bit-exact.  FP32/BF16 storage: within the stated bound of the FP64 oracle."""
+    Nc, clo, chi, cboxes, flo, fhi, fboxes = _two_level(ratio)
+    cold = rand_field((C, Nc, Nc, Nc), 11, dtype)
+    cnew = rand_field((C, Nc, Nc, Nc), 12, dtype)
+    gc_old = gpu_level(clo, chi, boxes=cboxes, ncomp=C, ngrow=1, dtype=dtype)
+    gc_new = gpu_level(clo, chi, boxes=cboxes, ncomp=C, ngrow=1, dtype=dtype)
+    gf = gpu_level(flo, fhi, boxes=fboxes, ncomp=C, ngrow=2, dtype=dtype)
     gc_old.from_host(cold)
     gc_new.from_host(cnew)
     gc_old.fill_boundary()
     gc_new.fill_boundary()
-    CL = oracle.Level(cboxes, clo, chi, 1, 1)
-    FL = oracle.Level(fboxes, flo, fhi, 2, 1)
-    fd = FL.from_dense(rand_field((1, 2 * Nc, 2 * Nc, 2 * Nc), 13))
+    CL = oracle.Level(cboxes, clo, chi, 1, C)
+    FL = oracle.Level(fboxes, flo, fhi, 2, C)
+    fd = FL.from_dense(rand_field((C, ratio * Nc, ratio * Nc, ratio * Nc), 13, dtype))
     for b in range(FL.nbox):
         gf.fab_from_host(b, FL.fab(fd, b))
-    mf.mf_interp_cf(gf.h, gc_old.h, gc_new.h, 0.5, 2)
-    oracle.interp_cf(FL, CL, 2, 0.5, CL.from_dense(cold), CL.from_dense(cnew), fd)
-    _fabs_equal(gf, FL, fd)
+    mf.mf_interp_cf(gf.h, gc_old.h, gc_new.h, alpha, ratio)
+    oracle.interp_cf(FL, CL, ratio, alpha, CL.from_dense(cold), CL.from_dense(cnew), fd)
+    if dtype == "f64":
+        _fabs_equal(gf, FL, fd)
+    else:
+        _fabs_close(gf, FL, fd, LOWP_BOUND[dtype])
 
 
-def test_average_down_bit_exact_fp64():
-    Nc, clo, chi, cboxes, flo, fhi, fboxes = _two_level()
-    gc = gpu_level(clo, chi, boxes=cboxes, ngrow=1)
-    gf = gpu_level(flo, fhi, boxes=fboxes, ngrow=1)
-    cden = rand_field((1, Nc, Nc, Nc), 14)
-    fden = rand_field((1, 2 * Nc, 2 * Nc, 2 * Nc), 15)
+@pytest.mark.parametrize("dtype,ratio,C", [("f64", 2, 1), ("f64", 4, 2), ("f32", 2, 2), ("f32", 4, 1),
+                                           ("bf16", 2, 1), ("bf16", 4, 2)])
+def test_average_down_matches_oracle(dtype, ratio, C):
+    """FP64: bit-exact.  FP32/BF16 storage: within the stated bound of the FP64 oracle."""
+    Nc, clo, chi, cboxes, flo, fhi, fboxes = _two_level(ratio)
+    gc = gpu_level(clo, chi, boxes=cboxes, ncomp=C, ngrow=1, dtype=dtype)
+    gf = gpu_level(flo, fhi, boxes=fboxes, ncomp=C, ngrow=1, dtype=dtype)
+    cden = rand_field((C, Nc, Nc, Nc), 14, dtype)
+    fden = rand_field((C, ratio * Nc, ratio * Nc, ratio * Nc), 15, dtype)
     gc.from_host(cden)
     gf.from_host(fden)
-    mf.mf_average_down(gf.h, gc.h, 2)
-    CL = oracle.Level(cboxes, clo, chi, 1, 1)
-    FL = oracle.Level(fboxes, flo, fhi, 1, 1)
+    mf.mf_average_down(gf.h, gc.h, ratio)
+    CL = oracle.Level(cboxes, clo, chi, 1, C)
+    FL = oracle.Level(fboxes, flo, fhi, 1, C)
     cd = CL.from_dense(cden)
-    oracle.average_down(FL, CL, 2, FL.from_dense(fden), cd)
-    np.testing.assert_array_equal(gc.to_host(), CL.to_dense(cd))
+    oracle.average_down(FL, CL, ratio, FL.from_dense(fden), cd)
+    ref = CL.to_dense(cd)
+    if dtype == "f64":
+        np.testing.assert_array_equal(gc.to_host(), ref)
+    else:
+        got = gc.to_host()
+        assert float(np.max(np.abs(got - ref))) <= LOWP_BOUND[dtype] * np.max(np.abs(fden))
+        covered = np.zeros((Nc, Nc, Nc), dtype=bool)
+        for b in fboxes:
+            covered[b[2] // ratio:b[5] // ratio + 1, b[1] // ratio:b[4] // ratio + 1,
+                    b[0] // ratio:b[3] // ratio + 1] = True
+        np.testing.assert_array_equal(got[:, ~covered], cden[:, ~covered])  # nothing else written
 
 
 def test_amr_advance_fp64_matches_oracle():

@@ -197,3 +197,12 @@ def test_set_tile_roundtrip():
         assert mf.mf_get_tile(h)[1] is True
     finally:
         mf.mf_destroy(h)
+
+
+def test_eval_modes_box_equals_the_block_of_the_full_grid():
+    """The sub-box evaluator of the seeded inputs gives the same bits as the full grid."""
+    import synth
+    m = synth.sine_modes(1604, 100, 4, 8)
+    full = synth.eval_modes((32, 32, 32), m)
+    blk = synth.eval_modes_box(32, (5, 7, 9), (10, 12, 14), m)
+    np.testing.assert_array_equal(full[9:19, 7:19, 5:19], blk)
