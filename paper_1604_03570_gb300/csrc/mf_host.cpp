@@ -219,6 +219,23 @@ struct RefluxPlan {
     std::vector<CCell> cells;
     DevBuf d_faces, d_ff, d_cells, d_regc, d_regf;
 };
+// The coarse level's ghost exchange inside the two-level advance, limited to the ghost cells
+// that are read.  Per FillBoundary region of the coarse level: the bounding box of its cells that
+// the interpolation reads (ip), that the interpolation or the coarse flux registers read (cf),
+// and, for face regions, of the cells whose source lies within one cell of the fine-covered
+// region (stale: the average-down and the flux correction rewrite those sources after the
+// stencil's ghost push delivered them).  Boxes as {lo[3], n[3]} within the region, n[0] = 0
+// for none.
+struct AmrFill {
+    const mf_t *fine = nullptr;
+    int ratio = 0, R = 0;
+    bool reflux = false;
+    std::vector<std::array<int, 6>> ip, cf, stale;
+    unsigned long long gen = ~0ull;  // the coarse build generation the task lists belong to
+    std::vector<FbTask> t_first, t_next, t_post;
+    DevBuf d_first, d_next, d_post;
+};
+
 struct AvgPlan {
     const mf_t *fine = nullptr;
     int ratio = 0;
@@ -264,6 +281,7 @@ struct mf {
     DevBuf d_maps, d_tfab, d_err, d_smaps, d_strips, d_fbtasks_adv, d_push, d_fbtasks_res;
     std::vector<FbTask> fbtasks_res;  // the fill left once the stencil pushes face ghosts
     bool tma_push = false;
+    bool push_pref = true;         // the autotuner's choice between the ghost push and the face fill
     bool tma_strips = false;  // x halos pulled from neighbour boxes (fill skips x faces)
     int tma_R = 0;            // radius the maps were encoded for (0 = none)
     bool tma_ok = false;      // current tile shape fits the TMA kernel
@@ -291,6 +309,7 @@ struct mf {
     std::vector<std::unique_ptr<InterpPlan>> interp;
     std::vector<std::unique_ptr<RefluxPlan>> reflux;
     std::vector<std::unique_ptr<AvgPlan>> avg;
+    std::vector<std::unique_ptr<AmrFill>> amrfill;
     ~mf() {
         graphs.clear();
         for (auto e : ev) cudaEventDestroy(e);
@@ -350,43 +369,55 @@ static long long elem_at(const FabInfo &f, int i, int j, int k) {  // global (i,
 // ------------------------------------------------------------------ FillBoundary list
 
 // FillBoundary tasks for the entries selected by `use`: CTA-sized pieces (256 threads x 4 cells).
-static void make_fill_tasks(const mf_t *m, const std::vector<char> &use, std::vector<FbTask> &out) {
+// Appends the fill tasks of one FillBoundary region (or a clipped part of one).
+static void append_fill_tasks(const mf_t *m, const FbEntry &en, std::vector<FbTask> &out) {
     const int kTask = 256;  // one warp of the fill kernel: 32 lanes x 8 cells (or vectors)
     const long long V = 16 / m->esize;  // elements per 16-byte vector
-    out.clear();
-    for (int e = 0; e < (int)m->fb.size(); ++e) {
-        if (!use[e]) continue;
-        const FbEntry &en = m->fb[e];
-        const FabInfo &sf = m->fabs[en.sfab], &df = m->fabs[en.dfab];
-        // rows that start and end on 16-byte boundaries on both sides copy as 16-byte vectors
-        // (pitches, planes and component strides are whole 32-byte sectors by construction)
-        const bool vec = en.n[0] % V == 0 && en.src % V == 0 && en.dst % V == 0;
-        const long long u = vec ? V : 1;
-        const int n0 = (int)(en.n[0] / u);
-        const long long cells = (long long)n0 * en.n[1] * en.n[2] * m->ncomp;
-        for (long long f = 0; f < cells; f += kTask) {
-            FbTask t{};
-            t.src = en.src / u;
-            t.dst = en.dst / u;
-            t.s_pl = (int)(sf.plane / u);
-            t.d_pl = (int)(df.plane / u);
-            t.s_cs = (int)(sf.cstride / u);
-            t.d_cs = (int)(df.cstride / u);
-            t.s_px = (int)(sf.px / u);
-            t.d_px = (int)(df.px / u);
-            t.n0 = n0;
-            t.n1 = en.n[1];
-            t.n2 = en.n[2];
-            t.first = (int)f;
-            t.count = (int)std::min<long long>(kTask, cells - f);
-            t.level = en.level;
-            t.f0 = make_fastdiv((uint32_t)n0);
-            t.f1 = make_fastdiv((uint32_t)en.n[1]);
-            t.f2 = make_fastdiv((uint32_t)en.n[2]);
-            t.vec = vec ? 1 : 0;
-            out.push_back(t);
-        }
+    const FabInfo &sf = m->fabs[en.sfab], &df = m->fabs[en.dfab];
+    // rows that start and end on 16-byte boundaries on both sides copy as 16-byte vectors
+    // (pitches, planes and component strides are whole 32-byte sectors by construction)
+    const bool vec = en.n[0] % V == 0 && en.src % V == 0 && en.dst % V == 0;
+    const long long u = vec ? V : 1;
+    const int n0 = (int)(en.n[0] / u);
+    const long long cells = (long long)n0 * en.n[1] * en.n[2] * m->ncomp;
+    for (long long f = 0; f < cells; f += kTask) {
+        FbTask t{};
+        t.src = en.src / u;
+        t.dst = en.dst / u;
+        t.s_pl = (int)(sf.plane / u);
+        t.d_pl = (int)(df.plane / u);
+        t.s_cs = (int)(sf.cstride / u);
+        t.d_cs = (int)(df.cstride / u);
+        t.s_px = (int)(sf.px / u);
+        t.d_px = (int)(df.px / u);
+        t.n0 = n0;
+        t.n1 = en.n[1];
+        t.n2 = en.n[2];
+        t.first = (int)f;
+        t.count = (int)std::min<long long>(kTask, cells - f);
+        t.level = en.level;
+        t.f0 = make_fastdiv((uint32_t)n0);
+        t.f1 = make_fastdiv((uint32_t)en.n[1]);
+        t.f2 = make_fastdiv((uint32_t)en.n[2]);
+        t.vec = vec ? 1 : 0;
+        out.push_back(t);
     }
+}
+
+static void make_fill_tasks(const mf_t *m, const std::vector<char> &use, std::vector<FbTask> &out) {
+    out.clear();
+    for (int e = 0; e < (int)m->fb.size(); ++e)
+        if (use[e]) append_fill_tasks(m, m->fb[e], out);
+}
+
+// The part [lo, lo + n) (offsets within the region) of FillBoundary region e.
+static FbEntry clip_entry(const mf_t *m, int e, const int lo[3], const int n[3]) {
+    FbEntry c = m->fb[e];
+    const FabInfo &sf = m->fabs[c.sfab], &df = m->fabs[c.dfab];
+    c.src += lo[2] * sf.plane + (long long)lo[1] * sf.px + lo[0];
+    c.dst += lo[2] * df.plane + (long long)lo[1] * df.px + lo[0];
+    for (int d = 0; d < 3; ++d) c.n[d] = n[d];
+    return c;
 }
 
 static int build_fb(mf_t *m) {
@@ -757,6 +788,7 @@ extern "C" int mf_set_tile(mf_t *m, const int tile[3]) {
     for (int d = 0; d < 3; ++d)
         if (tile[d] > 32767) return fail(MF_EINVAL, "tile size too large");
     m->tile_auto = false;
+    m->push_pref = true;
     int rc = set_tiles(m, tile);
     if (rc) return rc;
     m->tma_R = 0;
@@ -1250,6 +1282,10 @@ static int enqueue_fill(mf_t *m, int which, cudaStream_t s) {
     return 0;
 }
 
+// The stencil writes the y and z face ghosts of the level it produces (the ghost push), so later
+// steps fill only the residual regions.
+static bool use_push(const mf_t *m) { return m->use_tma && m->tma_ok && m->tma_push && m->push_pref; }
+
 // The ghost exchange a time step needs: with the TMA stencil, only the face regions it reads
 // from ghost cells (edges and corners are never read by a star stencil; x faces whose tiles
 // take their halo from the neighbour box are skipped).
@@ -1383,6 +1419,7 @@ static int autotune(mf_t *m, int R, bool fp64diff, const double *lam) {
         int rc = set_tiles(m, c.t.data());
         if (rc) return rc;
         if ((rc = enqueue_stencil(m, m->cur, R, fp64diff, lam, m->stream, true))) return rc;
+        if (!ms) return 0;
         CU(cudaEventRecord(e0, m->stream));
         for (int i = 0; i < n; ++i)
             if ((rc = enqueue_stencil(m, m->cur, R, fp64diff, lam, m->stream, true))) return rc;
@@ -1412,13 +1449,41 @@ static int autotune(mf_t *m, int R, bool fp64diff, const double *lam) {
             r2[j] = std::min(r2[j], ms);
         }
     Cand bc = cands[r1[std::min_element(r2.begin(), r2.end()) - r2.begin()].second];
+    m->tile_auto = false;
+    m->push_pref = true;
+    int rc = time_cand(bc, 1, nullptr);  // installs the schedule (and builds its lists)
+    // with that schedule, one step as the advance runs it: the ghost push and the residual fill,
+    // or the face fill and the stencil alone, whichever is faster on this level
+    if (!rc && m->use_tma && m->tma_ok && m->tma_push) {
+        auto time_mode = [&](bool push, int n, float *ms) -> int {
+            for (int i = -1; i < n; ++i) {
+                if (i == 0) CU(cudaEventRecord(e0, m->stream));
+                int r = 0;
+                if (!push) r = enqueue_fill_step(m, m->cur, m->stream);
+                else if (!m->fbtasks_res.empty())
+                    CU(launch_fill(m->dtype, level_ptrs(m, m->cur), (const FbTask *)m->d_fbtasks_res.p,
+                                   (int)m->fbtasks_res.size(), 0, m->stream));
+                if (!r) r = enqueue_stencil(m, m->cur, R, fp64diff, lam, m->stream, push);
+                if (r) return r;
+            }
+            CU(cudaEventRecord(e1, m->stream));
+            CU(cudaEventSynchronize(e1));
+            CU(cudaEventElapsedTime(ms, e0, e1));
+            return 0;
+        };
+        float tp = 1e30f, tf = 1e30f;
+        for (int pass = 0; pass < 3 && !rc; ++pass) {
+            float a = 0, b = 0;
+            if (!(rc = time_mode(true, 6, &a)) && !(rc = time_mode(false, 6, &b))) {
+                tp = std::min(tp, a);
+                tf = std::min(tf, b);
+            }
+        }
+        m->push_pref = tp <= tf;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    m->tile_auto = false;
-    m->tma_rows = bc.rows;
-    m->tma_ns_pref = bc.ns;
-    m->tma_gb = bc.gb;
-    return set_tiles(m, bc.t.data());
+    return rc;
 }
 
 extern "C" int mf_set_schedule(mf_t *m, const int in[3]) {
@@ -1615,7 +1680,7 @@ extern "C" int mf_advance(mf_t *m, const mf_stencil *st, double dt, int nsteps) 
         int body = 0, from = m->cur;
         PhaseLog log{m, m->timing};
         body = log.start();
-        const bool push = m->use_tma && m->tma_ok && m->tma_push;
+        const bool push = use_push(m);
         for (int s = 0; s < nsteps && !body; ++s) {
             if (push && s > 0) {
                 // the previous stencil launch pushed the face ghosts; fill what is left
@@ -1685,7 +1750,7 @@ extern "C" int mf_rk3_advance(mf_t *m, const mf_stencil *st, double dt, int nste
         int body = 0, a = m->cur;
         PhaseLog log{m, m->timing};
         body = log.start();
-        const bool push = m->use_tma && m->tma_ok && m->tma_push;
+        const bool push = use_push(m);
         // pushed[l]: the launch that last wrote level l also wrote its face ghosts
         bool pushed[3] = {false, false, false};
         for (int step = 0; step < nsteps && !body; ++step) {
@@ -2038,6 +2103,134 @@ static AvgPlan *get_avg(const mf_t *fine, mf_t *crse, int ratio, int *rc) {
     return crse->avg.back().get();
 }
 
+// Bounding box, per FillBoundary region of m, of the destination cells whose element offset
+// (component 0) is marked in bits.
+static void mark_parts(const mf_t *m, const std::vector<uint64_t> &bits, std::vector<std::array<int, 6>> &out) {
+    out.assign(m->fb.size(), std::array<int, 6>{0, 0, 0, 0, 0, 0});
+    for (size_t e = 0; e < m->fb.size(); ++e) {
+        const FbEntry &en = m->fb[e];
+        const FabInfo &df = m->fabs[en.dfab];
+        int lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, hi[3] = {-1, -1, -1};
+        for (int z = 0; z < en.n[2]; ++z)
+            for (int y = 0; y < en.n[1]; ++y)
+                for (int x = 0; x < en.n[0]; ++x) {
+                    const long long el = en.dst + z * df.plane + (long long)y * df.px + x;
+                    if (!((bits[(size_t)el >> 6] >> (el & 63)) & 1)) continue;
+                    const int p[3] = {x, y, z};
+                    for (int d = 0; d < 3; ++d) { lo[d] = std::min(lo[d], p[d]); hi[d] = std::max(hi[d], p[d]); }
+                }
+        if (hi[0] >= 0) out[e] = {lo[0], lo[1], lo[2], hi[0] - lo[0] + 1, hi[1] - lo[1] + 1, hi[2] - lo[2] + 1};
+    }
+}
+
+static void append_parts(const mf_t *m, const std::vector<std::array<int, 6>> &parts, std::vector<FbTask> &out) {
+    for (size_t e = 0; e < parts.size(); ++e)
+        if (parts[e][3] > 0) append_fill_tasks(m, clip_entry(m, (int)e, parts[e].data(), parts[e].data() + 3), out);
+}
+
+static AmrFill *get_amr_fill(mf_t *crse, const mf_t *fine, int ratio, int R, const InterpPlan *ip,
+                             const RefluxPlan *rp, int *rc) {
+    AmrFill *af = nullptr;
+    for (auto &p : crse->amrfill)
+        if (p->fine == fine && p->ratio == ratio && p->R == R && p->reflux == (rp != nullptr)) af = p.get();
+    if (!af) {
+        auto p = std::make_unique<AmrFill>();
+        p->fine = fine;
+        p->ratio = ratio;
+        p->R = R;
+        p->reflux = rp != nullptr;
+        // cells the interpolation reads: the 8 coarse points of every interpolated fine cell
+        std::vector<uint64_t> bits((crse->level_elems + 63) / 64, 0);
+        auto set = [&](long long el) { bits[(size_t)el >> 6] |= 1ull << (el & 63); };
+        for (size_t q = 0; q < ip->runs.size(); ++q) {
+            const InterpRun &run = ip->runs[q];
+            for (int t = 0; t < ip->cells.start[q + 1] - ip->cells.start[q]; ++t) {
+                int ix[3] = {run.I, run.J, run.K};
+                ix[run.axis] += t;
+                int k[3];
+                for (int d = 0; d < 3; ++d) k[d] = floor_div(2 * ix[d] + 1 - ratio, 2 * ratio);
+                const long long cb = run.cbase + (long long)k[2] * run.cplane + (long long)k[1] * run.cpx + k[0];
+                for (int dz = 0; dz < 2; ++dz)
+                    for (int dy = 0; dy < 2; ++dy)
+                        for (int dx = 0; dx < 2; ++dx) set(cb + (long long)dz * run.cplane + dy * run.cpx + dx);
+            }
+        }
+        mark_parts(crse, bits, p->ip);
+        // ... and the cells of the coarse flux lines across the coarse-fine faces
+        if (rp)
+            for (const CFace &f : rp->faces)
+                for (int k = -R + 1; k <= R; ++k) set(f.c_low + k * f.dstride);
+        mark_parts(crse, bits, p->cf);
+        // face regions whose source lies within one cell (26 directions, periodic) of a covered cell
+        const Box &cd = crse->domain;
+        const int L[3] = {cd.len(0), cd.len(1), cd.len(2)};
+        std::vector<unsigned char> cov((size_t)L[0] * L[1] * L[2], 0), tmp;
+        auto at = [&](int x, int y, int z) { return ((size_t)z * L[1] + y) * L[0] + x; };
+        for (const Box &b : fine->boxes)
+            for (int z = floor_div(b.lo[2], ratio); z <= floor_div(b.hi[2], ratio); ++z)
+                for (int y = floor_div(b.lo[1], ratio); y <= floor_div(b.hi[1], ratio); ++y)
+                    for (int x = floor_div(b.lo[0], ratio); x <= floor_div(b.hi[0], ratio); ++x)
+                        cov[at(wrap_idx(x, cd.lo[0], L[0]) - cd.lo[0], wrap_idx(y, cd.lo[1], L[1]) - cd.lo[1],
+                               wrap_idx(z, cd.lo[2], L[2]) - cd.lo[2])] = 1;
+        for (int d = 0; d < 3; ++d) {  // dilate by one cell along each direction in turn
+            tmp = cov;
+            for (int z = 0; z < L[2]; ++z)
+                for (int y = 0; y < L[1]; ++y)
+                    for (int x = 0; x < L[0]; ++x) {
+                        int p[3] = {x, y, z};
+                        if (tmp[at(x, y, z)]) continue;
+                        for (int sgn = -1; sgn <= 1; sgn += 2) {
+                            int q[3] = {p[0], p[1], p[2]};
+                            q[d] = (q[d] + sgn + L[d]) % L[d];
+                            if (tmp[at(q[0], q[1], q[2])]) { cov[at(x, y, z)] = 1; break; }
+                        }
+                    }
+        }
+        p->stale.assign(crse->fb.size(), std::array<int, 6>{0, 0, 0, 0, 0, 0});
+        for (size_t e = 0; e < crse->fb.size(); ++e) {
+            const int kind = crse->fb_kind[e];
+            if (kind < 2 || kind > 5) continue;  // the push writes the y and z face regions
+            const FbEntry &en = crse->fb[e];
+            const auto &cr = crse->fb_corner[e];
+            int lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, hi[3] = {-1, -1, -1};
+            for (int z = 0; z < en.n[2]; ++z)
+                for (int y = 0; y < en.n[1]; ++y)
+                    for (int x = 0; x < en.n[0]; ++x) {
+                        if (!cov[at(cr[3] + x - cd.lo[0], cr[4] + y - cd.lo[1], cr[5] + z - cd.lo[2])]) continue;
+                        const int pp[3] = {x, y, z};
+                        for (int d = 0; d < 3; ++d) { lo[d] = std::min(lo[d], pp[d]); hi[d] = std::max(hi[d], pp[d]); }
+                    }
+            if (hi[0] >= 0) p->stale[e] = {lo[0], lo[1], lo[2], hi[0] - lo[0] + 1, hi[1] - lo[1] + 1, hi[2] - lo[2] + 1};
+        }
+        crse->amrfill.push_back(std::move(p));
+        af = crse->amrfill.back().get();
+    }
+    if (af->gen != crse->gen) {
+        // first step: the step's face fill and the read cells; later steps with the ghost push:
+        // the residual fill, the stale faces and the read cells; after the coarse stencil: the
+        // cells the interpolation reads from the new coarse data
+        const bool strips = crse->use_tma && crse->tma_ok && crse->tma_strips;
+        const bool push = strips && use_push(crse);
+        af->t_first = strips ? crse->fbtasks_adv : crse->fbtasks;
+        if (strips) append_parts(crse, af->cf, af->t_first);
+        af->t_next.clear();
+        if (push) {
+            af->t_next = crse->fbtasks_res;
+            append_parts(crse, af->stale, af->t_next);
+            append_parts(crse, af->cf, af->t_next);
+        }
+        af->t_post.clear();
+        append_parts(crse, af->ip, af->t_post);
+        if ((*rc = af->d_first.upload(af->t_first, crse->stream))) return nullptr;
+        if ((*rc = af->d_next.upload(af->t_next, crse->stream))) return nullptr;
+        if ((*rc = af->d_post.upload(af->t_post, crse->stream))) return nullptr;
+        if (cudaStreamSynchronize(crse->stream) != cudaSuccess) { *rc = fail(MF_ECUDA, "sync"); return nullptr; }
+        af->gen = crse->gen;
+    }
+    *rc = 0;
+    return af;
+}
+
 static int enqueue_interp(mf_t *fine, int fwhich, const mf_t *cold, int cold_which, const mf_t *cnew, int cnew_which,
                           InterpPlan *plan, int ratio, double alpha, cudaStream_t s) {
     CU(launch_interp(fine->dtype, fine->level_ptr(fwhich), cold->level_ptr(cold_which), cnew->level_ptr(cnew_which),
@@ -2113,6 +2306,10 @@ extern "C" int mf_amr_advance(mf_t *crse, mf_t *fine, const mf_stencil *st, doub
     if (fine->tile_auto && (rc = autotune(fine, R, fp64diff, lam_f))) return rc;
     if (crse->use_tma && crse->tma_R != R && (rc = build_tma(crse, R))) return rc;
     if (fine->use_tma && fine->tma_R != R && (rc = build_tma(fine, R))) return rc;
+    AmrFill *af = get_amr_fill(crse, fine, ratio, R, ip, rp, &rc);
+    if (!af) return rc;
+    const bool cpush = use_push(crse);
+    const bool fpush = use_push(fine);
     // the coarse stream orders everything; the fine stream waits for nothing else (same
     // stream expected); capture the whole advance into one graph
     char buf[160];
@@ -2125,20 +2322,35 @@ extern "C" int mf_amr_advance(mf_t *crse, mf_t *fine, const mf_stencil *st, doub
         cudaStream_t s = crse->cap;
         int body = 0, c = crse->cur, f = fine->cur;
         PhaseLog log{crse, false};
+        auto fill = [&](mf_t *m, int which, const DevBuf &t, size_t n) -> int {
+            if (!n) return 0;
+            int b = log.before(0);
+            if (!b && launch_fill(m->dtype, level_ptrs(m, which), (const FbTask *)t.p, (int)n, 0, s) != cudaSuccess)
+                b = fail(MF_ECUDA, "fill launch failed");
+            return b;
+        };
         for (int step = 0; step < ncrse_steps && !body; ++step) {
-            // full exchange: the coarse-fine interpolation reads coarse edge and corner ghosts
-            const bool cf = !crse->fbtasks.empty();
+            // the coarse ghosts read in this step: the stencil's faces (or, with the ghost push,
+            // what the push does not deliver or the last average-down and correction made
+            // stale) and the cells the interpolation and the flux registers read
             const int nface = rp ? (int)rp->faces.size() : 0;
-            if (!(body = log.before(0, cf))) body = enqueue_fill(crse, c, s);
+            if (step == 0 || !cpush) body = fill(crse, c, af->d_first, af->t_first.size());
+            else body = fill(crse, c, af->d_next, af->t_next.size());
             if (!body && rp && !(body = log.before(2, nface > 0)))  // coarse face fluxes at the interface
                 body = launch_cf_coarse_flux(crse->dtype, R, crse->level_ptr(c), (const CFace *)rp->d_faces.p, nface,
                                              crse->ncomp, wc, (double *)rp->d_regc.p, s) == cudaSuccess
                            ? 0
                            : fail(MF_ECUDA, "flux register launch failed");
-            if (!body && !(body = log.before(1))) body = enqueue_stencil(crse, c, R, fp64diff, lam_c, s);
-            if (!body && !(body = log.before(0, cf))) body = enqueue_fill(crse, 1 - c, s);
+            if (!body && !(body = log.before(1))) body = enqueue_stencil(crse, c, R, fp64diff, lam_c, s, cpush);
+            if (!body) body = fill(crse, 1 - c, af->d_post, af->t_post.size());  // read by the interpolation
             for (int sub = 0; sub < nsub && !body; ++sub) {
-                if (!(body = log.before(0, fill_step_tasks(fine) > 0))) body = enqueue_fill_step(fine, f, s);
+                // the fine level steps like a single level: a face fill first, then the push
+                // and the residual fill; the interpolation writes the coarse-fine ghosts
+                if ((step == 0 && sub == 0) || !fpush) {
+                    if (!(body = log.before(0, fill_step_tasks(fine) > 0))) body = enqueue_fill_step(fine, f, s);
+                } else {
+                    body = fill(fine, f, fine->d_fbtasks_res, fine->fbtasks_res.size());
+                }
                 if (!body && !(body = log.before(2, !ip->runs.empty())))
                     body = enqueue_interp(fine, f, crse, c, crse, 1 - c, ip, ratio, (double)sub / (double)nsub, s);
                 if (!body && rp && !(body = log.before(2, nface > 0)))  // fine face fluxes, this substep
@@ -2147,7 +2359,7 @@ extern "C" int mf_amr_advance(mf_t *crse, mf_t *fine, const mf_stencil *st, doub
                                                (double *)rp->d_regf.p, sub == 0, s) == cudaSuccess
                                ? 0
                                : fail(MF_ECUDA, "flux register launch failed");
-                if (!body && !(body = log.before(1))) body = enqueue_stencil(fine, f, R, fp64diff, lam_f, s);
+                if (!body && !(body = log.before(1))) body = enqueue_stencil(fine, f, R, fp64diff, lam_f, s, fpush);
                 f = 1 - f;
             }
             if (!body && !(body = log.before(3, !ap->regs.empty())))
