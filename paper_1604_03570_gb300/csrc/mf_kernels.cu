@@ -565,8 +565,9 @@ __device__ __forceinline__ void ld_children(const S *p, S (&v)[RR]) {
 // Average-down (Sec. 2.3): one thread per coarse cell of the work list, the mean of its RR^3
 // fine children summed z, y, x ascending, times 1/RR^3 (a power of two: the same value as
 // the division), in the storage type's native precision.  Consecutive lanes take consecutive
-// coarse x, so each fine row is read as one contiguous span per warp.
-template <typename S, int RR, bool VEC>
+// coarse x, so each fine row is read as one contiguous span per warp.  A warp takes U
+// consecutive 32-cell chunks at a time with all their loads issued before the sums.
+template <typename S, int RR, bool VEC, int U>
 __global__ void __launch_bounds__(256) k_avgdown(const S *__restrict__ fbase, S *__restrict__ cbase,
                                                  const AvgRegion *__restrict__ regs, const int *__restrict__ rstart,
                                                  const int *__restrict__ wfirst, int nregs, int ncells, int ncomp) {
@@ -575,28 +576,51 @@ __global__ void __launch_bounds__(256) k_avgdown(const S *__restrict__ fbase, S 
     const A inv = (A)(1.0 / (double)(RR * RR * RR));
     const int nw = (ncells + 31) >> 5;
     const int lane = threadIdx.x & 31;
-    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw; w += (gridDim.x * blockDim.x) >> 5) {
-        int q, t;
-        warp_segment(rstart, __ldg(wfirst + w), nregs, ncells, w << 5, q, t);
-        if ((w << 5) + lane >= ncells) continue;
-        const AvgRegion rg = regs[q];
-        const int x = t % rg.n[0], yz = t / rg.n[0];
-        const int y = yz % rg.n[1], z = yz / rg.n[1];
-        const S *fp = fbase + rg.fsrc + (long long)z * RR * rg.fplane + (long long)y * RR * rg.fpx + x * RR;
-        S *cp = cbase + rg.cdst + (long long)z * rg.cplane + (long long)y * rg.cpx + x;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int w0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * U; w0 < nw; w0 += nwarps * U) {
+        bool act[U];
+        const S *fp[U];
+        S *cp[U];
+        int fpl[U], fpx[U], fcs[U], ccs[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int w = w0 + u;
+            act[u] = false;
+            if (w >= nw) continue;  // warp-uniform
+            int q, t;
+            warp_segment(rstart, __ldg(wfirst + w), nregs, ncells, w << 5, q, t);
+            if ((w << 5) + lane >= ncells) continue;
+            const AvgRegion rg = regs[q];
+            const int x = t % rg.n[0], yz = t / rg.n[0];
+            const int y = yz % rg.n[1], z = yz / rg.n[1];
+            fp[u] = fbase + rg.fsrc + (long long)z * RR * rg.fplane + (long long)y * RR * rg.fpx + x * RR;
+            cp[u] = cbase + rg.cdst + (long long)z * rg.cplane + (long long)y * rg.cpx + x;
+            fpl[u] = rg.fplane;
+            fpx[u] = rg.fpx;
+            fcs[u] = rg.fcs;
+            ccs[u] = rg.ccs;
+            act[u] = true;
+        }
         for (int c = 0; c < ncomp; ++c) {
-            const S *fc = fp + (long long)c * rg.fcs;
-            A s = (A)0;
+            S v[U][RR * RR][RR];
 #pragma unroll
-            for (int dz = 0; dz < RR; ++dz)
+            for (int u = 0; u < U; ++u)
+                if (act[u]) {
+                    const S *fc = fp[u] + (long long)c * fcs[u];
 #pragma unroll
-                for (int dy = 0; dy < RR; ++dy) {
-                    S v[RR];
-                    ld_children<S, RR, VEC>(fc + (long long)dz * rg.fplane + (long long)dy * rg.fpx, v);
-#pragma unroll
-                    for (int dx = 0; dx < RR; ++dx) s = O::add(s, to_arith<A>(v[dx]));
+                    for (int r = 0; r < RR * RR; ++r)
+                        ld_children<S, RR, VEC>(fc + (long long)(r / RR) * fpl[u] + (long long)(r % RR) * fpx[u], v[u][r]);
                 }
-            st(cp + (long long)c * rg.ccs, O::mul(s, inv));
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (act[u]) {
+                    A s = (A)0;
+#pragma unroll
+                    for (int r = 0; r < RR * RR; ++r)
+#pragma unroll
+                        for (int dx = 0; dx < RR; ++dx) s = O::add(s, to_arith<A>(v[u][r][dx]));
+                    st(cp[u] + (long long)c * ccs[u], O::mul(s, inv));
+                }
         }
     }
 }
@@ -796,21 +820,21 @@ cudaError_t launch_interp(int dtype, void *fbase, const void *cold, const void *
     switch (dtype) {
         case F64: {
             const int g = persistent_grid(k_interp<double>, 256, blocks);
-            k_interp<<<g, 256, 0, s>>>((double *)fbase, (const double *)cold, (const double *)cnew, runs, rstart,
-                                       wfirst, nruns, ncells, ncomp, ratio, alpha);
+            k_interp<double><<<g, 256, 0, s>>>((double *)fbase, (const double *)cold, (const double *)cnew,
+                                                         runs, rstart, wfirst, nruns, ncells, ncomp, ratio, alpha);
             break;
         }
         case F32: {
             const int g = persistent_grid(k_interp<float>, 256, blocks);
-            k_interp<<<g, 256, 0, s>>>((float *)fbase, (const float *)cold, (const float *)cnew, runs, rstart,
-                                       wfirst, nruns, ncells, ncomp, ratio, alpha);
+            k_interp<float><<<g, 256, 0, s>>>((float *)fbase, (const float *)cold, (const float *)cnew, runs,
+                                                        rstart, wfirst, nruns, ncells, ncomp, ratio, alpha);
             break;
         }
         default: {
             const int g = persistent_grid(k_interp<__nv_bfloat16>, 256, blocks);
-            k_interp<<<g, 256, 0, s>>>((__nv_bfloat16 *)fbase, (const __nv_bfloat16 *)cold,
-                                       (const __nv_bfloat16 *)cnew, runs, rstart, wfirst, nruns, ncells, ncomp, ratio,
-                                       alpha);
+            k_interp<__nv_bfloat16><<<g, 256, 0, s>>>((__nv_bfloat16 *)fbase, (const __nv_bfloat16 *)cold,
+                                                                (const __nv_bfloat16 *)cnew, runs, rstart, wfirst,
+                                                                nruns, ncells, ncomp, ratio, alpha);
         }
     }
     return cudaGetLastError();
@@ -820,8 +844,10 @@ template <typename S, int RR, bool VEC>
 static void avgdown_t(const void *fbase, void *cbase, const AvgRegion *regs, const int *rstart, const int *wfirst,
                       int nregs, int ncells, int ncomp, cudaStream_t s) {
     const int blocks = (int)(((long long)ncells + 255) / 256);
-    const int g = persistent_grid(k_avgdown<S, RR, VEC>, 256, blocks);
-    k_avgdown<S, RR, VEC><<<g, 256, 0, s>>>((const S *)fbase, (S *)cbase, regs, rstart, wfirst, nregs, ncells, ncomp);
+    constexpr int U = RR == 2 ? 2 : 1;
+    const int g = persistent_grid(k_avgdown<S, RR, VEC, U>, 256, blocks);
+    k_avgdown<S, RR, VEC, U><<<g, 256, 0, s>>>((const S *)fbase, (S *)cbase, regs, rstart, wfirst, nregs, ncells,
+                                               ncomp);
 }
 
 template <typename S>
