@@ -303,7 +303,24 @@ def rk3_line(mf, torch, flush, args, hbm):
             "schedule": mf.mf_get_schedule(m.h)}
 
 
-def amr_line(mf, torch, flush, args):
+def amr_step_bytes(S, Nc, mgs, fboxes, r, nsub, g_interp):
+    """Algorithmic bytes of one coarse step of the two-level advance: each level's stencil reads
+    and writes its valid cells once and reads its face halo (radius 1), the fine level nsub
+    times; each interpolation writes its ghost cells and reads the coarse cells under them at
+    two time levels (1/r^3 as many); the average-down reads every fine cell and writes one
+    coarse cell per r^3."""
+    ext = fboxes[:, 3:] - fboxes[:, :3] + 1
+    Vf = int(ext.prod(axis=1).sum())
+    face_f = int((2 * (ext[:, 0] * ext[:, 1] + ext[:, 1] * ext[:, 2] + ext[:, 0] * ext[:, 2])).sum())
+    nb = (Nc // mgs) ** 3
+    coarse = 2 * Nc ** 3 + nb * 6 * mgs * mgs
+    fine = nsub * (2 * Vf + face_f)
+    interp = nsub * (g_interp + 2 * g_interp / r ** 3)
+    avg = Vf + Vf / r ** 3
+    return S * (coarse + fine + interp + avg)
+
+
+def amr_line(mf, torch, flush, args, hbm):
     """The two-level workload with refluxing: coarse 256^3 in 64 boxes of 64^3, a fine level at
     ratio 2 on the seeded sphere boxes, 2 fine substeps per coarse step, FP32, 50 coarse steps
     per bench step; cells counted once per coarse step on the coarse level and once per
@@ -334,9 +351,15 @@ def amr_line(mf, torch, flush, args):
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
     Vc = Nc ** 3
-    Vf = int(((fboxes[:, 3:] - fboxes[:, :3] + 1).prod(axis=1)).sum())
+    ext = fboxes[:, 3:] - fboxes[:, :3] + 1
+    Vf = int(ext.prod(axis=1).sum())
+    # interpolated ghost cells: the fine ghost shell less the cells other fine boxes fill
+    g_interp = int(((ext + 2).prod(axis=1) - ext.prod(axis=1)).sum()) - mf.mf_fb_regions(gf.h)[1]
+    step_bytes = amr_step_bytes(4, Nc, cfg["max_grid_size"], fboxes, r, nsub, g_interp)
     return {"value": (Vc + nsub * Vf) * n / (ms * 1e-3), "unit": "cell-updates/s (coarse per step + fine per substep)",
-            "ms_per_bench_step": ms,
+            "ms_per_bench_step": ms, "interp_ghost_cells": g_interp,
+            "step_bytes": step_bytes, "step_frac": step_bytes * n / (ms * 1e-3) / 1e9 / hbm,
+            "schedule": {"coarse": mf.mf_get_schedule(gc.h), "fine": mf.mf_get_schedule(gf.h)},
             "workload": "amr2lev256_sphere: coarse 256^3 (64 boxes of 64^3) + %d fine boxes (%d cells) at ratio 2, "
                         "2 substeps, refluxing, FP32, %d coarse steps per bench step" % (len(fboxes), Vf, n),
             "launches_per_bench_step": mf.mf_launch_count(gc.h)}
@@ -537,7 +560,7 @@ def run_ours(args, cfg, ws, rank, local):
         out["fp64_plain_per_box"] = {"value": vplain, "unit": UNIT,
                                      "launches_per_time_step": 2 * nbox}
         out["rk3_8th"] = rk3_line(mf, torch, flush, args, hbm)
-        out["amr2lev_reflux"] = amr_line(mf, torch, flush, args)
+        out["amr2lev_reflux"] = amr_line(mf, torch, flush, args, hbm)
         out["speedup_batched_vs_fp64_plain_per_box"] = value / vplain
         if rank == 0 and ws == 1:
             out["cpu_baseline"] = cpu_baseline(cfg)
@@ -569,8 +592,8 @@ def main():
             flush_rd.max()
 
         peaks, _ = measured_peaks()
-        line = rk3_line(mf, torch, flush, args, float(peaks["hbm_gbs"])) if args.only == "rk3_8th" \
-            else amr_line(mf, torch, flush, args)
+        hbm = float(peaks["hbm_gbs"])
+        line = rk3_line(mf, torch, flush, args, hbm) if args.only == "rk3_8th" else amr_line(mf, torch, flush, args, hbm)
         print(json.dumps({args.only: line}))
         return 0
     out = run_ours(args, cfg, ws, rank, local)

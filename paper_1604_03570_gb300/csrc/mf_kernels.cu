@@ -213,18 +213,24 @@ __global__ void __launch_bounds__(256) k_cf_coarse_flux(const S *__restrict__ ba
     }
 }
 
-template <typename S, int R>
+// NFF = r^2 fine faces per coarse face, a compile-time count so that all their loads issue
+// before the ordered sum.
+template <typename S, int R, int NFF>
 __global__ void __launch_bounds__(256) k_cf_fine_flux(const S *__restrict__ base, const CFace *__restrict__ faces,
-                                                      const FFace *__restrict__ ff, int n, int nff, int ncomp,
-                                                      RefluxW w, double *reg, int first) {
+                                                      const FFace *__restrict__ ff, int n, int ncomp, RefluxW w,
+                                                      double *reg, int first) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * ncomp; i += gridDim.x * blockDim.x) {
         const int e = i / ncomp, c = i - e * ncomp;
         const int f0 = faces[e].ffirst;
-        double sum = 0.0;
-        for (int k = 0; k < nff; ++k) {
+        double fl[NFF];
+#pragma unroll
+        for (int k = 0; k < NFF; ++k) {
             const FFace g = ff[f0 + k];
-            sum = __dadd_rn(sum, line_flux<S, R>(base + g.f_low + c * g.cstride, g.dstride));
+            fl[k] = line_flux<S, R>(base + g.f_low + c * g.cstride, g.dstride);
         }
+        double sum = 0.0;
+#pragma unroll
+        for (int k = 0; k < NFF; ++k) sum = __dadd_rn(sum, fl[k]);
         const double v = __dmul_rn(w.w[c], sum);
         reg[i] = first ? v : __dadd_rn(reg[i], v);
     }
@@ -262,17 +268,25 @@ static cudaError_t cf_coarse_s(int R, const void *base, const CFace *faces, int 
     return cudaGetLastError();
 }
 
-template <typename S>
-static cudaError_t cf_fine_s(int R, const void *base, const CFace *faces, const FFace *ff, int n, int nff, int ncomp,
+template <typename S, int NFF>
+static cudaError_t cf_fine_t(int R, const void *base, const CFace *faces, const FFace *ff, int n, int ncomp,
                              const RefluxW &w, double *reg, bool first, cudaStream_t s) {
     const int g = blocks_for((long long)n * ncomp);
     switch (R) {
-        case 1: k_cf_fine_flux<S, 1><<<g, 256, 0, s>>>((const S *)base, faces, ff, n, nff, ncomp, w, reg, first); break;
-        case 2: k_cf_fine_flux<S, 2><<<g, 256, 0, s>>>((const S *)base, faces, ff, n, nff, ncomp, w, reg, first); break;
-        case 4: k_cf_fine_flux<S, 4><<<g, 256, 0, s>>>((const S *)base, faces, ff, n, nff, ncomp, w, reg, first); break;
+        case 1: k_cf_fine_flux<S, 1, NFF><<<g, 256, 0, s>>>((const S *)base, faces, ff, n, ncomp, w, reg, first); break;
+        case 2: k_cf_fine_flux<S, 2, NFF><<<g, 256, 0, s>>>((const S *)base, faces, ff, n, ncomp, w, reg, first); break;
+        case 4: k_cf_fine_flux<S, 4, NFF><<<g, 256, 0, s>>>((const S *)base, faces, ff, n, ncomp, w, reg, first); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+template <typename S>
+static cudaError_t cf_fine_s(int R, const void *base, const CFace *faces, const FFace *ff, int n, int nff, int ncomp,
+                             const RefluxW &w, double *reg, bool first, cudaStream_t s) {
+    if (nff == 4) return cf_fine_t<S, 4>(R, base, faces, ff, n, ncomp, w, reg, first, s);
+    if (nff == 16) return cf_fine_t<S, 16>(R, base, faces, ff, n, ncomp, w, reg, first, s);
+    return cudaErrorInvalidValue;  // ratio 2 or 4
 }
 
 cudaError_t launch_cf_coarse_flux(int dtype, int R, const void *base, const CFace *faces, int n, int ncomp,

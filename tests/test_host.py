@@ -206,3 +206,18 @@ def test_eval_modes_box_equals_the_block_of_the_full_grid():
     full = synth.eval_modes((32, 32, 32), m)
     blk = synth.eval_modes_box(32, (5, 7, 9), (10, 12, 14), m)
     np.testing.assert_array_equal(full[9:19, 7:19, 5:19], blk)
+
+
+def test_two_level_step_bytes_by_hand():
+    """The benchmark's algorithmic bytes of one coarse step: coarse 32^3 in 8 boxes of 16^3,
+    one fine box of 16^3 at ratio 2, 2 substeps, FP32, its whole ghost shell interpolated."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    fb = np.array([[8, 8, 8, 23, 23, 23]])
+    g_interp = 18 ** 3 - 16 ** 3
+    coarse = 2 * 32 ** 3 + 8 * 6 * 16 * 16       # valid cells read + written, face halo read
+    fine = 2 * (2 * 16 ** 3 + 6 * 16 * 16)      # per substep
+    interp = 2 * (g_interp + 2 * g_interp / 8)  # ghost writes + coarse reads at two times
+    avg = 16 ** 3 + 16 ** 3 / 8
+    assert bench.amr_step_bytes(4, 32, 16, fb, 2, 2, g_interp) == 4 * (coarse + fine + interp + avg)
