@@ -47,7 +47,7 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="headline only (no FP64, e2e, CPU baseline)")
     p.add_argument("--tile", default=None, help="fixed tile 'x,y,z' instead of the autotuner (0 = whole box)")
     p.add_argument("--kernel", default="tma", choices=["tma", "global"], help="stencil kernel variant")
-    p.add_argument("--only", default=None, choices=["rk3_8th", "amr2lev_reflux"],
+    p.add_argument("--only", default=None, choices=["rk3_8th", "amr2lev_reflux", "manybox512"],
                    help="run only this secondary line (for profiling) and print it")
     p.add_argument("--schedule", default=None,
                    help="fixed schedule 'x,y,z,rows,stages,group_bytes' instead of the autotuner")
@@ -264,6 +264,51 @@ def whole_job_rate(ws, units_per_rank, seconds):
 
 
 RK3_CFG = dict(N=256, max_grid_size=64, ngrow=4, ncomp=1, R=4, nsteps=20, dtype="f32", nmodes=8, kmax=8)
+
+
+def manybox_step_bytes(S, C, boxes, R):
+    """Compulsory bytes of one time step of a level: every valid cell read and written once,
+    and the face halo of radius R read (the stencil's x halos come from the neighbour boxes and
+    its y/z face ghosts are written by the producing tiles, so no ghost region is copied as
+    such)."""
+    ext = boxes[:, 3:] - boxes[:, :3] + 1
+    V = int(ext.prod(axis=1).sum())
+    face = int((2 * (ext[:, 0] * ext[:, 1] + ext[:, 1] * ext[:, 2] + ext[:, 0] * ext[:, 2])).sum())
+    return S * C * (2 * V + R * face)
+
+
+def manybox_line(mf, torch, flush, args, hbm):
+    """512^3 with 2 components in 4096 and 32768 uneven boxes of 8^3-32^3, 2 ghost cells, the
+    13-point stencil, FP32, 50 time steps per bench step: the whole level in one launch per
+    phase of a captured graph, whatever the box count."""
+    cfg = synth.WORKLOADS["c5"]
+    N, R, C, n = cfg["N"], cfg["R"], cfg["ncomp"], cfg["nsteps"]
+    dense = synth.initial_field(cfg)
+    dt = synth.dt_for(cfg)
+    out = {}
+    for target in (4096, 32768):
+        boxes = synth.uneven_boxes(N, target)
+        g = mf.MultiFab([0, 0, 0], [N - 1] * 3, boxes=boxes, ncomp=C, ngrow=cfg["ngrow"], dtype="f32")
+        g.from_host(dense)
+        for _ in range(max(1, args.warmup)):
+            g.advance(R, [1.0] * C, dt, n)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush()
+            ev[k][0].record(g.stream)
+            g.advance(R, [1.0] * C, dt, n)
+            ev[k][1].record(g.stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+        step_bytes = manybox_step_bytes(4, C, boxes, R)
+        out[str(target)] = {"value": N ** 3 * n / (ms * 1e-3), "unit": UNIT, "ms_per_bench_step": ms,
+                            "boxes": target, "step_bytes": step_bytes,
+                            "step_frac": step_bytes * n / (ms * 1e-3) / 1e9 / hbm,
+                            "launches_per_bench_step": mf.mf_launch_count(g.h), "schedule": mf.mf_get_schedule(g.h)}
+        del g
+    out["workload"] = ("manybox512_c2: periodic 512^3, 2 components, 4096 / 32768 uneven boxes of 8^3-32^3, "
+                       "ngrow 2, 13-point stencil, FP32, %d steps per bench step" % n)
+    return out
 
 
 def rk3_line(mf, torch, flush, args, hbm):
@@ -559,8 +604,13 @@ def run_ours(args, cfg, ws, rank, local):
                                             "flops_per_cell": FLOPS_PER_CELL[R]}}
         out["fp64_plain_per_box"] = {"value": vplain, "unit": UNIT,
                                      "launches_per_time_step": 2 * nbox}
-        out["rk3_8th"] = rk3_line(mf, torch, flush, args, hbm)
-        out["amr2lev_reflux"] = amr_line(mf, torch, flush, args, hbm)
+        # secondary lines: a failure is reported in its own entry and does not void the headline
+        for key, line in (("rk3_8th", rk3_line), ("amr2lev_reflux", amr_line), ("manybox512", manybox_line)):
+            try:
+                out[key] = line(mf, torch, flush, args, hbm)
+            except Exception as e:  # noqa: BLE001
+                out[key] = {"error": "%s: %s" % (type(e).__name__, e)}
+                torch.cuda.synchronize()
         out["speedup_batched_vs_fp64_plain_per_box"] = value / vplain
         if rank == 0 and ws == 1:
             out["cpu_baseline"] = cpu_baseline(cfg)
@@ -593,7 +643,8 @@ def main():
 
         peaks, _ = measured_peaks()
         hbm = float(peaks["hbm_gbs"])
-        line = rk3_line(mf, torch, flush, args, hbm) if args.only == "rk3_8th" else amr_line(mf, torch, flush, args, hbm)
+        line = {"rk3_8th": rk3_line, "amr2lev_reflux": amr_line, "manybox512": manybox_line}[args.only](
+            mf, torch, flush, args, hbm)
         print(json.dumps({args.only: line}))
         return 0
     out = run_ours(args, cfg, ws, rank, local)

@@ -1072,11 +1072,35 @@ static void find_strips(mf_t *m, int R, std::vector<TileStrip> &st, std::vector<
             }
         }
     }
+    // a tile whose column has one owner uses its strip whether or not the rest of the face
+    // does; the fill copies only the parts of unserved faces that tiles without a strip read
     for (size_t i = 0; i < served.size(); ++i) served[i] = served[i] && touched[i];
-    // a tile uses a strip only if its whole face is served (so the face is never filled)
-    for (size_t w = 0; w < m->tiles.size(); ++w) {
-        if (st[w].lfab >= 0 && !served[2 * m->tiles[w].fab]) st[w].lfab = -1;
-        if (st[w].rfab >= 0 && !served[2 * m->tiles[w].fab + 1]) st[w].rfab = -1;
+}
+
+// The x-face FillBoundary region e (kind 0 or 1) restricted to the rows and planes of the tiles
+// of its destination box that read that x halo from ghost cells (no strip on that side).  The
+// tiles of different components may be cut at different planes and a fill task copies every
+// component, so the parts come from the tiles of all components (each distinct part once).
+// tiles_of[b]: the indices of box b's tiles.
+static void append_unserved_x(const mf_t *m, int e, const std::vector<TileStrip> &st,
+                              const std::vector<std::vector<int>> &tiles_of, std::vector<FbTask> &out) {
+    const FbEntry &en = m->fb[e];
+    const int side = m->fb_kind[e];
+    const auto &cr = m->fb_corner[e];
+    const Box &B = m->boxes[en.dfab];
+    std::vector<std::array<int, 4>> parts;
+    for (int w : tiles_of[en.dfab]) {
+        const Tile &t = m->tiles[w];
+        if ((side == 0 ? st[w].lfab : st[w].rfab) >= 0) continue;
+        const int ylo = std::max(cr[1], B.lo[1] + t.y0), yhi = std::min(cr[1] + en.n[1], B.lo[1] + t.y0 + t.ty);
+        const int zlo = std::max(cr[2], B.lo[2] + t.z0), zhi = std::min(cr[2] + en.n[2], B.lo[2] + t.z0 + t.tz);
+        if (ylo < yhi && zlo < zhi) parts.push_back({ylo, yhi, zlo, zhi});
+    }
+    std::sort(parts.begin(), parts.end());
+    parts.erase(std::unique(parts.begin(), parts.end()), parts.end());
+    for (const auto &q : parts) {
+        const int lo[3] = {0, q[0] - cr[1], q[2] - cr[2]}, n[3] = {en.n[0], q[1] - q[0], q[3] - q[2]};
+        append_fill_tasks(m, clip_entry(m, e, lo, n), out);
     }
 }
 
@@ -1190,19 +1214,22 @@ static int build_tma(mf_t *m, int R) {
             if (r != CUDA_SUCCESS) return fail(MF_ECUDA, "cuTensorMapEncodeTiled (strip) failed (%d)", (int)r);
         }
     // the fill inside the advance: faces only (the star stencil reads no edge or corner), and
-    // no x face that the stencil pulls from the neighbour
-    std::vector<char> use(m->fb.size(), 0);
+    // of the x faces only the parts that tiles without a strip read
+    std::vector<std::vector<int>> tiles_of(m->boxes.size());
+    for (size_t w = 0; w < m->tiles.size(); ++w) tiles_of[m->tiles[w].fab].push_back((int)w);
+    m->fbtasks_adv.clear();
     for (size_t e = 0; e < m->fb.size(); ++e) {
         const int k = m->fb_kind[e];
-        if (k == 6) continue;
-        if (k < 2 && served[2 * (size_t)m->fb[e].dfab + k]) continue;
-        use[e] = 1;
+        if (k == 6 || (k < 2 && served[2 * (size_t)m->fb[e].dfab + k])) continue;
+        if (k < 2) append_unserved_x(m, (int)e, strips, tiles_of, m->fbtasks_adv);
+        else append_fill_tasks(m, m->fb[e], m->fbtasks_adv);
     }
-    make_fill_tasks(m, use, m->fbtasks_adv);
     // ghost push: every y/z face region is written by the tiles that compute its source cells;
-    // only x faces not served by strips remain for the fill of later steps
+    // the fill of later steps copies only the x faces not served by strips and the regions of
+    // tiles with more than kMaxPush pieces (such a tile pushes nothing)
     std::vector<PushPiece> pieces;
-    bool push_ok = true;
+    std::vector<int> piece_entry;     // the FillBoundary region of each piece
+    std::vector<char> unpushed(m->fb.size(), 0);
     {
         std::vector<std::vector<int>> by_src(m->boxes.size());
         for (size_t e = 0; e < m->fb.size(); ++e)
@@ -1235,16 +1262,22 @@ static int build_tma(mf_t *m, int R) {
                 pp.full_row = pp.x0 == 0 && pp.nx == t.tx && dx == m->boxes[en.dfab].lo[0] &&
                               m->boxes[en.dfab].len(0) == t.tx;
                 pieces.push_back(pp);
+                piece_entry.push_back(e);
             }
             strips[w].pcount = (int)pieces.size() - strips[w].pfirst;
-            if (strips[w].pcount > kMaxPush) push_ok = false;
+            if (strips[w].pcount > kMaxPush) {  // this tile pushes nothing; the fill copies its regions
+                for (size_t i = strips[w].pfirst; i < pieces.size(); ++i) unpushed[piece_entry[i]] = 1;
+                pieces.resize(strips[w].pfirst);
+                piece_entry.resize(strips[w].pfirst);
+                strips[w].pcount = 0;
+            }
         }
-        std::vector<char> res(m->fb.size(), 0);
+        m->fbtasks_res.clear();
         for (size_t e = 0; e < m->fb.size(); ++e) {
             const int k = m->fb_kind[e];
-            res[e] = k < 2 && !served[2 * (size_t)m->fb[e].dfab + k];
+            if (k < 2 && !served[2 * (size_t)m->fb[e].dfab + k]) append_unserved_x(m, (int)e, strips, tiles_of, m->fbtasks_res);
+            else if (unpushed[e]) append_fill_tasks(m, m->fb[e], m->fbtasks_res);
         }
-        make_fill_tasks(m, res, m->fbtasks_res);
     }
     int rc;
     if ((rc = m->d_maps.upload(maps, m->stream))) return rc;
@@ -1265,7 +1298,7 @@ static int build_tma(mf_t *m, int R) {
     m->tma_strip_w = XW;
     m->tma_ok = true;
     m->tma_strips = true;
-    m->tma_push = push_ok;
+    m->tma_push = true;
     return 0;
 }
 

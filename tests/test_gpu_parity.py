@@ -169,6 +169,41 @@ def test_advance_fp64_uneven_boxes_matches_oracle(R):
     assert rel_err(g.to_host(), ref) <= FP64_TOL
 
 
+def _crowded_boxes():
+    """One 16^3 box among 448 boxes of 4^3 in a 32^3 domain: the big box's tile is the source of
+    64 ghost-face pieces of its small neighbours, more than a tile can push."""
+    boxes = [[0, 0, 0, 15, 15, 15]]
+    for z in range(0, 32, 4):
+        for y in range(0, 32, 4):
+            for x in range(0, 32, 4):
+                if x < 16 and y < 16 and z < 16:
+                    continue
+                boxes.append([x, y, z, x + 3, y + 3, z + 3])
+    return np.array(boxes, dtype=np.int32)
+
+
+@pytest.mark.parametrize("R", [1, 2])
+def test_advance_with_a_crowded_tile_matches_oracle_and_the_global_kernel(R):
+    """A tile with too many ghost-push pieces pushes nothing and leaves its regions to the fill
+    of the next step, while its neighbours push theirs: FP64 within the oracle tolerance, and
+    the same bits as the global-memory kernel."""
+    lo, hi = [0, 0, 0], [31, 31, 31]
+    boxes = _crowded_boxes()
+    dt = {1: 0.15, 2: 0.1125}[R] / (32 * 32)
+    dense = synth.eval_modes((32, 32, 32), synth.sine_modes(1604, 50 + R, 8, 8))[None]
+    outs = []
+    for kern in (mf.MF_KERNEL_TMA, mf.MF_KERNEL_GLOBAL):
+        g = gpu_level(lo, hi, boxes=boxes, ngrow=R, dtype="f64")
+        g.set_tile((0, 0, 0))
+        mf.mf_set_kernel(g.h, kern)
+        g.from_host(dense)
+        g.advance(R, [1.0], dt, 5)
+        outs.append(g.to_host())
+    ref = _oracle_advance(boxes, lo, hi, R, 1, R, dt * 32.0 * 32.0, 5, dense)
+    assert rel_err(outs[0], ref) <= FP64_TOL
+    np.testing.assert_array_equal(outs[0], outs[1])
+
+
 def test_heat64_fp64_workload_matches_oracle():
     """The 64^3 / 8 boxes of 32^3 / 10-step FP64 workload at full size."""
     cfg = synth.WORKLOADS["c1"]

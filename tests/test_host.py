@@ -221,3 +221,15 @@ def test_two_level_step_bytes_by_hand():
     interp = 2 * (g_interp + 2 * g_interp / 8)  # ghost writes + coarse reads at two times
     avg = 16 ** 3 + 16 ** 3 / 8
     assert bench.amr_step_bytes(4, 32, 16, fb, 2, 2, g_interp) == 4 * (coarse + fine + interp + avg)
+
+
+def test_level_step_bytes_by_hand():
+    """The benchmark's compulsory bytes of one step of a level of uneven boxes: two boxes of
+    8x16x32 and 32x32x32, 2 components, radius 2, FP32."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    boxes = np.array([[0, 0, 0, 7, 15, 31], [8, 0, 0, 39, 31, 31]])
+    V = 8 * 16 * 32 + 32 ** 3
+    face = 2 * (8 * 16 + 16 * 32 + 8 * 32) + 6 * 32 * 32
+    assert bench.manybox_step_bytes(4, 2, boxes, 2) == 4 * 2 * (2 * V + 2 * face)
