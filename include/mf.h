@@ -166,11 +166,15 @@ int mf_fill_boundary(mf_t *mf);
  * (1 - alpha) * crse_old + alpha * crse_new (current time levels of the two handles, which
  * may be the same handle).  The coarse level must cover its domain, have ngrow >= 1, have
  * its ghosts filled, and fine domain = ratio * coarse domain.  Runs on the fine handle's stream.
+ * Arithmetic: FP64 for FP64 levels (the definition's order of operations, the weight product
+ * (wz wy) wx, terms summed z, y, x ascending); FP32 for FP32 and BF16 levels, same order.
  */
 int mf_interp_cf(mf_t *fine, const mf_t *crse_old, const mf_t *crse_new, double alpha, int ratio);
 
 /* mf_average_down -- every coarse valid cell whose children are all fine valid cells becomes
- * their mean (current time levels).  Runs on the coarse handle's stream. */
+ * their mean (current time levels): the r^3 children summed z, y, x ascending, times 1/r^3, in
+ * FP64 for FP64 levels and FP32 for FP32/BF16 levels.  ratio 2 or 4; fine boxes must start and
+ * end on multiples of ratio (MF_EINVAL otherwise).  Runs on the coarse handle's stream. */
 int mf_average_down(const mf_t *fine, mf_t *crse, int ratio);
 
 /*
@@ -180,6 +184,10 @@ int mf_average_down(const mf_t *fine, mf_t *crse, int ratio);
  * tiles go through one persistent launch per phase; the whole advance is captured once as a
  * CUDA graph and replayed.  With MF_PLAIN_PER_BOX it runs the untiled per-box baseline.
  * lam_c = D_c dt / dx^2 = D_c dt N_x^2.  Returns MF_EUNSTABLE if max_c lam_c * 3 |sigma_R(pi)| > 2.
+ * Only the ghost cells the stencil reads are exchanged: x halos may be read straight from the
+ * neighbour box, and the stencil may write the y/z face ghosts of the level it produces (the
+ * autotuner times both ways).  The ghost cells of the result are therefore not all current:
+ * call mf_fill_boundary before reading them.
  */
 int mf_advance(mf_t *mf, const mf_stencil *st, double dt, int nsteps);
 
@@ -196,6 +204,9 @@ int mf_advance(mf_t *mf, const mf_stencil *st, double dt, int nsteps);
  * region is on the cell's high side, -1 on its low side; fluxes in FP64 from the coarse state at
  * the start of the step and from each substep's fine state after its fill and interpolation.
  * The fine boxes must consist of whole coarse cells (MF_EINVAL otherwise).
+ * Inside the advance each level exchanges only the ghost cells that are read (the coarse level:
+ * the stencil's faces and the cells the interpolation and the flux registers read); the ghost
+ * cells of the results are not all current.
  */
 int mf_amr_advance(mf_t *crse, mf_t *fine, const mf_stencil *st, double dt_crse, int ncrse_steps, int nsub,
                    int ratio);
