@@ -162,7 +162,7 @@ def run_reference(args, cfg):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-def cpu_baseline(cfg, budget_s=15.0):
+def cpu_baseline(cfg, target_s=15.0):
     import oracle
     N = cfg["N"]
     lo, hi = [0, 0, 0], [N - 1] * 3
@@ -172,7 +172,7 @@ def cpu_baseline(cfg, budget_s=15.0):
     t0 = time.perf_counter()
     u = oracle.advance(L, u, cfg["R"], lam, 1)
     t1 = time.perf_counter() - t0
-    n = max(1, min(cfg["nsteps"], int(budget_s / max(t1, 1e-3)) - 1))
+    n = max(1, min(cfg["nsteps"], int(target_s / max(t1, 1e-3)) - 1))
     t0 = time.perf_counter()
     oracle.advance(L, u, cfg["R"], lam, n)
     t = time.perf_counter() - t0

@@ -1462,7 +1462,7 @@ static int autotune(mf_t *m, int R, bool fp64diff, const double *lam) {
         *ms /= (float)n;
         return 0;
     };
-    // round 1: every candidate, 3 launches; round 2: the four fastest, 3 interleaved passes of
+    // first pass: every candidate, 3 launches; second: the four fastest, 3 interleaved passes of
     // 6 launches each, keeping each candidate's best pass
     std::vector<std::pair<float, size_t>> r1;
     for (size_t i = 0; i < cands.size(); ++i) {

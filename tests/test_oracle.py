@@ -54,7 +54,7 @@ def test_coefficients_match_published_table(R):
 
 @pytest.mark.parametrize("R", [1, 2, 4])
 def test_flux_coefficients_telescoping(R):
-    """b_m = sum_{j>=m} c_j, printed values of the survey's reading for R = 2 and 4."""
+    """b_m = sum_{j>=m} c_j, summed by hand from the classical weights for R = 2 and 4."""
     b = coeffs.flux_coefficients(R)
     expected = {1: [Fraction(1)], 2: [Fraction(15, 12), Fraction(-1, 12)],
                 4: [Fraction(205, 144), Fraction(-127, 720), Fraction(17, 720), Fraction(-1, 560)]}[R]
