@@ -1440,9 +1440,16 @@ static int autotune(mf_t *m, int R, bool fp64diff, const double *lam) {
             cands.push_back({t, 2, 0, 16});
         }
     }
-    cudaEvent_t e0, e1;
-    CU(cudaEventCreate(&e0));
-    CU(cudaEventCreate(&e1));
+    struct Events {  // destroyed on every return
+        cudaEvent_t a = nullptr, b = nullptr;
+        ~Events() {
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+        }
+    } ev;
+    CU(cudaEventCreate(&ev.a));
+    CU(cudaEventCreate(&ev.b));
+    cudaEvent_t e0 = ev.a, e1 = ev.b;
     // time one candidate: a warm-up launch (also encodes the tensor maps), then n launches,
     // with the ghost push on as in mf_advance (the other level is scratch here)
     auto time_cand = [&](const Cand &c, int n, float *ms) -> int {
@@ -1468,7 +1475,7 @@ static int autotune(mf_t *m, int R, bool fp64diff, const double *lam) {
     for (size_t i = 0; i < cands.size(); ++i) {
         float ms = 0;
         int rc = time_cand(cands[i], 3, &ms);
-        if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
+        if (rc) return rc;
         r1.push_back({ms, i});
     }
     std::sort(r1.begin(), r1.end());
@@ -1478,7 +1485,7 @@ static int autotune(mf_t *m, int R, bool fp64diff, const double *lam) {
         for (size_t j = 0; j < top; ++j) {
             float ms = 0;
             int rc = time_cand(cands[r1[j].second], 6, &ms);
-            if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
+            if (rc) return rc;
             r2[j] = std::min(r2[j], ms);
         }
     Cand bc = cands[r1[std::min_element(r2.begin(), r2.end()) - r2.begin()].second];
@@ -1514,8 +1521,6 @@ static int autotune(mf_t *m, int R, bool fp64diff, const double *lam) {
         }
         m->push_pref = tp <= tf;
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     return rc;
 }
 
