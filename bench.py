@@ -604,8 +604,10 @@ def run_ours(args, cfg, ws, rank, local):
                                             "flops_per_cell": FLOPS_PER_CELL[R]}}
         out["fp64_plain_per_box"] = {"value": vplain, "unit": UNIT,
                                      "launches_per_time_step": 2 * nbox}
-        # secondary lines: a failure is reported in its own entry and does not void the headline
-        for key, line in (("rk3_8th", rk3_line), ("amr2lev_reflux", amr_line), ("manybox512", manybox_line)):
+        # secondary lines, on one GPU only (the scaling runs compare the headline); a failure is
+        # reported in its own entry and does not void the headline
+        secondary = (("rk3_8th", rk3_line), ("amr2lev_reflux", amr_line), ("manybox512", manybox_line))
+        for key, line in (secondary if ws == 1 else ()):
             try:
                 out[key] = line(mf, torch, flush, args, hbm)
             except Exception as e:  # noqa: BLE001
