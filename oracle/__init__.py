@@ -29,6 +29,11 @@ What each function follows (section of arXiv 1604.03570):
                          readings are trilinear space / linear time interpolation of uncovered
                          fine ghosts, the mean of the children, and a coarse step followed by
                          ``nsub`` fine substeps and an average-down.
+* ``CFFaces`` / ``cf_coarse_flux`` / ``cf_fine_flux`` / ``reflux`` -- flux correction at the
+                         coarse-fine interface of the subcycled two-level step (the paper names
+                         it without a formula; read as Berger-Colella): the coarse faces of
+                         uncovered cells next to the fine region, their coarse flux and the sum of
+                         their r^2 fine face fluxes, and the correction of the coarse cell.
 
 The C part (``mf_oracle.c``) is compiled with ``gcc -O2 -ffp-contract=off`` on first use.
 """
