@@ -327,7 +327,6 @@ struct mf {
 
 static void build_layout(mf_t *m) {
     const int g = m->ngrow, S = m->esize;
-    const int A = 16 / S;                  // elements per 16 bytes
     const long long align = 256 / S;       // FArrayBox start alignment in elements
     long long off = 0;
     m->fabs.clear();
