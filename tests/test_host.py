@@ -233,3 +233,18 @@ def test_level_step_bytes_by_hand():
     V = 8 * 16 * 32 + 32 ** 3
     face = 2 * (8 * 16 + 16 * 32 + 8 * 32) + 6 * 32 * 32
     assert bench.manybox_step_bytes(4, 2, boxes, 2) == 4 * 2 * (2 * V + 2 * face)
+
+
+@pytest.mark.parametrize("N,mgs,g,C,dtype", [(256, 64, 1, 1, "f32"), (512, 128, 4, 5, "f32"), (64, 32, 1, 1, "f64"),
+                                              (256, 64, 2, 2, "bf16")])
+def test_bench_level_bytes_match_the_library_layout(N, mgs, g, C, dtype):
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    import paper_1604_03570_gb300 as mf
+    h = mf.mf_create([0, 0, 0], [N - 1] * 3, mgs, C, g, dtype)
+    try:
+        S = {"f64": 8, "f32": 4, "bf16": 2}[dtype]
+        assert bench.level_bytes(N, mgs, g, C, S) == mf.mf_bytes(h) // 2
+    finally:
+        mf.mf_destroy(h)
