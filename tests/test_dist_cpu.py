@@ -90,3 +90,13 @@ def test_reference_arm_prints_the_contract_line():
     import synth
     assert line["config"] == bench.workload_config(synth.WORKLOADS["c2"])
     assert "%" not in json.dumps(line["config"])
+
+
+def test_cpu_baseline_entry():
+    """The GPU arm's cpu_baseline entry: the oracle timed on a bounded sample of the workload."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import synth
+    cb = bench.cpu_baseline(synth.WORKLOADS["c2"], target_s=0.5)
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] > 0 and cb["unit"] == bench.UNIT
+    assert cb["sample"].startswith("1 of the 100 FP64 time steps")
