@@ -357,16 +357,18 @@ def _level_from_fn(level, N, fn):
     return level.from_dense(fn(xx, y, z)[None])
 
 
-def test_interp_reproduces_linear_field_exactly():
+@pytest.mark.parametrize("alpha", [0.5, 0.25, 0.75])
+def test_interp_reproduces_linear_field_exactly(alpha):
     """Trilinear interpolation is exact on linear data (dyadic values, exact bits), and the
-    time blend at alpha = 1/2 of two linear fields is their mean."""
+    time blend of two linear fields is (1 - alpha) old + alpha new (at alpha != 1/2 a swap of
+    the two levels shows)."""
     Nc = 8
     crse, fine = _fine_setup(Nc)
     f_old = lambda x, y, z: 0.5 + 0.25 * x - 0.75 * y + 0.125 * z
     f_new = lambda x, y, z: 1.5 - 0.5 * x + 0.25 * y + 0.375 * z
     c_old, c_new = _level_from_fn(crse, Nc, f_old), _level_from_fn(crse, Nc, f_new)
     fd = fine.alloc()
-    n = oracle.interp_cf(fine, crse, 2, 0.5, c_old, c_new, fd)
+    n = oracle.interp_cf(fine, crse, 2, alpha, c_old, c_new, fd)
     xf = (np.arange(2 * Nc) + 0.5) / (2 * Nc)
     checked = 0
     for b, B in enumerate(fine.boxes):
@@ -378,7 +380,7 @@ def test_interp_reproduces_linear_field_exactly():
                     if np.isnan(v):
                         continue
                     x, y, z = xf[i], xf[j], xf[k]
-                    assert v == 0.5 * f_old(x, y, z) + 0.5 * f_new(x, y, z)
+                    assert v == (1 - alpha) * f_old(x, y, z) + alpha * f_new(x, y, z)
                     checked += 1
     assert checked == n > 0
 
