@@ -199,6 +199,19 @@ def test_set_tile_roundtrip():
         mf.mf_destroy(h)
 
 
+@pytest.mark.parametrize("rows,stages,gb", [(3, 0, 16), (0, 3, 16), (0, 32, 16), (0, 0, 24)])
+def test_set_schedule_rejects_out_of_range_values(rows, stages, gb):
+    """Rows per thread 1-2, ring slots a power of two up to 16, row groups of 16 or 32 bytes."""
+    h = mf.mf_create([0, 0, 0], [63, 63, 63], 32, 1, 1, "f32")
+    try:
+        with pytest.raises(mf.MFError) as e:
+            mf.mf_set_schedule(h, rows, stages, gb)
+        assert e.value.code == mf.MF_EINVAL
+        mf.mf_set_schedule(h, 2, 8, 32)  # in range: accepted before any device memory exists
+    finally:
+        mf.mf_destroy(h)
+
+
 def test_eval_modes_box_equals_the_block_of_the_full_grid():
     """The sub-box evaluator of the seeded inputs gives the same bits as the full grid."""
     import synth
