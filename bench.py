@@ -47,7 +47,7 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="headline only (no FP64, e2e, CPU baseline)")
     p.add_argument("--tile", default=None, help="fixed tile 'x,y,z' instead of the autotuner (0 = whole box)")
     p.add_argument("--kernel", default="tma", choices=["tma", "global"], help="stencil kernel variant")
-    p.add_argument("--only", default=None, choices=["rk3_8th", "amr2lev_reflux", "manybox512"],
+    p.add_argument("--only", default=None, choices=["bf16_batched", "rk3_8th", "amr2lev_reflux", "manybox512"],
                    help="run only this secondary line (for profiling) and print it")
     p.add_argument("--schedule", default=None,
                    help="fixed schedule 'x,y,z,rows,stages,group_bytes' instead of the autotuner")
@@ -322,6 +322,25 @@ def manybox_line(mf, torch, flush, args, hbm):
     out["workload"] = ("manybox512_c2: periodic 512^3, 2 components, 4096 / 32768 uneven boxes of 8^3-32^3, "
                        "ngrow 2, 13-point stencil, FP32, %d steps per bench step" % n)
     return out
+
+
+def bf16_line(mf, torch, flush, args, hbm):
+    """The headline grid (256^3 in 64 boxes of 64^3, 7-point, 100 steps per bench step) stored in
+    BF16 with FP32 arithmetic: throughput, compulsory bytes per step (valid cells read and
+    written, face halo read) and their fraction of the measured peak."""
+    cfg = synth.WORKLOADS["c2"]
+    N, R, n, mgs = cfg["N"], cfg["R"], cfg["nsteps"], cfg["max_grid_size"]
+    dt = synth.dt_for(cfg)
+    g = mf.MultiFab([0, 0, 0], [N - 1] * 3, max_grid_size=mgs, ncomp=1, ngrow=cfg["ngrow"], dtype="bf16")
+    g.from_host(synth.initial_field(cfg))
+    for _ in range(max(1, args.warmup)):
+        g.advance(R, [1.0], dt, n)
+    t = time_advances(g, R, [1.0], dt, n, args.steps, flush)
+    ms = sum(t) / len(t)
+    step_bytes = 2 * (2 * N ** 3 + (N // mgs) ** 3 * 6 * R * mgs * mgs)
+    return {"value": N ** 3 * n / (ms * 1e-3), "unit": UNIT, "ms_per_bench_step": ms, "step_bytes": step_bytes,
+            "step_frac": step_bytes * n / (ms * 1e-3) / 1e9 / hbm, "schedule": mf.mf_get_schedule(g.h),
+            "workload": "heat256_64x64 in BF16 storage (FP32 arithmetic), %d steps per bench step" % n}
 
 
 def rk3_line(mf, torch, flush, args, hbm):
@@ -618,7 +637,8 @@ def run_ours(args, cfg, ws, rank, local):
                                      "launches_per_time_step": 2 * nbox}
         # secondary lines, on one GPU only (the scaling runs compare the headline); a failure is
         # reported in its own entry and does not void the headline
-        secondary = (("rk3_8th", rk3_line), ("amr2lev_reflux", amr_line), ("manybox512", manybox_line))
+        secondary = (("bf16_batched", bf16_line), ("rk3_8th", rk3_line), ("amr2lev_reflux", amr_line),
+                     ("manybox512", manybox_line))
         for key, line in (secondary if ws == 1 else ()):
             try:
                 out[key] = line(mf, torch, flush, args, hbm)
@@ -657,7 +677,8 @@ def main():
 
         peaks, _ = measured_peaks()
         hbm = float(peaks["hbm_gbs"])
-        line = {"rk3_8th": rk3_line, "amr2lev_reflux": amr_line, "manybox512": manybox_line}[args.only](
+        line = {"bf16_batched": bf16_line, "rk3_8th": rk3_line, "amr2lev_reflux": amr_line,
+                "manybox512": manybox_line}[args.only](
             mf, torch, flush, args, hbm)
         print(json.dumps({args.only: line}))
         return 0
