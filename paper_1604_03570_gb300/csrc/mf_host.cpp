@@ -201,6 +201,8 @@ struct CellList {
     }
 };
 
+// Coarse-fine interpolation plan of a fine level against one coarse layout: the runs of fine
+// ghost cells no fine box covers, numbered cell by cell.
 struct InterpPlan {
     const mf_t *crse = nullptr;
     int ratio = 0;
@@ -219,6 +221,7 @@ struct RefluxPlan {
     std::vector<CCell> cells;
     DevBuf d_faces, d_ff, d_cells, d_regc, d_regf;
 };
+
 // The coarse level's ghost exchange inside the two-level advance, limited to the ghost cells
 // that are read.  Per FillBoundary region of the coarse level: the bounding box of its cells that
 // the interpolation reads (ip), that the interpolation or the coarse flux registers read (cf),
@@ -236,6 +239,8 @@ struct AmrFill {
     DevBuf d_first, d_next, d_post;
 };
 
+// Average-down plan of a coarse level from one fine level: the coarse regions under the fine
+// boxes, numbered cell by cell.
 struct AvgPlan {
     const mf_t *fine = nullptr;
     int ratio = 0;
