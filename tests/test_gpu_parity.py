@@ -431,7 +431,10 @@ def test_average_down_matches_oracle(dtype, ratio, C):
         np.testing.assert_array_equal(got[:, ~covered], cden[:, ~covered])  # nothing else written
 
 
-def test_amr_advance_fp64_matches_oracle():
+@pytest.mark.parametrize("kernel", [mf.MF_KERNEL_TMA, mf.MF_KERNEL_GLOBAL])
+def test_amr_advance_fp64_matches_oracle(kernel):
+    """Both stencil kernels: the TMA one takes x halos from neighbour boxes, pushes face ghosts
+    and leaves the rest to restricted fills; the global one reads every ghost cell."""
     Nc, clo, chi, cboxes, flo, fhi, fboxes = _two_level()
     modes = synth.sine_modes(1604, 50, 4, 3)
     cden = synth.eval_modes((Nc, Nc, Nc), modes)[None]
@@ -439,6 +442,8 @@ def test_amr_advance_fp64_matches_oracle():
     dt_c = 0.075 / (Nc * Nc)
     gc = gpu_level(clo, chi, boxes=cboxes, ngrow=1)
     gf = gpu_level(flo, fhi, boxes=fboxes, ngrow=1)
+    mf.mf_set_kernel(gc.h, kernel)
+    mf.mf_set_kernel(gf.h, kernel)
     gc.from_host(cden)
     gf.from_host(fden)
     mf.mf_amr_advance(gc.h, gf.h, 1, [1.0], dt_c, 3, 2, 2)
