@@ -430,8 +430,7 @@ def amr_line(mf, torch, flush, args, hbm):
     Vc = Nc ** 3
     ext = fboxes[:, 3:] - fboxes[:, :3] + 1
     Vf = int(ext.prod(axis=1).sum())
-    # interpolated ghost cells: the fine ghost shell less the cells other fine boxes fill
-    g_interp = int(((ext + 2).prod(axis=1) - ext.prod(axis=1)).sum()) - mf.mf_fb_regions(gf.h)[1]
+    g_interp = mf.mf_interp_cells(gf.h, gc.h, r)[0]  # interpolated fine ghost cells per substep
     step_bytes = amr_step_bytes(4, Nc, cfg["max_grid_size"], fboxes, r, nsub, g_interp)
     return {"value": (Vc + nsub * Vf) * n / (ms * 1e-3), "unit": "cell-updates/s (coarse per step + fine per substep)",
             "ms_per_bench_step": ms, "interp_ghost_cells": g_interp,

@@ -171,6 +171,12 @@ int mf_fill_boundary(mf_t *mf);
  */
 int mf_interp_cf(mf_t *fine, const mf_t *crse_old, const mf_t *crse_new, double alpha, int ratio);
 
+/* mf_interp_cells -- the number of fine ghost cells (per component) that mf_interp_cf writes:
+ * the ghost cells of the fine boxes whose point lies in no fine box.  *runs_out (may be NULL)
+ * gets the number of runs of the interpolation work list.  Host lists only: needs no attached
+ * memory.  Negative error code (MF_EINVAL) for a bad ratio or layouts that do not nest. */
+long long mf_interp_cells(const mf_t *fine, const mf_t *crse, int ratio, long long *runs_out);
+
 /* mf_average_down -- every coarse valid cell whose children are all fine valid cells becomes
  * their mean (current time levels): the r^3 children summed z, y, x ascending, times 1/r^3, in
  * FP64 for FP64 levels and FP32 for FP32/BF16 levels.  ratio 2 or 4; fine boxes must start and

@@ -2303,6 +2303,16 @@ extern "C" int mf_interp_cf(mf_t *fine, const mf_t *crse_old, const mf_t *crse_n
                           fine->stream);
 }
 
+extern "C" long long mf_interp_cells(const mf_t *fine, const mf_t *crse, int ratio, long long *runs_out) {
+    if (!fine || !crse) return fail(MF_EINVAL, "null handle");
+    if (ratio != 2 && ratio != 4) return fail(MF_EINVAL, "ratio must be 2 or 4");
+    InterpPlan plan;  // host lists only: no device memory, no attach needed
+    int rc = build_interp(const_cast<mf_t *>(fine), crse, ratio, plan);
+    if (rc) return rc;
+    if (runs_out) *runs_out = (long long)plan.runs.size();
+    return plan.cells.ncells;
+}
+
 extern "C" int mf_average_down(const mf_t *fine, mf_t *crse, int ratio) {
     int rc = need_attached(crse);
     if (rc) return rc;

@@ -261,3 +261,46 @@ def test_bench_level_bytes_match_the_library_layout(N, mgs, g, C, dtype):
         assert bench.level_bytes(N, mgs, g, C, S) == mf.mf_bytes(h) // 2
     finally:
         mf.mf_destroy(h)
+
+
+@pytest.mark.parametrize("ratio,g", [(2, 1), (2, 2), (4, 1), (4, 2)])
+def test_interp_work_list_holds_exactly_the_oracles_cells(ratio, g):
+    """The interpolation work list (built on the host, no device memory) holds as many cells as
+    the oracle interpolates: the fine ghost cells whose point lies in no fine box."""
+    Nc = 16
+    base = np.array([[4, 4, 4, 7, 11, 7], [8, 4, 4, 11, 7, 9], [0, 0, 12, 3, 3, 15]])
+    fb = np.concatenate([base[:, :3] * ratio, (base[:, 3:] + 1) * ratio - 1], axis=1).astype(np.int32)
+    hc = mf.mf_create([0, 0, 0], [Nc - 1] * 3, 8, 1, 1, "f64")
+    hf = mf.mf_create_boxes([0, 0, 0], [ratio * Nc - 1] * 3, fb, 1, g, "f64")
+    try:
+        n, runs = mf.mf_interp_cells(hf, hc, ratio)
+        CL = oracle.Level(oracle.chop([0, 0, 0], [Nc - 1] * 3, 8), [0, 0, 0], [Nc - 1] * 3, 1, 1)
+        FL = oracle.Level(fb, [0, 0, 0], [ratio * Nc - 1] * 3, g, 1)
+        assert n == oracle.interp_cf(FL, CL, ratio, 0.0, CL.alloc(), CL.alloc(), FL.alloc()) > 0
+        assert 0 < runs < n  # runs of several cells
+        with pytest.raises(mf.MFError) as e:
+            mf.mf_interp_cells(hf, hc, 3)
+        assert e.value.code == mf.MF_EINVAL
+    finally:
+        mf.mf_destroy(hf)
+        mf.mf_destroy(hc)
+
+
+def test_interp_work_list_of_the_sphere_workload():
+    """The two-level workload: the work list, the oracle and the bench's shell count agree."""
+    cfg = synth.WORKLOADS["c4"]
+    Nc, r = cfg["N"], cfg["ratio"]
+    fb = synth.sphere_fine_boxes(Nc, ratio=r)
+    hc = mf.mf_create([0, 0, 0], [Nc - 1] * 3, cfg["max_grid_size"], 1, 1, "f32")
+    hf = mf.mf_create_boxes([0, 0, 0], [r * Nc - 1] * 3, fb, 1, 1, "f32")
+    try:
+        n, runs = mf.mf_interp_cells(hf, hc, r)
+        ext = fb[:, 3:] - fb[:, :3] + 1
+        assert n == int(((ext + 2).prod(axis=1) - ext.prod(axis=1)).sum()) - mf.mf_fb_regions(hf)[1]
+        CL = oracle.Level(oracle.chop([0, 0, 0], [Nc - 1] * 3, cfg["max_grid_size"]), [0, 0, 0], [Nc - 1] * 3, 1, 1)
+        FL = oracle.Level(fb, [0, 0, 0], [r * Nc - 1] * 3, 1, 1)
+        assert n == oracle.interp_cf(FL, CL, r, 0.0, CL.alloc(), CL.alloc(), FL.alloc())
+        assert n / runs > 10  # runs follow the ghost slabs, not x alone
+    finally:
+        mf.mf_destroy(hf)
+        mf.mf_destroy(hc)
