@@ -177,6 +177,14 @@ int mf_interp_cf(mf_t *fine, const mf_t *crse_old, const mf_t *crse_new, double 
  * memory.  Negative error code (MF_EINVAL) for a bad ratio or layouts that do not nest. */
 long long mf_interp_cells(const mf_t *fine, const mf_t *crse, int ratio, long long *runs_out);
 
+/* mf_reflux_faces -- the number of coarse faces of the coarse-fine interface that the
+ * refluxing of mf_amr_advance (MF_REFLUX) corrects across: faces of coarse cells in no fine box
+ * whose other side is covered by the fine level (periodic images included).  *cells_out (may
+ * be NULL) gets the number of coarse cells corrected.  Host lists only: needs no attached
+ * memory.  MF_EINVAL for a bad ratio, fine boxes not made of whole coarse cells, or levels that
+ * do not nest. */
+long long mf_reflux_faces(const mf_t *fine, const mf_t *crse, int ratio, long long *cells_out);
+
 /* mf_average_down -- every coarse valid cell whose children are all fine valid cells becomes
  * their mean (current time levels): the r^3 children summed z, y, x ascending, times 1/r^3, in
  * FP64 for FP64 levels and FP32 for FP32/BF16 levels.  ratio 2 or 4; fine boxes must start and

@@ -2313,6 +2313,16 @@ extern "C" long long mf_interp_cells(const mf_t *fine, const mf_t *crse, int rat
     return plan.cells.ncells;
 }
 
+extern "C" long long mf_reflux_faces(const mf_t *fine, const mf_t *crse, int ratio, long long *cells_out) {
+    if (!fine || !crse) return fail(MF_EINVAL, "null handle");
+    if (ratio != 2 && ratio != 4) return fail(MF_EINVAL, "ratio must be 2 or 4");
+    RefluxPlan plan;  // host lists only
+    int rc = build_reflux(fine, crse, ratio, plan);
+    if (rc) return rc;
+    if (cells_out) *cells_out = (long long)plan.cells.size();
+    return (long long)plan.faces.size();
+}
+
 extern "C" int mf_average_down(const mf_t *fine, mf_t *crse, int ratio) {
     int rc = need_attached(crse);
     if (rc) return rc;

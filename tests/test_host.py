@@ -304,3 +304,33 @@ def test_interp_work_list_of_the_sphere_workload():
     finally:
         mf.mf_destroy(hf)
         mf.mf_destroy(hc)
+
+
+def test_reflux_faces_match_the_oracle():
+    """The refluxing plan (host lists only) has the oracle's coarse-fine faces and corrected
+    coarse cells: a small layout with periodic images, and the 225-box sphere workload."""
+    small = np.array([[8, 8, 4, 15, 23, 19], [16, 8, 4, 23, 15, 11], [0, 24, 26, 5, 31, 31],
+                      [26, 24, 26, 31, 31, 31]], dtype=np.int32)
+    for Nc, mgs, fb in ((16, 8, small), (256, 64, synth.sphere_fine_boxes(256, ratio=2))):
+        hc = mf.mf_create([0, 0, 0], [Nc - 1] * 3, mgs, 1, 1, "f64")
+        hf = mf.mf_create_boxes([0, 0, 0], [2 * Nc - 1] * 3, fb, 1, 1, "f64")
+        try:
+            n, cells = mf.mf_reflux_faces(hf, hc, 2)
+            CL = oracle.Level(oracle.chop([0, 0, 0], [Nc - 1] * 3, mgs), [0, 0, 0], [Nc - 1] * 3, 1, 1)
+            FL = oracle.Level(fb, [0, 0, 0], [2 * Nc - 1] * 3, 1, 1)
+            cf = oracle.CFFaces(CL, FL, 2)
+            assert n == cf.n > 0
+            assert cells == len({tuple(f[:3]) for f in cf.faces})
+        finally:
+            mf.mf_destroy(hf)
+            mf.mf_destroy(hc)
+    # fine boxes that are not whole coarse cells are refused
+    hc = mf.mf_create([0, 0, 0], [15, 15, 15], 8, 1, 1, "f64")
+    hf = mf.mf_create_boxes([0, 0, 0], [31, 31, 31], np.array([[1, 0, 0, 8, 7, 7]], dtype=np.int32), 1, 1, "f64")
+    try:
+        with pytest.raises(mf.MFError) as e:
+            mf.mf_reflux_faces(hf, hc, 2)
+        assert e.value.code == mf.MF_EINVAL
+    finally:
+        mf.mf_destroy(hf)
+        mf.mf_destroy(hc)
