@@ -458,6 +458,31 @@ def test_amr_advance_fp64_matches_oracle(kernel):
     assert float(np.max(np.abs(fo[mask] - fr[mask])) / np.max(np.abs(fr[mask]))) <= FP64_TOL
 
 
+def test_amr_advance_ratio4_fp64_matches_oracle():
+    """Ratio 4 with 4 fine substeps (lam_f = 4 lam_c), two components: FP64 within the oracle
+    tolerance on both levels."""
+    Nc, clo, chi, cboxes, flo, fhi, fboxes = _two_level(4)
+    C = 2
+    modes = [synth.sine_modes(1604, 60 + c, 4, 3) for c in range(C)]
+    cden = np.stack([synth.eval_modes((Nc, Nc, Nc), m) for m in modes])
+    fden = np.stack([synth.eval_modes((4 * Nc,) * 3, m) for m in modes])
+    dt_c = 0.0375 / (Nc * Nc)
+    gc = gpu_level(clo, chi, boxes=cboxes, ncomp=C, ngrow=1)
+    gf = gpu_level(flo, fhi, boxes=fboxes, ncomp=C, ngrow=1)
+    gc.from_host(cden)
+    gf.from_host(fden)
+    mf.mf_amr_advance(gc.h, gf.h, 1, [1.0, 1.0], dt_c, 2, 4, 4)
+    CL = oracle.Level(cboxes, clo, chi, 1, C)
+    FL = oracle.Level(fboxes, flo, fhi, 1, C)
+    c_out, f_out = oracle.amr_advance(CL, FL, 1, dt_c * float(Nc * Nc), CL.from_dense(cden), FL.from_dense(fden), 2,
+                                      nsub=4, ratio=4)
+    assert rel_err(gc.to_host(), CL.to_dense(c_out)) <= FP64_TOL
+    fo, fr = gf.to_host(), FL.to_dense(f_out)
+    mask = ~np.isnan(fr)
+    np.testing.assert_array_equal(mask, ~np.isnan(fo))
+    assert float(np.max(np.abs(fo[mask] - fr[mask])) / np.max(np.abs(fr[mask]))) <= FP64_TOL
+
+
 # --------------------------------------------------------------------------- errors on the GPU path
 
 def test_unstable_dt_rejected():
