@@ -316,6 +316,9 @@ struct mf {
     std::vector<std::unique_ptr<AvgPlan>> avg;
     std::vector<std::unique_ptr<AmrFill>> amrfill;
     ~mf() {
+        // work this handle queued may still run: let it finish before its graphs and device
+        // lists go (an error here, e.g. after the context is gone, leaves nothing to wait for)
+        if (attached) cudaStreamSynchronize(stream);
         graphs.clear();
         for (auto e : ev) cudaEventDestroy(e);
         if (cap) cudaStreamDestroy(cap);
