@@ -86,6 +86,8 @@ int mf_create(mf_t **out, const int domain_lo[3], const int domain_hi[3], int ma
 int mf_create_boxes(mf_t **out, const int domain_lo[3], const int domain_hi[3], const int *boxes,
                     int nboxes, int ncomp, int ngrow, int dtype);
 
+/* Releases the handle (metadata, device work lists, graphs), after waiting for the work it queued
+ * on its attached stream.  The field memory stays the caller's. */
 void mf_destroy(mf_t *mf);
 
 /* Layout queries (host only). */
