@@ -179,6 +179,12 @@ int mf_interp_cf(mf_t *fine, const mf_t *crse_old, const mf_t *crse_new, double 
  * memory.  Negative error code (MF_EINVAL) for a bad ratio or layouts that do not nest. */
 long long mf_interp_cells(const mf_t *fine, const mf_t *crse, int ratio, long long *runs_out);
 
+/* mf_avgdown_cells -- the number of coarse cells (per component) mf_average_down writes: the
+ * coarse valid cells under the fine boxes.  *regions_out (may be NULL) gets the number of
+ * (fine box, coarse box) regions of its work list.  Host lists only: needs no attached memory.
+ * MF_EINVAL for a bad ratio, fine boxes not aligned to the ratio, or levels that do not nest. */
+long long mf_avgdown_cells(const mf_t *fine, const mf_t *crse, int ratio, long long *regions_out);
+
 /* mf_reflux_faces -- the number of coarse faces of the coarse-fine interface that the
  * refluxing of mf_amr_advance (MF_REFLUX) corrects across: faces of coarse cells in no fine box
  * whose other side is covered by the fine level (periodic images included).  *cells_out (may

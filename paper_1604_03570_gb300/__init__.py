@@ -33,7 +33,7 @@ EXPORTS = [
     "mf_advance", "mf_amr_advance", "mf_sum", "mf_step_bytes", "mf_current", "mf_last_error", "mf_set_timing",
     "mf_phase_ms", "mf_set_kernel", "mf_sum_strided_noalloc", "mf_get_schedule", "mf_launch_count",
     "mf_fp64_fma_rate", "mf_set_schedule", "mf_reduce", "mf_stage_bytes", "mf_attach_stage",
-    "mf_rk3_advance", "mf_interp_cells", "mf_reflux_faces",
+    "mf_rk3_advance", "mf_interp_cells", "mf_reflux_faces", "mf_avgdown_cells",
 ]
 
 
@@ -92,6 +92,7 @@ def _load():
         "mf_rk3_advance": (I, [P, ctypes.POINTER(mf_stencil), D, I]),
         "mf_interp_cells": (LL, [P, P, I, ctypes.POINTER(LL)]),
         "mf_reflux_faces": (LL, [P, P, I, ctypes.POINTER(LL)]),
+        "mf_avgdown_cells": (LL, [P, P, I, ctypes.POINTER(LL)]),
         "mf_sum_strided_noalloc": (I, [P, I, I, I, I, LL, LL, ctypes.POINTER(D), P]),
     }
     for name, (res, args) in sig.items():
@@ -173,6 +174,13 @@ def mf_interp_cells(fine, crse, ratio):
     runs = ctypes.c_longlong()
     n = _check(lib.mf_interp_cells(fine, crse, int(ratio), ctypes.byref(runs)))
     return int(n), int(runs.value)
+
+
+def mf_avgdown_cells(fine, crse, ratio):
+    """(coarse cells the average-down writes, regions of its work list); host lists only."""
+    regs = ctypes.c_longlong()
+    n = _check(lib.mf_avgdown_cells(fine, crse, int(ratio), ctypes.byref(regs)))
+    return int(n), int(regs.value)
 
 
 def mf_reflux_faces(fine, crse, ratio):

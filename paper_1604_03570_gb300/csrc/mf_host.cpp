@@ -2326,6 +2326,16 @@ extern "C" long long mf_reflux_faces(const mf_t *fine, const mf_t *crse, int rat
     return (long long)plan.faces.size();
 }
 
+extern "C" long long mf_avgdown_cells(const mf_t *fine, const mf_t *crse, int ratio, long long *regions_out) {
+    if (!fine || !crse) return fail(MF_EINVAL, "null handle");
+    if (ratio != 2 && ratio != 4) return fail(MF_EINVAL, "ratio must be 2 or 4");
+    AvgPlan plan;  // host lists only
+    int rc = build_avg(fine, const_cast<mf_t *>(crse), ratio, plan);
+    if (rc) return rc;
+    if (regions_out) *regions_out = (long long)plan.regs.size();
+    return plan.cells.ncells;
+}
+
 extern "C" int mf_average_down(const mf_t *fine, mf_t *crse, int ratio) {
     int rc = need_attached(crse);
     if (rc) return rc;

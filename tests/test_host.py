@@ -334,3 +334,24 @@ def test_reflux_faces_match_the_oracle():
     finally:
         mf.mf_destroy(hf)
         mf.mf_destroy(hc)
+
+
+def test_average_down_work_list_holds_exactly_the_oracles_cells():
+    """The average-down work list (host lists only) covers the coarse cells the oracle writes:
+    a small layout at ratio 2 and 4, and the 225-box sphere workload."""
+    base = np.array([[4, 4, 4, 7, 11, 7], [8, 4, 4, 11, 7, 9], [0, 0, 12, 3, 3, 15]])
+    cases = [(16, 8, r, np.concatenate([base[:, :3] * r, (base[:, 3:] + 1) * r - 1], axis=1).astype(np.int32))
+             for r in (2, 4)]
+    cases.append((256, 64, 2, synth.sphere_fine_boxes(256, ratio=2)))
+    for Nc, mgs, r, fb in cases:
+        hc = mf.mf_create([0, 0, 0], [Nc - 1] * 3, mgs, 1, 1, "f64")
+        hf = mf.mf_create_boxes([0, 0, 0], [r * Nc - 1] * 3, fb, 1, 1, "f64")
+        try:
+            n, regions = mf.mf_avgdown_cells(hf, hc, r)
+            CL = oracle.Level(oracle.chop([0, 0, 0], [Nc - 1] * 3, mgs), [0, 0, 0], [Nc - 1] * 3, 1, 1)
+            FL = oracle.Level(fb, [0, 0, 0], [r * Nc - 1] * 3, 1, 1)
+            assert n == oracle.average_down(FL, CL, r, FL.alloc(), CL.alloc()) > 0
+            assert len(fb) <= regions
+        finally:
+            mf.mf_destroy(hf)
+            mf.mf_destroy(hc)
