@@ -149,11 +149,16 @@ def test_layout_bytes_alignment():
             mf.mf_destroy(h)
 
 
-@pytest.mark.parametrize("bad", ["overlap", "outside", "ngrow", "ncomp", "dtype", "empty"])
+@pytest.mark.parametrize("bad", ["overlap", "outside", "ngrow", "ncomp", "dtype", "empty", "no_boxes", "too_large"])
 def test_create_rejects_bad_arguments(bad):
     lo, hi = [0, 0, 0], [15, 15, 15]
     boxes = [[0, 0, 0, 7, 7, 7], [8, 0, 0, 15, 7, 7]]
     kw = dict(ncomp=1, ngrow=1, dtype="f64")
+    if bad == "no_boxes":
+        boxes = np.zeros((0, 6), dtype=np.int32)
+    elif bad == "too_large":  # one FArrayBox of 1302^3 > 2^31 elements (offsets inside one are 32-bit)
+        lo, hi = [0, 0, 0], [1299, 1299, 1299]
+        boxes = [[0, 0, 0, 1299, 1299, 1299]]
     if bad == "overlap":
         boxes = [[0, 0, 0, 7, 7, 7], [7, 0, 0, 15, 7, 7]]
     elif bad == "outside":
