@@ -148,6 +148,28 @@ def test_advance_fp64_matches_oracle(R, layout):
     assert rel_err(g.to_host(), ref) <= FP64_TOL
 
 
+@pytest.mark.parametrize("R", [1, 2, 4])
+def test_single_box_domain_matches_oracle(R):
+    """One box equal to the periodic domain (the paper's single-grid setup): every x halo, face
+    push and fill is the box with itself.  Default schedule (autotuned, TMA kernel), FP64 against
+    the oracle, and the FillBoundary of an FP32 copy equal to numpy's periodic pad."""
+    N = 32
+    lo, hi = [0, 0, 0], [N - 1] * 3
+    boxes = np.array([[0, 0, 0, N - 1, N - 1, N - 1]], dtype=np.int32)
+    dt = {1: 0.15, 2: 0.1125, 4: 0.09}[R] / float(N * N)
+    dense = synth.eval_modes((N, N, N), synth.sine_modes(1604, 70 + R, 8, 8))[None]
+    g = gpu_level(lo, hi, boxes=boxes, ngrow=R, dtype="f64")
+    g.from_host(dense)
+    g.advance(R, [1.0], dt, 6)
+    ref = _oracle_advance(boxes, lo, hi, R, 1, R, dt * float(N * N), 6, dense)
+    assert rel_err(g.to_host(), ref) <= FP64_TOL
+    f = gpu_level(lo, hi, boxes=boxes, ngrow=R, dtype="f32")
+    d32 = round_to(dense, "f32")
+    f.from_host(d32)
+    f.fill_boundary()
+    np.testing.assert_array_equal(f.fab_to_host(0)[0], np.pad(d32[0], R, mode="wrap"))
+
+
 CUBE_UNEVEN = np.array([
     [0, 0, 0, 15, 23, 7], [16, 0, 0, 31, 8, 7], [16, 9, 0, 31, 31, 7], [0, 24, 0, 15, 31, 7],
     [0, 0, 8, 7, 31, 31], [8, 0, 8, 31, 15, 20], [8, 16, 8, 31, 31, 20], [8, 0, 21, 31, 31, 31]], dtype=np.int32)
