@@ -315,6 +315,7 @@ def manybox_line(mf, torch, flush, args, hbm):
         ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
         step_bytes = manybox_step_bytes(4, C, boxes, R)
         out[str(target)] = {"value": N ** 3 * n / (ms * 1e-3), "unit": UNIT, "ms_per_bench_step": ms,
+                            "cell_comp_updates_per_s": N ** 3 * C * n / (ms * 1e-3),
                             "boxes": target, "step_bytes": step_bytes,
                             "step_frac": step_bytes * n / (ms * 1e-3) / 1e9 / hbm,
                             "launches_per_bench_step": mf.mf_launch_count(g.h), "schedule": mf.mf_get_schedule(g.h)}
