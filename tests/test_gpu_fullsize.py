@@ -12,9 +12,10 @@ facts that hold at any size and owe nothing to the CUDA path:
 * the two-level workload has no closed form; there the FP64 oracle runs two full coarse steps
   (both fine substeps, both interpolation times, two average-downs).
 
-FP64 must agree within 1e-12 (relative max norm).  FP32 has no analytic bound: the bound
-below allows 2e-7 relative per step (5e-7 for the 25-point stencil) and each test prints the
-measured value.
+FP64 must agree within 1e-12 (relative max norm).  FP32 storage has no analytic bound (parity
+unpinned analytically): each workload's bound is about twice the max-norm relative error
+measured on GB300 for it (F32_MEASURED), so that a regression of 2x or more fails, and each
+test prints its measured value next to the bound.
 """
 import functools
 import math
@@ -35,8 +36,21 @@ pytestmark = pytest.mark.gpu
 FP64_TOL = 1e-12
 
 
-def f32_tol(nsteps, R):
-    return (5e-7 if R == 4 else 2e-7) * nsteps
+# Max-norm relative error of the FP32-storage path measured on GB300 per full-size workload
+# (against the closed form or the FP64 oracle); the test bound is F32_BOUND_FACTOR times it.
+F32_MEASURED = {
+    "heat256": 2.6e-7,      # 256^3, 7-point, 100 steps
+    "diff8th512": 2.6e-7,   # 512^3 x 5, 25-point, 20 steps
+    "manybox512": 1.3e-7,   # 512^3 x 2 in 4096 / 32768 boxes, 13-point, 50 steps
+    "amr2lev256": 1.6e-7,   # two levels, 2 coarse steps
+    "rk3_8th256": 4.9e-7,   # RK3, 25-point, 256^3, 20 steps
+    "amr2lev256_reflux_drift": 3.7e-13,  # composite-sum drift with refluxing, 2 coarse steps
+}
+F32_BOUND_FACTOR = 2.0
+
+
+def f32_tol(workload):
+    return F32_BOUND_FACTOR * F32_MEASURED[workload]
 
 
 def rel_err(out, ref):
@@ -96,7 +110,7 @@ def test_heat256_full_size_matches_exact_mode_decay(dtype):
     g.advance(1, [1.0], dt, n)
     s1 = g.sum(0)
     err = rel_err(g.to_host(), exact_modes(N, field_modes(cfg, 0), 1, lam, n)[None])
-    tol = FP64_TOL if dtype == "f64" else f32_tol(n, 1)
+    tol = FP64_TOL if dtype == "f64" else f32_tol("heat256")
     print("MEASURED heat256 %s rel_err %.3e (bound %.1e) schedule %s" % (dtype, err, tol, mf.mf_get_schedule(g.h)))
     assert err <= tol
     if dtype == "f64":  # flux form on a periodic level: the sum is invariant up to rounding
@@ -127,9 +141,9 @@ def test_diff8th512_full_size_matches_exact_fourier_solution():
             worst[dtype] = max(worst[dtype], float(np.max(np.abs(outs[dtype][0][c] - ex))) / scale)
         del ex
     print("MEASURED diff8th512 f64 %.3e f32 %.3e (bounds %.1e, %.1e) schedules %s %s"
-          % (worst["f64"], worst["f32"], FP64_TOL, f32_tol(n, R), outs["f64"][1], outs["f32"][1]))
+          % (worst["f64"], worst["f32"], FP64_TOL, f32_tol("diff8th512"), outs["f64"][1], outs["f32"][1]))
     assert worst["f64"] <= FP64_TOL
-    assert worst["f32"] <= f32_tol(n, R)
+    assert worst["f32"] <= f32_tol("diff8th512")
 
 
 # --------------------------------------------------------------------------- 512^3 in 4096 .. 32768 uneven boxes, 13-point
@@ -155,7 +169,7 @@ def test_manybox512_full_size_matches_exact_mode_decay(target, dtype):
     g.from_host(dense)
     g.advance(R, [1.0] * C, dt, n)
     err = rel_err(g.to_host(), exact)
-    tol = FP64_TOL if dtype == "f64" else f32_tol(n, R)
+    tol = FP64_TOL if dtype == "f64" else f32_tol("manybox512")
     print("MEASURED manybox512 %d %s rel_err %.3e (bound %.1e) schedule %s"
           % (target, dtype, err, tol, mf.mf_get_schedule(g.h)))
     assert err <= tol
@@ -186,9 +200,7 @@ def test_amr2lev256_full_size_matches_oracle():
         fo = gf.to_host()
         np.testing.assert_array_equal(np.isnan(fo), np.isnan(f_ref))
         ec, ef = rel_err(gc.to_host(), c_ref), rel_err(fo, f_ref)
-        # FP32: the stencil's per-step rounding over coarse steps and fine substeps, plus the
-        # rounding of every interpolated ghost value
-        tol = FP64_TOL if dtype == "f64" else 2.0 * f32_tol(steps * (1 + nsub), 1)
+        tol = FP64_TOL if dtype == "f64" else f32_tol("amr2lev256")
         print("MEASURED amr2lev256 %s coarse %.3e fine %.3e (bound %.1e) launches %s"
               % (dtype, ec, ef, tol, mf.mf_launch_count(gc.h)))
         assert ec <= tol and ef <= tol
@@ -216,7 +228,7 @@ def test_rk3_8th256_full_size_matches_the_stability_polynomial(dtype):
     g.from_host(dense)
     g.rk3_advance(R, [1.0], dt, n)
     err = rel_err(g.to_host(), exact)
-    tol = FP64_TOL if dtype == "f64" else f32_tol(3 * n, R)
+    tol = FP64_TOL if dtype == "f64" else f32_tol("rk3_8th256")
     print("MEASURED rk3_8th256 %s rel_err %.3e (bound %.1e) schedule %s" % (dtype, err, tol, mf.mf_get_schedule(g.h)))
     assert err <= tol
 
@@ -265,6 +277,7 @@ def test_amr2lev256_reflux_full_size_matches_oracle_and_conserves():
             assert ec <= FP64_TOL and ef <= FP64_TOL
             assert drift <= steps * (1 + nsub) * 1e-15
         else:
-            print("MEASURED amr2lev256 reflux f32 composite drift %.3e" % drift)
-            assert drift <= steps * (1 + nsub) * 1e-7
+            bound = f32_tol("amr2lev256_reflux_drift")
+            print("MEASURED amr2lev256 reflux f32 composite drift %.3e (bound %.1e)" % (drift, bound))
+            assert drift <= bound
         del gc, gf

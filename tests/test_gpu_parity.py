@@ -314,10 +314,12 @@ def test_schedule_invariance_bitwise_and_parity(dtype, R):
 
 # --------------------------------------------------------------------------- reduced precision
 
-@pytest.mark.parametrize("dtype,bound", [("f32", 2e-6), ("bf16", 3e-2)])
+# measured on GB300: FP32 1.3e-7, BF16 5.4e-3; the bounds are about twice that
+@pytest.mark.parametrize("dtype,bound", [("f32", 2.6e-7), ("bf16", 1.1e-2)])
 def test_reduced_precision_error_bound(dtype, bound):
     """FP32 / BF16 storage with FP32 arithmetic against the FP64 oracle on the same rounded
-    input: the stated bound (parity unpinned analytically; measured)."""
+    input: the stated bound (parity unpinned analytically), about twice the measured error so
+    that a 2x accuracy regression fails."""
     lo, hi = [0, 0, 0], [31, 31, 31]
     dense = round_to(synth.eval_modes((32, 32, 32), synth.sine_modes(1604, 40, 8, 8))[None], dtype)
     dt = 0.15 / 1024
@@ -326,7 +328,7 @@ def test_reduced_precision_error_bound(dtype, bound):
     g.advance(1, [1.0], dt, 10)
     ref = _oracle_advance(oracle.chop(lo, hi, 16), lo, hi, 1, 1, 1, 0.15, 10, dense)
     err = rel_err(g.to_host(), ref)
-    print("%s rel err after 10 steps: %.3e" % (dtype, err))
+    print("MEASURED reduced precision %s rel err after 10 steps: %.3e (bound %.1e)" % (dtype, err, bound))
     assert err <= bound
 
 

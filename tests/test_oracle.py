@@ -344,10 +344,16 @@ def test_bruteforce_exact_rational(N, R, mgs, nsteps):
 
 # --------------------------------------------------------------------------- AMR pieces
 
-def _fine_setup(Nc=8, gf=1):
+# Fine boxes of the two-box setup at ratio 2 (coarse cells 2..3 x 2..5 x 2..3 and 4..5 x 2..3 x
+# 2..4); at ratio r the same coarse cells, refined by r.
+_FINE_COARSE_CELLS = [[2, 2, 2, 3, 5, 3], [4, 2, 2, 5, 3, 4]]
+
+
+def _fine_setup(Nc=8, gf=1, ratio=2):
     crse = oracle.Level(oracle.chop([0, 0, 0], [Nc - 1] * 3, 4), [0, 0, 0], [Nc - 1] * 3, 1, 1)
-    fboxes = np.array([[4, 4, 4, 7, 11, 7], [8, 4, 4, 11, 7, 9]], dtype=np.int32)
-    fine = oracle.Level(fboxes, [0, 0, 0], [2 * Nc - 1] * 3, gf, 1)
+    fboxes = np.array([[ratio * b[d] for d in range(3)] + [ratio * (b[3 + d] + 1) - 1 for d in range(3)]
+                       for b in _FINE_COARSE_CELLS], dtype=np.int32)
+    fine = oracle.Level(fboxes, [0, 0, 0], [ratio * Nc - 1] * 3, gf, 1)
     return crse, fine
 
 
@@ -357,19 +363,24 @@ def _level_from_fn(level, N, fn):
     return level.from_dense(fn(xx, y, z)[None])
 
 
+@pytest.mark.parametrize("ratio", [2, 4])
 @pytest.mark.parametrize("alpha", [0.5, 0.25, 0.75])
-def test_interp_reproduces_linear_field_exactly(alpha):
-    """Trilinear interpolation is exact on linear data (dyadic values, exact bits), and the
-    time blend of two linear fields is (1 - alpha) old + alpha new (at alpha != 1/2 a swap of
-    the two levels shows)."""
+def test_interp_reproduces_linear_field_exactly(alpha, ratio):
+    """Trilinear interpolation is exact on linear data: every interpolated fine ghost equals
+    the linear function at the fine cell centre, bit for bit (dyadic coefficients and
+    centres; the weights are multiples of 1/4 at ratio 2 and of 1/8 at ratio 4), and the time
+    blend of two linear fields is (1 - alpha) old + alpha new (at alpha != 1/2 a swap of the
+    two levels shows).  A wrong weight offset at one ratio fails here."""
     Nc = 8
-    crse, fine = _fine_setup(Nc)
+    crse, fine = _fine_setup(Nc, ratio=ratio)
     f_old = lambda x, y, z: 0.5 + 0.25 * x - 0.75 * y + 0.125 * z
-    f_new = lambda x, y, z: 1.5 - 0.5 * x + 0.25 * y + 0.375 * z
+    # no blend (alpha = 0, 1/4, 1/2, 3/4) has gradient components summing to zero, so a
+    # position error common to the three directions cannot cancel
+    f_new = lambda x, y, z: 1.5 - 0.5 * x + 0.25 * y + 0.875 * z
     c_old, c_new = _level_from_fn(crse, Nc, f_old), _level_from_fn(crse, Nc, f_new)
     fd = fine.alloc()
-    n = oracle.interp_cf(fine, crse, 2, alpha, c_old, c_new, fd)
-    xf = (np.arange(2 * Nc) + 0.5) / (2 * Nc)
+    n = oracle.interp_cf(fine, crse, ratio, alpha, c_old, c_new, fd)
+    xf = (np.arange(ratio * Nc) + 0.5) / (ratio * Nc)
     checked = 0
     for b, B in enumerate(fine.boxes):
         fab = fine.fab(fd, b)[0]
@@ -385,13 +396,15 @@ def test_interp_reproduces_linear_field_exactly(alpha):
     assert checked == n > 0
 
 
-def test_interp_fills_exactly_the_uncovered_ghosts():
+@pytest.mark.parametrize("ratio", [2, 4])
+def test_interp_fills_exactly_the_uncovered_ghosts(ratio):
     """Brute-force coverage count: fine ghosts whose periodic point lies in no fine box."""
     Nc = 8
-    crse, fine = _fine_setup(Nc)
+    Nf = ratio * Nc
+    crse, fine = _fine_setup(Nc, ratio=ratio)
     ones = crse.from_dense(np.ones((1, Nc, Nc, Nc)))
     fd = fine.alloc()
-    n = oracle.interp_cf(fine, crse, 2, 0.0, ones, ones, fd)
+    n = oracle.interp_cf(fine, crse, ratio, 0.0, ones, ones, fd)
     expect = 0
     for B in fine.boxes:
         for k in range(B[2] - 1, B[5] + 2):
@@ -400,7 +413,7 @@ def test_interp_fills_exactly_the_uncovered_ghosts():
                     inside = B[0] <= i <= B[3] and B[1] <= j <= B[4] and B[2] <= k <= B[5]
                     if inside:
                         continue
-                    p = (i % 16, j % 16, k % 16)
+                    p = (i % Nf, j % Nf, k % Nf)
                     covered = any(o[0] <= p[0] <= o[3] and o[1] <= p[1] <= o[4] and o[2] <= p[2] <= o[5]
                                   for o in fine.boxes)
                     expect += 0 if covered else 1
@@ -410,68 +423,125 @@ def test_interp_fills_exactly_the_uncovered_ghosts():
     assert vals.size == n and np.all(vals == 1.0)
 
 
-def test_interp_weights_at_periodic_wrap():
-    """Near the domain edge the coarse index wraps: a fine box at the corner of the domain
-    interpolating a coarse field constant along each periodic line gets the constant."""
+@pytest.mark.parametrize("ratio", [2, 4])
+def test_interp_weights_at_periodic_wrap(ratio):
+    """Near the domain edge the coarse index wraps.  A fine box at the corner of the domain
+    interpolates a coarse field that is constant along each periodic line: every ghost gets
+    the constant.  Then a coarse field that is linear in y and constant in x and z (so the
+    wrap in x and z cannot change it): the ghosts on the x and z sides, which stay inside the
+    domain in y (fine rows j >= r/2, whose coarse rows k0 = floor((2j + 1 - r) / 2r) and
+    k0 + 1 do not wrap), get the linear function at their centre exactly."""
     Nc = 8
+    Nf = ratio * Nc
+    s = 2 * ratio  # box side: two coarse cells
     crse = oracle.Level(oracle.chop([0, 0, 0], [Nc - 1] * 3, 4), [0, 0, 0], [Nc - 1] * 3, 1, 1)
-    fine = oracle.Level([[0, 0, 0, 3, 3, 3]], [0, 0, 0], [2 * Nc - 1] * 3, 2, 1)
+    fine = oracle.Level([[0, 0, 0, s - 1, s - 1, s - 1]], [0, 0, 0], [Nf - 1] * 3, 2, 1)
     c = crse.from_dense(np.full((1, Nc, Nc, Nc), 3.25))
     fd = fine.alloc()
-    n = oracle.interp_cf(fine, crse, 2, 0.25, c, c, fd)
-    assert n == 8 ** 3 - 4 ** 3
+    n = oracle.interp_cf(fine, crse, ratio, 0.25, c, c, fd)
+    assert n == (s + 4) ** 3 - s ** 3
     vals = fine.fab(fd, 0)[0]
     assert np.all(vals[~np.isnan(vals)] == 3.25)
+    fn = lambda x, y, z: 0.75 + 0.5 * y
+    cl = _level_from_fn(crse, Nc, fn)
+    fd = fine.alloc()
+    oracle.interp_cf(fine, crse, ratio, 0.0, cl, cl, fd)
+    fab = fine.fab(fd, 0)[0]
+    yf = (np.arange(Nf) + 0.5) / Nf
+    checked = 0
+    for k in range(-2, s + 2):
+        for j in range(ratio // 2, s):  # the coarse y rows of these fine rows do not wrap
+            for i in range(-2, s + 2):
+                if 0 <= i < s and 0 <= k < s:
+                    continue
+                assert fab[k + 2, j + 2, i + 2] == fn(0.0, yf[j], 0.0)
+                checked += 1
+    assert checked > 0
 
 
-def test_average_down_of_constant_refinement_is_identity():
+@pytest.mark.parametrize("ratio", [2, 4])
+def test_average_down_of_constant_refinement_is_identity(ratio):
+    """Each coarse value copied into its r^3 children averages back to itself (a 1/r^2 or a
+    wrong child count at one ratio fails here)."""
     Nc = 8
-    crse, fine = _fine_setup(Nc)
-    # dyadic values with few significant bits, so that the 8-term sum is exact
+    crse, fine = _fine_setup(Nc, ratio=ratio)
+    # dyadic values with few significant bits, so that the r^3-term sum is exact
     dense_c = np.random.default_rng(2).integers(-512, 512, size=(1, Nc, Nc, Nc)) / 64.0
-    dense_f = np.repeat(np.repeat(np.repeat(dense_c, 2, axis=1), 2, axis=2), 2, axis=3)
+    dense_f = dense_c
+    for ax in (1, 2, 3):
+        dense_f = np.repeat(dense_f, ratio, axis=ax)
     fd = fine.from_dense(dense_f)
     cd = crse.from_dense(dense_c)
     before = crse.to_dense(cd)
-    n = oracle.average_down(fine, crse, 2, fd, cd)
+    n = oracle.average_down(fine, crse, ratio, fd, cd)
     assert n == (2 * 4 * 2) + (2 * 2 * 3)
     np.testing.assert_array_equal(crse.to_dense(cd), before)
 
 
-def test_average_down_of_linear_field():
-    """The mean of the 8 children of a linear field is its value at the coarse centre."""
+@pytest.mark.parametrize("ratio", [2, 4])
+def test_average_down_of_linear_field(ratio):
+    """The mean of the r^3 children of a linear field is its value at the coarse centre."""
     Nc = 8
-    crse, fine = _fine_setup(Nc)
+    crse, fine = _fine_setup(Nc, ratio=ratio)
     fn = lambda x, y, z: 0.25 + 0.5 * x - 0.25 * y + 0.75 * z
-    fd = _level_from_fn(fine, 2 * Nc, fn)
+    fd = _level_from_fn(fine, ratio * Nc, fn)
     cd = crse.from_dense(np.zeros((1, Nc, Nc, Nc)))
-    oracle.average_down(fine, crse, 2, fd, cd)
+    oracle.average_down(fine, crse, ratio, fd, cd)
     xc = (np.arange(Nc) + 0.5) / Nc
     dense = crse.to_dense(cd)[0]
     for B in fine.boxes:
-        for k in range(B[2] // 2, B[5] // 2 + 1):
-            for j in range(B[1] // 2, B[4] // 2 + 1):
-                for i in range(B[0] // 2, B[3] // 2 + 1):
+        for k in range(B[2] // ratio, B[5] // ratio + 1):
+            for j in range(B[1] // ratio, B[4] // ratio + 1):
+                for i in range(B[0] // ratio, B[3] // ratio + 1):
                     assert dense[k, j, i] == fn(xc[i], xc[j], xc[k])
 
 
-def test_amr_with_full_fine_cover_equals_fine_single_level():
+@pytest.mark.parametrize("ratio,nsub,lam_c", [(2, 2, 0.075), (4, 4, 0.0375)])
+def test_amr_with_full_fine_cover_equals_fine_single_level(ratio, nsub, lam_c):
     """A fine level covering the whole domain needs no interpolation: after n coarse steps
-    the fine data equal 2n single-level fine steps with lam_f = 2 lam_c, bit for bit, and the
-    coarse data equal the average-down of that fine result."""
+    the fine data equal n * nsub single-level fine steps with lam_f = lam_c r^2 / nsub
+    (= 0.15 here), bit for bit, and the coarse data equal the average-down of that fine
+    result."""
     Nc = 8
+    Nf = ratio * Nc
     crse = oracle.Level(oracle.chop([0, 0, 0], [Nc - 1] * 3, 4), [0, 0, 0], [Nc - 1] * 3, 1, 1)
-    fine = oracle.Level(oracle.chop([0, 0, 0], [2 * Nc - 1] * 3, 8), [0, 0, 0], [2 * Nc - 1] * 3, 1, 1)
-    dense_f = _rand((1, 2 * Nc, 2 * Nc, 2 * Nc), seed=9)
+    fine = oracle.Level(oracle.chop([0, 0, 0], [Nf - 1] * 3, 8), [0, 0, 0], [Nf - 1] * 3, 1, 1)
+    dense_f = _rand((1, Nf, Nf, Nf), seed=9)
     fd = fine.from_dense(dense_f)
     cd = crse.from_dense(np.zeros((1, Nc, Nc, Nc)))
-    oracle.average_down(fine, crse, 2, fd, cd)
-    c_out, f_out = oracle.amr_advance(crse, fine, 1, 0.075, cd, fd, 3)
-    f_ref = oracle.advance(fine, fd, 1, 0.15, 6)
+    oracle.average_down(fine, crse, ratio, fd, cd)
+    ncrse = 3
+    c_out, f_out = oracle.amr_advance(crse, fine, 1, lam_c, cd, fd, ncrse, nsub=nsub, ratio=ratio)
+    f_ref = oracle.advance(fine, fd, 1, 0.15, ncrse * nsub)
     np.testing.assert_array_equal(fine.to_dense(f_out), fine.to_dense(f_ref))
     c_ref = crse.from_dense(np.zeros((1, Nc, Nc, Nc)))
-    oracle.average_down(fine, crse, 2, f_ref, c_ref)
+    oracle.average_down(fine, crse, ratio, f_ref, c_ref)
     np.testing.assert_array_equal(crse.to_dense(c_out), crse.to_dense(c_ref))
+
+
+@pytest.mark.parametrize("ratio,nsub,lam_c", [(2, 2, 0.075), (4, 4, 0.0375)])
+def test_amr_partial_cover_keeps_constant_and_conserves_with_reflux(ratio, nsub, lam_c):
+    """A fine level covering part of the domain at ratio r with nsub substeps: a constant
+    state stays constant (interpolation weights sum to one at every substep time, the
+    average-down is a mean), and with refluxing the composite sum is conserved to rounding."""
+    Nc = 8
+    crse, fine = _fine_setup(Nc, ratio=ratio)
+    cd = crse.from_dense(np.full((1, Nc, Nc, Nc), 2.0))
+    fd = fine.from_dense(np.full((1, ratio * Nc, ratio * Nc, ratio * Nc), 2.0))
+    c_out, f_out = oracle.amr_advance(crse, fine, 1, lam_c, cd, fd, 2, nsub=nsub, ratio=ratio)
+    assert np.all(crse.to_dense(c_out) == 2.0)
+    fo = fine.to_dense(f_out)
+    assert np.all(fo[~np.isnan(fo)] == 2.0)
+    fd = fine.from_dense(_rand((1, ratio * Nc, ratio * Nc, ratio * Nc), seed=31))
+    cd = crse.from_dense(_rand((1, Nc, Nc, Nc), seed=32))
+    oracle.average_down(fine, crse, ratio, fd, cd)
+    s0, a0 = _composite_sum(crse, fine, cd, fd, ratio=ratio)
+    c1, f1 = oracle.amr_advance(crse, fine, 1, lam_c, cd, fd, 2, nsub=nsub, ratio=ratio, reflux_faces=True)
+    s1, _ = _composite_sum(crse, fine, c1, f1, ratio=ratio)
+    assert abs(s1 - s0) <= 2 * nsub * 1e-15 * a0, s1 - s0
+    c2, f2 = oracle.amr_advance(crse, fine, 1, lam_c, cd, fd, 2, nsub=nsub, ratio=ratio)
+    s2, _ = _composite_sum(crse, fine, c2, f2, ratio=ratio)
+    assert abs(s2 - s0) > 1e-6 * a0  # no refluxing, no conservation
 
 
 def _composite_sum(crse, fine, cdata, fdata, ratio=2, comp=0):
@@ -584,16 +654,18 @@ def test_fill_with_offset_domain_equals_numpy_wrap():
         np.testing.assert_array_equal(L.fab(u, b)[0], padded[s[2]:e[2], s[1]:e[1], s[0]:e[0]])
 
 
-def test_average_down_matches_block_mean():
-    """Random fine data: the average-down equals numpy's mean over 2x2x2 blocks."""
+@pytest.mark.parametrize("ratio", [2, 4])
+def test_average_down_matches_block_mean(ratio):
+    """Random fine data: the average-down equals numpy's mean over r x r x r blocks."""
     Nc = 8
-    crse, fine = _fine_setup(Nc)
-    dense_f = _rand((1, 2 * Nc, 2 * Nc, 2 * Nc), seed=4)
+    crse, fine = _fine_setup(Nc, ratio=ratio)
+    dense_f = _rand((1, ratio * Nc, ratio * Nc, ratio * Nc), seed=4)
     fd = fine.from_dense(dense_f)
     cd = crse.from_dense(np.zeros((1, Nc, Nc, Nc)))
-    oracle.average_down(fine, crse, 2, fd, cd)
-    block = dense_f[0].reshape(Nc, 2, Nc, 2, Nc, 2).mean(axis=(1, 3, 5))
+    oracle.average_down(fine, crse, ratio, fd, cd)
+    block = dense_f[0].reshape(Nc, ratio, Nc, ratio, Nc, ratio).mean(axis=(1, 3, 5))
     dense = crse.to_dense(cd)[0]
     for B in fine.boxes:
-        sl = (slice(B[2] // 2, B[5] // 2 + 1), slice(B[1] // 2, B[4] // 2 + 1), slice(B[0] // 2, B[3] // 2 + 1))
-        np.testing.assert_allclose(dense[sl], block[sl], rtol=0, atol=4e-16 * np.max(np.abs(block)))
+        sl = (slice(B[2] // ratio, B[5] // ratio + 1), slice(B[1] // ratio, B[4] // ratio + 1),
+              slice(B[0] // ratio, B[3] // ratio + 1))
+        np.testing.assert_allclose(dense[sl], block[sl], rtol=0, atol=ratio * 4e-16 * np.max(np.abs(block)))
