@@ -87,14 +87,20 @@ int mf_create_boxes(mf_t **out, const int domain_lo[3], const int domain_hi[3], 
                     int nboxes, int ncomp, int ngrow, int dtype);
 
 /* Releases the handle (metadata, device work lists, graphs), after waiting for the work it queued
- * on its attached stream.  The field memory stays the caller's. */
+ * on its attached stream.  The field memory stays the caller's.  Sec. 3.1 gives a MultiFab no
+ * explicit lifetime call; this is the end of the handle that mf_create made.  A NULL handle is
+ * ignored. */
 void mf_destroy(mf_t *mf);
 
 /* Layout queries (host only). */
 int mf_nboxes(const mf_t *mf);
 int mf_get_boxes(const mf_t *mf, int *boxes /* nboxes*6 */);
 /* Bytes of device memory mf_attach needs: two time levels of all FArrayBoxes, each
- * FArrayBox 256-byte aligned, rows padded so that every valid row starts 16-byte aligned. */
+ * FArrayBox 256-byte aligned, rows padded so that every valid row starts 16-byte aligned.
+ * Sec. 3.1: an FArrayBox holds its grid's data, grown by the ghost cells, as one contiguous
+ * array; here all FArrayBoxes of a level follow each other in one caller-owned allocation,
+ * two time levels because the forward-Euler update of Sec. 4.1 is read out of place.
+ * 0 for a NULL handle. */
 size_t mf_bytes(const mf_t *mf);
 /* Number of FillBoundary copy regions (box-box intersections incl. periodic images) and
  * the number of ghost cells per component they write. */
@@ -108,6 +114,11 @@ long long mf_get_fb_regions(const mf_t *mf, int *out, long long max);
  * memory of the current device) and the CUDA stream (cudaStream_t, may be NULL for the
  * legacy stream) every later call runs on.  Builds and uploads the FillBoundary list and the
  * tile work list.  May be called again to move the handle to another buffer or stream.
+ * Sec. 3.1: the FArrayBox data of a MultiFab are contiguous arrays, and every process holds
+ * the list of all grids for communication within a level; here the caller allocates the
+ * arrays and the library precomputes the box-box intersection list of FillBoundary once,
+ * from that grid list.  MF_EALIGN for a misaligned or short buffer; MF_ENOMEM when the
+ * metadata allocation fails.
  */
 int mf_attach(mf_t *mf, void *dev_ptr, size_t bytes, void *cuda_stream);
 
@@ -144,7 +155,10 @@ int mf_get_schedule(const mf_t *mf, int out[7]);
  * (ghosts unchanged); cells of the dense array outside every box are ignored.
  * mf_copy_to_host writes every dense cell: valid data where a box covers it, NaN elsewhere.
  * Both convert to/from the storage type on the GPU and stage through the non-current time
- * level, which they overwrite.
+ * level, which they overwrite.  Sec. 3.1: an FArrayBox's index-space information turns its
+ * 1-D array into a multi-dimensional one (component slowest, x fastest, the Fortran order the
+ * paper's kernels see); these calls apply that map between the boxes and one dense array.
+ * FP64 to BF16 rounds to nearest even; FP64 to FP32 rounds to nearest.
  */
 int mf_copy_from_host(mf_t *mf, const double *dense);
 int mf_copy_to_host(mf_t *mf, double *dense);
@@ -196,7 +210,11 @@ long long mf_reflux_faces(const mf_t *fine, const mf_t *crse, int ratio, long lo
 /* mf_average_down -- every coarse valid cell whose children are all fine valid cells becomes
  * their mean (current time levels): the r^3 children summed z, y, x ascending, times 1/r^3, in
  * FP64 for FP64 levels and FP32 for FP32/BF16 levels.  ratio 2 or 4; fine boxes must start and
- * end on multiples of ratio (MF_EINVAL otherwise).  Runs on the coarse handle's stream. */
+ * end on multiples of ratio (MF_EINVAL otherwise).  Runs on the coarse handle's stream.
+ * Sec. 3 (levels of a nested hierarchy whose mesh spacings differ by a ratio of 2 or 4) and
+ * Sec. 1 (subcycled AMR time stepping) use the coarse data under a fine level without
+ * defining how they are set; the reading taken here is the conservative one, the mean of the
+ * children. */
 int mf_average_down(const mf_t *fine, mf_t *crse, int ratio);
 
 /*
@@ -214,7 +232,11 @@ int mf_average_down(const mf_t *fine, mf_t *crse, int ratio);
 int mf_advance(mf_t *mf, const mf_stencil *st, double dt, int nsteps);
 
 /*
- * mf_amr_advance -- two-level subcycled advance (fine = crse refined by ratio): per coarse step,
+ * mf_amr_advance -- two-level subcycled advance (fine = crse refined by ratio).  Sec. 1 states
+ * that BoxLib supports several time-subcycling modes for AMR and Sec. 3 that levels differ by a
+ * ratio of 2 or 4, without defining a scheme; the reading taken here is the standard
+ * Berger-Oliger subcycling below (coarse step first, then nsub fine substeps with coarse ghost
+ * data linear in time, then the average-down).  Per coarse step,
  * FillBoundary + stencil on the coarse level; then nsub fine substeps of dt/nsub, each
  * FillBoundary + coarse-fine interpolation at alpha = s/nsub + stencil; then average-down
  * onto the new coarse level.  Both levels must have the same dtype and ncomp.
@@ -310,12 +332,13 @@ const char *mf_last_error(void);
  *        data + x + y*sy + z*sz (strides in elements, sy >= nx, sz >= sy*ny); dtype MF_F64,
  *        MF_F32 or MF_BF16.  nx*ny*nz <= 268,435,456 cells, else MF_EINVAL.
  * out    host pointer receiving the sum.  stream: cudaStream_t (NULL = legacy stream); the
- *        call enqueues two kernels and a copy on it and synchronises it.
+ *        call enqueues two kernels and a copy on it and then waits for that stream, so it
+ *        returns MF_ESTATE, enqueueing nothing, when the stream is capturing a graph.
  * Scratch: a file-scope device array of 1 MiB (65,536 block partials), present on every GPU
  * that loads the library until the process exits.  The first call on a device looks up the
- * array's device address (with that device current) and caches it; make that first call
- * before any stream capture.  Every call reuses the same array, so calls whose kernels overlap
- * on the GPU (other streams, other host threads) race and must be serialised by the caller.
+ * array's device address (with that device current) and caches it.  Every call reuses the
+ * same array, so calls whose kernels overlap on the GPU (other streams, other host threads)
+ * race and must be serialised by the caller.
  */
 int mf_sum_strided_noalloc(const void *data, int dtype, int nx, int ny, int nz, long long sy, long long sz,
                            double *out, void *stream);

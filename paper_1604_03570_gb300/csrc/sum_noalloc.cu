@@ -97,10 +97,17 @@ extern "C" int mf_sum_strided_noalloc(const void *data, int dtype, int nx, int n
                  (long long)kMaxBlocks * kCellsPerBlock);
         return fail_na(MF_EINVAL, buf);
     }
+    cudaStream_t s = (cudaStream_t)stream;
+    // the call ends by waiting for its result, which a capturing stream cannot do: refuse
+    // before enqueueing anything, so that the caller's capture stays intact
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t ce = cudaStreamIsCapturing(s, &cs);
+    if (ce != cudaSuccess) return fail_na(MF_ECUDA, cudaGetErrorString(ce));
+    if (cs != cudaStreamCaptureStatusNone)
+        return fail_na(MF_ESTATE, "mf_sum_strided_noalloc waits for its result and cannot run on a capturing stream");
     double2 *scratch = nullptr;
     int rc = scratch_for_current_device(&scratch);
     if (rc) return rc;
-    cudaStream_t s = (cudaStream_t)stream;
     switch (dtype) {
         case MF_F64:
             k_sum_strided_partial<<<(int)nblocks, kThreads, 0, s>>>((const double *)data, nx, ny, sy, sz, ncell,

@@ -3,7 +3,7 @@
 Some callers cannot allocate device memory (another component owns every allocation, or an
 allocation inside a real-time loop is not allowed).  For them the library offers a sum that
 uses a fixed scratch array compiled into the library.  This test calls it through the C ABI
-twice in a row, on differently sized and typed inputs, and checks each result against the
+three times in a row, on differently sized and typed inputs, and checks each result against the
 handle-based mf_sum of the same cells (both compensated FP64 sums, each within 2 ulp of the
 correctly rounded sum).  It runs last so that a failure here leaves every other test run.
 """
@@ -35,21 +35,46 @@ def _strided_device_copy(dense, torch_dtype, pad):
     return full, nx + pad, ny * (nx + pad)
 
 
-@pytest.mark.parametrize("first,second", [(("f64", (40, 24, 33)), ("f32", (64, 64, 64)))])
-def test_noalloc_sum_matches_mf_sum_on_two_calls_in_a_row(first, second):
+def test_noalloc_sum_matches_mf_sum_on_calls_in_a_row():
+    """Three calls in a row on one shared scratch array: FP64 (8 blocks), FP32 (64 blocks),
+    then BF16 (1 block, on the legacy stream).  The last call is smaller than the one before
+    it, so stale partial sums of the 64-block call would show in its result."""
     rng = np.random.default_rng(2718)
-    for dtype, (nz, ny, nx) in (first, second):
-        tdt = torch.float64 if dtype == "f64" else torch.float32
-        dense = 1.0 + rng.standard_normal((nz, ny, nx))
+    calls = [("f64", (40, 24, 33), torch.float64, None),
+             ("f32", (64, 64, 64), torch.float32, None),
+             ("bf16", (5, 7, 9), torch.bfloat16, 0)]
+    for dtype, (nz, ny, nx), tdt, stream in calls:
+        if dtype == "bf16":
+            dense = rng.integers(-128, 128, size=(nz, ny, nx)) / 16.0  # 8 significant bits: exact in BF16
+        else:
+            dense = 1.0 + rng.standard_normal((nz, ny, nx))
         if dtype == "f32":
             dense = dense.astype(np.float32).astype(np.float64)
         ref = _reference(dense, dtype, 16)
         arr, sy, sz = _strided_device_copy(dense, tdt, pad=7)
-        got = mf.mf_sum_strided_noalloc(arr.data_ptr(), dtype, nx, ny, nz, sy, sz,
-                                        torch.cuda.current_stream().cuda_stream)
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        got = mf.mf_sum_strided_noalloc(arr.data_ptr(), dtype, nx, ny, nz, sy, sz, stream)
         exact = math.fsum(dense.ravel().tolist())
         assert abs(got - ref) <= 4 * math.ulp(abs(ref)), (dtype, got, ref)
         assert abs(got - exact) <= 2 * math.ulp(abs(exact)), (dtype, got, exact)
+
+
+def test_noalloc_sum_refuses_a_capturing_stream():
+    """The call waits for its result, so on a stream that is capturing a graph it returns
+    MF_ESTATE without enqueueing anything, and the capture stays usable."""
+    arr = torch.ones(64, dtype=torch.float32, device="cuda")
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        with pytest.raises(mf.MFError) as e:
+            mf.mf_sum_strided_noalloc(arr.data_ptr(), "f32", 64, 1, 1, 64, 64, s.cuda_stream)
+        arr.add_(1.0)
+    assert e.value.code == mf.MF_ESTATE
+    g.replay()
+    torch.cuda.synchronize()
+    assert float(arr.sum()) == 128.0
+    assert mf.mf_sum_strided_noalloc(arr.data_ptr(), "f32", 64, 1, 1, 64, 64) == 128.0
 
 
 def test_noalloc_sum_rejects_inputs_beyond_its_scratch():
