@@ -47,11 +47,17 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="headline only (no FP64, e2e, CPU baseline)")
     p.add_argument("--tile", default=None, help="fixed tile 'x,y,z' instead of the autotuner (0 = whole box)")
     p.add_argument("--kernel", default="tma", choices=["tma", "global"], help="stencil kernel variant")
-    p.add_argument("--only", default=None, choices=["bf16_batched", "rk3_8th", "amr2lev_reflux", "manybox512"],
+    p.add_argument("--only", default=None,
+                   choices=["bf16_batched", "rk3_8th", "amr2lev_reflux", "manybox512", "fp64_fixed"],
                    help="run only this secondary line (for profiling) and print it")
     p.add_argument("--schedule", default=None,
                    help="fixed schedule 'x,y,z,rows,stages,group_bytes' instead of the autotuner")
-    return p.parse_args()
+    p.add_argument("--fixed", action="store_true",
+                   help="headline with --dtype f64: fixed-point differences (MF_FIXED_DIFF)")
+    a = p.parse_args()
+    if a.fixed and a.dtype != "f64":
+        p.error("--fixed needs --dtype f64")
+    return a
 
 
 def dist_env():
@@ -198,7 +204,8 @@ def cpu_baseline(cfg, target_s=15.0):
 # ------------------------------------------------------------------ our arm
 
 KERNEL_SOURCES = {
-    "k_stencil_tma": ["stencil_tma_kernel.cuh", "stencil_tma.cu", "stencil_common.cuh", "mf_internal.h"],
+    "k_stencil_tma": ["stencil_tma_kernel.cuh", "stencil_tma.cu", "stencil_tma_fix.cu", "fixed_diff.cuh",
+                      "stencil_common.cuh", "mf_internal.h"],
     "k_stencil": ["mf_kernels.cu", "stencil_common.cuh", "mf_internal.h"],
 }
 
@@ -277,6 +284,83 @@ def whole_job_rate(ws, units_per_rank, seconds):
 
 
 RK3_CFG = dict(N=256, max_grid_size=64, ngrow=4, ncomp=1, R=4, nsteps=20, dtype="f32", nmodes=8, kmax=8)
+
+
+def stencil_phase(mfab, R, D, dt, nsteps, flags, steps, flush):
+    """Device time of the stencil launches of one advance, from the events the graph records
+    wherever the kind of launch changes: (average stencil launch in s, fill ms per advance,
+    launch counts)."""
+    import paper_1604_03570_gb300 as mf
+    mf.mf_set_timing(mfab.h, 1)
+    for _ in range(2):
+        mf.mf_advance(mfab.h, R, D, dt, nsteps, flags)
+    fill_ms = st_ms = 0.0
+    for _ in range(steps):
+        time_advances(mfab, R, D, dt, nsteps, 1, flush, flags)
+        a, b = mf.mf_phase_ms(mfab.h)
+        fill_ms += a
+        st_ms += b
+    mf.mf_set_timing(mfab.h, 0)
+    launches = mf.mf_launch_count(mfab.h)
+    return st_ms * 1e-3 / (launches["stencil"] * steps), fill_ms / steps, launches
+
+
+def fixed_line(mf, torch, flush, args, hbm):
+    """The headline grid stored in FP64 with the differences in exact fixed-point integers and one
+    FP64 FMA per cell (MF_FIXED_DIFF): FP64-accurate results (<= 1e-12 of the oracle, checked by
+    the full-size tests) at memory speed.  Reports the step's fraction of the HBM roofline on
+    the FP64 step bytes, the stencil kernel's own fraction, and the speedup over the plain
+    per-box FP64 sweep (the untiled MFIter loop, FP64 arithmetic) and the batched FP64 one."""
+    cfg = dict(synth.WORKLOADS[WORKLOAD])
+    N, R, nsteps, C = cfg["N"], cfg["R"], cfg["nsteps"], cfg["ncomp"]
+    lo, hi = [0, 0, 0], [N - 1] * 3
+    D = [1.0] * C
+    dt = synth.dt_for(cfg)
+    V = N ** 3
+    dense = synth.initial_field(cfg)
+    FIX = mf.MF_FIXED_DIFF
+
+    def level():
+        m = mf.MultiFab(lo, hi, max_grid_size=cfg["max_grid_size"], ncomp=C, ngrow=cfg["ngrow"], dtype="f64")
+        m.from_host(dense)
+        return m
+
+    g = level()
+    for _ in range(2):
+        mf.mf_advance(g.h, R, D, dt, nsteps, FIX)
+    K = max(3, args.steps // 2)
+    t = time_advances(g, R, D, dt, nsteps, K, flush, FIX)
+    v = V * nsteps * K / (sum(t) * 1e-3)
+    step_bytes = mf.mf_step_bytes(g.h, R)
+    st_s, fill_ms, launches = stencil_phase(g, R, D, dt, nsteps, FIX, K, flush)
+    b = cfg["max_grid_size"]
+    nbox = (N // b) ** 3
+    st_bytes = 8 * C * (2 * V + nbox * 6 * R * b * b)
+    sched = mf.mf_get_schedule(g.h)
+    del g
+    torch.cuda.empty_cache()
+    f64 = level()
+    for _ in range(2):
+        mf.mf_advance(f64.h, R, D, dt, nsteps)
+    t64 = time_advances(f64, R, D, dt, nsteps, 2, flush)
+    v64 = V * nsteps * 2 / (sum(t64) * 1e-3)
+    del f64
+    plain = level()
+    mf.mf_advance(plain.h, R, D, dt, nsteps, mf.MF_PLAIN_PER_BOX)
+    tp = time_advances(plain, R, D, dt, nsteps, 2, flush, mf.MF_PLAIN_PER_BOX)
+    vplain = V * nsteps * 2 / (sum(tp) * 1e-3)
+    del plain
+    torch.cuda.empty_cache()
+    return {"value": v, "unit": UNIT, "workload": WORKLOAD + ", FP64 storage, MF_FIXED_DIFF",
+            "ms_per_bench_step": sum(t) / K, "step_bytes": step_bytes,
+            "step_frac": step_bytes * nsteps * K / (sum(t) * 1e-3) / 1e9 / hbm,
+            "kernel": {"name": "k_stencil_tma<f64,fixed,R=%d>" % R, "avg_launch_us": st_s * 1e6,
+                       "algorithmic_bytes_per_launch": st_bytes, "achieved_gbs": st_bytes / st_s / 1e9,
+                       "frac": st_bytes / st_s / 1e9 / hbm},
+            "fill_phase_us_per_bench_step": fill_ms * 1e3,
+            "launches_per_bench_step": launches, "schedule": sched,
+            "fp64_batched_value": v64, "fp64_plain_per_box_value": vplain,
+            "speedup_vs_fp64_plain_per_box": v / vplain, "speedup_vs_fp64_batched": v / v64}
 
 
 def manybox_step_bytes(S, C, boxes, R):
@@ -483,14 +567,15 @@ def run_ours(args, cfg, ws, rank, local):
         head.set_tile(tuple(v[:3]))
         mf.mf_set_schedule(head.h, *v[3:6])
     mf.mf_set_kernel(head.h, mf.MF_KERNEL_TMA if args.kernel == "tma" else mf.MF_KERNEL_GLOBAL)
+    hflags = mf.MF_FIXED_DIFF if args.fixed else 0
     for _ in range(args.warmup):
-        mf.mf_advance(head.h, R, D, dt, nsteps)
+        mf.mf_advance(head.h, R, D, dt, nsteps, hflags)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        times = time_advances(head, R, D, dt, nsteps, args.steps, flush)
+        times = time_advances(head, R, D, dt, nsteps, args.steps, flush, hflags)
     torch.cuda.synchronize()
     total_ms = max_over_ranks(sum(times), dist, dev)
     if dist:
@@ -501,16 +586,17 @@ def run_ours(args, cfg, ws, rank, local):
     launches = mf.mf_launch_count(head.h)  # of one mf_advance (the graph replayed every bench step)
     sched = mf.mf_get_schedule(head.h)
     kname = "k_stencil_tma" if sched["kernel"] == "tma" else "k_stencil"
+    kvar = "%s,fixed" % args.dtype if args.fixed else args.dtype
 
     # ---- roofline of the dominant kernel (stencil): events inside the graph wherever the kind
     # of launch changes, so the back-to-back stencil launches are timed without nodes between
     mf.mf_set_timing(head.h, 1)
     for _ in range(2):
-        mf.mf_advance(head.h, R, D, dt, nsteps)
+        mf.mf_advance(head.h, R, D, dt, nsteps, hflags)
     fill_ms, st_ms = 0.0, 0.0
     t_timed = []
     for _ in range(args.steps):
-        t_timed += time_advances(head, R, D, dt, nsteps, 1, flush)
+        t_timed += time_advances(head, R, D, dt, nsteps, 1, flush, hflags)
         a, b = mf.mf_phase_ms(head.h)
         fill_ms += a
         st_ms += b
@@ -528,9 +614,9 @@ def run_ours(args, cfg, ws, rank, local):
     hbm = float(peaks["hbm_gbs"])
     achieved = st_bytes / st_avg_s / 1e9
     step_bytes = mf.mf_step_bytes(head.h, R)
-    roof = {"bound": "hbm", "kernel": "%s<%s,R=%d>" % (kname, args.dtype, R), "achieved": achieved, "peak": hbm,
+    roof = {"bound": "hbm", "kernel": "%s<%s,R=%d>" % (kname, kvar, R), "achieved": achieved, "peak": hbm,
             "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind + " (STREAM-style copy)",
-            "traffic": traffic_for(kname, WORKLOAD, args.dtype),
+            "traffic": traffic_for(kname, WORKLOAD, kvar),
             "algorithmic_bytes_per_launch": st_bytes, "avg_launch_us": st_avg_s * 1e6,
             "stencil_launches_per_bench_step": launches["stencil"],
             "fill_launches_per_bench_step": launches["fill"],
@@ -601,7 +687,7 @@ def run_ours(args, cfg, ws, rank, local):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             mf.mf_copy_from_host(head.h, pin_in)
-            mf.mf_advance(head.h, R, D, dt, nsteps)
+            mf.mf_advance(head.h, R, D, dt, nsteps, hflags)
             mf.mf_copy_to_host(head.h, pin_out)
             t1 = time.perf_counter()
             if k >= args.warmup:
@@ -637,8 +723,8 @@ def run_ours(args, cfg, ws, rank, local):
                                      "launches_per_time_step": 2 * nbox}
         # secondary lines, on one GPU only (the scaling runs compare the headline); a failure is
         # reported in its own entry and does not void the headline
-        secondary = (("bf16_batched", bf16_line), ("rk3_8th", rk3_line), ("amr2lev_reflux", amr_line),
-                     ("manybox512", manybox_line))
+        secondary = (("fp64_fixed", fixed_line), ("bf16_batched", bf16_line), ("rk3_8th", rk3_line),
+                     ("amr2lev_reflux", amr_line), ("manybox512", manybox_line))
         for key, line in (secondary if ws == 1 else ()):
             try:
                 out[key] = line(mf, torch, flush, args, hbm)
@@ -678,7 +764,7 @@ def main():
         peaks, _ = measured_peaks()
         hbm = float(peaks["hbm_gbs"])
         line = {"bf16_batched": bf16_line, "rk3_8th": rk3_line, "amr2lev_reflux": amr_line,
-                "manybox512": manybox_line}[args.only](
+                "manybox512": manybox_line, "fp64_fixed": fixed_line}[args.only](
             mf, torch, flush, args, hbm)
         print(json.dumps({args.only: line}))
         return 0

@@ -48,13 +48,15 @@ enum {
     MF_FP64_DIFF = 1,     /* FP32/BF16 storage: compute the flux differences in FP64 */
     MF_PLAIN_PER_BOX = 2, /* the untiled baseline of Sec. 3.1: one launch per box per phase,
                              launched eagerly, no work list, no graph */
-    MF_REFLUX = 4         /* mf_amr_advance only: Berger-Colella refluxing (see there) */
+    MF_REFLUX = 4,        /* mf_amr_advance only: Berger-Colella refluxing (see there) */
+    MF_FIXED_DIFF = 8     /* mf_advance, FP64 storage, TMA kernel: the differences in exact
+                             fixed-point integer arithmetic, one FP64 operation per cell (below) */
 };
 
 typedef struct {
     int kind;                  /* mf_stencil_kind */
     const double *diffusivity; /* [ncomp] D_c > 0 */
-    int flags;                 /* MF_FP64_DIFF | MF_PLAIN_PER_BOX | MF_REFLUX */
+    int flags;                 /* MF_FP64_DIFF | MF_PLAIN_PER_BOX | MF_REFLUX | MF_FIXED_DIFF */
 } mf_stencil;
 
 /* Error codes */
@@ -228,6 +230,18 @@ int mf_average_down(const mf_t *fine, mf_t *crse, int ratio);
  * neighbour box, and the stencil may write the y/z face ghosts of the level it produces (the
  * autotuner times both ways).  The ghost cells of the result are therefore not all current:
  * call mf_fill_boundary before reading them.
+ *
+ * MF_FIXED_DIFF (FP64 storage; TMA kernel; not with MF_PLAIN_PER_BOX): the same operator, with
+ * the update evaluated as u + lam * D in one FP64 fused multiply-add and the Laplacian D formed
+ * exactly.  Every value read is mapped to a 64-bit integer on a grid Q fixed per component for
+ * each step, Q = 2^(1 - B) * 2^E with 2^E <= max|u| < 2^(E + 1) over the level's valid cells and
+ * B = 58, 55, 46 bits for R = 1, 2, 4; the integer Laplacian is exact and is rounded once to
+ * FP64 (toward zero).  Per step, |D - Lap u| <= sum_j |c_j| * Q + 2^-52 |D| (c_j the operator's
+ * weights): 12 * 2^-57 max|u| + 2^-52 |D| at R = 1.  The grid of each step comes from the level maximum the previous step's kernel
+ * reduces (the first from one extra pass over the level), so the results are bitwise
+ * independent of tiles and box layout.  A non-finite value in the level makes the next
+ * synchronising call fail with MF_ECUDA.  FP64 arithmetic is slow next to memory bandwidth on
+ * some GPUs (GB300 issues about 2 FP64 operations per clock per SM); this path needs one.
  */
 int mf_advance(mf_t *mf, const mf_stencil *st, double dt, int nsteps);
 
@@ -304,7 +318,8 @@ int mf_set_timing(mf_t *mf, int on);
 int mf_phase_ms(mf_t *mf, double out[2]);
 
 /* Kernel launches of the last mf_advance (or, on the coarse handle, mf_amr_advance) call:
- * out[0] ghost-fill, out[1] stencil, out[2] coarse-fine interpolation and flux-register,
+ * out[0] ghost-fill (and, with MF_FIXED_DIFF, the one level-maximum pass), out[1] stencil,
+ * out[2] coarse-fine interpolation and flux-register,
  * out[3] average-down and reflux launches.  Launches whose work list is empty are not made and not counted. */
 int mf_launch_count(const mf_t *mf, int out[4]);
 

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libmf.so")
 MF_F64, MF_F32, MF_BF16 = 0, 1, 2
 DTYPES = {"f64": MF_F64, "f32": MF_F32, "bf16": MF_BF16}
 MF_LAP2_7PT, MF_LAP4_13PT, MF_LAP8_25PT = 1, 2, 4
-MF_FP64_DIFF, MF_PLAIN_PER_BOX, MF_REFLUX = 1, 2, 4
+MF_FP64_DIFF, MF_PLAIN_PER_BOX, MF_REFLUX, MF_FIXED_DIFF = 1, 2, 4, 8
 MF_KERNEL_TMA, MF_KERNEL_GLOBAL = 0, 1
 MF_RED_SUM, MF_RED_MAX, MF_RED_MIN, MF_RED_NORM0, MF_RED_NORM1, MF_RED_NORM2 = 0, 1, 2, 3, 4, 5
 REDUCTIONS = {"sum": MF_RED_SUM, "max": MF_RED_MAX, "min": MF_RED_MIN, "norm0": MF_RED_NORM0,

@@ -284,11 +284,14 @@ struct mf {
     DevBuf d_rowpre;  // first valid row (y, z) of every FArrayBox in the reductions' row list
     // TMA-staged stencil: tensor maps of every FArrayBox over each time level, plane geometry
     DevBuf d_maps, d_tfab, d_err, d_smaps, d_strips, d_fbtasks_adv, d_push, d_fbtasks_res;
+    // fixed-point differences (MF_FIXED_DIFF): three sets of kMaxComp words, each the high word
+    // of the largest |u| of one level per component (see mf_advance)
+    DevBuf d_fix;
     std::vector<FbTask> fbtasks_res;  // the fill left once the stencil pushes face ghosts
     bool tma_push = false;
     bool push_pref = true;         // the autotuner's choice between the ghost push and the face fill
     bool tma_strips = false;  // x halos pulled from neighbour boxes (fill skips x faces)
-    int tma_R = 0;            // radius the maps were encoded for (0 = none)
+    int tma_R = 0;            // tma_key of the radius and arithmetic the maps were built for (0 = none)
     bool tma_ok = false;      // current tile shape fits the TMA kernel
     int tma_cpt = 32, tma_slot = 0, tma_ns = 0;  // tma_cpt: CTA threads of the TMA stencil
     int tma_rows = 2;     // rows per consumer thread (autotuned; clipped to what the radius allows)
@@ -744,6 +747,7 @@ extern "C" int mf_attach(mf_t *m, void *dev_ptr, size_t bytes, void *stream) {
     if ((rc = m->d_tfab.ensure(m->fabs.size() * sizeof(TmaFab)))) return rc;
     if ((rc = m->d_err.ensure(sizeof(int)))) return rc;
     CU(cudaMemsetAsync(m->d_err.p, 0, sizeof(int), m->stream));
+    if ((rc = m->d_fix.ensure(3 * kMaxComp * sizeof(unsigned int)))) return rc;
     m->tma_R = 0;
     if ((rc = m->d_sumout.ensure(sizeof(double)))) return rc;
     CU(cudaStreamSynchronize(m->stream));  // host vectors may change after return
@@ -763,7 +767,8 @@ static int check_device_error(mf_t *m) {
     CU(cudaMemcpy(&e, m->d_err.p, sizeof(int), cudaMemcpyDeviceToHost));
     if (e) {
         cudaMemsetAsync(m->d_err.p, 0, sizeof(int), m->stream);
-        return fail(MF_ECUDA, "a bounded wait inside a stencil kernel expired (device error word %d)", e);
+        if (e & 1) return fail(MF_ECUDA, "a bounded wait inside a stencil kernel expired (device error word %d)", e);
+        return fail(MF_ECUDA, "a non-finite value reached the fixed-point stencil (MF_FIXED_DIFF; device error word %d)", e);
     }
     return 0;
 }
@@ -985,8 +990,8 @@ static int eff_gb(const mf_t *m, int R) {
 // thread than the kernel keeps in registers.  A box whose two x faces are served by strips
 // (served[2b], served[2b+1]) loads only its valid cells of each row, rounded up to 16 bytes;
 // the others load the whole row, ghost columns and padding included.
-static bool tma_geometry(mf_t *m, int R, const std::vector<char> &served, std::vector<TmaFab> &tf, int &slot_bytes,
-                         int &gpt) {
+static bool tma_geometry(mf_t *m, int R, bool fix, const std::vector<char> &served, std::vector<TmaFab> &tf,
+                         int &slot_bytes, int &gpt) {
     const int S = m->esize, A = 16 / S, g = m->ngrow;
     tf.assign(m->fabs.size(), TmaFab{});
     int maxplane = 0, maxgroups = 0;
@@ -1014,7 +1019,7 @@ static bool tma_geometry(mf_t *m, int R, const std::vector<char> &served, std::v
     }
     // a producer warp plus one consumer thread per group, rounded up to a warp
     gpt = 32 + (maxgroups + 31) / 32 * 32;
-    if (gpt > tma_max_threads(R)) return false;
+    if (gpt > (fix ? tma_max_threads_fix(R) : tma_max_threads(R))) return false;
     slot_bytes = (maxplane + 127) / 128 * 128;
     return true;
 }
@@ -1143,12 +1148,17 @@ static void balance_tiles(const mf_t *m, int G, std::vector<Tile> &out, std::vec
     while (cur < G) first[++cur] = (int)out.size();
 }
 
-static int build_tma(mf_t *m, int R) {
+// The TMA build (tensor maps, plane geometry, schedule, push and fill lists) depends on the
+// radius and, through the CTA size and residency, on the kernel variant: plain arithmetic, or
+// the fixed-point differences of FP64 storage.
+static int tma_key(int R, bool fix) { return R + (fix ? 8 : 0); }
+
+static int build_tma(mf_t *m, int R, bool fix = false) {
     invalidate_graphs(m);
     m->tma_ok = false;
     m->tma_strips = false;
     m->tma_push = false;
-    m->tma_R = R;
+    m->tma_R = tma_key(R, fix);
     m->tma_grid = 0;
     m->cta_tiles.clear();
     if (!m->use_tma) return 0;
@@ -1164,7 +1174,7 @@ static int build_tma(mf_t *m, int R) {
         std::vector<TileStrip> st0;
         std::vector<char> served0;
         find_strips(m, R, st0, served0);
-        if (!tma_geometry(m, R, served0, tf, main_slot, gpt)) return 0;
+        if (!tma_geometry(m, R, fix, served0, tf, main_slot, gpt)) return 0;
     }
     const int strip_bytes = XW * srows * S;
     const int strip_pitch = (strip_bytes + 127) / 128 * 128;
@@ -1175,7 +1185,8 @@ static int build_tma(mf_t *m, int R) {
     if (ns < 2 * R + 1 || (long long)ns * slot + 128 > 200 * 1024) return 0;
     if (m->tile[2] <= 0) {
         // whole-box z extent: split the columns over exactly one wave of CTAs
-        const int per_sm = tma_ctas_per_sm(m->dtype, R, eff_rows(m, R), eff_gb(m, R), gpt, ns * slot + 128);
+        const int per_sm = fix ? tma_ctas_per_sm_fix(R, eff_rows(m, R), eff_gb(m, R), gpt, ns * slot + 128)
+                               : tma_ctas_per_sm(m->dtype, R, eff_rows(m, R), eff_gb(m, R), gpt, ns * slot + 128);
         if (per_sm < 1) return 0;
         const int G = per_sm * sm_count();
         balance_tiles(m, G, m->tiles, m->cta_tiles);
@@ -1362,12 +1373,18 @@ static StencilParams stencil_params(const mf_t *m, int from, const double *lam, 
     return p;
 }
 
+// fixstep >= 0: the fixed-point-difference kernel (FP64 storage), as step fixstep of an advance:
+// it reads word set fixstep % 3 (the largest |u| of level `from`), accumulates the largest |u|
+// it writes into set (fixstep + 1) % 3 and clears set (fixstep + 2) % 3 for the step after it.
 static int enqueue_stencil(mf_t *m, int from, int R, bool fp64diff, const double *lam, cudaStream_t s,
-                           bool push = false, const StageArgs &sa = StageArgs{}) {
-    if (m->use_tma && m->tma_R != R) {
-        int rc = build_tma(m, R);
+                           bool push = false, const StageArgs &sa = StageArgs{}, int fixstep = -1) {
+    const bool fix = fixstep >= 0;
+    if (m->use_tma && m->tma_R != tma_key(R, fix)) {
+        int rc = build_tma(m, R, fix);
         if (rc) return rc;
     }
+    if (fix && !(m->use_tma && m->tma_ok))
+        return fail(MF_EINVAL, "MF_FIXED_DIFF runs on the TMA stencil, which this tile shape or kernel choice excludes");
     if (m->use_tma && m->tma_ok) {
         StencilTmaParams p{};
         p.maps = (const CUtensorMap *)m->d_maps.p + (size_t)from * m->fabs.size();
@@ -1394,11 +1411,31 @@ static int enqueue_stencil(mf_t *m, int from, int R, bool fp64diff, const double
         p.push = (push && m->tma_push) ? (const PushPiece *)m->d_push.p : nullptr;
         p.cta_tiles = m->tma_grid ? (const int *)m->d_cta.p : nullptr;
         for (int c = 0; c < m->ncomp; ++c) p.lam[0][c] = lam[c];
+        if (fix) {
+            unsigned int *w = (unsigned int *)m->d_fix.p;
+            p.fix_in = w + (fixstep % 3) * kMaxComp;
+            p.fix_out = w + ((fixstep + 1) % 3) * kMaxComp;
+            p.fix_clear = w + ((fixstep + 2) % 3) * kMaxComp;
+            for (int c = 0; c < m->ncomp; ++c) p.lam[0][c] = lam[c] / fix_den(R);
+            CU(launch_stencil_tma_fix(R, eff_rows(m, R), eff_gb(m, R), m->tma_cpt, p, m->tma_grid, s));
+            return 0;
+        }
         CU(launch_stencil_tma(m->dtype, R, fp64diff, eff_rows(m, R), eff_gb(m, R), m->tma_cpt, p, m->tma_grid, s));
         return 0;
     }
     StencilParams p = stencil_params(m, from, lam, sa);
     CU(launch_stencil(m->dtype, R, fp64diff, p, m->block[0], m->block[1], 0, s));
+    return 0;
+}
+
+// The first grid of a fixed-point advance: all three word sets cleared, then set 0 = the largest
+// |u| of level `which` (valid cells), which step 0 reads.
+static int enqueue_fix_start(mf_t *m, int which, cudaStream_t s) {
+    CU(cudaMemsetAsync(m->d_fix.p, 0, 3 * kMaxComp * sizeof(unsigned int), s));
+    int maxz = 1;
+    for (auto &f : m->fabs) maxz = std::max(maxz, f.n[2]);
+    CU(launch_fix_emax(m->level_ptr(which), (const FabInfo *)m->d_fabs.p, (int)m->fabs.size(), m->ncomp, maxz,
+                       (unsigned int *)m->d_fix.p, s));
     return 0;
 }
 
@@ -1432,11 +1469,17 @@ static int check_stencil(const mf_t *m, const mf_stencil *st, double dt, double 
 // Autotune: time every candidate schedule -- tile shape, and for the TMA kernel rows per
 // thread and ring depth -- on the live data (current -> other level, which is scratch at this
 // point) and keep the fastest.  Synchronous; runs once per handle.
-static int autotune(mf_t *m, int R, bool fp64diff, const double *lam) {
+static int autotune(mf_t *m, int R, bool fp64diff, const double *lam, bool fix = false) {
     auto tiles = tile_candidates(m);
     struct Cand { std::array<int, 3> t; int rows, ns, gb; };
     std::vector<Cand> cands;
+    const int fixstep = fix ? 0 : -1;  // every timed launch reads word set 0 (level cur)
+    if (fix) {
+        int rc = enqueue_fix_start(m, m->cur, m->stream);
+        if (rc) return rc;
+    }
     for (auto &t : tiles) {
+        if (fix && !(m->use_tma && t[0] == 0)) continue;  // the fixed-point path is TMA only
         if (m->use_tma && t[0] == 0) {
             for (int rows = 1; rows <= tma_max_rows(R); ++rows)
                 for (int gb : {16, 32})
@@ -1465,11 +1508,18 @@ static int autotune(mf_t *m, int R, bool fp64diff, const double *lam) {
         m->tma_gb = c.gb;
         int rc = set_tiles(m, c.t.data());
         if (rc) return rc;
-        if ((rc = enqueue_stencil(m, m->cur, R, fp64diff, lam, m->stream, true))) return rc;
+        if (fix) {  // a tile shape the TMA kernel cannot take is no candidate here
+            if ((rc = build_tma(m, R, true))) return rc;
+            if (!(m->use_tma && m->tma_ok)) {
+                if (ms) *ms = 1e30f;
+                return 0;
+            }
+        }
+        if ((rc = enqueue_stencil(m, m->cur, R, fp64diff, lam, m->stream, true, StageArgs{}, fixstep))) return rc;
         if (!ms) return 0;
         CU(cudaEventRecord(e0, m->stream));
         for (int i = 0; i < n; ++i)
-            if ((rc = enqueue_stencil(m, m->cur, R, fp64diff, lam, m->stream, true))) return rc;
+            if ((rc = enqueue_stencil(m, m->cur, R, fp64diff, lam, m->stream, true, StageArgs{}, fixstep))) return rc;
         CU(cudaEventRecord(e1, m->stream));
         CU(cudaEventSynchronize(e1));
         CU(cudaEventElapsedTime(ms, e0, e1));
@@ -1510,7 +1560,7 @@ static int autotune(mf_t *m, int R, bool fp64diff, const double *lam) {
                 else if (!m->fbtasks_res.empty())
                     CU(launch_fill(m->dtype, level_ptrs(m, m->cur), (const FbTask *)m->d_fbtasks_res.p,
                                    (int)m->fbtasks_res.size(), 0, m->stream));
-                if (!r) r = enqueue_stencil(m, m->cur, R, fp64diff, lam, m->stream, push);
+                if (!r) r = enqueue_stencil(m, m->cur, R, fp64diff, lam, m->stream, push, StageArgs{}, fixstep);
                 if (r) return r;
             }
             CU(cudaEventRecord(e1, m->stream));
@@ -1548,7 +1598,7 @@ extern "C" int mf_set_schedule(mf_t *m, const int in[3]) {
 extern "C" int mf_get_schedule(const mf_t *m, int out[7]) {
     if (!m || !out) return fail(MF_EINVAL, "null argument");
     for (int d = 0; d < 3; ++d) out[d] = m->tile[d];
-    const int R = m->tma_R ? m->tma_R : 1;
+    const int R = m->tma_R ? (m->tma_R & 7) : 1;
     out[3] = eff_rows(m, R);
     out[4] = m->tma_ns;
     out[5] = (m->use_tma && m->tma_ok) ? MF_KERNEL_TMA : MF_KERNEL_GLOBAL;
@@ -1708,15 +1758,22 @@ extern "C" int mf_advance(mf_t *m, const mf_stencil *st, double dt, int nsteps) 
     if (nsteps == 0) return 0;
     const int R = st->kind;
     const bool fp64diff = (st->flags & MF_FP64_DIFF) && m->dtype != F64;
+    const bool fixed = (st->flags & MF_FIXED_DIFF) != 0;
     if (st->flags & MF_REFLUX) return fail(MF_EINVAL, "MF_REFLUX applies to mf_amr_advance only");
+    if (fixed) {
+        if (m->dtype != F64) return fail(MF_EINVAL, "MF_FIXED_DIFF applies to FP64 storage");
+        if (st->flags & MF_PLAIN_PER_BOX) return fail(MF_EINVAL, "MF_FIXED_DIFF does not combine with MF_PLAIN_PER_BOX");
+        if (!m->use_tma) return fail(MF_EINVAL, "MF_FIXED_DIFF runs on the TMA stencil (MF_KERNEL_TMA)");
+    }
     if (st->flags & MF_PLAIN_PER_BOX) {
         if (fp64diff) return fail(MF_EINVAL, "MF_PLAIN_PER_BOX does not combine with MF_FP64_DIFF");
         return advance_plain(m, R, lam, nsteps);
     }
-    if (m->tile_auto && (rc = autotune(m, R, fp64diff, lam))) return rc;
-    if (m->use_tma && m->tma_R != R && (rc = build_tma(m, R))) return rc;  // never inside a capture
+    if (m->tile_auto && (rc = autotune(m, R, fp64diff, lam, fixed))) return rc;
+    if (m->use_tma && m->tma_R != tma_key(R, fixed) && (rc = build_tma(m, R, fixed))) return rc;  // never inside a capture
+    if (fixed && !m->tma_ok) return fail(MF_EINVAL, "MF_FIXED_DIFF runs on the TMA stencil, which this tile shape excludes");
     char kb[48];
-    snprintf(kb, sizeof kb, "%s|g%llu", m->timing ? "advT" : "adv", m->gen);
+    snprintf(kb, sizeof kb, "%s|g%llu|x%d", m->timing ? "advT" : "adv", m->gen, (int)fixed);
     const std::string key = graph_key(kb, R, fp64diff, lam, m->ncomp, nsteps, m->cur);
     auto it = m->graphs.find(key);
     if (it == m->graphs.end()) {
@@ -1725,6 +1782,8 @@ extern "C" int mf_advance(mf_t *m, const mf_stencil *st, double dt, int nsteps) 
         int body = 0, from = m->cur;
         PhaseLog log{m, m->timing};
         body = log.start();
+        // the fixed-point grid of the first step: the largest |u| of the current level
+        if (fixed && !body && !(body = log.before(0))) body = enqueue_fix_start(m, from, m->cap);
         const bool push = use_push(m);
         for (int s = 0; s < nsteps && !body; ++s) {
             if (push && s > 0) {
@@ -1738,7 +1797,7 @@ extern "C" int mf_advance(mf_t *m, const mf_stencil *st, double dt, int nsteps) 
                 body = enqueue_fill_step(m, from, m->cap);
             }
             if (!body) body = log.before(1);
-            if (!body) body = enqueue_stencil(m, from, R, fp64diff, lam, m->cap, push);
+            if (!body) body = enqueue_stencil(m, from, R, fp64diff, lam, m->cap, push, StageArgs{}, fixed ? s : -1);
             from = 1 - from;
         }
         if (!body) body = log.finish();
@@ -1779,12 +1838,13 @@ extern "C" int mf_rk3_advance(mf_t *m, const mf_stencil *st, double dt, int nste
     double lam[kMaxComp];
     if ((rc = check_stencil(m, st, dt, lam, 1.0))) return rc;
     if (nsteps < 0) return fail(MF_EINVAL, "nsteps must be >= 0");
-    if (st->flags & (MF_PLAIN_PER_BOX | MF_REFLUX)) return fail(MF_EINVAL, "MF_PLAIN_PER_BOX and MF_REFLUX do not apply to mf_rk3_advance");
+    if (st->flags & (MF_PLAIN_PER_BOX | MF_REFLUX | MF_FIXED_DIFF))
+        return fail(MF_EINVAL, "MF_PLAIN_PER_BOX, MF_REFLUX and MF_FIXED_DIFF do not apply to mf_rk3_advance");
     if (nsteps == 0) return 0;
     const int R = st->kind;
     const bool fp64diff = (st->flags & MF_FP64_DIFF) && m->dtype != F64;
     if (m->tile_auto && (rc = autotune(m, R, fp64diff, lam))) return rc;
-    if (m->use_tma && m->tma_R != R && (rc = build_tma(m, R))) return rc;  // never inside a capture
+    if (m->use_tma && m->tma_R != tma_key(R, false) && (rc = build_tma(m, R))) return rc;  // never inside a capture
     char kb[48];
     snprintf(kb, sizeof kb, "%s|g%llu", m->timing ? "rk3T" : "rk3", m->gen);
     const std::string key = graph_key(kb, R, fp64diff, lam, m->ncomp, nsteps, m->cur);
@@ -2354,7 +2414,8 @@ extern "C" int mf_amr_advance(mf_t *crse, mf_t *fine, const mf_stencil *st, doub
     if (ratio != 2 && ratio != 4) return fail(MF_EINVAL, "ratio must be 2 or 4");
     if (nsub < 1) return fail(MF_EINVAL, "nsub must be >= 1");
     if (ncrse_steps < 0) return fail(MF_EINVAL, "ncrse_steps must be >= 0");
-    if (st && (st->flags & MF_PLAIN_PER_BOX)) return fail(MF_EINVAL, "MF_PLAIN_PER_BOX is single-level only");
+    if (st && (st->flags & (MF_PLAIN_PER_BOX | MF_FIXED_DIFF)))
+        return fail(MF_EINVAL, "MF_PLAIN_PER_BOX and MF_FIXED_DIFF are single-level only");
     double lam_c[kMaxComp], lam_f[kMaxComp];
     if ((rc = check_stencil(crse, st, dt_crse, lam_c, 1.0))) return rc;
     // fine: dx_f = dx_c / ratio, dt_f = dt_c / nsub; lam_f = D dt_f / dx_f^2 on the fine domain
@@ -2379,8 +2440,8 @@ extern "C" int mf_amr_advance(mf_t *crse, mf_t *fine, const mf_stencil *st, doub
     }
     if (crse->tile_auto && (rc = autotune(crse, R, fp64diff, lam_c))) return rc;
     if (fine->tile_auto && (rc = autotune(fine, R, fp64diff, lam_f))) return rc;
-    if (crse->use_tma && crse->tma_R != R && (rc = build_tma(crse, R))) return rc;
-    if (fine->use_tma && fine->tma_R != R && (rc = build_tma(fine, R))) return rc;
+    if (crse->use_tma && crse->tma_R != tma_key(R, false) && (rc = build_tma(crse, R))) return rc;
+    if (fine->use_tma && fine->tma_R != tma_key(R, false) && (rc = build_tma(fine, R))) return rc;
     AmrFill *af = get_amr_fill(crse, fine, ratio, R, ip, rp, &rc);
     if (!af) return rc;
     const bool cpush = use_push(crse);

@@ -176,11 +176,29 @@ struct StencilTmaParams {
     const void *u0[kMaxLev];   // Runge-Kutta stage: state at the start of the step (nullptr: plain step)
     double rk_a, rk_b;         // the stage writes rk_a * u0 + rk_b * (forward-Euler value)
     double lam[kMaxLev][kMaxComp];
+    // fixed-point differences (FP64 storage, MF_FIXED_DIFF), per component: the high word of the
+    // largest |u| of the input level (read), the same for the output level (atomicMax), and a
+    // third word set cleared by the launch for the launch after it (see mf_advance)
+    const unsigned int *fix_in;
+    unsigned int *fix_out;
+    unsigned int *fix_clear;
 };
+
+// Denominator of the integer weights of the fixed-point path at radius R (fixed_diff.cuh FixW):
+// the launch takes lam / fix_den(R).
+inline double fix_den(int R) { return R == 1 ? 1.0 : R == 2 ? 12.0 : 5040.0; }
 
 // ---- launchers (mf_kernels.cu, stencil_tma.cu); all asynchronous on `s`
 cudaError_t launch_stencil_tma(int dtype, int R, bool fp64diff, int rows, int gb, int nt, const StencilTmaParams &p,
                                int grid, cudaStream_t s);
+// the fixed-point-difference variant (FP64 storage, p.fix_* set; stencil_tma_fix.cu)
+cudaError_t launch_stencil_tma_fix(int R, int rows, int gb, int nt, const StencilTmaParams &p, int grid, cudaStream_t s);
+int tma_ctas_per_sm_fix(int R, int rows, int gb, int nt, int smem);
+int tma_max_threads_fix(int R);  // largest CTA of the fixed-point variant
+// the high word of the largest |u| of every component of one FP64 level (valid cells) into out[c],
+// by atomicMax (out cleared by the caller)
+cudaError_t launch_fix_emax(const void *base, const FabInfo *ftab, int nfab, int ncomp, int maxz, unsigned int *out,
+                            cudaStream_t s);
 // the Runge-Kutta-stage variant (p.u0 set); launch_stencil_tma dispatches to it
 cudaError_t launch_stencil_tma_rk(int dtype, int R, bool fp64diff, int rows, int gb, int nt, const StencilTmaParams &p,
                                   int grid, cudaStream_t s);

@@ -24,6 +24,7 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "fixed_diff.cuh"
 #include "mf_internal.h"
 #include "stencil_common.cuh"
 
@@ -165,7 +166,9 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 // consumer warp keeps the tile's push pieces in a small shared-memory table, written once per
 // tile, and tests a piece's z range before touching it.
 // The CTA has 32 + (consumer groups rounded up to a warp) threads.
-template <int R> struct TmaBounds { static constexpr int threads = R == 4 ? 416 : 544; };
+template <int R, typename A = float> struct TmaBounds { static constexpr int threads = R == 4 ? 416 : 544; };
+// the fixed-point path keeps 64-bit integers in its queues: fewer threads, more registers each
+template <int R> struct TmaBounds<R, FixA> { static constexpr int threads = R == 4 ? 288 : 416; };
 
 // One ghost-push piece as a consumer warp keeps it (see the tile prologue).
 struct PushRec {
@@ -177,18 +180,21 @@ struct PushRec {
 
 
 template <typename S, typename A, int R, int ROWS, int GB, bool RK>
-__global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __grid_constant__ StencilTmaParams p) {
+__global__ void __launch_bounds__(TmaBounds<R, A>::threads) k_stencil_tma(const __grid_constant__ StencilTmaParams p) {
     using V = VG<S, GB>;
     constexpr int VX = V::n;  // cells per group: one GB-byte vector of a row
     // FP32 arithmetic at radius 1: pairs of cells through the packed f32x2 instructions
     constexpr bool kPair = std::is_same<A, float>::value && R == 1 && VX % 2 == 0;
+    // exact fixed-point differences, FP64 update (fixed_diff.cuh)
+    constexpr bool kFix = std::is_same<A, FixA>::value;
+    static_assert(!kFix || (std::is_same<S, double>::value && !RK), "fixed-point differences: FP64 storage, plain steps");
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];
     unsigned char *slots = (unsigned char *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     const int NS = p.nstages;  // power of two
     const int tid = threadIdx.x;
     const int ncw = (int)(blockDim.x >> 5) - 1;  // consumer warps
-    __shared__ PushRec ptab[TmaBounds<R>::threads / 32 - 1][kMaxPush];  // per consumer warp
+    __shared__ PushRec ptab[TmaBounds<R, A>::threads / 32 - 1][kMaxPush];  // per consumer warp
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(&full[s], 1);
@@ -205,6 +211,11 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
     if (*(volatile int *)p.err) return;  // an earlier launch already failed: do nothing
+    if constexpr (kFix) {
+        // the words the next launch accumulates into: read by the previous launch (complete
+        // now), written by no thread of this one
+        if (blockIdx.x == 0 && tid < kMaxComp) p.fix_clear[tid] = 0u;
+    }
     // this CTA's tiles: its own range of a balanced schedule, else every gridDim.x-th tile
     int w0 = blockIdx.x, w1 = p.ntiles, ws = gridDim.x;
     if (p.cta_tiles) {
@@ -370,7 +381,8 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
         // the common case for the whole warp: every thread active with all its rows, whole groups,
         // no row-end completion store -- each plane is then ROWS vector stores
         const bool plain_st = __all_sync(0xffffffffu, act && nrow == ROWS && full && !lpad && !rpad);
-        const A lam = (A)p.lam[f.level][t.comp];
+        using LT = typename std::conditional<kFix, double, A>::type;
+        const LT lam = (LT)p.lam[f.level][t.comp];  // fixed-point path: lam / den
 
         // Pieces that cover every plane of the tile and whole rows (the y faces) become one
         // destination pointer per row of this thread, advanced a plane per step; the rest (z faces,
@@ -412,158 +424,9 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
         }
         const uint32_t wm = __reduce_or_sync(0xffffffffu, slow);
 
-        A q[ROWS][VX][2 * R + 1];  // z queue per cell: q[r][c][i] = u(z - R + i)
-        A fzm[ROWS][VX];
-        bool ok = true;
-#pragma unroll
-        for (int pl = 0; pl < 2 * R; ++pl) {
-            ok = ok && wait_seq(seq + pl);
-            const S *sp = slot_ptr(seq + pl);
-#pragma unroll
-            for (int r = 0; r < ROWS; ++r) {
-                A v[VX];
-                V::ld(sp + soff + r * bx, v);
-#pragma unroll
-                for (int c = 0; c < VX; ++c) q[r][c][pl] = v[c];
-            }
-        }
-        if (!__all_sync(0xffffffffu, ok)) {  // the whole warp leaves together
-            if (lane == 0) atomicOr(p.err, 1);
-            return;
-        }
-#pragma unroll
-        for (int r = 0; r < ROWS; ++r)
-#pragma unroll
-            for (int c = 0; c < VX; ++c) fzm[r][c] = face_flux<A, R>(q[r][c], R - 1);
-        // planes 0 .. R-1 live on in the queues only; so do planes tz + R .. 2R - 1 of a tile
-        // thinner than R (never a centre plane, and below the planes the z loop releases)
-        for (int pl = 0; pl < 2 * R; ++pl)
-            if (pl < R || pl >= t.tz + R) release(seq + pl);
-
-#pragma unroll(kPair ? 2 : 1)
-        for (int k = 0; k < t.tz; ++k) {
-            if (!__all_sync(0xffffffffu, wait_seq(seq + k + 2 * R))) {
-                if (lane == 0) atomicOr(p.err, 1);
-                return;
-            }
-            const S *newp = slot_ptr(seq + k + 2 * R);
-            const S *cp = slot_ptr(seq + k + R);
-#pragma unroll
-            for (int r = 0; r < ROWS; ++r) {
-                A v[VX];
-                V::ld(newp + soff + r * bx, v);
-#pragma unroll
-                for (int c = 0; c < VX; ++c) q[r][c][2 * R] = v[c];
-            }
-            // y window per column: wy[m][c] = u(x + c, y0 - R + m), m = 0 .. 2R+ROWS-1 (the set's
-            // own rows from the queues, the rest from the centre plane)
-            A wy[2 * R + ROWS][VX];
-            const S *cc = cp + soff;
-#pragma unroll
-            for (int m = 0; m < 2 * R + ROWS; ++m) {
-                if (m >= R && m < R + ROWS) continue;
-                V::ld(cc + (m - R) * bx, wy[m]);
-            }
-#pragma unroll
-            for (int r = 0; r < ROWS; ++r)
-#pragma unroll
-                for (int c = 0; c < VX; ++c) wy[R + r][c] = q[r][c][R];
-            // y-face fluxes at y0 - 1/2 + r, r = 0 .. ROWS (inner faces shared by two rows)
-            A fy[ROWS + 1][VX];
-            if constexpr (kPair) {  // radius 1: the flux is a difference, two cells per instruction
-#pragma unroll
-                for (int r = 0; r <= ROWS; ++r)
-#pragma unroll
-                    for (int c = 0; c < VX; c += 2) {
-                        const F2 d = sub2(F2{wy[r + 1][c], wy[r + 1][c + 1]}, F2{wy[r][c], wy[r][c + 1]});
-                        fy[r][c] = d.x;
-                        fy[r][c + 1] = d.y;
-                    }
-            } else {
-#pragma unroll
-                for (int c = 0; c < VX; ++c) {
-                    A col[2 * R + ROWS];
-#pragma unroll
-                    for (int m = 0; m < 2 * R + ROWS; ++m) col[m] = wy[m][c];
-#pragma unroll
-                    for (int r = 0; r <= ROWS; ++r) fy[r][c] = face_flux<A, R>(col, R - 1 + r);
-                }
-            }
-            A out[ROWS][VX];
-#pragma unroll
-            for (int r = 0; r < ROWS; ++r) {
-                // x window: w[i] = u(x0 - R + i), i = 0 .. VX + 2R - 1
-                A wx[VX + 2 * R];
-#pragma unroll
-                for (int i = 0; i < R; ++i) {
-                    wx[i] = ld_smem<S, A>(cp + hl[r][i]);
-                    wx[R + VX + i] = ld_smem<S, A>(cp + hr[r][i]);
-                }
-#pragma unroll
-                for (int c = 0; c < VX; ++c) wx[R + c] = q[r][c][R];
-                if (cov) {  // the box face is inside this group: x neighbours from the strips
-#pragma unroll
-                    for (int c = 0; c < VX; ++c)
-                        if (cov & (1u << c)) wx[R + c] = ld_smem<S, A>(cp + cob + r * p.strip_w + c);
-                }
-                A fx[VX + 1];  // x-face fluxes: fx[c] is the face left of cell c
-#pragma unroll
-                for (int c = 0; c <= VX; ++c) fx[c] = face_flux<A, R>(wx, c + R - 1);
-                if constexpr (kPair) {
-                    // the same operations as update_cell_f in the same order, two cells at a time:
-                    // ((fxp - fxm) + (fyp - fym)) + (fzp - fzm), then u + lam * div
-#pragma unroll
-                    for (int c = 0; c < VX; c += 2) {
-                        const F2 u = F2{q[r][c][1], q[r][c + 1][1]};
-                        const F2 fzp = sub2(F2{q[r][c][2], q[r][c + 1][2]}, u);
-                        const F2 dx = F2{Ar<A>::sub(fx[c + 1], fx[c]), Ar<A>::sub(fx[c + 2], fx[c + 1])};
-                        const F2 dy = sub2(F2{fy[r + 1][c], fy[r + 1][c + 1]}, F2{fy[r][c], fy[r][c + 1]});
-                        const F2 dz = sub2(fzp, F2{fzm[r][c], fzm[r][c + 1]});
-                        const F2 o = fma2(F2{lam, lam}, add2(add2(dx, dy), dz), u);
-                        out[r][c] = o.x;
-                        out[r][c + 1] = o.y;
-                        fzm[r][c] = fzp.x;
-                        fzm[r][c + 1] = fzp.y;
-                        q[r][c][0] = q[r][c][1];
-                        q[r][c][1] = q[r][c][2];
-                        q[r][c + 1][0] = q[r][c + 1][1];
-                        q[r][c + 1][1] = q[r][c + 1][2];
-                    }
-                } else {
-#pragma unroll
-                    for (int c = 0; c < VX; ++c) {
-                        const A fzp = face_flux<A, R>(q[r][c], R);
-                        out[r][c] = update_cell_f<A>(fx[c + 1], fx[c], fy[r + 1][c], fy[r][c], fzp, fzm[r][c],
-                                                     q[r][c][R], lam);
-                        fzm[r][c] = fzp;
-#pragma unroll
-                        for (int i = 0; i < 2 * R; ++i) q[r][c][i] = q[r][c][i + 1];
-                    }
-                }
-            }
-            // every read of the centre plane (and of the last R planes) is done
-            release(seq + k + R);
-            if (k >= t.tz - R) release(seq + k + 2 * R);
-            S *o = op;
-            op += f.plane;
-            if constexpr (RK) {  // a Runge-Kutta stage: rk_a * u0 + rk_b * (forward-Euler value)
-                const A rka = (A)p.rk_a, rkb = (A)p.rk_b;
-#pragma unroll
-                for (int r = 0; r < ROWS; ++r) {
-                    if (r >= nrow) continue;
-                    A u[VX];
-                    const S *urow = u0p + r * f.px;
-                    if (full) {
-                        V::ld(urow, u);
-                    } else {
-#pragma unroll
-                        for (int c = 0; c < VX; ++c) u[c] = x0c + c < f.n[0] ? ld<S, A>(urow + c) : (A)0;
-                    }
-#pragma unroll
-                    for (int c = 0; c < VX; ++c) out[r][c] = rk_combine<A>(out[r][c], u[c], rka, rkb);
-                }
-                u0p += f.plane;
-            }
+        // stores of output plane k at o: the tile's rows (with row-end completion stores where a
+        // group fills half a sector) and the ghost push into neighbour boxes
+        auto store_plane = [&](auto &out, int k, S *o) {
             if (plain_st) {
 #pragma unroll
                 for (int r = 0; r < ROWS; ++r) V::st(o + r * f.px, out[r]);
@@ -622,6 +485,269 @@ __global__ void __launch_bounds__(TmaBounds<R>::threads) k_stencil_tma(const __g
                     }
                 }
             }
+        };
+        if constexpr (kFix) {
+            // the level's grid for this component (fixed_diff.cuh); a non-finite maximum is
+            // reported through the error word (bit 2) and the launch completes as usual
+            // volatile: the word was written by the previous launch, which this one may have
+            // overlapped (programmatic dependent launch); a cached copy of an earlier step's
+            // value must not be read
+            const uint32_t wmax = *(volatile const uint32_t *)(p.fix_in + t.comp);
+            if (wmax >= 0x7ff00000u && lane == 0) atomicOr(p.err, 2);
+            const int T0 = fix_t0<R>(wmax);
+            uint32_t omax = 0u;  // fix_key of the largest value this thread writes to a valid cell
+            long long q[ROWS][VX][2 * R + 1];  // z queue per cell, fixed point: q[r][c][i] = K(z - R + i)
+            bool ok = true;
+#pragma unroll
+            for (int pl = 0; pl < 2 * R; ++pl) {
+                ok = ok && wait_seq(seq + pl);
+                const S *sp = slot_ptr(seq + pl);
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) {
+                    double v[VX];
+                    V::template ld<double>(sp + soff + r * bx, v);
+#pragma unroll
+                    for (int c = 0; c < VX; ++c) q[r][c][pl] = fix_of(v[c], T0);
+                }
+            }
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) atomicOr(p.err, 1);
+                return;
+            }
+            for (int pl = 0; pl < 2 * R; ++pl)
+                if (pl < R || pl >= t.tz + R) release(seq + pl);
+            for (int k = 0; k < t.tz; ++k) {
+                if (!__all_sync(0xffffffffu, wait_seq(seq + k + 2 * R))) {
+                    if (lane == 0) atomicOr(p.err, 1);
+                    return;
+                }
+                const S *newp = slot_ptr(seq + k + 2 * R);
+                const S *cp = slot_ptr(seq + k + R);
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) {
+                    double v[VX];
+                    V::template ld<double>(newp + soff + r * bx, v);
+#pragma unroll
+                    for (int c = 0; c < VX; ++c) q[r][c][2 * R] = fix_of(v[c], T0);
+                }
+                // y window per column: wy[m][c] = K(x + c, y0 - R + m)
+                long long wy[2 * R + ROWS][VX];
+                const S *cc = cp + soff;
+#pragma unroll
+                for (int m = 0; m < 2 * R + ROWS; ++m) {
+                    if (m >= R && m < R + ROWS) continue;
+                    double v[VX];
+                    V::template ld<double>(cc + (m - R) * bx, v);
+#pragma unroll
+                    for (int c = 0; c < VX; ++c) wy[m][c] = fix_of(v[c], T0);
+                }
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+                    for (int c = 0; c < VX; ++c) wy[R + r][c] = q[r][c][R];
+                double out[ROWS][VX];
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) {
+                    // x window: wx[i] = K(x0 - R + i)
+                    long long wx[VX + 2 * R];
+#pragma unroll
+                    for (int i = 0; i < R; ++i) {
+                        wx[i] = fix_of(cp[hl[r][i]], T0);
+                        wx[R + VX + i] = fix_of(cp[hr[r][i]], T0);
+                    }
+#pragma unroll
+                    for (int c = 0; c < VX; ++c) wx[R + c] = q[r][c][R];
+                    if (cov) {  // the box face is inside this group: x neighbours from the strips
+#pragma unroll
+                        for (int c = 0; c < VX; ++c)
+                            if (cov & (1u << c)) wx[R + c] = fix_of(cp[cob + r * p.strip_w + c], T0);
+                    }
+                    double u[VX];  // the centre values in FP64, for the update
+                    V::template ld<double>(cc + r * bx, u);
+#pragma unroll
+                    for (int c = 0; c < VX; ++c) {
+                        // direct form in exact integer arithmetic (wrapping unsigned sums: only the
+                        // unused results of ghost or padding positions can exceed the headroom)
+                        unsigned long long L = (unsigned long long)(FixW<R>::w0() * q[r][c][R]);
+#pragma unroll
+                        for (int m = 1; m <= R; ++m) {
+                            const unsigned long long pair =
+                                ((unsigned long long)wx[R + c + m] + (unsigned long long)wx[R + c - m]) +
+                                ((unsigned long long)wy[R + r + m][c] + (unsigned long long)wy[R + r - m][c]) +
+                                ((unsigned long long)q[r][c][R + m] + (unsigned long long)q[r][c][R - m]);
+                            L += (unsigned long long)FixW<R>::w(m) * pair;
+                        }
+                        out[r][c] = __fma_rn(lam, fix_to_f64((long long)L, T0), u[c]);
+                        if (act && r < nrow && x0c + c < f.n[0]) omax = max(omax, fix_key(out[r][c]));
+#pragma unroll
+                        for (int i = 0; i < 2 * R; ++i) q[r][c][i] = q[r][c][i + 1];
+                    }
+                }
+                // every read of the centre plane (and of the last R planes) is done
+                release(seq + k + R);
+                if (k >= t.tz - R) release(seq + k + 2 * R);
+                S *o = op;
+                op += f.plane;
+                store_plane(out, k, o);
+            }
+            // the level maximum of the output, per component, for the next launch's grid
+            omax = __reduce_max_sync(0xffffffffu, omax);
+            if (lane == 0 && omax) atomicMax(p.fix_out + t.comp, omax);
+        } else {
+            A q[ROWS][VX][2 * R + 1];  // z queue per cell: q[r][c][i] = u(z - R + i)
+            A fzm[ROWS][VX];
+            bool ok = true;
+#pragma unroll
+            for (int pl = 0; pl < 2 * R; ++pl) {
+                ok = ok && wait_seq(seq + pl);
+                const S *sp = slot_ptr(seq + pl);
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) {
+                    A v[VX];
+                    V::ld(sp + soff + r * bx, v);
+#pragma unroll
+                    for (int c = 0; c < VX; ++c) q[r][c][pl] = v[c];
+                }
+            }
+            if (!__all_sync(0xffffffffu, ok)) {  // the whole warp leaves together
+                if (lane == 0) atomicOr(p.err, 1);
+                return;
+            }
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+                for (int c = 0; c < VX; ++c) fzm[r][c] = face_flux<A, R>(q[r][c], R - 1);
+            // planes 0 .. R-1 live on in the queues only; so do planes tz + R .. 2R - 1 of a tile
+            // thinner than R (never a centre plane, and below the planes the z loop releases)
+            for (int pl = 0; pl < 2 * R; ++pl)
+                if (pl < R || pl >= t.tz + R) release(seq + pl);
+
+#pragma unroll(kPair ? 2 : 1)
+            for (int k = 0; k < t.tz; ++k) {
+                if (!__all_sync(0xffffffffu, wait_seq(seq + k + 2 * R))) {
+                    if (lane == 0) atomicOr(p.err, 1);
+                    return;
+                }
+                const S *newp = slot_ptr(seq + k + 2 * R);
+                const S *cp = slot_ptr(seq + k + R);
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) {
+                    A v[VX];
+                    V::ld(newp + soff + r * bx, v);
+#pragma unroll
+                    for (int c = 0; c < VX; ++c) q[r][c][2 * R] = v[c];
+                }
+                // y window per column: wy[m][c] = u(x + c, y0 - R + m), m = 0 .. 2R+ROWS-1 (the set's
+                // own rows from the queues, the rest from the centre plane)
+                A wy[2 * R + ROWS][VX];
+                const S *cc = cp + soff;
+#pragma unroll
+                for (int m = 0; m < 2 * R + ROWS; ++m) {
+                    if (m >= R && m < R + ROWS) continue;
+                    V::ld(cc + (m - R) * bx, wy[m]);
+                }
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+                    for (int c = 0; c < VX; ++c) wy[R + r][c] = q[r][c][R];
+                // y-face fluxes at y0 - 1/2 + r, r = 0 .. ROWS (inner faces shared by two rows)
+                A fy[ROWS + 1][VX];
+                if constexpr (kPair) {  // radius 1: the flux is a difference, two cells per instruction
+#pragma unroll
+                    for (int r = 0; r <= ROWS; ++r)
+#pragma unroll
+                        for (int c = 0; c < VX; c += 2) {
+                            const F2 d = sub2(F2{wy[r + 1][c], wy[r + 1][c + 1]}, F2{wy[r][c], wy[r][c + 1]});
+                            fy[r][c] = d.x;
+                            fy[r][c + 1] = d.y;
+                        }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < VX; ++c) {
+                        A col[2 * R + ROWS];
+#pragma unroll
+                        for (int m = 0; m < 2 * R + ROWS; ++m) col[m] = wy[m][c];
+#pragma unroll
+                        for (int r = 0; r <= ROWS; ++r) fy[r][c] = face_flux<A, R>(col, R - 1 + r);
+                    }
+                }
+                A out[ROWS][VX];
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) {
+                    // x window: w[i] = u(x0 - R + i), i = 0 .. VX + 2R - 1
+                    A wx[VX + 2 * R];
+#pragma unroll
+                    for (int i = 0; i < R; ++i) {
+                        wx[i] = ld_smem<S, A>(cp + hl[r][i]);
+                        wx[R + VX + i] = ld_smem<S, A>(cp + hr[r][i]);
+                    }
+#pragma unroll
+                    for (int c = 0; c < VX; ++c) wx[R + c] = q[r][c][R];
+                    if (cov) {  // the box face is inside this group: x neighbours from the strips
+#pragma unroll
+                        for (int c = 0; c < VX; ++c)
+                            if (cov & (1u << c)) wx[R + c] = ld_smem<S, A>(cp + cob + r * p.strip_w + c);
+                    }
+                    A fx[VX + 1];  // x-face fluxes: fx[c] is the face left of cell c
+#pragma unroll
+                    for (int c = 0; c <= VX; ++c) fx[c] = face_flux<A, R>(wx, c + R - 1);
+                    if constexpr (kPair) {
+                        // the same operations as update_cell_f in the same order, two cells at a time:
+                        // ((fxp - fxm) + (fyp - fym)) + (fzp - fzm), then u + lam * div
+#pragma unroll
+                        for (int c = 0; c < VX; c += 2) {
+                            const F2 u = F2{q[r][c][1], q[r][c + 1][1]};
+                            const F2 fzp = sub2(F2{q[r][c][2], q[r][c + 1][2]}, u);
+                            const F2 dx = F2{Ar<A>::sub(fx[c + 1], fx[c]), Ar<A>::sub(fx[c + 2], fx[c + 1])};
+                            const F2 dy = sub2(F2{fy[r + 1][c], fy[r + 1][c + 1]}, F2{fy[r][c], fy[r][c + 1]});
+                            const F2 dz = sub2(fzp, F2{fzm[r][c], fzm[r][c + 1]});
+                            const F2 o = fma2(F2{lam, lam}, add2(add2(dx, dy), dz), u);
+                            out[r][c] = o.x;
+                            out[r][c + 1] = o.y;
+                            fzm[r][c] = fzp.x;
+                            fzm[r][c + 1] = fzp.y;
+                            q[r][c][0] = q[r][c][1];
+                            q[r][c][1] = q[r][c][2];
+                            q[r][c + 1][0] = q[r][c + 1][1];
+                            q[r][c + 1][1] = q[r][c + 1][2];
+                        }
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < VX; ++c) {
+                            const A fzp = face_flux<A, R>(q[r][c], R);
+                            out[r][c] = update_cell_f<A>(fx[c + 1], fx[c], fy[r + 1][c], fy[r][c], fzp, fzm[r][c],
+                                                         q[r][c][R], lam);
+                            fzm[r][c] = fzp;
+#pragma unroll
+                            for (int i = 0; i < 2 * R; ++i) q[r][c][i] = q[r][c][i + 1];
+                        }
+                    }
+                }
+                // every read of the centre plane (and of the last R planes) is done
+                release(seq + k + R);
+                if (k >= t.tz - R) release(seq + k + 2 * R);
+                S *o = op;
+                op += f.plane;
+                if constexpr (RK) {  // a Runge-Kutta stage: rk_a * u0 + rk_b * (forward-Euler value)
+                    const A rka = (A)p.rk_a, rkb = (A)p.rk_b;
+#pragma unroll
+                    for (int r = 0; r < ROWS; ++r) {
+                        if (r >= nrow) continue;
+                        A u[VX];
+                        const S *urow = u0p + r * f.px;
+                        if (full) {
+                            V::ld(urow, u);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < VX; ++c) u[c] = x0c + c < f.n[0] ? ld<S, A>(urow + c) : (A)0;
+                        }
+#pragma unroll
+                        for (int c = 0; c < VX; ++c) out[r][c] = rk_combine<A>(out[r][c], u[c], rka, rkb);
+                    }
+                    u0p += f.plane;
+                }
+                store_plane(out, k, o);
+            }
         }
         seq += (uint32_t)(t.tz + 2 * R);
     }
@@ -642,7 +768,7 @@ static cudaError_t tma_configure(int smem) {
 
 template <typename S, typename A, int R, int ROWS, int GB, bool RK>
 static cudaError_t tma_t(int nt, const StencilTmaParams &p, int grid, cudaStream_t s) {
-    if (nt < 64 || nt > TmaBounds<R>::threads || nt % 32) return cudaErrorInvalidValue;
+    if (nt < 64 || nt > TmaBounds<R, A>::threads || nt % 32) return cudaErrorInvalidValue;
     const int smem = p.nstages * p.slot_bytes + 128;
     auto kern = k_stencil_tma<S, A, R, ROWS, GB, RK>;
     cudaError_t e = tma_configure<S, A, R, ROWS, GB, RK>(smem);

@@ -88,7 +88,12 @@ def exact_fourier(u0, R, lam, n):
 
 
 def level(lo, hi, dtype, **kw):
-    return mf.MultiFab(lo, hi, dtype=dtype, **kw)
+    """dtype "f64fixed": FP64 storage, advanced with the fixed-point differences (MF_FIXED_DIFF)."""
+    return mf.MultiFab(lo, hi, dtype="f64" if dtype == "f64fixed" else dtype, **kw)
+
+
+def flags_of(dtype):
+    return mf.MF_FIXED_DIFF if dtype == "f64fixed" else 0
 
 
 def field_modes(cfg, c):
@@ -97,7 +102,7 @@ def field_modes(cfg, c):
 
 # --------------------------------------------------------------------------- 256^3 / 64 boxes, 7-point, 100 steps
 
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("dtype", ["f64", "f64fixed", "f32"])
 def test_heat256_full_size_matches_exact_mode_decay(dtype):
     cfg = synth.WORKLOADS["c2"]
     N, n = cfg["N"], cfg["nsteps"]
@@ -107,13 +112,13 @@ def test_heat256_full_size_matches_exact_mode_decay(dtype):
     g = level([0, 0, 0], [N - 1] * 3, dtype, max_grid_size=cfg["max_grid_size"], ngrow=cfg["ngrow"])
     g.from_host(dense)
     s0 = g.sum(0)
-    g.advance(1, [1.0], dt, n)
+    g.advance(1, [1.0], dt, n, flags_of(dtype))
     s1 = g.sum(0)
     err = rel_err(g.to_host(), exact_modes(N, field_modes(cfg, 0), 1, lam, n)[None])
-    tol = FP64_TOL if dtype == "f64" else f32_tol("heat256")
+    tol = f32_tol("heat256") if dtype == "f32" else FP64_TOL
     print("MEASURED heat256 %s rel_err %.3e (bound %.1e) schedule %s" % (dtype, err, tol, mf.mf_get_schedule(g.h)))
     assert err <= tol
-    if dtype == "f64":  # flux form on a periodic level: the sum is invariant up to rounding
+    if dtype != "f32":  # flux form on a periodic level: the sum is invariant up to rounding
         assert abs(s1 - s0) <= n * 1e-15 * float(np.sum(np.abs(dense)))
 
 
@@ -129,7 +134,7 @@ def test_diff8th512_full_size_matches_exact_fourier_solution():
     for dtype in ("f64", "f32"):
         g = level([0, 0, 0], [N - 1] * 3, dtype, max_grid_size=cfg["max_grid_size"], ncomp=C, ngrow=cfg["ngrow"])
         g.from_host(dense)
-        g.advance(R, list(D), dt, n)
+        g.advance(R, list(D), dt, n, flags_of(dtype))
         outs[dtype] = (g.to_host(), mf.mf_get_schedule(g.h))
         del g
         torch.cuda.empty_cache()
@@ -158,7 +163,7 @@ def _manybox_fields():
     return dense, exact
 
 
-@pytest.mark.parametrize("target,dtype", [(4096, "f32"), (32768, "f32"), (32768, "f64")])
+@pytest.mark.parametrize("target,dtype", [(4096, "f32"), (32768, "f32"), (32768, "f64"), (32768, "f64fixed")])
 def test_manybox512_full_size_matches_exact_mode_decay(target, dtype):
     cfg = synth.WORKLOADS["c5"]
     N, n, R, C = cfg["N"], cfg["nsteps"], cfg["R"], cfg["ncomp"]
@@ -167,9 +172,9 @@ def test_manybox512_full_size_matches_exact_mode_decay(target, dtype):
     dt = synth.dt_for(cfg)
     g = level([0, 0, 0], [N - 1] * 3, dtype, boxes=boxes, ncomp=C, ngrow=cfg["ngrow"])
     g.from_host(dense)
-    g.advance(R, [1.0] * C, dt, n)
+    g.advance(R, [1.0] * C, dt, n, flags_of(dtype))
     err = rel_err(g.to_host(), exact)
-    tol = FP64_TOL if dtype == "f64" else f32_tol("manybox512")
+    tol = f32_tol("manybox512") if dtype == "f32" else FP64_TOL
     print("MEASURED manybox512 %d %s rel_err %.3e (bound %.1e) schedule %s"
           % (target, dtype, err, tol, mf.mf_get_schedule(g.h)))
     assert err <= tol
