@@ -284,8 +284,7 @@ struct mf {
     DevBuf d_rowpre;  // first valid row (y, z) of every FArrayBox in the reductions' row list
     // TMA-staged stencil: tensor maps of every FArrayBox over each time level, plane geometry
     DevBuf d_maps, d_tfab, d_err, d_smaps, d_strips, d_fbtasks_adv, d_push, d_fbtasks_res;
-    // fixed-point differences (MF_FIXED_DIFF): three sets of kMaxComp words, each the high word
-    // of the largest |u| of one level per component (see mf_advance)
+    // fixed-point steps (MF_FIXED_DIFF): three FixSet grid states that rotate over the steps
     DevBuf d_fix;
     std::vector<FbTask> fbtasks_res;  // the fill left once the stencil pushes face ghosts
     bool tma_push = false;
@@ -747,7 +746,7 @@ extern "C" int mf_attach(mf_t *m, void *dev_ptr, size_t bytes, void *stream) {
     if ((rc = m->d_tfab.ensure(m->fabs.size() * sizeof(TmaFab)))) return rc;
     if ((rc = m->d_err.ensure(sizeof(int)))) return rc;
     CU(cudaMemsetAsync(m->d_err.p, 0, sizeof(int), m->stream));
-    if ((rc = m->d_fix.ensure(3 * kMaxComp * sizeof(unsigned int)))) return rc;
+    if ((rc = m->d_fix.ensure(3 * sizeof(FixSet)))) return rc;
     m->tma_R = 0;
     if ((rc = m->d_sumout.ensure(sizeof(double)))) return rc;
     CU(cudaStreamSynchronize(m->stream));  // host vectors may change after return
@@ -980,10 +979,13 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 // The schedule a radius-R launch uses: rows per thread clipped to what R allows; 32-byte
 // groups only where that variant exists, else 16-byte groups.
-static int eff_rows(const mf_t *m, int R) { return std::min(m->tma_rows, tma_max_rows(R)); }
-static int eff_gb(const mf_t *m, int R) {
-    return tma_has_group(m->dtype, R, eff_rows(m, R), m->tma_gb) ? m->tma_gb : 16;
+// The schedule the TMA build uses: the chosen rows and group bytes where the kernel variant
+// (plain arithmetic, or fixed point -- bit 8 of the build key) has them.
+static bool tma_has(const mf_t *m, int R, int rows, int gb) {
+    return (m->tma_R & 8) ? tma_has_group_fix(R, rows, gb) : tma_has_group(m->dtype, R, rows, gb);
 }
+static int eff_rows(const mf_t *m, int R) { return std::min(m->tma_rows, tma_max_rows(R)); }
+static int eff_gb(const mf_t *m, int R) { return tma_has(m, R, eff_rows(m, R), m->tma_gb) ? m->tma_gb : 16; }
 
 // Plane geometry of every FArrayBox for the current tile shape and radius R; false when a
 // box needs a plane wider than the TMA box limit (256 per dimension) or more cells per
@@ -1015,11 +1017,15 @@ static bool tma_geometry(mf_t *m, int R, bool fix, const std::vector<char> &serv
         tf[b].xs = narrow ? xvg : 0;
         tf[b].xv = xvg - tf[b].xs;
         if (tf[b].bx > 256 || tf[b].by > 256) return false;
-        maxplane = std::max(maxplane, tf[b].bx * tf[b].by * S);
+        // slack rows after the plane: a thread of a tile's last, partial row set reads up to
+        // rows - 1 rows past it (values that feed only unused results), and a 32-byte group
+        // on a narrow row up to 16 bytes past the last row
+        const int slack = std::max(eff_rows(m, R) - 1, eff_gb(m, R) > 16 ? 1 : 0);
+        maxplane = std::max(maxplane, tf[b].bx * (tf[b].by + slack) * S);
     }
     // a producer warp plus one consumer thread per group, rounded up to a warp
     gpt = 32 + (maxgroups + 31) / 32 * 32;
-    if (gpt > (fix ? tma_max_threads_fix(R) : tma_max_threads(R))) return false;
+    if (gpt > (fix ? tma_max_threads_fix(R, eff_rows(m, R), eff_gb(m, R)) : tma_max_threads(R))) return false;
     slot_bytes = (maxplane + 127) / 128 * 128;
     return true;
 }
@@ -1181,11 +1187,12 @@ static int build_tma(mf_t *m, int R, bool fix = false) {
     const int slot = main_slot + 2 * strip_pitch;
     int ns = m->tma_ns_pref ? m->tma_ns_pref : (R == 4 ? 16 : 8);  // ring slots (power of two)
     if (ns < 2 * R + 1) ns = R == 4 ? 16 : 8;
-    while (ns > 8 && (long long)ns * slot + 128 > 160 * 1024) ns /= 2;
-    if (ns < 2 * R + 1 || (long long)ns * slot + 128 > 200 * 1024) return 0;
+    const int rings = fix ? 2 : 1;  // the fixed-point kernel keeps a converted copy of every slot
+    while (ns > 8 && (long long)rings * ns * slot + 128 > 160 * 1024) ns /= 2;
+    if (ns < 2 * R + 1 || (long long)rings * ns * slot + 128 > 200 * 1024) return 0;
     if (m->tile[2] <= 0) {
         // whole-box z extent: split the columns over exactly one wave of CTAs
-        const int per_sm = fix ? tma_ctas_per_sm_fix(R, eff_rows(m, R), eff_gb(m, R), gpt, ns * slot + 128)
+        const int per_sm = fix ? tma_ctas_per_sm_fix(R, eff_rows(m, R), eff_gb(m, R), gpt, 2 * ns * slot + 128)
                                : tma_ctas_per_sm(m->dtype, R, eff_rows(m, R), eff_gb(m, R), gpt, ns * slot + 128);
         if (per_sm < 1) return 0;
         const int G = per_sm * sm_count();
@@ -1373,9 +1380,22 @@ static StencilParams stencil_params(const mf_t *m, int from, const double *lam, 
     return p;
 }
 
-// fixstep >= 0: the fixed-point-difference kernel (FP64 storage), as step fixstep of an advance:
-// it reads word set fixstep % 3 (the largest |u| of level `from`), accumulates the largest |u|
-// it writes into set (fixstep + 1) % 3 and clears set (fixstep + 2) % 3 for the step after it.
+// round(lam / den * 2^64) exactly (lam < 1): lam = m 2^(e - 53) with a 53-bit integer m.
+static unsigned long long fix_q(double lam, int den) {
+    int e = 0;
+    const double f = std::frexp(lam, &e);
+    const unsigned long long mant = (unsigned long long)std::ldexp(f, 53);
+    const int sh = e + 11;  // lam 2^64 = mant 2^(e + 11)
+    unsigned __int128 num = mant, dd = (unsigned __int128)den;
+    if (sh >= 0) num <<= sh;
+    else if (-sh < 100) dd <<= -sh;
+    else return 0ull;
+    return (unsigned long long)((num + dd / 2) / dd);
+}
+
+// fixstep >= 0: the fixed-point kernel (the level holds 64-bit fixed point), as step fixstep of an
+// advance: it reads grid state fixstep % 3 (level `from`), writes state (fixstep + 1) % 3 (the
+// level it produces) and clears state (fixstep + 2) % 3 for the step after it.
 static int enqueue_stencil(mf_t *m, int from, int R, bool fp64diff, const double *lam, cudaStream_t s,
                            bool push = false, const StageArgs &sa = StageArgs{}, int fixstep = -1) {
     const bool fix = fixstep >= 0;
@@ -1412,11 +1432,11 @@ static int enqueue_stencil(mf_t *m, int from, int R, bool fp64diff, const double
         p.cta_tiles = m->tma_grid ? (const int *)m->d_cta.p : nullptr;
         for (int c = 0; c < m->ncomp; ++c) p.lam[0][c] = lam[c];
         if (fix) {
-            unsigned int *w = (unsigned int *)m->d_fix.p;
-            p.fix_in = w + (fixstep % 3) * kMaxComp;
-            p.fix_out = w + ((fixstep + 1) % 3) * kMaxComp;
-            p.fix_clear = w + ((fixstep + 2) % 3) * kMaxComp;
-            for (int c = 0; c < m->ncomp; ++c) p.lam[0][c] = lam[c] / fix_den(R);
+            FixSet *w = (FixSet *)m->d_fix.p;
+            p.fix_in = w + fixstep % 3;
+            p.fix_out = w + (fixstep + 1) % 3;
+            p.fix_clear = w + (fixstep + 2) % 3;
+            for (int c = 0; c < m->ncomp; ++c) p.fix_q[c] = fix_q(lam[c], fix_den(R));
             CU(launch_stencil_tma_fix(R, eff_rows(m, R), eff_gb(m, R), m->tma_cpt, p, m->tma_grid, s));
             return 0;
         }
@@ -1428,14 +1448,31 @@ static int enqueue_stencil(mf_t *m, int from, int R, bool fp64diff, const double
     return 0;
 }
 
-// The first grid of a fixed-point advance: all three word sets cleared, then set 0 = the largest
-// |u| of level `which` (valid cells), which step 0 reads.
-static int enqueue_fix_start(mf_t *m, int which, cudaStream_t s) {
-    CU(cudaMemsetAsync(m->d_fix.p, 0, 3 * kMaxComp * sizeof(unsigned int), s));
+static int fab_maxz(const mf_t *m) {
     int maxz = 1;
     for (auto &f : m->fabs) maxz = std::max(maxz, f.n[2]);
-    CU(launch_fix_emax(m->level_ptr(which), (const FabInfo *)m->d_fabs.p, (int)m->fabs.size(), m->ncomp, maxz,
-                       (unsigned int *)m->d_fix.p, s));
+    return maxz;
+}
+
+// Entering the fixed-point representation at the start of an advance: the three grid states
+// cleared, the largest |u| of level `which` reduced, and the level's valid cells mapped in place
+// to 64-bit fixed point on the first grid (state 0, which step 0 reads).  convert = false (the
+// autotuner's timing launches) leaves the data and the cleared states as they are.
+static int enqueue_fix_start(mf_t *m, int which, int R, cudaStream_t s, bool convert = true) {
+    CU(cudaMemsetAsync(m->d_fix.p, 0, 3 * sizeof(FixSet), s));
+    if (!convert) return 0;
+    FixSet *w = (FixSet *)m->d_fix.p;
+    const FabInfo *ft = (const FabInfo *)m->d_fabs.p;
+    const int nf = (int)m->fabs.size(), mz = fab_maxz(m);
+    CU(launch_fix_emax(m->level_ptr(which), ft, nf, m->ncomp, mz, w, s));
+    CU(launch_fix_in(R, m->level_ptr(which), ft, nf, m->ncomp, mz, w, (int *)m->d_err.p, s));
+    return 0;
+}
+
+// Leaving it after nsteps steps: level `which` back to FP64 from the grid of state nsteps % 3.
+static int enqueue_fix_end(mf_t *m, int which, int nsteps, cudaStream_t s) {
+    CU(launch_fix_out(m->level_ptr(which), (const FabInfo *)m->d_fabs.p, (int)m->fabs.size(), m->ncomp, fab_maxz(m),
+                      (const FixSet *)m->d_fix.p + nsteps % 3, s));
     return 0;
 }
 
@@ -1473,9 +1510,11 @@ static int autotune(mf_t *m, int R, bool fp64diff, const double *lam, bool fix =
     auto tiles = tile_candidates(m);
     struct Cand { std::array<int, 3> t; int rows, ns, gb; };
     std::vector<Cand> cands;
-    const int fixstep = fix ? 0 : -1;  // every timed launch reads word set 0 (level cur)
+    // fixed point: the timing launches read the FP64 data as if it were fixed point, from cleared
+    // grid states (the time does not depend on the values)
+    const int fixstep = fix ? 0 : -1;
     if (fix) {
-        int rc = enqueue_fix_start(m, m->cur, m->stream);
+        int rc = enqueue_fix_start(m, m->cur, R, m->stream, false);
         if (rc) return rc;
     }
     for (auto &t : tiles) {
@@ -1483,7 +1522,7 @@ static int autotune(mf_t *m, int R, bool fp64diff, const double *lam, bool fix =
         if (m->use_tma && t[0] == 0) {
             for (int rows = 1; rows <= tma_max_rows(R); ++rows)
                 for (int gb : {16, 32})
-                    if (tma_has_group(m->dtype, R, rows, gb))
+                    if (fix ? tma_has_group_fix(R, rows, gb) : tma_has_group(m->dtype, R, rows, gb))
                         for (int ns : {4, 8, 16})
                             if (ns >= 2 * R + 1) cands.push_back({t, rows, ns, gb});
         } else {
@@ -1777,13 +1816,18 @@ extern "C" int mf_advance(mf_t *m, const mf_stencil *st, double dt, int nsteps) 
     const std::string key = graph_key(kb, R, fp64diff, lam, m->ncomp, nsteps, m->cur);
     auto it = m->graphs.find(key);
     if (it == m->graphs.end()) {
-        if (m->timing && (rc = ensure_events(m, 2 * nsteps + 1))) return rc;
+        // an event wherever the kind of launch changes: at most two per step, the start, and the
+        // fixed-point conversions before and after the steps
+        if (m->timing && (rc = ensure_events(m, 2 * nsteps + 1 + (fixed ? 2 : 0)))) return rc;
         if ((rc = capture_begin(m))) return rc;
         int body = 0, from = m->cur;
         PhaseLog log{m, m->timing};
         body = log.start();
-        // the fixed-point grid of the first step: the largest |u| of the current level
-        if (fixed && !body && !(body = log.before(0))) body = enqueue_fix_start(m, from, m->cap);
+        // into the fixed-point representation (two passes over the level, counted with the fills)
+        if (fixed && !body && !(body = log.before(0))) {
+            body = enqueue_fix_start(m, from, R, m->cap);
+            if (!body) body = log.before(0);
+        }
         const bool push = use_push(m);
         for (int s = 0; s < nsteps && !body; ++s) {
             if (push && s > 0) {
@@ -1800,6 +1844,8 @@ extern "C" int mf_advance(mf_t *m, const mf_stencil *st, double dt, int nsteps) 
             if (!body) body = enqueue_stencil(m, from, R, fp64diff, lam, m->cap, push, StageArgs{}, fixed ? s : -1);
             from = 1 - from;
         }
+        // back to FP64 (one pass, counted with the fills)
+        if (fixed && !body && !(body = log.before(0))) body = enqueue_fix_end(m, from, nsteps, m->cap);
         if (!body) body = log.finish();
         if ((rc = capture_end(m, key, body))) return rc;
         it = m->graphs.find(key);

@@ -176,17 +176,27 @@ struct StencilTmaParams {
     const void *u0[kMaxLev];   // Runge-Kutta stage: state at the start of the step (nullptr: plain step)
     double rk_a, rk_b;         // the stage writes rk_a * u0 + rk_b * (forward-Euler value)
     double lam[kMaxLev][kMaxComp];
-    // fixed-point differences (FP64 storage, MF_FIXED_DIFF), per component: the high word of the
-    // largest |u| of the input level (read), the same for the output level (atomicMax), and a
-    // third word set cleared by the launch for the launch after it (see mf_advance)
-    const unsigned int *fix_in;
-    unsigned int *fix_out;
-    unsigned int *fix_clear;
+    // fixed-point steps (MF_FIXED_DIFF; the level holds 64-bit fixed point): the grid state of
+    // the input level (read), of the output level (written), and a third set cleared for the
+    // launch after this one (see FixSet and mf_advance), and per component
+    // fix_q = round(lam / den * 2^64)
+    const struct FixSet *fix_in;
+    struct FixSet *fix_out;
+    struct FixSet *fix_clear;
+    unsigned long long fix_q[kMaxComp];
 };
 
-// Denominator of the integer weights of the fixed-point path at radius R (fixed_diff.cuh FixW):
-// the launch takes lam / fix_den(R).
-inline double fix_den(int R) { return R == 1 ? 1.0 : R == 2 ? 12.0 : 5040.0; }
+// Grid state of one level in the fixed-point path, per component: M the OR of all |K| (its bit
+// length is that of the largest |K|; 64-bit atomicOr), E the grid exponent (the level holds K = u / 2^E), key the high word of the largest
+// |u| of an FP64 level (the first grid).  Three sets rotate over the steps of an advance.
+struct FixSet {
+    unsigned long long M[kMaxComp];
+    int E[kMaxComp];
+    unsigned int key[kMaxComp];
+};
+
+// Denominator of the integer weights of the fixed-point path at radius R (fixed_diff.cuh FixW).
+inline int fix_den(int R) { return R == 1 ? 1 : R == 2 ? 12 : 5040; }
 
 // ---- launchers (mf_kernels.cu, stencil_tma.cu); all asynchronous on `s`
 cudaError_t launch_stencil_tma(int dtype, int R, bool fp64diff, int rows, int gb, int nt, const StencilTmaParams &p,
@@ -194,11 +204,18 @@ cudaError_t launch_stencil_tma(int dtype, int R, bool fp64diff, int rows, int gb
 // the fixed-point-difference variant (FP64 storage, p.fix_* set; stencil_tma_fix.cu)
 cudaError_t launch_stencil_tma_fix(int R, int rows, int gb, int nt, const StencilTmaParams &p, int grid, cudaStream_t s);
 int tma_ctas_per_sm_fix(int R, int rows, int gb, int nt, int smem);
-int tma_max_threads_fix(int R);  // largest CTA of the fixed-point variant
-// the high word of the largest |u| of every component of one FP64 level (valid cells) into out[c],
-// by atomicMax (out cleared by the caller)
-cudaError_t launch_fix_emax(const void *base, const FabInfo *ftab, int nfab, int ncomp, int maxz, unsigned int *out,
+int tma_max_threads_fix(int R, int rows, int gb);  // largest CTA of a fixed-point schedule
+bool tma_has_group_fix(int R, int rows, int gb);   // whether the fixed-point path has that schedule
+// The conversion passes of a fixed-point advance over the valid cells of one level (in place):
+// the largest |u| of every component of an FP64 level into set->key (atomicMax; set cleared by the
+// caller); FP64 -> fixed point on the first grid, recording set->E and set->M (err |= 2 for a
+// non-finite maximum); fixed point on grid set->E -> FP64.
+cudaError_t launch_fix_emax(const void *base, const FabInfo *ftab, int nfab, int ncomp, int maxz, FixSet *set,
                             cudaStream_t s);
+cudaError_t launch_fix_in(int R, void *base, const FabInfo *ftab, int nfab, int ncomp, int maxz, FixSet *set, int *err,
+                          cudaStream_t s);
+cudaError_t launch_fix_out(void *base, const FabInfo *ftab, int nfab, int ncomp, int maxz, const FixSet *set,
+                           cudaStream_t s);
 // the Runge-Kutta-stage variant (p.u0 set); launch_stencil_tma dispatches to it
 cudaError_t launch_stencil_tma_rk(int dtype, int R, bool fp64diff, int rows, int gb, int nt, const StencilTmaParams &p,
                                   int grid, cudaStream_t s);

@@ -41,6 +41,7 @@ template <> __device__ __forceinline__ double ld<__nv_bfloat16, double>(const __
 }
 
 __device__ __forceinline__ void st(double *p, double v) { *p = v; }
+__device__ __forceinline__ void st(long long *p, long long v) { *p = v; }
 __device__ __forceinline__ void st(float *p, float v) { *p = v; }
 __device__ __forceinline__ void st(float *p, double v) { *p = __double2float_rn(v); }
 __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }

@@ -115,6 +115,17 @@ template <> struct V16<__nv_bfloat16> {
     }
 };
 
+template <> struct V16<long long> {  // the fixed-point path's 64-bit integers
+    static constexpr int n = 2;
+    template <typename A> static __device__ __forceinline__ void ld(const long long *p, A *o) {
+        const longlong2 v = *(const longlong2 *)p;
+        o[0] = (A)v.x; o[1] = (A)v.y;
+    }
+    static __device__ __forceinline__ void st(long long *p, const long long *v) {
+        *(longlong2 *)p = make_longlong2(v[0], v[1]);
+    }
+};
+
 // Groups of a thread's row: GB = 16 bytes (V16), or GB = 32 bytes -- one whole 32-byte
 // sector, stored with one 256-bit store -- for FP32 and FP64 storage.
 template <typename S, int GB> struct VG;
@@ -151,6 +162,18 @@ template <> struct VG<double, 32> {
     }
 };
 
+template <> struct VG<long long, 32> {
+    static constexpr int n = 4;
+    template <typename A> static __device__ __forceinline__ void ld(const long long *p, A *o) {
+        V16<long long>::ld(p, o);
+        V16<long long>::ld(p + 2, o + 2);
+    }
+    static __device__ __forceinline__ void st(long long *p, const long long *v) {
+        asm volatile("st.global.v4.b64 [%0], {%1, %2, %3, %4};" ::"l"(p), "l"(v[0]), "l"(v[1]), "l"(v[2]), "l"(v[3])
+                     : "memory");
+    }
+};
+
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -169,6 +192,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 template <int R, typename A = float> struct TmaBounds { static constexpr int threads = R == 4 ? 416 : 544; };
 // the fixed-point path keeps 64-bit integers in its queues: fewer threads, more registers each
 template <int R> struct TmaBounds<R, FixA> { static constexpr int threads = R == 4 ? 288 : 416; };
+// The launch bound of one schedule: the fixed-point path's 2-row, 32-byte-group schedule keeps
+// eight cells per thread and takes more registers (smaller CTAs).
+template <int R, typename A, int ROWS, int GB> struct TmaThreads { static constexpr int value = TmaBounds<R, A>::threads; };
+template <> struct TmaThreads<1, FixA, 2, 32> { static constexpr int value = 288; };
 
 // One ghost-push piece as a consumer warp keeps it (see the tile prologue).
 struct PushRec {
@@ -180,21 +207,21 @@ struct PushRec {
 
 
 template <typename S, typename A, int R, int ROWS, int GB, bool RK>
-__global__ void __launch_bounds__(TmaBounds<R, A>::threads) k_stencil_tma(const __grid_constant__ StencilTmaParams p) {
+__global__ void __launch_bounds__(TmaThreads<R, A, ROWS, GB>::value) k_stencil_tma(const __grid_constant__ StencilTmaParams p) {
     using V = VG<S, GB>;
     constexpr int VX = V::n;  // cells per group: one GB-byte vector of a row
     // FP32 arithmetic at radius 1: pairs of cells through the packed f32x2 instructions
     constexpr bool kPair = std::is_same<A, float>::value && R == 1 && VX % 2 == 0;
     // exact fixed-point differences, FP64 update (fixed_diff.cuh)
     constexpr bool kFix = std::is_same<A, FixA>::value;
-    static_assert(!kFix || (std::is_same<S, double>::value && !RK), "fixed-point differences: FP64 storage, plain steps");
+    static_assert(!kFix || (std::is_same<S, long long>::value && !RK), "fixed-point steps: 64-bit storage, plain steps");
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];
     unsigned char *slots = (unsigned char *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     const int NS = p.nstages;  // power of two
     const int tid = threadIdx.x;
     const int ncw = (int)(blockDim.x >> 5) - 1;  // consumer warps
-    __shared__ PushRec ptab[TmaBounds<R, A>::threads / 32 - 1][kMaxPush];  // per consumer warp
+    __shared__ PushRec ptab[TmaThreads<R, A, ROWS, GB>::value / 32 - 1][kMaxPush];  // per consumer warp
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(&full[s], 1);
@@ -212,9 +239,14 @@ __global__ void __launch_bounds__(TmaBounds<R, A>::threads) k_stencil_tma(const 
     asm volatile("griddepcontrol.wait;" ::: "memory");
     if (*(volatile int *)p.err) return;  // an earlier launch already failed: do nothing
     if constexpr (kFix) {
-        // the words the next launch accumulates into: read by the previous launch (complete
-        // now), written by no thread of this one
-        if (blockIdx.x == 0 && tid < kMaxComp) p.fix_clear[tid] = 0u;
+        // grid bookkeeping, once per launch: the output grid of each component from its input
+        // grid and the largest |K| of the input level (fixed_diff.cuh), and the clearing of the
+        // set the launch after this one accumulates into (read by the launch before this one,
+        // complete now; touched by no other thread of this one)
+        if (blockIdx.x == 0 && tid < kMaxComp) {
+            p.fix_out->E[tid] = p.fix_in->E[tid] + fix_bits(p.fix_in->M[tid]) + kFixH - FixW<R>::B;
+            p.fix_clear->M[tid] = 0ull;
+        }
     }
     // this CTA's tiles: its own range of a balanced schedule, else every gridDim.x-th tile
     int w0 = blockIdx.x, w1 = p.ntiles, ws = gridDim.x;
@@ -487,16 +519,23 @@ __global__ void __launch_bounds__(TmaBounds<R, A>::threads) k_stencil_tma(const 
             }
         };
         if constexpr (kFix) {
-            // the level's grid for this component (fixed_diff.cuh); a non-finite maximum is
-            // reported through the error word (bit 2) and the launch completes as usual
-            // volatile: the word was written by the previous launch, which this one may have
-            // overlapped (programmatic dependent launch); a cached copy of an earlier step's
-            // value must not be read
-            const uint32_t wmax = *(volatile const uint32_t *)(p.fix_in + t.comp);
-            if (wmax >= 0x7ff00000u && lane == 0) atomicOr(p.err, 2);
-            const int T0 = fix_t0<R>(wmax);
-            uint32_t omax = 0u;  // fix_key of the largest value this thread writes to a valid cell
-            long long q[ROWS][VX][2 * R + 1];  // z queue per cell, fixed point: q[r][c][i] = K(z - R + i)
+            // this component's grid change: t = 64 - (E - E') from the largest |K| of the input
+            // level (volatile: written by the previous launch, which this one may have overlapped)
+            const unsigned long long M = *(volatile const unsigned long long *)&p.fix_in->M[t.comp];
+            const int tt = 64 - FixW<R>::B + kFixH + fix_bits(M);
+            const unsigned long long lq = p.fix_q[t.comp];
+            const uint32_t qh = (uint32_t)(lq >> 32), ql = (uint32_t)lq;
+            const bool same_grid = tt == 64;  // the common case: K' = K + L q / 2^64
+            // the OR of the high words of |K'| (ones' complement) over this thread's valid cells
+            // (bit r * VX + c of vbits) bounds the largest |K'| (fix_bits)
+            uint32_t omax = 0u;
+            uint32_t vbits = 0u;
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+                for (int c = 0; c < VX; ++c)
+                    if (act && r < nrow && x0c + c < f.n[0]) vbits |= 1u << (r * VX + c);
+            long long q[ROWS][VX][2 * R + 1];  // z queue per cell: q[r][c][i] = K(z - R + i)
             bool ok = true;
 #pragma unroll
             for (int pl = 0; pl < 2 * R; ++pl) {
@@ -504,10 +543,10 @@ __global__ void __launch_bounds__(TmaBounds<R, A>::threads) k_stencil_tma(const 
                 const S *sp = slot_ptr(seq + pl);
 #pragma unroll
                 for (int r = 0; r < ROWS; ++r) {
-                    double v[VX];
-                    V::template ld<double>(sp + soff + r * bx, v);
+                    long long v[VX];
+                    V::template ld<long long>(sp + soff + r * bx, v);
 #pragma unroll
-                    for (int c = 0; c < VX; ++c) q[r][c][pl] = fix_of(v[c], T0);
+                    for (int c = 0; c < VX; ++c) q[r][c][pl] = v[c];
                 }
             }
             if (!__all_sync(0xffffffffu, ok)) {
@@ -516,6 +555,7 @@ __global__ void __launch_bounds__(TmaBounds<R, A>::threads) k_stencil_tma(const 
             }
             for (int pl = 0; pl < 2 * R; ++pl)
                 if (pl < R || pl >= t.tz + R) release(seq + pl);
+#pragma unroll(2 * R + 1)
             for (int k = 0; k < t.tz; ++k) {
                 if (!__all_sync(0xffffffffu, wait_seq(seq + k + 2 * R))) {
                     if (lane == 0) atomicOr(p.err, 1);
@@ -525,10 +565,10 @@ __global__ void __launch_bounds__(TmaBounds<R, A>::threads) k_stencil_tma(const 
                 const S *cp = slot_ptr(seq + k + R);
 #pragma unroll
                 for (int r = 0; r < ROWS; ++r) {
-                    double v[VX];
-                    V::template ld<double>(newp + soff + r * bx, v);
+                    long long v[VX];
+                    V::template ld<long long>(newp + soff + r * bx, v);
 #pragma unroll
-                    for (int c = 0; c < VX; ++c) q[r][c][2 * R] = fix_of(v[c], T0);
+                    for (int c = 0; c < VX; ++c) q[r][c][2 * R] = v[c];
                 }
                 // y window per column: wy[m][c] = K(x + c, y0 - R + m)
                 long long wy[2 * R + ROWS][VX];
@@ -536,34 +576,28 @@ __global__ void __launch_bounds__(TmaBounds<R, A>::threads) k_stencil_tma(const 
 #pragma unroll
                 for (int m = 0; m < 2 * R + ROWS; ++m) {
                     if (m >= R && m < R + ROWS) continue;
-                    double v[VX];
-                    V::template ld<double>(cc + (m - R) * bx, v);
-#pragma unroll
-                    for (int c = 0; c < VX; ++c) wy[m][c] = fix_of(v[c], T0);
+                    V::template ld<long long>(cc + (m - R) * bx, wy[m]);
                 }
 #pragma unroll
                 for (int r = 0; r < ROWS; ++r)
 #pragma unroll
                     for (int c = 0; c < VX; ++c) wy[R + r][c] = q[r][c][R];
-                double out[ROWS][VX];
+                long long out[ROWS][VX];
 #pragma unroll
                 for (int r = 0; r < ROWS; ++r) {
-                    // x window: wx[i] = K(x0 - R + i)
-                    long long wx[VX + 2 * R];
+                    long long wx[VX + 2 * R];  // x window: wx[i] = K(x0 - R + i)
 #pragma unroll
                     for (int i = 0; i < R; ++i) {
-                        wx[i] = fix_of(cp[hl[r][i]], T0);
-                        wx[R + VX + i] = fix_of(cp[hr[r][i]], T0);
+                        wx[i] = cp[hl[r][i]];
+                        wx[R + VX + i] = cp[hr[r][i]];
                     }
 #pragma unroll
                     for (int c = 0; c < VX; ++c) wx[R + c] = q[r][c][R];
                     if (cov) {  // the box face is inside this group: x neighbours from the strips
 #pragma unroll
                         for (int c = 0; c < VX; ++c)
-                            if (cov & (1u << c)) wx[R + c] = fix_of(cp[cob + r * p.strip_w + c], T0);
+                            if (cov & (1u << c)) wx[R + c] = cp[cob + r * p.strip_w + c];
                     }
-                    double u[VX];  // the centre values in FP64, for the update
-                    V::template ld<double>(cc + r * bx, u);
 #pragma unroll
                     for (int c = 0; c < VX; ++c) {
                         // direct form in exact integer arithmetic (wrapping unsigned sums: only the
@@ -577,12 +611,18 @@ __global__ void __launch_bounds__(TmaBounds<R, A>::threads) k_stencil_tma(const 
                                 ((unsigned long long)q[r][c][R + m] + (unsigned long long)q[r][c][R - m]);
                             L += (unsigned long long)FixW<R>::w(m) * pair;
                         }
-                        out[r][c] = __fma_rn(lam, fix_to_f64((long long)L, T0), u[c]);
-                        if (act && r < nrow && x0c + c < f.n[0]) omax = max(omax, fix_key(out[r][c]));
-#pragma unroll
-                        for (int i = 0; i < 2 * R; ++i) q[r][c][i] = q[r][c][i + 1];
+                        out[r][c] = same_grid ? q[r][c][R] + fix_incr(L, qh, ql)
+                                              : fix_update(q[r][c][R], (long long)L, lq, tt);
+                        const int hw = (int)(out[r][c] >> 32);
+                        if (vbits & (1u << (r * VX + c))) omax |= (uint32_t)(hw ^ (hw >> 31));
                     }
                 }
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+                    for (int c = 0; c < VX; ++c)
+#pragma unroll
+                        for (int i = 0; i < 2 * R; ++i) q[r][c][i] = q[r][c][i + 1];
                 // every read of the centre plane (and of the last R planes) is done
                 release(seq + k + R);
                 if (k >= t.tz - R) release(seq + k + 2 * R);
@@ -590,9 +630,10 @@ __global__ void __launch_bounds__(TmaBounds<R, A>::threads) k_stencil_tma(const 
                 op += f.plane;
                 store_plane(out, k, o);
             }
-            // the level maximum of the output, per component, for the next launch's grid
-            omax = __reduce_max_sync(0xffffffffu, omax);
-            if (lane == 0 && omax) atomicMax(p.fix_out + t.comp, omax);
+            // the bit length of the largest |K'| of the output, per component, for the next
+            // launch's grid: an OR over the warp, then an atomic OR
+            omax = __reduce_or_sync(0xffffffffu, omax);
+            if (lane == 0 && omax) atomicOr(&p.fix_out->M[t.comp], (unsigned long long)omax << 32);
         } else {
             A q[ROWS][VX][2 * R + 1];  // z queue per cell: q[r][c][i] = u(z - R + i)
             A fzm[ROWS][VX];
@@ -768,7 +809,7 @@ static cudaError_t tma_configure(int smem) {
 
 template <typename S, typename A, int R, int ROWS, int GB, bool RK>
 static cudaError_t tma_t(int nt, const StencilTmaParams &p, int grid, cudaStream_t s) {
-    if (nt < 64 || nt > TmaBounds<R, A>::threads || nt % 32) return cudaErrorInvalidValue;
+    if (nt < 64 || nt > TmaThreads<R, A, ROWS, GB>::value || nt % 32) return cudaErrorInvalidValue;
     const int smem = p.nstages * p.slot_bytes + 128;
     auto kern = k_stencil_tma<S, A, R, ROWS, GB, RK>;
     cudaError_t e = tma_configure<S, A, R, ROWS, GB, RK>(smem);
@@ -813,6 +854,9 @@ static T tma_dispatch(int R, int rows, int gb, F &&f, T fallback) {
             break;
         case (2 * 4 + 1) * 2 + 1:
             if constexpr (kHasWide<S>) return f.template run<2, 1, 32>();
+            break;
+        case (1 * 4 + 2) * 2 + 1:
+            if constexpr (std::is_same<S, long long>::value) return f.template run<1, 2, 32>();
             break;
     }
     return fallback;
