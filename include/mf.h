@@ -49,8 +49,8 @@ enum {
     MF_PLAIN_PER_BOX = 2, /* the untiled baseline of Sec. 3.1: one launch per box per phase,
                              launched eagerly, no work list, no graph */
     MF_REFLUX = 4,        /* mf_amr_advance only: Berger-Colella refluxing (see there) */
-    MF_FIXED_DIFF = 8     /* mf_advance, FP64 storage, TMA kernel: the differences in exact
-                             fixed-point integer arithmetic, one FP64 operation per cell (below) */
+    MF_FIXED_DIFF = 8     /* mf_advance, FP64 storage, TMA kernel: the steps in exact 64-bit
+                             fixed-point integer arithmetic (see mf_advance) */
 };
 
 typedef struct {
@@ -231,17 +231,21 @@ int mf_average_down(const mf_t *fine, mf_t *crse, int ratio);
  * autotuner times both ways).  The ghost cells of the result are therefore not all current:
  * call mf_fill_boundary before reading them.
  *
- * MF_FIXED_DIFF (FP64 storage; TMA kernel; not with MF_PLAIN_PER_BOX): the same operator, with
- * the update evaluated as u + lam * D in one FP64 fused multiply-add and the Laplacian D formed
- * exactly.  Every value read is mapped to a 64-bit integer on a grid Q fixed per component for
- * each step, Q = 2^(1 - B) * 2^E with 2^E <= max|u| < 2^(E + 1) over the level's valid cells and
- * B = 58, 55, 46 bits for R = 1, 2, 4; the integer Laplacian is exact and is rounded once to
- * FP64 (toward zero).  Per step, |D - Lap u| <= sum_j |c_j| * Q + 2^-52 |D| (c_j the operator's
- * weights): 12 * 2^-57 max|u| + 2^-52 |D| at R = 1.  The grid of each step comes from the level maximum the previous step's kernel
- * reduces (the first from one extra pass over the level), so the results are bitwise
- * independent of tiles and box layout.  A non-finite value in the level makes the next
- * synchronising call fail with MF_ECUDA.  FP64 arithmetic is slow next to memory bandwidth on
- * some GPUs (GB300 issues about 2 FP64 operations per clock per SM); this path needs one.
+ * MF_FIXED_DIFF (FP64 storage; TMA kernel; not with MF_PLAIN_PER_BOX): the same operator
+ * stepped in exact 64-bit integer arithmetic, with no FP64 arithmetic inside the time loop.  The
+ * advance maps the level's valid cells once from FP64 to fixed point, K = u / 2^E on a grid per
+ * component taken from the largest exponent present; every step forms the integer Laplacian L
+ * exactly and writes K' = round((K 2^64 + L q) / 2^t), q = round(lam / den * 2^64) with den
+ * the operator's common denominator (1, 12, 5040 for R = 1, 2, 4), on the next step's grid
+ * (t = 64 - (E - E'), E' from the level maximum the step before reduced, so the precision
+ * follows a decaying solution); after the last step the valid cells are mapped back to FP64.
+ * |K| stays below 2^B, B = 58, 55, 46 bits for R = 1, 2, 4, so each step's error is a few units
+ * of 2^E, about 2^(3 - B) max|u|.  The grids come from level-wide maxima, so the results are
+ * bitwise independent of tiles and box layout.  After such an advance the ghost cells hold
+ * fixed-point bit patterns, not FP64 values: call mf_fill_boundary before reading them.  A
+ * non-finite value in the level makes the next synchronising call fail with MF_ECUDA.  FP64
+ * arithmetic is slow next to memory bandwidth on some GPUs (GB300 issues about 2 FP64
+ * operations per clock per SM); this path needs none per cell.
  */
 int mf_advance(mf_t *mf, const mf_stencil *st, double dt, int nsteps);
 
@@ -318,7 +322,7 @@ int mf_set_timing(mf_t *mf, int on);
 int mf_phase_ms(mf_t *mf, double out[2]);
 
 /* Kernel launches of the last mf_advance (or, on the coarse handle, mf_amr_advance) call:
- * out[0] ghost-fill (and, with MF_FIXED_DIFF, the one level-maximum pass), out[1] stencil,
+ * out[0] ghost-fill (and, with MF_FIXED_DIFF, the three conversion passes), out[1] stencil,
  * out[2] coarse-fine interpolation and flux-register,
  * out[3] average-down and reflux launches.  Launches whose work list is empty are not made and not counted. */
 int mf_launch_count(const mf_t *mf, int out[4]);
