@@ -48,15 +48,19 @@ def parse():
     p.add_argument("--tile", default=None, help="fixed tile 'x,y,z' instead of the autotuner (0 = whole box)")
     p.add_argument("--kernel", default="tma", choices=["tma", "global"], help="stencil kernel variant")
     p.add_argument("--only", default=None,
-                   choices=["bf16_batched", "rk3_8th", "amr2lev_reflux", "manybox512", "fp64_fixed"],
+                   choices=["bf16_batched", "rk3_8th", "amr2lev_reflux", "manybox512", "fp64_fixed", "diff8th512"],
                    help="run only this secondary line (for profiling) and print it")
     p.add_argument("--schedule", default=None,
                    help="fixed schedule 'x,y,z,rows,stages,group_bytes' instead of the autotuner")
     p.add_argument("--fixed", action="store_true",
                    help="headline with --dtype f64: fixed-point differences (MF_FIXED_DIFF)")
+    p.add_argument("--plain", action="store_true",
+                   help="headline as the untiled per-box sweep (MF_PLAIN_PER_BOX), for profiling the baseline")
     a = p.parse_args()
     if a.fixed and a.dtype != "f64":
         p.error("--fixed needs --dtype f64")
+    if a.plain and (a.fixed or not a.no_extras):
+        p.error("--plain profiles the headline alone: with --no-extras, without --fixed")
     return a
 
 
@@ -363,6 +367,41 @@ def fixed_line(mf, torch, flush, args, hbm):
             "speedup_vs_fp64_plain_per_box": v / vplain, "speedup_vs_fp64_batched": v / v64}
 
 
+def diff8th_line(mf, torch, flush, args, hbm):
+    """The 8th-order workload (Sec. 4.2's 25-point operator on 5 components): periodic 512^3 in 64
+    boxes of 128^3, 4 ghost cells, per-component diffusivities, 20 forward-Euler steps per bench
+    step, FP32 and FP64 storage.  The initial field (8 seeded modes per component plus 1e-6
+    noise) is evaluated on the device by the same generator as the host's (synth)."""
+    cfg = synth.WORKLOADS["c3"]
+    N, R, C, n, mgs = cfg["N"], cfg["R"], cfg["ncomp"], cfg["nsteps"], cfg["max_grid_size"]
+    D = [float(d) for d in synth.diffusivities(cfg)]
+    dt = synth.dt_for(cfg)
+    dense = synth.initial_field_device(cfg, "cuda").cpu().pin_memory()
+    torch.cuda.empty_cache()
+    V, nbox = N ** 3, (N // mgs) ** 3
+    out = {"workload": "diff8th512_c5: periodic 512^3, 64 boxes of 128^3, ngrow 4, 5 components, 25-point "
+                       "8th-order stencil, D_c in [0.5, 2], %d forward-Euler steps per bench step" % n}
+    K = max(2, args.steps // 4)
+    for dtype, S in (("f32", 4), ("f64", 8)):
+        g = mf.MultiFab([0, 0, 0], [N - 1] * 3, max_grid_size=mgs, ncomp=C, ngrow=cfg["ngrow"], dtype=dtype)
+        g.from_host(dense)
+        g.advance(R, D, dt, n)  # autotune and capture
+        t = time_advances(g, R, D, dt, n, K, flush)
+        ms = sum(t) / len(t)
+        step_bytes = g.step_bytes(R)
+        st_s, fill_ms, _ = stencil_phase(g, R, D, dt, n, 0, 2, flush)
+        out[dtype] = {"value": V * n / (ms * 1e-3), "unit": UNIT, "ms_per_bench_step": ms,
+                      "cell_comp_updates_per_s": V * C * n / (ms * 1e-3), "step_bytes": step_bytes,
+                      "step_frac": step_bytes * n / (ms * 1e-3) / 1e9 / hbm,
+                      "stencil_launch_us": st_s * 1e6, "fill_phase_us_per_step": fill_ms * 1e3 / n,
+                      "stencil_frac": S * C * (2 * V + nbox * 6 * R * mgs * mgs) / st_s / 1e9 / hbm,
+                      "launches_per_bench_step": mf.mf_launch_count(g.h), "schedule": mf.mf_get_schedule(g.h)}
+        del g
+        torch.cuda.empty_cache()
+    out["speedup_f32_vs_f64"] = out["f32"]["value"] / out["f64"]["value"]
+    return out
+
+
 def manybox_step_bytes(S, C, boxes, R):
     """Compulsory bytes of one time step of a level: every valid cell read and written once,
     and the face halo of radius R read (the stencil's x halos come from the neighbour boxes and
@@ -567,7 +606,7 @@ def run_ours(args, cfg, ws, rank, local):
         head.set_tile(tuple(v[:3]))
         mf.mf_set_schedule(head.h, *v[3:6])
     mf.mf_set_kernel(head.h, mf.MF_KERNEL_TMA if args.kernel == "tma" else mf.MF_KERNEL_GLOBAL)
-    hflags = mf.MF_FIXED_DIFF if args.fixed else 0
+    hflags = mf.MF_FIXED_DIFF if args.fixed else mf.MF_PLAIN_PER_BOX if args.plain else 0
     for _ in range(args.warmup):
         mf.mf_advance(head.h, R, D, dt, nsteps, hflags)
     torch.cuda.synchronize()
@@ -590,18 +629,24 @@ def run_ours(args, cfg, ws, rank, local):
 
     # ---- roofline of the dominant kernel (stencil): events inside the graph wherever the kind
     # of launch changes, so the back-to-back stencil launches are timed without nodes between
-    mf.mf_set_timing(head.h, 1)
-    for _ in range(2):
-        mf.mf_advance(head.h, R, D, dt, nsteps, hflags)
     fill_ms, st_ms = 0.0, 0.0
     t_timed = []
-    for _ in range(args.steps):
-        t_timed += time_advances(head, R, D, dt, nsteps, 1, flush, hflags)
-        a, b = mf.mf_phase_ms(head.h)
-        fill_ms += a
-        st_ms += b
-    mf.mf_set_timing(head.h, 0)
-    st_avg_s = st_ms * 1e-3 / (launches["stencil"] * args.steps)
+    if args.plain:  # eager per-box launches: no graph events; the whole step stands in for the stencil
+        t_timed = list(times)
+        st_ms = sum(times)
+    else:
+        mf.mf_set_timing(head.h, 1)
+        for _ in range(2):
+            mf.mf_advance(head.h, R, D, dt, nsteps, hflags)
+        for _ in range(args.steps):
+            t_timed += time_advances(head, R, D, dt, nsteps, 1, flush, hflags)
+            a, b = mf.mf_phase_ms(head.h)
+            fill_ms += a
+            st_ms += b
+        mf.mf_set_timing(head.h, 0)
+    st_avg_s = st_ms * 1e-3 / (max(1, launches["stencil"]) * args.steps)
+    if args.plain:
+        st_avg_s = st_ms * 1e-3 / (nsteps * args.steps)  # one time step of all per-box launches
     S = {"f64": 8, "f32": 4, "bf16": 2}[args.dtype]
     nbox = (N // cfg["max_grid_size"]) ** 3
     b = cfg["max_grid_size"]
@@ -724,7 +769,7 @@ def run_ours(args, cfg, ws, rank, local):
         # secondary lines, on one GPU only (the scaling runs compare the headline); a failure is
         # reported in its own entry and does not void the headline
         secondary = (("fp64_fixed", fixed_line), ("bf16_batched", bf16_line), ("rk3_8th", rk3_line),
-                     ("amr2lev_reflux", amr_line), ("manybox512", manybox_line))
+                     ("diff8th512", diff8th_line), ("amr2lev_reflux", amr_line), ("manybox512", manybox_line))
         for key, line in (secondary if ws == 1 else ()):
             try:
                 out[key] = line(mf, torch, flush, args, hbm)
@@ -764,7 +809,7 @@ def main():
         peaks, _ = measured_peaks()
         hbm = float(peaks["hbm_gbs"])
         line = {"bf16_batched": bf16_line, "rk3_8th": rk3_line, "amr2lev_reflux": amr_line,
-                "manybox512": manybox_line, "fp64_fixed": fixed_line}[args.only](
+                "manybox512": manybox_line, "fp64_fixed": fixed_line, "diff8th512": diff8th_line}[args.only](
             mf, torch, flush, args, hbm)
         print(json.dumps({args.only: line}))
         return 0

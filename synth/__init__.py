@@ -298,3 +298,56 @@ def initial_field(cfg, N=None, seed=FIELD_SEED):
         if "noise" in cfg["init"]:
             out[c] += noise(seed, 200 + c, shape, cfg["noise"])
     return out
+
+
+# ------------------------------------------------------------------ the same fields on a device
+
+def _u64(v):
+    """A uint64 constant as the int64 with the same bits (torch has no uint64 arithmetic)."""
+    v = int(v) & 0xFFFFFFFFFFFFFFFF
+    return v - (1 << 64) if v >= (1 << 63) else v
+
+
+def _torch_mix(z):
+    """The SplitMix64 output function on int64 tensors holding uint64 bits (wrapping products,
+    logical right shifts)."""
+    def shr(x, s):
+        return (x >> s) & ((1 << (64 - s)) - 1)
+    z = (z ^ shr(z, 30)) * _u64(_M1)
+    z = (z ^ shr(z, 27)) * _u64(_M2)
+    return z ^ shr(z, 31)
+
+
+def initial_field_device(cfg, device, N=None, seed=FIELD_SEED, comps=None):
+    """initial_field evaluated with torch on `device` (float64 (C, N, N, N)): the same modes and
+    the same counter-based noise draws, for workloads too large to generate on the host in a
+    benchmark.  Agrees with initial_field to rounding (the sines are evaluated in a different
+    order of operations)."""
+    import torch
+    N = N or cfg["N"]
+    C = cfg["ncomp"]
+    comps = range(C) if comps is None else comps
+    out = torch.empty((len(comps), N, N, N), dtype=torch.float64, device=device)
+    x = (torch.arange(N, dtype=torch.float64, device=device) + 0.5) / N
+    for i, c in enumerate(comps):
+        acc = out[i]
+        acc.zero_()
+        for k, a, ph in sine_modes(seed, 100 + c, cfg["nmodes"], cfg["kmax"]):
+            # sin(2 pi k.x + ph) = Im(e^{i ph} e^{2 pi i kx x} e^{2 pi i ky y} e^{2 pi i kz z})
+            ex = torch.polar(torch.ones_like(x), 2.0 * math.pi * k[0] * x)
+            ey = torch.polar(torch.ones_like(x), 2.0 * math.pi * k[1] * x)
+            ez = torch.polar(torch.ones_like(x), 2.0 * math.pi * k[2] * x) * complex(math.cos(ph), math.sin(ph))
+            for z0 in range(0, N, 32):
+                z1 = min(N, z0 + 32)
+                blk = ez[z0:z1, None, None] * (ey[None, :, None] * ex[None, None, :])
+                acc[z0:z1] += a * blk.imag
+        if "noise" in cfg["init"]:
+            key = int(_key(seed, 200 + c))
+            lo, hi = -cfg["noise"], cfg["noise"]
+            for z0 in range(0, N, 32):
+                z1 = min(N, z0 + 32)
+                idx = torch.arange(z0 * N * N, z1 * N * N, dtype=torch.int64, device=device)
+                z = _torch_mix(_u64(key) + (idx + 1) * _u64(GOLDEN))
+                u = ((z >> 11) & ((1 << 53) - 1)).to(torch.float64) * (1.0 / 9007199254740992.0)
+                acc[z0:z1] += (lo + (hi - lo) * u).reshape(z1 - z0, N, N)
+    return out

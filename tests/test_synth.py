@@ -70,3 +70,16 @@ def test_initial_field_is_layout_free_and_seeded():
     modes = synth.sine_modes(synth.FIELD_SEED, 3, 8, 16)
     full = synth.eval_modes((32, 32, 32), modes)
     assert full.shape == (32, 32, 32) and np.abs(full).max() <= 1.0
+
+
+def test_device_field_generator_matches_host_generator():
+    """initial_field_device (torch) gives the host generator's field: identical noise draws,
+    modes to rounding."""
+    torch = pytest.importorskip("torch")
+    cfg = dict(synth.WORKLOADS["c3"])
+    host = synth.initial_field(cfg, N=24)
+    dev = synth.initial_field_device(cfg, "cpu", N=24).numpy()
+    assert host.shape == dev.shape
+    assert float(np.max(np.abs(host - dev))) <= 1e-14
+    no_modes = dict(cfg, nmodes=0)
+    np.testing.assert_array_equal(synth.initial_field(no_modes, N=12), synth.initial_field_device(no_modes, "cpu", N=12).numpy())
