@@ -186,6 +186,9 @@ def run_reference(args, cfg):
 
 
 def cpu_baseline(cfg, target_s=15.0):
+    """The oracle as it stands on the host cores: single-threaded (the reported baseline), and
+    with the paper's threaded loop over boxes (Sec. 3.3) on every core, on the same steps, with
+    a check that both give the same bits."""
     import oracle
     N = cfg["N"]
     lo, hi = [0, 0, 0], [N - 1] * 3
@@ -197,12 +200,20 @@ def cpu_baseline(cfg, target_s=15.0):
     t1 = time.perf_counter() - t0
     n = max(1, min(cfg["nsteps"], int(target_s / max(t1, 1e-3)) - 1))
     t0 = time.perf_counter()
-    oracle.advance(L, u, cfg["R"], lam, n)
+    serial = oracle.advance(L, u, cfg["R"], lam, n)
     t = time.perf_counter() - t0
+    threads = oracle.omp_threads()
+    t0 = time.perf_counter()
+    threaded = oracle.advance_omp(L, u, cfg["R"], lam, n)
+    t_omp = time.perf_counter() - t0
+    nbox = (N // cfg["max_grid_size"]) ** 3
     return {"value": N ** 3 * n / t, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%d of the %d FP64 time steps of the %d^3 / %d-box workload, single-threaded C oracle "
-                      "(gcc -O2 -ffp-contract=off) on the GPU host" % (n, cfg["nsteps"], N,
-                                                                         (N // cfg["max_grid_size"]) ** 3)}
+                      "(gcc -O2 -ffp-contract=off) on the GPU host" % (n, cfg["nsteps"], N, nbox),
+            "openmp": {"value": N ** 3 * n / t_omp, "unit": UNIT, "cores": threads, "nproc": os.cpu_count(),
+                       "kind": "oracle, boxes of each phase shared among OpenMP threads (Sec. 3.3)",
+                       "sample": "the same %d steps" % n,
+                       "bitwise_equal_to_single_thread": bool(np.array_equal(serial, threaded))}}
 
 
 # ------------------------------------------------------------------ our arm

@@ -55,10 +55,14 @@ _lib = None
 
 
 def build(force=False):
-    """Compile the C oracle (plain gcc, no CUDA)."""
+    """Compile the C oracle (plain gcc, no CUDA; with OpenMP for orc_advance_omp where gcc has it)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".%d.tmp" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        try:
+            subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -84,6 +88,10 @@ def lib():
             L.orc_stencil_direct.argtypes = [I, P, I, I, I, P, P, P, P]
             L.orc_advance.restype = I
             L.orc_advance.argtypes = [I, P, P, P, I, I, I, P, P, I, P, P]
+            L.orc_advance_omp.restype = I
+            L.orc_advance_omp.argtypes = [I, P, P, P, I, I, I, P, P, I, P, P]
+            L.orc_omp_threads.restype = I
+            L.orc_omp_threads.argtypes = []
             L.orc_interp_cf.restype = LNG
             L.orc_interp_cf.argtypes = [I, P, P, P, I, I, P, P, P, I, I, I, D, P, P, P]
             L.orc_average_down.restype = LNG
@@ -188,6 +196,23 @@ def advance(level, data, R, lam, nsteps):
     which = lib().orc_advance(level.nbox, _p(level.boxes), _p(level.dlo), _p(level.dhi), level.g, level.C, int(R),
                               _p(b), _p(lam), int(nsteps), _p(a), _p(other))
     return a if which == 0 else other
+
+
+def advance_omp(level, data, R, lam, nsteps):
+    """advance with the paper's threaded loop (Sec. 3.3): the boxes of each phase shared among
+    OpenMP threads; the same bits as advance.  A CPU baseline, not part of the compared method."""
+    lam = _lam_array(level, lam)
+    b = np.array([float(x) for x in coeffs.flux_coefficients(R)], dtype=np.float64)
+    a = np.array(data, dtype=np.float64, copy=True)
+    other = level.alloc()
+    which = lib().orc_advance_omp(level.nbox, _p(level.boxes), _p(level.dlo), _p(level.dhi), level.g, level.C,
+                                  int(R), _p(b), _p(lam), int(nsteps), _p(a), _p(other))
+    return a if which == 0 else other
+
+
+def omp_threads():
+    """Threads advance_omp uses (1 without OpenMP)."""
+    return int(lib().orc_omp_threads())
 
 
 # Stage weights of the three-stage SSP Runge-Kutta scheme: stage s returns

@@ -23,6 +23,11 @@
  *     its formula -- the readings are trilinear in space, linear in time, and the mean of
  *     the children).
  *
+ * The paper's threaded loop (Sec. 3.3: the iterations over tiles shared among OpenMP threads) is
+ * orc_advance_omp: the same per-box work, distributed over the boxes of a level with an OpenMP
+ * parallel loop, giving the same bits as orc_advance (a reported CPU baseline, not part of the
+ * compared method).
+ *
  * Compile with -O2 -ffp-contract=off so that every product and sum is rounded on its own.
  * All arrays are double precision.  Boxes are passed as int[6] = {lo0,lo1,lo2,hi0,hi1,hi2}
  * with inclusive bounds.  The FArrayBoxes of a level are stored back to back in box order.
@@ -30,6 +35,9 @@
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ---------------------------------------------------------------- boxes and layout */
 
@@ -159,27 +167,34 @@ void orc_dense_from_fabs(int nbox, const int *boxes, const int *dlo, const int *
  * the periodic domain.  Ghost cells whose point no box owns (a level that does not cover
  * the domain) are left untouched.  Returns the number of ghost cells written per component.
  */
+/* the ghost cells of box b (writes only them; reads valid cells of other boxes) */
+static long fill_box(int b, int nbox, const int *boxes, const int *dlo, const int *dhi, int g, int ncomp,
+                     const long *off, double *data)
+{
+    long written = 0;
+    const int *B = boxes + 6 * b;
+    long offb = off[b];
+    for (int k = B[2] - g; k <= B[5] + g; ++k)
+        for (int j = B[1] - g; j <= B[4] + g; ++j)
+            for (int i = B[0] - g; i <= B[3] + g; ++i) {
+                if (box_contains(B, i, j, k)) continue;
+                int wi = wrap(i, dlo[0], dhi[0]), wj = wrap(j, dlo[1], dhi[1]), wk = wrap(k, dlo[2], dhi[2]);
+                int a = find_owner(nbox, boxes, wi, wj, wk);
+                if (a < 0) continue;
+                const int *A = boxes + 6 * a;
+                long offa = off[a];
+                for (int c = 0; c < ncomp; ++c)
+                    data[offb + fab_index(B, g, i, j, k, c)] = data[offa + fab_index(A, g, wi, wj, wk, c)];
+                ++written;
+            }
+    return written;
+}
+
 long orc_fill_boundary(int nbox, const int *boxes, const int *dlo, const int *dhi, int g, int ncomp, double *data)
 {
     long written = 0;
     long *off = fab_offsets(nbox, boxes, g, ncomp);
-    for (int b = 0; b < nbox; ++b) {
-        const int *B = boxes + 6 * b;
-        long offb = off[b];
-        for (int k = B[2] - g; k <= B[5] + g; ++k)
-            for (int j = B[1] - g; j <= B[4] + g; ++j)
-                for (int i = B[0] - g; i <= B[3] + g; ++i) {
-                    if (box_contains(B, i, j, k)) continue;
-                    int wi = wrap(i, dlo[0], dhi[0]), wj = wrap(j, dlo[1], dhi[1]), wk = wrap(k, dlo[2], dhi[2]);
-                    int a = find_owner(nbox, boxes, wi, wj, wk);
-                    if (a < 0) continue;
-                    const int *A = boxes + 6 * a;
-                    long offa = off[a];
-                    for (int c = 0; c < ncomp; ++c)
-                        data[offb + fab_index(B, g, i, j, k, c)] = data[offa + fab_index(A, g, wi, wj, wk, c)];
-                    ++written;
-                }
-    }
+    for (int b = 0; b < nbox; ++b) written += fill_box(b, nbox, boxes, dlo, dhi, g, ncomp, off, data);
     free(off);
     return written;
 }
@@ -194,11 +209,11 @@ long orc_fill_boundary(int nbox, const int *boxes, const int *dlo, const int *dh
  * b[0..R-1] holds b_1..b_R; lam[c] = D_c dt / dx^2.  Reads the ghost cells of src
  * (FillBoundary must have run) and writes the valid cells of dst only.
  */
-void orc_stencil_flux(int nbox, const int *boxes, int g, int ncomp, int R, const double *bcoef, const double *lam,
-                      const double *src, double *dst)
+/* the valid cells of box b of dst */
+static void stencil_flux_box(int b, const int *boxes, int g, int ncomp, int R, const double *bcoef, const double *lam,
+                             const long *offs, const double *src, double *dst)
 {
-    long *offs = fab_offsets(nbox, boxes, g, ncomp);
-    for (int b = 0; b < nbox; ++b) {
+    {
         const int *B = boxes + 6 * b;
         long off = offs[b];
         long n[3] = {B[3] - B[0] + 1, B[4] - B[1] + 1, B[5] - B[2] + 1};
@@ -248,6 +263,13 @@ void orc_stencil_flux(int nbox, const int *boxes, int g, int ncomp, int R, const
         }
         for (int d = 0; d < 3; ++d) free(F[d]);
     }
+}
+
+void orc_stencil_flux(int nbox, const int *boxes, int g, int ncomp, int R, const double *bcoef, const double *lam,
+                      const double *src, double *dst)
+{
+    long *offs = fab_offsets(nbox, boxes, g, ncomp);
+    for (int b = 0; b < nbox; ++b) stencil_flux_box(b, boxes, g, ncomp, R, bcoef, lam, offs, src, dst);
     free(offs);
 }
 
@@ -298,6 +320,41 @@ int orc_advance(int nbox, const int *boxes, const int *dlo, const int *dhi, int 
         orc_stencil_flux(nbox, boxes, g, ncomp, R, bcoef, lam, cur, nxt);
         double *t = cur; cur = nxt; nxt = t;
     }
+    return cur == a ? 0 : 1;
+}
+
+/* The threads orc_advance_omp uses (1 when the library was built without OpenMP). */
+int orc_omp_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/*
+ * orc_advance with the paper's threaded loop (Sec. 3.3): in each phase the boxes are shared among
+ * OpenMP threads.  Every box's ghost fill writes only that box's ghost cells and reads only valid
+ * cells, and every box's stencil writes only that box's valid cells, so the bits equal orc_advance's.
+ */
+int orc_advance_omp(int nbox, const int *boxes, const int *dlo, const int *dhi, int g, int ncomp, int R,
+                    const double *bcoef, const double *lam, int nsteps, double *a, double *b)
+{
+    double *cur = a, *nxt = b;
+    long *off = fab_offsets(nbox, boxes, g, ncomp);
+    for (int s = 0; s < nsteps; ++s) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+        for (int i = 0; i < nbox; ++i) fill_box(i, nbox, boxes, dlo, dhi, g, ncomp, off, cur);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+        for (int i = 0; i < nbox; ++i) stencil_flux_box(i, boxes, g, ncomp, R, bcoef, lam, off, cur, nxt);
+        double *t = cur; cur = nxt; nxt = t;
+    }
+    free(off);
     return cur == a ? 0 : 1;
 }
 

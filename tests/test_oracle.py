@@ -669,3 +669,16 @@ def test_average_down_matches_block_mean(ratio):
         sl = (slice(B[2] // ratio, B[5] // ratio + 1), slice(B[1] // ratio, B[4] // ratio + 1),
               slice(B[0] // ratio, B[3] // ratio + 1))
         np.testing.assert_allclose(dense[sl], block[sl], rtol=0, atol=ratio * 4e-16 * np.max(np.abs(block)))
+
+
+@pytest.mark.parametrize("R", [1, 2, 4])
+def test_threaded_oracle_gives_the_same_bits(R):
+    """The paper's threaded loop over boxes (Sec. 3.3; the CPU baseline) against the
+    single-threaded oracle: identical bits, on an uneven layout."""
+    lo, hi = [0, 0, 0], [23, 15, 19]
+    boxes = np.array([[0, 0, 0, 9, 15, 7], [10, 0, 0, 23, 6, 7], [10, 7, 0, 23, 15, 7], [0, 0, 8, 5, 15, 19],
+                      [6, 0, 8, 23, 8, 12], [6, 9, 8, 23, 15, 12], [6, 0, 13, 23, 15, 19]], dtype=np.int32)
+    L = oracle.Level(boxes, lo, hi, R, 2)
+    u = L.from_dense(_rand((2, 20, 16, 24), seed=40 + R))
+    lam = {1: 0.15, 2: 0.1125, 4: 0.09}[R]
+    np.testing.assert_array_equal(oracle.advance_omp(L, u, R, lam, 3), oracle.advance(L, u, R, lam, 3))
