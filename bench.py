@@ -425,37 +425,45 @@ def manybox_step_bytes(S, C, boxes, R):
 
 
 def manybox_line(mf, torch, flush, args, hbm):
-    """512^3 with 2 components in 4096 and 32768 uneven boxes of 8^3-32^3, 2 ghost cells, the
-    13-point stencil, FP32, 50 time steps per bench step: the whole level in one launch per
-    phase of a captured graph, whatever the box count."""
+    """512^3 with 2 components in 4096, 8192, 16384 and 32768 uneven boxes of 8^3-32^3, 2 ghost
+    cells, the 13-point stencil, 50 time steps per bench step: the whole level in one launch per
+    phase of a captured graph, whatever the box count.  FP32 at every box count, and FP64-accurate
+    (fixed-point steps, MF_FIXED_DIFF) at the two ends; the field is evaluated on the device by
+    the seeded generator."""
     cfg = synth.WORKLOADS["c5"]
     N, R, C, n = cfg["N"], cfg["R"], cfg["ncomp"], cfg["nsteps"]
-    dense = synth.initial_field(cfg)
+    dense = synth.initial_field_device(cfg, "cuda").cpu().pin_memory()
+    torch.cuda.empty_cache()
     dt = synth.dt_for(cfg)
     out = {}
-    for target in (4096, 32768):
+    runs = [(t, "f32", 0) for t in cfg["targets"]] + [(t, "f64fixed", mf.MF_FIXED_DIFF) for t in (4096, 32768)]
+    for target, dtype, flags in runs:
         boxes = synth.uneven_boxes(N, target)
-        g = mf.MultiFab([0, 0, 0], [N - 1] * 3, boxes=boxes, ncomp=C, ngrow=cfg["ngrow"], dtype="f32")
+        g = mf.MultiFab([0, 0, 0], [N - 1] * 3, boxes=boxes, ncomp=C, ngrow=cfg["ngrow"],
+                        dtype="f64" if flags else dtype)
         g.from_host(dense)
         for _ in range(max(1, args.warmup)):
-            g.advance(R, [1.0] * C, dt, n)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        for k in range(args.steps):
+            g.advance(R, [1.0] * C, dt, n, flags)
+        K = max(2, args.steps // 2)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        for k in range(K):
             flush()
             ev[k][0].record(g.stream)
-            g.advance(R, [1.0] * C, dt, n)
+            g.advance(R, [1.0] * C, dt, n, flags)
             ev[k][1].record(g.stream)
         torch.cuda.synchronize()
-        ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-        step_bytes = manybox_step_bytes(4, C, boxes, R)
-        out[str(target)] = {"value": N ** 3 * n / (ms * 1e-3), "unit": UNIT, "ms_per_bench_step": ms,
-                            "cell_comp_updates_per_s": N ** 3 * C * n / (ms * 1e-3),
-                            "boxes": target, "step_bytes": step_bytes,
-                            "step_frac": step_bytes * n / (ms * 1e-3) / 1e9 / hbm,
-                            "launches_per_bench_step": mf.mf_launch_count(g.h), "schedule": mf.mf_get_schedule(g.h)}
+        ms = sum(a.elapsed_time(b) for a, b in ev) / K
+        step_bytes = manybox_step_bytes(8 if flags else 4, C, boxes, R)
+        out["%d_%s" % (target, dtype)] = {
+            "value": N ** 3 * n / (ms * 1e-3), "unit": UNIT, "ms_per_bench_step": ms,
+            "cell_comp_updates_per_s": N ** 3 * C * n / (ms * 1e-3), "boxes": target, "dtype": dtype,
+            "step_bytes": step_bytes, "step_frac": step_bytes * n / (ms * 1e-3) / 1e9 / hbm,
+            "launches_per_bench_step": mf.mf_launch_count(g.h), "schedule": mf.mf_get_schedule(g.h)}
         del g
-    out["workload"] = ("manybox512_c2: periodic 512^3, 2 components, 4096 / 32768 uneven boxes of 8^3-32^3, "
-                       "ngrow 2, 13-point stencil, FP32, %d steps per bench step" % n)
+        torch.cuda.empty_cache()
+    out["workload"] = ("manybox512_c2: periodic 512^3, 2 components, 4096-32768 uneven boxes of 8^3-32^3, "
+                       "ngrow 2, 13-point stencil, FP32 and FP64-accurate fixed-point steps, %d steps per bench "
+                       "step" % n)
     return out
 
 

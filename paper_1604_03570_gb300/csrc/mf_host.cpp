@@ -1025,7 +1025,7 @@ static bool tma_geometry(mf_t *m, int R, bool fix, const std::vector<char> &serv
     }
     // a producer warp plus one consumer thread per group, rounded up to a warp
     gpt = 32 + (maxgroups + 31) / 32 * 32;
-    if (gpt > (fix ? tma_max_threads_fix(R, eff_rows(m, R), eff_gb(m, R)) : tma_max_threads(R))) return false;
+    if (gpt > (fix ? tma_max_threads_fix(R, eff_rows(m, R), eff_gb(m, R)) : tma_max_threads(m->dtype, R))) return false;
     slot_bytes = (maxplane + 127) / 128 * 128;
     return true;
 }

@@ -221,7 +221,7 @@ cudaError_t launch_stencil_tma_rk(int dtype, int R, bool fp64diff, int rows, int
                                   int grid, cudaStream_t s);
 // whether the TMA stencil has a schedule with rows rows of gb-byte groups per thread
 bool tma_has_group(int dtype, int R, int rows, int gb);
-int tma_max_threads(int R);      // largest CTA of the TMA stencil for radius R
+int tma_max_threads(int dtype, int R);  // largest CTA of the TMA stencil for a storage type and radius R
 int tma_max_rows(int R);         // most rows of 16-byte groups a TMA stencil thread may compute
 // resident CTAs per SM of the TMA stencil with nt threads and smem dynamic shared bytes (0: none)
 int tma_ctas_per_sm(int dtype, int R, int rows, int gb, int nt, int smem);

@@ -110,6 +110,30 @@ __device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) {
     return r;
 }
 
+__device__ __forceinline__ F2 mul2(F2 a, F2 b) {
+    F2 r;
+    asm("{\n\t.reg .b64 a, b, d;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
+        "mul.rn.f32x2 d, a, b;\n\tmov.b64 {%0, %1}, d;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+
+// face_flux<float, R> of two lines at once (qa, qb; the same face index c): the same operations
+// in the same order, each lane rounded as the scalar code rounds it.
+template <int R>
+__device__ __forceinline__ F2 face_flux2(const float *qa, const float *qb, int c) {
+    if constexpr (R == 1) return sub2(F2{qa[c + 1], qb[c + 1]}, F2{qa[c], qb[c]});
+    const float b1 = (float)FluxW<R>::b(1);
+    F2 f = mul2(F2{b1, b1}, sub2(F2{qa[c + 1], qb[c + 1]}, F2{qa[c], qb[c]}));
+#pragma unroll
+    for (int m = 2; m <= R; ++m) {
+        const float bm = (float)FluxW<R>::b(m);
+        f = fma2(F2{bm, bm}, sub2(F2{qa[c + m], qb[c + m]}, F2{qa[c + 1 - m], qb[c + 1 - m]}), f);
+    }
+    return f;
+}
+
 // Runge-Kutta stage combination a * u0 + b * e of the state at the start of the step (u0) and
 // the forward-Euler value e: one rounding of the product b * e, one of the fused multiply-add.
 template <typename A> __device__ __forceinline__ A rk_combine(A e, A u0, A a, A b) {

@@ -7,7 +7,7 @@ namespace mfk {
 
 template <typename S, typename A, int R, int ROWS, int GB>
 static int tma_occ(int nt, int smem) {
-    if (nt < 64 || nt > TmaBounds<R>::threads || nt % 32) return 0;
+    if (nt < 64 || nt > TmaThreads<S, R, A, ROWS, GB>::value || nt % 32) return 0;
     if (tma_configure<S, A, R, ROWS, GB, false>(smem) != cudaSuccess) return 0;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stencil_tma<S, A, R, ROWS, GB, false>, nt, smem) !=
@@ -36,7 +36,10 @@ int tma_ctas_per_sm(int dtype, int R, int rows, int gb, int nt, int smem) {
     return 0;
 }
 
-int tma_max_threads(int R) { return R == 1 ? TmaBounds<1>::threads : R == 2 ? TmaBounds<2>::threads : TmaBounds<4>::threads; }
+int tma_max_threads(int dtype, int R) {
+    if (dtype == BF16) return TmaThreads<__nv_bfloat16, 1, float, 1, 16>::value;
+    return R == 1 ? TmaBounds<1>::threads : R == 2 ? TmaBounds<2>::threads : TmaBounds<4>::threads;
+}
 int tma_max_rows(int R) { return R == 4 ? 1 : 2; }
 bool tma_has_group(int dtype, int R, int rows, int gb) {
     if (gb == 16) return rows >= 1 && rows <= tma_max_rows(R);

@@ -18,7 +18,7 @@ namespace {
 struct OccFix {
     int nt, smem;
     template <int R, int ROWS, int GB> int run() {
-        if (nt < 64 || nt > TmaThreads<R, FixA, ROWS, GB>::value || nt % 32) return 0;
+        if (nt < 64 || nt > TmaThreads<long long, R, FixA, ROWS, GB>::value || nt % 32) return 0;
         if (tma_configure<long long, FixA, R, ROWS, GB, false>(smem) != cudaSuccess) return 0;
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stencil_tma<long long, FixA, R, ROWS, GB, false>,
@@ -63,7 +63,7 @@ int tma_ctas_per_sm_fix(int R, int rows, int gb, int nt, int smem) {
 
 namespace {
 struct MaxThreadsFix {
-    template <int R, int ROWS, int GB> int run() { return TmaThreads<R, FixA, ROWS, GB>::value; }
+    template <int R, int ROWS, int GB> int run() { return TmaThreads<long long, R, FixA, ROWS, GB>::value; }
 };
 }  // namespace
 

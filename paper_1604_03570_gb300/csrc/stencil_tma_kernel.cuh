@@ -194,8 +194,12 @@ template <int R, typename A = float> struct TmaBounds { static constexpr int thr
 template <int R> struct TmaBounds<R, FixA> { static constexpr int threads = R == 4 ? 288 : 416; };
 // The launch bound of one schedule: the fixed-point path's 2-row, 32-byte-group schedule keeps
 // eight cells per thread and takes more registers (smaller CTAs).
-template <int R, typename A, int ROWS, int GB> struct TmaThreads { static constexpr int value = TmaBounds<R, A>::threads; };
-template <> struct TmaThreads<1, FixA, 2, 32> { static constexpr int value = 288; };
+// BF16 storage: a 16-byte group holds 8 cells, so its tiles need few threads, and its unpacked
+// FP32 windows many registers.
+template <typename S, int R, typename A, int ROWS, int GB> struct TmaThreads {
+    static constexpr int value = std::is_same<S, __nv_bfloat16>::value ? 288 : TmaBounds<R, A>::threads;
+};
+template <> struct TmaThreads<long long, 1, FixA, 2, 32> { static constexpr int value = 288; };
 
 // One ghost-push piece as a consumer warp keeps it (see the tile prologue).
 struct PushRec {
@@ -207,11 +211,14 @@ struct PushRec {
 
 
 template <typename S, typename A, int R, int ROWS, int GB, bool RK>
-__global__ void __launch_bounds__(TmaThreads<R, A, ROWS, GB>::value) k_stencil_tma(const __grid_constant__ StencilTmaParams p) {
+__global__ void __launch_bounds__(TmaThreads<S, R, A, ROWS, GB>::value) k_stencil_tma(const __grid_constant__ StencilTmaParams p) {
     using V = VG<S, GB>;
     constexpr int VX = V::n;  // cells per group: one GB-byte vector of a row
     // FP32 arithmetic at radius 1: pairs of cells through the packed f32x2 instructions
     constexpr bool kPair = std::is_same<A, float>::value && R == 1 && VX % 2 == 0;
+    // FP32 arithmetic at radius 2 and 4: the face fluxes and the update of pairs of cells through
+    // the packed instructions (face_flux2), the same operations in the same order as the scalar code
+    constexpr bool kPairR = std::is_same<A, float>::value && R > 1 && VX % 2 == 0;
     // exact fixed-point differences, FP64 update (fixed_diff.cuh)
     constexpr bool kFix = std::is_same<A, FixA>::value;
     static_assert(!kFix || (std::is_same<S, long long>::value && !RK), "fixed-point steps: 64-bit storage, plain steps");
@@ -221,7 +228,7 @@ __global__ void __launch_bounds__(TmaThreads<R, A, ROWS, GB>::value) k_stencil_t
     const int NS = p.nstages;  // power of two
     const int tid = threadIdx.x;
     const int ncw = (int)(blockDim.x >> 5) - 1;  // consumer warps
-    __shared__ PushRec ptab[TmaThreads<R, A, ROWS, GB>::value / 32 - 1][kMaxPush];  // per consumer warp
+    __shared__ PushRec ptab[TmaThreads<S, R, A, ROWS, GB>::value / 32 - 1][kMaxPush];  // per consumer warp
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(&full[s], 1);
@@ -702,6 +709,22 @@ __global__ void __launch_bounds__(TmaThreads<R, A, ROWS, GB>::value) k_stencil_t
                             fy[r][c] = d.x;
                             fy[r][c + 1] = d.y;
                         }
+                } else if constexpr (kPairR) {
+#pragma unroll
+                    for (int c = 0; c < VX; c += 2) {
+                        float ca[2 * R + ROWS], cb[2 * R + ROWS];
+#pragma unroll
+                        for (int m = 0; m < 2 * R + ROWS; ++m) {
+                            ca[m] = wy[m][c];
+                            cb[m] = wy[m][c + 1];
+                        }
+#pragma unroll
+                        for (int r = 0; r <= ROWS; ++r) {
+                            const F2 fyr = face_flux2<R>(ca, cb, R - 1 + r);
+                            fy[r][c] = fyr.x;
+                            fy[r][c + 1] = fyr.y;
+                        }
+                    }
                 } else {
 #pragma unroll
                     for (int c = 0; c < VX; ++c) {
@@ -730,8 +753,18 @@ __global__ void __launch_bounds__(TmaThreads<R, A, ROWS, GB>::value) k_stencil_t
                             if (cov & (1u << c)) wx[R + c] = ld_smem<S, A>(cp + cob + r * p.strip_w + c);
                     }
                     A fx[VX + 1];  // x-face fluxes: fx[c] is the face left of cell c
+                    if constexpr (kPairR) {
 #pragma unroll
-                    for (int c = 0; c <= VX; ++c) fx[c] = face_flux<A, R>(wx, c + R - 1);
+                        for (int c = 0; c < VX; c += 2) {
+                            const F2 fxc = face_flux2<R>(wx, wx + 1, c + R - 1);
+                            fx[c] = fxc.x;
+                            fx[c + 1] = fxc.y;
+                        }
+                        fx[VX] = face_flux<A, R>(wx, VX + R - 1);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c <= VX; ++c) fx[c] = face_flux<A, R>(wx, c + R - 1);
+                    }
                     if constexpr (kPair) {
                         // the same operations as update_cell_f in the same order, two cells at a time:
                         // ((fxp - fxm) + (fyp - fym)) + (fzp - fzm), then u + lam * div
@@ -751,6 +784,26 @@ __global__ void __launch_bounds__(TmaThreads<R, A, ROWS, GB>::value) k_stencil_t
                             q[r][c][1] = q[r][c][2];
                             q[r][c + 1][0] = q[r][c + 1][1];
                             q[r][c + 1][1] = q[r][c + 1][2];
+                        }
+                    } else if constexpr (kPairR) {
+                        // update_cell_f's operations in its order, two cells at a time
+#pragma unroll
+                        for (int c = 0; c < VX; c += 2) {
+                            const F2 fzp = face_flux2<R>(q[r][c], q[r][c + 1], R);
+                            const F2 u = F2{q[r][c][R], q[r][c + 1][R]};
+                            const F2 dx = sub2(F2{fx[c + 1], fx[c + 2]}, F2{fx[c], fx[c + 1]});
+                            const F2 dy = sub2(F2{fy[r + 1][c], fy[r + 1][c + 1]}, F2{fy[r][c], fy[r][c + 1]});
+                            const F2 dz = sub2(fzp, F2{fzm[r][c], fzm[r][c + 1]});
+                            const F2 o = fma2(F2{lam, lam}, add2(add2(dx, dy), dz), u);
+                            out[r][c] = o.x;
+                            out[r][c + 1] = o.y;
+                            fzm[r][c] = fzp.x;
+                            fzm[r][c + 1] = fzp.y;
+#pragma unroll
+                            for (int i = 0; i < 2 * R; ++i) {
+                                q[r][c][i] = q[r][c][i + 1];
+                                q[r][c + 1][i] = q[r][c + 1][i + 1];
+                            }
                         }
                     } else {
 #pragma unroll
@@ -809,7 +862,7 @@ static cudaError_t tma_configure(int smem) {
 
 template <typename S, typename A, int R, int ROWS, int GB, bool RK>
 static cudaError_t tma_t(int nt, const StencilTmaParams &p, int grid, cudaStream_t s) {
-    if (nt < 64 || nt > TmaThreads<R, A, ROWS, GB>::value || nt % 32) return cudaErrorInvalidValue;
+    if (nt < 64 || nt > TmaThreads<S, R, A, ROWS, GB>::value || nt % 32) return cudaErrorInvalidValue;
     const int smem = p.nstages * p.slot_bytes + 128;
     auto kern = k_stencil_tma<S, A, R, ROWS, GB, RK>;
     cudaError_t e = tma_configure<S, A, R, ROWS, GB, RK>(smem);
