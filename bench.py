@@ -54,6 +54,9 @@ def parse():
                    help="fixed schedule 'x,y,z,rows,stages,group_bytes' instead of the autotuner")
     p.add_argument("--fixed", action="store_true",
                    help="headline with --dtype f64: fixed-point differences (MF_FIXED_DIFF)")
+    p.add_argument("--c3-n", type=int, default=None,
+                   help="with --only diff8th512: domain edge N instead of 512 (a smaller level to profile)")
+    p.add_argument("--c3-dtype", default="f32,f64", help="with --only diff8th512: storage types to run")
     p.add_argument("--plain", action="store_true",
                    help="headline as the untiled per-box sweep (MF_PLAIN_PER_BOX), for profiling the baseline")
     a = p.parse_args()
@@ -383,19 +386,29 @@ def diff8th_line(mf, torch, flush, args, hbm):
     boxes of 128^3, 4 ghost cells, per-component diffusivities, 20 forward-Euler steps per bench
     step, FP32 and FP64 storage.  The initial field (8 seeded modes per component plus 1e-6
     noise) is evaluated on the device by the same generator as the host's (synth)."""
-    cfg = synth.WORKLOADS["c3"]
+    cfg = dict(synth.WORKLOADS["c3"])
+    if args.only == "diff8th512" and args.c3_n:
+        cfg["N"] = args.c3_n
     N, R, C, n, mgs = cfg["N"], cfg["R"], cfg["ncomp"], cfg["nsteps"], cfg["max_grid_size"]
     D = [float(d) for d in synth.diffusivities(cfg)]
     dt = synth.dt_for(cfg)
-    dense = synth.initial_field_device(cfg, "cuda").cpu().pin_memory()
+    dense = synth.initial_field_device(cfg, "cuda", N=N).cpu().pin_memory()
     torch.cuda.empty_cache()
     V, nbox = N ** 3, (N // mgs) ** 3
-    out = {"workload": "diff8th512_c5: periodic 512^3, 64 boxes of 128^3, ngrow 4, 5 components, 25-point "
-                       "8th-order stencil, D_c in [0.5, 2], %d forward-Euler steps per bench step" % n}
+    out = {"workload": "diff8th512_c5: periodic %d^3, %d boxes of 128^3, ngrow 4, 5 components, 25-point "
+                       "8th-order stencil, D_c in [0.5, 2], %d forward-Euler steps per bench step"
+                       % (N, (N // mgs) ** 3, n)}
     K = max(2, args.steps // 4)
+    dtypes = args.c3_dtype.split(",") if args.only == "diff8th512" else ["f32", "f64"]
     for dtype, S in (("f32", 4), ("f64", 8)):
+        if dtype not in dtypes:
+            continue
         g = mf.MultiFab([0, 0, 0], [N - 1] * 3, max_grid_size=mgs, ncomp=C, ngrow=cfg["ngrow"], dtype=dtype)
         g.from_host(dense)
+        if args.only == "diff8th512" and args.schedule:
+            v = [int(x) for x in args.schedule.split(",")]
+            g.set_tile(tuple(v[:3]))
+            mf.mf_set_schedule(g.h, *v[3:6])
         g.advance(R, D, dt, n)  # autotune and capture
         t = time_advances(g, R, D, dt, n, K, flush)
         ms = sum(t) / len(t)
@@ -409,7 +422,8 @@ def diff8th_line(mf, torch, flush, args, hbm):
                       "launches_per_bench_step": mf.mf_launch_count(g.h), "schedule": mf.mf_get_schedule(g.h)}
         del g
         torch.cuda.empty_cache()
-    out["speedup_f32_vs_f64"] = out["f32"]["value"] / out["f64"]["value"]
+    if "f32" in out and "f64" in out:
+        out["speedup_f32_vs_f64"] = out["f32"]["value"] / out["f64"]["value"]
     return out
 
 

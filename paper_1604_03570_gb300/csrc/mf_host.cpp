@@ -977,14 +977,16 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-// The schedule a radius-R launch uses: rows per thread clipped to what R allows; 32-byte
-// groups only where that variant exists, else 16-byte groups.
 // The schedule the TMA build uses: the chosen rows and group bytes where the kernel variant
-// (plain arithmetic, or fixed point -- bit 8 of the build key) has them.
+// (plain arithmetic, or fixed point -- bit 8 of the build key) has them, else one row and
+// 16-byte groups.
 static bool tma_has(const mf_t *m, int R, int rows, int gb) {
     return (m->tma_R & 8) ? tma_has_group_fix(R, rows, gb) : tma_has_group(m->dtype, R, rows, gb);
 }
-static int eff_rows(const mf_t *m, int R) { return std::min(m->tma_rows, tma_max_rows(R)); }
+static int eff_rows(const mf_t *m, int R) {
+    const int rows = std::min(m->tma_rows, tma_max_rows(R));
+    return tma_has(m, R, rows, 16) ? rows : 1;
+}
 static int eff_gb(const mf_t *m, int R) { return tma_has(m, R, eff_rows(m, R), m->tma_gb) ? m->tma_gb : 16; }
 
 // Plane geometry of every FArrayBox for the current tile shape and radius R; false when a
@@ -1187,12 +1189,14 @@ static int build_tma(mf_t *m, int R, bool fix = false) {
     const int slot = main_slot + 2 * strip_pitch;
     int ns = m->tma_ns_pref ? m->tma_ns_pref : (R == 4 ? 16 : 8);  // ring slots (power of two)
     if (ns < 2 * R + 1) ns = R == 4 ? 16 : 8;
-    const int rings = fix ? 2 : 1;  // the fixed-point kernel keeps a converted copy of every slot
-    while (ns > 8 && (long long)rings * ns * slot + 128 > 160 * 1024) ns /= 2;
-    if (ns < 2 * R + 1 || (long long)rings * ns * slot + 128 > 200 * 1024) return 0;
+    // the ring shrinks towards 160 KB while it keeps 2R + 1 planes and some in flight; a CTA may
+    // take up to 227 KB of shared memory, of which the kernel's static tables use below 8 KB
+    const int ns_floor = R == 4 ? 16 : 8;
+    while (ns > ns_floor && (long long)ns * slot + 128 > 160 * 1024) ns /= 2;
+    if (ns < 2 * R + 1 || (long long)ns * slot + 128 > 227 * 1024 - 8192) return 0;
     if (m->tile[2] <= 0) {
         // whole-box z extent: split the columns over exactly one wave of CTAs
-        const int per_sm = fix ? tma_ctas_per_sm_fix(R, eff_rows(m, R), eff_gb(m, R), gpt, 2 * ns * slot + 128)
+        const int per_sm = fix ? tma_ctas_per_sm_fix(R, eff_rows(m, R), eff_gb(m, R), gpt, ns * slot + 128)
                                : tma_ctas_per_sm(m->dtype, R, eff_rows(m, R), eff_gb(m, R), gpt, ns * slot + 128);
         if (per_sm < 1) return 0;
         const int G = per_sm * sm_count();

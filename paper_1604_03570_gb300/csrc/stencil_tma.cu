@@ -40,9 +40,9 @@ int tma_max_threads(int dtype, int R) {
     if (dtype == BF16) return TmaThreads<__nv_bfloat16, 1, float, 1, 16>::value;
     return R == 1 ? TmaBounds<1>::threads : R == 2 ? TmaBounds<2>::threads : TmaBounds<4>::threads;
 }
-int tma_max_rows(int R) { return R == 4 ? 1 : 2; }
+int tma_max_rows(int) { return 2; }
 bool tma_has_group(int dtype, int R, int rows, int gb) {
-    if (gb == 16) return rows >= 1 && rows <= tma_max_rows(R);
+    if (gb == 16) return rows >= 1 && rows <= tma_max_rows(R) && !(R == 4 && rows == 2 && dtype == BF16);
     return gb == 32 && dtype != BF16 && R <= 2 && rows == 1;
 }
 

@@ -70,7 +70,7 @@ struct MaxThreadsFix {
 int tma_max_threads_fix(int R, int rows, int gb) { return tma_dispatch<long long>(R, rows, gb, MaxThreadsFix{}, 0); }
 
 bool tma_has_group_fix(int R, int rows, int gb) {
-    if (gb == 16) return rows >= 1 && rows <= tma_max_rows(R);
+    if (gb == 16) return rows >= 1 && rows <= (R == 4 ? 1 : 2);
     return gb == 32 && ((R == 1 && rows <= 2) || (R == 2 && rows == 1));
 }
 

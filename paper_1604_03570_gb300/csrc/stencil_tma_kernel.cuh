@@ -189,17 +189,19 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 // consumer warp keeps the tile's push pieces in a small shared-memory table, written once per
 // tile, and tests a piece's z range before touching it.
 // The CTA has 32 + (consumer groups rounded up to a warp) threads.
-template <int R, typename A = float> struct TmaBounds { static constexpr int threads = R == 4 ? 416 : 544; };
-// the fixed-point path keeps 64-bit integers in its queues: fewer threads, more registers each
-template <int R> struct TmaBounds<R, FixA> { static constexpr int threads = R == 4 ? 288 : 416; };
-// The launch bound of one schedule: the fixed-point path's 2-row, 32-byte-group schedule keeps
-// eight cells per thread and takes more registers (smaller CTAs).
-// BF16 storage: a 16-byte group holds 8 cells, so its tiles need few threads, and its unpacked
-// FP32 windows many registers.
+// Launch bounds and registers: ptxas gives a kernel bounded to w warps per CTA at most
+// 16384 / ceil(w / 4) / 32 registers per thread, rounded down to a multiple of 8 (17 warps: 96,
+// 13-16: 128, 9-12: 168, up to 8: 255).  At radius 1 and 2 the 17-warp bound keeps the kernels
+// at 96 registers, so that two 9-warp CTAs share an SM; the 25-point stencil, the
+// fixed-point path's 64-bit queues and BF16 storage's unpacked 8-cell groups take 168 (12
+// warps) or 128 (13 warps).
+template <int R, typename A = float> struct TmaBounds { static constexpr int threads = R == 4 ? 384 : 544; };
+template <int R> struct TmaBounds<R, FixA> { static constexpr int threads = R == 4 ? 384 : 416; };
 template <typename S, int R, typename A, int ROWS, int GB> struct TmaThreads {
-    static constexpr int value = std::is_same<S, __nv_bfloat16>::value ? 288 : TmaBounds<R, A>::threads;
+    static constexpr int value = std::is_same<S, __nv_bfloat16>::value ? 384 : TmaBounds<R, A>::threads;
 };
-template <> struct TmaThreads<long long, 1, FixA, 2, 32> { static constexpr int value = 288; };
+// the fixed-point path's 2-row, 32-byte-group schedule keeps eight 64-bit cells per thread
+template <> struct TmaThreads<long long, 1, FixA, 2, 32> { static constexpr int value = 384; };
 
 // One ghost-push piece as a consumer warp keeps it (see the tile prologue).
 struct PushRec {
@@ -404,6 +406,22 @@ __global__ void __launch_bounds__(TmaThreads<S, R, A, ROWS, GB>::value) k_stenci
             }
             cob = rso + y0 * xw + ts.ridx0 + x0c - n0;
         }
+        // Where R cells are a whole number of 16-byte vectors (R = 4 in FP32, R >= 2 in FP64), the
+        // x halo of a row is usually R consecutive, aligned shared-memory elements on each side
+        // (box widths and row pitches multiples of 16 bytes): then it is read as vectors.  The
+        // whole warp takes the vector path or the per-cell one.
+        constexpr int kHV = (R * (int)sizeof(S)) % 16 == 0 ? R * (int)sizeof(S) / 16 : 0;  // vectors per side
+        bool hvec = false;
+        if constexpr (kHV > 0) {
+            bool ok = true;
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+                ok = ok && (hl[r][0] * (int)sizeof(S)) % 16 == 0 && (hr[r][0] * (int)sizeof(S)) % 16 == 0;
+#pragma unroll
+                for (int i = 1; i < R; ++i) ok = ok && hl[r][i] == hl[r][0] + i && hr[r][i] == hr[r][0] + i;
+            }
+            hvec = __all_sync(0xffffffffu, ok);
+        }
         const long long ooff = f.org + t.comp * f.cstride + (long long)t.z0 * f.plane + (long long)(t.y0 + y0) * f.px + x0c;
         S *op = (S *)p.dst[f.level] + ooff;
         // Runge-Kutta stage: the state at the start of the step, at the output's position
@@ -593,10 +611,18 @@ __global__ void __launch_bounds__(TmaThreads<S, R, A, ROWS, GB>::value) k_stenci
 #pragma unroll
                 for (int r = 0; r < ROWS; ++r) {
                     long long wx[VX + 2 * R];  // x window: wx[i] = K(x0 - R + i)
+                    if (kHV > 0 && hvec) {
 #pragma unroll
-                    for (int i = 0; i < R; ++i) {
-                        wx[i] = cp[hl[r][i]];
-                        wx[R + VX + i] = cp[hr[r][i]];
+                        for (int j = 0; j < kHV; ++j) {
+                            V16<S>::template ld<long long>(cp + hl[r][0] + j * V16<S>::n, wx + j * V16<S>::n);
+                            V16<S>::template ld<long long>(cp + hr[r][0] + j * V16<S>::n, wx + R + VX + j * V16<S>::n);
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < R; ++i) {
+                            wx[i] = cp[hl[r][i]];
+                            wx[R + VX + i] = cp[hr[r][i]];
+                        }
                     }
 #pragma unroll
                     for (int c = 0; c < VX; ++c) wx[R + c] = q[r][c][R];
@@ -670,7 +696,9 @@ __global__ void __launch_bounds__(TmaThreads<S, R, A, ROWS, GB>::value) k_stenci
             for (int pl = 0; pl < 2 * R; ++pl)
                 if (pl < R || pl >= t.tz + R) release(seq + pl);
 
-#pragma unroll(kPair ? 2 : 1)
+            // unrolled by two at radius 1 (packed pairs) and 4, so that half the queue shifts become
+            // register renames (at radius 2 the unrolled loop spills)
+#pragma unroll(kPair || R == 4 ? 2 : 1)
             for (int k = 0; k < t.tz; ++k) {
                 if (!__all_sync(0xffffffffu, wait_seq(seq + k + 2 * R))) {
                     if (lane == 0) atomicOr(p.err, 1);
@@ -678,6 +706,23 @@ __global__ void __launch_bounds__(TmaThreads<S, R, A, ROWS, GB>::value) k_stenci
                 }
                 const S *newp = slot_ptr(seq + k + 2 * R);
                 const S *cp = slot_ptr(seq + k + R);
+                // Runge-Kutta stage: the state at the start of the step at this plane's cells, read
+                // from global memory before the arithmetic that hides its latency
+                A u0v[RK ? ROWS : 1][VX];
+                if constexpr (RK) {
+#pragma unroll
+                    for (int r = 0; r < ROWS; ++r) {
+                        if (r >= nrow) continue;
+                        const S *urow = u0p + r * f.px;
+                        if (full) {
+                            V::ld(urow, u0v[r]);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < VX; ++c) u0v[r][c] = x0c + c < f.n[0] ? ld<S, A>(urow + c) : (A)0;
+                        }
+                    }
+                    u0p += f.plane;
+                }
 #pragma unroll
                 for (int r = 0; r < ROWS; ++r) {
                     A v[VX];
@@ -740,10 +785,18 @@ __global__ void __launch_bounds__(TmaThreads<S, R, A, ROWS, GB>::value) k_stenci
                 for (int r = 0; r < ROWS; ++r) {
                     // x window: w[i] = u(x0 - R + i), i = 0 .. VX + 2R - 1
                     A wx[VX + 2 * R];
+                    if (kHV > 0 && hvec) {
 #pragma unroll
-                    for (int i = 0; i < R; ++i) {
-                        wx[i] = ld_smem<S, A>(cp + hl[r][i]);
-                        wx[R + VX + i] = ld_smem<S, A>(cp + hr[r][i]);
+                        for (int j = 0; j < kHV; ++j) {
+                            V16<S>::ld(cp + hl[r][0] + j * V16<S>::n, wx + j * V16<S>::n);
+                            V16<S>::ld(cp + hr[r][0] + j * V16<S>::n, wx + R + VX + j * V16<S>::n);
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < R; ++i) {
+                            wx[i] = ld_smem<S, A>(cp + hl[r][i]);
+                            wx[R + VX + i] = ld_smem<S, A>(cp + hr[r][i]);
+                        }
                     }
 #pragma unroll
                     for (int c = 0; c < VX; ++c) wx[R + c] = q[r][c][R];
@@ -827,18 +880,9 @@ __global__ void __launch_bounds__(TmaThreads<S, R, A, ROWS, GB>::value) k_stenci
 #pragma unroll
                     for (int r = 0; r < ROWS; ++r) {
                         if (r >= nrow) continue;
-                        A u[VX];
-                        const S *urow = u0p + r * f.px;
-                        if (full) {
-                            V::ld(urow, u);
-                        } else {
 #pragma unroll
-                            for (int c = 0; c < VX; ++c) u[c] = x0c + c < f.n[0] ? ld<S, A>(urow + c) : (A)0;
-                        }
-#pragma unroll
-                        for (int c = 0; c < VX; ++c) out[r][c] = rk_combine<A>(out[r][c], u[c], rka, rkb);
+                        for (int c = 0; c < VX; ++c) out[r][c] = rk_combine<A>(out[r][c], u0v[r][c], rka, rkb);
                     }
-                    u0p += f.plane;
                 }
                 store_plane(out, k, o);
             }
@@ -902,6 +946,9 @@ static T tma_dispatch(int R, int rows, int gb, F &&f, T fallback) {
         case (2 * 4 + 1) * 2: return f.template run<2, 1, 16>();
         case (2 * 4 + 2) * 2: return f.template run<2, 2, 16>();
         case (4 * 4 + 1) * 2: return f.template run<4, 1, 16>();
+        case (4 * 4 + 2) * 2:  // the 25-point stencil, two rows per thread: FP32 and FP64 storage
+            if constexpr (kHasWide<S> && !std::is_same<S, long long>::value) return f.template run<4, 2, 16>();
+            break;
         case (1 * 4 + 1) * 2 + 1:
             if constexpr (kHasWide<S>) return f.template run<1, 1, 32>();
             break;
