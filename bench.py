@@ -450,11 +450,14 @@ def manybox_line(mf, torch, flush, args, hbm):
     torch.cuda.empty_cache()
     dt = synth.dt_for(cfg)
     out = {}
-    runs = [(t, "f32", 0) for t in cfg["targets"]] + [(t, "f64fixed", mf.MF_FIXED_DIFF) for t in (4096, 32768)]
-    for target, dtype, flags in runs:
+    # (boxes, storage, flags, regions of at most this many cells per side or 0 for one FArrayBox
+    # per box)
+    runs = ([(t, "f32", 0, 0) for t in cfg["targets"]] + [(t, "f64fixed", mf.MF_FIXED_DIFF, 0) for t in (4096, 32768)]
+            + [(t, "f32", 0, 128) for t in (4096, 32768)] + [(32768, "f64fixed", mf.MF_FIXED_DIFF, 128)])
+    for target, dtype, flags, max_region in runs:
         boxes = synth.uneven_boxes(N, target)
         g = mf.MultiFab([0, 0, 0], [N - 1] * 3, boxes=boxes, ncomp=C, ngrow=cfg["ngrow"],
-                        dtype="f64" if flags else dtype)
+                        dtype="f64" if flags else dtype, max_region=max_region or None)
         g.from_host(dense)
         for _ in range(max(1, args.warmup)):
             g.advance(R, [1.0] * C, dt, n, flags)
@@ -467,17 +470,21 @@ def manybox_line(mf, torch, flush, args, hbm):
             ev[k][1].record(g.stream)
         torch.cuda.synchronize()
         ms = sum(a.elapsed_time(b) for a, b in ev) / K
-        step_bytes = manybox_step_bytes(8 if flags else 4, C, boxes, R)
-        out["%d_%s" % (target, dtype)] = {
+        # compulsory bytes of the storage: the regions' faces for a regional level
+        step_bytes = manybox_step_bytes(8 if flags else 4, C, g.regions, R)
+        key = "%d_%s%s" % (target, dtype, "_regional" if max_region else "")
+        out[key] = {
             "value": N ** 3 * n / (ms * 1e-3), "unit": UNIT, "ms_per_bench_step": ms,
             "cell_comp_updates_per_s": N ** 3 * C * n / (ms * 1e-3), "boxes": target, "dtype": dtype,
-            "step_bytes": step_bytes, "step_frac": step_bytes * n / (ms * 1e-3) / 1e9 / hbm,
+            "regions": mf.mf_nregions(g.h), "step_bytes": step_bytes,
+            "step_frac": step_bytes * n / (ms * 1e-3) / 1e9 / hbm,
             "launches_per_bench_step": mf.mf_launch_count(g.h), "schedule": mf.mf_get_schedule(g.h)}
         del g
         torch.cuda.empty_cache()
     out["workload"] = ("manybox512_c2: periodic 512^3, 2 components, 4096-32768 uneven boxes of 8^3-32^3, "
                        "ngrow 2, 13-point stencil, FP32 and FP64-accurate fixed-point steps, %d steps per bench "
-                       "step" % n)
+                       "step; *_regional: the same boxes stored in regions of at most 128^3 (mf_create_regional)"
+                       % n)
     return out
 
 

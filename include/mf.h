@@ -88,6 +88,37 @@ int mf_create(mf_t **out, const int domain_lo[3], const int domain_hi[3], int ma
 int mf_create_boxes(mf_t **out, const int domain_lo[3], const int domain_hi[3], const int *boxes,
                     int nboxes, int ncomp, int ngrow, int dtype);
 
+/*
+ * mf_create_regional -- a level from a box list, as mf_create_boxes, stored in regions.
+ * Sec. 2 (TiDA, Fig. 2): a grid's data may be allocated as several regions, each one contiguous
+ * block, and the tiles of the iteration space are logical, independent of that layout.  Here
+ * the level's boxes are grouped into regions, rectangles that their boxes cover exactly with
+ * sides of at most max_region cells (1 <= max_region <= 240), found by cutting the boxes'
+ * bounding box along planes that cross no box (mf_box_regions); the FArrayBoxes, their ghost
+ * cells and FillBoundary belong to the regions, and the boxes stay the level's cells and
+ * logical tiles.  A level of many small boxes then keeps ghost cells only around its regions:
+ * no fill between the boxes of one region.  Every computation gives the same bits as the
+ * same boxes stored one FArrayBox each.
+ * mf_nboxes, mf_get_boxes and mf_copy_fab_to_host / _from_host address the boxes as given:
+ * the box grown by ngrow is read from its region, and only the box's own cells are written (its
+ * ghost frame there is other boxes' cells or the region's ghost cells); mf_fb_regions, mf_get_fb_regions, mf_interp_cells,
+ * mf_avgdown_cells, mf_reflux_faces, mf_step_bytes and mf_bytes describe the regions' storage.
+ */
+int mf_create_regional(mf_t **out, const int domain_lo[3], const int domain_hi[3], const int *boxes,
+                       int nboxes, int ncomp, int ngrow, int dtype, int max_region);
+
+/* The regions mf_create_regional makes from a box list (host only; boxes as for
+ * mf_create_boxes, assumed disjoint): returns their number, writes region_of[i], the region
+ * of box i, and, when regions_out is not NULL (room for nboxes * 6 ints), the regions as
+ * {lo[3], hi[3]}.  A region is either a rectangle its boxes cover exactly, every side at most
+ * max_region, or a single box that no cut separates from the others. */
+int mf_box_regions(const int *boxes, int nboxes, int max_region, int *regions_out, int *region_of);
+/* The storage of a level: its FArrayBoxes (the regions of a regional level, the boxes
+ * otherwise) as {lo[3], hi[3]} into regions_out (room for mf_nregions * 6 ints), and the
+ * FArrayBox of each box into region_of (room for mf_nboxes ints); either may be NULL. */
+int mf_nregions(const mf_t *mf);
+int mf_get_regions(const mf_t *mf, int *regions_out, int *region_of);
+
 /* Releases the handle (metadata, device work lists, graphs), after waiting for the work it queued
  * on its attached stream.  The field memory stays the caller's.  Sec. 3.1 gives a MultiFab no
  * explicit lifetime call; this is the end of the handle that mf_create made.  A NULL handle is
@@ -165,7 +196,9 @@ int mf_get_schedule(const mf_t *mf, int out[7]);
 int mf_copy_from_host(mf_t *mf, const double *dense);
 int mf_copy_to_host(mf_t *mf, double *dense);
 
-/* One FArrayBox including ghosts, (ncomp, nz+2g, ny+2g, nx+2g) doubles, current time level. */
+/* One box including ghosts, (ncomp, nz+2g, ny+2g, nx+2g) doubles, current time level: the
+ * box's FArrayBox (Sec. 3.1), or on a regional level the box's window of its region (see
+ * mf_create_regional: there _from_host writes the box's own cells only). */
 int mf_copy_fab_to_host(mf_t *mf, int box, double *out);
 int mf_copy_fab_from_host(mf_t *mf, int box, const double *in);
 

@@ -33,7 +33,8 @@ EXPORTS = [
     "mf_advance", "mf_amr_advance", "mf_sum", "mf_step_bytes", "mf_current", "mf_last_error", "mf_set_timing",
     "mf_phase_ms", "mf_set_kernel", "mf_sum_strided_noalloc", "mf_get_schedule", "mf_launch_count",
     "mf_fp64_fma_rate", "mf_set_schedule", "mf_reduce", "mf_stage_bytes", "mf_attach_stage",
-    "mf_rk3_advance", "mf_interp_cells", "mf_reflux_faces", "mf_avgdown_cells",
+    "mf_rk3_advance", "mf_interp_cells", "mf_reflux_faces", "mf_avgdown_cells", "mf_create_regional",
+    "mf_box_regions", "mf_nregions", "mf_get_regions",
 ]
 
 
@@ -94,6 +95,10 @@ def _load():
         "mf_reflux_faces": (LL, [P, P, I, ctypes.POINTER(LL)]),
         "mf_avgdown_cells": (LL, [P, P, I, ctypes.POINTER(LL)]),
         "mf_sum_strided_noalloc": (I, [P, I, I, I, I, LL, LL, ctypes.POINTER(D), P]),
+        "mf_create_regional": (I, [PP, P, P, P, I, I, I, I, I]),
+        "mf_box_regions": (I, [P, I, I, P, P]),
+        "mf_nregions": (I, [P]),
+        "mf_get_regions": (I, [P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -143,6 +148,36 @@ def mf_create_boxes(domain_lo, domain_hi, boxes, ncomp, ngrow, dtype):
     _check(lib.mf_create_boxes(ctypes.byref(h), _ptr(lo), _ptr(hi), _ptr(b), b.shape[0], int(ncomp), int(ngrow),
                                _dtype_code(dtype)))
     return h
+
+
+def mf_create_regional(domain_lo, domain_hi, boxes, ncomp, ngrow, dtype, max_region):
+    h = ctypes.c_void_p()
+    lo, hi = _i3(domain_lo), _i3(domain_hi)
+    b = np.ascontiguousarray(np.asarray(boxes, dtype=np.int32).reshape(-1, 6))
+    _check(lib.mf_create_regional(ctypes.byref(h), _ptr(lo), _ptr(hi), _ptr(b), b.shape[0], int(ncomp), int(ngrow),
+                                  _dtype_code(dtype), int(max_region)))
+    return h
+
+
+def mf_box_regions(boxes, max_region):
+    """(regions (n, 6) int32, region of each box) that mf_create_regional makes from a box list."""
+    b = np.ascontiguousarray(np.asarray(boxes, dtype=np.int32).reshape(-1, 6))
+    regs = np.zeros((b.shape[0], 6), dtype=np.int32)
+    of = np.zeros(b.shape[0], dtype=np.int32)
+    n = _check(lib.mf_box_regions(_ptr(b), b.shape[0], int(max_region), _ptr(regs), _ptr(of)))
+    return regs[:n].copy(), of
+
+
+def mf_nregions(h):
+    return _check(lib.mf_nregions(h))
+
+
+def mf_get_regions(h):
+    """(regions (n, 6) int32, FArrayBox of each box) of a level's storage."""
+    regs = np.zeros((mf_nregions(h), 6), dtype=np.int32)
+    of = np.zeros(mf_nboxes(h), dtype=np.int32)
+    _check(lib.mf_get_regions(h, _ptr(regs), _ptr(of)))
+    return regs, of
 
 
 def mf_destroy(h):
@@ -357,14 +392,34 @@ def mf_last_error():
 
 # ------------------------------------------------------------------ convenience: torch-backed level
 
+def _chop(domain_lo, domain_hi, mgs):
+    """The boxes mf_create makes: the domain chopped into max_grid_size blocks, x fastest."""
+    lo, hi = _i3(domain_lo), _i3(domain_hi)
+    n = (hi - lo + mgs) // mgs
+    out = []
+    for bz in range(n[2]):
+        for by in range(n[1]):
+            for bx in range(n[0]):
+                a = lo + np.array([bx, by, bz]) * mgs
+                out.append(list(a) + list(np.minimum(a + mgs - 1, hi)))
+    return np.asarray(out, dtype=np.int32)
+
+
 class MultiFab:
     """One level on the current CUDA device: a libmf handle plus its torch-allocated field
     memory, attached to the current torch stream."""
 
     def __init__(self, domain_lo, domain_hi, max_grid_size=None, boxes=None, ncomp=1, ngrow=1, dtype="f64",
-                 stream=None):
+                 stream=None, max_region=None):
+        """max_region: store the boxes in regions of at most that many cells per side
+        (mf_create_regional); boxes=None with max_region chops the domain by max_grid_size
+        first."""
         import torch
-        if boxes is None:
+        if max_region:
+            if boxes is None:
+                boxes = _chop(domain_lo, domain_hi, max_grid_size)
+            self.h = mf_create_regional(domain_lo, domain_hi, boxes, ncomp, ngrow, dtype, max_region)
+        elif boxes is None:
             self.h = mf_create(domain_lo, domain_hi, max_grid_size, ncomp, ngrow, dtype)
         else:
             self.h = mf_create_boxes(domain_lo, domain_hi, boxes, ncomp, ngrow, dtype)
@@ -383,6 +438,10 @@ class MultiFab:
     @property
     def boxes(self):
         return mf_get_boxes(self.h)
+
+    @property
+    def regions(self):
+        return mf_get_regions(self.h)[0]
 
     def fab_shape(self, b):
         B = self.boxes[b]

@@ -252,7 +252,13 @@ struct AvgPlan {
 
 struct mf {
     Box domain;
-    std::vector<Box> boxes;
+    std::vector<Box> boxes;  // the FArrayBoxes: the boxes, or the regions of a regional level
+    // Regional storage (Sec. 2, Fig. 2): the level's data live in regions, each a rectangle that
+    // a group of its boxes covers exactly, and the boxes are logical tiles of the regions: they
+    // keep defining the level's cells but no longer their own allocations or ghost cells.
+    bool regional = false;
+    std::vector<Box> lboxes;      // the boxes of a regional level, in the order given
+    std::vector<int> lbox_region;  // the region holding each of them
     int ncomp = 1, ngrow = 0, dtype = F64, esize = 8;
     // layout
     std::vector<FabInfo> fabs;     // level slot 0
@@ -607,16 +613,83 @@ extern "C" int mf_create(mf_t **out, const int domain_lo[3], const int domain_hi
     return 0;
 }
 
-extern "C" int mf_create_boxes(mf_t **out, const int domain_lo[3], const int domain_hi[3], const int *boxes,
-                               int nboxes, int ncomp, int ngrow, int dtype) {
-    if (!out) return fail(MF_EINVAL, "null out");
-    *out = nullptr;
-    int rc = check_create(domain_lo, domain_hi, ncomp, ngrow, dtype);
-    if (rc) return rc;
+// Regions of a list of disjoint boxes (regional storage): rectangles, each covered exactly by
+// the boxes it holds, with every side at most max_ext cells.  Guillotine recursion over the
+// boxes' bounding box: a rectangle that its boxes cover and that fits becomes a region;
+// otherwise (too large, or with holes) it is cut by the plane that crosses no box and lies
+// closest to the middle of the longest side that has one, and each part (shrunk to its boxes'
+// bounding box) is treated the same way.  Boxes that no such plane separates each become a
+// region of their own.
+// region_of[i]: the region of box i.
+static void build_regions(const std::vector<Box> &bx, int max_ext, std::vector<Box> &regions,
+                          std::vector<int> &region_of) {
+    regions.clear();
+    region_of.assign(bx.size(), -1);
+    std::vector<int> all(bx.size());
+    for (size_t i = 0; i < bx.size(); ++i) all[i] = (int)i;
+    auto bbox = [&](const std::vector<int> &ids) {
+        Box r = bx[ids[0]];
+        for (int i : ids)
+            for (int d = 0; d < 3; ++d) { r.lo[d] = std::min(r.lo[d], bx[i].lo[d]); r.hi[d] = std::max(r.hi[d], bx[i].hi[d]); }
+        return r;
+    };
+    auto emit = [&](const Box &r, const std::vector<int> &ids) {
+        for (int i : ids) region_of[i] = (int)regions.size();
+        regions.push_back(r);
+    };
+    // explicit stack: (ids) per pending rectangle
+    std::vector<std::vector<int>> stack;
+    stack.push_back(std::move(all));
+    while (!stack.empty()) {
+        std::vector<int> ids = std::move(stack.back());
+        stack.pop_back();
+        const Box r = bbox(ids);
+        long long vol = 0;
+        for (int i : ids) vol += bx[i].cells();
+        const bool covered = vol == r.cells();
+        const bool fits = r.len(0) <= max_ext && r.len(1) <= max_ext && r.len(2) <= max_ext;
+        if (covered && fits) {  // (a single box is covered by itself)
+            emit(r, ids);
+            continue;
+        }
+        // the cut: a plane x_d = p (between cells p - 1 and p) that no box crosses
+        int best_d = -1, best_p = 0;
+        int dims[3] = {0, 1, 2};
+        std::sort(dims, dims + 3, [&](int a, int b) { return r.len(a) > r.len(b) || (r.len(a) == r.len(b) && a < b); });
+        for (int d : dims) {
+            std::vector<std::pair<int, int>> iv;  // crossed cut positions (lo, hi]
+            iv.reserve(ids.size());
+            for (int i : ids) iv.push_back({bx[i].lo[d], bx[i].hi[d]});
+            std::sort(iv.begin(), iv.end());
+            const double mid = r.lo[d] + r.len(d) * 0.5;
+            int reach = iv[0].second;  // positions <= reach are crossed by a box seen so far
+            double bestdist = 1e30;
+            for (size_t k = 1; k < iv.size(); ++k) {
+                const int p = iv[k].first;  // a box starts here: a cut if no earlier box crosses p
+                if (p > reach && std::fabs(p - mid) < bestdist) {
+                    bestdist = std::fabs(p - mid);
+                    best_p = p;
+                    best_d = d;
+                }
+                reach = std::max(reach, iv[k].second);
+            }
+            if (best_d >= 0) break;
+        }
+        if (best_d < 0) {
+            for (int i : ids) emit(bx[i], {i});
+            continue;
+        }
+        std::vector<int> a, b;
+        for (int i : ids) (bx[i].hi[best_d] < best_p ? a : b).push_back(i);
+        stack.push_back(std::move(b));
+        stack.push_back(std::move(a));
+    }
+}
+
+static int read_boxes(const int *boxes, int nboxes, const int domain_lo[3], const int domain_hi[3],
+                      std::vector<Box> &out) {
     if (nboxes < 1 || !boxes) return fail(MF_EINVAL, "need at least one box");
-    std::unique_ptr<mf_t> m(new (std::nothrow) mf_t());
-    if (!m) return fail(MF_ENOMEM, "host allocation");
-    for (int d = 0; d < 3; ++d) { m->domain.lo[d] = domain_lo[d]; m->domain.hi[d] = domain_hi[d]; }
+    out.clear();
     for (int i = 0; i < nboxes; ++i) {
         Box b;
         for (int d = 0; d < 3; ++d) { b.lo[d] = boxes[6 * i + d]; b.hi[d] = boxes[6 * i + 3 + d]; }
@@ -625,17 +698,37 @@ extern "C" int mf_create_boxes(mf_t **out, const int domain_lo[3], const int dom
             if (b.lo[d] < domain_lo[d] || b.hi[d] > domain_hi[d]) return fail(MF_EINVAL, "box %d outside the domain", i);
             if (b.len(d) > 32767) return fail(MF_EINVAL, "box side above 32767");
         }
-        m->boxes.push_back(b);
+        out.push_back(b);
     }
     // overlap check through the bin hash
+    Box dom;
+    for (int d = 0; d < 3; ++d) { dom.lo[d] = domain_lo[d]; dom.hi[d] = domain_hi[d]; }
     BinHash hash;
-    hash.build(m->domain, m->boxes);
+    hash.build(dom, out);
     std::vector<int> cand, stamp(nboxes, -1);
     for (int i = 0; i < nboxes; ++i) {
-        hash.query(m->boxes[i], cand, stamp, i);
+        hash.query(out[i], cand, stamp, i);
         for (int a : cand)
-            if (a != i && !intersect(m->boxes[a], m->boxes[i]).empty())
+            if (a != i && !intersect(out[a], out[i]).empty())
                 return fail(MF_EINVAL, "boxes %d and %d overlap", std::min(a, i), std::max(a, i));
+    }
+    return 0;
+}
+
+static int create_from_boxes(mf_t **out, const int domain_lo[3], const int domain_hi[3], const int *boxes,
+                             int nboxes, int ncomp, int ngrow, int dtype, int max_region) {
+    if (!out) return fail(MF_EINVAL, "null out");
+    *out = nullptr;
+    int rc = check_create(domain_lo, domain_hi, ncomp, ngrow, dtype);
+    if (rc) return rc;
+    std::unique_ptr<mf_t> m(new (std::nothrow) mf_t());
+    if (!m) return fail(MF_ENOMEM, "host allocation");
+    for (int d = 0; d < 3; ++d) { m->domain.lo[d] = domain_lo[d]; m->domain.hi[d] = domain_hi[d]; }
+    if ((rc = read_boxes(boxes, nboxes, domain_lo, domain_hi, m->boxes))) return rc;
+    if (max_region > 0) {
+        m->regional = true;
+        m->lboxes = m->boxes;
+        build_regions(m->lboxes, max_region, m->boxes, m->lbox_region);
     }
     m->ncomp = ncomp;
     m->ngrow = ngrow;
@@ -647,14 +740,58 @@ extern "C" int mf_create_boxes(mf_t **out, const int domain_lo[3], const int dom
     return 0;
 }
 
+extern "C" int mf_create_boxes(mf_t **out, const int domain_lo[3], const int domain_hi[3], const int *boxes,
+                               int nboxes, int ncomp, int ngrow, int dtype) {
+    return create_from_boxes(out, domain_lo, domain_hi, boxes, nboxes, ncomp, ngrow, dtype, 0);
+}
+
+extern "C" int mf_create_regional(mf_t **out, const int domain_lo[3], const int domain_hi[3], const int *boxes,
+                                  int nboxes, int ncomp, int ngrow, int dtype, int max_region) {
+    if (max_region < 1 || max_region > 240)
+        return fail(MF_EINVAL, "max_region must be in [1, 240] (a region row, ghosts included, fits one TMA box)");
+    return create_from_boxes(out, domain_lo, domain_hi, boxes, nboxes, ncomp, ngrow, dtype, max_region);
+}
+
+extern "C" int mf_box_regions(const int *boxes, int nboxes, int max_region, int *regions_out, int *region_of_out) {
+    if (!boxes || nboxes < 1 || max_region < 1 || !region_of_out) return fail(MF_EINVAL, "bad argument");
+    std::vector<Box> bx(nboxes), rg;
+    std::vector<int> of;
+    for (int i = 0; i < nboxes; ++i)
+        for (int d = 0; d < 3; ++d) { bx[i].lo[d] = boxes[6 * i + d]; bx[i].hi[d] = boxes[6 * i + 3 + d]; }
+    build_regions(bx, max_region, rg, of);
+    for (int i = 0; i < nboxes; ++i) region_of_out[i] = of[i];
+    if (regions_out)
+        for (size_t r = 0; r < rg.size(); ++r)
+            for (int d = 0; d < 3; ++d) { regions_out[6 * r + d] = rg[r].lo[d]; regions_out[6 * r + 3 + d] = rg[r].hi[d]; }
+    return (int)rg.size();
+}
+
 extern "C" void mf_destroy(mf_t *m) { delete m; }
 
-extern "C" int mf_nboxes(const mf_t *m) { return m ? (int)m->boxes.size() : fail(MF_EINVAL, "null handle"); }
+static const std::vector<Box> &user_boxes(const mf_t *m) { return m->regional ? m->lboxes : m->boxes; }
+
+extern "C" int mf_nboxes(const mf_t *m) { return m ? (int)user_boxes(m).size() : fail(MF_EINVAL, "null handle"); }
 
 extern "C" int mf_get_boxes(const mf_t *m, int *out) {
     if (!m || !out) return fail(MF_EINVAL, "null argument");
-    for (size_t i = 0; i < m->boxes.size(); ++i)
-        for (int d = 0; d < 3; ++d) { out[6 * i + d] = m->boxes[i].lo[d]; out[6 * i + 3 + d] = m->boxes[i].hi[d]; }
+    const auto &bx = user_boxes(m);
+    for (size_t i = 0; i < bx.size(); ++i)
+        for (int d = 0; d < 3; ++d) { out[6 * i + d] = bx[i].lo[d]; out[6 * i + 3 + d] = bx[i].hi[d]; }
+    return 0;
+}
+
+extern "C" int mf_nregions(const mf_t *m) { return m ? (int)m->boxes.size() : fail(MF_EINVAL, "null handle"); }
+
+extern "C" int mf_get_regions(const mf_t *m, int *regions_out, int *region_of_out) {
+    if (!m) return fail(MF_EINVAL, "null handle");
+    if (regions_out)
+        for (size_t i = 0; i < m->boxes.size(); ++i)
+            for (int d = 0; d < 3; ++d) {
+                regions_out[6 * i + d] = m->boxes[i].lo[d];
+                regions_out[6 * i + 3 + d] = m->boxes[i].hi[d];
+            }
+    if (region_of_out)
+        for (size_t i = 0; i < user_boxes(m).size(); ++i) region_of_out[i] = m->regional ? m->lbox_region[i] : (int)i;
     return 0;
 }
 
@@ -897,23 +1034,33 @@ static uint16_t double_to_bf16(double d) {
     return (uint16_t)(u >> 16);
 }
 
-static void fab_shape(const mf_t *m, int b, long long sh[3]) {
-    for (int d = 0; d < 3; ++d) sh[d] = m->fabs[b].n[d] + 2 * m->ngrow;
+// The window of box `box` (a logical box of a regional level) in its FArrayBox: the FArrayBox,
+// the box's lower corner relative to the FArrayBox's valid corner, and the grown box's shape.
+static int fab_window(const mf_t *m, int box, int *fab, int off[3], long long sh[3]) {
+    if (box < 0 || box >= (int)user_boxes(m).size()) return fail(MF_EINVAL, "bad box");
+    *fab = m->regional ? m->lbox_region[box] : box;
+    const Box &b = user_boxes(m)[box], &r = m->boxes[*fab];
+    for (int d = 0; d < 3; ++d) {
+        off[d] = b.lo[d] - r.lo[d];
+        sh[d] = b.len(d) + 2 * m->ngrow;
+    }
+    return 0;
 }
 
 extern "C" int mf_copy_fab_to_host(mf_t *m, int box, double *out) {
     int rc = need_attached(m);
     if (rc) return rc;
-    if (box < 0 || box >= (int)m->boxes.size() || !out) return fail(MF_EINVAL, "bad box or null out");
-    const FabInfo &f = m->fabs[box];
+    int fab, off[3];
+    long long sh[3];
+    if (!out) return fail(MF_EINVAL, "null out");
+    if ((rc = fab_window(m, box, &fab, off, sh))) return rc;
+    const FabInfo &f = m->fabs[fab];
     const size_t n = (size_t)f.cstride * m->ncomp;
     std::vector<char> raw(n * m->esize);
-    CU(cudaMemcpyAsync(raw.data(), (char *)m->level_ptr(m->cur) + (size_t)m->fab_start[box] * m->esize,
+    CU(cudaMemcpyAsync(raw.data(), (char *)m->level_ptr(m->cur) + (size_t)m->fab_start[fab] * m->esize,
                        raw.size(), cudaMemcpyDeviceToHost, m->stream));
     CU(cudaStreamSynchronize(m->stream));
-    long long sh[3];
-    fab_shape(m, box, sh);
-    const long long org_local = f.org - m->fab_start[box];
+    const long long org_local = f.org - m->fab_start[fab] + off[2] * f.plane + (long long)off[1] * f.px + off[0];
     const int g = m->ngrow;
     size_t q = 0;
     for (int c = 0; c < m->ncomp; ++c)
@@ -934,16 +1081,17 @@ extern "C" int mf_copy_fab_to_host(mf_t *m, int box, double *out) {
 extern "C" int mf_copy_fab_from_host(mf_t *m, int box, const double *in) {
     int rc = need_attached(m);
     if (rc) return rc;
-    if (box < 0 || box >= (int)m->boxes.size() || !in) return fail(MF_EINVAL, "bad box or null in");
-    const FabInfo &f = m->fabs[box];
+    int fab, off[3];
+    long long sh[3];
+    if (!in) return fail(MF_EINVAL, "null in");
+    if ((rc = fab_window(m, box, &fab, off, sh))) return rc;
+    const FabInfo &f = m->fabs[fab];
     const size_t n = (size_t)f.cstride * m->ncomp;
     std::vector<char> raw(n * m->esize);
-    char *dev = (char *)m->level_ptr(m->cur) + (size_t)m->fab_start[box] * m->esize;
+    char *dev = (char *)m->level_ptr(m->cur) + (size_t)m->fab_start[fab] * m->esize;
     CU(cudaMemcpyAsync(raw.data(), dev, raw.size(), cudaMemcpyDeviceToHost, m->stream));
     CU(cudaStreamSynchronize(m->stream));
-    long long sh[3];
-    fab_shape(m, box, sh);
-    const long long org_local = f.org - m->fab_start[box];
+    const long long org_local = f.org - m->fab_start[fab] + off[2] * f.plane + (long long)off[1] * f.px + off[0];
     const int g = m->ngrow;
     size_t q = 0;
     for (int c = 0; c < m->ncomp; ++c)
@@ -953,6 +1101,10 @@ extern "C" int mf_copy_fab_from_host(mf_t *m, int box, const double *in) {
                     const long long at = org_local + c * f.cstride + (z - g) * f.plane + (y - g) * f.px + (x - g);
                     char *p = raw.data() + at * m->esize;
                     const double v = in[q++];
+                    // in a region the box's ghost frame is other boxes' cells or the region's ghosts:
+                    // only the box's own cells are written
+                    if (m->regional && (x < g || y < g || z < g || x >= sh[0] - g || y >= sh[1] - g || z >= sh[2] - g))
+                        continue;
                     if (m->dtype == F64) memcpy(p, &v, 8);
                     else if (m->dtype == F32) { float t = (float)v; memcpy(p, &t, 4); }
                     else { uint16_t t = double_to_bf16(v); memcpy(p, &t, 2); }

@@ -218,8 +218,8 @@ __global__ void __launch_bounds__(TmaThreads<S, R, A, ROWS, GB>::value) k_stenci
     constexpr int VX = V::n;  // cells per group: one GB-byte vector of a row
     // FP32 arithmetic at radius 1: pairs of cells through the packed f32x2 instructions
     constexpr bool kPair = std::is_same<A, float>::value && R == 1 && VX % 2 == 0;
-    // FP32 arithmetic at radius 2 and 4: the face fluxes and the update of pairs of cells through
-    // the packed instructions (face_flux2), the same operations in the same order as the scalar code
+    // FP32 arithmetic at radius 2 and 4: the y and z face fluxes and the update of pairs of cells
+    // through the packed instructions (face_flux2), the operations and order of the scalar code
     constexpr bool kPairR = std::is_same<A, float>::value && R > 1 && VX % 2 == 0;
     // exact fixed-point differences, FP64 update (fixed_diff.cuh)
     constexpr bool kFix = std::is_same<A, FixA>::value;
@@ -805,19 +805,12 @@ __global__ void __launch_bounds__(TmaThreads<S, R, A, ROWS, GB>::value) k_stenci
                         for (int c = 0; c < VX; ++c)
                             if (cov & (1u << c)) wx[R + c] = ld_smem<S, A>(cp + cob + r * p.strip_w + c);
                     }
-                    A fx[VX + 1];  // x-face fluxes: fx[c] is the face left of cell c
-                    if constexpr (kPairR) {
+                    // x-face fluxes: fx[c] is the face left of cell c (scalar: the packed form would
+                    // pair neighbouring window values, which sit in unaligned register pairs, and
+                    // measured slower)
+                    A fx[VX + 1];
 #pragma unroll
-                        for (int c = 0; c < VX; c += 2) {
-                            const F2 fxc = face_flux2<R>(wx, wx + 1, c + R - 1);
-                            fx[c] = fxc.x;
-                            fx[c + 1] = fxc.y;
-                        }
-                        fx[VX] = face_flux<A, R>(wx, VX + R - 1);
-                    } else {
-#pragma unroll
-                        for (int c = 0; c <= VX; ++c) fx[c] = face_flux<A, R>(wx, c + R - 1);
-                    }
+                    for (int c = 0; c <= VX; ++c) fx[c] = face_flux<A, R>(wx, c + R - 1);
                     if constexpr (kPair) {
                         // the same operations as update_cell_f in the same order, two cells at a time:
                         // ((fxp - fxm) + (fyp - fym)) + (fzp - fzm), then u + lam * div
