@@ -602,7 +602,8 @@ def amr_line(mf, torch, flush, args, hbm):
             "schedule": {"coarse": mf.mf_get_schedule(gc.h), "fine": mf.mf_get_schedule(gf.h)},
             "workload": "amr2lev256_sphere: coarse 256^3 (64 boxes of 64^3) + %d fine boxes (%d cells) at ratio 2, "
                         "2 substeps, refluxing, FP32, %d coarse steps per bench step" % (len(fboxes), Vf, n),
-            "launches_per_bench_step": mf.mf_launch_count(gc.h)}
+            "launches_per_bench_step": mf.mf_launch_count(gc.h),
+            "launches_per_coarse_step": sum(mf.mf_launch_count(gc.h).values()) / n}
 
 
 def run_ours(args, cfg, ws, rank, local):

@@ -2667,6 +2667,12 @@ extern "C" int mf_amr_advance(mf_t *crse, mf_t *fine, const mf_stencil *st, doub
                 b = fail(MF_ECUDA, "fill launch failed");
             return b;
         };
+        // Independent work shares launches (launch_fill_interp, launch_fill_cflux,
+        // launch_avg_reflux): per coarse step a coarse fill, the coarse stencil, the fill of the
+        // new coarse level with the coarse face fluxes of the old one, then per substep the fine
+        // fill with the interpolation, the fine face fluxes and the fine stencil, and last the
+        // average-down with the flux correction.
+        auto pair_kind = [](size_t a, size_t b, int ka, int kb) { return b ? kb : ka; };
         for (int step = 0; step < ncrse_steps && !body; ++step) {
             // the coarse ghosts read in this step: the stencil's faces (or, with the ghost push,
             // what the push does not deliver or the last average-down and correction made
@@ -2674,23 +2680,34 @@ extern "C" int mf_amr_advance(mf_t *crse, mf_t *fine, const mf_stencil *st, doub
             const int nface = rp ? (int)rp->faces.size() : 0;
             if (step == 0 || !cpush) body = fill(crse, c, af->d_first, af->t_first.size());
             else body = fill(crse, c, af->d_next, af->t_next.size());
-            if (!body && rp && !(body = log.before(2, nface > 0)))  // coarse face fluxes at the interface
-                body = launch_cf_coarse_flux(crse->dtype, R, crse->level_ptr(c), (const CFace *)rp->d_faces.p, nface,
-                                             crse->ncomp, wc, (double *)rp->d_regc.p, s) == cudaSuccess
-                           ? 0
-                           : fail(MF_ECUDA, "flux register launch failed");
             if (!body && !(body = log.before(1))) body = enqueue_stencil(crse, c, R, fp64diff, lam_c, s, cpush);
-            if (!body) body = fill(crse, 1 - c, af->d_post, af->t_post.size());  // read by the interpolation
+            // the new level's ghosts that the interpolation reads, and the coarse face fluxes at
+            // the interface from the old level (which the stencil only read)
+            const size_t npost = af->t_post.size();
+            if (!body && !(body = log.before(pair_kind(npost, (size_t)nface, 0, 2), npost + nface > 0)))
+                body = launch_fill_cflux(crse->dtype, R, level_ptrs(crse, 1 - c), (const FbTask *)af->d_post.p,
+                                         (int)npost, crse->level_ptr(c), rp ? (const CFace *)rp->d_faces.p : nullptr,
+                                         nface, crse->ncomp, wc, rp ? (double *)rp->d_regc.p : nullptr,
+                                         s) == cudaSuccess
+                           ? 0
+                           : fail(MF_ECUDA, "coarse fill / flux register launch failed");
             for (int sub = 0; sub < nsub && !body; ++sub) {
                 // the fine level steps like a single level: a face fill first, then the push
                 // and the residual fill; the interpolation writes the coarse-fine ghosts
-                if ((step == 0 && sub == 0) || !fpush) {
-                    if (!(body = log.before(0, fill_step_tasks(fine) > 0))) body = enqueue_fill_step(fine, f, s);
-                } else {
-                    body = fill(fine, f, fine->d_fbtasks_res, fine->fbtasks_res.size());
-                }
-                if (!body && !(body = log.before(2, !ip->runs.empty())))
-                    body = enqueue_interp(fine, f, crse, c, crse, 1 - c, ip, ratio, (double)sub / (double)nsub, s);
+                const bool face = (step == 0 && sub == 0) || !fpush;
+                const bool strips = fine->use_tma && fine->tma_ok && fine->tma_strips;
+                const DevBuf &ft = face ? (strips ? fine->d_fbtasks_adv : fine->d_fbtasks) : fine->d_fbtasks_res;
+                const size_t nft = face ? fill_step_tasks(fine) : fine->fbtasks_res.size();
+                const InterpArgs ia{fine->level_ptr(f), crse->level_ptr(c), crse->level_ptr(1 - c),
+                                    (const InterpRun *)ip->d_runs.p, (const int *)ip->cells.d_start.p,
+                                    (const int *)ip->cells.d_wfirst.p, (int)ip->runs.size(), ip->cells.ncells,
+                                    fine->ncomp, ratio, (double)sub / (double)nsub};
+                const size_t nip = ip->runs.empty() ? 0 : (size_t)ip->cells.ncells;
+                if (!(body = log.before(pair_kind(nft, nip, 0, 2), nft + nip > 0)))
+                    body = launch_fill_interp(fine->dtype, level_ptrs(fine, f), (const FbTask *)ft.p, (int)nft, ia,
+                                              s) == cudaSuccess
+                               ? 0
+                               : fail(MF_ECUDA, "fine fill / interpolation launch failed");
                 if (!body && rp && !(body = log.before(2, nface > 0)))  // fine face fluxes, this substep
                     body = launch_cf_fine_flux(fine->dtype, R, fine->level_ptr(f), (const CFace *)rp->d_faces.p,
                                                (const FFace *)rp->d_ff.p, nface, ratio * ratio, fine->ncomp, wf,
@@ -2700,14 +2717,19 @@ extern "C" int mf_amr_advance(mf_t *crse, mf_t *fine, const mf_stencil *st, doub
                 if (!body && !(body = log.before(1))) body = enqueue_stencil(fine, f, R, fp64diff, lam_f, s, fpush);
                 f = 1 - f;
             }
-            if (!body && !(body = log.before(3, !ap->regs.empty())))
-                body = enqueue_avg(fine, f, crse, 1 - c, ap, ratio, s);
-            if (!body && rp && !(body = log.before(3, !rp->cells.empty())))  // the flux correction
-                body = launch_reflux_apply(crse->dtype, crse->level_ptr(1 - c), (const CCell *)rp->d_cells.p,
-                                           (int)rp->cells.size(), (const CFace *)rp->d_faces.p, crse->ncomp,
-                                           (const double *)rp->d_regc.p, (const double *)rp->d_regf.p, s) == cudaSuccess
+            // the average-down writes the covered coarse cells, the flux correction the uncovered
+            // ones next to the interface
+            const AvgArgs aa{fine->level_ptr(f), crse->level_ptr(1 - c), (const AvgRegion *)ap->d_regs.p,
+                             (const int *)ap->cells.d_start.p, (const int *)ap->cells.d_wfirst.p, (int)ap->regs.size(),
+                             ap->regs.empty() ? 0 : ap->cells.ncells, fine->ncomp, ratio, ap->vec};
+            const RefluxArgs ra{crse->level_ptr(1 - c), rp ? (const CCell *)rp->d_cells.p : nullptr,
+                                rp ? (int)rp->cells.size() : 0, rp ? (const CFace *)rp->d_faces.p : nullptr,
+                                crse->ncomp, rp ? (const double *)rp->d_regc.p : nullptr,
+                                rp ? (const double *)rp->d_regf.p : nullptr};
+            if (!body && !(body = log.before(3, aa.ncells + ra.ncell > 0)))
+                body = launch_avg_reflux(crse->dtype, aa, ra, s) == cudaSuccess
                            ? 0
-                           : fail(MF_ECUDA, "reflux launch failed");
+                           : fail(MF_ECUDA, "average-down / reflux launch failed");
             c = 1 - c;
         }
         if ((rc = capture_end(crse, key, body))) return rc;

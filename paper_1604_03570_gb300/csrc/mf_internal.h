@@ -284,6 +284,41 @@ cudaError_t launch_interp(int dtype, void *fbase, const void *cold, const void *
 cudaError_t launch_avgdown(int dtype, const void *fbase, void *cbase, const AvgRegion *regs, const int *rstart,
                            const int *wfirst, int nregs, int ncells, int ncomp, int ratio, bool vec, cudaStream_t s);
 
+// Paired launches of the two-level advance (two independent jobs, one launch each would take).
+struct InterpArgs {
+    void *fbase;
+    const void *cold, *cnew;
+    const InterpRun *runs;
+    const int *rstart, *wfirst;
+    int nruns, ncells, ncomp, ratio;
+    double alpha;
+};
+struct AvgArgs {
+    const void *fbase;
+    void *cbase;
+    const AvgRegion *regs;
+    const int *rstart, *wfirst;
+    int nregs, ncells, ncomp, ratio;
+    bool vec;
+};
+struct RefluxArgs {
+    void *base;
+    const CCell *cells;
+    int ncell;
+    const CFace *faces;
+    int ncomp;
+    const double *regc, *regf;
+};
+// a fine level's ghost fill and its coarse-fine interpolation (disjoint ghost cells)
+cudaError_t launch_fill_interp(int dtype, const LevelPtrs &lv, const FbTask *tasks, int ntasks, const InterpArgs &ia,
+                               cudaStream_t s);
+// a fill of the new coarse level and the coarse face fluxes of the old one
+cudaError_t launch_fill_cflux(int dtype, int R, const LevelPtrs &lv, const FbTask *tasks, int ntasks,
+                              const void *cbase, const CFace *faces, int nface, int ncomp, const RefluxW &w,
+                              double *reg, cudaStream_t s);
+// the average-down (covered coarse cells) and the flux correction (uncovered ones)
+cudaError_t launch_avg_reflux(int dtype, const AvgArgs &aa, const RefluxArgs &ra, cudaStream_t s);
+
 int sm_count();
 
 // Sets the message mf_last_error() returns on this thread; returns code.

@@ -69,24 +69,46 @@ __device__ __forceinline__ void fill_copy(E *base, const FbTask &tk, int lane, i
         if (off + lane + 32 * u < tk.count) db[dof[u]] = v[u];
 }
 
+// Jobs: the work of one kernel, run by a range of a launch's blocks.  run(b, nb) does what block
+// b of an nb-block launch of that kernel does, so one kernel body serves its own launch and a
+// shared one (k_pair: two jobs that neither read what the other writes nor write the same
+// cells, in one launch).
+
 template <typename E>
-__global__ void __launch_bounds__(256) k_fill(LevelPtrs lv, const FbTask *__restrict__ tasks, int ntasks) {
-    constexpr int W = (int)(sizeof(FbTask) / 8);
-    const int lane = threadIdx.x & 31;
-    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
-    for (int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); t < ntasks; t += nwarps) {
-        unsigned long long word = 0;
-        if (lane < W) word = __ldg((const unsigned long long *)(tasks + t) + lane);
-        FbTaskWords h;
+struct FillJob {
+    LevelPtrs lv;
+    const FbTask *tasks;
+    int ntasks;
+    __device__ __forceinline__ void run(int b, int nb) const {
+        constexpr int W = (int)(sizeof(FbTask) / 8);
+        const int lane = threadIdx.x & 31;
+        const int nwarps = (int)(((unsigned)nb * blockDim.x) >> 5);
+        for (int t = (int)(((unsigned)b * blockDim.x + threadIdx.x) >> 5); t < ntasks; t += nwarps) {
+            unsigned long long word = 0;
+            if (lane < W) word = __ldg((const unsigned long long *)(tasks + t) + lane);
+            FbTaskWords h;
 #pragma unroll
-        for (int i = 0; i < W; ++i) h.w[i] = __shfl_sync(0xffffffffu, word, i);
-        if (h.t.vec) {  // two halves of 4 vectors per lane (registers)
-            fill_copy<uint4, kFillCellsPerLane / 2>((uint4 *)lv.base[h.t.level], h.t, lane, 0);
-            fill_copy<uint4, kFillCellsPerLane / 2>((uint4 *)lv.base[h.t.level], h.t, lane, 16 * kFillCellsPerLane);
-        } else {
-            fill_copy<E, kFillCellsPerLane>((E *)lv.base[h.t.level], h.t, lane, 0);
+            for (int i = 0; i < W; ++i) h.w[i] = __shfl_sync(0xffffffffu, word, i);
+            if (h.t.vec) {  // two halves of 4 vectors per lane (registers)
+                fill_copy<uint4, kFillCellsPerLane / 2>((uint4 *)lv.base[h.t.level], h.t, lane, 0);
+                fill_copy<uint4, kFillCellsPerLane / 2>((uint4 *)lv.base[h.t.level], h.t, lane, 16 * kFillCellsPerLane);
+            } else {
+                fill_copy<E, kFillCellsPerLane>((E *)lv.base[h.t.level], h.t, lane, 0);
+            }
         }
     }
+};
+
+template <typename E>
+__global__ void __launch_bounds__(256) k_fill(LevelPtrs lv, const FbTask *__restrict__ tasks, int ntasks) {
+    FillJob<E>{lv, tasks, ntasks}.run(blockIdx.x, gridDim.x);
+}
+
+// Two jobs in one launch: blocks [0, na) run a, the rest run b.
+template <typename J1, typename J2>
+__global__ void __launch_bounds__(256) k_pair(J1 a, int na, J2 b) {
+    if ((int)blockIdx.x < na) a.run(blockIdx.x, na);
+    else b.run((int)blockIdx.x - na, (int)gridDim.x - na);
 }
 
 // Per-box baseline: the entries of one destination box, one thread per cell.
@@ -204,13 +226,25 @@ __device__ __forceinline__ double line_flux(const S *low, long long dstride) {
 }
 
 template <typename S, int R>
+struct CFluxJob {
+    const S *base;
+    const CFace *faces;
+    int n, ncomp;
+    RefluxW w;
+    double *reg;
+    __device__ __forceinline__ void run(int b, int nb) const {
+        for (int i = b * blockDim.x + threadIdx.x; i < n * ncomp; i += nb * blockDim.x) {
+            const int e = i / ncomp, c = i - e * ncomp;
+            const CFace f = faces[e];
+            reg[i] = __dmul_rn(w.w[c], line_flux<S, R>(base + f.c_low + c * f.cstride, f.dstride));
+        }
+    }
+};
+
+template <typename S, int R>
 __global__ void __launch_bounds__(256) k_cf_coarse_flux(const S *__restrict__ base, const CFace *__restrict__ faces,
                                                         int n, int ncomp, RefluxW w, double *reg) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * ncomp; i += gridDim.x * blockDim.x) {
-        const int e = i / ncomp, c = i - e * ncomp;
-        const CFace f = faces[e];
-        reg[i] = __dmul_rn(w.w[c], line_flux<S, R>(base + f.c_low + c * f.cstride, f.dstride));
-    }
+    CFluxJob<S, R>{base, faces, n, ncomp, w, reg}.run(blockIdx.x, gridDim.x);
 }
 
 // NFF = r^2 fine faces per coarse face, a compile-time count so that all their loads issue
@@ -237,20 +271,33 @@ __global__ void __launch_bounds__(256) k_cf_fine_flux(const S *__restrict__ base
 }
 
 template <typename S>
+struct RefluxJob {
+    S *base;
+    const CCell *cells;
+    int ncell;
+    const CFace *faces;
+    int ncomp;
+    const double *regc, *regf;
+    __device__ __forceinline__ void run(int b, int nb) const {
+        for (int i = b * blockDim.x + threadIdx.x; i < ncell * ncomp; i += nb * blockDim.x) {
+            const int j = i / ncomp, c = i - j * ncomp;
+            const CCell cl = cells[j];
+            double corr = 0.0;
+            for (int e = cl.efirst; e < cl.efirst + cl.ecount; ++e) {
+                const double d = __dsub_rn(regf[(long long)e * ncomp + c], regc[(long long)e * ncomp + c]);
+                corr = __dadd_rn(corr, faces[e].sc > 0 ? d : -d);
+            }
+            S *p = base + cl.c_elem + c * cl.cstride;
+            from_f64(p, __dadd_rn(to_f64(*p), corr));
+        }
+    }
+};
+
+template <typename S>
 __global__ void __launch_bounds__(256) k_reflux_apply(S *base, const CCell *__restrict__ cells, int ncell,
                                                       const CFace *__restrict__ faces, int ncomp,
                                                       const double *__restrict__ regc, const double *__restrict__ regf) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell * ncomp; i += gridDim.x * blockDim.x) {
-        const int j = i / ncomp, c = i - j * ncomp;
-        const CCell cl = cells[j];
-        double corr = 0.0;
-        for (int e = cl.efirst; e < cl.efirst + cl.ecount; ++e) {
-            const double d = __dsub_rn(regf[(long long)e * ncomp + c], regc[(long long)e * ncomp + c]);
-            corr = __dadd_rn(corr, faces[e].sc > 0 ? d : -d);
-        }
-        S *p = base + cl.c_elem + c * cl.cstride;
-        from_f64(p, __dadd_rn(to_f64(*p), corr));
-    }
+    RefluxJob<S>{base, cells, ncell, faces, ncomp, regc, regf}.run(blockIdx.x, gridDim.x);
 }
 
 static int blocks_for(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 65535)); }
@@ -509,46 +556,61 @@ __device__ __forceinline__ void lin_w(int i, int r, int &k0, A &w1) {
 // coarse points, accumulated z, y, x ascending with the weight product (wz wy) wx -- the
 // arithmetic of the storage type's native precision (FP64 for FP64, FP32 otherwise).
 template <typename S>
+struct InterpJob {
+    S *fbase;
+    const S *cold, *cnew;
+    const InterpRun *runs;
+    const int *rstart, *wfirst;
+    int nruns, ncells, ncomp, ratio;
+    double alpha;
+    __device__ __forceinline__ void run(int b, int nb) const {
+        using A = typename NativeArith<S>::T;
+        using O = Ar<A>;
+        const A a1 = (A)alpha, a0 = (A)(1.0 - alpha);
+        const int nw = (ncells + 31) >> 5;
+        const int lane = threadIdx.x & 31;
+        for (int w = (b * blockDim.x + threadIdx.x) >> 5; w < nw; w += (nb * blockDim.x) >> 5) {
+            int q, t;
+            warp_segment(rstart, __ldg(wfirst + w), nruns, ncells, w << 5, q, t);
+            if ((w << 5) + lane >= ncells) continue;
+            const InterpRun run = runs[q];
+            int ix[3] = {run.I, run.J, run.K};
+            ix[run.axis] += t;
+            int kx, ky, kz;
+            A wx1, wy1, wz1;
+            lin_w(ix[0], ratio, kx, wx1);
+            lin_w(ix[1], ratio, ky, wy1);
+            lin_w(ix[2], ratio, kz, wz1);
+            const A wx[2] = {O::sub((A)1, wx1), wx1}, wy[2] = {O::sub((A)1, wy1), wy1},
+                    wz[2] = {O::sub((A)1, wz1), wz1};
+            const long long cb = run.cbase + (long long)kz * run.cplane + (long long)ky * run.cpx + kx;
+            S *fo = fbase + run.fdst + (long long)t * run.fstep;
+            for (int c = 0; c < ncomp; ++c) {
+                const S *po = cold + cb + (long long)c * run.ccs, *pn = cnew + cb + (long long)c * run.ccs;
+                A v = (A)0;
+#pragma unroll
+                for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+                    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                        for (int dx = 0; dx < 2; ++dx) {
+                            const int o = dz * run.cplane + dy * run.cpx + dx;
+                            const A tv = O::add(O::mul(a0, ld<S, A>(po + o)), O::mul(a1, ld<S, A>(pn + o)));
+                            v = O::add(v, O::mul(O::mul(O::mul(wz[dz], wy[dy]), wx[dx]), tv));
+                        }
+                st(fo + (long long)c * run.fcs, v);
+            }
+        }
+    }
+};
+
+template <typename S>
 __global__ void __launch_bounds__(256) k_interp(S *__restrict__ fbase, const S *__restrict__ cold,
                                                 const S *__restrict__ cnew, const InterpRun *__restrict__ runs,
                                                 const int *__restrict__ rstart, const int *__restrict__ wfirst,
                                                 int nruns, int ncells, int ncomp, int ratio, double alpha) {
-    using A = typename NativeArith<S>::T;
-    using O = Ar<A>;
-    const A a1 = (A)alpha, a0 = (A)(1.0 - alpha);
-    const int nw = (ncells + 31) >> 5;
-    const int lane = threadIdx.x & 31;
-    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw; w += (gridDim.x * blockDim.x) >> 5) {
-        int q, t;
-        warp_segment(rstart, __ldg(wfirst + w), nruns, ncells, w << 5, q, t);
-        if ((w << 5) + lane >= ncells) continue;
-        const InterpRun run = runs[q];
-        int ix[3] = {run.I, run.J, run.K};
-        ix[run.axis] += t;
-        int kx, ky, kz;
-        A wx1, wy1, wz1;
-        lin_w(ix[0], ratio, kx, wx1);
-        lin_w(ix[1], ratio, ky, wy1);
-        lin_w(ix[2], ratio, kz, wz1);
-        const A wx[2] = {O::sub((A)1, wx1), wx1}, wy[2] = {O::sub((A)1, wy1), wy1}, wz[2] = {O::sub((A)1, wz1), wz1};
-        const long long cb = run.cbase + (long long)kz * run.cplane + (long long)ky * run.cpx + kx;
-        S *fo = fbase + run.fdst + (long long)t * run.fstep;
-        for (int c = 0; c < ncomp; ++c) {
-            const S *po = cold + cb + (long long)c * run.ccs, *pn = cnew + cb + (long long)c * run.ccs;
-            A v = (A)0;
-#pragma unroll
-            for (int dz = 0; dz < 2; ++dz)
-#pragma unroll
-                for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-                    for (int dx = 0; dx < 2; ++dx) {
-                        const int o = dz * run.cplane + dy * run.cpx + dx;
-                        const A tv = O::add(O::mul(a0, ld<S, A>(po + o)), O::mul(a1, ld<S, A>(pn + o)));
-                        v = O::add(v, O::mul(O::mul(O::mul(wz[dz], wy[dy]), wx[dx]), tv));
-                    }
-            st(fo + (long long)c * run.fcs, v);
-        }
-    }
+    InterpJob<S>{fbase, cold, cnew, runs, rstart, wfirst, nruns, ncells, ncomp, ratio, alpha}.run(blockIdx.x,
+                                                                                                   gridDim.x);
 }
 
 // Vector load of the RR consecutive fine children along x (RR * sizeof(S) bytes, aligned to
@@ -582,61 +644,74 @@ __device__ __forceinline__ void ld_children(const S *p, S (&v)[RR]) {
 // coarse x, so each fine row is read as one contiguous span per warp.  A warp takes U
 // consecutive 32-cell chunks at a time with all their loads issued before the sums.
 template <typename S, int RR, bool VEC, int U>
+struct AvgJob {
+    const S *fbase;
+    S *cbase;
+    const AvgRegion *regs;
+    const int *rstart, *wfirst;
+    int nregs, ncells, ncomp;
+    __device__ __forceinline__ void run(int b, int nb) const {
+        using A = typename NativeArith<S>::T;
+        using O = Ar<A>;
+        const A inv = (A)(1.0 / (double)(RR * RR * RR));
+        const int nw = (ncells + 31) >> 5;
+        const int lane = threadIdx.x & 31;
+        const int nwarps = (nb * blockDim.x) >> 5;
+        for (int w0 = ((b * blockDim.x + threadIdx.x) >> 5) * U; w0 < nw; w0 += nwarps * U) {
+            bool act[U];
+            const S *fp[U];
+            S *cp[U];
+            int fpl[U], fpx[U], fcs[U], ccs[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int w = w0 + u;
+                act[u] = false;
+                if (w >= nw) continue;  // warp-uniform
+                int q, t;
+                warp_segment(rstart, __ldg(wfirst + w), nregs, ncells, w << 5, q, t);
+                if ((w << 5) + lane >= ncells) continue;
+                const AvgRegion rg = regs[q];
+                const int x = t % rg.n[0], yz = t / rg.n[0];
+                const int y = yz % rg.n[1], z = yz / rg.n[1];
+                fp[u] = fbase + rg.fsrc + (long long)z * RR * rg.fplane + (long long)y * RR * rg.fpx + x * RR;
+                cp[u] = cbase + rg.cdst + (long long)z * rg.cplane + (long long)y * rg.cpx + x;
+                fpl[u] = rg.fplane;
+                fpx[u] = rg.fpx;
+                fcs[u] = rg.fcs;
+                ccs[u] = rg.ccs;
+                act[u] = true;
+            }
+            for (int c = 0; c < ncomp; ++c) {
+                S v[U][RR * RR][RR];
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (act[u]) {
+                        const S *fc = fp[u] + (long long)c * fcs[u];
+#pragma unroll
+                        for (int r = 0; r < RR * RR; ++r)
+                            ld_children<S, RR, VEC>(fc + (long long)(r / RR) * fpl[u] + (long long)(r % RR) * fpx[u],
+                                                    v[u][r]);
+                    }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (act[u]) {
+                        A sum = (A)0;
+#pragma unroll
+                        for (int r = 0; r < RR * RR; ++r)
+#pragma unroll
+                            for (int dx = 0; dx < RR; ++dx) sum = O::add(sum, to_arith<A>(v[u][r][dx]));
+                        st(cp[u] + (long long)c * ccs[u], O::mul(sum, inv));
+                    }
+            }
+        }
+    }
+};
+
+template <typename S, int RR, bool VEC, int U>
 __global__ void __launch_bounds__(256) k_avgdown(const S *__restrict__ fbase, S *__restrict__ cbase,
                                                  const AvgRegion *__restrict__ regs, const int *__restrict__ rstart,
                                                  const int *__restrict__ wfirst, int nregs, int ncells, int ncomp) {
-    using A = typename NativeArith<S>::T;
-    using O = Ar<A>;
-    const A inv = (A)(1.0 / (double)(RR * RR * RR));
-    const int nw = (ncells + 31) >> 5;
-    const int lane = threadIdx.x & 31;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int w0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * U; w0 < nw; w0 += nwarps * U) {
-        bool act[U];
-        const S *fp[U];
-        S *cp[U];
-        int fpl[U], fpx[U], fcs[U], ccs[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int w = w0 + u;
-            act[u] = false;
-            if (w >= nw) continue;  // warp-uniform
-            int q, t;
-            warp_segment(rstart, __ldg(wfirst + w), nregs, ncells, w << 5, q, t);
-            if ((w << 5) + lane >= ncells) continue;
-            const AvgRegion rg = regs[q];
-            const int x = t % rg.n[0], yz = t / rg.n[0];
-            const int y = yz % rg.n[1], z = yz / rg.n[1];
-            fp[u] = fbase + rg.fsrc + (long long)z * RR * rg.fplane + (long long)y * RR * rg.fpx + x * RR;
-            cp[u] = cbase + rg.cdst + (long long)z * rg.cplane + (long long)y * rg.cpx + x;
-            fpl[u] = rg.fplane;
-            fpx[u] = rg.fpx;
-            fcs[u] = rg.fcs;
-            ccs[u] = rg.ccs;
-            act[u] = true;
-        }
-        for (int c = 0; c < ncomp; ++c) {
-            S v[U][RR * RR][RR];
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (act[u]) {
-                    const S *fc = fp[u] + (long long)c * fcs[u];
-#pragma unroll
-                    for (int r = 0; r < RR * RR; ++r)
-                        ld_children<S, RR, VEC>(fc + (long long)(r / RR) * fpl[u] + (long long)(r % RR) * fpx[u], v[u][r]);
-                }
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (act[u]) {
-                    A s = (A)0;
-#pragma unroll
-                    for (int r = 0; r < RR * RR; ++r)
-#pragma unroll
-                        for (int dx = 0; dx < RR; ++dx) s = O::add(s, to_arith<A>(v[u][r][dx]));
-                    st(cp[u] + (long long)c * ccs[u], O::mul(s, inv));
-                }
-        }
-    }
+    AvgJob<S, RR, VEC, U>{fbase, cbase, regs, rstart, wfirst, nregs, ncells, ncomp}.run(blockIdx.x, gridDim.x);
 }
 
 // ------------------------------------------------------------------ launchers
@@ -887,6 +962,111 @@ cudaError_t launch_avgdown(int dtype, const void *fbase, void *cbase, const AvgR
             avgdown_s<__nv_bfloat16>(fbase, cbase, regs, rstart, wfirst, nregs, ncells, ncomp, ratio, vec, s);
     }
     return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ paired launches
+// Two independent jobs of the two-level advance in one launch, each with the block count its
+// own launch would have; an empty job leaves the other to its own launcher.
+
+template <typename K>
+static int job_grid(K kernel, int blocks) {
+    return persistent_grid(kernel, 256, blocks);
+}
+
+template <typename J1, typename J2>
+static cudaError_t launch_pair(const J1 &a, int na, const J2 &b, int nb, cudaStream_t s) {
+    k_pair<J1, J2><<<na + nb, 256, 0, s>>>(a, na, b);
+    return cudaGetLastError();
+}
+
+template <typename E, typename S>
+static cudaError_t fill_interp_t(const LevelPtrs &lv, const FbTask *tasks, int ntasks, const InterpArgs &ia,
+                                 cudaStream_t s) {
+    const FillJob<E> a{lv, tasks, ntasks};
+    const InterpJob<S> b{(S *)ia.fbase, (const S *)ia.cold, (const S *)ia.cnew, ia.runs, ia.rstart, ia.wfirst,
+                         ia.nruns, ia.ncells, ia.ncomp, ia.ratio, ia.alpha};
+    return launch_pair(a, job_grid(k_fill<E>, (ntasks + 7) / 8), b,
+                       job_grid(k_interp<S>, (int)(((long long)ia.ncells + 255) / 256)), s);
+}
+
+cudaError_t launch_fill_interp(int dtype, const LevelPtrs &lv, const FbTask *tasks, int ntasks, const InterpArgs &ia,
+                               cudaStream_t s) {
+    if (ntasks == 0)
+        return launch_interp(dtype, ia.fbase, ia.cold, ia.cnew, ia.runs, ia.rstart, ia.wfirst, ia.nruns, ia.ncells,
+                             ia.ncomp, ia.ratio, ia.alpha, s);
+    if (ia.ncells == 0) return launch_fill(dtype, lv, tasks, ntasks, 0, s);
+    switch (dtype) {
+        case F64: return fill_interp_t<unsigned long long, double>(lv, tasks, ntasks, ia, s);
+        case F32: return fill_interp_t<unsigned int, float>(lv, tasks, ntasks, ia, s);
+        case BF16: return fill_interp_t<unsigned short, __nv_bfloat16>(lv, tasks, ntasks, ia, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename E, typename S, int R>
+static cudaError_t fill_cflux_t(const LevelPtrs &lv, const FbTask *tasks, int ntasks, const void *cbase,
+                                const CFace *faces, int nface, int ncomp, const RefluxW &w, double *reg,
+                                cudaStream_t s) {
+    const FillJob<E> a{lv, tasks, ntasks};
+    const CFluxJob<S, R> b{(const S *)cbase, faces, nface, ncomp, w, reg};
+    return launch_pair(a, job_grid(k_fill<E>, (ntasks + 7) / 8), b, blocks_for((long long)nface * ncomp), s);
+}
+
+template <typename E, typename S>
+static cudaError_t fill_cflux_s(int R, const LevelPtrs &lv, const FbTask *tasks, int ntasks, const void *cbase,
+                                const CFace *faces, int nface, int ncomp, const RefluxW &w, double *reg,
+                                cudaStream_t s) {
+    switch (R) {
+        case 1: return fill_cflux_t<E, S, 1>(lv, tasks, ntasks, cbase, faces, nface, ncomp, w, reg, s);
+        case 2: return fill_cflux_t<E, S, 2>(lv, tasks, ntasks, cbase, faces, nface, ncomp, w, reg, s);
+        case 4: return fill_cflux_t<E, S, 4>(lv, tasks, ntasks, cbase, faces, nface, ncomp, w, reg, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_fill_cflux(int dtype, int R, const LevelPtrs &lv, const FbTask *tasks, int ntasks,
+                              const void *cbase, const CFace *faces, int nface, int ncomp, const RefluxW &w,
+                              double *reg, cudaStream_t s) {
+    if (ntasks == 0) return launch_cf_coarse_flux(dtype, R, cbase, faces, nface, ncomp, w, reg, s);
+    if (nface == 0) return launch_fill(dtype, lv, tasks, ntasks, 0, s);
+    switch (dtype) {
+        case F64: return fill_cflux_s<unsigned long long, double>(R, lv, tasks, ntasks, cbase, faces, nface, ncomp, w, reg, s);
+        case F32: return fill_cflux_s<unsigned int, float>(R, lv, tasks, ntasks, cbase, faces, nface, ncomp, w, reg, s);
+        case BF16:
+            return fill_cflux_s<unsigned short, __nv_bfloat16>(R, lv, tasks, ntasks, cbase, faces, nface, ncomp, w, reg, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename S, int RR, bool VEC>
+static cudaError_t avg_reflux_t(const AvgArgs &aa, const RefluxArgs &ra, cudaStream_t s) {
+    constexpr int U = RR == 2 ? 2 : 1;
+    const AvgJob<S, RR, VEC, U> a{(const S *)aa.fbase, (S *)aa.cbase, aa.regs, aa.rstart, aa.wfirst, aa.nregs,
+                                  aa.ncells, aa.ncomp};
+    const RefluxJob<S> b{(S *)ra.base, ra.cells, ra.ncell, ra.faces, ra.ncomp, ra.regc, ra.regf};
+    return launch_pair(a, job_grid(k_avgdown<S, RR, VEC, U>, (int)(((long long)aa.ncells + 255) / 256)), b,
+                       blocks_for((long long)ra.ncell * ra.ncomp), s);
+}
+
+template <typename S>
+static cudaError_t avg_reflux_s(const AvgArgs &aa, const RefluxArgs &ra, cudaStream_t s) {
+    if (aa.ratio == 2) return aa.vec ? avg_reflux_t<S, 2, true>(aa, ra, s) : avg_reflux_t<S, 2, false>(aa, ra, s);
+    return aa.vec ? avg_reflux_t<S, 4, true>(aa, ra, s) : avg_reflux_t<S, 4, false>(aa, ra, s);
+}
+
+cudaError_t launch_avg_reflux(int dtype, const AvgArgs &aa, const RefluxArgs &ra, cudaStream_t s) {
+    if (ra.ncell == 0)
+        return launch_avgdown(dtype, aa.fbase, aa.cbase, aa.regs, aa.rstart, aa.wfirst, aa.nregs, aa.ncells, aa.ncomp,
+                              aa.ratio, aa.vec, s);
+    if (aa.ncells == 0)
+        return launch_reflux_apply(dtype, ra.base, ra.cells, ra.ncell, ra.faces, ra.ncomp, ra.regc, ra.regf, s);
+    if (aa.ratio != 2 && aa.ratio != 4) return cudaErrorInvalidValue;
+    switch (dtype) {
+        case F64: return avg_reflux_s<double>(aa, ra, s);
+        case F32: return avg_reflux_s<float>(aa, ra, s);
+        case BF16: return avg_reflux_s<__nv_bfloat16>(aa, ra, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace mfk
