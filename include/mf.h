@@ -182,6 +182,28 @@ int mf_set_schedule(mf_t *mf, const int in[3]);
  * wave of CTAs. */
 int mf_get_schedule(const mf_t *mf, int out[7]);
 
+/* Tile shapes per box-size class (Sec. 3.2: the tile size may change from loop to loop; here it
+ * may also change with the size of the box, within one launch).  A box's class is its y extent:
+ * up to 8, 16, 32 or 64 cells, or above (classes 0-4).  mf_set_class_tile gives the boxes of
+ * class cls the tile y extent ty and, where the level's tile has a z extent, the z extent tz
+ * (0 = the whole box, -1 = the level's tile shape); it turns the autotuner off, and mf_set_tile
+ * resets every class to -1.  mf_get_class_tiles writes per class {1 if the level has boxes of
+ * that class else 0, ty, tz}.  Results do not depend on the tile shapes (identical bits).  The
+ * autotuner, after choosing the level's schedule, times other shapes for each class holding at
+ * least 5% of the cells and keeps those that make the launch faster by more than 2%.
+ * MF_EINVAL for a class or extent out of range. */
+int mf_set_class_tile(mf_t *mf, int cls, int ty, int tz);
+int mf_get_class_tiles(const mf_t *mf, int out[15]);
+
+/* The autotuner keeps its choice per level geometry, storage type, components, ghost width,
+ * radius, arithmetic, kernel and GPU for the life of the process.  When the environment variable
+ * MF_AUTOTUNE_CACHE names a file, choices are also read from that file and appended to it, one
+ * text line each (the key, then tile[3], rows, ring slots, group bytes, push, and the per-class
+ * y and z extents), so that a later process skips the timing runs; unreadable lines are
+ * ignored.  mf_autotune_cache_reset forgets the process's choices (the file, if any, is read
+ * again at the next lookup).  Host only; always returns 0. */
+int mf_autotune_cache_reset(void);
+
 /*
  * Dense host arrays are (ncomp, Nz, Ny, Nx) doubles over the whole domain, x fastest.
  * mf_copy_from_host writes the valid cells of every box of the current time level

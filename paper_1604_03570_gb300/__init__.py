@@ -34,7 +34,8 @@ EXPORTS = [
     "mf_phase_ms", "mf_set_kernel", "mf_sum_strided_noalloc", "mf_get_schedule", "mf_launch_count",
     "mf_fp64_fma_rate", "mf_set_schedule", "mf_reduce", "mf_stage_bytes", "mf_attach_stage",
     "mf_rk3_advance", "mf_interp_cells", "mf_reflux_faces", "mf_avgdown_cells", "mf_create_regional",
-    "mf_box_regions", "mf_nregions", "mf_get_regions",
+    "mf_box_regions", "mf_nregions", "mf_get_regions", "mf_set_class_tile", "mf_get_class_tiles",
+    "mf_autotune_cache_reset",
 ]
 
 
@@ -99,6 +100,9 @@ def _load():
         "mf_box_regions": (I, [P, I, I, P, P]),
         "mf_nregions": (I, [P]),
         "mf_get_regions": (I, [P, P, P]),
+        "mf_set_class_tile": (I, [P, I, I, I]),
+        "mf_get_class_tiles": (I, [P, P]),
+        "mf_autotune_cache_reset": (I, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -178,6 +182,21 @@ def mf_get_regions(h):
     of = np.zeros(mf_nboxes(h), dtype=np.int32)
     _check(lib.mf_get_regions(h, _ptr(regs), _ptr(of)))
     return regs, of
+
+
+def mf_set_class_tile(h, cls, ty, tz):
+    _check(lib.mf_set_class_tile(h, int(cls), int(ty), int(tz)))
+
+
+def mf_get_class_tiles(h):
+    """{class: (ty, tz)} for the box-size classes present on the level (-1: the level's shape)."""
+    out = np.zeros(15, dtype=np.int32)
+    _check(lib.mf_get_class_tiles(h, _ptr(out)))
+    return {k: (int(out[3 * k + 1]), int(out[3 * k + 2])) for k in range(5) if out[3 * k]}
+
+
+def mf_autotune_cache_reset():
+    _check(lib.mf_autotune_cache_reset())
 
 
 def mf_destroy(h):
@@ -342,7 +361,8 @@ def mf_get_schedule(h):
     out = np.zeros(7, dtype=np.int32)
     _check(lib.mf_get_schedule(h, _ptr(out)))
     return {"tile": tuple(int(v) for v in out[:3]), "rows": int(out[3]), "stages": int(out[4]),
-            "kernel": "tma" if out[5] == MF_KERNEL_TMA else "global", "group_bytes": int(out[6])}
+            "kernel": "tma" if out[5] == MF_KERNEL_TMA else "global", "group_bytes": int(out[6]),
+            "class_tiles": {k: v for k, v in mf_get_class_tiles(h).items() if v != (-1, -1)}}
 
 
 def mf_set_timing(h, on):

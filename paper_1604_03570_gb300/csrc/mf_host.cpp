@@ -27,6 +27,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -277,6 +278,10 @@ struct mf {
     // tiles
     int tile[3] = {0, 0, 0};
     bool tile_auto = true;
+    // tile shapes per box-size class (tile_class): the y and z tile extents of the boxes of a
+    // class, -1 for the level's (tile[1], tile[2]); a z override applies only where the level's
+    // tile has a z extent (with a whole-box z extent the balanced schedule splits every box)
+    int cty[kTileClasses] = {-1, -1, -1, -1, -1}, ctz[kTileClasses] = {-1, -1, -1, -1, -1};
     std::vector<Tile> tiles;
     int block[2] = {32, 8};
     // attach
@@ -513,12 +518,22 @@ static int build_fb(mf_t *m) {
 
 // ------------------------------------------------------------------ tiles
 
+// The box-size class of an FArrayBox for its tile shape: its y extent up to 8, 16, 32, 64 cells,
+// or above.
+static int tile_class(const FabInfo &f) {
+    const int ny = f.n[1];
+    return ny <= 8 ? 0 : ny <= 16 ? 1 : ny <= 32 ? 2 : ny <= 64 ? 3 : 4;
+}
+
 static void make_tiles(const mf_t *m, const int tile[3], std::vector<Tile> &out) {
     out.clear();
     for (int b = 0; b < (int)m->boxes.size(); ++b) {
         const FabInfo &f = m->fabs[b];
+        const int k = tile_class(f);
+        int sh[3] = {tile[0], m->cty[k] >= 0 ? m->cty[k] : tile[1], tile[2]};
+        if (tile[2] > 0 && m->ctz[k] >= 0) sh[2] = m->ctz[k];
         int t[3];
-        for (int d = 0; d < 3; ++d) t[d] = (tile[d] <= 0 || tile[d] > f.n[d]) ? f.n[d] : tile[d];
+        for (int d = 0; d < 3; ++d) t[d] = (sh[d] <= 0 || sh[d] > f.n[d]) ? f.n[d] : sh[d];
         for (int c = 0; c < m->ncomp; ++c)
             for (int z = 0; z < f.n[2]; z += t[2])
                 for (int y = 0; y < f.n[1]; y += t[1])
@@ -937,9 +952,32 @@ extern "C" int mf_set_tile(mf_t *m, const int tile[3]) {
         if (tile[d] > 32767) return fail(MF_EINVAL, "tile size too large");
     m->tile_auto = false;
     m->push_pref = true;
+    for (int k = 0; k < kTileClasses; ++k) m->cty[k] = m->ctz[k] = -1;
     int rc = set_tiles(m, tile);
     if (rc) return rc;
     m->tma_R = 0;
+    return 0;
+}
+
+extern "C" int mf_set_class_tile(mf_t *m, int cls, int ty, int tz) {
+    if (!m) return fail(MF_EINVAL, "null handle");
+    if (cls < 0 || cls >= kTileClasses) return fail(MF_EINVAL, "class must be in [0, %d)", kTileClasses);
+    if (ty < -1 || tz < -1 || ty > 32767 || tz > 32767) return fail(MF_EINVAL, "tile extents must be -1, 0 or positive");
+    m->cty[cls] = ty;
+    m->ctz[cls] = tz;
+    m->tile_auto = false;
+    return set_tiles(m, m->tile);
+}
+
+extern "C" int mf_get_class_tiles(const mf_t *m, int out[3 * kTileClasses]) {
+    if (!m || !out) return fail(MF_EINVAL, "null argument");
+    int cells[kTileClasses] = {0};
+    for (auto &f : m->fabs) cells[tile_class(f)] = 1;
+    for (int k = 0; k < kTileClasses; ++k) {
+        out[3 * k] = cells[k];
+        out[3 * k + 1] = m->cty[k];
+        out[3 * k + 2] = m->ctz[k];
+    }
     return 0;
 }
 
@@ -1662,7 +1700,115 @@ static int check_stencil(const mf_t *m, const mf_stencil *st, double dt, double 
 // Autotune: time every candidate schedule -- tile shape, and for the TMA kernel rows per
 // thread and ring depth -- on the live data (current -> other level, which is scratch at this
 // point) and keep the fastest.  Synchronous; runs once per handle.
+// ------------------------------------------------------------------ autotuner schedule cache
+// The autotuner's choice per level geometry, kind of step and GPU, kept for the process and, when
+// the environment variable MF_AUTOTUNE_CACHE names a file, read from and appended to that file
+// (one line per choice: the key, then tile[3], rows, ring slots, group bytes, push, and the
+// per-class y and z tile extents), so that a level seen before skips the timing runs.
+struct TuneChoice {
+    int tile[3], rows, ns, gb, push;
+    int cty[kTileClasses], ctz[kTileClasses];
+};
+
+static std::mutex g_tune_mu;
+static std::map<std::string, TuneChoice> g_tune;
+static std::string g_tune_loaded;  // the file read into g_tune ("" = none)
+
+static std::string tune_key(const mf_t *m, int R, bool fp64diff, bool fix) {
+    unsigned long long h = 1469598103934665603ull;  // FNV-1a over the storage geometry
+    auto mix = [&](long long v) {
+        for (int i = 0; i < 8; ++i) {
+            h ^= (unsigned long long)((v >> (8 * i)) & 0xff);
+            h *= 1099511628211ull;
+        }
+    };
+    mix((long long)m->boxes.size());
+    for (auto &b : m->boxes)
+        for (int d = 0; d < 3; ++d) { mix(b.lo[d]); mix(b.hi[d]); }
+    for (int d = 0; d < 3; ++d) { mix(m->domain.lo[d]); mix(m->domain.hi[d]); }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    std::string name = cudaGetDeviceProperties(&prop, dev) == cudaSuccess ? prop.name : "gpu";
+    for (auto &ch : name)
+        if (ch == ' ' || ch == '\t') ch = '_';
+    char buf[256];
+    snprintf(buf, sizeof buf, "v1:%016llx:d%d:c%d:g%d:R%d:x%d:f%d:k%d:sm%d:%s", h, m->dtype, m->ncomp, m->ngrow, R,
+             (int)fp64diff, (int)fix, (int)m->use_tma, sm_count(), name.c_str());
+    return buf;
+}
+
+static void tune_load_locked() {
+    const char *path = getenv("MF_AUTOTUNE_CACHE");
+    if (!path || !*path || g_tune_loaded == path) return;
+    g_tune_loaded = path;
+    FILE *fp = fopen(path, "r");
+    if (!fp) return;
+    char line[1024];
+    while (fgets(line, sizeof line, fp)) {
+        char key[512];
+        TuneChoice c;
+        int n = 0;
+        if (sscanf(line, "%511s %d %d %d %d %d %d %d%n", key, &c.tile[0], &c.tile[1], &c.tile[2], &c.rows, &c.ns,
+                   &c.gb, &c.push, &n) != 8)
+            continue;
+        bool ok = true;
+        const char *q = line + n;
+        for (int k = 0; k < kTileClasses && ok; ++k) {
+            int used = 0;
+            ok = sscanf(q, "%d %d%n", &c.cty[k], &c.ctz[k], &used) == 2;
+            q += used;
+        }
+        if (ok) g_tune[key] = c;  // later lines win
+    }
+    fclose(fp);
+}
+
+static bool tune_get(const std::string &key, TuneChoice &c) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load_locked();
+    auto it = g_tune.find(key);
+    if (it == g_tune.end()) return false;
+    c = it->second;
+    return true;
+}
+
+static void tune_put(const std::string &key, const TuneChoice &c) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load_locked();
+    g_tune[key] = c;
+    const char *path = getenv("MF_AUTOTUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *fp = fopen(path, "a");
+    if (!fp) return;
+    fprintf(fp, "%s %d %d %d %d %d %d %d", key.c_str(), c.tile[0], c.tile[1], c.tile[2], c.rows, c.ns, c.gb, c.push);
+    for (int k = 0; k < kTileClasses; ++k) fprintf(fp, " %d %d", c.cty[k], c.ctz[k]);
+    fprintf(fp, "\n");
+    fclose(fp);
+}
+
+extern "C" int mf_autotune_cache_reset(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.clear();
+    g_tune_loaded.clear();
+    return 0;
+}
+
 static int autotune(mf_t *m, int R, bool fp64diff, const double *lam, bool fix = false) {
+    const std::string key = tune_key(m, R, fp64diff, fix);
+    {
+        TuneChoice c;
+        if (tune_get(key, c)) {
+            for (int k = 0; k < kTileClasses; ++k) { m->cty[k] = c.cty[k]; m->ctz[k] = c.ctz[k]; }
+            m->tma_rows = c.rows;
+            m->tma_ns_pref = c.ns;
+            m->tma_gb = c.gb;
+            m->tile_auto = false;
+            m->push_pref = c.push != 0;
+            return set_tiles(m, c.tile);
+        }
+    }
+    for (int k = 0; k < kTileClasses; ++k) m->cty[k] = m->ctz[k] = -1;
     auto tiles = tile_candidates(m);
     struct Cand { std::array<int, 3> t; int rows, ns, gb; };
     std::vector<Cand> cands;
@@ -1744,6 +1890,71 @@ static int autotune(mf_t *m, int R, bool fp64diff, const double *lam, bool fix =
     m->tile_auto = false;
     m->push_pref = true;
     int rc = time_cand(bc, 1, nullptr);  // installs the schedule (and builds its lists)
+    // Per box-size class (tile_class; Sec. 3.2: tile sizes per loop, here per box size within one
+    // launch): other y (and, with a tile z extent, z) extents for the boxes of one class, the
+    // other classes as chosen, kept where the level's launch gets faster by more than 2%.
+    // Classes holding at least 5% of the cells, largest first, on levels with two or more.
+    if (!rc && bc.t[0] == 0 && m->use_tma) {
+        double cells[kTileClasses] = {0}, total = 0;
+        int ymax[kTileClasses] = {0}, zmax[kTileClasses] = {0};
+        for (auto &f : m->fabs) {
+            const int k = tile_class(f);
+            const double v = (double)f.n[0] * f.n[1] * f.n[2];
+            cells[k] += v;
+            total += v;
+            ymax[k] = std::max(ymax[k], f.n[1]);
+            zmax[k] = std::max(zmax[k], f.n[2]);
+        }
+        int order[kTileClasses], nc = 0;
+        for (int k = 0; k < kTileClasses; ++k)
+            if (cells[k] > 0) order[nc++] = k;
+        std::sort(order, order + nc, [&](int a, int b) { return cells[a] > cells[b]; });
+        auto best_of = [&](float *ms) -> int {
+            float a = 0, b = 0;
+            int r = time_cand(bc, 6, &a);
+            if (!r) r = time_cand(bc, 6, &b);
+            *ms = std::min(a, b);
+            return r;
+        };
+        float cur = 0;
+        if (nc >= 2 && !(rc = best_of(&cur))) {
+            for (int oi = 0; oi < nc && !rc; ++oi) {
+                const int k = order[oi];
+                if (cells[k] < 0.05 * total) continue;
+                const int ty0 = m->cty[k], tz0 = m->ctz[k];
+                int bty = ty0, btz = tz0;
+                float best = cur;
+                // the class's candidates (a size at or above the class's largest extent is the
+                // whole box), each once, the current shape excluded
+                std::vector<std::pair<int, int>> cand;
+                for (int ty : {4, 8, 16, 32, 0})
+                    for (int tz : {8, 16, 32, 0}) {
+                        const int y = ty >= ymax[k] ? 0 : ty;
+                        const int z = bc.t[2] > 0 ? (tz >= zmax[k] ? 0 : tz) : -1;
+                        const int y0 = ty0 >= 0 ? ty0 : (bc.t[1] >= ymax[k] ? 0 : bc.t[1]);
+                        const int z0 = bc.t[2] > 0 ? (tz0 >= 0 ? tz0 : (bc.t[2] >= zmax[k] ? 0 : bc.t[2])) : -1;
+                        if ((y == y0 && z == z0) || std::find(cand.begin(), cand.end(), std::make_pair(y, z)) != cand.end())
+                            continue;
+                        cand.push_back({y, z});
+                    }
+                for (auto &yz : cand) {
+                    m->cty[k] = yz.first;
+                    m->ctz[k] = yz.second;
+                    float ms = 0;
+                    if ((rc = best_of(&ms))) break;
+                    if (ms < best * 0.98f) {
+                        best = ms;
+                        bty = yz.first;
+                        btz = yz.second;
+                    }
+                }
+                m->cty[k] = bty;
+                m->ctz[k] = btz;
+                cur = best;
+            }
+            if (!rc) rc = time_cand(bc, 1, nullptr);  // installs the per-class shapes
+        }
+    }
     // with that schedule, one step as the advance runs it: the ghost push and the residual fill,
     // or the face fill and the stencil alone, whichever is faster on this level
     if (!rc && m->use_tma && m->tma_ok && m->tma_push) {
@@ -1772,6 +1983,16 @@ static int autotune(mf_t *m, int R, bool fp64diff, const double *lam, bool fix =
             }
         }
         m->push_pref = tp <= tf;
+    }
+    if (!rc) {
+        TuneChoice c;
+        for (int d = 0; d < 3; ++d) c.tile[d] = m->tile[d];
+        c.rows = bc.rows;
+        c.ns = bc.ns;
+        c.gb = bc.gb;
+        c.push = m->push_pref ? 1 : 0;
+        for (int k = 0; k < kTileClasses; ++k) { c.cty[k] = m->cty[k]; c.ctz[k] = m->ctz[k]; }
+        tune_put(key, c);
     }
     return rc;
 }

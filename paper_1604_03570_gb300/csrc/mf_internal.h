@@ -121,6 +121,7 @@ struct StencilParams {
 
 constexpr int kMaxStages = 16;
 constexpr int kMaxPush = 16;  // ghost-push pieces per tile
+constexpr int kTileClasses = 5;  // box-size classes of the tile shapes (the host's tile_class)
 
 struct TmaFab {
     int bx, by;   // box of one plane load: bx elements of each of by rows

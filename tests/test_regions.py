@@ -137,3 +137,26 @@ def test_regional_create_rejects_overlapping_boxes():
     with pytest.raises(mf.MFError) as e:
         mf.mf_create_regional([0, 0, 0], [15, 15, 15], boxes, 1, 1, "f64", 32)
     assert e.value.code == mf.MF_EINVAL
+
+
+def test_class_tiles_are_checked_and_reported():
+    """Tile shapes per box-size class (the box's y extent: <= 8, 16, 32, 64, above): arguments
+    checked, the classes present reported, mf_set_tile resets them (host only)."""
+    boxes = synth.uneven_boxes(64, 96, base=32, quantum=8)
+    h = mf.mf_create_boxes([0, 0, 0], [63, 63, 63], boxes, 1, 1, "f32")
+    try:
+        ny = boxes[:, 4] - boxes[:, 1] + 1
+        present = {int(np.searchsorted([8, 16, 32, 64], v)) for v in ny}
+        assert set(mf.mf_get_class_tiles(h)) == present
+        assert all(v == (-1, -1) for v in mf.mf_get_class_tiles(h).values())
+        mf.mf_set_class_tile(h, 0, 4, 0)
+        assert mf.mf_get_class_tiles(h)[0] == (4, 0)
+        for bad in [(5, 4, 8), (-1, 4, 8), (0, -2, 8), (0, 4, -3)]:
+            with pytest.raises(mf.MFError) as e:
+                mf.mf_set_class_tile(h, *bad)
+            assert e.value.code == mf.MF_EINVAL
+        mf.mf_set_tile(h, (0, 8, 8))
+        assert all(v == (-1, -1) for v in mf.mf_get_class_tiles(h).values())
+    finally:
+        mf.mf_destroy(h)
+    assert mf.mf_autotune_cache_reset() is None
