@@ -696,13 +696,20 @@ __global__ void __launch_bounds__(TmaThreads<S, R, A, ROWS, GB>::value) k_stenci
             for (int pl = 0; pl < 2 * R; ++pl)
                 if (pl < R || pl >= t.tz + R) release(seq + pl);
 
+            // Two copies of the plane loop: the common case for the whole warp (x halos as
+            // vectors, no strip cell inside a group, whole-row stores, nothing to push) without
+            // the per-row tests, so that each plane is one basic block; and the general one.
+            const bool fast = kHV > 0 && hvec && plain_st && !__any_sync(0xffffffffu, cov != 0u) &&
+                              !__any_sync(0xffffffffu, fmask != 0u) && wm == 0u;
+            auto plane_loop = [&](auto fast_t) -> bool {
+                constexpr bool FAST = decltype(fast_t)::value;
             // unrolled by two at radius 1 (packed pairs) and 4, so that half the queue shifts become
             // register renames (at radius 2 the unrolled loop spills)
 #pragma unroll(kPair || R == 4 ? 2 : 1)
             for (int k = 0; k < t.tz; ++k) {
                 if (!__all_sync(0xffffffffu, wait_seq(seq + k + 2 * R))) {
                     if (lane == 0) atomicOr(p.err, 1);
-                    return;
+                    return false;
                 }
                 const S *newp = slot_ptr(seq + k + 2 * R);
                 const S *cp = slot_ptr(seq + k + R);
@@ -712,9 +719,9 @@ __global__ void __launch_bounds__(TmaThreads<S, R, A, ROWS, GB>::value) k_stenci
                 if constexpr (RK) {
 #pragma unroll
                     for (int r = 0; r < ROWS; ++r) {
-                        if (r >= nrow) continue;
+                        if (!FAST && r >= nrow) continue;
                         const S *urow = u0p + r * f.px;
-                        if (full) {
+                        if (FAST || full) {
                             V::ld(urow, u0v[r]);
                         } else {
 #pragma unroll
@@ -785,7 +792,7 @@ __global__ void __launch_bounds__(TmaThreads<S, R, A, ROWS, GB>::value) k_stenci
                 for (int r = 0; r < ROWS; ++r) {
                     // x window: w[i] = u(x0 - R + i), i = 0 .. VX + 2R - 1
                     A wx[VX + 2 * R];
-                    if (kHV > 0 && hvec) {
+                    if (FAST || (kHV > 0 && hvec)) {
 #pragma unroll
                         for (int j = 0; j < kHV; ++j) {
                             V16<S>::ld(cp + hl[r][0] + j * V16<S>::n, wx + j * V16<S>::n);
@@ -800,7 +807,7 @@ __global__ void __launch_bounds__(TmaThreads<S, R, A, ROWS, GB>::value) k_stenci
                     }
 #pragma unroll
                     for (int c = 0; c < VX; ++c) wx[R + c] = q[r][c][R];
-                    if (cov) {  // the box face is inside this group: x neighbours from the strips
+                    if (!FAST && cov) {  // the box face is inside this group: x neighbours from the strips
 #pragma unroll
                         for (int c = 0; c < VX; ++c)
                             if (cov & (1u << c)) wx[R + c] = ld_smem<S, A>(cp + cob + r * p.strip_w + c);
@@ -872,13 +879,23 @@ __global__ void __launch_bounds__(TmaThreads<S, R, A, ROWS, GB>::value) k_stenci
                     const A rka = (A)p.rk_a, rkb = (A)p.rk_b;
 #pragma unroll
                     for (int r = 0; r < ROWS; ++r) {
-                        if (r >= nrow) continue;
+                        if (!FAST && r >= nrow) continue;
 #pragma unroll
                         for (int c = 0; c < VX; ++c) out[r][c] = rk_combine<A>(out[r][c], u0v[r][c], rka, rkb);
                     }
                 }
-                store_plane(out, k, o);
+                if constexpr (FAST) {
+#pragma unroll
+                    for (int r = 0; r < ROWS; ++r) V::st(o + r * f.px, out[r]);
+                } else {
+                    store_plane(out, k, o);
+                }
             }
+                return true;
+            };
+            const bool ok_loop = (kHV > 0 && fast) ? plane_loop(std::integral_constant<bool, kHV != 0>{})
+                                                   : plane_loop(std::false_type{});
+            if (!ok_loop) return;
         }
         seq += (uint32_t)(t.tz + 2 * R);
     }
