@@ -580,11 +580,16 @@ __global__ void __launch_bounds__(TmaThreads<S, R, A, ROWS, GB>::value) k_stenci
             }
             for (int pl = 0; pl < 2 * R; ++pl)
                 if (pl < R || pl >= t.tz + R) release(seq + pl);
+            // as in the plain path below: a copy of the plane loop for the warp's common case (no
+            // strip cell inside a group, whole-row stores), one basic block per plane
+            const bool fast = (kHV == 0 || hvec) && plain_st && !__any_sync(0xffffffffu, cov != 0u);
+            auto plane_loop = [&](auto fast_t) -> bool {
+                constexpr bool FAST = decltype(fast_t)::value;
 #pragma unroll(2 * R + 1)
             for (int k = 0; k < t.tz; ++k) {
                 if (!__all_sync(0xffffffffu, wait_seq(seq + k + 2 * R))) {
                     if (lane == 0) atomicOr(p.err, 1);
-                    return;
+                    return false;
                 }
                 const S *newp = slot_ptr(seq + k + 2 * R);
                 const S *cp = slot_ptr(seq + k + R);
@@ -611,7 +616,7 @@ __global__ void __launch_bounds__(TmaThreads<S, R, A, ROWS, GB>::value) k_stenci
 #pragma unroll
                 for (int r = 0; r < ROWS; ++r) {
                     long long wx[VX + 2 * R];  // x window: wx[i] = K(x0 - R + i)
-                    if (kHV > 0 && hvec) {
+                    if (kHV > 0 && (FAST || hvec)) {
 #pragma unroll
                         for (int j = 0; j < kHV; ++j) {
                             V16<S>::template ld<long long>(cp + hl[r][0] + j * V16<S>::n, wx + j * V16<S>::n);
@@ -626,7 +631,7 @@ __global__ void __launch_bounds__(TmaThreads<S, R, A, ROWS, GB>::value) k_stenci
                     }
 #pragma unroll
                     for (int c = 0; c < VX; ++c) wx[R + c] = q[r][c][R];
-                    if (cov) {  // the box face is inside this group: x neighbours from the strips
+                    if (!FAST && cov) {  // the box face is inside this group: x neighbours from the strips
 #pragma unroll
                         for (int c = 0; c < VX; ++c)
                             if (cov & (1u << c)) wx[R + c] = cp[cob + r * p.strip_w + c];
@@ -663,6 +668,9 @@ __global__ void __launch_bounds__(TmaThreads<S, R, A, ROWS, GB>::value) k_stenci
                 op += f.plane;
                 store_plane(out, k, o);
             }
+                return true;
+            };
+            if (!(fast ? plane_loop(std::true_type{}) : plane_loop(std::false_type{}))) return;
             // the bit length of the largest |K'| of the output, per component, for the next
             // launch's grid: an OR over the warp, then an atomic OR
             omax = __reduce_or_sync(0xffffffffu, omax);
@@ -697,10 +705,9 @@ __global__ void __launch_bounds__(TmaThreads<S, R, A, ROWS, GB>::value) k_stenci
                 if (pl < R || pl >= t.tz + R) release(seq + pl);
 
             // Two copies of the plane loop: the common case for the whole warp (x halos as
-            // vectors, no strip cell inside a group, whole-row stores, nothing to push) without
-            // the per-row tests, so that each plane is one basic block; and the general one.
-            const bool fast = kHV > 0 && hvec && plain_st && !__any_sync(0xffffffffu, cov != 0u) &&
-                              !__any_sync(0xffffffffu, fmask != 0u) && wm == 0u;
+            // vectors, no strip cell inside a group, whole-row stores) without the per-row tests,
+            // so that each plane is one basic block; and the general one.
+            const bool fast = kHV > 0 && hvec && plain_st && !__any_sync(0xffffffffu, cov != 0u);
             auto plane_loop = [&](auto fast_t) -> bool {
                 constexpr bool FAST = decltype(fast_t)::value;
             // unrolled by two at radius 1 (packed pairs) and 4, so that half the queue shifts become
@@ -884,12 +891,7 @@ __global__ void __launch_bounds__(TmaThreads<S, R, A, ROWS, GB>::value) k_stenci
                         for (int c = 0; c < VX; ++c) out[r][c] = rk_combine<A>(out[r][c], u0v[r][c], rka, rkb);
                     }
                 }
-                if constexpr (FAST) {
-#pragma unroll
-                    for (int r = 0; r < ROWS; ++r) V::st(o + r * f.px, out[r]);
-                } else {
-                    store_plane(out, k, o);
-                }
+                store_plane(out, k, o);
             }
                 return true;
             };
