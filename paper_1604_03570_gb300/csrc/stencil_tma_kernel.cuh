@@ -581,7 +581,8 @@ __global__ void __launch_bounds__(TmaThreads<S, R, A, ROWS, GB>::value) k_stenci
             for (int pl = 0; pl < 2 * R; ++pl)
                 if (pl < R || pl >= t.tz + R) release(seq + pl);
             // as in the plain path below: a copy of the plane loop for the warp's common case (no
-            // strip cell inside a group, whole-row stores), one basic block per plane
+            // strip cell inside a group, whole-row stores), one basic block per plane (a third copy
+            // for tiles that push nothing measured slower here)
             const bool fast = (kHV == 0 || hvec) && plain_st && !__any_sync(0xffffffffu, cov != 0u);
             auto plane_loop = [&](auto fast_t) -> bool {
                 constexpr bool FAST = decltype(fast_t)::value;
@@ -704,12 +705,15 @@ __global__ void __launch_bounds__(TmaThreads<S, R, A, ROWS, GB>::value) k_stenci
             for (int pl = 0; pl < 2 * R; ++pl)
                 if (pl < R || pl >= t.tz + R) release(seq + pl);
 
-            // Two copies of the plane loop: the common case for the whole warp (x halos as
+            // Three copies of the plane loop: the common case for the whole warp (x halos as
             // vectors, no strip cell inside a group, whole-row stores) without the per-row tests,
-            // so that each plane is one basic block; and the general one.
+            // so that each plane is one basic block, once with plain row stores for warps that push
+            // nothing and once through the push; and the general one.
             const bool fast = kHV > 0 && hvec && plain_st && !__any_sync(0xffffffffu, cov != 0u);
-            auto plane_loop = [&](auto fast_t) -> bool {
-                constexpr bool FAST = decltype(fast_t)::value;
+            const bool nopush = !__any_sync(0xffffffffu, fmask != 0u) && wm == 0u;
+            auto plane_loop = [&](auto mode_t) -> bool {
+                constexpr int MODE = decltype(mode_t)::value;  // 0 general, 1 fast, 2 fast without push
+                constexpr bool FAST = MODE > 0;
             // unrolled by two at radius 1 (packed pairs) and 4, so that half the queue shifts become
             // register renames (at radius 2 the unrolled loop spills)
 #pragma unroll(kPair || R == 4 ? 2 : 1)
@@ -891,12 +895,18 @@ __global__ void __launch_bounds__(TmaThreads<S, R, A, ROWS, GB>::value) k_stenci
                         for (int c = 0; c < VX; ++c) out[r][c] = rk_combine<A>(out[r][c], u0v[r][c], rka, rkb);
                     }
                 }
-                store_plane(out, k, o);
+                if constexpr (MODE == 2) {
+#pragma unroll
+                    for (int r = 0; r < ROWS; ++r) V::st(o + r * f.px, out[r]);
+                } else {
+                    store_plane(out, k, o);
+                }
             }
                 return true;
             };
-            const bool ok_loop = (kHV > 0 && fast) ? plane_loop(std::integral_constant<bool, kHV != 0>{})
-                                                   : plane_loop(std::false_type{});
+            const bool ok_loop = !(kHV > 0 && fast) ? plane_loop(std::integral_constant<int, 0>{})
+                                 : nopush ? plane_loop(std::integral_constant<int, kHV != 0 ? 2 : 0>{})
+                                          : plane_loop(std::integral_constant<int, kHV != 0 ? 1 : 0>{});
             if (!ok_loop) return;
         }
         seq += (uint32_t)(t.tz + 2 * R);
