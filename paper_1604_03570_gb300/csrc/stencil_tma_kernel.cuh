@@ -706,10 +706,11 @@ __global__ void __launch_bounds__(TmaThreads<S, R, A, ROWS, GB>::value) k_stenci
                 if (pl < R || pl >= t.tz + R) release(seq + pl);
 
             // Three copies of the plane loop: the common case for the whole warp (x halos as
-            // vectors, no strip cell inside a group, whole-row stores) without the per-row tests,
+            // vectors where R cells fill them, no strip cell inside a group, whole-row stores)
+            // without the per-row tests,
             // so that each plane is one basic block, once with plain row stores for warps that push
             // nothing and once through the push; and the general one.
-            const bool fast = kHV > 0 && hvec && plain_st && !__any_sync(0xffffffffu, cov != 0u);
+            const bool fast = (kHV == 0 || hvec) && plain_st && !__any_sync(0xffffffffu, cov != 0u);
             const bool nopush = !__any_sync(0xffffffffu, fmask != 0u) && wm == 0u;
             auto plane_loop = [&](auto mode_t) -> bool {
                 constexpr int MODE = decltype(mode_t)::value;  // 0 general, 1 fast, 2 fast without push
@@ -803,7 +804,7 @@ __global__ void __launch_bounds__(TmaThreads<S, R, A, ROWS, GB>::value) k_stenci
                 for (int r = 0; r < ROWS; ++r) {
                     // x window: w[i] = u(x0 - R + i), i = 0 .. VX + 2R - 1
                     A wx[VX + 2 * R];
-                    if (FAST || (kHV > 0 && hvec)) {
+                    if (kHV > 0 && (FAST || hvec)) {
 #pragma unroll
                         for (int j = 0; j < kHV; ++j) {
                             V16<S>::ld(cp + hl[r][0] + j * V16<S>::n, wx + j * V16<S>::n);
@@ -904,9 +905,9 @@ __global__ void __launch_bounds__(TmaThreads<S, R, A, ROWS, GB>::value) k_stenci
             }
                 return true;
             };
-            const bool ok_loop = !(kHV > 0 && fast) ? plane_loop(std::integral_constant<int, 0>{})
-                                 : nopush ? plane_loop(std::integral_constant<int, kHV != 0 ? 2 : 0>{})
-                                          : plane_loop(std::integral_constant<int, kHV != 0 ? 1 : 0>{});
+            const bool ok_loop = !fast    ? plane_loop(std::integral_constant<int, 0>{})
+                                 : nopush ? plane_loop(std::integral_constant<int, 2>{})
+                                          : plane_loop(std::integral_constant<int, 1>{});
             if (!ok_loop) return;
         }
         seq += (uint32_t)(t.tz + 2 * R);
