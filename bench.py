@@ -57,6 +57,9 @@ def parse():
     p.add_argument("--c3-n", type=int, default=None,
                    help="with --only diff8th512: domain edge N instead of 512 (a smaller level to profile)")
     p.add_argument("--c3-dtype", default="f32,f64", help="with --only diff8th512: storage types to run")
+    p.add_argument("--c5", default=None,
+                   help="with --only manybox512: run one level, 'boxes,storage[,max_region]' (storage f32 or "
+                        "f64fixed), for profiling")
     p.add_argument("--plain", action="store_true",
                    help="headline as the untiled per-box sweep (MF_PLAIN_PER_BOX), for profiling the baseline")
     a = p.parse_args()
@@ -454,6 +457,9 @@ def manybox_line(mf, torch, flush, args, hbm):
     # per box)
     runs = ([(t, "f32", 0, 0) for t in cfg["targets"]] + [(t, "f64fixed", mf.MF_FIXED_DIFF, 0) for t in (4096, 32768)]
             + [(t, "f32", 0, 128) for t in (4096, 32768)] + [(32768, "f64fixed", mf.MF_FIXED_DIFF, 128)])
+    if args.only == "manybox512" and args.c5:
+        v = args.c5.split(",")
+        runs = [r for r in runs if r[0] == int(v[0]) and r[1] == v[1] and r[3] == (int(v[2]) if len(v) > 2 else 0)]
     for target, dtype, flags, max_region in runs:
         boxes = synth.uneven_boxes(N, target)
         g = mf.MultiFab([0, 0, 0], [N - 1] * 3, boxes=boxes, ncomp=C, ngrow=cfg["ngrow"],
