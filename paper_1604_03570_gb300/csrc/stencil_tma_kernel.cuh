@@ -671,7 +671,12 @@ __global__ void __launch_bounds__(TmaThreads<S, R, A, ROWS, GB>::value) k_stenci
             }
                 return true;
             };
-            if (!(fast ? plane_loop(std::true_type{}) : plane_loop(std::false_type{}))) return;
+            // (one-row schedules keep the single loop: the second copy slowed their general loop,
+            // which the many small tiles of a many-box level mostly take)
+            bool ok_loop;
+            if constexpr (ROWS > 1) ok_loop = fast ? plane_loop(std::true_type{}) : plane_loop(std::false_type{});
+            else ok_loop = plane_loop(std::false_type{});
+            if (!ok_loop) return;
             // the bit length of the largest |K'| of the output, per component, for the next
             // launch's grid: an OR over the warp, then an atomic OR
             omax = __reduce_or_sync(0xffffffffu, omax);
