@@ -1,12 +1,12 @@
 """GPU parity of the fixed-point-difference path (MF_FIXED_DIFF, FP64 storage) against the FP64
 oracle, through the C ABI.
 
-The path evaluates the same flux-form forward-Euler step as the FP64 kernel, with the Laplacian
-formed exactly in 64-bit integers on a per-step, per-component grid taken from the level maximum,
-and the update in one FP64 FMA.  Bars: max-norm relative error <= 1e-12 against the oracle
-(the benchmark spec), identical bits for every tile shape, box layout and schedule, the grid following a
-decaying solution (a Nyquist mode shrinking by 0.8 per step), zero and extreme-magnitude fields,
-and the rejection of what the path does not take.
+The path evaluates the same flux-form forward-Euler step as the FP64 kernel on a level held as
+64-bit fixed point inside an advance: the Laplacian formed exactly in 64-bit integers, the update
+rounded onto a per-step, per-component grid taken from the level maximum.  Bars: max-norm
+relative error <= 1e-12 against the FP64 oracle, identical bits for every tile shape, box layout
+and schedule, the grid following a decaying solution (a Nyquist mode shrinking by 0.8 per step),
+zero and extreme-magnitude fields, and the rejection of what the path does not take.
 """
 import math
 
