@@ -327,8 +327,8 @@ def stencil_phase(mfab, R, D, dt, nsteps, flags, steps, flush):
 
 
 def fixed_line(mf, torch, flush, args, hbm):
-    """The headline grid stored in FP64 with the differences in exact fixed-point integers and one
-    FP64 FMA per cell (MF_FIXED_DIFF): FP64-accurate results (<= 1e-12 of the oracle, checked by
+    """The headline grid stored in FP64 and stepped as 64-bit fixed point, exact integer
+    differences and an integer update (MF_FIXED_DIFF): FP64-accurate results (<= 1e-12 of the oracle, checked by
     the full-size tests) at memory speed.  Reports the step's fraction of the HBM roofline on
     the FP64 step bytes, the stencil kernel's own fraction, and the speedup over the plain
     per-box FP64 sweep (the untiled MFIter loop, FP64 arithmetic) and the batched FP64 one."""

@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(TmaThreads<S, R, A, ROWS, GB>::value) k_stenci
     // FP32 arithmetic at radius 2 and 4: the y and z face fluxes and the update of pairs of cells
     // through the packed instructions (face_flux2), the operations and order of the scalar code
     constexpr bool kPairR = std::is_same<A, float>::value && R > 1 && VX % 2 == 0;
-    // exact fixed-point differences, FP64 update (fixed_diff.cuh)
+    // exact fixed-point steps on 64-bit integers (fixed_diff.cuh)
     constexpr bool kFix = std::is_same<A, FixA>::value;
     static_assert(!kFix || (std::is_same<S, long long>::value && !RK), "fixed-point steps: 64-bit storage, plain steps");
     extern __shared__ unsigned char smem_raw[];
