@@ -465,6 +465,10 @@ def manybox_line(mf, torch, flush, args, hbm):
         g = mf.MultiFab([0, 0, 0], [N - 1] * 3, boxes=boxes, ncomp=C, ngrow=cfg["ngrow"],
                         dtype="f64" if flags else dtype, max_region=max_region or None)
         g.from_host(dense)
+        if args.only == "manybox512" and args.c5 and args.schedule:
+            v = [int(x) for x in args.schedule.split(",")]
+            g.set_tile(tuple(v[:3]))
+            mf.mf_set_schedule(g.h, *v[3:6])
         for _ in range(max(1, args.warmup)):
             g.advance(R, [1.0] * C, dt, n, flags)
         K = max(2, args.steps // 2)
