@@ -82,8 +82,8 @@ int mf_create(mf_t **out, const int domain_lo[3], const int domain_hi[3], int ma
 
 /*
  * mf_create_boxes -- a level from an explicit box list (nboxes * 6 ints).  Boxes must lie in
- * the domain and must not overlap; they need not cover the domain (a refined level, Sec. 3:
- * "not necessarily of equal size and shape", "do not necessarily span the entire domain").
+ * the domain and must not overlap; they need not cover the domain, nor be of one size or shape
+ * (a refined level, Sec. 3).
  */
 int mf_create_boxes(mf_t **out, const int domain_lo[3], const int domain_hi[3], const int *boxes,
                     int nboxes, int ncomp, int ngrow, int dtype);
