@@ -160,3 +160,20 @@ def test_class_tiles_are_checked_and_reported():
     finally:
         mf.mf_destroy(h)
     assert mf.mf_autotune_cache_reset() is None
+
+
+def test_region_edge_cases():
+    """Negative coordinates, a box larger than max_region (kept as its own region), and
+    max_region 1 (only single-cell boxes could share; none do)."""
+    boxes = np.array([[-8, -8, -8, -1, -1, -1], [0, -8, -8, 7, -1, -1],       # two 8^3 boxes side by side
+                      [-8, 0, -8, 7, 39, -1]], dtype=np.int32)              # a 16 x 40 x 8 slab
+    regs, of = mf.mf_box_regions(boxes, 16)
+    check_regions(boxes, regs, of, 16)
+    assert of[0] == of[1] and of[2] != of[0]                                   # the cubes merge, the slab stays
+    np.testing.assert_array_equal(regs[of[2]], boxes[2])
+    np.testing.assert_array_equal(regs[of[0]], [-8, -8, -8, 7, -1, -1])
+    regs, of = mf.mf_box_regions(boxes, 1)
+    assert len(regs) == 3
+    np.testing.assert_array_equal(regs[of], boxes)
+    one = mf.mf_box_regions(boxes[:1], 4)
+    np.testing.assert_array_equal(one[0], boxes[:1])
