@@ -289,6 +289,10 @@ struct mf {
     size_t bytes = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;    // private stream for graph capture
+    // a second capture stream and two events: a branch of the two-level advance's graph that runs
+    // beside the coarse stencil (the first fine substep)
+    cudaStream_t cap2 = nullptr;
+    cudaEvent_t fork_ev[2] = {nullptr, nullptr};
     int cur = 0;
     bool attached = false;
     DevBuf d_fabs, d_fb, d_fbtasks, d_tiles, d_cbeg, d_partials, d_sumout;
@@ -335,6 +339,9 @@ struct mf {
         graphs.clear();
         for (auto e : ev) cudaEventDestroy(e);
         if (cap) cudaStreamDestroy(cap);
+        if (cap2) cudaStreamDestroy(cap2);
+        for (auto e : fork_ev)
+            if (e) cudaEventDestroy(e);
         if (h_sum) cudaFreeHost(h_sum);
     }
     // Runge-Kutta stage level (slot 2), caller-owned like the two time levels
@@ -871,6 +878,9 @@ extern "C" int mf_attach(mf_t *m, void *dev_ptr, size_t bytes, void *stream) {
     m->stream = (cudaStream_t)stream;
     m->cur = 0;
     if (!m->cap) CU(cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking));
+    if (!m->cap2) CU(cudaStreamCreateWithFlags(&m->cap2, cudaStreamNonBlocking));
+    for (auto &e : m->fork_ev)
+        if (!e) CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     if (!m->h_sum) CU(cudaMallocHost((void **)&m->h_sum, sizeof(double)));
     int rc;
     if ((rc = m->d_fabs.upload(m->fabs, m->stream))) return rc;
@@ -2894,6 +2904,11 @@ extern "C" int mf_amr_advance(mf_t *crse, mf_t *fine, const mf_stencil *st, doub
         // fill with the interpolation, the fine face fluxes and the fine stencil, and last the
         // average-down with the flux correction.
         auto pair_kind = [](size_t a, size_t b, int ka, int kb) { return b ? kb : ka; };
+        // The first fine substep reads only the old coarse level (its interpolation is at
+        // alpha = 0), so in an untimed advance it runs as a graph branch beside the coarse stencil
+        // and the new coarse level's fill; the branches join before the second substep.
+        const bool branch = !log.timing && crse->cap2 && crse->fork_ev[0] && crse->fork_ev[1];
+        auto ev_ok = [](cudaError_t e) { return e == cudaSuccess ? 0 : fail(MF_ECUDA, "graph branch: %s", cudaGetErrorString(e)); };
         for (int step = 0; step < ncrse_steps && !body; ++step) {
             // the coarse ghosts read in this step: the stencil's faces (or, with the ghost push,
             // what the push does not deliver or the last average-down and correction made
@@ -2901,18 +2916,22 @@ extern "C" int mf_amr_advance(mf_t *crse, mf_t *fine, const mf_stencil *st, doub
             const int nface = rp ? (int)rp->faces.size() : 0;
             if (step == 0 || !cpush) body = fill(crse, c, af->d_first, af->t_first.size());
             else body = fill(crse, c, af->d_next, af->t_next.size());
-            if (!body && !(body = log.before(1))) body = enqueue_stencil(crse, c, R, fp64diff, lam_c, s, cpush);
-            // the new level's ghosts that the interpolation reads, and the coarse face fluxes at
-            // the interface from the old level (which the stencil only read)
-            const size_t npost = af->t_post.size();
-            if (!body && !(body = log.before(pair_kind(npost, (size_t)nface, 0, 2), npost + nface > 0)))
-                body = launch_fill_cflux(crse->dtype, R, level_ptrs(crse, 1 - c), (const FbTask *)af->d_post.p,
-                                         (int)npost, crse->level_ptr(c), rp ? (const CFace *)rp->d_faces.p : nullptr,
-                                         nface, crse->ncomp, wc, rp ? (double *)rp->d_regc.p : nullptr,
-                                         s) == cudaSuccess
-                           ? 0
-                           : fail(MF_ECUDA, "coarse fill / flux register launch failed");
-            for (int sub = 0; sub < nsub && !body; ++sub) {
+            auto coarse_part = [&]() -> int {
+                int b = log.before(1);
+                if (!b) b = enqueue_stencil(crse, c, R, fp64diff, lam_c, s, cpush);
+                // the new level's ghosts that the interpolation reads, and the coarse face fluxes
+                // at the interface from the old level (which the stencil only read)
+                const size_t npost = af->t_post.size();
+                if (!b && !(b = log.before(pair_kind(npost, (size_t)nface, 0, 2), npost + nface > 0)))
+                    b = launch_fill_cflux(crse->dtype, R, level_ptrs(crse, 1 - c), (const FbTask *)af->d_post.p,
+                                          (int)npost, crse->level_ptr(c), rp ? (const CFace *)rp->d_faces.p : nullptr,
+                                          nface, crse->ncomp, wc, rp ? (double *)rp->d_regc.p : nullptr,
+                                          s) == cudaSuccess
+                            ? 0
+                            : fail(MF_ECUDA, "coarse fill / flux register launch failed");
+                return b;
+            };
+            auto sub_step = [&](int sub, cudaStream_t ss) -> int {
                 // the fine level steps like a single level: a face fill first, then the push
                 // and the residual fill; the interpolation writes the coarse-fine ghosts
                 const bool face = (step == 0 && sub == 0) || !fpush;
@@ -2924,19 +2943,34 @@ extern "C" int mf_amr_advance(mf_t *crse, mf_t *fine, const mf_stencil *st, doub
                                     (const int *)ip->cells.d_wfirst.p, (int)ip->runs.size(), ip->cells.ncells,
                                     fine->ncomp, ratio, (double)sub / (double)nsub};
                 const size_t nip = ip->runs.empty() ? 0 : (size_t)ip->cells.ncells;
-                if (!(body = log.before(pair_kind(nft, nip, 0, 2), nft + nip > 0)))
-                    body = launch_fill_interp(fine->dtype, level_ptrs(fine, f), (const FbTask *)ft.p, (int)nft, ia,
-                                              s) == cudaSuccess
-                               ? 0
-                               : fail(MF_ECUDA, "fine fill / interpolation launch failed");
-                if (!body && rp && !(body = log.before(2, nface > 0)))  // fine face fluxes, this substep
-                    body = launch_cf_fine_flux(fine->dtype, R, fine->level_ptr(f), (const CFace *)rp->d_faces.p,
-                                               (const FFace *)rp->d_ff.p, nface, ratio * ratio, fine->ncomp, wf,
-                                               (double *)rp->d_regf.p, sub == 0, s) == cudaSuccess
-                               ? 0
-                               : fail(MF_ECUDA, "flux register launch failed");
-                if (!body && !(body = log.before(1))) body = enqueue_stencil(fine, f, R, fp64diff, lam_f, s, fpush);
+                int b = 0;
+                if (!(b = log.before(pair_kind(nft, nip, 0, 2), nft + nip > 0)))
+                    b = launch_fill_interp(fine->dtype, level_ptrs(fine, f), (const FbTask *)ft.p, (int)nft, ia,
+                                           ss) == cudaSuccess
+                            ? 0
+                            : fail(MF_ECUDA, "fine fill / interpolation launch failed");
+                if (!b && rp && !(b = log.before(2, nface > 0)))  // fine face fluxes, this substep
+                    b = launch_cf_fine_flux(fine->dtype, R, fine->level_ptr(f), (const CFace *)rp->d_faces.p,
+                                            (const FFace *)rp->d_ff.p, nface, ratio * ratio, fine->ncomp, wf,
+                                            (double *)rp->d_regf.p, sub == 0, ss) == cudaSuccess
+                            ? 0
+                            : fail(MF_ECUDA, "flux register launch failed");
+                if (!b && !(b = log.before(1))) b = enqueue_stencil(fine, f, R, fp64diff, lam_f, ss, fpush);
                 f = 1 - f;
+                return b;
+            };
+            if (!body && branch) {
+                cudaStream_t s2 = crse->cap2;
+                body = ev_ok(cudaEventRecord(crse->fork_ev[0], s));
+                if (!body) body = ev_ok(cudaStreamWaitEvent(s2, crse->fork_ev[0], 0));
+                if (!body) body = sub_step(0, s2);
+                if (!body) body = coarse_part();
+                if (!body) body = ev_ok(cudaEventRecord(crse->fork_ev[1], s2));
+                if (!body) body = ev_ok(cudaStreamWaitEvent(s, crse->fork_ev[1], 0));
+                for (int sub = 1; sub < nsub && !body; ++sub) body = sub_step(sub, s);
+            } else if (!body) {
+                body = coarse_part();
+                for (int sub = 0; sub < nsub && !body; ++sub) body = sub_step(sub, s);
             }
             // the average-down writes the covered coarse cells, the flux correction the uncovered
             // ones next to the interface

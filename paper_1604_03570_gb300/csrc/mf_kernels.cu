@@ -567,6 +567,9 @@ struct InterpJob {
         using A = typename NativeArith<S>::T;
         using O = Ar<A>;
         const A a1 = (A)alpha, a0 = (A)(1.0 - alpha);
+        // at alpha = 0 the new coarse level is not read: the first substep of a coarse step may
+        // run while that level is being computed (its value would only be scaled by 0)
+        const bool tnew = alpha != 0.0;
         const int nw = (ncells + 31) >> 5;
         const int lane = threadIdx.x & 31;
         for (int w = (b * blockDim.x + threadIdx.x) >> 5; w < nw; w += (nb * blockDim.x) >> 5) {
@@ -595,7 +598,8 @@ struct InterpJob {
 #pragma unroll
                         for (int dx = 0; dx < 2; ++dx) {
                             const int o = dz * run.cplane + dy * run.cpx + dx;
-                            const A tv = O::add(O::mul(a0, ld<S, A>(po + o)), O::mul(a1, ld<S, A>(pn + o)));
+                            const A tv = tnew ? O::add(O::mul(a0, ld<S, A>(po + o)), O::mul(a1, ld<S, A>(pn + o)))
+                                              : O::mul(a0, ld<S, A>(po + o));
                             v = O::add(v, O::mul(O::mul(O::mul(wz[dz], wy[dy]), wx[dx]), tv));
                         }
                 st(fo + (long long)c * run.fcs, v);
