@@ -195,8 +195,9 @@ int mf_get_schedule(const mf_t *mf, int out[7]);
 int mf_set_class_tile(mf_t *mf, int cls, int ty, int tz);
 int mf_get_class_tiles(const mf_t *mf, int out[15]);
 
-/* The autotuner keeps its choice per level geometry, storage type, components, ghost width,
- * radius, arithmetic, kernel and GPU for the life of the process.  When the environment variable
+/* The autotuner (Sec. 3.2 and Table 1: the tile size is a parameter whose best value depends on
+ * the machine and the loop) keeps its choice per level geometry, storage type, components, ghost
+ * width, radius, arithmetic, kernel and GPU for the life of the process.  When the environment variable
  * MF_AUTOTUNE_CACHE names a file, choices are also read from that file and appended to it, one
  * text line each (the key, then tile[3], rows, ring slots, group bytes, push, and the per-class
  * y and z extents), so that a later process skips the timing runs; unreadable lines are
