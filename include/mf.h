@@ -111,11 +111,12 @@ int mf_create_regional(mf_t **out, const int domain_lo[3], const int domain_hi[3
  * mf_create_boxes, assumed disjoint): returns their number, writes region_of[i], the region
  * of box i, and, when regions_out is not NULL (room for nboxes * 6 ints), the regions as
  * {lo[3], hi[3]}.  A region is either a rectangle its boxes cover exactly, every side at most
- * max_region, or a single box that no cut separates from the others. */
+ * max_region, or a single box that no cut separates from the others.  Sec. 2 (Fig. 2): regions
+ * are the contiguous blocks a grid's data is allocated in. */
 int mf_box_regions(const int *boxes, int nboxes, int max_region, int *regions_out, int *region_of);
-/* The storage of a level: its FArrayBoxes (the regions of a regional level, the boxes
- * otherwise) as {lo[3], hi[3]} into regions_out (room for mf_nregions * 6 ints), and the
- * FArrayBox of each box into region_of (room for mf_nboxes ints); either may be NULL. */
+/* The storage of a level (Sec. 2, Sec. 3.1): its FArrayBoxes (the regions of a regional level,
+ * the boxes otherwise) as {lo[3], hi[3]} into regions_out (room for mf_nregions * 6 ints), and
+ * the FArrayBox of each box into region_of (room for mf_nboxes ints); either may be NULL. */
 int mf_nregions(const mf_t *mf);
 int mf_get_regions(const mf_t *mf, int *regions_out, int *region_of);
 
@@ -125,7 +126,8 @@ int mf_get_regions(const mf_t *mf, int *regions_out, int *region_of);
  * ignored. */
 void mf_destroy(mf_t *mf);
 
-/* Layout queries (host only). */
+/* Layout queries (host only): the level's boxes, the grids of Sec. 3 (the BoxArray of
+ * Sec. 3.1), as {lo[3], hi[3]} each. */
 int mf_nboxes(const mf_t *mf);
 int mf_get_boxes(const mf_t *mf, int *boxes /* nboxes*6 */);
 /* Bytes of device memory mf_attach needs: two time levels of all FArrayBoxes, each
@@ -135,10 +137,10 @@ int mf_get_boxes(const mf_t *mf, int *boxes /* nboxes*6 */);
  * two time levels because the forward-Euler update of Sec. 4.1 is read out of place.
  * 0 for a NULL handle. */
 size_t mf_bytes(const mf_t *mf);
-/* Number of FillBoundary copy regions (box-box intersections incl. periodic images) and
- * the number of ghost cells per component they write. */
+/* Number of FillBoundary copy regions (box-box intersections incl. periodic images; Sec. 3.1's
+ * ghost exchange) and the number of ghost cells per component they write. */
 long long mf_fb_regions(const mf_t *mf, long long *ghost_cells_out);
-/* Copies up to max regions as 11 ints each: {dst box, src box, dst lo[3] (global index,
+/* Copies up to max regions (Sec. 3.1's intersection list) as 11 ints each: {dst box, src box, dst lo[3] (global index,
  * may lie outside the domain), src lo[3] (inside the domain), extent[3]}. */
 long long mf_get_fb_regions(const mf_t *mf, int *out, long long max);
 
@@ -162,13 +164,14 @@ int mf_attach(mf_t *mf, void *dev_ptr, size_t bytes, void *cuda_stream);
 int mf_set_tile(mf_t *mf, const int tile[3]);
 int mf_get_tile(const mf_t *mf, int tile[3]);
 
-/* Stencil kernel variant.  MF_KERNEL_TMA (default): tile planes staged into shared memory by
+/* Stencil kernel variant (how the Sec. 4.1 kernel reads its neighbours; the paper has one CPU
+ * kernel, so no counterpart of the choice).  MF_KERNEL_TMA (default): tile planes staged into shared memory by
  * TMA bulk-tensor copies (used whenever the tile shape fits, else the next one).
  * MF_KERNEL_GLOBAL: neighbours read through L1 from global memory.  Both give identical bits. */
 enum { MF_KERNEL_TMA = 0, MF_KERNEL_GLOBAL = 1 };
 int mf_set_kernel(mf_t *mf, int variant);
 
-/* Schedule of the TMA stencil besides the tile shape: in[0] rows per thread (1 or 2; 0 = 2),
+/* Schedule of the TMA stencil besides the tile shape (Sec. 3.2's tiling, GPU-side parameters): in[0] rows per thread (1 or 2; 0 = 2),
  * in[1] shared-memory ring slots (a power of two up to 16; 0 = by radius), in[2] bytes per
  * row group of a thread (16 or 32; 0 = 16).  Where a radius or storage type lacks the
  * combination the launch falls back to 16-byte groups and the rows the radius allows.
@@ -176,7 +179,7 @@ int mf_set_kernel(mf_t *mf, int variant);
  * it; MF_EINVAL for values out of range. */
 int mf_set_schedule(mf_t *mf, const int in[3]);
 
-/* The schedule in use (after the autotuner, if it ran): {tile x, y, z, rows per thread, ring
+/* The schedule in use (Sec. 3.2; after the autotuner, if it ran): {tile x, y, z, rows per thread, ring
  * slots, kernel variant in use (MF_KERNEL_*), bytes per row group of a thread (16 or 32)}.
  * A tile z extent of 0 means whole boxes, which the TMA kernel splits in z evenly over one
  * wave of CTAs. */
@@ -245,19 +248,22 @@ int mf_fill_boundary(mf_t *mf);
  */
 int mf_interp_cf(mf_t *fine, const mf_t *crse_old, const mf_t *crse_new, double alpha, int ratio);
 
-/* mf_interp_cells -- the number of fine ghost cells (per component) that mf_interp_cf writes:
+/* mf_interp_cells -- (Sec. 3, the interpolation of mf_interp_cf) the number of fine ghost cells
+ * (per component) that mf_interp_cf writes:
  * the ghost cells of the fine boxes whose point lies in no fine box.  *runs_out (may be NULL)
  * gets the number of runs of the interpolation work list.  Host lists only: needs no attached
  * memory.  Negative error code (MF_EINVAL) for a bad ratio or layouts that do not nest. */
 long long mf_interp_cells(const mf_t *fine, const mf_t *crse, int ratio, long long *runs_out);
 
-/* mf_avgdown_cells -- the number of coarse cells (per component) mf_average_down writes: the
+/* mf_avgdown_cells -- (Sec. 3, the average-down of mf_average_down) the number of coarse cells
+ * (per component) mf_average_down writes: the
  * coarse valid cells under the fine boxes.  *regions_out (may be NULL) gets the number of
  * (fine box, coarse box) regions of its work list.  Host lists only: needs no attached memory.
  * MF_EINVAL for a bad ratio, fine boxes not aligned to the ratio, or levels that do not nest. */
 long long mf_avgdown_cells(const mf_t *fine, const mf_t *crse, int ratio, long long *regions_out);
 
-/* mf_reflux_faces -- the number of coarse faces of the coarse-fine interface that the
+/* mf_reflux_faces -- (Sec. 3's subcycled levels, the refluxing of mf_amr_advance) the number of
+ * coarse faces of the coarse-fine interface that the
  * refluxing of mf_amr_advance (MF_REFLUX) corrects across: faces of coarse cells in no fine box
  * whose other side is covered by the fine level (periodic images included).  *cells_out (may
  * be NULL) gets the number of coarse cells corrected.  Host lists only: needs no attached
@@ -364,8 +370,9 @@ int mf_sum(mf_t *mf, int comp, double *out);
 enum { MF_RED_SUM = 0, MF_RED_MAX = 1, MF_RED_MIN = 2, MF_RED_NORM0 = 3, MF_RED_NORM1 = 4, MF_RED_NORM2 = 5 };
 int mf_reduce(mf_t *mf, int comp, int op, double *out);
 
-/* Algorithmic bytes per step of the sweep: S*C*(2V + 2G + G_face) (valid cells read and
- * written, ghost cells copied, face ghosts read by the stencil of radius R). */
+/* Algorithmic bytes per step of the sweep (Sec. 4.1's fill and kernel): S*C*(2V + 2G + G_face)
+ * (valid cells read and written, ghost cells copied, face ghosts read by the stencil of radius
+ * R). */
 double mf_step_bytes(const mf_t *mf, int R);
 
 /* Phase timing (Sec. 4.1 times the ghost fill and the kernel separately): when on, the
@@ -377,7 +384,8 @@ double mf_step_bytes(const mf_t *mf, int R);
 int mf_set_timing(mf_t *mf, int on);
 int mf_phase_ms(mf_t *mf, double out[2]);
 
-/* Kernel launches of the last mf_advance (or, on the coarse handle, mf_amr_advance) call:
+/* Kernel launches of the last mf_advance (or, on the coarse handle, mf_amr_advance) call
+ * (measurement support; the paper counts threads, not launches, so no counterpart):
  * out[0] ghost-fill (and, with MF_FIXED_DIFF, the three conversion passes), out[1] stencil,
  * out[2] coarse-fine interpolation and flux-register,
  * out[3] average-down and reflux launches.  Launches whose work list is empty are not made and not counted. */
@@ -387,12 +395,14 @@ int mf_launch_count(const mf_t *mf, int out[4]);
  * FMA): 8 independent FMA chains per thread, 8 CTAs of 256 threads per SM, best of three
  * timed launches on `stream` (cudaStream_t; NULL = legacy stream).  The ceiling of the FP64
  * sweep on parts whose FP64 rate is low next to their memory bandwidth.  Measurement support,
- * not part of the method; allocates and frees 8 bytes of device memory and synchronises. */
+ * not part of the method (no counterpart in the paper); allocates and frees 8 bytes of device memory and synchronises. */
 int mf_fp64_fma_rate(double *tflops, void *stream);
 
-/* Which time level (0 or 1) is current. */
+/* Which time level (0 or 1) is current (Sec. 4.1's out-of-place update alternates them). */
 int mf_current(const mf_t *mf);
 
+/* The thread-local message of the last failing call (error reporting: no counterpart in the
+ * paper). */
 const char *mf_last_error(void);
 
 /*
