@@ -177,3 +177,25 @@ def test_region_edge_cases():
     np.testing.assert_array_equal(regs[of], boxes)
     one = mf.mf_box_regions(boxes[:1], 4)
     np.testing.assert_array_equal(one[0], boxes[:1])
+
+
+def test_regional_step_bytes_count_the_regions_faces():
+    """mf_step_bytes of a regional level is the per-box formula S*C*(2V + 2G + G_face) on its
+    regions: the same valid cells, fewer ghost and face cells (host only)."""
+    lo, hi = [0, 0, 0], [63, 63, 63]
+    boxes = synth.uneven_boxes(64, 96, base=32, quantum=8)
+    a = mf.mf_create_boxes(lo, hi, boxes, 2, 2, "f32")
+    b = mf.mf_create_regional(lo, hi, boxes, 2, 2, "f32", 64)   # one region: the whole domain
+    try:
+        V = 64 ** 3
+        _, Ga = mf.mf_fb_regions(a)
+        _, Gb = mf.mf_fb_regions(b)
+        assert Gb == 68 ** 3 - 64 ** 3 and Gb < Ga
+        ext = boxes[:, 3:] - boxes[:, :3] + 1
+        face_a = int((2 * (ext[:, 0] * ext[:, 1] + ext[:, 1] * ext[:, 2] + ext[:, 0] * ext[:, 2])).sum()) * 2
+        face_b = 6 * 64 * 64 * 2
+        assert mf.mf_step_bytes(a, 2) == 4 * 2 * (2 * V + 2 * Ga + face_a)
+        assert mf.mf_step_bytes(b, 2) == 4 * 2 * (2 * V + 2 * Gb + face_b)
+    finally:
+        mf.mf_destroy(a)
+        mf.mf_destroy(b)
